@@ -1,0 +1,435 @@
+"""Pins for the CPU oracle (no GPU).
+
+Each test ties the oracle to something other than itself: the paper's printed
+per-level flop shares (Section 3, Fig. 5), closed forms of 2x2 cases, factors
+that are exact in binary64 (integer / dyadic constructions), exact rational
+brute force on tiny inputs, LAPACK through scipy, and the backward-error bound
+of the benchmark spec (residual / (n eps ||A||) <= 10).  The planted-mistake
+tests show that each check fails when a plausible error (a dropped update, a
+wrong sign, a transposed block, a swapped pivot) is put into the oracle's
+output.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.linalg.lapack as lapack
+
+from paper_1602_06763_gb300 import inputs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+EPS = 2.0 ** -53
+BOUND = 10.0
+
+
+def load(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+# ----------------------------------------------------------------------------
+# split rule and the paper's flop shares
+# ----------------------------------------------------------------------------
+
+def test_split_rule(oracle):
+    for n in range(2, 600):
+        n1 = oracle.split(n)
+        assert 0 < n1 < n
+        if n >= 16:
+            assert n1 % 8 == 0 and abs(n1 - n / 2) <= 4
+
+
+def _round_half_up(x, d):
+    q = 10 ** d
+    return math.floor(x * q + 0.5) / q
+
+
+def test_trtri_level_flop_shares_match_paper(oracle):
+    g = load("trtri_flop_shares.json")
+    # exact halving (a power-of-two multiple of 8) reproduces the paper's
+    # 2 (n/2)^3 / (n^3/3) derivation level by level
+    n = 2048
+    shares, total = oracle.trtri_level_flops(n, c=g["c_paper"], levels=4)
+    assert total == pytest.approx(n ** 3 / 3.0, rel=1e-12)
+    pct = 100.0 * shares / (n ** 3 / 3.0)
+    for got, want, d in zip(pct, g["shares_percent_printed"], g["printed_decimals"]):
+        assert _round_half_up(got, d) == pytest.approx(want)
+    # the paper's own size n = 2000 with the paper's split rule
+    shares, total = oracle.trtri_level_flops(g["n_paper"], c=g["c_paper"], levels=4)
+    pct = 100.0 * shares / (g["n_paper"] ** 3 / 3.0)
+    assert np.all(np.abs(pct - np.array(g["shares_percent_printed"])) < 0.06)
+    # TRMM + TRSM carry more than 99.6 % of the flops for c < 100
+    for c in (24, 99):
+        shares, total = oracle.trtri_level_flops(g["n_paper"], c=c, levels=64)
+        assert 100.0 * shares.sum() / total >= g["blas3_share_percent_at_least"]
+
+
+# ----------------------------------------------------------------------------
+# closed forms
+# ----------------------------------------------------------------------------
+
+def test_closed_forms_2x2(oracle):
+    g = load("closed_forms_2x2.json")
+    A = np.array(g["potrf"]["A"], order="F")
+    L, info = oracle.potrf(A, c=1)
+    assert info == 0
+    assert np.array_equal(np.tril(L), np.array(g["potrf"]["L"]))
+
+    A = np.array(g["getrf"]["A"], order="F")
+    LU, ipiv, info = oracle.getrf(A, c=1)
+    assert info == 0 and list(ipiv) == g["getrf"]["ipiv"]
+    assert LU[0, 0] == 3.0 and LU[0, 1] == 4.0
+    assert LU[1, 0] == 1.0 / 3.0                     # one correctly rounded division
+    assert abs(LU[1, 1] - 2.0 / 3.0) <= 2 * EPS      # u22 = 2 - (1/3)*4
+
+    L = np.array(g["trtri"]["L"], order="F")
+    X, info = oracle.trtri(L, c=1)
+    assert info == 0 and np.array_equal(np.tril(X), np.array(g["trtri"]["X"]))
+
+    L = np.array(g["lauum"]["L"], order="F")
+    A = oracle.lauum(L, c=1)
+    assert np.array_equal(np.tril(A), np.array(g["lauum"]["A"]))
+
+
+def test_closed_forms_3x3_symbolic(oracle):
+    sympy = pytest.importorskip("sympy")
+    a, b, c, d, e, f = (sympy.Rational(v) for v in (9, 3, 6, 5, 2, 14))
+    M = sympy.Matrix([[a, b, c], [b, d, e], [c, e, f]])
+    Lsym = M.cholesky(hermitian=False)
+    A = np.array(M.tolist(), dtype=np.float64, order="F")
+    L, info = oracle.potrf(A, c=1)
+    assert info == 0
+    Lexp = np.array(Lsym.evalf(30).tolist(), dtype=np.float64)
+    assert np.max(np.abs(np.tril(L) - Lexp)) <= 8 * EPS * np.max(np.abs(Lexp))
+    # TRTRI of the symbolic factor, LAUUM of it
+    X, info = oracle.trtri(np.asfortranarray(Lexp), c=1)
+    Xexp = np.array(Lsym.inv().evalf(30).tolist(), dtype=np.float64)
+    assert np.max(np.abs(np.tril(X) - Xexp)) <= 16 * EPS * np.max(np.abs(Xexp))
+    P = oracle.lauum(np.asfortranarray(Lexp), c=1)
+    Pexp = np.array((Lsym.T * Lsym).evalf(30).tolist(), dtype=np.float64)
+    assert np.max(np.abs(np.tril(P) - np.tril(Pexp))) <= 16 * EPS * np.max(np.abs(Pexp))
+
+
+# ----------------------------------------------------------------------------
+# exact constructions (bit-exact expected results)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("c", [1, 2, 24, 6])
+def test_integer_cholesky_6x6_exact(oracle, c):
+    L = inputs.integer_chol_6()
+    A = inputs.product_lower(L)
+    F, info = oracle.potrf(A, c=c)
+    assert info == 0
+    assert np.array_equal(np.tril(F), L)
+    assert np.array_equal(np.triu(F, 1), np.triu(A, 1))   # upper part untouched
+
+
+@pytest.mark.parametrize("n,c", [(37, 1), (100, 24), (130, 130), (200, 8)])
+def test_integer_cholesky_exact(oracle, n, c):
+    L = inputs.integer_chol(n, seed=inputs.seed_for(0, n))
+    A = inputs.product_lower(L)
+    F, info = oracle.potrf(A, c=c)
+    assert info == 0 and np.array_equal(np.tril(F), L)
+    assert oracle.res_chol(A, F) == 0.0
+
+
+@pytest.mark.parametrize("n,c", [(7, 1), (50, 2), (130, 24), (97, 97), (160, 16)])
+def test_dyadic_lu_exact(oracle, n, c):
+    A, L, U, perm = inputs.dyadic_lu(n, seed=inputs.seed_for(1, n))
+    F, ipiv, info = oracle.getrf(A, c=c)
+    assert info == 0
+    assert np.array_equal(ipiv, inputs.expected_ipiv(perm))
+    assert np.array_equal(np.tril(F, -1) + np.eye(n), L)
+    assert np.array_equal(np.triu(F), U)
+
+
+def test_lu_rectangular_shapes(oracle):
+    for m, n in [(90, 40), (40, 90), (65, 64), (1, 30), (30, 1)]:
+        A = inputs.uniform(m, n, seed=inputs.seed_for(1, 1000 + m + n))
+        F, ipiv, info = oracle.getrf(A, c=8)
+        assert info == 0 and oracle.res_lu(A, F, ipiv) <= BOUND
+        Fs, piv, infos = lapack.dgetrf(A)
+        assert np.array_equal(ipiv, piv + 1)
+
+
+@pytest.mark.parametrize("n,c", [(5, 1), (64, 24), (150, 16), (201, 201)])
+def test_integer_trtri_exact(oracle, n, c):
+    L = inputs.integer_trtri(n, seed=inputs.seed_for(1, 300 + n))
+    X, info = oracle.trtri(L, c=c)
+    assert info == 0
+    # L X = I exactly (integer matmul on exactly representable dyadics)
+    prod = np.tril(L) @ np.tril(X)
+    assert np.array_equal(prod, np.eye(n))
+    # trtri(trtri(L)) = L
+    Y, info = oracle.trtri(X, c=c)
+    assert np.array_equal(np.tril(Y), np.tril(L))
+    assert np.array_equal(np.triu(X, 1), np.triu(L, 1))   # upper part untouched
+
+
+@pytest.mark.parametrize("n,c", [(3, 1), (70, 24), (129, 16)])
+def test_integer_lauum_exact(oracle, n, c):
+    L = inputs.integer_chol(n, seed=inputs.seed_for(1, 500 + n))
+    P = oracle.lauum(L, c=c)
+    Li = np.tril(L).astype(np.int64)
+    want = (Li.T @ Li).astype(np.float64)
+    assert np.array_equal(np.tril(P), np.tril(want))
+    assert np.array_equal(np.triu(P, 1), np.triu(L, 1))
+
+
+# ----------------------------------------------------------------------------
+# exact rational brute force on tiny inputs
+# ----------------------------------------------------------------------------
+
+def _gepp_fractions(A):
+    """Gaussian elimination with partial pivoting in exact rationals
+    (independent of the oracle): returns LU (Fractions), ipiv (1-based), the
+    relative gap between the top two candidates of each column."""
+    n = len(A)
+    M = [[Fraction(x) for x in row] for row in A]
+    ipiv, gaps = [], []
+    for j in range(n):
+        cand = sorted(((abs(M[i][j]), i) for i in range(j, n)), key=lambda t: (-t[0], t[1]))
+        p = cand[0][1]
+        if len(cand) > 1 and cand[0][0] > 0:
+            gaps.append(float((cand[0][0] - cand[1][0]) / cand[0][0]))
+        else:
+            gaps.append(1.0)
+        ipiv.append(p + 1)
+        M[j], M[p] = M[p], M[j]
+        if M[j][j] != 0:
+            for i in range(j + 1, n):
+                M[i][j] = M[i][j] / M[j][j]
+                for k in range(j + 1, n):
+                    M[i][k] -= M[i][j] * M[j][k]
+    return M, ipiv, gaps
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_lu_brute_force_rational(oracle, n):
+    for k in range(5):
+        A = inputs.uniform(n, n, seed=inputs.seed_for(1, 700 + 10 * n + k))
+        M, ipiv, gaps = _gepp_fractions(A.tolist())
+        F, piv, info = oracle.getrf(A, c=1 + k % 3)
+        assert info == 0
+        assert all(g > 1e-12 for g in gaps)
+        assert list(piv) == ipiv
+        exact = np.array([[float(x) for x in row] for row in M])
+        assert np.max(np.abs(F - exact)) <= 64 * n * EPS * max(1.0, np.max(np.abs(exact)))
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 8])
+def test_cholesky_brute_force_rational(oracle, n):
+    import decimal
+    decimal.getcontext().prec = 50
+    for k in range(4):
+        A = inputs.spd_bbt(n, seed=inputs.seed_for(0, 800 + 10 * n + k))
+        # exact LDL^T in rationals, then L sqrt(D) to 50 digits
+        M = [[Fraction(x) for x in row] for row in A.tolist()]
+        Lr = [[Fraction(0)] * n for _ in range(n)]
+        D = [Fraction(0)] * n
+        for j in range(n):
+            D[j] = M[j][j] - sum(Lr[j][t] ** 2 * D[t] for t in range(j))
+            Lr[j][j] = Fraction(1)
+            for i in range(j + 1, n):
+                Lr[i][j] = (M[i][j] - sum(Lr[i][t] * Lr[j][t] * D[t] for t in range(j))) / D[j]
+        sq = [decimal.Decimal(d.numerator) / decimal.Decimal(d.denominator) for d in D]
+        sq = [s.sqrt() for s in sq]
+        exact = np.zeros((n, n))
+        for j in range(n):
+            for i in range(j, n):
+                v = decimal.Decimal(Lr[i][j].numerator) / decimal.Decimal(Lr[i][j].denominator)
+                exact[i, j] = float(v * sq[j])
+        F, info = oracle.potrf(A, c=1 + k % 3)
+        assert info == 0
+        assert np.max(np.abs(np.tril(F) - exact)) <= 16 * n * EPS * np.max(np.abs(exact))
+
+
+def test_trtri_lauum_brute_force_rational(oracle):
+    for n in (1, 3, 6):
+        L = np.tril(inputs.uniform(n, n, seed=inputs.seed_for(1, 900 + n)))
+        L[np.diag_indices(n)] += 2.0
+        Lf = [[Fraction(x) for x in row] for row in L.tolist()]
+        # exact inverse by forward substitution on L x = e_j
+        X = [[Fraction(0)] * n for _ in range(n)]
+        for j in range(n):
+            for i in range(j, n):
+                rhs = Fraction(1 if i == j else 0) - sum(Lf[i][k] * X[k][j] for k in range(j, i))
+                X[i][j] = rhs / Lf[i][i]
+        Xe = np.array([[float(x) for x in r] for r in X])
+        Xo, info = oracle.trtri(np.asfortranarray(L), c=2)
+        assert np.max(np.abs(np.tril(Xo) - Xe)) <= 32 * n * EPS * np.max(np.abs(Xe))
+        P = [[sum(Lf[k][i] * Lf[k][j] for k in range(n)) for j in range(n)] for i in range(n)]
+        Pe = np.array([[float(x) for x in r] for r in P])
+        Po = oracle.lauum(np.asfortranarray(L), c=2)
+        assert np.max(np.abs(np.tril(Po) - np.tril(Pe))) <= 8 * n * EPS * np.max(np.abs(Pe))
+
+
+# ----------------------------------------------------------------------------
+# LAPACK (scipy) cross-checks: special cases that reduce to a library routine
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 17, 100, 257])
+def test_potrf_vs_lapack(oracle, n):
+    A = inputs.spd_bbt(n, seed=inputs.seed_for(0, n))
+    for c in (1, 2, 24, n):
+        F, info = oracle.potrf(A, c=c)
+        assert info == 0 and oracle.res_chol(A, F) <= BOUND
+        Ls, infos = lapack.dpotrf(A, lower=1)
+        kappa = np.linalg.cond(A)
+        assert np.max(np.abs(np.tril(F) - np.tril(Ls))) <= 2 * BOUND * n * EPS * kappa * np.max(np.abs(Ls))
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 100, 257])
+def test_getrf_vs_lapack(oracle, n):
+    A = inputs.uniform(n, n, seed=inputs.seed_for(1, n))
+    Fs, piv, infos = lapack.dgetrf(A)
+    for c in (1, 2, 24, n):
+        F, ipiv, info = oracle.getrf(A, c=c)
+        assert info == 0 and oracle.res_lu(A, F, ipiv) <= BOUND
+        assert np.array_equal(ipiv, piv + 1)
+        kappa = np.linalg.cond(A)
+        assert np.max(np.abs(F - Fs)) <= 2 * BOUND * n * EPS * kappa * max(1.0, np.max(np.abs(Fs)))
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 128, 200])
+def test_trtri_lauum_potri_vs_lapack(oracle, n):
+    A = inputs.spd_bbt(n, seed=inputs.seed_for(1, 100 + n))
+    L, info = oracle.potrf(A, c=24)
+    L = np.asfortranarray(np.tril(L))
+    for c in (1, 2, 24, n):
+        X, info = oracle.trtri(L, c=c)
+        assert info == 0 and oracle.res_trtri(L, X) <= BOUND
+        Xs, infos = lapack.dtrtri(L, lower=1)
+        kl = np.linalg.cond(L)
+        assert np.max(np.abs(np.tril(X) - np.tril(Xs))) <= 2 * BOUND * n * EPS * kl * np.max(np.abs(Xs))
+        P = oracle.lauum(L, c=c)
+        Ps, infos = lapack.dlauum(L, lower=1)
+        assert np.max(np.abs(np.tril(P) - np.tril(Ps))) <= 4 * n * EPS * np.max(np.abs(Ps))
+        Ai, info = oracle.potri(L, c=c)
+        assert info == 0 and oracle.res_potri(A, Ai) <= BOUND
+
+
+# ----------------------------------------------------------------------------
+# info semantics (LAPACK's meanings)
+# ----------------------------------------------------------------------------
+
+def test_potrf_info_not_spd(oracle):
+    n = 60
+    A = inputs.spd_bbt(n, seed=inputs.seed_for(0, 42))
+    for k in (0, 7, 31, 59):
+        B = A.copy(order="F")
+        B[k, k] = -1.0
+        for c in (1, 8, 24, n):
+            F, info = oracle.potrf(B, c=c)
+            _, infos = lapack.dpotrf(B, lower=1)
+            assert info == infos > 0
+            assert np.allclose(np.tril(F[: info - 1, : info - 1]),
+                               np.linalg.cholesky(B[: info - 1, : info - 1]), rtol=1e-12, atol=1e-12)
+
+
+def test_getrf_info_singular(oracle):
+    n = 50
+    A = inputs.uniform(n, n, seed=inputs.seed_for(1, 43))
+    for k in (0, 13, 49):
+        B = A.copy(order="F")
+        B[:, k] = 0.0
+        for c in (1, 8, n):
+            F, ipiv, info = oracle.getrf(B, c=c)
+            Fs, piv, infos = lapack.dgetrf(B)
+            assert info == infos == k + 1
+            assert np.array_equal(ipiv, piv + 1)
+            assert oracle.res_lu(B, F, ipiv) <= BOUND
+
+
+def test_trtri_info_zero_diagonal(oracle):
+    n = 40
+    L = np.tril(inputs.uniform(n, n, seed=inputs.seed_for(1, 44))) + 3 * np.eye(n)
+    L = np.asfortranarray(L)
+    L[17, 17] = 0.0
+    L[30, 30] = 0.0
+    X, info = oracle.trtri(L, c=8)
+    assert info == 18 and np.array_equal(X, L)
+
+
+# ----------------------------------------------------------------------------
+# random residual bounds and crossover invariance (spec bound <= 10)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [3, 64, 129, 300, 512])
+def test_residual_bounds_all_crossovers(oracle, n):
+    A = inputs.spd_bbt(n, seed=inputs.seed_for(0, 1000 + n))
+    G = inputs.uniform(n, n, seed=inputs.seed_for(1, 1000 + n))
+    for c in (1, 2, 24, n):
+        L, info = oracle.potrf(A, c=c)
+        assert info == 0 and oracle.res_chol(A, L) <= BOUND
+        F, ipiv, info = oracle.getrf(G, c=c)
+        assert info == 0 and oracle.res_lu(G, F, ipiv) <= BOUND
+    x = inputs.normal(n, 1, seed=7).ravel()
+    assert oracle.probe_chol(A, L, x) <= BOUND
+    assert oracle.probe_lu(G, F, ipiv, x) <= BOUND
+
+
+def test_laswp_definition(oracle):
+    A = inputs.uniform(9, 4, seed=1)
+    ipiv = np.array([3, 2, 9, 4], dtype=np.int32)
+    B = oracle.laswp(A, 0, 4, ipiv)
+    want = A.copy()
+    for i, p in enumerate(ipiv):
+        want[[i, p - 1]] = want[[p - 1, i]]
+    assert np.array_equal(B, want)
+
+
+def test_solves_backward_error(oracle):
+    n = 120
+    A = inputs.uniform(n, n, seed=inputs.seed_for(2, 1))
+    B = inputs.normal(n, 3, seed=inputs.seed_for(2, 2))
+    F, ipiv, info = oracle.getrf(A, c=24)
+    X = oracle.getrs(F, ipiv, B)
+    assert oracle.backward_error(A, X, B) <= 10 * n * EPS
+    S = inputs.spd_bbt(n, seed=inputs.seed_for(2, 3))
+    L, info = oracle.potrf(S, c=24)
+    X = oracle.potrs(L, B)
+    assert oracle.backward_error(S, X, B) <= 10 * n * EPS
+
+
+# ----------------------------------------------------------------------------
+# planted mistakes: each pin fails on a plausible error in the oracle's output
+# ----------------------------------------------------------------------------
+
+def test_planted_mistakes_are_caught(oracle):
+    n = 96
+    A = inputs.spd_bbt(n, seed=inputs.seed_for(0, 5))
+    L, info = oracle.potrf(A, c=24)
+    L = np.asfortranarray(np.tril(L))
+    # dropped SYRK update: factor A22 without subtracting A21 A21^T
+    n1 = oracle.split(n)
+    bad = L.copy(order="F")
+    bad[n1:, n1:] = np.linalg.cholesky(A[n1:, n1:])
+    assert oracle.res_chol(A, bad) > 1e6
+    # wrong sign in one entry
+    bad = L.copy(order="F")
+    bad[50, 3] = -bad[50, 3]
+    assert oracle.res_chol(A, bad) > 1e3
+    # transposed off-diagonal block (A21 <-> A12^T shape mix-up)
+    bad = L.copy(order="F")
+    bad[n1:n1 + 8, :8] = bad[n1:n1 + 8, :8].T
+    assert oracle.res_chol(A, bad) > 1e3
+    # swapped pivot in LU
+    G = inputs.uniform(n, n, seed=inputs.seed_for(1, 5))
+    F, ipiv, info = oracle.getrf(G, c=24)
+    p2 = ipiv.copy()
+    p2[10] = p2[10] + 1 if p2[10] < n else p2[10] - 1
+    assert oracle.res_lu(G, F, p2) > 1e3
+    # TRTRI with the TRSM sign dropped
+    X, info = oracle.trtri(L, c=24)
+    bad = np.asfortranarray(np.tril(X))
+    bad[n1:, :n1] = -bad[n1:, :n1]
+    assert oracle.res_trtri(L, bad) > 1e3
+    # probe residuals flag the same mistake
+    x = inputs.normal(n, 1, seed=3).ravel()
+    badL = L.copy(order="F")
+    badL[50, 3] = -badL[50, 3]
+    assert oracle.probe_chol(A, badL, x) > 1e3
