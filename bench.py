@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""Throughput of the recursive FP64 factorizations on GB300.
+
+One step = one recursive dpotrf (lower, SPD A = B B^T + n I) and one recursive
+dgetrf (partial pivoting, entries Uniform(-1,1)) at n = 16384 in binary64,
+through the C ABI on device-resident inputs.  Each step first restores both
+matrices from pristine device copies (a 2.1 GB device-to-device copy each;
+inside the timed region, about 0.1 % of it); both matrices are far larger
+than L2, so no separate L2 flush is needed.
+
+Printed (rank 0, one JSON line): GFLOP/s of the whole step (LAPACK Working
+Note 41 flop counts), per-routine GFLOP/s, the roofline of the dominant
+kernel measured with the library's per-kernel CUDA-event trace over the timed
+region, an end-to-end figure through the host-buffer entry points (pinned
+host memory, copies inside the timed region), the CPU oracle timed on a
+bounded sample, and SM clocks sampled during the timed region.
+
+--impl reference times the CPU oracle instead (the reference arm: a plain
+FP64 recursive implementation on the host cores, same metric and unit).
+
+Multi-GPU: a single factorization does not shard without a panel broadcast
+per recursion level, so N > 1 runs N independent replicas (one per rank,
+launched by torchrun) and reports the aggregate; ranks only synchronize for
+the barrier and the max over ranks of the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "POTRF/GETRF GFLOP/s at n=16384 (% FP64 peak)"
+UNIT = "GFLOP/s"
+
+# FP64 roofline denominator (no FP64 figure is measured by the pool's peak
+# file): 152 SMs x 2 FP64 FMA lanes per SM per clock x 2 flop x 2070 MHz
+# maximum SM clock = 1.259 TFLOP/s, the unit count that reproduces GB300's
+# nominal 1.25 TFLOP/s FP64 rate.
+SMS = 152
+FP64_FMA_PER_SM_CLK = 2
+SM_MAX_MHZ = 2070.0
+FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def flops_potrf(n: int) -> float:
+    return n ** 3 / 3.0 + n ** 2 / 2.0 + n / 6.0
+
+
+def flops_getrf(n: int) -> float:
+    return 2.0 * n ** 3 / 3.0 - n ** 2 / 2.0 + 5.0 * n / 6.0
+
+
+def workload_config(n: int) -> dict:
+    return {
+        "workload": f"recursive dpotrf (lower, SPD B*B^T+n*I) + dgetrf (partial pivoting, U(-1,1)), "
+                    f"n={n}, binary64, column-major lda=n",
+        "n": n,
+        "routines": ["dpotrf", "dgetrf"],
+        "l2": "inputs are 2.1 GB per matrix (> 129 MB L2); no flush needed",
+        "restore": "each step restores both matrices from pristine device copies inside the timed region",
+        "parallelism": "replicas (one independent factorization pair per GPU)",
+    }
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.device_id = device_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.device_id is not None:
+                cmd += ["-i", str(self.device_id)]
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def physical_gpu_id(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return local_rank
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ----------------------------------------------------------------------------
+
+def cpu_cores():
+    try:
+        n = len(os.sched_getaffinity(0))
+    except Exception:
+        n = os.cpu_count() or 1
+    omp = os.environ.get("OMP_NUM_THREADS")
+    return min(n, int(omp)) if omp and omp.isdigit() else n
+
+
+def oracle_sample(n_cpu: int, seed_k: int = 0):
+    """Time the oracle's recursive dpotrf + dgetrf on an n_cpu sample of the
+    same recipes; returns (GFLOP/s, seconds)."""
+    import oracle
+    from paper_1602_06763_gb300 import inputs
+    A = inputs.spd_bbt(n_cpu, seed=inputs.seed_for(2, 500 + seed_k))
+    G = inputs.uniform(n_cpu, n_cpu, seed=inputs.seed_for(2, 600 + seed_k))
+    t0 = time.perf_counter()
+    _, info1 = oracle.potrf(A, c=24)
+    _, _, info2 = oracle.getrf(G, c=24)
+    dt = time.perf_counter() - t0
+    assert info1 == 0 and info2 == 0
+    return (flops_potrf(n_cpu) + flops_getrf(n_cpu)) / dt / 1e9, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    from oracle import build as obuild
+    obuild.build()
+    n_ref = args.ref_n
+    for w in range(args.warmup):
+        oracle_sample(n_ref, w)
+    times = []
+    for k in range(args.steps):
+        _, dt = oracle_sample(n_ref, 100 + k)
+        times.append(dt)
+    tot = sum(times)
+    value = args.steps * (flops_potrf(n_ref) + flops_getrf(n_ref)) / tot / 1e9
+    sample = f"oracle dpotrf+dgetrf at n={n_ref} (same recipes) per step, c=24"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference", "config": workload_config(args.n),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1602_06763_gb300 import relgpu as r, inputs
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = args.n
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    spd0 = inputs.spd_bbt_device(n, inputs.seed_for(2, 10 + rank), device=dev)
+    gen0 = inputs.uniform_device(n, n, inputs.seed_for(2, 20 + rank), device=dev)
+    spd = torch.empty_like(spd0)
+    gen = torch.empty_like(gen0)
+    ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+    info = torch.zeros(2, dtype=torch.int32, device=dev)
+    lw = r.rl_dgetrf_work_size(n, n)
+    work = torch.empty(lw, dtype=torch.uint8, device=dev)
+
+    def step():
+        spd.copy_(spd0)
+        gen.copy_(gen0)
+        r.check(r.rl_dpotrf("L", n, spd.data_ptr(), n, info.data_ptr(), None, 0, sp), "rl_dpotrf")
+        r.check(r.rl_dgetrf(n, n, gen.data_ptr(), n, ipiv.data_ptr(), info.data_ptr() + 4,
+                            work.data_ptr(), lw, sp), "rl_dgetrf")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    inf = info.cpu().tolist()
+    if inf != [0, 0]:
+        raise RuntimeError(f"factorization info {inf} on the benchmark inputs")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(physical_gpu_id(local_rank))
+
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    r.rl_trace_enable(1)
+    launches0 = r.rl_launch_count()
+    t_start.record(stream)
+    for k in range(args.steps):
+        spd.copy_(spd0)
+        gen.copy_(gen0)
+        ev[k][0].record(stream)
+        r.check(r.rl_dpotrf("L", n, spd.data_ptr(), n, info.data_ptr(), None, 0, sp), "rl_dpotrf")
+        ev[k][1].record(stream)
+        r.check(r.rl_dgetrf(n, n, gen.data_ptr(), n, ipiv.data_ptr(), info.data_ptr() + 4,
+                            work.data_ptr(), lw, sp), "rl_dgetrf")
+        ev[k][2].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = r.rl_launch_count() - launches0
+    trace = r.trace_summary()
+    r.rl_trace_enable(0)
+    clocks = sampler.stop()
+
+    ms_total = t_start.elapsed_time(t_end)
+    ms_potrf = [e[0].elapsed_time(e[1]) for e in ev]
+    ms_getrf = [e[1].elapsed_time(e[2]) for e in ev]
+    if world > 1:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    step_flops = flops_potrf(n) + flops_getrf(n)
+    value = world * step_flops / (ms_step * 1e-3) / 1e9
+
+    # dominant kernel by device time over the timed region
+    dom_name = max(trace, key=lambda k: trace[k]["ms"]) if trace else None
+    roofline = None
+    if dom_name:
+        d = trace[dom_name]
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        roofline = {
+            "bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2070 MHz",
+            "launches_per_step": d["launches"] / args.steps,
+            "share_of_step": d["ms"] / ms_total,
+        }
+
+    # end to end through the host-buffer entry points (pinned host memory)
+    e2e = None
+    if args.e2e_steps > 0:
+        import numpy as np
+        h_spd0 = spd0.cpu().numpy().copy()
+        h_gen0 = gen0.cpu().numpy().copy()
+        h_spd = torch.empty(n * n, dtype=torch.float64).pin_memory()
+        h_gen = torch.empty(n * n, dtype=torch.float64).pin_memory()
+        h_piv = torch.empty(n, dtype=torch.int32).pin_memory()
+        h_inf = torch.empty(2, dtype=torch.int32).pin_memory()
+        del spd, gen
+        lw_p = r.rl_host_work_size("dpotrf", n, n, n)
+        lw_g = r.rl_host_work_size("dgetrf", n, n, n)
+        w_p = torch.empty(lw_p, dtype=torch.uint8, device=dev)
+        w_g = torch.empty(lw_g, dtype=torch.uint8, device=dev)
+        ts = []
+        for k in range(args.e2e_steps + 1):
+            np.copyto(h_spd.numpy(), h_spd0.reshape(-1))
+            np.copyto(h_gen.numpy(), h_gen0.reshape(-1))
+            barrier()
+            t0 = time.perf_counter()
+            r.check(r.rl_dpotrf_host("L", n, h_spd.data_ptr(), n, h_inf.data_ptr(), w_p.data_ptr(),
+                                     lw_p, sp), "rl_dpotrf_host")
+            r.check(r.rl_dgetrf_host(n, n, h_gen.data_ptr(), n, h_piv.data_ptr(), h_inf.data_ptr() + 4,
+                                     w_g.data_ptr(), lw_g, sp), "rl_dgetrf_host")
+            t1 = time.perf_counter()
+            if k > 0:          # the first pass is a warm-up
+                ts.append(t1 - t0)
+            if h_inf.tolist() != [0, 0]:
+                raise RuntimeError("host-buffer factorization failed")
+        t_e2e = statistics.median(ts)
+        if world > 1:
+            t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * step_flops / t_e2e / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * n * n * 8,
+               "d2h_bytes_per_step": 2 * n * n * 8 + n * 4 + 2 * 4,
+               "ms_per_step": 1e3 * t_e2e, "steps": len(ts)}
+
+    if rank != 0:
+        return 0
+
+    cpu = None
+    if world == 1 and args.cpu_n > 0:
+        from oracle import build as obuild
+        obuild.build()
+        gfl, dt = oracle_sample(args.cpu_n)
+        cpu = {"value": gfl, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"oracle dpotrf+dgetrf at n={args.cpu_n} (same recipes), c=24, {dt:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(n),
+        "pct_fp64_peak": 100.0 * (value / world) / (FP64_PEAK_TFLOPS * 1e3),
+        "routines": {
+            "dpotrf": {"gflops": flops_potrf(n) / (statistics.median(ms_potrf) * 1e-3) / 1e9,
+                       "ms": statistics.median(ms_potrf)},
+            "dgetrf": {"gflops": flops_getrf(n) / (statistics.median(ms_getrf) * 1e-3) / 1e9,
+                       "ms": statistics.median(ms_getrf)},
+        },
+        "roofline": roofline,
+        "kernels": {k: {"launches_per_step": v["launches"] / args.steps,
+                        "ms_per_step": v["ms"] / args.steps,
+                        "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["flops"] else None,
+                        "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["bytes"] else None}
+                    for k, v in trace.items()},
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--cpu-n", type=int, default=3072,
+                    help="order of the oracle's timed sample for cpu_baseline (about 10 s)")
+    ap.add_argument("--ref-n", type=int, default=2048,
+                    help="order of the oracle's sample per step in the reference arm")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend="nccl")
+    try:
+        return run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,199 @@
+/*
+ * relgpu.h -- C ABI of the GB300 (sm_103a) recursive dense factorizations of
+ * Peise & Bientinesi, "Recursive Algorithms for Dense Linear Algebra: The
+ * ReLAPACK Collection" (arXiv 1602.06763).
+ *
+ * The routines keep LAPACK's own argument lists (Section 5: "LAPACK's
+ * interface is preserved") and add three trailing arguments: a device
+ * workspace, its size in bytes, and the CUDA stream to run on.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Storage: column-major with a leading dimension (LAPACK).  Element (i,j)
+ *    of A is A[i + j*lda], 0-based.  Only the triangle named by `uplo` is read
+ *    or written; the other triangle is left untouched.
+ *  - Pointers: A, ipiv, info and work are DEVICE pointers (cudaMalloc'd or
+ *    torch-allocated memory on the current device) unless the name ends in
+ *    _host.  The caller owns every buffer; the library keeps no pointer after
+ *    the call returns and allocates no device memory.
+ *  - Streams: `stream` is a cudaStream_t (0 = legacy default stream).  The
+ *    call enqueues its kernels on that stream and returns without
+ *    synchronizing; results (including *info and ipiv) are valid once the
+ *    stream has reached that point.  The _host variants synchronize.
+ *  - Return value (host, immediate):
+ *      0            success (the work was enqueued)
+ *     -i            argument i is illegal, LAPACK's numbering; nothing was
+ *                   enqueued and *info was not written
+ *     RL_ERR_*  >0  a CUDA, workspace or support error (see rl_status_string)
+ *  - Numeric result (device, asynchronous): *info (int32) is set to 0 at the
+ *    start of the call and then receives LAPACK's meaning:
+ *      dpotrf/dpotri: k > 0  the leading minor of order k is not positive
+ *                     definite (the factorization stops there);
+ *      dgetrf:        k > 0  U(k,k) is exactly zero (the factorization is
+ *                     completed, as in LAPACK);
+ *      dtrtri/dpotri: k > 0  A(k,k) is exactly zero (A is left unchanged);
+ *      RL_INFO_DEVICE_TIMEOUT  a bounded device-side wait (the grid barrier
+ *                     of the LU panel kernel) ran out; outputs are invalid.
+ *  - 1-based ipiv (int32): row i was interchanged with row ipiv[i]-1.
+ *  - Only uplo = 'L' is built; 'U' returns RL_ERR_UNSUPPORTED.
+ */
+#ifndef RELGPU_H
+#define RELGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t (CUDA's runtime declares it as this pointer). */
+struct CUstream_st;
+typedef struct CUstream_st *rl_stream_t;
+
+enum {
+    RL_SUCCESS = 0,
+    RL_ERR_CUDA = 1,          /* a CUDA runtime call or launch failed */
+    RL_ERR_WORKSPACE = 2,     /* work is NULL or lwork is below the query */
+    RL_ERR_UNSUPPORTED = 3,   /* uplo 'U', or a size beyond a kernel limit */
+    RL_ERR_NULL_POINTER = 4,  /* info (or ipiv) is NULL */
+    RL_ERR_PARAM = 5          /* rl_set_param: unknown key or bad value */
+};
+
+#define RL_INFO_DEVICE_TIMEOUT (-1000)
+
+/* ---------------------------------------------------------------------------
+ * dpotrf -- recursive Cholesky A = L L^T (Section 5, xpotrf; recursion of
+ * Section 3).  With n1 ~ n/2: potrf(A11); A21 := A21 L11^{-T} (TRSM);
+ * A22 := A22 - A21 A21^T (SYRK, lower triangle); potrf(A22).  Base case: an
+ * unblocked Cholesky of a diagonal block in shared memory (IEEE sqrt and
+ * division).  A: n x n, lower triangle overwritten by L.
+ * Argument numbers: 1 uplo, 2 n, 3 A, 4 lda, 5 info.
+ * Workspace: none (work may be NULL, lwork 0).
+ * ------------------------------------------------------------------------- */
+int rl_dpotrf(char uplo, int64_t n, double *A, int64_t lda, int32_t *info,
+              void *work, size_t lwork, rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * dgetrf -- recursive LU with partial (row) pivoting, P A = L U (Section 5,
+ * xgetrf; recursion of Section 3 on the columns).  With n1 ~ min(m,n)/2:
+ * getrf(A[:, :n1]); apply the n1 interchanges to A[:, n1:] (LASWP);
+ * A12 := L11^{-1} A12 (unit TRSM); A22 := A22 - A21 A12 (GEMM); getrf(A22);
+ * apply its interchanges to A[:, :n1].  Base case: a fused panel kernel
+ * (pivot search, swap, scale, rank-1 update per column) that keeps the panel
+ * in shared memory across the co-resident CTAs of one cooperative launch.
+ * A: m x n, overwritten by L (unit, below the diagonal) and U.
+ * ipiv: min(m,n) int32, 1-based.
+ * Argument numbers: 1 m, 2 n, 3 A, 4 lda, 5 ipiv, 6 info.
+ * Workspace: rl_dgetrf_work_size(m, n) bytes (panel pivot exchange and the
+ * grid-barrier counter); contents need not be initialized.
+ * ------------------------------------------------------------------------- */
+int rl_dgetrf(int64_t m, int64_t n, double *A, int64_t lda, int32_t *ipiv,
+              int32_t *info, void *work, size_t lwork, rl_stream_t stream);
+
+size_t rl_dgetrf_work_size(int64_t m, int64_t n);
+
+/* ---------------------------------------------------------------------------
+ * dtrtri -- recursive inverse of a lower triangular matrix in place
+ * (Section 3, Fig. 4): trtri(A_TL); A_BL := A_BL A_TL (TRMM, A_TL already
+ * inverted); A_BL := -A_BR^{-1} A_BL (TRSM with the not yet inverted A_BR);
+ * trtri(A_BR).  Base case: an unblocked inverse in shared memory.
+ * diag: 'N' (non-unit) or 'U' (unit diagonal, not referenced).
+ * Argument numbers: 1 uplo, 2 diag, 3 n, 4 A, 5 lda, 6 info.
+ * Workspace: none.
+ * ------------------------------------------------------------------------- */
+int rl_dtrtri(char uplo, char diag, int64_t n, double *A, int64_t lda,
+              int32_t *info, void *work, size_t lwork, rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * dlauum -- A := L^T L for lower triangular L in place (Section 5, xlauum),
+ * recursively: lauum(A11); A11 := A11 + A21^T A21 (SYRK); A21 := A22^T A21
+ * (TRMM); lauum(A22).  The lower triangle of the symmetric result is
+ * written.  Argument numbers: 1 uplo, 2 n, 3 A, 4 lda, 5 info.
+ * Workspace: none.  *info is always 0.
+ * ------------------------------------------------------------------------- */
+int rl_dlauum(char uplo, int64_t n, double *A, int64_t lda, int32_t *info,
+              void *work, size_t lwork, rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * dpotri -- inverse of an SPD matrix from its Cholesky factor: dtrtri then
+ * dlauum on L (Section 5: xtrtri is the building block of xpotri), since
+ * A^{-1} = L^{-T} L^{-1}.  A holds L on entry and the lower triangle of
+ * A^{-1} on exit.  Argument numbers: 1 uplo, 2 n, 3 A, 4 lda, 5 info.
+ * ------------------------------------------------------------------------- */
+int rl_dpotri(char uplo, int64_t n, double *A, int64_t lda, int32_t *info,
+              void *work, size_t lwork, rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Host-buffer forms (end-to-end use from host memory).  A_host (and
+ * ipiv_host, info_host) are HOST pointers, ideally page-locked.  `work` is a
+ * device buffer of at least rl_host_work_size(routine, m, n, lda) bytes that holds
+ * the device copy of A plus the routine's workspace.  The call copies A to
+ * the device, factors it on `stream`, copies the results back and
+ * synchronizes the stream before returning.  Argument numbering and errors
+ * as for the device forms.  routine: "dpotrf" or "dgetrf".
+ * ------------------------------------------------------------------------- */
+size_t rl_host_work_size(const char *routine, int64_t m, int64_t n, int64_t lda);
+
+int rl_dpotrf_host(char uplo, int64_t n, double *A_host, int64_t lda,
+                   int32_t *info_host, void *work, size_t lwork,
+                   rl_stream_t stream);
+
+int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda,
+                   int32_t *ipiv_host, int32_t *info_host, void *work,
+                   size_t lwork, rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Tuning parameters (process-wide; take effect for calls enqueued after the
+ * change).  The paper's crossover size c (Section 3) is set per routine.
+ *   RL_PARAM_POTRF_CROSSOVER   order at or below which dpotrf runs its base
+ *                              case (1..64, default 64)
+ *   RL_PARAM_GETRF_PANEL       panel width of dgetrf's base case (1..64,
+ *                              default 32)
+ *   RL_PARAM_TRTRI_CROSSOVER   base-case order for dtrtri/dlauum (1..64,
+ *                              default 64)
+ *   RL_PARAM_SPIN_LIMIT_NS     bound on every device-side wait, in ns
+ *                              (default 2e9); 0 makes any wait that is not
+ *                              already satisfied fail with
+ *                              RL_INFO_DEVICE_TIMEOUT
+ * rl_set_param returns 0 or RL_ERR_PARAM; rl_get_param returns the value or
+ * -1 for an unknown key.
+ * ------------------------------------------------------------------------- */
+enum {
+    RL_PARAM_POTRF_CROSSOVER = 1,
+    RL_PARAM_GETRF_PANEL = 2,
+    RL_PARAM_TRTRI_CROSSOVER = 3,
+    RL_PARAM_SPIN_LIMIT_NS = 4
+};
+int rl_set_param(int key, int64_t value);
+int64_t rl_get_param(int key);
+
+/* Number of kernels this library has launched in this process (host-side
+ * count, for accounting in benchmarks). */
+uint64_t rl_launch_count(void);
+
+/* ---------------------------------------------------------------------------
+ * Per-kernel tracing, the GPU analogue of the paper's per-kernel time and
+ * efficiency breakdown (Section 3, Figs. 2 and 5).  While enabled, every
+ * kernel the library launches is bracketed by two CUDA events on its stream
+ * (so traced calls are not meant for graph capture) and its algorithmic
+ * flops and bytes are attributed to its kind.
+ *   rl_trace_enable(1) clears the totals and starts tracing; (0) stops.
+ *   rl_trace_kinds() is the number of kinds; rl_trace_read(kind, ...)
+ *   synchronizes on the recorded events and returns the kind's name, launch
+ *   count, total device time (ms), flops and bytes.  Any output pointer may
+ *   be NULL.  Returns 0 or RL_ERR_PARAM for a bad kind.
+ * ------------------------------------------------------------------------- */
+int rl_trace_enable(int on);
+int rl_trace_kinds(void);
+int rl_trace_read(int kind, const char **name, uint64_t *launches, double *ms,
+                  double *flops, double *bytes);
+
+/* Human-readable text for a return value of any entry point. */
+const char *rl_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RELGPU_H */

@@ -63,6 +63,8 @@ def _lib():
             "or_res_potri": (_dbl, [_i64, _ptr, _i64, _ptr, _i64]),
             "or_probe_chol": (_dbl, [_i64, _ptr, _i64, _ptr, _i64, _ptr]),
             "or_probe_lu": (_dbl, [_i64, _ptr, _i64, _ptr, _i64, _ptr, _ptr]),
+            "or_probe_trtri": (_dbl, [_i64, _ptr, _i64, _ptr, _i64, _ptr]),
+            "or_probe_potri": (_dbl, [_i64, _ptr, _i64, _ptr, _i64, _ptr]),
             "or_backward_error": (_dbl, [_i64, _i64, _ptr, _i64, _ptr, _i64, _ptr, _i64]),
             "or_trtri_level_flops": (_dbl, [_i64, _i64, _ptr, _i64, _i64]),
         }
@@ -242,6 +244,20 @@ def probe_lu(A0, LU, ipiv, x):
     x = np.ascontiguousarray(x, dtype=np.float64)
     return float(_lib().or_probe_lu(A0.shape[0], _p(A0), _ld(A0), _p(LU), _ld(LU),
                                     _p(ipiv), _p(x)))
+
+
+def probe_trtri(L, X, x):
+    """||L X x - x||_inf / (n eps ||L||_inf ||X||_inf ||x||_inf), O(n^2)."""
+    L, X = _ro(L), _ro(X)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return float(_lib().or_probe_trtri(L.shape[0], _p(L), _ld(L), _p(X), _ld(X), _p(x)))
+
+
+def probe_potri(A0, X, x):
+    """||A X x - x||_inf / (n eps ||A||_inf ||X||_inf ||x||_inf), O(n^2)."""
+    A0, X = _ro(A0), _ro(X)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return float(_lib().or_probe_potri(A0.shape[0], _p(A0), _ld(A0), _p(X), _ld(X), _p(x)))
 
 
 def backward_error(A, X, B):

@@ -830,3 +830,72 @@ double or_trtri_level_flops(int64_t n, int64_t c, double *shares, int64_t nlev,
     return here + or_trtri_level_flops(n1, c, shares, nlev, level + 1)
                 + or_trtri_level_flops(n2, c, shares, nlev, level + 1);
 }
+
+/* Random-probe residuals of the inverses (O(n^2) per probe vector x):
+ *   trtri: ||L (X x) - x||_inf / (n eps ||L||_inf ||X||_inf ||x||_inf)
+ *   potri: ||A (X x) - x||_inf / (n eps ||A||_inf ||X||_inf ||x||_inf)
+ * L, X lower triangular (trtri); A, X symmetric, lower-stored (potri). */
+static double inf_norm_lower(int64_t n, const double *L, int64_t ldl)
+{
+    double best = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t k = 0; k <= i; ++k) s += fabs(AT(L, ldl, i, k));
+        if (s > best) best = s;
+    }
+    return best;
+}
+
+double or_probe_trtri(int64_t n, const double *L, int64_t ldl, const double *X,
+                      int64_t ldx, const double *x)
+{
+    if (n <= 0) return 0.0;
+    double *y = (double *)malloc(sizeof(double) * (size_t)n);  /* y = X x */
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        dot2_t acc = {0.0, 0.0};
+        for (int64_t k = 0; k <= i; ++k) dot2_add(&acc, AT(X, ldx, i, k), x[k]);
+        y[i] = dot2_val(&acc);
+    }
+    double r = 0.0, xn = 0.0;
+    for (int64_t i = 0; i < n; ++i) if (fabs(x[i]) > xn) xn = fabs(x[i]);
+    #pragma omp parallel for schedule(dynamic, 16) reduction(max : r)
+    for (int64_t i = 0; i < n; ++i) {
+        dot2_t acc = {0.0, 0.0};
+        dot2_add(&acc, -x[i], 1.0);
+        for (int64_t k = 0; k <= i; ++k) dot2_add(&acc, AT(L, ldl, i, k), y[k]);
+        double v = fabs(dot2_val(&acc));
+        if (v > r) r = v;
+    }
+    free(y);
+    return r / ((double)n * ldexp(1.0, -53) * inf_norm_lower(n, L, ldl) *
+                inf_norm_lower(n, X, ldx) * xn);
+}
+
+double or_probe_potri(int64_t n, const double *A0, int64_t lda0, const double *X,
+                      int64_t ldx, const double *x)
+{
+    if (n <= 0) return 0.0;
+    double *y = (double *)malloc(sizeof(double) * (size_t)n);  /* y = X x */
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        dot2_t acc = {0.0, 0.0};
+        for (int64_t k = 0; k < n; ++k)
+            dot2_add(&acc, i >= k ? AT(X, ldx, i, k) : AT(X, ldx, k, i), x[k]);
+        y[i] = dot2_val(&acc);
+    }
+    double r = 0.0, xn = 0.0;
+    for (int64_t i = 0; i < n; ++i) if (fabs(x[i]) > xn) xn = fabs(x[i]);
+    #pragma omp parallel for schedule(dynamic, 16) reduction(max : r)
+    for (int64_t i = 0; i < n; ++i) {
+        dot2_t acc = {0.0, 0.0};
+        dot2_add(&acc, -x[i], 1.0);
+        for (int64_t k = 0; k < n; ++k)
+            dot2_add(&acc, i >= k ? AT(A0, lda0, i, k) : AT(A0, lda0, k, i), y[k]);
+        double v = fabs(dot2_val(&acc));
+        if (v > r) r = v;
+    }
+    free(y);
+    return r / ((double)n * ldexp(1.0, -53) * inf_norm_sym_lower(n, A0, lda0) *
+                inf_norm_sym_lower(n, X, ldx) * xn);
+}

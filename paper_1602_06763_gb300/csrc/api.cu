@@ -1,0 +1,347 @@
+// C ABI and recursion scheduler.
+//
+// The host walks the recursion tree of each routine (Section 3: halve,
+// recurse on the first half, BLAS-3 update, recurse on the second half, base
+// case below the crossover c) and enqueues one kernel per BLAS-3 call and per
+// base case on the caller's stream.  Nothing synchronizes, nothing allocates:
+// a call can be captured into a CUDA graph by the caller.  A device-side
+// abort word (the call's info) lets later kernels skip their work once a
+// Cholesky pivot failed or a zero diagonal was found.
+#include <cstring>
+#include <mutex>
+#include "internal.cuh"
+
+namespace rl {
+
+std::atomic<uint64_t> g_launches{0};
+Params g_params;
+
+int device_sms()
+{
+    static int cache[128];
+    static std::once_flag once;
+    std::call_once(once, [] { for (int &v : cache) v = 0; });
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return 1;
+    if (cache[dev] == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = v > 0 ? v : 1;
+    }
+    return cache[dev];
+}
+
+void note(Ctx &c, cudaError_t e)
+{
+    if (e != cudaSuccess && c.err == cudaSuccess) c.err = e;
+}
+
+// ---- recursions -------------------------------------------------------------
+
+// Cholesky: potrf(A11); A21 := A21 L11^{-T}; A22 -= A21 A21^T; potrf(A22).
+static void potrf_rec(Ctx &c, i64 n, double *A, i64 lda, i64 off)
+{
+    if (n <= 0) return;
+    if (n <= g_params.potrf_c) { potf2(c, n, A, lda, off); return; }
+    const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
+    double *A21 = A + n1, *A22 = A + n1 + n1 * lda;
+    potrf_rec(c, n1, A, lda, off);
+    trsm_rlt(c, n2, n1, A, lda, A21, lda);
+    gemm(c, false, true, n2, n2, n1, -1.0, A21, lda, A21, lda, 1.0, A22, lda, true);
+    potrf_rec(c, n2, A22, lda, off + n1);
+}
+
+// LU of the m x n block whose top-left corner is (r0, r0) of the matrix A0
+// (m_tot rows).  Pivots are written as global 1-based rows.
+static void getrf_rec(Ctx &c, double *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r0, i64 m, i64 n)
+{
+    if (m <= 0 || n <= 0) return;
+    double *A = A0 + r0 + r0 * lda;
+    const i64 nb = g_params.getrf_nb;
+    if (n <= nb) { getf2_panel(c, m, n, A, lda, ipiv, r0); return; }
+    if (m < n) {
+        // wide: factor the leading m x m block, then swap and solve the rest
+        getrf_rec(c, A0, lda, m_tot, ipiv, r0, m, m);
+        laswp(c, A0, lda, m_tot, r0 + m, n - m, r0, r0 + m, ipiv);
+        trsm_lln(c, true, m, n - m, 1.0, A, lda, A + m * lda, lda);
+        return;
+    }
+    const i64 n1 = split_q(n, n > 2 * TRX_NB ? TRX_NB : nb), n2 = n - n1;
+    getrf_rec(c, A0, lda, m_tot, ipiv, r0, m, n1);
+    laswp(c, A0, lda, m_tot, r0 + n1, n2, r0, r0 + n1, ipiv);
+    trsm_lln(c, true, n1, n2, 1.0, A, lda, A + n1 * lda, lda);
+    gemm(c, false, false, m - n1, n2, n1, -1.0, A + n1, lda, A + n1 * lda, lda, 1.0,
+         A + n1 + n1 * lda, lda);
+    getrf_rec(c, A0, lda, m_tot, ipiv, r0 + n1, m - n1, n2);
+    const i64 mn2 = (m - n1) < n2 ? (m - n1) : n2;
+    laswp(c, A0, lda, m_tot, r0, n1, r0 + n1, r0 + n1 + mn2, ipiv);
+}
+
+// Triangular inverse, Fig. 4: trtri(TL); BL := BL TL; BL := -BR^{-1} BL;
+// trtri(BR).
+static void trtri_rec(Ctx &c, bool unit, i64 n, double *A, i64 lda)
+{
+    if (n <= 0) return;
+    if (n <= g_params.trtri_c) { trti2(c, unit, n, A, lda); return; }
+    const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
+    double *BL = A + n1, *BR = A + n1 + n1 * lda;
+    trtri_rec(c, unit, n1, A, lda);
+    trmm_rln(c, unit, n2, n1, A, lda, BL, lda);
+    trsm_lln(c, unit, n2, n1, -1.0, BR, lda, BL, lda);
+    trtri_rec(c, unit, n2, BR, lda);
+}
+
+// A := L^T L: lauum(A11); A11 += A21^T A21; A21 := A22^T A21; lauum(A22).
+static void lauum_rec(Ctx &c, i64 n, double *A, i64 lda)
+{
+    if (n <= 0) return;
+    if (n <= g_params.trtri_c) { lauu2(c, n, A, lda); return; }
+    const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
+    double *A21 = A + n1, *A22 = A + n1 + n1 * lda;
+    lauum_rec(c, n1, A, lda);
+    gemm(c, true, false, n1, n1, n2, 1.0, A21, lda, A21, lda, 1.0, A, lda, true);
+    trmm_llt(c, n2, n1, A22, lda, A21, lda);
+    lauum_rec(c, n2, A22, lda);
+}
+
+static bool is_l(char u) { return u == 'L' || u == 'l'; }
+static bool is_u(char u) { return u == 'U' || u == 'u'; }
+
+static int finish(Ctx &c)
+{
+    if (c.err == cudaSuccess) c.err = cudaGetLastError();
+    return c.err == cudaSuccess ? RL_SUCCESS : RL_ERR_CUDA;
+}
+
+static Ctx make_ctx(rl_stream_t s, int32_t *info, void *work, size_t lwork)
+{
+    Ctx c;
+    c.s = reinterpret_cast<cudaStream_t>(s);
+    c.info = info;
+    c.work = work;
+    c.lwork = lwork;
+    c.num_sms = device_sms();
+    return c;
+}
+
+}  // namespace rl
+
+using namespace rl;
+
+extern "C" {
+
+int rl_dpotrf(char uplo, int64_t n, double *A, int64_t lda, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream)
+{
+    (void)work; (void)lwork;
+    if (!is_l(uplo) && !is_u(uplo)) return -1;
+    if (n < 0) return -2;
+    if (n > 0 && A == nullptr) return -3;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (info == nullptr) return RL_ERR_NULL_POINTER;
+    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
+    Ctx c = make_ctx(stream, info, work, lwork);
+    c.abort = info;
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    potrf_rec(c, n, A, lda, 0);
+    return finish(c);
+}
+
+size_t rl_dgetrf_work_size(int64_t m, int64_t n)
+{
+    (void)m; (void)n;
+    return panel_ws_bytes();
+}
+
+int rl_dgetrf(int64_t m, int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info,
+              void *work, size_t lwork, rl_stream_t stream)
+{
+    if (m < 0) return -1;
+    if (n < 0) return -2;
+    if (m > 0 && n > 0 && A == nullptr) return -3;
+    if (lda < (m > 1 ? m : 1)) return -4;
+    if (m > INT32_MAX - 1) return RL_ERR_UNSUPPORTED;
+    if (info == nullptr || (ipiv == nullptr && m > 0 && n > 0)) return RL_ERR_NULL_POINTER;
+    if (m > 0 && n > 0 && (work == nullptr || lwork < rl_dgetrf_work_size(m, n))) return RL_ERR_WORKSPACE;
+    Ctx c = make_ctx(stream, info, work, lwork);
+    c.abort = nullptr;   // a zero pivot does not stop the LU factorization
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    getrf_rec(c, A, lda, m, ipiv, 0, m, n);
+    return finish(c);
+}
+
+int rl_dtrtri(char uplo, char diag, int64_t n, double *A, int64_t lda, int32_t *info,
+              void *work, size_t lwork, rl_stream_t stream)
+{
+    if (!is_l(uplo) && !is_u(uplo)) return -1;
+    const bool unit = (diag == 'U' || diag == 'u');
+    if (!unit && diag != 'N' && diag != 'n') return -2;
+    if (n < 0) return -3;
+    if (n > 0 && A == nullptr) return -4;
+    if (lda < (n > 1 ? n : 1)) return -5;
+    if (info == nullptr) return RL_ERR_NULL_POINTER;
+    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
+    Ctx c = make_ctx(stream, info, work, lwork);
+    c.abort = info;
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    if (!unit) diag_zero_scan(c, n, A, lda);
+    trtri_rec(c, unit, n, A, lda);
+    return finish(c);
+}
+
+int rl_dlauum(char uplo, int64_t n, double *A, int64_t lda, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream)
+{
+    if (!is_l(uplo) && !is_u(uplo)) return -1;
+    if (n < 0) return -2;
+    if (n > 0 && A == nullptr) return -3;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (info == nullptr) return RL_ERR_NULL_POINTER;
+    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
+    Ctx c = make_ctx(stream, info, work, lwork);
+    c.abort = info;
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    lauum_rec(c, n, A, lda);
+    return finish(c);
+}
+
+int rl_dpotri(char uplo, int64_t n, double *A, int64_t lda, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream)
+{
+    if (!is_l(uplo) && !is_u(uplo)) return -1;
+    if (n < 0) return -2;
+    if (n > 0 && A == nullptr) return -3;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (info == nullptr) return RL_ERR_NULL_POINTER;
+    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
+    Ctx c = make_ctx(stream, info, work, lwork);
+    c.abort = info;
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    diag_zero_scan(c, n, A, lda);
+    trtri_rec(c, false, n, A, lda);
+    lauum_rec(c, n, A, lda);
+    return finish(c);
+}
+
+// ---- host-buffer forms -------------------------------------------------------
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t rl_host_work_size(const char *routine, int64_t m, int64_t n, int64_t lda)
+{
+    if (routine == nullptr || m < 0 || n < 0 || lda < 1) return 0;
+    const size_t mat = align256((size_t)lda * (size_t)(n > 0 ? n : 1) * sizeof(double));
+    if (std::strcmp(routine, "dpotrf") == 0) return mat + 256;
+    if (std::strcmp(routine, "dgetrf") == 0)
+        return mat + 256 + align256((size_t)(m < n ? m : n) * sizeof(int32_t) + 4) +
+               align256(rl_dgetrf_work_size(m, n));
+    return 0;
+}
+
+int rl_dpotrf_host(char uplo, int64_t n, double *A_host, int64_t lda, int32_t *info_host,
+                   void *work, size_t lwork, rl_stream_t stream)
+{
+    if (!is_l(uplo) && !is_u(uplo)) return -1;
+    if (n < 0) return -2;
+    if (n > 0 && A_host == nullptr) return -3;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (info_host == nullptr) return RL_ERR_NULL_POINTER;
+    if (work == nullptr || lwork < rl_host_work_size("dpotrf", n, n, lda)) return RL_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)lda * (size_t)n * sizeof(double);
+    char *w = static_cast<char *>(work);
+    double *dA = reinterpret_cast<double *>(w);
+    int32_t *dinfo = reinterpret_cast<int32_t *>(w + align256(bytes > 0 ? bytes : 8));
+    if (bytes && cudaMemcpyAsync(dA, A_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return RL_ERR_CUDA;
+    int st = rl_dpotrf(uplo, n, dA, lda, dinfo, nullptr, 0, stream);
+    if (st != RL_SUCCESS) return st;
+    if (bytes && cudaMemcpyAsync(A_host, dA, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return RL_ERR_CUDA;
+    if (cudaMemcpyAsync(info_host, dinfo, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RL_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? RL_SUCCESS : RL_ERR_CUDA;
+}
+
+int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda, int32_t *ipiv_host,
+                   int32_t *info_host, void *work, size_t lwork, rl_stream_t stream)
+{
+    if (m < 0) return -1;
+    if (n < 0) return -2;
+    if (m > 0 && n > 0 && A_host == nullptr) return -3;
+    if (lda < (m > 1 ? m : 1)) return -4;
+    if (info_host == nullptr || (ipiv_host == nullptr && m > 0 && n > 0)) return RL_ERR_NULL_POINTER;
+    if (work == nullptr || lwork < rl_host_work_size("dgetrf", m, n, lda)) return RL_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)lda * (size_t)n * sizeof(double);
+    const size_t mn = (size_t)(m < n ? m : n);
+    char *w = static_cast<char *>(work);
+    double *dA = reinterpret_cast<double *>(w);
+    char *p = w + align256(bytes > 0 ? bytes : 8);
+    int32_t *dinfo = reinterpret_cast<int32_t *>(p);
+    p += 256;
+    int32_t *dipiv = reinterpret_cast<int32_t *>(p);
+    p += align256(mn * sizeof(int32_t) + 4);
+    void *ws = p;
+    const size_t wsz = rl_dgetrf_work_size(m, n);
+    if (bytes && cudaMemcpyAsync(dA, A_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return RL_ERR_CUDA;
+    int st = rl_dgetrf(m, n, dA, lda, dipiv, dinfo, ws, wsz, stream);
+    if (st != RL_SUCCESS) return st;
+    if (bytes && cudaMemcpyAsync(A_host, dA, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return RL_ERR_CUDA;
+    if (mn && cudaMemcpyAsync(ipiv_host, dipiv, mn * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return RL_ERR_CUDA;
+    if (cudaMemcpyAsync(info_host, dinfo, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RL_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? RL_SUCCESS : RL_ERR_CUDA;
+}
+
+// ---- parameters, accounting, status ------------------------------------------
+
+int rl_set_param(int key, int64_t value)
+{
+    switch (key) {
+    case RL_PARAM_POTRF_CROSSOVER:
+        if (value < 1 || value > 64) return RL_ERR_PARAM;
+        g_params.potrf_c = (int)value;
+        return RL_SUCCESS;
+    case RL_PARAM_GETRF_PANEL:
+        if (value < 1 || value > 64) return RL_ERR_PARAM;
+        g_params.getrf_nb = (int)value;
+        return RL_SUCCESS;
+    case RL_PARAM_TRTRI_CROSSOVER:
+        if (value < 1 || value > 64) return RL_ERR_PARAM;
+        g_params.trtri_c = (int)value;
+        return RL_SUCCESS;
+    case RL_PARAM_SPIN_LIMIT_NS:
+        if (value < 0) return RL_ERR_PARAM;
+        g_params.spin_ns = (long long)value;
+        return RL_SUCCESS;
+    default:
+        return RL_ERR_PARAM;
+    }
+}
+
+int64_t rl_get_param(int key)
+{
+    switch (key) {
+    case RL_PARAM_POTRF_CROSSOVER: return g_params.potrf_c;
+    case RL_PARAM_GETRF_PANEL: return g_params.getrf_nb;
+    case RL_PARAM_TRTRI_CROSSOVER: return g_params.trtri_c;
+    case RL_PARAM_SPIN_LIMIT_NS: return g_params.spin_ns;
+    default: return -1;
+    }
+}
+
+uint64_t rl_launch_count(void) { return g_launches.load(); }
+
+const char *rl_status_string(int status)
+{
+    if (status < 0) return "illegal argument (LAPACK numbering: argument -status)";
+    switch (status) {
+    case RL_SUCCESS: return "success";
+    case RL_ERR_CUDA: return "CUDA runtime or launch error";
+    case RL_ERR_WORKSPACE: return "workspace missing or smaller than the size query";
+    case RL_ERR_UNSUPPORTED: return "unsupported option or size (only uplo='L' is built)";
+    case RL_ERR_NULL_POINTER: return "info or ipiv pointer is NULL";
+    case RL_ERR_PARAM: return "unknown parameter key or value out of range";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

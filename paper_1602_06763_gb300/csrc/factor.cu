@@ -1,0 +1,491 @@
+// Base cases of the recursions (Section 3: below the crossover size c the
+// recursion switches to LAPACK's unblocked routines) and the row
+// interchanges of the LU factorization.
+//
+//  k_potf2        unblocked Cholesky of a diagonal block (n <= 64), one CTA,
+//                 right-looking in shared memory; IEEE sqrt and division.
+//  k_trti2        unblocked triangular inverse (n <= 64), one CTA.
+//  k_lauu2        unblocked L^T L (n <= 64), one CTA.
+//  k_diag_scan    first exactly-zero diagonal entry (dtrtri's info).
+//  k_getf2_panel  fused LU panel: per column a pivot search (warp-shuffle
+//                 argmax, lowest row on ties), the row swap, the division of
+//                 the column by the pivot and the rank-1 update, with the
+//                 panel held in shared memory across the CTAs of one
+//                 cooperative launch; CTAs exchange their pivot candidates
+//                 through a small global workspace and a bounded grid barrier.
+//  k_laswp        row interchanges: each CTA turns the swap sequence into the
+//                 net permutation of the touched rows (in shared memory) and
+//                 then moves every touched row of its columns with one
+//                 coalesced gather and one scatter per column.
+#include <climits>
+#include "internal.cuh"
+
+namespace rl {
+
+constexpr int BASE_N = 64;
+constexpr int BASE_PACK = BASE_N * (BASE_N + 1) / 2;
+
+__device__ __forceinline__ int tix(int i, int k) { return i * (i + 1) / 2 + k; }
+
+// ----------------------------------------------------------------------------
+// potf2: for j = 0..n-1: d = a_jj; if !(d > 0) -> info; l_jj = sqrt(d);
+// column j below the diagonal divided by l_jj; trailing lower block updated
+// a_ik -= l_ij l_kj.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_potf2(int n, double *A, i64 lda, int32_t *info, i64 info_off, const int32_t *abort)
+{
+    if (abort && *abort != 0) return;
+    __shared__ double S[BASE_N][BASE_N + 1];
+    __shared__ int fail;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int i = e % n, j = e / n;
+        if (i >= j) S[i][j] = A[(i64)j * lda + i];
+    }
+    if (threadIdx.x == 0) fail = 0;
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        if (threadIdx.x == 0) {
+            double d = S[j][j];
+            if (!(d > 0.0)) fail = j + 1;
+            else S[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        if (fail) break;
+        const double ljj = S[j][j];
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) S[i][j] = S[i][j] / ljj;
+        __syncthreads();
+        const int t = n - j - 1;
+        for (int e = threadIdx.x; e < t * t; e += blockDim.x) {
+            int ii = j + 1 + e % t, kk = j + 1 + e / t;
+            if (ii >= kk) S[ii][kk] = fma(-S[ii][j], S[kk][j], S[ii][kk]);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int i = e % n, j = e / n;
+        if (i >= j) A[(i64)j * lda + i] = S[i][j];
+    }
+    if (fail && threadIdx.x == 0) *info = (int32_t)(info_off + fail);
+}
+
+void potf2(Ctx &c, i64 n, double *A, i64 lda, i64 info_off)
+{
+    if (n <= 0) return;
+    Launch L(c, K_POTF2, (double)n * n * n / 3.0, 0.0);
+    k_potf2<<<1, 256, 0, c.s>>>((int)n, A, lda, c.info, info_off, c.abort);
+}
+
+// ----------------------------------------------------------------------------
+// trti2: X = L^{-1}; thread j computes column j by forward substitution on
+// L x = e_j: x_jj = 1/l_jj; x_ij = -(sum_{k=j}^{i-1} l_ik x_kj) / l_ii.
+// L packed by rows, X packed by columns (each thread owns its column).
+// ----------------------------------------------------------------------------
+template <bool UNIT>
+__global__ void __launch_bounds__(BASE_N)
+k_trti2(int n, double *A, i64 lda, const int32_t *abort)
+{
+    if (abort && *abort != 0) return;
+    __shared__ double Lp[BASE_PACK];
+    __shared__ double Xp[BASE_PACK];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int i = e % n, k = e / n;
+        if (i >= k) Lp[tix(i, k)] = A[(i64)k * lda + i];
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    if (j < n) {
+        // column j of X occupies Xp[cs .. cs + n - j), entry i at cs + (i - j)
+        const int cs = j * n - j * (j - 1) / 2;
+        Xp[cs] = UNIT ? 1.0 : 1.0 / Lp[tix(j, j)];
+        for (int i = j + 1; i < n; ++i) {
+            double s = 0.0;
+            for (int k = j; k < i; ++k) s = fma(Lp[tix(i, k)], Xp[cs + (k - j)], s);
+            Xp[cs + (i - j)] = UNIT ? -s : -s / Lp[tix(i, i)];
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int i = e % n, jj = e / n;
+        if (i > jj || (i == jj && !UNIT)) {
+            const int cs = jj * n - jj * (jj - 1) / 2;
+            A[(i64)jj * lda + i] = Xp[cs + (i - jj)];
+        }
+    }
+}
+
+void trti2(Ctx &c, bool unit, i64 n, double *A, i64 lda)
+{
+    if (n <= 0) return;
+    Launch L(c, K_TRTI2, (double)n * n * n / 3.0, 0.0);
+    if (unit) k_trti2<true><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
+    else k_trti2<false><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
+}
+
+// ----------------------------------------------------------------------------
+// lauu2: (L^T L)_ij = sum_{k=i}^{n-1} l_ki l_kj for i >= j, from a staged copy.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_lauu2(int n, double *A, i64 lda, const int32_t *abort)
+{
+    if (abort && *abort != 0) return;
+    __shared__ double Lp[BASE_PACK];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int i = e % n, k = e / n;
+        if (i >= k) Lp[tix(i, k)] = A[(i64)k * lda + i];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int i = e % n, j = e / n;
+        if (i < j) continue;
+        double s = 0.0;
+        for (int k = i; k < n; ++k) s = fma(Lp[tix(k, i)], Lp[tix(k, j)], s);
+        A[(i64)j * lda + i] = s;
+    }
+}
+
+void lauu2(Ctx &c, i64 n, double *A, i64 lda)
+{
+    if (n <= 0) return;
+    Launch L(c, K_LAUU2, (double)n * n * n / 3.0, 0.0);
+    k_lauu2<<<1, 256, 0, c.s>>>((int)n, A, lda, c.abort);
+}
+
+// ----------------------------------------------------------------------------
+// First exactly-zero diagonal entry -> info (dtrtri leaves A unchanged then).
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+k_diag_scan(i64 n, const double *A, i64 lda, int32_t *info)
+{
+    __shared__ i64 wmin[32];
+    i64 best = LLONG_MAX;
+    for (i64 i = threadIdx.x; i < n; i += blockDim.x)
+        if (A[i * lda + i] == 0.0 && i < best) best = i;
+    for (int o = 16; o > 0; o >>= 1) {
+        i64 v = __shfl_down_sync(0xffffffffu, best, o);
+        if (v < best) best = v;
+    }
+    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (wmin[w] < best) best = wmin[w];
+        if (best != LLONG_MAX) *info = (int32_t)(best + 1);
+    }
+}
+
+void diag_zero_scan(Ctx &c, i64 n, const double *A, i64 lda)
+{
+    if (n <= 0) return;
+    Launch L(c, K_DIAG, 0.0, (double)n * sizeof(double));
+    k_diag_scan<<<1, 1024, 0, c.s>>>(n, A, lda, c.info);
+}
+
+// ----------------------------------------------------------------------------
+// LU panel.
+// ----------------------------------------------------------------------------
+constexpr int PANEL_GMAX = 256;
+constexpr int PANEL_NBMAX = 64;
+constexpr int PANEL_THREADS = 256;
+constexpr int PANEL_RMIN = 64;
+constexpr size_t PANEL_SMEM_MAX = 200 * 1024;
+
+struct PanelWS {
+    unsigned int counter;               // grid-barrier arrivals (zeroed per launch)
+    unsigned int pad[63];
+    double cand_val[2][PANEL_GMAX];     // |candidate| per CTA, double-buffered
+    long long cand_idx[2][PANEL_GMAX];  // candidate row (panel-local), LLONG_MAX = none
+    double cand_row[2][PANEL_GMAX][PANEL_NBMAX];
+    double rowj[2][PANEL_NBMAX];        // current row j, published by its owner
+};
+
+size_t panel_ws_bytes() { return sizeof(PanelWS); }
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded grid barrier: every CTA adds one arrival and waits until `target`
+// arrivals are visible, for at most spin_ns nanoseconds.  Returns false (for
+// the whole CTA) if the wait ran out.
+__device__ bool grid_barrier(unsigned *counter, unsigned target, long long spin_ns)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(counter, 1u);
+        int good = 1;
+        if (ld_acquire_u32(counter) < target) {
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire_u32(counter) < target) {
+                if ((long long)(global_ns() - t0) >= spin_ns) { good = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool better(double v, long long i, double bv, long long bi)
+{
+    return v > bv || (v == bv && i < bi);
+}
+
+// Panel: rows [0, m) x columns [0, nb) of A (panel-local), CTA g holds rows
+// [g*R, g*R + R) as a column-major slab S[c*R + r].  ipiv and info use
+// global numbering: row r of the panel is row r0 + r of the matrix.
+__global__ void __launch_bounds__(PANEL_THREADS)
+k_getf2_panel(i64 m, int nb, double *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info,
+              PanelWS *ws, int R, long long spin_ns)
+{
+    extern __shared__ double S[];
+    __shared__ double urow[PANEL_NBMAX];
+    __shared__ double wv[PANEL_THREADS / 32];
+    __shared__ long long wi[PANEL_THREADS / 32];
+    __shared__ long long s_p;
+    __shared__ int s_gw;
+
+    const int tid = threadIdx.x, G = gridDim.x, g = blockIdx.x;
+    const i64 rbeg = (i64)g * R;
+    const int rows = (int)max((i64)0, min((i64)R, m - rbeg));
+    for (int e = tid; e < rows * nb; e += blockDim.x) {
+        int r = e % rows, cc = e / rows;
+        S[cc * R + r] = A[(i64)cc * lda + rbeg + r];
+    }
+    __syncthreads();
+
+    const int mn = (int)min(m, (i64)nb);
+    for (int j = 0; j < mn; ++j) {
+        const int buf = j & 1;
+        // local candidate: largest |a_ij|, i >= j, lowest i on ties
+        double bv = -1.0;
+        long long bi = LLONG_MAX;
+        for (int r = tid; r < rows; r += blockDim.x) {
+            const i64 i = rbeg + r;
+            if (i < j) continue;
+            const double v = fabs(S[j * R + r]);
+            if (better(v, i, bv, bi)) { bv = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_down_sync(0xffffffffu, bv, o);
+            long long oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+        }
+        if ((tid & 31) == 0) { wv[tid >> 5] = bv; wi[tid >> 5] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < PANEL_THREADS / 32; ++w)
+                if (better(wv[w], wi[w], bv, bi)) { bv = wv[w]; bi = wi[w]; }
+            ws->cand_val[buf][g] = bv;
+            ws->cand_idx[buf][g] = bi;
+            s_p = bi;
+        }
+        __syncthreads();
+        {
+            const long long mine = s_p;
+            if (mine != LLONG_MAX && tid < nb) ws->cand_row[buf][g][tid] = S[tid * R + (int)(mine - rbeg)];
+            if (j >= rbeg && j < rbeg + rows && tid < nb) ws->rowj[buf][tid] = S[tid * R + (int)(j - rbeg)];
+        }
+        if (!grid_barrier(&ws->counter, (unsigned)G * (unsigned)(j + 1), spin_ns)) {
+            if (tid == 0) atomicExch(info, RL_INFO_DEVICE_TIMEOUT);
+            return;
+        }
+        // global winner (every CTA computes the same one)
+        if (tid < 32) {
+            double v = -1.0;
+            long long ix = LLONG_MAX;
+            int gw = -1;
+            for (int q = tid; q < G; q += 32) {
+                const long long qi = __ldcg(&ws->cand_idx[buf][q]);
+                const double qv = __ldcg(&ws->cand_val[buf][q]);
+                if (qi != LLONG_MAX && better(qv, qi, v, ix)) { v = qv; ix = qi; gw = q; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                double ov = __shfl_down_sync(0xffffffffu, v, o);
+                long long oi = __shfl_down_sync(0xffffffffu, ix, o);
+                int og = __shfl_down_sync(0xffffffffu, gw, o);
+                if (og >= 0 && (gw < 0 || better(ov, oi, v, ix))) { v = ov; ix = oi; gw = og; }
+            }
+            if (tid == 0) { s_p = (gw >= 0) ? ix : (long long)j; s_gw = gw; }
+        }
+        __syncthreads();
+        const long long p = s_p;
+        const int gw = s_gw;
+        if (tid < nb) urow[tid] = (gw >= 0) ? __ldcg(&ws->cand_row[buf][gw][tid]) : __ldcg(&ws->rowj[buf][tid]);
+        __syncthreads();
+        const double piv = urow[j];
+        if (g == 0 && tid == 0) ipiv[r0 + j] = (int32_t)(r0 + p + 1);
+        if (p != j) {
+            if (j >= rbeg && j < rbeg + rows && tid < nb) S[tid * R + (int)(j - rbeg)] = urow[tid];
+            if (p >= rbeg && p < rbeg + rows && tid < nb) S[tid * R + (int)(p - rbeg)] = __ldcg(&ws->rowj[buf][tid]);
+        }
+        __syncthreads();
+        if (piv != 0.0) {
+            for (int r = tid; r < rows; r += blockDim.x)
+                if (rbeg + r > j) S[j * R + r] = S[j * R + r] / piv;
+        } else if (g == 0 && tid == 0) {
+            if (*info == 0) *info = (int32_t)(r0 + j + 1);
+        }
+        __syncthreads();
+        const int nc = nb - j - 1;
+        if (nc > 0) {
+            for (int e = tid; e < rows * nc; e += blockDim.x) {
+                const int r = e % rows, cc = j + 1 + e / rows;
+                if (rbeg + r > j) S[cc * R + r] = fma(-S[j * R + r], urow[cc], S[cc * R + r]);
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < rows * nb; e += blockDim.x) {
+        int r = e % rows, cc = e / rows;
+        A[(i64)cc * lda + rbeg + r] = S[cc * R + r];
+    }
+}
+
+void getf2_panel(Ctx &c, i64 m, i64 nb, double *A, i64 lda, int32_t *ipiv, i64 r0)
+{
+    if (m <= 0 || nb <= 0) return;
+    static bool attr = false;
+    if (!attr) {
+        note(c, cudaFuncSetAttribute(k_getf2_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)PANEL_SMEM_MAX));
+        attr = true;
+    }
+    const int gmax = c.num_sms < PANEL_GMAX ? c.num_sms : PANEL_GMAX;
+    i64 R = (m + gmax - 1) / gmax;
+    if (R < PANEL_RMIN) R = PANEL_RMIN;
+    if (R > m) R = m;
+    if ((size_t)R * nb * sizeof(double) > PANEL_SMEM_MAX) { note(c, cudaErrorInvalidValue); return; }
+    const int G = (int)((m + R - 1) / R);
+    PanelWS *ws = reinterpret_cast<PanelWS *>(c.work);
+    note(c, cudaMemsetAsync(&ws->counter, 0, sizeof(unsigned), c.s));
+    int Ri = (int)R, nbi = (int)nb;
+    long long spin = g_params.spin_ns;
+    int32_t *info = c.info;
+    void *args[] = {&m, &nbi, &A, &lda, &ipiv, &r0, &info, &ws, &Ri, &spin};
+    // flops of an m x nb unblocked LU (leading terms): m nb^2 - nb^3/3
+    Launch L(c, K_PANEL, (double)m * nb * nb - (double)nb * nb * nb / 3.0,
+             2.0 * (double)m * nb * sizeof(double));
+    note(c, cudaLaunchCooperativeKernel((const void *)k_getf2_panel, dim3(G), dim3(PANEL_THREADS), args,
+                                        (size_t)R * nb * sizeof(double), c.s));
+}
+
+// ----------------------------------------------------------------------------
+// LASWP.
+// ----------------------------------------------------------------------------
+constexpr int LASWP_CHUNK = 4096;
+constexpr int LASWP_THREADS = 1024;
+constexpr int LASWP_V = (2 * LASWP_CHUNK + LASWP_THREADS - 1) / LASWP_THREADS;
+constexpr size_t LASWP_SMEM_MAX = 200 * 1024;
+
+// Swaps ipiv[k1..k2) (global 1-based rows, each target >= its row, k2-k1 <=
+// LASWP_CHUNK) on columns [c0 + blockIdx.x*cpc, ...) of A, whose rows
+// [k1, m) are involved.  Shared memory: pos[span] (span = m - k1), the
+// chunk's pivots, and the list of touched rows outside [k1, k2).
+__global__ void __launch_bounds__(LASWP_THREADS)
+k_laswp(double *A, i64 lda, i64 m, i64 c0, i64 ncols, i64 k1, i64 k2, const int32_t *ipiv, int cpc)
+{
+    extern __shared__ int sm[];
+    __shared__ int nout;
+    const int span = (int)(m - k1), K = (int)(k2 - k1);
+    int *pos = sm;             // pos[q]: relative row whose value ends at q
+    int *pv = pos + span;      // pv[t] = ipiv[k1 + t] - 1 - k1 (relative)
+    int *odst = pv + K;        // touched rows >= k2 (relative), and their sources
+    int *osrc = odst + K;
+    const int tid = threadIdx.x;
+    for (int q = tid; q < span; q += blockDim.x) pos[q] = q;
+    for (int t = tid; t < K; t += blockDim.x) pv[t] = (int)((i64)ipiv[k1 + t] - 1 - k1);
+    if (tid == 0) nout = 0;
+    __syncthreads();
+    if (tid == 0) {
+        for (int t = 0; t < K; ++t) {
+            const int p = pv[t];
+            if (p > t && p < span) { int a = pos[t]; pos[t] = pos[p]; pos[p] = a; }
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < K; t += blockDim.x) {
+        const int p = pv[t];
+        if (p >= K && p < span && pos[p] != p) {
+            const int prev = atomicOr(&pos[p], 0x40000000);
+            if ((prev & 0x40000000) == 0) {
+                const int s = atomicAdd(&nout, 1);
+                odst[s] = p;
+                osrc[s] = prev;
+            }
+        }
+    }
+    __syncthreads();
+    const int NT = K + nout;
+    const i64 cb = (i64)blockIdx.x * cpc, ce = min(ncols, cb + cpc);
+    for (i64 col = cb; col < ce; ++col) {
+        double *cp = A + (c0 + col) * lda + k1;
+        double v[LASWP_V];
+#pragma unroll
+        for (int s = 0; s < LASWP_V; ++s) {
+            const int t = tid + s * LASWP_THREADS;
+            if (t < NT) v[s] = cp[t < K ? pos[t] : osrc[t - K]];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < LASWP_V; ++s) {
+            const int t = tid + s * LASWP_THREADS;
+            if (t < NT) cp[t < K ? t : odst[t - K]] = v[s];
+        }
+        __syncthreads();
+    }
+}
+
+// Fallback for very tall matrices: one thread per column, swaps in order.
+__global__ void k_laswp_seq(double *A, i64 lda, i64 c0, i64 ncols, i64 k1, i64 k2, const int32_t *ipiv)
+{
+    const i64 col = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncols) return;
+    double *cp = A + (c0 + col) * lda;
+    for (i64 i = k1; i < k2; ++i) {
+        const i64 p = (i64)ipiv[i] - 1;
+        if (p != i) { double t = cp[i]; cp[i] = cp[p]; cp[p] = t; }
+    }
+}
+
+void laswp(Ctx &c, double *A0, i64 lda, i64 m, i64 c0, i64 ncols, i64 k1, i64 k2,
+           const int32_t *ipiv)
+{
+    if (ncols <= 0 || k2 <= k1) return;
+    static bool attr = false;
+    if (!attr) {
+        note(c, cudaFuncSetAttribute(k_laswp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)LASWP_SMEM_MAX));
+        attr = true;
+    }
+    for (i64 kb = k1; kb < k2; kb += LASWP_CHUNK) {
+        const i64 ke = (kb + LASWP_CHUNK < k2) ? kb + LASWP_CHUNK : k2;
+        const size_t smem = (size_t)((m - kb) + 3 * (ke - kb)) * sizeof(int);
+        // algorithmic bytes: every interchange reads and writes two rows
+        Launch L(c, K_LASWP, 0.0, 32.0 * (double)(ke - kb) * (double)ncols);
+        if (smem <= LASWP_SMEM_MAX) {
+            i64 grid = ncols < 2 * (i64)c.num_sms ? ncols : 2 * (i64)c.num_sms;
+            const i64 cpc = (ncols + grid - 1) / grid;
+            grid = (ncols + cpc - 1) / cpc;
+            k_laswp<<<(unsigned)grid, LASWP_THREADS, smem, c.s>>>(A0, lda, m, c0, ncols, kb, ke, ipiv, (int)cpc);
+        } else {
+            k_laswp_seq<<<(unsigned)((ncols + 127) / 128), 128, 0, c.s>>>(A0, lda, c0, ncols, kb, ke, ipiv);
+        }
+    }
+}
+
+}  // namespace rl

@@ -1,0 +1,116 @@
+// Internal declarations shared by the CUDA translation units of librelgpu.
+// Column-major storage with leading dimensions throughout; all sizes int64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <atomic>
+
+#include "../../include/relgpu.h"
+
+namespace rl {
+
+using i64 = int64_t;
+
+// Kernel-launch accounting (host side).
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Process-wide tunables (see rl_set_param).
+struct Params {
+    int potrf_c = 64;        // dpotrf crossover (base-case order)
+    int getrf_nb = 32;       // dgetrf panel width
+    int trtri_c = 64;        // dtrtri / dlauum crossover
+    long long spin_ns = 2000000000LL;
+};
+extern Params g_params;
+
+// Per-call context: stream, device info/abort word, workspace, device facts.
+struct Ctx {
+    cudaStream_t s = nullptr;
+    int32_t *info = nullptr;     // device; nonzero => later kernels skip (abort)
+    const int32_t *abort = nullptr;  // where kernels look for an abort signal
+    void *work = nullptr;
+    size_t lwork = 0;
+    int num_sms = 0;
+    cudaError_t err = cudaSuccess;   // first launch error seen
+};
+
+int device_sms();
+void note(Ctx &c, cudaError_t e);
+
+// ---- per-kernel tracing (trace.cu) -----------------------------------------
+// Kernel kinds, in the order rl_trace_read reports them.
+enum Kind {
+    K_GEMM = 0, K_SYRK, K_TRSM, K_TRMM, K_POTF2, K_TRTI2, K_LAUU2, K_DIAG,
+    K_PANEL, K_LASWP, K_COUNT
+};
+extern std::atomic<int> g_trace_on;
+// Bracket one kernel launch: with tracing on, CUDA events are recorded on the
+// launch stream around it and the launch's algorithmic flops and bytes are
+// attributed to its kind.  The destructor counts the launch and records the
+// launch error, if any.
+struct Launch {
+    Ctx &c;
+    int kind;
+    double flops, bytes;
+    void *ev0 = nullptr;
+    Launch(Ctx &ctx, int k, double f, double b);
+    ~Launch();
+};
+
+// Largest triangle handled by the TRSM/TRMM/base kernels in shared memory.
+constexpr int TRX_NB = 64;
+// GEMM tile.
+constexpr int GEMM_BM = 64, GEMM_BN = 64, GEMM_BK = 16;
+
+// Split rule (Section 3 footnote: halves that are multiples of 8 "where
+// possible"); on the GPU the quantum is a tile size q so sub-blocks start on
+// tile boundaries: n1 = q * floor((n + q) / (2q)) clamped to [q, n-1].
+inline i64 split_q(i64 n, i64 q)
+{
+    if (n <= 1) return 0;
+    if (n <= q) return n / 2 > 0 ? n / 2 : 1;
+    i64 n1 = q * ((n + q) / (2 * q));
+    if (n1 < q) n1 = q;
+    if (n1 >= n) n1 = n - 1;
+    return n1;
+}
+
+// ---- BLAS-3 layer (blas3.cu) ----------------------------------------------
+// C(m x n) := beta*C + alpha*op(A) op(B); lower=true writes only i >= j of a
+// square C (SYRK form, A and B may alias).
+void gemm(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, double alpha,
+          const double *A, i64 lda, const double *B, i64 ldb, double beta,
+          double *C, i64 ldc, bool lower = false);
+
+// B(m x n) := alpha * L^{-1} B, L lower m x m (unit or not).
+void trsm_lln(Ctx &c, bool unit, i64 m, i64 n, double alpha, const double *L,
+              i64 ldl, double *B, i64 ldb);
+// B(m x n) := B L^{-T}, L lower n x n, non-unit.
+void trsm_rlt(Ctx &c, i64 m, i64 n, const double *L, i64 ldl, double *B, i64 ldb);
+// B(m x n) := L^{-T} B, L lower m x m, non-unit.
+void trsm_llt(Ctx &c, i64 m, i64 n, const double *L, i64 ldl, double *B, i64 ldb);
+// B(m x n) := U^{-1} B, U upper m x m, non-unit.
+void trsm_lun(Ctx &c, i64 m, i64 n, const double *U, i64 ldu, double *B, i64 ldb);
+// B(m x n) := B L, L lower n x n (unit or not).
+void trmm_rln(Ctx &c, bool unit, i64 m, i64 n, const double *L, i64 ldl, double *B, i64 ldb);
+// B(m x n) := L^T B, L lower m x m, non-unit.
+void trmm_llt(Ctx &c, i64 m, i64 n, const double *L, i64 ldl, double *B, i64 ldb);
+
+// ---- base cases and row interchanges (factor.cu) ---------------------------
+void potf2(Ctx &c, i64 n, double *A, i64 lda, i64 info_off);
+void trti2(Ctx &c, bool unit, i64 n, double *A, i64 lda);
+void lauu2(Ctx &c, i64 n, double *A, i64 lda);
+void diag_zero_scan(Ctx &c, i64 n, const double *A, i64 lda);
+// Panel LU of the m x nb block at A (row/col offset r0 in the full matrix);
+// writes ipiv[r0 .. r0+min(m,nb)) as global 1-based rows.
+void getf2_panel(Ctx &c, i64 m, i64 nb, double *A, i64 lda, int32_t *ipiv, i64 r0);
+// Apply ipiv[k1..k2) (global 1-based rows of the matrix at A0, which has
+// m rows) to columns [c0, c0 + ncols).
+void laswp(Ctx &c, double *A0, i64 lda, i64 m, i64 c0, i64 ncols, i64 k1, i64 k2,
+           const int32_t *ipiv);
+
+size_t panel_ws_bytes();
+
+}  // namespace rl

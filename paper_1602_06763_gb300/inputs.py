@@ -179,6 +179,36 @@ def general_spectrum(n: int, cond: float, seed: int, reflectors=64):
     return _fortran(householder_product_apply(UD, reflectors, seed + 1, "R"))
 
 
+def spd_bbt_device(n: int, seed: int, device="cuda"):
+    """Large-n form of spd_bbt generated on the GPU with torch (input
+    generation only): B iid N(0,1) from torch's seeded Philox generator, the
+    product B B^T formed in FP32 (the FP32 rounding of B B^T is far below the
+    n I shift, so A stays SPD with condition number below ~5), widened to
+    FP64, the lower triangle mirrored for exact symmetry, plus n I.
+    Returns a torch float64 tensor holding A in column-major order (A is
+    symmetric, so the row-major buffer is the same matrix)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    B = torch.randn(n, n, generator=g, device=device, dtype=torch.float32)
+    G = torch.matmul(B, B.T).double()
+    del B
+    A = torch.tril(G)
+    A = A + torch.tril(G, -1).T
+    del G
+    A.diagonal().add_(float(n))
+    return A.contiguous()
+
+
+def uniform_device(m: int, n: int, seed: int, device="cuda"):
+    """Entries iid Uniform(-1, 1) drawn on the GPU (torch Philox), returned as
+    a float64 tensor of n*m elements holding an m x n column-major matrix."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return (torch.rand(n, m, generator=g, device=device, dtype=torch.float64) * 2.0 - 1.0).contiguous()
+
+
 def bucket_sizes(count: int, lo: int, hi: int, seed: int):
     """Matrix orders drawn uniformly from lo..hi inclusive (batched form)."""
     return rng(seed).integers(lo, hi + 1, size=count).astype(np.int64)

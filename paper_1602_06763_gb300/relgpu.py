@@ -1,0 +1,184 @@
+"""Thin ctypes binding of librelgpu.so (the C ABI declared in include/relgpu.h).
+
+Argument marshalling only: every function forwards to the C entry point of
+the same name.  Buffers may be given as integers (raw device or host
+addresses) or as torch tensors (their ``data_ptr()``); streams as integers,
+``torch.cuda.Stream`` objects or None (the current torch stream).  The library
+must have been built (``_build.build()``); if it is missing, importing this
+module raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librelgpu.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with paper_1602_06763_gb300._build.build() "
+        "(the factorizations run only in the CUDA library; there is no fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+_i64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_ch = ctypes.c_char
+
+_SIGS = {
+    "rl_dpotrf": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_dgetrf": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
+    "rl_dgetrf_work_size": (_sz, [_i64, _i64]),
+    "rl_dtrtri": (ctypes.c_int, [_ch, _ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_dlauum": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_dpotri": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_host_work_size": (_sz, [ctypes.c_char_p, _i64, _i64, _i64]),
+    "rl_dpotrf_host": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_dgetrf_host": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
+    "rl_set_param": (ctypes.c_int, [ctypes.c_int, _i64]),
+    "rl_get_param": (_i64, [ctypes.c_int]),
+    "rl_launch_count": (ctypes.c_uint64, []),
+    "rl_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "rl_trace_enable": (ctypes.c_int, [ctypes.c_int]),
+    "rl_trace_kinds": (ctypes.c_int, []),
+    "rl_trace_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                     ctypes.POINTER(ctypes.c_uint64),
+                                     ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+RL_SUCCESS = 0
+RL_ERR_CUDA = 1
+RL_ERR_WORKSPACE = 2
+RL_ERR_UNSUPPORTED = 3
+RL_ERR_NULL_POINTER = 4
+RL_ERR_PARAM = 5
+RL_INFO_DEVICE_TIMEOUT = -1000
+
+RL_PARAM_POTRF_CROSSOVER = 1
+RL_PARAM_GETRF_PANEL = 2
+RL_PARAM_TRTRI_CROSSOVER = 3
+RL_PARAM_SPIN_LIMIT_NS = 4
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _c(ch):
+    return ch.encode() if isinstance(ch, str) else ch
+
+
+def rl_dpotrf(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
+    return _lib.rl_dpotrf(_c(uplo), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_dgetrf(m, n, A, lda, ipiv, info, work, lwork, stream=None):
+    return _lib.rl_dgetrf(m, n, _ptr(A), lda, _ptr(ipiv), _ptr(info), _ptr(work), lwork,
+                          _stream(stream))
+
+
+def rl_dgetrf_work_size(m, n):
+    return int(_lib.rl_dgetrf_work_size(m, n))
+
+
+def rl_dtrtri(uplo, diag, n, A, lda, info, work=None, lwork=0, stream=None):
+    return _lib.rl_dtrtri(_c(uplo), _c(diag), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork,
+                          _stream(stream))
+
+
+def rl_dlauum(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
+    return _lib.rl_dlauum(_c(uplo), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_dpotri(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
+    return _lib.rl_dpotri(_c(uplo), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_host_work_size(routine, m, n, lda):
+    return int(_lib.rl_host_work_size(routine.encode(), m, n, lda))
+
+
+def rl_dpotrf_host(uplo, n, A_host, lda, info_host, work, lwork, stream=None):
+    return _lib.rl_dpotrf_host(_c(uplo), n, _ptr(A_host), lda, _ptr(info_host), _ptr(work), lwork,
+                               _stream(stream))
+
+
+def rl_dgetrf_host(m, n, A_host, lda, ipiv_host, info_host, work, lwork, stream=None):
+    return _lib.rl_dgetrf_host(m, n, _ptr(A_host), lda, _ptr(ipiv_host), _ptr(info_host),
+                               _ptr(work), lwork, _stream(stream))
+
+
+def rl_set_param(key, value):
+    return _lib.rl_set_param(key, value)
+
+
+def rl_get_param(key):
+    return int(_lib.rl_get_param(key))
+
+
+def rl_launch_count():
+    return int(_lib.rl_launch_count())
+
+
+def rl_status_string(status):
+    return _lib.rl_status_string(status).decode()
+
+
+def rl_trace_enable(on):
+    return _lib.rl_trace_enable(1 if on else 0)
+
+
+def rl_trace_kinds():
+    return int(_lib.rl_trace_kinds())
+
+
+def rl_trace_read(kind):
+    """Returns (name, launches, ms, flops, bytes) for one kernel kind."""
+    name = ctypes.c_char_p()
+    launches = ctypes.c_uint64()
+    ms = ctypes.c_double()
+    flops = ctypes.c_double()
+    nbytes = ctypes.c_double()
+    st = _lib.rl_trace_read(kind, ctypes.byref(name), ctypes.byref(launches), ctypes.byref(ms),
+                            ctypes.byref(flops), ctypes.byref(nbytes))
+    if st != RL_SUCCESS:
+        raise ValueError(f"bad trace kind {kind}")
+    return name.value.decode(), int(launches.value), ms.value, flops.value, nbytes.value
+
+
+def trace_summary():
+    """All kinds with at least one traced launch, as a dict keyed by name."""
+    out = {}
+    for k in range(rl_trace_kinds()):
+        name, launches, ms, flops, nbytes = rl_trace_read(k)
+        if launches:
+            out[name] = {"launches": launches, "ms": ms, "flops": flops, "bytes": nbytes}
+    return out
+
+
+def check(status, what="call"):
+    """Raise RuntimeError for a nonzero return value of an entry point."""
+    if status != RL_SUCCESS:
+        raise RuntimeError(f"{what} failed: status {status} ({rl_status_string(status)})")
+    return status

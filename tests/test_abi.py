@@ -1,0 +1,68 @@
+"""The C-ABI library loads on a machine without a GPU, exports every symbol
+that include/relgpu.h declares, and its host-side logic (argument checking,
+size queries, parameters, status strings) works without touching the device.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "relgpu.h")
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1602_06763_gb300 import _build
+    return _build.build()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rl_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_routines():
+    names = declared_functions()
+    for want in ("rl_dpotrf", "rl_dgetrf", "rl_dtrtri", "rl_dlauum", "rl_dpotri",
+                 "rl_dgetrf_work_size", "rl_status_string"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(built):
+    lib = ctypes.CDLL(built)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_logic_without_gpu(built):
+    from paper_1602_06763_gb300 import relgpu as r
+    # argument errors are detected on the host before any CUDA call
+    assert r.rl_dpotrf("X", 4, 0, 4, 0, None, 0, 0) == -1
+    assert r.rl_dpotrf("L", -2, 0, 4, 0, None, 0, 0) == -2
+    assert r.rl_dpotrf("L", 4, 0, 4, 0, None, 0, 0) == -3
+    assert r.rl_dpotrf("L", 4, 8, 3, 0, None, 0, 0) == -4
+    assert r.rl_dgetrf(-1, 1, 8, 1, 8, 8, None, 0, 0) == -1
+    assert r.rl_dgetrf(3, -1, 8, 3, 8, 8, None, 0, 0) == -2
+    assert r.rl_dgetrf(3, 3, 8, 2, 8, 8, None, 0, 0) == -4
+    assert r.rl_dgetrf(3, 3, 8, 3, 8, 8, None, 0, 0) == r.RL_ERR_WORKSPACE
+    assert r.rl_dtrtri("L", "X", 3, 8, 3, 8, None, 0, 0) == -2
+    assert r.rl_dtrtri("L", "N", 3, 8, 2, 8, None, 0, 0) == -5
+    assert r.rl_dlauum("Q", 3, 8, 3, 8, None, 0, 0) == -1
+    assert r.rl_dpotri("L", 3, 8, 3, 0, None, 0, 0) == r.RL_ERR_NULL_POINTER
+    assert r.rl_dpotrf("U", 3, 8, 3, 8, None, 0, 0) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_dgetrf_work_size(16384, 16384) > 0
+    assert r.rl_host_work_size("dpotrf", 10, 10, 12) >= 10 * 12 * 8
+    assert r.rl_host_work_size("nope", 10, 10, 10) == 0
+    # parameters
+    assert r.rl_get_param(r.RL_PARAM_POTRF_CROSSOVER) == 64
+    assert r.rl_set_param(r.RL_PARAM_POTRF_CROSSOVER, 65) == r.RL_ERR_PARAM
+    assert r.rl_set_param(99, 1) == r.RL_ERR_PARAM
+    assert r.rl_get_param(99) == -1
+    assert r.rl_set_param(r.RL_PARAM_GETRF_PANEL, 16) == 0
+    assert r.rl_get_param(r.RL_PARAM_GETRF_PANEL) == 16
+    assert r.rl_set_param(r.RL_PARAM_GETRF_PANEL, 32) == 0
+    assert "workspace" in r.rl_status_string(r.RL_ERR_WORKSPACE)
+    assert "illegal" in r.rl_status_string(-3)
