@@ -125,6 +125,34 @@ int rl_dpotri(char uplo, int64_t n, double *A, int64_t lda, int32_t *info,
               void *work, size_t lwork, rl_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * BLAS-3 layer (Section 2: the Level-3 kernels the recursions are built on),
+ * exported for direct use and per-kernel measurement.  BLAS semantics and
+ * argument numbering; all matrices on the device, stream-ordered, no
+ * workspace.  Supported options (others return RL_ERR_UNSUPPORTED):
+ *   rl_dgemm  any transa/transb: C := alpha op(A) op(B) + beta C
+ *   rl_dsyrk  uplo 'L', trans 'N' (C := alpha A A^T + beta C) or 'T'
+ *             (C := alpha A^T A + beta C); only the lower triangle is written
+ *   rl_dtrsm  uplo 'L' with (side 'L', transa 'N', diag 'N'/'U'),
+ *             (side 'L', transa 'T', diag 'N'), (side 'R', transa 'T',
+ *             diag 'N'); and uplo 'U', side 'L', transa 'N', diag 'N'
+ *   rl_dtrmm  uplo 'L', alpha 1, with (side 'R', transa 'N', diag 'N'/'U')
+ *             or (side 'L', transa 'T', diag 'N')
+ * TRSM and TRMM recurse by halving the triangle (GEMM off the diagonal,
+ * substitution in shared memory for blocks of order <= 64).
+ * ------------------------------------------------------------------------- */
+int rl_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+             const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+             double *C, int64_t ldc, rl_stream_t stream);
+int rl_dsyrk(char uplo, char trans, int64_t n, int64_t k, double alpha, const double *A,
+             int64_t lda, double beta, double *C, int64_t ldc, rl_stream_t stream);
+int rl_dtrsm(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+             double alpha, const double *A, int64_t lda, double *B, int64_t ldb,
+             rl_stream_t stream);
+int rl_dtrmm(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+             double alpha, const double *A, int64_t lda, double *B, int64_t ldb,
+             rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Host-buffer forms (end-to-end use from host memory).  A_host (and
  * ipiv_host, info_host) are HOST pointers, ideally page-locked.  `work` is a
  * device buffer of at least rl_host_work_size(routine, m, n, lda) bytes that holds

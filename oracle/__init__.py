@@ -57,6 +57,13 @@ def _lib():
             "or_potrs": (None, [_i64, _i64, _ptr, _i64, _ptr, _i64]),
             "or_gemm": (None, [ctypes.c_int, ctypes.c_int, _i64, _i64, _i64, _dbl,
                                _ptr, _i64, _ptr, _i64, _ptr, _i64]),
+            "or_syrk_lower": (None, [ctypes.c_int, _i64, _i64, _dbl, _ptr, _i64, _ptr, _i64]),
+            "or_trsm_llnx": (None, [ctypes.c_int, _i64, _i64, _dbl, _ptr, _i64, _ptr, _i64]),
+            "or_trsm_rltn": (None, [_i64, _i64, _ptr, _i64, _ptr, _i64]),
+            "or_trsm_lunn": (None, [_i64, _i64, _ptr, _i64, _ptr, _i64]),
+            "or_trsm_lltn": (None, [_i64, _i64, _ptr, _i64, _ptr, _i64]),
+            "or_trmm_rlnn": (None, [_i64, _i64, _ptr, _i64, _ptr, _i64]),
+            "or_trmm_lltn": (None, [_i64, _i64, _ptr, _i64, _ptr, _i64]),
             "or_res_chol": (_dbl, [_i64, _ptr, _i64, _ptr, _i64]),
             "or_res_lu": (_dbl, [_i64, _i64, _ptr, _i64, _ptr, _i64, _ptr]),
             "or_res_trtri": (_dbl, [_i64, _ptr, _i64, _ptr, _i64]),
@@ -178,6 +185,64 @@ def gemm(A, B, C, alpha=1.0, ta=False, tb=False):
     _lib().or_gemm(int(ta), int(tb), m, n, k, alpha, _p(A), _ld(A), _p(B), _ld(B),
                    _p(C), _ld(C))
     return C
+
+
+def syrk_lower(A, C, alpha=1.0, trans=False):
+    """Lower triangle of C + alpha op(A) op(A)^T (op(A) = A^T if trans)."""
+    A = _f64(A)
+    C = _f64(C)
+    n = C.shape[0]
+    k = A.shape[0] if trans else A.shape[1]
+    _lib().or_syrk_lower(int(trans), n, k, alpha, _p(A), _ld(A), _p(C), _ld(C))
+    return C
+
+
+def trsm_lln(L, B, alpha=1.0, unit=False):
+    """alpha L^{-1} B, L lower (forward substitution by columns)."""
+    L = _f64(L)
+    B = _f64(B)
+    _lib().or_trsm_llnx(int(unit), B.shape[0], B.shape[1], alpha, _p(L), _ld(L), _p(B), _ld(B))
+    return B
+
+
+def trsm_rlt(L, B):
+    """B L^{-T}, L lower non-unit."""
+    L = _f64(L)
+    B = _f64(B)
+    _lib().or_trsm_rltn(B.shape[0], B.shape[1], _p(L), _ld(L), _p(B), _ld(B))
+    return B
+
+
+def trsm_lun(U, B):
+    """U^{-1} B, U upper non-unit (back substitution)."""
+    U = _f64(U)
+    B = _f64(B)
+    _lib().or_trsm_lunn(B.shape[0], B.shape[1], _p(U), _ld(U), _p(B), _ld(B))
+    return B
+
+
+def trsm_llt(L, B):
+    """L^{-T} B, L lower non-unit."""
+    L = _f64(L)
+    B = _f64(B)
+    _lib().or_trsm_lltn(B.shape[0], B.shape[1], _p(L), _ld(L), _p(B), _ld(B))
+    return B
+
+
+def trmm_rln(L, B):
+    """B L, L lower non-unit."""
+    L = _f64(L)
+    B = _f64(B)
+    _lib().or_trmm_rlnn(B.shape[0], B.shape[1], _p(L), _ld(L), _p(B), _ld(B))
+    return B
+
+
+def trmm_llt(L, B):
+    """L^T B, L lower non-unit."""
+    L = _f64(L)
+    B = _f64(B)
+    _lib().or_trmm_lltn(B.shape[0], B.shape[1], _p(L), _ld(L), _p(B), _ld(B))
+    return B
 
 
 def getrs(LU, ipiv, B):

@@ -46,7 +46,7 @@ static void potrf_rec(Ctx &c, i64 n, double *A, i64 lda, i64 off)
     const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
     double *A21 = A + n1, *A22 = A + n1 + n1 * lda;
     potrf_rec(c, n1, A, lda, off);
-    trsm_rlt(c, n2, n1, A, lda, A21, lda);
+    trsm_rlt(c, n2, n1, 1.0, A, lda, A21, lda);
     gemm(c, false, true, n2, n2, n1, -1.0, A21, lda, A21, lda, 1.0, A22, lda, true);
     potrf_rec(c, n2, A22, lda, off + n1);
 }
@@ -86,7 +86,7 @@ static void trtri_rec(Ctx &c, bool unit, i64 n, double *A, i64 lda)
     const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
     double *BL = A + n1, *BR = A + n1 + n1 * lda;
     trtri_rec(c, unit, n1, A, lda);
-    trmm_rln(c, unit, n2, n1, A, lda, BL, lda);
+    trmm_rln(c, unit, n2, n1, 1.0, A, lda, BL, lda);
     trsm_lln(c, unit, n2, n1, -1.0, BR, lda, BL, lda);
     trtri_rec(c, unit, n2, BR, lda);
 }
@@ -100,7 +100,7 @@ static void lauum_rec(Ctx &c, i64 n, double *A, i64 lda)
     double *A21 = A + n1, *A22 = A + n1 + n1 * lda;
     lauum_rec(c, n1, A, lda);
     gemm(c, true, false, n1, n1, n2, 1.0, A21, lda, A21, lda, 1.0, A, lda, true);
-    trmm_llt(c, n2, n1, A22, lda, A21, lda);
+    trmm_llt(c, n2, n1, 1.0, A22, lda, A21, lda);
     lauum_rec(c, n2, A22, lda);
 }
 
@@ -220,6 +220,91 @@ int rl_dpotri(char uplo, int64_t n, double *A, int64_t lda, int32_t *info, void 
     diag_zero_scan(c, n, A, lda);
     trtri_rec(c, false, n, A, lda);
     lauum_rec(c, n, A, lda);
+    return finish(c);
+}
+
+// ---- BLAS-3 layer ------------------------------------------------------------
+
+static bool is_n(char t) { return t == 'N' || t == 'n'; }
+static bool is_t(char t) { return t == 'T' || t == 't' || t == 'C' || t == 'c'; }
+static i64 imax1(i64 v) { return v > 1 ? v : 1; }
+
+int rl_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+             const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C,
+             int64_t ldc, rl_stream_t stream)
+{
+    if (!is_n(transa) && !is_t(transa)) return -1;
+    if (!is_n(transb) && !is_t(transb)) return -2;
+    if (m < 0) return -3;
+    if (n < 0) return -4;
+    if (k < 0) return -5;
+    const bool ta = is_t(transa), tb = is_t(transb);
+    if (lda < imax1(ta ? k : m)) return -8;
+    if (ldb < imax1(tb ? n : k)) return -10;
+    if (ldc < imax1(m)) return -13;
+    Ctx c = make_ctx(stream, nullptr, nullptr, 0);
+    gemm(c, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, false);
+    return finish(c);
+}
+
+int rl_dsyrk(char uplo, char trans, int64_t n, int64_t k, double alpha, const double *A,
+             int64_t lda, double beta, double *C, int64_t ldc, rl_stream_t stream)
+{
+    if (!is_l(uplo) && !is_u(uplo)) return -1;
+    if (!is_n(trans) && !is_t(trans)) return -2;
+    if (n < 0) return -3;
+    if (k < 0) return -4;
+    const bool t = is_t(trans);
+    if (lda < imax1(t ? k : n)) return -7;
+    if (ldc < imax1(n)) return -10;
+    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
+    Ctx c = make_ctx(stream, nullptr, nullptr, 0);
+    gemm(c, t, !t, n, n, k, alpha, A, lda, A, lda, beta, C, ldc, true);
+    return finish(c);
+}
+
+static int check_tr(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+                    int64_t lda, int64_t ldb)
+{
+    const bool left = (side == 'L' || side == 'l');
+    if (!left && side != 'R' && side != 'r') return -1;
+    if (!is_l(uplo) && !is_u(uplo)) return -2;
+    if (!is_n(transa) && !is_t(transa)) return -3;
+    if (diag != 'N' && diag != 'n' && diag != 'U' && diag != 'u') return -4;
+    if (m < 0) return -5;
+    if (n < 0) return -6;
+    if (lda < imax1(left ? m : n)) return -9;
+    if (ldb < imax1(m)) return -11;
+    return 0;
+}
+
+int rl_dtrsm(char side, char uplo, char transa, char diag, int64_t m, int64_t n, double alpha,
+             const double *A, int64_t lda, double *B, int64_t ldb, rl_stream_t stream)
+{
+    int st = check_tr(side, uplo, transa, diag, m, n, lda, ldb);
+    if (st) return st;
+    const bool left = (side == 'L' || side == 'l'), lower = is_l(uplo), tr = is_t(transa);
+    const bool unit = (diag == 'U' || diag == 'u');
+    Ctx c = make_ctx(stream, nullptr, nullptr, 0);
+    if (lower && left && !tr) trsm_lln(c, unit, m, n, alpha, A, lda, B, ldb);
+    else if (lower && left && tr && !unit) trsm_llt(c, m, n, alpha, A, lda, B, ldb);
+    else if (lower && !left && tr && !unit) trsm_rlt(c, m, n, alpha, A, lda, B, ldb);
+    else if (!lower && left && !tr && !unit) trsm_lun(c, m, n, alpha, A, lda, B, ldb);
+    else return RL_ERR_UNSUPPORTED;
+    return finish(c);
+}
+
+int rl_dtrmm(char side, char uplo, char transa, char diag, int64_t m, int64_t n, double alpha,
+             const double *A, int64_t lda, double *B, int64_t ldb, rl_stream_t stream)
+{
+    int st = check_tr(side, uplo, transa, diag, m, n, lda, ldb);
+    if (st) return st;
+    const bool left = (side == 'L' || side == 'l'), lower = is_l(uplo), tr = is_t(transa);
+    const bool unit = (diag == 'U' || diag == 'u');
+    Ctx c = make_ctx(stream, nullptr, nullptr, 0);
+    if (lower && !left && !tr) trmm_rln(c, unit, m, n, alpha, A, lda, B, ldb);
+    else if (lower && left && tr && !unit) trmm_llt(c, m, n, alpha, A, lda, B, ldb);
+    else return RL_ERR_UNSUPPORTED;
     return finish(c);
 }
 

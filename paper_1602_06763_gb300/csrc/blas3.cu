@@ -166,224 +166,131 @@ void gemm(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, double alpha, const dou
     else if (ta && !tb) launch_gemm<true, false, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     else launch_gemm<true, true, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
 }
-
 // ----------------------------------------------------------------------------
-// Triangle (order <= 64) staged in shared memory, packed by rows:
-// l_ik (k <= i) at Lp[i(i+1)/2 + k].
+// Triangle kernels for blocks of order <= 64 (the leaves of the TRSM/TRMM
+// recursion).  Each vector of B (a row or a column, depending on the side)
+// is owned by a group of 4 consecutive lanes; lane q of the group holds the
+// elements e = q, q+4, q+8, ... in registers.  The triangle is staged in
+// shared memory, packed by rows, padded to the template order NB with an
+// identity block, so every loop has a compile-time trip count.
+//
+//   FWD  (forward substitution)  x_j /= d_j, then x_k -= x_j M(k,j), k > j
+//        serves B L^{-T} (rows) and L^{-1} B (columns), M = L.
+//   BWD  (backward substitution) x_j /= d_j, then x_k -= x_j M(j,k), k < j,
+//        for j descending; serves L^{-T} B (M(j,k) = l_jk) and U^{-1} B
+//        (M(j,k) = u_kj, the triangle staged transposed).
+//   MUL  (in-place product)      b = old x_k; x_k = b d_k; x_j += b M(k,j),
+//        j < k, for k ascending; serves B L (rows) and L^T B (columns).
+// The right-looking form gives up to NB/4 independent FMAs per lane per step
+// and four warps per 32 vectors, enough to keep the FP64 pipes busy.
 // ----------------------------------------------------------------------------
-constexpr int TRI_PACK = TRX_NB * (TRX_NB + 1) / 2;
-constexpr int BASE_COLS = 32;   // columns (or rows) of B per CTA in base kernels
+constexpr int TRI_THREADS = 128;       // 32 vectors x 4 lanes
+constexpr int TRI_VECS = TRI_THREADS / 4;
+enum TriOp { TRI_FWD = 0, TRI_BWD = 1, TRI_MUL = 2 };
 
 __device__ __forceinline__ int tri_ix(int i, int k) { return i * (i + 1) / 2 + k; }
 
-__device__ __forceinline__ void load_tri(double *Lp, const double *L, i64 ldl, int nt)
+// Stage the order-n triangle of T (lower if !TRANS_UPPER, else the upper
+// triangle stored transposed) into P, padded with identity up to NB.
+template <int NB, bool TRANS_UPPER>
+__device__ __forceinline__ void stage_tri(double *P, const double *T, i64 ldt, int n, bool unit)
 {
-    for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
-        int i = e % nt, k = e / nt;
-        if (i >= k) Lp[tri_ix(i, k)] = L[(i64)k * ldl + i];
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int i = e % NB, k = e / NB;
+        if (i < k) continue;
+        double v;
+        if (i < n && k < n) v = TRANS_UPPER ? T[(i64)i * ldt + k] : T[(i64)k * ldt + i];
+        else v = (i == k) ? 1.0 : 0.0;
+        if (unit && i == k) v = 1.0;
+        P[tri_ix(i, k)] = v;
     }
 }
 
-// B(m x n) := alpha * L^{-1} B, m <= 64; one thread per column of B.
-template <bool UNIT>
-__global__ void __launch_bounds__(BASE_COLS)
-k_trsm_lln_base(int m, i64 n, double alpha, const double *__restrict__ L, i64 ldl,
-                double *B, i64 ldb, const int32_t *abort)
-{
-    if (abort && *abort != 0) return;
-    __shared__ double Lp[TRI_PACK];
-    __shared__ double Bs[TRX_NB][BASE_COLS + 1];
-    const i64 c0 = (i64)blockIdx.x * BASE_COLS;
-    const int nc = (int)min((i64)BASE_COLS, n - c0);
-    load_tri(Lp, L, ldl, m);
-    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
-        int i = e % m, j = e / m;
-        Bs[i][j] = B[(c0 + j) * ldb + i];
-    }
-    __syncthreads();
-    const int j = threadIdx.x;
-    if (j < nc) {
-        for (int i = 0; i < m; ++i) {
-            double s = alpha * Bs[i][j];
-            const double *li = Lp + tri_ix(i, 0);
-            for (int k = 0; k < i; ++k) s = fma(-li[k], Bs[k][j], s);
-            Bs[i][j] = UNIT ? s : s / li[i];
-        }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
-        int i = e % m, jj = e / m;
-        B[(c0 + jj) * ldb + i] = Bs[i][jj];
-    }
-}
-
-// B(m x n) := B L^{-T}, n <= 64; one thread per row of B:
-// x_j = (b_j - sum_{k<j} x_k l_jk) / l_jj.
-__global__ void __launch_bounds__(BASE_COLS)
-k_trsm_rlt_base(i64 m, int n, const double *__restrict__ L, i64 ldl, double *B, i64 ldb,
-                const int32_t *abort)
+template <int NB, int OP, bool ROWS, bool UNIT, bool TRANS_UPPER>
+__global__ void __launch_bounds__(TRI_THREADS)
+k_tri(i64 nvec, int n, double alpha, const double *__restrict__ T, i64 ldt, double *B, i64 ldb,
+      const int32_t *abort)
 {
     if (abort && *abort != 0) return;
-    __shared__ double Lp[TRI_PACK];
-    __shared__ double Bs[TRX_NB][BASE_COLS + 1];   // Bs[col][row]
-    const i64 r0 = (i64)blockIdx.x * BASE_COLS;
-    const int nr = (int)min((i64)BASE_COLS, m - r0);
-    load_tri(Lp, L, ldl, n);
-    for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
-        int r = e % nr, j = e / nr;
-        Bs[j][r] = B[(i64)j * ldb + r0 + r];
-    }
+    __shared__ double P[NB * (NB + 1) / 2];
+    stage_tri<NB, TRANS_UPPER>(P, T, ldt, n, UNIT);
     __syncthreads();
-    const int r = threadIdx.x;
-    if (r < nr) {
-        for (int j = 0; j < n; ++j) {
-            double s = Bs[j][r];
-            const double *lj = Lp + tri_ix(j, 0);
-            for (int k = 0; k < j; ++k) s = fma(-Bs[k][r], lj[k], s);
-            Bs[j][r] = s / lj[j];
+    constexpr int E = NB / 4;
+    const int q = threadIdx.x & 3;
+    const int gbase = threadIdx.x & 28;              // first lane of this group
+    const i64 v = (i64)blockIdx.x * TRI_VECS + (threadIdx.x >> 2);
+    const bool live = v < nvec;
+    double x[E];
+#pragma unroll
+    for (int t = 0; t < E; ++t) {
+        const int e = 4 * t + q;
+        double b = 0.0;
+        if (live && e < n) b = ROWS ? B[(i64)e * ldb + v] : B[v * ldb + e];
+        x[t] = alpha * b;
+    }
+    if (OP == TRI_FWD) {
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            const int s = j >> 2, own = j & 3;
+            if (!UNIT && q == own) x[s] = x[s] / P[tri_ix(j, j)];
+            const double xj = __shfl_sync(0xffffffffu, x[s], gbase | own);
+#pragma unroll
+            for (int t = 0; t < E; ++t) {
+                const int k = 4 * t + q;
+                if (k > j) x[t] = fma(-xj, P[tri_ix(k, j)], x[t]);
+            }
+        }
+    } else if (OP == TRI_BWD) {
+#pragma unroll
+        for (int j = NB - 1; j >= 0; --j) {
+            const int s = j >> 2, own = j & 3;
+            if (!UNIT && q == own) x[s] = x[s] / P[tri_ix(j, j)];
+            const double xj = __shfl_sync(0xffffffffu, x[s], gbase | own);
+#pragma unroll
+            for (int t = 0; t < E; ++t) {
+                const int k = 4 * t + q;
+                if (k < j) x[t] = fma(-xj, P[tri_ix(j, k)], x[t]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            const int s = k >> 2, own = k & 3;
+            const double bk = __shfl_sync(0xffffffffu, x[s], gbase | own);
+            if (q == own) x[s] = UNIT ? bk : bk * P[tri_ix(k, k)];
+#pragma unroll
+            for (int t = 0; t < E; ++t) {
+                const int j = 4 * t + q;
+                if (j < k) x[t] = fma(bk, P[tri_ix(k, j)], x[t]);
+            }
         }
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
-        int rr = e % nr, j = e / nr;
-        B[(i64)j * ldb + r0 + rr] = Bs[j][rr];
+    if (live) {
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const int e = 4 * t + q;
+            if (e < n) {
+                if (ROWS) B[(i64)e * ldb + v] = x[t];
+                else B[v * ldb + e] = x[t];
+            }
+        }
     }
 }
 
-// B(m x n) := L^{-T} B, m <= 64; one thread per column (back substitution):
-// x_i = (b_i - sum_{k>i} l_ki x_k) / l_ii.
-__global__ void __launch_bounds__(BASE_COLS)
-k_trsm_llt_base(int m, i64 n, const double *__restrict__ L, i64 ldl, double *B, i64 ldb,
-                const int32_t *abort)
+template <int OP, bool ROWS, bool UNIT, bool TRANS_UPPER>
+static void launch_tri(Ctx &c, int kind, i64 nvec, int n, double alpha, const double *T, i64 ldt,
+                       double *B, i64 ldb)
 {
-    if (abort && *abort != 0) return;
-    __shared__ double Lp[TRI_PACK];
-    __shared__ double Bs[TRX_NB][BASE_COLS + 1];
-    const i64 c0 = (i64)blockIdx.x * BASE_COLS;
-    const int nc = (int)min((i64)BASE_COLS, n - c0);
-    load_tri(Lp, L, ldl, m);
-    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
-        int i = e % m, j = e / m;
-        Bs[i][j] = B[(c0 + j) * ldb + i];
-    }
-    __syncthreads();
-    const int j = threadIdx.x;
-    if (j < nc) {
-        for (int i = m - 1; i >= 0; --i) {
-            double s = Bs[i][j];
-            for (int k = i + 1; k < m; ++k) s = fma(-Lp[tri_ix(k, i)], Bs[k][j], s);
-            Bs[i][j] = s / Lp[tri_ix(i, i)];
-        }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
-        int i = e % m, jj = e / m;
-        B[(c0 + jj) * ldb + i] = Bs[i][jj];
-    }
+    if (nvec <= 0 || n <= 0) return;
+    const unsigned grid = (unsigned)((nvec + TRI_VECS - 1) / TRI_VECS);
+    Launch L(c, kind, (double)nvec * n * n, 0.0);
+    if (n <= 16)
+        k_tri<16, OP, ROWS, UNIT, TRANS_UPPER><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, T, ldt, B, ldb, c.abort);
+    else if (n <= 32)
+        k_tri<32, OP, ROWS, UNIT, TRANS_UPPER><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, T, ldt, B, ldb, c.abort);
+    else
+        k_tri<64, OP, ROWS, UNIT, TRANS_UPPER><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, T, ldt, B, ldb, c.abort);
 }
-
-// B(m x n) := U^{-1} B, U upper m x m (m <= 64); one thread per column:
-// x_i = (b_i - sum_{k>i} u_ik x_k) / u_ii.  U staged packed by columns of
-// its transpose: u_ik (k >= i) at Up[k(k+1)/2 + i].
-__global__ void __launch_bounds__(BASE_COLS)
-k_trsm_lun_base(int m, i64 n, const double *__restrict__ U, i64 ldu, double *B, i64 ldb,
-                const int32_t *abort)
-{
-    if (abort && *abort != 0) return;
-    __shared__ double Up[TRI_PACK];
-    __shared__ double Bs[TRX_NB][BASE_COLS + 1];
-    const i64 c0 = (i64)blockIdx.x * BASE_COLS;
-    const int nc = (int)min((i64)BASE_COLS, n - c0);
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        int i = e % m, k = e / m;
-        if (k >= i) Up[tri_ix(k, i)] = U[(i64)k * ldu + i];
-    }
-    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
-        int i = e % m, j = e / m;
-        Bs[i][j] = B[(c0 + j) * ldb + i];
-    }
-    __syncthreads();
-    const int j = threadIdx.x;
-    if (j < nc) {
-        for (int i = m - 1; i >= 0; --i) {
-            double s = Bs[i][j];
-            for (int k = i + 1; k < m; ++k) s = fma(-Up[tri_ix(k, i)], Bs[k][j], s);
-            Bs[i][j] = s / Up[tri_ix(i, i)];
-        }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
-        int i = e % m, jj = e / m;
-        B[(c0 + jj) * ldb + i] = Bs[i][jj];
-    }
-}
-
-// B(m x n) := B L, n <= 64; one thread per row, in place for ascending j:
-// b_j := sum_{k>=j} b_k l_kj (b_k, k >= j, still hold their old values).
-template <bool UNIT>
-__global__ void __launch_bounds__(BASE_COLS)
-k_trmm_rln_base(i64 m, int n, const double *__restrict__ L, i64 ldl, double *B, i64 ldb,
-                const int32_t *abort)
-{
-    if (abort && *abort != 0) return;
-    __shared__ double Lp[TRI_PACK];
-    __shared__ double Bs[TRX_NB][BASE_COLS + 1];
-    const i64 r0 = (i64)blockIdx.x * BASE_COLS;
-    const int nr = (int)min((i64)BASE_COLS, m - r0);
-    load_tri(Lp, L, ldl, n);
-    for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
-        int r = e % nr, j = e / nr;
-        Bs[j][r] = B[(i64)j * ldb + r0 + r];
-    }
-    __syncthreads();
-    const int r = threadIdx.x;
-    if (r < nr) {
-        for (int j = 0; j < n; ++j) {
-            double s = UNIT ? Bs[j][r] : Bs[j][r] * Lp[tri_ix(j, j)];
-            for (int k = j + 1; k < n; ++k) s = fma(Bs[k][r], Lp[tri_ix(k, j)], s);
-            Bs[j][r] = s;
-        }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
-        int rr = e % nr, j = e / nr;
-        B[(i64)j * ldb + r0 + rr] = Bs[j][rr];
-    }
-}
-
-// B(m x n) := L^T B, m <= 64; one thread per column, ascending i in place:
-// b_i := sum_{k>=i} l_ki b_k.
-__global__ void __launch_bounds__(BASE_COLS)
-k_trmm_llt_base(int m, i64 n, const double *__restrict__ L, i64 ldl, double *B, i64 ldb,
-                const int32_t *abort)
-{
-    if (abort && *abort != 0) return;
-    __shared__ double Lp[TRI_PACK];
-    __shared__ double Bs[TRX_NB][BASE_COLS + 1];
-    const i64 c0 = (i64)blockIdx.x * BASE_COLS;
-    const int nc = (int)min((i64)BASE_COLS, n - c0);
-    load_tri(Lp, L, ldl, m);
-    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
-        int i = e % m, j = e / m;
-        Bs[i][j] = B[(c0 + j) * ldb + i];
-    }
-    __syncthreads();
-    const int j = threadIdx.x;
-    if (j < nc) {
-        for (int i = 0; i < m; ++i) {
-            double s = Bs[i][j] * Lp[tri_ix(i, i)];
-            for (int k = i + 1; k < m; ++k) s = fma(Lp[tri_ix(k, i)], Bs[k][j], s);
-            Bs[i][j] = s;
-        }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
-        int i = e % m, jj = e / m;
-        B[(c0 + jj) * ldb + i] = Bs[i][jj];
-    }
-}
-
-static inline unsigned blocks_for(i64 count) { return (unsigned)((count + BASE_COLS - 1) / BASE_COLS); }
 
 // ----------------------------------------------------------------------------
 // Recursive drivers (halving with 64-aligned splits).
@@ -393,9 +300,8 @@ void trsm_lln(Ctx &c, bool unit, i64 m, i64 n, double alpha, const double *L, i6
 {
     if (m <= 0 || n <= 0) return;
     if (m <= TRX_NB) {
-        Launch K(c, K_TRSM, (double)n * m * m, 0.0);
-        if (unit) k_trsm_lln_base<true><<<blocks_for(n), BASE_COLS, 0, c.s>>>((int)m, n, alpha, L, ldl, B, ldb, c.abort);
-        else k_trsm_lln_base<false><<<blocks_for(n), BASE_COLS, 0, c.s>>>((int)m, n, alpha, L, ldl, B, ldb, c.abort);
+        if (unit) launch_tri<TRI_FWD, false, true, false>(c, K_TRSM, n, (int)m, alpha, L, ldl, B, ldb);
+        else launch_tri<TRI_FWD, false, false, false>(c, K_TRSM, n, (int)m, alpha, L, ldl, B, ldb);
         return;
     }
     const i64 m1 = split_q(m, TRX_NB), m2 = m - m1;
@@ -404,75 +310,71 @@ void trsm_lln(Ctx &c, bool unit, i64 m, i64 n, double alpha, const double *L, i6
     trsm_lln(c, unit, m2, n, 1.0, L + m1 + m1 * ldl, ldl, B + m1, ldb);
 }
 
-void trsm_rlt(Ctx &c, i64 m, i64 n, const double *L, i64 ldl, double *B, i64 ldb)
+void trsm_rlt(Ctx &c, i64 m, i64 n, double alpha, const double *L, i64 ldl, double *B, i64 ldb)
 {
     if (m <= 0 || n <= 0) return;
     if (n <= TRX_NB) {
-        Launch K(c, K_TRSM, (double)m * n * n, 0.0);
-        k_trsm_rlt_base<<<blocks_for(m), BASE_COLS, 0, c.s>>>(m, (int)n, L, ldl, B, ldb, c.abort);
+        launch_tri<TRI_FWD, true, false, false>(c, K_TRSM, m, (int)n, alpha, L, ldl, B, ldb);
         return;
     }
     const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
-    trsm_rlt(c, m, n1, L, ldl, B, ldb);
-    gemm(c, false, true, m, n2, n1, -1.0, B, ldb, L + n1, ldl, 1.0, B + n1 * ldb, ldb);
-    trsm_rlt(c, m, n2, L + n1 + n1 * ldl, ldl, B + n1 * ldb, ldb);
+    trsm_rlt(c, m, n1, alpha, L, ldl, B, ldb);
+    gemm(c, false, true, m, n2, n1, -1.0, B, ldb, L + n1, ldl, alpha, B + n1 * ldb, ldb);
+    trsm_rlt(c, m, n2, 1.0, L + n1 + n1 * ldl, ldl, B + n1 * ldb, ldb);
 }
 
-void trsm_llt(Ctx &c, i64 m, i64 n, const double *L, i64 ldl, double *B, i64 ldb)
+void trsm_llt(Ctx &c, i64 m, i64 n, double alpha, const double *L, i64 ldl, double *B, i64 ldb)
 {
     if (m <= 0 || n <= 0) return;
     if (m <= TRX_NB) {
-        Launch K(c, K_TRSM, (double)n * m * m, 0.0);
-        k_trsm_llt_base<<<blocks_for(n), BASE_COLS, 0, c.s>>>((int)m, n, L, ldl, B, ldb, c.abort);
+        launch_tri<TRI_BWD, false, false, false>(c, K_TRSM, n, (int)m, alpha, L, ldl, B, ldb);
         return;
     }
     const i64 m1 = split_q(m, TRX_NB), m2 = m - m1;
-    trsm_llt(c, m2, n, L + m1 + m1 * ldl, ldl, B + m1, ldb);
-    gemm(c, true, false, m1, n, m2, -1.0, L + m1, ldl, B + m1, ldb, 1.0, B, ldb);
-    trsm_llt(c, m1, n, L, ldl, B, ldb);
+    trsm_llt(c, m2, n, alpha, L + m1 + m1 * ldl, ldl, B + m1, ldb);
+    gemm(c, true, false, m1, n, m2, -1.0, L + m1, ldl, B + m1, ldb, alpha, B, ldb);
+    trsm_llt(c, m1, n, 1.0, L, ldl, B, ldb);
 }
 
-void trsm_lun(Ctx &c, i64 m, i64 n, const double *U, i64 ldu, double *B, i64 ldb)
+void trsm_lun(Ctx &c, i64 m, i64 n, double alpha, const double *U, i64 ldu, double *B, i64 ldb)
 {
     if (m <= 0 || n <= 0) return;
     if (m <= TRX_NB) {
-        Launch K(c, K_TRSM, (double)n * m * m, 0.0);
-        k_trsm_lun_base<<<blocks_for(n), BASE_COLS, 0, c.s>>>((int)m, n, U, ldu, B, ldb, c.abort);
+        launch_tri<TRI_BWD, false, false, true>(c, K_TRSM, n, (int)m, alpha, U, ldu, B, ldb);
         return;
     }
     const i64 m1 = split_q(m, TRX_NB), m2 = m - m1;
-    trsm_lun(c, m2, n, U + m1 + m1 * ldu, ldu, B + m1, ldb);
-    gemm(c, false, false, m1, n, m2, -1.0, U + m1 * ldu, ldu, B + m1, ldb, 1.0, B, ldb);
-    trsm_lun(c, m1, n, U, ldu, B, ldb);
+    trsm_lun(c, m2, n, alpha, U + m1 + m1 * ldu, ldu, B + m1, ldb);
+    gemm(c, false, false, m1, n, m2, -1.0, U + m1 * ldu, ldu, B + m1, ldb, alpha, B, ldb);
+    trsm_lun(c, m1, n, 1.0, U, ldu, B, ldb);
 }
 
-void trmm_rln(Ctx &c, bool unit, i64 m, i64 n, const double *L, i64 ldl, double *B, i64 ldb)
+void trmm_rln(Ctx &c, bool unit, i64 m, i64 n, double alpha, const double *L, i64 ldl, double *B,
+              i64 ldb)
 {
     if (m <= 0 || n <= 0) return;
     if (n <= TRX_NB) {
-        Launch K(c, K_TRMM, (double)m * n * n, 0.0);
-        if (unit) k_trmm_rln_base<true><<<blocks_for(m), BASE_COLS, 0, c.s>>>(m, (int)n, L, ldl, B, ldb, c.abort);
-        else k_trmm_rln_base<false><<<blocks_for(m), BASE_COLS, 0, c.s>>>(m, (int)n, L, ldl, B, ldb, c.abort);
+        if (unit) launch_tri<TRI_MUL, true, true, false>(c, K_TRMM, m, (int)n, alpha, L, ldl, B, ldb);
+        else launch_tri<TRI_MUL, true, false, false>(c, K_TRMM, m, (int)n, alpha, L, ldl, B, ldb);
         return;
     }
     const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
-    trmm_rln(c, unit, m, n1, L, ldl, B, ldb);
-    gemm(c, false, false, m, n1, n2, 1.0, B + n1 * ldb, ldb, L + n1, ldl, 1.0, B, ldb);
-    trmm_rln(c, unit, m, n2, L + n1 + n1 * ldl, ldl, B + n1 * ldb, ldb);
+    trmm_rln(c, unit, m, n1, alpha, L, ldl, B, ldb);
+    gemm(c, false, false, m, n1, n2, alpha, B + n1 * ldb, ldb, L + n1, ldl, 1.0, B, ldb);
+    trmm_rln(c, unit, m, n2, alpha, L + n1 + n1 * ldl, ldl, B + n1 * ldb, ldb);
 }
 
-void trmm_llt(Ctx &c, i64 m, i64 n, const double *L, i64 ldl, double *B, i64 ldb)
+void trmm_llt(Ctx &c, i64 m, i64 n, double alpha, const double *L, i64 ldl, double *B, i64 ldb)
 {
     if (m <= 0 || n <= 0) return;
     if (m <= TRX_NB) {
-        Launch K(c, K_TRMM, (double)n * m * m, 0.0);
-        k_trmm_llt_base<<<blocks_for(n), BASE_COLS, 0, c.s>>>((int)m, n, L, ldl, B, ldb, c.abort);
+        launch_tri<TRI_MUL, false, false, false>(c, K_TRMM, n, (int)m, alpha, L, ldl, B, ldb);
         return;
     }
     const i64 m1 = split_q(m, TRX_NB), m2 = m - m1;
-    trmm_llt(c, m1, n, L, ldl, B, ldb);
-    gemm(c, true, false, m1, n, m2, 1.0, L + m1, ldl, B + m1, ldb, 1.0, B, ldb);
-    trmm_llt(c, m2, n, L + m1 + m1 * ldl, ldl, B + m1, ldb);
+    trmm_llt(c, m1, n, alpha, L, ldl, B, ldb);
+    gemm(c, true, false, m1, n, m2, alpha, L + m1, ldl, B + m1, ldb, 1.0, B, ldb);
+    trmm_llt(c, m2, n, alpha, L + m1 + m1 * ldl, ldl, B + m1, ldb);
 }
 
 }  // namespace rl

@@ -37,35 +37,29 @@ k_potf2(int n, double *A, i64 lda, int32_t *info, i64 info_off, const int32_t *a
 {
     if (abort && *abort != 0) return;
     __shared__ double S[BASE_N][BASE_N + 1];
-    __shared__ int fail;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        int i = e % n, j = e / n;
-        if (i >= j) S[i][j] = A[(i64)j * lda + i];
-    }
-    if (threadIdx.x == 0) fail = 0;
+    __shared__ double col[BASE_N];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads
+    for (int j = ty; j < n; j += 16)
+        for (int i = j + tx; i < n; i += 16) S[i][j] = A[(i64)j * lda + i];
     __syncthreads();
+    int fail = 0;
     for (int j = 0; j < n; ++j) {
-        if (threadIdx.x == 0) {
-            double d = S[j][j];
-            if (!(d > 0.0)) fail = j + 1;
-            else S[j][j] = sqrt(d);
-        }
+        // every thread evaluates the pivot of column j identically
+        const double d = S[j][j];
+        if (!(d > 0.0)) { fail = j + 1; break; }
+        const double ljj = sqrt(d);
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) col[i] = S[i][j] / ljj;
         __syncthreads();
-        if (fail) break;
-        const double ljj = S[j][j];
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) S[i][j] = S[i][j] / ljj;
-        __syncthreads();
-        const int t = n - j - 1;
-        for (int e = threadIdx.x; e < t * t; e += blockDim.x) {
-            int ii = j + 1 + e % t, kk = j + 1 + e / t;
-            if (ii >= kk) S[ii][kk] = fma(-S[ii][j], S[kk][j], S[ii][kk]);
+        if (threadIdx.x == 0) S[j][j] = ljj;
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) S[i][j] = col[i];
+        for (int ii = j + 1 + ty; ii < n; ii += 16) {
+            const double lij = col[ii];
+            for (int kk = j + 1 + tx; kk <= ii; kk += 16) S[ii][kk] = fma(-lij, col[kk], S[ii][kk]);
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        int i = e % n, j = e / n;
-        if (i >= j) A[(i64)j * lda + i] = S[i][j];
-    }
+    for (int j = ty; j < n; j += 16)
+        for (int i = j + tx; i < n; i += 16) A[(i64)j * lda + i] = S[i][j];
     if (fail && threadIdx.x == 0) *info = (int32_t)(info_off + fail);
 }
 

@@ -87,16 +87,17 @@ void gemm(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, double alpha,
 // B(m x n) := alpha * L^{-1} B, L lower m x m (unit or not).
 void trsm_lln(Ctx &c, bool unit, i64 m, i64 n, double alpha, const double *L,
               i64 ldl, double *B, i64 ldb);
-// B(m x n) := B L^{-T}, L lower n x n, non-unit.
-void trsm_rlt(Ctx &c, i64 m, i64 n, const double *L, i64 ldl, double *B, i64 ldb);
-// B(m x n) := L^{-T} B, L lower m x m, non-unit.
-void trsm_llt(Ctx &c, i64 m, i64 n, const double *L, i64 ldl, double *B, i64 ldb);
-// B(m x n) := U^{-1} B, U upper m x m, non-unit.
-void trsm_lun(Ctx &c, i64 m, i64 n, const double *U, i64 ldu, double *B, i64 ldb);
-// B(m x n) := B L, L lower n x n (unit or not).
-void trmm_rln(Ctx &c, bool unit, i64 m, i64 n, const double *L, i64 ldl, double *B, i64 ldb);
-// B(m x n) := L^T B, L lower m x m, non-unit.
-void trmm_llt(Ctx &c, i64 m, i64 n, const double *L, i64 ldl, double *B, i64 ldb);
+// B(m x n) := alpha * B L^{-T}, L lower n x n, non-unit.
+void trsm_rlt(Ctx &c, i64 m, i64 n, double alpha, const double *L, i64 ldl, double *B, i64 ldb);
+// B(m x n) := alpha * L^{-T} B, L lower m x m, non-unit.
+void trsm_llt(Ctx &c, i64 m, i64 n, double alpha, const double *L, i64 ldl, double *B, i64 ldb);
+// B(m x n) := alpha * U^{-1} B, U upper m x m, non-unit.
+void trsm_lun(Ctx &c, i64 m, i64 n, double alpha, const double *U, i64 ldu, double *B, i64 ldb);
+// B(m x n) := alpha * B L, L lower n x n (unit or not).
+void trmm_rln(Ctx &c, bool unit, i64 m, i64 n, double alpha, const double *L, i64 ldl, double *B,
+              i64 ldb);
+// B(m x n) := alpha * L^T B, L lower m x m, non-unit.
+void trmm_llt(Ctx &c, i64 m, i64 n, double alpha, const double *L, i64 ldl, double *B, i64 ldb);
 
 // ---- base cases and row interchanges (factor.cu) ---------------------------
 void potf2(Ctx &c, i64 n, double *A, i64 lda, i64 info_off);

@@ -1,0 +1,127 @@
+"""Per-kernel timing of the library's building blocks through the C ABI.
+
+Used to profile one kernel at a time (an ncu capture of a single launch on a
+case that still exceeds L2) and to sweep tuning parameters.  Inputs are
+random device tensors; results are not checked here (the tests do that).
+
+    python -m paper_1602_06763_gb300.kbench --case dgemm --n 4096 --reps 3
+    python -m paper_1602_06763_gb300.kbench --case getrf --n 8192 --nb 32
+
+Prints one JSON line per case: median milliseconds, GFLOP/s (LAWN 41 flop
+counts for the factorizations, 2mnk for GEMM) and the per-kernel trace.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import statistics
+
+
+def main():
+    import torch
+    from . import relgpu as r
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", required=True,
+                    choices=["dgemm", "dsyrk", "dtrsm", "potrf", "getrf", "trtri", "lauum", "panel"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--m", type=int, default=0, help="rows (panel case); default n")
+    ap.add_argument("--k", type=int, default=0, help="inner dimension (dgemm/dsyrk); default n")
+    ap.add_argument("--nb", type=int, default=0, help="dgetrf panel width")
+    ap.add_argument("--c", type=int, default=0, help="dpotrf / dtrtri crossover")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--trace", action="store_true")
+    a = ap.parse_args()
+
+    if a.nb:
+        r.check(r.rl_set_param(r.RL_PARAM_GETRF_PANEL, a.nb))
+    if a.c:
+        r.check(r.rl_set_param(r.RL_PARAM_POTRF_CROSSOVER, a.c))
+        r.check(r.rl_set_param(r.RL_PARAM_TRTRI_CROSSOVER, a.c))
+    n = a.n
+    k = a.k or n
+    m = a.m or n
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev)
+    g.manual_seed(1234)
+    s = torch.cuda.current_stream().cuda_stream
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    if a.case in ("dgemm", "dsyrk"):
+        A = torch.rand(k, n, generator=g, device=dev, dtype=torch.float64)
+        B = torch.rand(n, k, generator=g, device=dev, dtype=torch.float64)
+        C = torch.rand(n, n, generator=g, device=dev, dtype=torch.float64)
+        if a.case == "dgemm":
+            flops = 2.0 * n * n * k
+            run = lambda: r.check(r.rl_dgemm("N", "N", n, n, k, -1.0, A, n, B, k, 1.0, C, n, s))
+        else:
+            flops = 1.0 * k * n * (n + 1)
+            run = lambda: r.check(r.rl_dsyrk("L", "N", n, k, -1.0, A, n, 1.0, C, n, s))
+        restore = lambda: None
+    elif a.case == "dtrsm":
+        L = torch.rand(n, n, generator=g, device=dev, dtype=torch.float64)
+        L.diagonal().add_(float(n))
+        B0 = torch.rand(n, n, generator=g, device=dev, dtype=torch.float64)
+        B = B0.clone()
+        flops = 1.0 * n * n * n
+        restore = lambda: B.copy_(B0)
+        run = lambda: r.check(r.rl_dtrsm("R", "L", "T", "N", n, n, 1.0, L, n, B, n, s))
+    else:
+        if a.case in ("potrf", "trtri", "lauum"):
+            X = torch.rand(n, n, generator=g, device=dev, dtype=torch.float64) - 0.5
+            A0 = X @ X.T
+            A0.diagonal().add_(float(n))
+            if a.case != "potrf":
+                r.check(r.rl_dpotrf("L", n, A0, n, info, None, 0, s))
+        else:
+            rows = m
+            A0 = torch.rand(n if a.case == "getrf" else n, rows, generator=g, device=dev,
+                            dtype=torch.float64) * 2 - 1
+        A = A0.clone()
+        restore = lambda: A.copy_(A0)
+        if a.case == "potrf":
+            flops = n ** 3 / 3.0
+            run = lambda: r.check(r.rl_dpotrf("L", n, A, n, info, None, 0, s))
+        elif a.case == "trtri":
+            flops = n ** 3 / 3.0
+            run = lambda: r.check(r.rl_dtrtri("L", "N", n, A, n, info, None, 0, s))
+        elif a.case == "lauum":
+            flops = n ** 3 / 3.0
+            run = lambda: r.check(r.rl_dlauum("L", n, A, n, info, None, 0, s))
+        else:
+            cols = n if a.case == "getrf" else (a.nb or r.rl_get_param(r.RL_PARAM_GETRF_PANEL))
+            rows = m
+            ipiv = torch.zeros(min(rows, cols), dtype=torch.int32, device=dev)
+            lw = r.rl_dgetrf_work_size(rows, cols)
+            work = torch.empty(lw, dtype=torch.uint8, device=dev)
+            mn = min(rows, cols)
+            flops = rows * cols * mn - (rows + cols) * mn * mn / 2.0 + mn ** 3 / 3.0
+            run = lambda: r.check(r.rl_dgetrf(rows, cols, A, rows, ipiv, info, work, lw, s))
+
+    for _ in range(a.warmup):
+        restore()
+        run()
+    torch.cuda.synchronize()
+    times = []
+    if a.trace:
+        r.rl_trace_enable(1)
+    for _ in range(a.reps):
+        restore()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    out = {"case": a.case, "n": n, "m": m, "k": k, "ms": statistics.median(times),
+           "gflops": flops / (statistics.median(times) * 1e-3) / 1e9, "info": int(info.item())}
+    if a.trace:
+        out["trace"] = r.trace_summary()
+        r.rl_trace_enable(0)
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

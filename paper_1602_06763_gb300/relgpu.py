@@ -41,6 +41,14 @@ _SIGS = {
     "rl_get_param": (_i64, [ctypes.c_int]),
     "rl_launch_count": (ctypes.c_uint64, []),
     "rl_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "rl_dgemm": (ctypes.c_int, [_ch, _ch, _i64, _i64, _i64, ctypes.c_double, _vp, _i64, _vp, _i64,
+                                ctypes.c_double, _vp, _i64, _vp]),
+    "rl_dsyrk": (ctypes.c_int, [_ch, _ch, _i64, _i64, ctypes.c_double, _vp, _i64, ctypes.c_double,
+                                _vp, _i64, _vp]),
+    "rl_dtrsm": (ctypes.c_int, [_ch, _ch, _ch, _ch, _i64, _i64, ctypes.c_double, _vp, _i64, _vp,
+                                _i64, _vp]),
+    "rl_dtrmm": (ctypes.c_int, [_ch, _ch, _ch, _ch, _i64, _i64, ctypes.c_double, _vp, _i64, _vp,
+                                _i64, _vp]),
     "rl_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "rl_trace_kinds": (ctypes.c_int, []),
     "rl_trace_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
@@ -113,6 +121,26 @@ def rl_dlauum(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
 
 def rl_dpotri(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
     return _lib.rl_dpotri(_c(uplo), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_dgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):
+    return _lib.rl_dgemm(_c(transa), _c(transb), m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb, beta,
+                         _ptr(C), ldc, _stream(stream))
+
+
+def rl_dsyrk(uplo, trans, n, k, alpha, A, lda, beta, C, ldc, stream=None):
+    return _lib.rl_dsyrk(_c(uplo), _c(trans), n, k, alpha, _ptr(A), lda, beta, _ptr(C), ldc,
+                         _stream(stream))
+
+
+def rl_dtrsm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream=None):
+    return _lib.rl_dtrsm(_c(side), _c(uplo), _c(transa), _c(diag), m, n, alpha, _ptr(A), lda,
+                         _ptr(B), ldb, _stream(stream))
+
+
+def rl_dtrmm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream=None):
+    return _lib.rl_dtrmm(_c(side), _c(uplo), _c(transa), _c(diag), m, n, alpha, _ptr(A), lda,
+                         _ptr(B), ldb, _stream(stream))
 
 
 def rl_host_work_size(routine, m, n, lda):

@@ -1,0 +1,146 @@
+"""The BLAS-3 layer (rl_dgemm / rl_dsyrk / rl_dtrsm / rl_dtrmm) against the
+oracle's plain definitions, on ragged shapes that cross the 64-wide tiles and
+the 64-order triangle blocks.
+
+Tolerances follow the standard elementwise error bounds of the operations:
+  GEMM/SYRK/TRMM: |C_gpu - C_ref| <= 2 k eps (|alpha| |op(A)| |op(B)| + |beta| |C|)
+  TRSM:           |op(T) X - alpha B| <= 4 n eps |op(T)| |X|  (backward error)
+where k (or n) is the inner dimension and eps = 2^-53.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1602_06763_gb300 import inputs
+
+from . import gpu_util as G
+
+pytestmark = pytest.mark.gpu
+EPS = 2.0 ** -53
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    yield
+
+
+def op(X, t):
+    return X.T if t == "T" else X
+
+
+@pytest.mark.parametrize("ta", ["N", "T"])
+@pytest.mark.parametrize("tb", ["N", "T"])
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (17, 65, 130), (64, 64, 64), (130, 33, 300), (300, 200, 7), (5, 129, 0)])
+def test_dgemm(ta, tb, m, n, k):
+    r = G.lib()
+    A = inputs.uniform(k if ta == "T" else m, m if ta == "T" else k, seed=m + 7 * n + 13 * k)
+    B = inputs.uniform(n if tb == "T" else k, k if tb == "T" else n, seed=m + 3 * n + 11 * k + 1)
+    C = inputs.uniform(m, n, seed=2 * m + n + k + 2)
+    alpha, beta = -0.75, 1.25
+    dA, dB, dC = G.DevMat(A, lda=A.shape[0] + 3), G.DevMat(B), G.DevMat(C, lda=m + 1)
+    assert r.rl_dgemm(ta, tb, m, n, k, alpha, dA.ptr(), dA.lda, dB.ptr(), dB.lda, beta, dC.ptr(), dC.lda) == 0
+    G.sync()
+    assert dA.canaries_intact() and dC.canaries_intact()
+    got = dC.get()
+    ref = oracle.gemm(A, B, beta * C, alpha=alpha, ta=(ta == "T"), tb=(tb == "T"))
+    bound = 2 * max(k, 1) * EPS * (abs(alpha) * np.abs(op(A, ta)) @ np.abs(op(B, tb)) + abs(beta) * np.abs(C)) + 1e-300
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+@pytest.mark.parametrize("trans", ["N", "T"])
+@pytest.mark.parametrize("n,k", [(1, 5), (65, 64), (200, 130), (64, 1)])
+def test_dsyrk_lower(trans, n, k):
+    r = G.lib()
+    A = inputs.uniform(k if trans == "T" else n, n if trans == "T" else k, seed=5 * n + k)
+    C = inputs.uniform(n, n, seed=n + 3 * k)
+    dA, dC = G.DevMat(A), G.DevMat(C, lda=n + 2)
+    assert r.rl_dsyrk("L", trans, n, k, -1.0, dA.ptr(), dA.lda, 1.0, dC.ptr(), dC.lda) == 0
+    G.sync()
+    assert dC.canaries_intact()
+    got = dC.get()
+    ref = oracle.syrk_lower(A, C, alpha=-1.0, trans=(trans == "T"))
+    oa = op(A, "T" if trans == "T" else "N")
+    bound = 2 * k * EPS * (np.abs(oa) @ np.abs(oa).T + np.abs(C)) + 1e-300
+    assert np.all(np.tril(np.abs(got - ref) <= bound))
+    assert np.array_equal(np.triu(got, 1), np.triu(C, 1))      # upper triangle untouched
+
+
+def _tri(n, seed, lower=True, unit=False):
+    T = inputs.uniform(n, n, seed=seed)
+    T = np.tril(T) if lower else np.triu(T)
+    T[np.diag_indices(n)] = 2.0 + np.abs(T[np.diag_indices(n)])
+    if unit:
+        T[np.diag_indices(n)] = 1.0
+    return np.asfortranarray(T)
+
+
+@pytest.mark.parametrize("case", ["LLNN", "LLNU", "LLTN", "RLTN", "LUNN"])
+@pytest.mark.parametrize("m,n", [(1, 1), (16, 33), (64, 64), (65, 130), (200, 17), (33, 200)])
+def test_dtrsm(case, m, n):
+    r = G.lib()
+    side, uplo, tr, diag = case
+    nt = m if side == "L" else n
+    T = _tri(nt, seed=m * 31 + n, lower=(uplo == "L"), unit=(diag == "U"))
+    B = inputs.uniform(m, n, seed=m + n * 17)
+    alpha = -1.5
+    dT, dB = G.DevMat(T, lda=nt + 1), G.DevMat(B, lda=m + 2)
+    assert r.rl_dtrsm(side, uplo, tr, diag, m, n, alpha, dT.ptr(), dT.lda, dB.ptr(), dB.lda) == 0
+    G.sync()
+    assert dB.canaries_intact() and dT.canaries_intact()
+    X = dB.get()
+    oT = op(T, tr)
+    lhs = oT @ X if side == "L" else X @ oT
+    bound = 4 * nt * EPS * (np.abs(oT) @ np.abs(X) if side == "L" else np.abs(X) @ np.abs(oT)) + 1e-300
+    assert np.all(np.abs(lhs - alpha * B) <= bound)
+    # against the oracle's substitution as well
+    if case == "LLNN":
+        ref = oracle.trsm_lln(T, B, alpha=alpha)
+    elif case == "LLNU":
+        ref = oracle.trsm_lln(T, B, alpha=alpha, unit=True)
+    elif case == "LLTN":
+        ref = alpha * oracle.trsm_llt(T, B)
+    elif case == "RLTN":
+        ref = alpha * oracle.trsm_rlt(T, B)
+    else:
+        ref = alpha * oracle.trsm_lun(T, B)
+    kappa = np.linalg.cond(T)
+    assert np.max(np.abs(X - ref)) <= 8 * nt * EPS * kappa * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("case", ["RLNN", "RLNU", "LLTN"])
+@pytest.mark.parametrize("m,n", [(1, 1), (16, 33), (64, 64), (65, 130), (200, 17), (33, 200)])
+def test_dtrmm(case, m, n):
+    r = G.lib()
+    side, uplo, tr, diag = case
+    nt = m if side == "L" else n
+    T = _tri(nt, seed=m * 7 + n, unit=(diag == "U"))
+    B = inputs.uniform(m, n, seed=m + n * 5)
+    alpha = 0.5
+    dT, dB = G.DevMat(T), G.DevMat(B, lda=m + 1)
+    assert r.rl_dtrmm(side, uplo, tr, diag, m, n, alpha, dT.ptr(), dT.lda, dB.ptr(), dB.lda) == 0
+    G.sync()
+    assert dB.canaries_intact()
+    got = dB.get()
+    if case == "LLTN":
+        ref = alpha * oracle.trmm_llt(T, B)
+        mag = np.abs(T.T) @ np.abs(B)
+    else:
+        ref = alpha * oracle.trmm_rln(T, B)
+        mag = np.abs(B) @ np.abs(T)
+    assert np.all(np.abs(got - ref) <= 2 * nt * EPS * abs(alpha) * mag + 1e-300)
+
+
+def test_blas3_unsupported_options():
+    r = G.lib()
+    t = G.torch()
+    buf = t.zeros(64, dtype=t.float64, device="cuda")
+    p = buf.data_ptr()
+    assert r.rl_dsyrk("U", "N", 4, 4, 1.0, p, 4, 1.0, p, 4) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_dtrsm("R", "L", "N", "N", 4, 4, 1.0, p, 4, p, 4) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_dtrmm("L", "L", "N", "N", 4, 4, 1.0, p, 4, p, 4) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_dgemm("X", "N", 4, 4, 4, 1.0, p, 4, p, 4, 1.0, p, 4) == -1
+    assert r.rl_dgemm("N", "N", 4, 4, 4, 1.0, p, 3, p, 4, 1.0, p, 4) == -8
+    assert r.rl_dtrsm("L", "L", "N", "N", 4, 4, 1.0, p, 3, p, 4) == -9

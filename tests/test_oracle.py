@@ -372,6 +372,34 @@ def test_residual_bounds_all_crossovers(oracle, n):
     assert oracle.probe_lu(G, F, ipiv, x) <= BOUND
 
 
+def test_blas3_definitions_vs_library(oracle):
+    import scipy.linalg as sl
+    A = inputs.uniform(37, 23, seed=1)
+    B = inputs.uniform(23, 41, seed=2)
+    C = inputs.uniform(37, 41, seed=3)
+    got = oracle.gemm(A, B, C, alpha=-2.0)
+    assert np.max(np.abs(got - (C - 2.0 * A @ B))) <= 64 * EPS * 23
+    got = oracle.gemm(A.T.copy(), B.T.copy(), C, alpha=1.0, ta=True, tb=True)
+    assert np.max(np.abs(got - (C + A @ B))) <= 64 * EPS * 23
+    S = inputs.uniform(30, 30, seed=4)
+    got = oracle.syrk_lower(A[:30], S, alpha=-1.0)
+    assert np.max(np.abs(np.tril(got - (S - A[:30] @ A[:30].T)))) <= 64 * EPS * 23
+    assert np.array_equal(np.triu(got, 1), np.triu(S, 1))
+    L = np.tril(inputs.uniform(23, 23, seed=5)) + 3 * np.eye(23)
+    U = np.triu(inputs.uniform(23, 23, seed=6)) + 3 * np.eye(23)
+    X = inputs.uniform(23, 9, seed=7)
+    Y = inputs.uniform(9, 23, seed=8)
+    tol = 1e-13
+    assert np.allclose(oracle.trsm_lln(L, X, alpha=0.5), sl.solve_triangular(L, 0.5 * X, lower=True), atol=tol)
+    Lu = np.tril(L, -1) + np.eye(23)
+    assert np.allclose(oracle.trsm_lln(L, X, unit=True), sl.solve_triangular(Lu, X, lower=True), atol=tol)
+    assert np.allclose(oracle.trsm_llt(L, X), sl.solve_triangular(L.T, X, lower=False), atol=tol)
+    assert np.allclose(oracle.trsm_lun(U, X), sl.solve_triangular(U, X, lower=False), atol=tol)
+    assert np.allclose(oracle.trsm_rlt(L, Y), sl.solve_triangular(L, Y.T, lower=True).T, atol=tol)
+    assert np.allclose(oracle.trmm_rln(L, Y), Y @ L, atol=tol)
+    assert np.allclose(oracle.trmm_llt(L, X), L.T @ X, atol=tol)
+
+
 def test_laswp_definition(oracle):
     A = inputs.uniform(9, 4, seed=1)
     ipiv = np.array([3, 2, 9, 4], dtype=np.int32)
