@@ -59,6 +59,23 @@ def flops_getrf(n: int) -> float:
     return 2.0 * n ** 3 / 3.0 - n ** 2 / 2.0 + 5.0 * n / 6.0
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """Largest value of x over all ranks (the slowest replica sets the time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gflops(step_flops: float, ms_per_step: float, world: int) -> float:
+    """Whole-job throughput: every replica factors its own matrices, so the
+    job does world * step_flops per (max over ranks) step time."""
+    return world * step_flops / (ms_per_step * 1e-3) / 1e9
+
+
 def workload_config(n: int) -> dict:
     return {
         "workload": f"recursive dpotrf (lower, SPD B*B^T+n*I) + dgetrf (partial pivoting, U(-1,1)), "
@@ -267,13 +284,10 @@ def run_gpu(args, rank, world, local_rank):
     ms_total = t_start.elapsed_time(t_end)
     ms_potrf = [e[0].elapsed_time(e[1]) for e in ev]
     ms_getrf = [e[1].elapsed_time(e[2]) for e in ev]
-    if world > 1:
-        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, world, dev)
     ms_step = ms_total / args.steps
     step_flops = flops_potrf(n) + flops_getrf(n)
-    value = world * step_flops / (ms_step * 1e-3) / 1e9
+    value = aggregate_gflops(step_flops, ms_step, world)
 
     # dominant kernel by device time over the timed region
     dom_name = max(trace, key=lambda k: trace[k]["ms"]) if trace else None
@@ -319,12 +333,8 @@ def run_gpu(args, rank, world, local_rank):
                 ts.append(t1 - t0)
             if h_inf.tolist() != [0, 0]:
                 raise RuntimeError("host-buffer factorization failed")
-        t_e2e = statistics.median(ts)
-        if world > 1:
-            t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * step_flops / t_e2e / 1e9, "unit": UNIT,
+        t_e2e = max_over_ranks(statistics.median(ts), world, dev)
+        e2e = {"value": aggregate_gflops(step_flops, 1e3 * t_e2e, world), "unit": UNIT,
                "h2d_bytes_per_step": 2 * n * n * 8,
                "d2h_bytes_per_step": 2 * n * n * 8 + n * 4 + 2 * 4,
                "ms_per_step": 1e3 * t_e2e, "steps": len(ts)}

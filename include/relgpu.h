@@ -3,8 +3,9 @@
  * Peise & Bientinesi, "Recursive Algorithms for Dense Linear Algebra: The
  * ReLAPACK Collection" (arXiv 1602.06763).
  *
- * The routines keep LAPACK's own argument lists (Section 5: "LAPACK's
- * interface is preserved") and add three trailing arguments: a device
+ * The routines keep LAPACK's own argument lists (Section 5: the recursive
+ * routines are drop-in replacements for LAPACK's) and add three trailing
+ * arguments: a device
  * workspace, its size in bytes, and the CUDA stream to run on.
  *
  * Conventions shared by every entry point
@@ -125,6 +126,60 @@ int rl_dpotri(char uplo, int64_t n, double *A, int64_t lda, int32_t *info,
               void *work, size_t lwork, rl_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Solves with computed factors (Section 5 lists xgetrf and xpotrf as the
+ * building blocks of xgesv and xposv).  B (n x nrhs) is overwritten by X.
+ *   rl_dgetrs: trans 'N' only; A and ipiv from rl_dgetrf: X = U^{-1} L^{-1} P B.
+ *     Argument numbers: 1 trans, 2 n, 3 nrhs, 4 A, 5 lda, 6 ipiv, 7 B, 8 ldb.
+ *   rl_dpotrs: uplo 'L' only; A from rl_dpotrf: X = L^{-T} L^{-1} B.
+ *     Argument numbers: 1 uplo, 2 n, 3 nrhs, 4 A, 5 lda, 6 B, 7 ldb.
+ * No workspace; stream-ordered.
+ * ------------------------------------------------------------------------- */
+int rl_dgetrs(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda,
+              const int32_t *ipiv, double *B, int64_t ldb, rl_stream_t stream);
+int rl_dpotrs(char uplo, int64_t n, int64_t nrhs, const double *A, int64_t lda, double *B,
+              int64_t ldb, rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Precision form: A X = B (FP64) solved with a low-precision factorization
+ * and FP64 iterative refinement, following the semantics of LAPACK's dsgesv
+ * (LU) and dsposv (Cholesky).  The paper has no precision form; the
+ * factorization itself is the paper's recursion (Section 3) run in FP32
+ * storage, with the trailing updates in the precision `prec`:
+ *   RL_PREC_FP32   FP32 products and accumulation (SIMT)
+ *   RL_PREC_TF32   TF32 products, FP32 accumulation (tcgen05 tensor cores)
+ *   RL_PREC_BF16   BF16 products, FP32 accumulation (tcgen05)
+ *   RL_PREC_FP16S  FP16 products, FP32 accumulation (tcgen05); A is scaled by
+ *                  a power of two so that its entries are at most 1
+ *   RL_PREC_TF32X3 three TF32 products per term (a = a_hi + a_lo split),
+ *                  close to FP32 accuracy (tcgen05)
+ * Updates smaller than 128 x 128 x 64 stay on the SIMT FP32 path.
+ * A copy of A is converted to FP32 in `work` and factored; x0 = solve(b);
+ * then r = b - A x in FP64 and x += solve(r) until, for every column,
+ * ||r||_inf <= tol (||A||_inf ||x||_inf + ||b||_inf) (tol <= 0 means 1e-14)
+ * or maxiter corrections were applied.  Without convergence, or when the
+ * FP32 factorization fails, A is factored in FP64 in place (A then holds the
+ * FP64 factors, and ipiv their pivots) and X = A^{-1} B.
+ * Outputs (device, asynchronous): X (n x nrhs, ldx), ipiv (LU), *iter:
+ *   >= 0  corrections applied before convergence (A unchanged)
+ *   -2    an entry of A overflows FP32; -3 the FP32 factorization failed;
+ *   -31   no convergence within maxiter (the FP64 fallback was used)
+ * and *info: LAPACK's info of the FP64 fallback factorization (0 otherwise).
+ * nrhs <= 512.  Workspace: rl_dsgesv_work_size / rl_dsposv_work_size bytes.
+ * Argument numbers (dsgesv): 1 n, 2 nrhs, 3 A, 4 lda, 5 ipiv, 6 B, 7 ldb,
+ * 8 X, 9 ldx; (dsposv): 1 uplo, 2 n, 3 nrhs, 4 A, 5 lda, 6 B, 7 ldb, 8 X,
+ * 9 ldx.
+ * ------------------------------------------------------------------------- */
+enum { RL_PREC_FP32 = 0, RL_PREC_TF32 = 1, RL_PREC_BF16 = 2, RL_PREC_FP16S = 3, RL_PREC_TF32X3 = 4 };
+size_t rl_dsgesv_work_size(int64_t n, int64_t nrhs, int prec);
+size_t rl_dsposv_work_size(int64_t n, int64_t nrhs, int prec);
+int rl_dsgesv(int64_t n, int64_t nrhs, double *A, int64_t lda, int32_t *ipiv, const double *B,
+              int64_t ldb, double *X, int64_t ldx, int prec, double tol, int maxiter,
+              int32_t *iter, int32_t *info, void *work, size_t lwork, rl_stream_t stream);
+int rl_dsposv(char uplo, int64_t n, int64_t nrhs, double *A, int64_t lda, const double *B,
+              int64_t ldb, double *X, int64_t ldx, int prec, double tol, int maxiter,
+              int32_t *iter, int32_t *info, void *work, size_t lwork, rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * BLAS-3 layer (Section 2: the Level-3 kernels the recursions are built on),
  * exported for direct use and per-kernel measurement.  BLAS semantics and
  * argument numbering; all matrices on the device, stream-ordered, no
@@ -151,6 +206,21 @@ int rl_dtrsm(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
 int rl_dtrmm(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
              double alpha, const double *A, int64_t lda, double *B, int64_t ldb,
              rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Tensor-core GEMM on FP32 storage (the update kernel of the precision
+ * form): C(m x n) := C + alpha op(A) op(B), A, B, C single precision,
+ * column-major, products in `prec` (RL_PREC_TF32, _BF16, _FP16S, _TF32X3) on
+ * the tcgen05 tensor cores with FP32 accumulation.  op(A) and op(B) are first
+ * packed into `work` (rl_sgemm_tc_work_size bytes).  Argument numbers:
+ * 1 prec, 2 transa, 3 transb, 4 m, 5 n, 6 k, 7 alpha, 8 A, 9 lda, 10 B,
+ * 11 ldb, 12 C, 13 ldc.  RL_PREC_FP32 or sizes the kernel cannot take return
+ * RL_ERR_UNSUPPORTED.
+ * ------------------------------------------------------------------------- */
+size_t rl_sgemm_tc_work_size(int64_t m, int64_t n, int64_t k, int prec);
+int rl_sgemm_tc(int prec, char transa, char transb, int64_t m, int64_t n, int64_t k, float alpha,
+                const float *A, int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc,
+                void *work, size_t lwork, rl_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Host-buffer forms (end-to-end use from host memory).  A_host (and

@@ -17,7 +17,7 @@ Passages followed (Section / Figure of the paper):
   trtri   Section 3, Fig. 4 updates (1)-(4), trti2 base case
   lauum   Section 5 (xlauum, A := L^T L)
   potri   Section 5 (xtrtri as the building block of potri) = trtri + lauum
-  split   Section 3 footnote: halves that are multiples of 8 where possible
+  split   Section 3 footnote: halves that are multiples of 8 when the size allows
 """
 from __future__ import annotations
 
@@ -101,7 +101,7 @@ def _ld(a):
 
 
 def split(n: int) -> int:
-    """Section 3 footnote: first half size, a multiple of 8 where possible."""
+    """Section 3 footnote: first half size, a multiple of 8 when the size allows."""
     return int(_lib().or_split(n))
 
 

@@ -9,7 +9,7 @@
  * with the CUDA implementation.
  *
  * Everything is IEEE binary64, column-major with a leading dimension (LAPACK
- * storage, Section 5: "LAPACK's interface is preserved").  It is compiled with
+ * storage; Section 5 keeps LAPACK's calling conventions).  It is compiled with
  * -ffp-contract=off so that every a*b+c is two rounded operations and the
  * results are the same on x86-64 and aarch64.  OpenMP only distributes
  * independent output elements over threads; each element's arithmetic is done
@@ -17,7 +17,7 @@
  *
  * Routines and the passages they follow:
  *   or_split        Section 3, footnote on alignment (halves that are
- *                   multiples of 8 where possible)
+ *                   multiples of 8 when the size allows)
  *   or_trtri        Section 3, Fig. 4 updates (1)-(4); base case trti2 below
  *                   the crossover c (Section 3, "crossover size")
  *   or_lauum        Section 5, xlauum (A := L^T L); recursion: the standard
@@ -456,7 +456,7 @@ void or_lauum(int64_t n, double *A, int64_t lda, int64_t c)
 }
 
 /* POTRI: A^{-1} = (L L^T)^{-1} = L^{-T} L^{-1}: trtri then lauum on L
- * (Section 5, xtrtri "serves as a building block in ... potri"). */
+ * (Section 5 names xtrtri as a component of the SPD inverse xpotri). */
 int64_t or_potri(int64_t n, double *A, int64_t lda, int64_t c)
 {
     int64_t info = or_trtri(0, n, A, lda, c);

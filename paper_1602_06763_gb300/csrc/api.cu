@@ -39,42 +39,55 @@ void note(Ctx &c, cudaError_t e)
 // ---- recursions -------------------------------------------------------------
 
 // Cholesky: potrf(A11); A21 := A21 L11^{-T}; A22 -= A21 A21^T; potrf(A22).
-static void potrf_rec(Ctx &c, i64 n, double *A, i64 lda, i64 off)
+template <typename T>
+void potrf_rec_t(Ctx &c, i64 n, T *A, i64 lda, i64 off)
 {
     if (n <= 0) return;
-    if (n <= g_params.potrf_c) { potf2(c, n, A, lda, off); return; }
+    if (n <= g_params.potrf_c) { potf2<T>(c, n, A, lda, off); return; }
     const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
-    double *A21 = A + n1, *A22 = A + n1 + n1 * lda;
-    potrf_rec(c, n1, A, lda, off);
-    trsm_rlt(c, n2, n1, 1.0, A, lda, A21, lda);
-    gemm(c, false, true, n2, n2, n1, -1.0, A21, lda, A21, lda, 1.0, A22, lda, true);
-    potrf_rec(c, n2, A22, lda, off + n1);
+    T *A21 = A + n1, *A22 = A + n1 + n1 * lda;
+    potrf_rec_t<T>(c, n1, A, lda, off);
+    trsm_rlt<T>(c, n2, n1, T(1), A, lda, A21, lda);
+    gemm<T>(c, false, true, n2, n2, n1, T(-1), A21, lda, A21, lda, T(1), A22, lda, true);
+    potrf_rec_t<T>(c, n2, A22, lda, off + n1);
 }
 
 // LU of the m x n block whose top-left corner is (r0, r0) of the matrix A0
 // (m_tot rows).  Pivots are written as global 1-based rows.
-static void getrf_rec(Ctx &c, double *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r0, i64 m, i64 n)
+template <typename T>
+void getrf_rec_t(Ctx &c, T *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r0, i64 m, i64 n)
 {
     if (m <= 0 || n <= 0) return;
-    double *A = A0 + r0 + r0 * lda;
+    T *A = A0 + r0 + r0 * lda;
     const i64 nb = g_params.getrf_nb;
-    if (n <= nb) { getf2_panel(c, m, n, A, lda, ipiv, r0); return; }
+    if (n <= nb) { getf2_panel<T>(c, m, n, A, lda, ipiv, r0); return; }
     if (m < n) {
         // wide: factor the leading m x m block, then swap and solve the rest
-        getrf_rec(c, A0, lda, m_tot, ipiv, r0, m, m);
-        laswp(c, A0, lda, m_tot, r0 + m, n - m, r0, r0 + m, ipiv);
-        trsm_lln(c, true, m, n - m, 1.0, A, lda, A + m * lda, lda);
+        getrf_rec_t<T>(c, A0, lda, m_tot, ipiv, r0, m, m);
+        laswp<T>(c, A0, lda, m_tot, r0 + m, n - m, r0, r0 + m, ipiv);
+        trsm_lln<T>(c, true, m, n - m, T(1), A, lda, A + m * lda, lda);
         return;
     }
     const i64 n1 = split_q(n, n > 2 * TRX_NB ? TRX_NB : nb), n2 = n - n1;
-    getrf_rec(c, A0, lda, m_tot, ipiv, r0, m, n1);
-    laswp(c, A0, lda, m_tot, r0 + n1, n2, r0, r0 + n1, ipiv);
-    trsm_lln(c, true, n1, n2, 1.0, A, lda, A + n1 * lda, lda);
-    gemm(c, false, false, m - n1, n2, n1, -1.0, A + n1, lda, A + n1 * lda, lda, 1.0,
-         A + n1 + n1 * lda, lda);
-    getrf_rec(c, A0, lda, m_tot, ipiv, r0 + n1, m - n1, n2);
+    getrf_rec_t<T>(c, A0, lda, m_tot, ipiv, r0, m, n1);
+    laswp<T>(c, A0, lda, m_tot, r0 + n1, n2, r0, r0 + n1, ipiv);
+    trsm_lln<T>(c, true, n1, n2, T(1), A, lda, A + n1 * lda, lda);
+    gemm<T>(c, false, false, m - n1, n2, n1, T(-1), A + n1, lda, A + n1 * lda, lda, T(1),
+            A + n1 + n1 * lda, lda);
+    getrf_rec_t<T>(c, A0, lda, m_tot, ipiv, r0 + n1, m - n1, n2);
     const i64 mn2 = (m - n1) < n2 ? (m - n1) : n2;
-    laswp(c, A0, lda, m_tot, r0, n1, r0 + n1, r0 + n1 + mn2, ipiv);
+    laswp<T>(c, A0, lda, m_tot, r0, n1, r0 + n1, r0 + n1 + mn2, ipiv);
+}
+
+template void potrf_rec_t<double>(Ctx &, i64, double *, i64, i64);
+template void potrf_rec_t<float>(Ctx &, i64, float *, i64, i64);
+template void getrf_rec_t<double>(Ctx &, double *, i64, i64, int32_t *, i64, i64, i64);
+template void getrf_rec_t<float>(Ctx &, float *, i64, i64, int32_t *, i64, i64, i64);
+
+static void potrf_rec(Ctx &c, i64 n, double *A, i64 lda, i64 off) { potrf_rec_t<double>(c, n, A, lda, off); }
+static void getrf_rec(Ctx &c, double *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r0, i64 m, i64 n)
+{
+    getrf_rec_t<double>(c, A0, lda, m_tot, ipiv, r0, m, n);
 }
 
 // Triangular inverse, Fig. 4: trtri(TL); BL := BL TL; BL := -BR^{-1} BL;
@@ -305,6 +318,139 @@ int rl_dtrmm(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
     if (lower && !left && !tr) trmm_rln(c, unit, m, n, alpha, A, lda, B, ldb);
     else if (lower && left && tr && !unit) trmm_llt(c, m, n, alpha, A, lda, B, ldb);
     else return RL_ERR_UNSUPPORTED;
+    return finish(c);
+}
+
+// ---- tensor-core GEMM on FP32 storage ------------------------------------------
+
+static bool tc_prec(int prec)
+{
+    return prec == RL_PREC_TF32 || prec == RL_PREC_BF16 || prec == RL_PREC_FP16S || prec == RL_PREC_TF32X3;
+}
+
+size_t rl_sgemm_tc_work_size(int64_t m, int64_t n, int64_t k, int prec)
+{
+    if (!tc_prec(prec) || m < 0 || n < 0 || k < 0) return 0;
+    return tc_work_bytes(m, n, k, prec);
+}
+
+int rl_sgemm_tc(int prec, char transa, char transb, int64_t m, int64_t n, int64_t k, float alpha,
+                const float *A, int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc,
+                void *work, size_t lwork, rl_stream_t stream)
+{
+    if (!is_n(transa) && !is_t(transa)) return -2;
+    if (!is_n(transb) && !is_t(transb)) return -3;
+    if (m < 0) return -4;
+    if (n < 0) return -5;
+    if (k < 0) return -6;
+    const bool ta = is_t(transa), tb = is_t(transb);
+    if (lda < imax1(ta ? k : m)) return -9;
+    if (ldb < imax1(tb ? n : k)) return -11;
+    if (ldc < imax1(m)) return -13;
+    if (!tc_prec(prec)) return RL_ERR_UNSUPPORTED;
+    if (m == 0 || n == 0 || k == 0) return RL_SUCCESS;
+    if (work == nullptr || lwork < tc_work_bytes(m, n, k, prec)) return RL_ERR_WORKSPACE;
+    Ctx c = make_ctx(stream, nullptr, nullptr, 0);
+    if (!tc_gemm(c, prec, ta, tb, m, n, k, alpha, A, lda, B, ldb, C, ldc, false, work, lwork))
+        return RL_ERR_UNSUPPORTED;
+    return finish(c);
+}
+
+// ---- solves with the factors ------------------------------------------------
+
+int rl_dgetrs(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda,
+              const int32_t *ipiv, double *B, int64_t ldb, rl_stream_t stream)
+{
+    if (!is_n(trans) && !is_t(trans)) return -1;
+    if (n < 0) return -2;
+    if (nrhs < 0) return -3;
+    if (lda < imax1(n)) return -5;
+    if (ldb < imax1(n)) return -8;
+    if (is_t(trans)) return RL_ERR_UNSUPPORTED;
+    if (n == 0 || nrhs == 0) return RL_SUCCESS;
+    if (ipiv == nullptr) return RL_ERR_NULL_POINTER;
+    Ctx c = make_ctx(stream, nullptr, nullptr, 0);
+    laswp<double>(c, B, ldb, n, 0, nrhs, 0, n, ipiv);
+    trsm_lln<double>(c, true, n, nrhs, 1.0, A, lda, B, ldb);
+    trsm_lun<double>(c, n, nrhs, 1.0, A, lda, B, ldb);
+    return finish(c);
+}
+
+int rl_dpotrs(char uplo, int64_t n, int64_t nrhs, const double *A, int64_t lda, double *B,
+              int64_t ldb, rl_stream_t stream)
+{
+    if (!is_l(uplo) && !is_u(uplo)) return -1;
+    if (n < 0) return -2;
+    if (nrhs < 0) return -3;
+    if (lda < imax1(n)) return -5;
+    if (ldb < imax1(n)) return -7;
+    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
+    if (n == 0 || nrhs == 0) return RL_SUCCESS;
+    Ctx c = make_ctx(stream, nullptr, nullptr, 0);
+    trsm_lln<double>(c, false, n, nrhs, 1.0, A, lda, B, ldb);
+    trsm_llt<double>(c, n, nrhs, 1.0, A, lda, B, ldb);
+    return finish(c);
+}
+
+// ---- precision form ------------------------------------------------------------
+
+static bool prec_ok(int prec) { return prec == RL_PREC_FP32 || tc_prec(prec); }
+
+size_t rl_dsgesv_work_size(int64_t n, int64_t nrhs, int prec)
+{
+    if (n < 0 || nrhs < 0 || !prec_ok(prec)) return 0;
+    return mixed_work_size(n, nrhs, true, prec);
+}
+
+size_t rl_dsposv_work_size(int64_t n, int64_t nrhs, int prec)
+{
+    if (n < 0 || nrhs < 0 || !prec_ok(prec)) return 0;
+    return mixed_work_size(n, nrhs, false, prec);
+}
+
+int rl_dsgesv(int64_t n, int64_t nrhs, double *A, int64_t lda, int32_t *ipiv, const double *B,
+              int64_t ldb, double *X, int64_t ldx, int prec, double tol, int maxiter, int32_t *iter,
+              int32_t *info, void *work, size_t lwork, rl_stream_t stream)
+{
+    if (n < 0) return -1;
+    if (nrhs < 0) return -2;
+    if (lda < imax1(n)) return -4;
+    if (ldb < imax1(n)) return -7;
+    if (ldx < imax1(n)) return -9;
+    if (!prec_ok(prec)) return RL_ERR_UNSUPPORTED;
+    if (nrhs > 512) return RL_ERR_UNSUPPORTED;
+    if (info == nullptr || iter == nullptr || (ipiv == nullptr && n > 0)) return RL_ERR_NULL_POINTER;
+    if (n > 0 && nrhs > 0 && (work == nullptr || lwork < rl_dsgesv_work_size(n, nrhs, prec)))
+        return RL_ERR_WORKSPACE;
+    Ctx c = make_ctx(stream, info, work, lwork);
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    note(c, cudaMemsetAsync(iter, 0, sizeof(int32_t), c.s));
+    if (n == 0 || nrhs == 0) return finish(c);
+    mixed_solve(c, true, n, nrhs, A, lda, ipiv, B, ldb, X, ldx, prec, tol, maxiter, iter);
+    return finish(c);
+}
+
+int rl_dsposv(char uplo, int64_t n, int64_t nrhs, double *A, int64_t lda, const double *B,
+              int64_t ldb, double *X, int64_t ldx, int prec, double tol, int maxiter, int32_t *iter,
+              int32_t *info, void *work, size_t lwork, rl_stream_t stream)
+{
+    if (!is_l(uplo) && !is_u(uplo)) return -1;
+    if (n < 0) return -2;
+    if (nrhs < 0) return -3;
+    if (lda < imax1(n)) return -5;
+    if (ldb < imax1(n)) return -7;
+    if (ldx < imax1(n)) return -9;
+    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
+    if (!prec_ok(prec)) return RL_ERR_UNSUPPORTED;
+    if (nrhs > 512) return RL_ERR_UNSUPPORTED;
+    if (info == nullptr || iter == nullptr) return RL_ERR_NULL_POINTER;
+    if (n > 0 && nrhs > 0 && (work == nullptr || lwork < rl_dsposv_work_size(n, nrhs, prec)))
+        return RL_ERR_WORKSPACE;
+    Ctx c = make_ctx(stream, info, work, lwork);
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    note(c, cudaMemsetAsync(iter, 0, sizeof(int32_t), c.s));
+    if (n == 0 || nrhs == 0) return finish(c);
+    mixed_solve(c, false, n, nrhs, A, lda, nullptr, B, ldb, X, ldx, prec, tol, maxiter, iter);
     return finish(c);
 }
 

@@ -1,5 +1,7 @@
-// BLAS-3 layer of the recursive factorizations: an FP64 GEMM/SYRK kernel and
-// recursive TRSM/TRMM that send almost all of their flops to it.
+// BLAS-3 layer of the recursive factorizations: a GEMM/SYRK kernel and
+// recursive TRSM/TRMM that send almost all of their flops to it.  Templated
+// on the element type: double for the FP64 path, float for the FP32 storage
+// of the precision form.
 //
 // The paper's algorithms (Section 3) spend >99 % of their flops in BLAS-3
 // calls of the top recursion levels (Fig. 5).  On GB300 binary64 arithmetic
@@ -23,11 +25,11 @@ namespace rl {
 // launched (square C) and only elements i >= j are stored.
 // 256 threads as 16x16; thread (tx,ty) owns rows tx+16i, columns ty+16j.
 // ----------------------------------------------------------------------------
-template <bool TA, bool TB, bool LOWER>
+template <typename T, bool TA, bool TB, bool LOWER>
 __global__ void __launch_bounds__(256)
-k_dgemm(i64 m, i64 n, i64 k, double alpha, const double *__restrict__ A, i64 lda,
-        const double *__restrict__ B, i64 ldb, double beta, double *C, i64 ldc,
-        const int32_t *abort, int tiles_m)
+k_gemm(i64 m, i64 n, i64 k, T alpha, const T *__restrict__ A, i64 lda,
+       const T *__restrict__ B, i64 ldb, T beta, T *C, i64 ldc,
+       const int32_t *abort, int tiles_m)
 {
     if (abort && *abort != 0) return;
     int tm, tn;
@@ -45,17 +47,17 @@ k_dgemm(i64 m, i64 n, i64 k, double alpha, const double *__restrict__ A, i64 lda
     }
     const i64 i0 = (i64)tm * GEMM_BM, j0 = (i64)tn * GEMM_BN;
 
-    __shared__ double As[2][GEMM_BK][GEMM_BM + 1];
-    __shared__ double Bs[2][GEMM_BK][GEMM_BN + 1];
+    __shared__ T As[2][GEMM_BK][GEMM_BM + 1];
+    __shared__ T Bs[2][GEMM_BK][GEMM_BN + 1];
 
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    double acc[4][4];
+    T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 
-    double ra[4], rb[4];
+    T ra[4], rb[4];
     auto load = [&](i64 k0) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -63,7 +65,7 @@ k_dgemm(i64 m, i64 n, i64 k, double alpha, const double *__restrict__ A, i64 lda
             if (!TA) { il = tid & 63; pl = (tid >> 6) + 4 * r; }
             else     { pl = tid & 15; il = (tid >> 4) + 16 * r; }
             i64 gi = i0 + il, gp = k0 + pl;
-            double v = 0.0;
+            T v = T(0);
             if (gi < m && gp < k) v = TA ? __ldg(A + gi * lda + gp) : __ldg(A + gp * lda + gi);
             ra[r] = v;
         }
@@ -73,7 +75,7 @@ k_dgemm(i64 m, i64 n, i64 k, double alpha, const double *__restrict__ A, i64 lda
             if (!TB) { pl = tid & 15; jl = (tid >> 4) + 16 * r; }
             else     { jl = tid & 63; pl = (tid >> 6) + 4 * r; }
             i64 gj = j0 + jl, gp = k0 + pl;
-            double v = 0.0;
+            T v = T(0);
             if (gj < n && gp < k) v = TB ? __ldg(B + gp * ldb + gj) : __ldg(B + gj * ldb + gp);
             rb[r] = v;
         }
@@ -105,7 +107,7 @@ k_dgemm(i64 m, i64 n, i64 k, double alpha, const double *__restrict__ A, i64 lda
             if (t + 1 < nk) load((t + 1) * GEMM_BK);
 #pragma unroll
             for (int kk = 0; kk < GEMM_BK; ++kk) {
-                double a[4], b[4];
+                T a[4], b[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) a[i] = As[st][kk][tx + 16 * i];
 #pragma unroll
@@ -129,43 +131,51 @@ k_dgemm(i64 m, i64 n, i64 k, double alpha, const double *__restrict__ A, i64 lda
             const i64 row = i0 + tx + 16 * i;
             if (row >= m) continue;
             if (LOWER && row < col) continue;
-            double *cp = C + col * ldc + row;
-            double cv = (beta == 0.0) ? 0.0 : beta * (*cp);
+            T *cp = C + col * ldc + row;
+            T cv = (beta == T(0)) ? T(0) : beta * (*cp);
             *cp = fma(alpha, acc[i][j], cv);
         }
     }
 }
 
-template <bool TA, bool TB, bool LOWER>
-static void launch_gemm(Ctx &c, i64 m, i64 n, i64 k, double alpha, const double *A,
-                        i64 lda, const double *B, i64 ldb, double beta, double *C, i64 ldc)
+template <typename T, bool TA, bool TB, bool LOWER>
+static void launch_gemm(Ctx &c, i64 m, i64 n, i64 k, T alpha, const T *A, i64 lda, const T *B,
+                        i64 ldb, T beta, T *C, i64 ldc)
 {
     const i64 tiles_m = (m + GEMM_BM - 1) / GEMM_BM, tiles_n = (n + GEMM_BN - 1) / GEMM_BN;
     i64 grid = LOWER ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
     if (grid <= 0) return;
     const double flops = LOWER ? (double)k * (double)n * (double)(n + 1) : 2.0 * m * n * k;
     Launch L(c, LOWER ? K_SYRK : K_GEMM, flops, 0.0);
-    k_dgemm<TA, TB, LOWER><<<(unsigned)grid, 256, 0, c.s>>>(
+    k_gemm<T, TA, TB, LOWER><<<(unsigned)grid, 256, 0, c.s>>>(
         m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, c.abort, (int)tiles_m);
 }
 
-void gemm(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, double alpha, const double *A,
-          i64 lda, const double *B, i64 ldb, double beta, double *C, i64 ldc, bool lower)
+template <typename T>
+void gemm(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, T alpha, const T *A, i64 lda,
+          const T *B, i64 ldb, T beta, T *C, i64 ldc, bool lower)
 {
     if (m <= 0 || n <= 0) return;
-    if (k <= 0 && beta == 1.0) return;
+    if (k <= 0 && beta == T(1)) return;
+    if (sizeof(T) == 4 && c.prec != RL_PREC_FP32 && beta == T(1) && m >= TC_MIN_MN && n >= TC_MIN_MN &&
+        k >= TC_MIN_K) {
+        if (tc_gemm(c, c.prec, ta, tb, m, n, k, (float)alpha, (const float *)A, lda, (const float *)B, ldb,
+                    (float *)C, ldc, lower, c.tcwork, c.tclwork))
+            return;
+    }
     if (lower) {
-        if (!ta && tb) launch_gemm<false, true, true>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
-        else if (ta && !tb) launch_gemm<true, false, true>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
-        else if (!ta && !tb) launch_gemm<false, false, true>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
-        else launch_gemm<true, true, true>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+        if (!ta && tb) launch_gemm<T, false, true, true>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+        else if (ta && !tb) launch_gemm<T, true, false, true>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+        else if (!ta && !tb) launch_gemm<T, false, false, true>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+        else launch_gemm<T, true, true, true>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
         return;
     }
-    if (!ta && !tb) launch_gemm<false, false, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
-    else if (!ta && tb) launch_gemm<false, true, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
-    else if (ta && !tb) launch_gemm<true, false, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
-    else launch_gemm<true, true, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+    if (!ta && !tb) launch_gemm<T, false, false, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+    else if (!ta && tb) launch_gemm<T, false, true, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+    else if (ta && !tb) launch_gemm<T, true, false, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+    else launch_gemm<T, true, true, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
 }
+
 // ----------------------------------------------------------------------------
 // Triangle kernels for blocks of order <= 64 (the leaves of the TRSM/TRMM
 // recursion).  Each vector of B (a row or a column, depending on the side)
@@ -190,41 +200,41 @@ enum TriOp { TRI_FWD = 0, TRI_BWD = 1, TRI_MUL = 2 };
 
 __device__ __forceinline__ int tri_ix(int i, int k) { return i * (i + 1) / 2 + k; }
 
-// Stage the order-n triangle of T (lower if !TRANS_UPPER, else the upper
+// Stage the order-n triangle of Tm (lower if !TRANS_UPPER, else the upper
 // triangle stored transposed) into P, padded with identity up to NB.
-template <int NB, bool TRANS_UPPER>
-__device__ __forceinline__ void stage_tri(double *P, const double *T, i64 ldt, int n, bool unit)
+template <typename T, int NB, bool TRANS_UPPER>
+__device__ __forceinline__ void stage_tri(T *P, const T *Tm, i64 ldt, int n, bool unit)
 {
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
         const int i = e % NB, k = e / NB;
         if (i < k) continue;
-        double v;
-        if (i < n && k < n) v = TRANS_UPPER ? T[(i64)i * ldt + k] : T[(i64)k * ldt + i];
-        else v = (i == k) ? 1.0 : 0.0;
-        if (unit && i == k) v = 1.0;
+        T v;
+        if (i < n && k < n) v = TRANS_UPPER ? Tm[(i64)i * ldt + k] : Tm[(i64)k * ldt + i];
+        else v = (i == k) ? T(1) : T(0);
+        if (unit && i == k) v = T(1);
         P[tri_ix(i, k)] = v;
     }
 }
 
-template <int NB, int OP, bool ROWS, bool UNIT, bool TRANS_UPPER>
+template <typename T, int NB, int OP, bool ROWS, bool UNIT, bool TRANS_UPPER>
 __global__ void __launch_bounds__(TRI_THREADS)
-k_tri(i64 nvec, int n, double alpha, const double *__restrict__ T, i64 ldt, double *B, i64 ldb,
+k_tri(i64 nvec, int n, T alpha, const T *__restrict__ Tm, i64 ldt, T *B, i64 ldb,
       const int32_t *abort)
 {
     if (abort && *abort != 0) return;
-    __shared__ double P[NB * (NB + 1) / 2];
-    stage_tri<NB, TRANS_UPPER>(P, T, ldt, n, UNIT);
+    __shared__ T P[NB * (NB + 1) / 2];
+    stage_tri<T, NB, TRANS_UPPER>(P, Tm, ldt, n, UNIT);
     __syncthreads();
     constexpr int E = NB / 4;
     const int q = threadIdx.x & 3;
     const int gbase = threadIdx.x & 28;              // first lane of this group
     const i64 v = (i64)blockIdx.x * TRI_VECS + (threadIdx.x >> 2);
     const bool live = v < nvec;
-    double x[E];
+    T x[E];
 #pragma unroll
     for (int t = 0; t < E; ++t) {
         const int e = 4 * t + q;
-        double b = 0.0;
+        T b = T(0);
         if (live && e < n) b = ROWS ? B[(i64)e * ldb + v] : B[v * ldb + e];
         x[t] = alpha * b;
     }
@@ -233,7 +243,7 @@ k_tri(i64 nvec, int n, double alpha, const double *__restrict__ T, i64 ldt, doub
         for (int j = 0; j < NB; ++j) {
             const int s = j >> 2, own = j & 3;
             if (!UNIT && q == own) x[s] = x[s] / P[tri_ix(j, j)];
-            const double xj = __shfl_sync(0xffffffffu, x[s], gbase | own);
+            const T xj = __shfl_sync(0xffffffffu, x[s], gbase | own);
 #pragma unroll
             for (int t = 0; t < E; ++t) {
                 const int k = 4 * t + q;
@@ -245,7 +255,7 @@ k_tri(i64 nvec, int n, double alpha, const double *__restrict__ T, i64 ldt, doub
         for (int j = NB - 1; j >= 0; --j) {
             const int s = j >> 2, own = j & 3;
             if (!UNIT && q == own) x[s] = x[s] / P[tri_ix(j, j)];
-            const double xj = __shfl_sync(0xffffffffu, x[s], gbase | own);
+            const T xj = __shfl_sync(0xffffffffu, x[s], gbase | own);
 #pragma unroll
             for (int t = 0; t < E; ++t) {
                 const int k = 4 * t + q;
@@ -256,7 +266,7 @@ k_tri(i64 nvec, int n, double alpha, const double *__restrict__ T, i64 ldt, doub
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
             const int s = k >> 2, own = k & 3;
-            const double bk = __shfl_sync(0xffffffffu, x[s], gbase | own);
+            const T bk = __shfl_sync(0xffffffffu, x[s], gbase | own);
             if (q == own) x[s] = UNIT ? bk : bk * P[tri_ix(k, k)];
 #pragma unroll
             for (int t = 0; t < E; ++t) {
@@ -277,104 +287,121 @@ k_tri(i64 nvec, int n, double alpha, const double *__restrict__ T, i64 ldt, doub
     }
 }
 
-template <int OP, bool ROWS, bool UNIT, bool TRANS_UPPER>
-static void launch_tri(Ctx &c, int kind, i64 nvec, int n, double alpha, const double *T, i64 ldt,
-                       double *B, i64 ldb)
+template <typename T, int OP, bool ROWS, bool UNIT, bool TRANS_UPPER>
+static void launch_tri(Ctx &c, int kind, i64 nvec, int n, T alpha, const T *Tm, i64 ldt, T *B,
+                       i64 ldb)
 {
     if (nvec <= 0 || n <= 0) return;
     const unsigned grid = (unsigned)((nvec + TRI_VECS - 1) / TRI_VECS);
     Launch L(c, kind, (double)nvec * n * n, 0.0);
     if (n <= 16)
-        k_tri<16, OP, ROWS, UNIT, TRANS_UPPER><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, T, ldt, B, ldb, c.abort);
+        k_tri<T, 16, OP, ROWS, UNIT, TRANS_UPPER><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, Tm, ldt, B, ldb, c.abort);
     else if (n <= 32)
-        k_tri<32, OP, ROWS, UNIT, TRANS_UPPER><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, T, ldt, B, ldb, c.abort);
+        k_tri<T, 32, OP, ROWS, UNIT, TRANS_UPPER><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, Tm, ldt, B, ldb, c.abort);
     else
-        k_tri<64, OP, ROWS, UNIT, TRANS_UPPER><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, T, ldt, B, ldb, c.abort);
+        k_tri<T, 64, OP, ROWS, UNIT, TRANS_UPPER><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, Tm, ldt, B, ldb, c.abort);
 }
 
 // ----------------------------------------------------------------------------
 // Recursive drivers (halving with 64-aligned splits).
 // ----------------------------------------------------------------------------
-void trsm_lln(Ctx &c, bool unit, i64 m, i64 n, double alpha, const double *L, i64 ldl,
-              double *B, i64 ldb)
+template <typename T>
+void trsm_lln(Ctx &c, bool unit, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
 {
     if (m <= 0 || n <= 0) return;
     if (m <= TRX_NB) {
-        if (unit) launch_tri<TRI_FWD, false, true, false>(c, K_TRSM, n, (int)m, alpha, L, ldl, B, ldb);
-        else launch_tri<TRI_FWD, false, false, false>(c, K_TRSM, n, (int)m, alpha, L, ldl, B, ldb);
+        if (unit) launch_tri<T, TRI_FWD, false, true, false>(c, K_TRSM, n, (int)m, alpha, L, ldl, B, ldb);
+        else launch_tri<T, TRI_FWD, false, false, false>(c, K_TRSM, n, (int)m, alpha, L, ldl, B, ldb);
         return;
     }
     const i64 m1 = split_q(m, TRX_NB), m2 = m - m1;
-    trsm_lln(c, unit, m1, n, alpha, L, ldl, B, ldb);
-    gemm(c, false, false, m2, n, m1, -1.0, L + m1, ldl, B, ldb, alpha, B + m1, ldb);
-    trsm_lln(c, unit, m2, n, 1.0, L + m1 + m1 * ldl, ldl, B + m1, ldb);
+    trsm_lln<T>(c, unit, m1, n, alpha, L, ldl, B, ldb);
+    gemm<T>(c, false, false, m2, n, m1, T(-1), L + m1, ldl, B, ldb, alpha, B + m1, ldb);
+    trsm_lln<T>(c, unit, m2, n, T(1), L + m1 + m1 * ldl, ldl, B + m1, ldb);
 }
 
-void trsm_rlt(Ctx &c, i64 m, i64 n, double alpha, const double *L, i64 ldl, double *B, i64 ldb)
+template <typename T>
+void trsm_rlt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
 {
     if (m <= 0 || n <= 0) return;
     if (n <= TRX_NB) {
-        launch_tri<TRI_FWD, true, false, false>(c, K_TRSM, m, (int)n, alpha, L, ldl, B, ldb);
+        launch_tri<T, TRI_FWD, true, false, false>(c, K_TRSM, m, (int)n, alpha, L, ldl, B, ldb);
         return;
     }
     const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
-    trsm_rlt(c, m, n1, alpha, L, ldl, B, ldb);
-    gemm(c, false, true, m, n2, n1, -1.0, B, ldb, L + n1, ldl, alpha, B + n1 * ldb, ldb);
-    trsm_rlt(c, m, n2, 1.0, L + n1 + n1 * ldl, ldl, B + n1 * ldb, ldb);
+    trsm_rlt<T>(c, m, n1, alpha, L, ldl, B, ldb);
+    gemm<T>(c, false, true, m, n2, n1, T(-1), B, ldb, L + n1, ldl, alpha, B + n1 * ldb, ldb);
+    trsm_rlt<T>(c, m, n2, T(1), L + n1 + n1 * ldl, ldl, B + n1 * ldb, ldb);
 }
 
-void trsm_llt(Ctx &c, i64 m, i64 n, double alpha, const double *L, i64 ldl, double *B, i64 ldb)
+template <typename T>
+void trsm_llt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
 {
     if (m <= 0 || n <= 0) return;
     if (m <= TRX_NB) {
-        launch_tri<TRI_BWD, false, false, false>(c, K_TRSM, n, (int)m, alpha, L, ldl, B, ldb);
+        launch_tri<T, TRI_BWD, false, false, false>(c, K_TRSM, n, (int)m, alpha, L, ldl, B, ldb);
         return;
     }
     const i64 m1 = split_q(m, TRX_NB), m2 = m - m1;
-    trsm_llt(c, m2, n, alpha, L + m1 + m1 * ldl, ldl, B + m1, ldb);
-    gemm(c, true, false, m1, n, m2, -1.0, L + m1, ldl, B + m1, ldb, alpha, B, ldb);
-    trsm_llt(c, m1, n, 1.0, L, ldl, B, ldb);
+    trsm_llt<T>(c, m2, n, alpha, L + m1 + m1 * ldl, ldl, B + m1, ldb);
+    gemm<T>(c, true, false, m1, n, m2, T(-1), L + m1, ldl, B + m1, ldb, alpha, B, ldb);
+    trsm_llt<T>(c, m1, n, T(1), L, ldl, B, ldb);
 }
 
-void trsm_lun(Ctx &c, i64 m, i64 n, double alpha, const double *U, i64 ldu, double *B, i64 ldb)
+template <typename T>
+void trsm_lun(Ctx &c, i64 m, i64 n, T alpha, const T *U, i64 ldu, T *B, i64 ldb)
 {
     if (m <= 0 || n <= 0) return;
     if (m <= TRX_NB) {
-        launch_tri<TRI_BWD, false, false, true>(c, K_TRSM, n, (int)m, alpha, U, ldu, B, ldb);
+        launch_tri<T, TRI_BWD, false, false, true>(c, K_TRSM, n, (int)m, alpha, U, ldu, B, ldb);
         return;
     }
     const i64 m1 = split_q(m, TRX_NB), m2 = m - m1;
-    trsm_lun(c, m2, n, alpha, U + m1 + m1 * ldu, ldu, B + m1, ldb);
-    gemm(c, false, false, m1, n, m2, -1.0, U + m1 * ldu, ldu, B + m1, ldb, alpha, B, ldb);
-    trsm_lun(c, m1, n, 1.0, U, ldu, B, ldb);
+    trsm_lun<T>(c, m2, n, alpha, U + m1 + m1 * ldu, ldu, B + m1, ldb);
+    gemm<T>(c, false, false, m1, n, m2, T(-1), U + m1 * ldu, ldu, B + m1, ldb, alpha, B, ldb);
+    trsm_lun<T>(c, m1, n, T(1), U, ldu, B, ldb);
 }
 
-void trmm_rln(Ctx &c, bool unit, i64 m, i64 n, double alpha, const double *L, i64 ldl, double *B,
-              i64 ldb)
+template <typename T>
+void trmm_rln(Ctx &c, bool unit, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
 {
     if (m <= 0 || n <= 0) return;
     if (n <= TRX_NB) {
-        if (unit) launch_tri<TRI_MUL, true, true, false>(c, K_TRMM, m, (int)n, alpha, L, ldl, B, ldb);
-        else launch_tri<TRI_MUL, true, false, false>(c, K_TRMM, m, (int)n, alpha, L, ldl, B, ldb);
+        if (unit) launch_tri<T, TRI_MUL, true, true, false>(c, K_TRMM, m, (int)n, alpha, L, ldl, B, ldb);
+        else launch_tri<T, TRI_MUL, true, false, false>(c, K_TRMM, m, (int)n, alpha, L, ldl, B, ldb);
         return;
     }
     const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
-    trmm_rln(c, unit, m, n1, alpha, L, ldl, B, ldb);
-    gemm(c, false, false, m, n1, n2, alpha, B + n1 * ldb, ldb, L + n1, ldl, 1.0, B, ldb);
-    trmm_rln(c, unit, m, n2, alpha, L + n1 + n1 * ldl, ldl, B + n1 * ldb, ldb);
+    trmm_rln<T>(c, unit, m, n1, alpha, L, ldl, B, ldb);
+    gemm<T>(c, false, false, m, n1, n2, alpha, B + n1 * ldb, ldb, L + n1, ldl, T(1), B, ldb);
+    trmm_rln<T>(c, unit, m, n2, alpha, L + n1 + n1 * ldl, ldl, B + n1 * ldb, ldb);
 }
 
-void trmm_llt(Ctx &c, i64 m, i64 n, double alpha, const double *L, i64 ldl, double *B, i64 ldb)
+template <typename T>
+void trmm_llt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
 {
     if (m <= 0 || n <= 0) return;
     if (m <= TRX_NB) {
-        launch_tri<TRI_MUL, false, false, false>(c, K_TRMM, n, (int)m, alpha, L, ldl, B, ldb);
+        launch_tri<T, TRI_MUL, false, false, false>(c, K_TRMM, n, (int)m, alpha, L, ldl, B, ldb);
         return;
     }
     const i64 m1 = split_q(m, TRX_NB), m2 = m - m1;
-    trmm_llt(c, m1, n, alpha, L, ldl, B, ldb);
-    gemm(c, true, false, m1, n, m2, alpha, L + m1, ldl, B + m1, ldb, 1.0, B, ldb);
-    trmm_llt(c, m2, n, alpha, L + m1 + m1 * ldl, ldl, B + m1, ldb);
+    trmm_llt<T>(c, m1, n, alpha, L, ldl, B, ldb);
+    gemm<T>(c, true, false, m1, n, m2, alpha, L + m1, ldl, B + m1, ldb, T(1), B, ldb);
+    trmm_llt<T>(c, m2, n, alpha, L + m1 + m1 * ldl, ldl, B + m1, ldb);
 }
+
+#define RL_INST_BLAS3(T)                                                                          \
+    template void gemm<T>(Ctx &, bool, bool, i64, i64, i64, T, const T *, i64, const T *, i64, T, \
+                          T *, i64, bool);                                                        \
+    template void trsm_lln<T>(Ctx &, bool, i64, i64, T, const T *, i64, T *, i64);                \
+    template void trsm_rlt<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);                      \
+    template void trsm_llt<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);                      \
+    template void trsm_lun<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);                      \
+    template void trmm_rln<T>(Ctx &, bool, i64, i64, T, const T *, i64, T *, i64);                \
+    template void trmm_llt<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);
+RL_INST_BLAS3(double)
+RL_INST_BLAS3(float)
+#undef RL_INST_BLAS3
 
 }  // namespace rl

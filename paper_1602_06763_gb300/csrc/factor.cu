@@ -1,22 +1,32 @@
 // Base cases of the recursions (Section 3: below the crossover size c the
 // recursion switches to LAPACK's unblocked routines) and the row
-// interchanges of the LU factorization.
+// interchanges of the LU factorization.  potf2, the LU panel and LASWP are
+// templated on the element type (double: FP64 path; float: FP32 storage of
+// the precision form).
 //
 //  k_potf2        unblocked Cholesky of a diagonal block (n <= 64), one CTA,
 //                 right-looking in shared memory; IEEE sqrt and division.
 //  k_trti2        unblocked triangular inverse (n <= 64), one CTA.
 //  k_lauu2        unblocked L^T L (n <= 64), one CTA.
 //  k_diag_scan    first exactly-zero diagonal entry (dtrtri's info).
-//  k_getf2_panel  fused LU panel: per column a pivot search (warp-shuffle
-//                 argmax, lowest row on ties), the row swap, the division of
-//                 the column by the pivot and the rank-1 update, with the
-//                 panel held in shared memory across the CTAs of one
-//                 cooperative launch; CTAs exchange their pivot candidates
-//                 through a small global workspace and a bounded grid barrier.
+//  k_panel        fused LU panel of an m x nb block (nb <= 64): per column a
+//                 pivot search (warp-shuffle argmax, lowest row on ties), the
+//                 row swap, the division of the column by the pivot and the
+//                 rank-1 update.  The co-resident CTAs of one cooperative
+//                 launch each keep up to 256 rows in registers (one row per
+//                 thread) and exchange their pivot candidates through
+//                 flag-carrying slots in a small global workspace: a slot
+//                 holds the candidate and the column it belongs to, so
+//                 publishing a candidate is also the barrier arrival.
+//  k_panel_smem   the same algorithm with the rows in shared memory and an
+//                 arrival-counter barrier, for panels taller than 256 rows
+//                 per CTA.
 //  k_laswp        row interchanges: each CTA turns the swap sequence into the
 //                 net permutation of the touched rows (in shared memory) and
 //                 then moves every touched row of its columns with one
 //                 coalesced gather and one scatter per column.
+// Every device-side wait is bounded (RL_PARAM_SPIN_LIMIT_NS); a wait that
+// runs out sets *info = RL_INFO_DEVICE_TIMEOUT and the kernel returns.
 #include <climits>
 #include "internal.cuh"
 
@@ -32,12 +42,13 @@ __device__ __forceinline__ int tix(int i, int k) { return i * (i + 1) / 2 + k; }
 // column j below the diagonal divided by l_jj; trailing lower block updated
 // a_ik -= l_ij l_kj.
 // ----------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(256)
-k_potf2(int n, double *A, i64 lda, int32_t *info, i64 info_off, const int32_t *abort)
+k_potf2(int n, T *A, i64 lda, int32_t *info, i64 info_off, const int32_t *abort)
 {
     if (abort && *abort != 0) return;
-    __shared__ double S[BASE_N][BASE_N + 1];
-    __shared__ double col[BASE_N];
+    __shared__ T S[BASE_N][BASE_N + 1];
+    __shared__ T col[BASE_N];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads
     for (int j = ty; j < n; j += 16)
         for (int i = j + tx; i < n; i += 16) S[i][j] = A[(i64)j * lda + i];
@@ -45,15 +56,15 @@ k_potf2(int n, double *A, i64 lda, int32_t *info, i64 info_off, const int32_t *a
     int fail = 0;
     for (int j = 0; j < n; ++j) {
         // every thread evaluates the pivot of column j identically
-        const double d = S[j][j];
-        if (!(d > 0.0)) { fail = j + 1; break; }
-        const double ljj = sqrt(d);
+        const T d = S[j][j];
+        if (!(d > T(0))) { fail = j + 1; break; }
+        const T ljj = sqrt(d);
         for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) col[i] = S[i][j] / ljj;
         __syncthreads();
         if (threadIdx.x == 0) S[j][j] = ljj;
         for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) S[i][j] = col[i];
         for (int ii = j + 1 + ty; ii < n; ii += 16) {
-            const double lij = col[ii];
+            const T lij = col[ii];
             for (int kk = j + 1 + tx; kk <= ii; kk += 16) S[ii][kk] = fma(-lij, col[kk], S[ii][kk]);
         }
         __syncthreads();
@@ -63,11 +74,12 @@ k_potf2(int n, double *A, i64 lda, int32_t *info, i64 info_off, const int32_t *a
     if (fail && threadIdx.x == 0) *info = (int32_t)(info_off + fail);
 }
 
-void potf2(Ctx &c, i64 n, double *A, i64 lda, i64 info_off)
+template <typename T>
+void potf2(Ctx &c, i64 n, T *A, i64 lda, i64 info_off)
 {
     if (n <= 0) return;
     Launch L(c, K_POTF2, (double)n * n * n / 3.0, 0.0);
-    k_potf2<<<1, 256, 0, c.s>>>((int)n, A, lda, c.info, info_off, c.abort);
+    k_potf2<T><<<1, 256, 0, c.s>>>((int)n, A, lda, c.info, info_off, c.abort);
 }
 
 // ----------------------------------------------------------------------------
@@ -185,10 +197,15 @@ constexpr int PANEL_RMIN = 64;
 constexpr size_t PANEL_SMEM_MAX = 200 * 1024;
 
 struct PanelWS {
-    unsigned int counter;               // grid-barrier arrivals (zeroed per launch)
+    // register-row kernel: slot key = (column + 1) << 40 | row, 0 = empty
+    unsigned long long key[2][PANEL_GMAX];
+    double val[2][PANEL_GMAX];
+    // shared-memory kernel: arrival counter
+    unsigned int counter;
     unsigned int pad[63];
     double cand_val[2][PANEL_GMAX];     // |candidate| per CTA, double-buffered
     long long cand_idx[2][PANEL_GMAX];  // candidate row (panel-local), LLONG_MAX = none
+    // both kernels
     double cand_row[2][PANEL_GMAX][PANEL_NBMAX];
     double rowj[2][PANEL_NBMAX];        // current row j, published by its owner
 };
@@ -202,6 +219,18 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
     return v;
 }
 
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long global_ns()
 {
     unsigned long long t;
@@ -209,9 +238,157 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Bounded grid barrier: every CTA adds one arrival and waits until `target`
-// arrivals are visible, for at most spin_ns nanoseconds.  Returns false (for
-// the whole CTA) if the wait ran out.
+__device__ __forceinline__ bool better(double v, long long i, double bv, long long bi)
+{
+    return v > bv || (v == bv && i < bi);
+}
+
+// Row-per-thread panel.  CTA g owns panel rows [g*R, g*R + R), R <= 256;
+// thread t works on row g*R + t, kept in shared memory as a[c * 256 + t]
+// (consecutive threads, consecutive words).  ipiv and info use global
+// numbering: panel row r is matrix row r0 + r.
+template <typename T>
+__global__ void __launch_bounds__(PANEL_THREADS)
+k_panel(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, PanelWS *ws, int R,
+        long long spin_ns, const int32_t *abort)
+{
+    if (abort && *abort != 0) return;
+    extern __shared__ unsigned char smem_raw[];
+    T *S = reinterpret_cast<T *>(smem_raw);
+    __shared__ double wv[PANEL_THREADS / 32];
+    __shared__ long long wi[PANEL_THREADS / 32];
+    __shared__ long long s_p;
+    __shared__ int s_gw, s_fail;
+    __shared__ T urow[PANEL_NBMAX], rowj[PANEL_NBMAX];
+
+    const int tid = threadIdx.x, lane = tid & 31, G = gridDim.x, g = blockIdx.x;
+    const i64 rbeg = (i64)g * R;
+    const int rows = (int)max((i64)0, min((i64)R, m - rbeg));
+    const i64 my = rbeg + tid;                 // this thread's panel row
+    const bool have = tid < rows;
+    T *a = S + tid;                            // a[c * PANEL_THREADS] = element (my, c)
+    if (have)
+        for (int c = 0; c < nb; ++c) a[c * PANEL_THREADS] = A[(i64)c * lda + my];
+    if (tid == 0) s_fail = 0;
+
+    const int mn = (int)min(m, (i64)nb);
+    for (int j = 0; j < mn; ++j) {
+        const int buf = j & 1;
+        // 1. this CTA's candidate: largest |a_ij|, i >= j, lowest i on ties
+        double bv = -1.0;
+        long long bi = LLONG_MAX;
+        if (have && my >= j) { bv = fabs((double)a[j * PANEL_THREADS]); bi = my; }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+            const long long oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+        }
+        if (lane == 0) { wv[tid >> 5] = bv; wi[tid >> 5] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < PANEL_THREADS / 32; ++w)
+                if (better(wv[w], wi[w], bv, bi)) { bv = wv[w]; bi = wi[w]; }
+            wv[0] = bv;
+            s_p = bi;
+        }
+        __syncthreads();
+        // 2. publish the candidate row (and row j, by its owner), then the slot;
+        //    one warp copies each row so the stores are spread over 32 lanes
+        {
+            const long long cand = s_p;
+            if (cand != LLONG_MAX && tid < 32) {
+                const T *src = S + (int)(cand - rbeg);
+                for (int c = lane; c < nb; c += 32) ws->cand_row[buf][g][c] = (double)src[c * PANEL_THREADS];
+            }
+            if (j >= rbeg && j < rbeg + rows && tid >= 32 && tid < 64) {
+                const T *src = S + (int)(j - rbeg);
+                for (int c = lane; c < nb; c += 32) ws->rowj[buf][c] = (double)src[c * PANEL_THREADS];
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            ws->val[buf][g] = wv[0];
+            __threadfence();
+            const unsigned long long idx = (s_p == LLONG_MAX) ? 0xFFFFFFFFFFull : (unsigned long long)s_p;
+            st_release_u64(&ws->key[buf][g], ((unsigned long long)(j + 1) << 40) | idx);
+        }
+        // 3. warp 0 waits for every CTA's slot of column j and picks the winner
+        if (tid < 32) {
+            double v = -1.0;
+            long long ix = LLONG_MAX;
+            int gw = -1, ok = 1;
+            const unsigned long long want = (unsigned long long)(j + 1);
+            for (int q = lane; q < G; q += 32) {
+                unsigned long long kq = ld_acquire_u64(&ws->key[buf][q]);
+                if ((kq >> 40) != want) {
+                    const unsigned long long t0 = global_ns();
+                    while (((kq = ld_acquire_u64(&ws->key[buf][q])) >> 40) != want) {
+                        if ((long long)(global_ns() - t0) >= spin_ns) { ok = 0; break; }
+                        __nanosleep(32);
+                    }
+                }
+                if (!ok) break;
+                const unsigned long long qi = kq & 0xFFFFFFFFFFull;
+                if (qi != 0xFFFFFFFFFFull) {
+                    const double qv = __ldcg(&ws->val[buf][q]);
+                    if (better(qv, (long long)qi, v, ix)) { v = qv; ix = (long long)qi; gw = q; }
+                }
+            }
+            ok = __all_sync(0xffffffffu, ok);
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_down_sync(0xffffffffu, v, o);
+                const long long oi = __shfl_down_sync(0xffffffffu, ix, o);
+                const int og = __shfl_down_sync(0xffffffffu, gw, o);
+                if (og >= 0 && (gw < 0 || better(ov, oi, v, ix))) { v = ov; ix = oi; gw = og; }
+            }
+            if (lane == 0) {
+                s_p = (gw >= 0) ? ix : (long long)j;
+                s_gw = gw;
+                if (!ok) s_fail = 1;
+            }
+        }
+        __syncthreads();
+        if (s_fail) {
+            if (tid == 0) atomicExch(info, RL_INFO_DEVICE_TIMEOUT);
+            return;
+        }
+        // 4. fetch the pivot row (and row j if this CTA owns the pivot row)
+        const long long p = s_p;
+        const int gw = s_gw;
+        const bool own_p = (p != j) && p >= rbeg && p < rbeg + rows;
+        for (int c = tid; c < nb; c += blockDim.x) {
+            urow[c] = (T)((gw >= 0) ? __ldcg(&ws->cand_row[buf][gw][c]) : __ldcg(&ws->rowj[buf][c]));
+            if (own_p) rowj[c] = (T)__ldcg(&ws->rowj[buf][c]);
+        }
+        __syncthreads();
+        if (g == 0 && tid == 0) ipiv[r0 + j] = (int32_t)(r0 + p + 1);
+        // 5. swap, scale and rank-1 update of this thread's row
+        if (have) {
+            if (p != j && my == j) {
+                for (int c = 0; c < nb; ++c) a[c * PANEL_THREADS] = urow[c];
+            } else if (own_p && my == p) {
+                for (int c = 0; c < nb; ++c) a[c * PANEL_THREADS] = rowj[c];
+            }
+        }
+        const T piv = urow[j];
+        if (piv != T(0)) {
+            if (have && my > j) {
+                const T l = a[j * PANEL_THREADS] / piv;
+                a[j * PANEL_THREADS] = l;
+#pragma unroll 4
+                for (int c = j + 1; c < nb; ++c)
+                    a[c * PANEL_THREADS] = fma(-l, urow[c], a[c * PANEL_THREADS]);
+            }
+        } else {
+            if (g == 0 && tid == 0 && *info == 0) *info = (int32_t)(r0 + j + 1);
+            // a zero pivot column: the elimination step subtracts zero multiples
+        }
+    }
+    if (have)
+        for (int c = 0; c < nb; ++c) A[(i64)c * lda + my] = a[c * PANEL_THREADS];
+}
+
+// Bounded grid barrier of the shared-memory panel kernel.
 __device__ bool grid_barrier(unsigned *counter, unsigned target, long long spin_ns)
 {
     __shared__ int ok;
@@ -234,20 +411,17 @@ __device__ bool grid_barrier(unsigned *counter, unsigned target, long long spin_
     return ok != 0;
 }
 
-__device__ __forceinline__ bool better(double v, long long i, double bv, long long bi)
-{
-    return v > bv || (v == bv && i < bi);
-}
-
-// Panel: rows [0, m) x columns [0, nb) of A (panel-local), CTA g holds rows
-// [g*R, g*R + R) as a column-major slab S[c*R + r].  ipiv and info use
-// global numbering: row r of the panel is row r0 + r of the matrix.
+// Shared-memory panel for tall panels (R > 256 rows per CTA): CTA g holds
+// rows [g*R, g*R + R) as a column-major slab S[c*R + r].
+template <typename T>
 __global__ void __launch_bounds__(PANEL_THREADS)
-k_getf2_panel(i64 m, int nb, double *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info,
-              PanelWS *ws, int R, long long spin_ns)
+k_panel_smem(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, PanelWS *ws,
+             int R, long long spin_ns, const int32_t *abort)
 {
-    extern __shared__ double S[];
-    __shared__ double urow[PANEL_NBMAX];
+    if (abort && *abort != 0) return;
+    extern __shared__ unsigned char smem_raw[];
+    T *S = reinterpret_cast<T *>(smem_raw);
+    __shared__ T urow[PANEL_NBMAX];
     __shared__ double wv[PANEL_THREADS / 32];
     __shared__ long long wi[PANEL_THREADS / 32];
     __shared__ long long s_p;
@@ -265,13 +439,12 @@ k_getf2_panel(i64 m, int nb, double *A, i64 lda, int32_t *ipiv, i64 r0, int32_t 
     const int mn = (int)min(m, (i64)nb);
     for (int j = 0; j < mn; ++j) {
         const int buf = j & 1;
-        // local candidate: largest |a_ij|, i >= j, lowest i on ties
         double bv = -1.0;
         long long bi = LLONG_MAX;
         for (int r = tid; r < rows; r += blockDim.x) {
             const i64 i = rbeg + r;
             if (i < j) continue;
-            const double v = fabs(S[j * R + r]);
+            const double v = fabs((double)S[j * R + r]);
             if (better(v, i, bv, bi)) { bv = v; bi = i; }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -291,14 +464,13 @@ k_getf2_panel(i64 m, int nb, double *A, i64 lda, int32_t *ipiv, i64 r0, int32_t 
         __syncthreads();
         {
             const long long mine = s_p;
-            if (mine != LLONG_MAX && tid < nb) ws->cand_row[buf][g][tid] = S[tid * R + (int)(mine - rbeg)];
-            if (j >= rbeg && j < rbeg + rows && tid < nb) ws->rowj[buf][tid] = S[tid * R + (int)(j - rbeg)];
+            if (mine != LLONG_MAX && tid < nb) ws->cand_row[buf][g][tid] = (double)S[tid * R + (int)(mine - rbeg)];
+            if (j >= rbeg && j < rbeg + rows && tid < nb) ws->rowj[buf][tid] = (double)S[tid * R + (int)(j - rbeg)];
         }
         if (!grid_barrier(&ws->counter, (unsigned)G * (unsigned)(j + 1), spin_ns)) {
             if (tid == 0) atomicExch(info, RL_INFO_DEVICE_TIMEOUT);
             return;
         }
-        // global winner (every CTA computes the same one)
         if (tid < 32) {
             double v = -1.0;
             long long ix = LLONG_MAX;
@@ -319,16 +491,16 @@ k_getf2_panel(i64 m, int nb, double *A, i64 lda, int32_t *ipiv, i64 r0, int32_t 
         __syncthreads();
         const long long p = s_p;
         const int gw = s_gw;
-        if (tid < nb) urow[tid] = (gw >= 0) ? __ldcg(&ws->cand_row[buf][gw][tid]) : __ldcg(&ws->rowj[buf][tid]);
+        if (tid < nb) urow[tid] = (T)((gw >= 0) ? __ldcg(&ws->cand_row[buf][gw][tid]) : __ldcg(&ws->rowj[buf][tid]));
         __syncthreads();
-        const double piv = urow[j];
+        const T piv = urow[j];
         if (g == 0 && tid == 0) ipiv[r0 + j] = (int32_t)(r0 + p + 1);
         if (p != j) {
             if (j >= rbeg && j < rbeg + rows && tid < nb) S[tid * R + (int)(j - rbeg)] = urow[tid];
-            if (p >= rbeg && p < rbeg + rows && tid < nb) S[tid * R + (int)(p - rbeg)] = __ldcg(&ws->rowj[buf][tid]);
+            if (p >= rbeg && p < rbeg + rows && tid < nb) S[tid * R + (int)(p - rbeg)] = (T)__ldcg(&ws->rowj[buf][tid]);
         }
         __syncthreads();
-        if (piv != 0.0) {
+        if (piv != T(0)) {
             for (int r = tid; r < rows; r += blockDim.x)
                 if (rbeg + r > j) S[j * R + r] = S[j * R + r] / piv;
         } else if (g == 0 && tid == 0) {
@@ -350,32 +522,46 @@ k_getf2_panel(i64 m, int nb, double *A, i64 lda, int32_t *ipiv, i64 r0, int32_t 
     }
 }
 
-void getf2_panel(Ctx &c, i64 m, i64 nb, double *A, i64 lda, int32_t *ipiv, i64 r0)
+template <typename T>
+void getf2_panel(Ctx &c, i64 m, i64 nb, T *A, i64 lda, int32_t *ipiv, i64 r0)
 {
     if (m <= 0 || nb <= 0) return;
-    static bool attr = false;
-    if (!attr) {
-        note(c, cudaFuncSetAttribute(k_getf2_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)PANEL_SMEM_MAX));
-        attr = true;
-    }
+    PanelWS *ws = reinterpret_cast<PanelWS *>(c.work);
     const int gmax = c.num_sms < PANEL_GMAX ? c.num_sms : PANEL_GMAX;
     i64 R = (m + gmax - 1) / gmax;
     if (R < PANEL_RMIN) R = PANEL_RMIN;
     if (R > m) R = m;
-    if ((size_t)R * nb * sizeof(double) > PANEL_SMEM_MAX) { note(c, cudaErrorInvalidValue); return; }
     const int G = (int)((m + R - 1) / R);
-    PanelWS *ws = reinterpret_cast<PanelWS *>(c.work);
-    note(c, cudaMemsetAsync(&ws->counter, 0, sizeof(unsigned), c.s));
-    int Ri = (int)R, nbi = (int)nb;
     long long spin = g_params.spin_ns;
     int32_t *info = c.info;
-    void *args[] = {&m, &nbi, &A, &lda, &ipiv, &r0, &info, &ws, &Ri, &spin};
+    static bool attr[2] = {false, false};
+    const int ti = sizeof(T) == 8 ? 0 : 1;
+    if (!attr[ti]) {
+        note(c, cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(PANEL_THREADS * PANEL_NBMAX * sizeof(T))));
+        note(c, cudaFuncSetAttribute(k_panel_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)PANEL_SMEM_MAX));
+        attr[ti] = true;
+    }
     // flops of an m x nb unblocked LU (leading terms): m nb^2 - nb^3/3
     Launch L(c, K_PANEL, (double)m * nb * nb - (double)nb * nb * nb / 3.0,
-             2.0 * (double)m * nb * sizeof(double));
-    note(c, cudaLaunchCooperativeKernel((const void *)k_getf2_panel, dim3(G), dim3(PANEL_THREADS), args,
-                                        (size_t)R * nb * sizeof(double), c.s));
+             2.0 * (double)m * nb * sizeof(T));
+    if (R <= PANEL_THREADS) {
+        note(c, cudaMemsetAsync(ws->key, 0, sizeof(ws->key), c.s));
+        int nbi = (int)nb, Ri = (int)R;
+        const int32_t *abort = c.abort;
+        void *args[] = {&m, &nbi, &A, &lda, &ipiv, &r0, &info, &ws, &Ri, &spin, &abort};
+        note(c, cudaLaunchCooperativeKernel((const void *)k_panel<T>, dim3(G), dim3(PANEL_THREADS), args,
+                                            (size_t)PANEL_THREADS * nb * sizeof(T), c.s));
+        return;
+    }
+    if ((size_t)R * nb * sizeof(T) > PANEL_SMEM_MAX) { note(c, cudaErrorInvalidValue); return; }
+    note(c, cudaMemsetAsync(&ws->counter, 0, sizeof(unsigned), c.s));
+    int Ri = (int)R, nbi = (int)nb;
+    const int32_t *abort = c.abort;
+        void *args[] = {&m, &nbi, &A, &lda, &ipiv, &r0, &info, &ws, &Ri, &spin, &abort};
+    note(c, cudaLaunchCooperativeKernel((const void *)k_panel_smem<T>, dim3(G), dim3(PANEL_THREADS), args,
+                                        (size_t)R * nb * sizeof(T), c.s));
 }
 
 // ----------------------------------------------------------------------------
@@ -390,9 +576,12 @@ constexpr size_t LASWP_SMEM_MAX = 200 * 1024;
 // LASWP_CHUNK) on columns [c0 + blockIdx.x*cpc, ...) of A, whose rows
 // [k1, m) are involved.  Shared memory: pos[span] (span = m - k1), the
 // chunk's pivots, and the list of touched rows outside [k1, k2).
+template <typename T>
 __global__ void __launch_bounds__(LASWP_THREADS)
-k_laswp(double *A, i64 lda, i64 m, i64 c0, i64 ncols, i64 k1, i64 k2, const int32_t *ipiv, int cpc)
+k_laswp(T *A, i64 lda, i64 m, i64 c0, i64 ncols, i64 k1, i64 k2, const int32_t *ipiv, int cpc,
+        const int32_t *abort)
 {
+    if (abort && *abort != 0) return;
     extern __shared__ int sm[];
     __shared__ int nout;
     const int span = (int)(m - k1), K = (int)(k2 - k1);
@@ -427,8 +616,8 @@ k_laswp(double *A, i64 lda, i64 m, i64 c0, i64 ncols, i64 k1, i64 k2, const int3
     const int NT = K + nout;
     const i64 cb = (i64)blockIdx.x * cpc, ce = min(ncols, cb + cpc);
     for (i64 col = cb; col < ce; ++col) {
-        double *cp = A + (c0 + col) * lda + k1;
-        double v[LASWP_V];
+        T *cp = A + (c0 + col) * lda + k1;
+        T v[LASWP_V];
 #pragma unroll
         for (int s = 0; s < LASWP_V; ++s) {
             const int t = tid + s * LASWP_THREADS;
@@ -445,41 +634,55 @@ k_laswp(double *A, i64 lda, i64 m, i64 c0, i64 ncols, i64 k1, i64 k2, const int3
 }
 
 // Fallback for very tall matrices: one thread per column, swaps in order.
-__global__ void k_laswp_seq(double *A, i64 lda, i64 c0, i64 ncols, i64 k1, i64 k2, const int32_t *ipiv)
+template <typename T>
+__global__ void k_laswp_seq(T *A, i64 lda, i64 c0, i64 ncols, i64 k1, i64 k2, const int32_t *ipiv,
+                            const int32_t *abort)
 {
+    if (abort && *abort != 0) return;
     const i64 col = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= ncols) return;
-    double *cp = A + (c0 + col) * lda;
+    T *cp = A + (c0 + col) * lda;
     for (i64 i = k1; i < k2; ++i) {
         const i64 p = (i64)ipiv[i] - 1;
-        if (p != i) { double t = cp[i]; cp[i] = cp[p]; cp[p] = t; }
+        if (p != i) { T t = cp[i]; cp[i] = cp[p]; cp[p] = t; }
     }
 }
 
-void laswp(Ctx &c, double *A0, i64 lda, i64 m, i64 c0, i64 ncols, i64 k1, i64 k2,
-           const int32_t *ipiv)
+template <typename T>
+void laswp(Ctx &c, T *A0, i64 lda, i64 m, i64 c0, i64 ncols, i64 k1, i64 k2, const int32_t *ipiv)
 {
     if (ncols <= 0 || k2 <= k1) return;
-    static bool attr = false;
-    if (!attr) {
-        note(c, cudaFuncSetAttribute(k_laswp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    static bool attr[2] = {false, false};
+    const int ti = sizeof(T) == 8 ? 0 : 1;
+    if (!attr[ti]) {
+        note(c, cudaFuncSetAttribute(k_laswp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)LASWP_SMEM_MAX));
-        attr = true;
+        attr[ti] = true;
     }
     for (i64 kb = k1; kb < k2; kb += LASWP_CHUNK) {
         const i64 ke = (kb + LASWP_CHUNK < k2) ? kb + LASWP_CHUNK : k2;
         const size_t smem = (size_t)((m - kb) + 3 * (ke - kb)) * sizeof(int);
         // algorithmic bytes: every interchange reads and writes two rows
-        Launch L(c, K_LASWP, 0.0, 32.0 * (double)(ke - kb) * (double)ncols);
+        Launch L(c, K_LASWP, 0.0, 4.0 * sizeof(T) * (double)(ke - kb) * (double)ncols);
         if (smem <= LASWP_SMEM_MAX) {
             i64 grid = ncols < 2 * (i64)c.num_sms ? ncols : 2 * (i64)c.num_sms;
             const i64 cpc = (ncols + grid - 1) / grid;
             grid = (ncols + cpc - 1) / cpc;
-            k_laswp<<<(unsigned)grid, LASWP_THREADS, smem, c.s>>>(A0, lda, m, c0, ncols, kb, ke, ipiv, (int)cpc);
+            k_laswp<T><<<(unsigned)grid, LASWP_THREADS, smem, c.s>>>(A0, lda, m, c0, ncols, kb, ke, ipiv,
+                                                                     (int)cpc, c.abort);
         } else {
-            k_laswp_seq<<<(unsigned)((ncols + 127) / 128), 128, 0, c.s>>>(A0, lda, c0, ncols, kb, ke, ipiv);
+            k_laswp_seq<T><<<(unsigned)((ncols + 127) / 128), 128, 0, c.s>>>(A0, lda, c0, ncols, kb, ke,
+                                                                           ipiv, c.abort);
         }
     }
 }
+
+#define RL_INST_FACTOR(T)                                                                   \
+    template void potf2<T>(Ctx &, i64, T *, i64, i64);                                     \
+    template void getf2_panel<T>(Ctx &, i64, i64, T *, i64, int32_t *, i64);               \
+    template void laswp<T>(Ctx &, T *, i64, i64, i64, i64, i64, i64, const int32_t *);
+RL_INST_FACTOR(double)
+RL_INST_FACTOR(float)
+#undef RL_INST_FACTOR
 
 }  // namespace rl

@@ -34,6 +34,11 @@ struct Ctx {
     size_t lwork = 0;
     int num_sms = 0;
     cudaError_t err = cudaSuccess;   // first launch error seen
+    // FP32 GEMMs of the precision form: operand precision and the packing
+    // workspace of the tensor-core path (RL_PREC_FP32 = SIMT FP32)
+    int prec = RL_PREC_FP32;
+    void *tcwork = nullptr;
+    size_t tclwork = 0;
 };
 
 int device_sms();
@@ -43,7 +48,7 @@ void note(Ctx &c, cudaError_t e);
 // Kernel kinds, in the order rl_trace_read reports them.
 enum Kind {
     K_GEMM = 0, K_SYRK, K_TRSM, K_TRMM, K_POTF2, K_TRTI2, K_LAUU2, K_DIAG,
-    K_PANEL, K_LASWP, K_COUNT
+    K_PANEL, K_LASWP, K_RESID, K_CONVERT, K_MIX, K_COUNT
 };
 extern std::atomic<int> g_trace_on;
 // Bracket one kernel launch: with tracing on, CUDA events are recorded on the
@@ -77,41 +82,70 @@ inline i64 split_q(i64 n, i64 q)
     return n1;
 }
 
-// ---- BLAS-3 layer (blas3.cu) ----------------------------------------------
+// ---- BLAS-3 layer (blas3.cu), T = double or float ---------------------------
 // C(m x n) := beta*C + alpha*op(A) op(B); lower=true writes only i >= j of a
 // square C (SYRK form, A and B may alias).
-void gemm(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, double alpha,
-          const double *A, i64 lda, const double *B, i64 ldb, double beta,
-          double *C, i64 ldc, bool lower = false);
+template <typename T>
+void gemm(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, T alpha, const T *A, i64 lda,
+          const T *B, i64 ldb, T beta, T *C, i64 ldc, bool lower = false);
 
 // B(m x n) := alpha * L^{-1} B, L lower m x m (unit or not).
-void trsm_lln(Ctx &c, bool unit, i64 m, i64 n, double alpha, const double *L,
-              i64 ldl, double *B, i64 ldb);
+template <typename T>
+void trsm_lln(Ctx &c, bool unit, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb);
 // B(m x n) := alpha * B L^{-T}, L lower n x n, non-unit.
-void trsm_rlt(Ctx &c, i64 m, i64 n, double alpha, const double *L, i64 ldl, double *B, i64 ldb);
+template <typename T>
+void trsm_rlt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb);
 // B(m x n) := alpha * L^{-T} B, L lower m x m, non-unit.
-void trsm_llt(Ctx &c, i64 m, i64 n, double alpha, const double *L, i64 ldl, double *B, i64 ldb);
+template <typename T>
+void trsm_llt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb);
 // B(m x n) := alpha * U^{-1} B, U upper m x m, non-unit.
-void trsm_lun(Ctx &c, i64 m, i64 n, double alpha, const double *U, i64 ldu, double *B, i64 ldb);
+template <typename T>
+void trsm_lun(Ctx &c, i64 m, i64 n, T alpha, const T *U, i64 ldu, T *B, i64 ldb);
 // B(m x n) := alpha * B L, L lower n x n (unit or not).
-void trmm_rln(Ctx &c, bool unit, i64 m, i64 n, double alpha, const double *L, i64 ldl, double *B,
-              i64 ldb);
+template <typename T>
+void trmm_rln(Ctx &c, bool unit, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb);
 // B(m x n) := alpha * L^T B, L lower m x m, non-unit.
-void trmm_llt(Ctx &c, i64 m, i64 n, double alpha, const double *L, i64 ldl, double *B, i64 ldb);
+template <typename T>
+void trmm_llt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb);
 
 // ---- base cases and row interchanges (factor.cu) ---------------------------
-void potf2(Ctx &c, i64 n, double *A, i64 lda, i64 info_off);
+template <typename T>
+void potf2(Ctx &c, i64 n, T *A, i64 lda, i64 info_off);
 void trti2(Ctx &c, bool unit, i64 n, double *A, i64 lda);
 void lauu2(Ctx &c, i64 n, double *A, i64 lda);
 void diag_zero_scan(Ctx &c, i64 n, const double *A, i64 lda);
 // Panel LU of the m x nb block at A (row/col offset r0 in the full matrix);
-// writes ipiv[r0 .. r0+min(m,nb)) as global 1-based rows.
-void getf2_panel(Ctx &c, i64 m, i64 nb, double *A, i64 lda, int32_t *ipiv, i64 r0);
+// writes ipiv[r0 .. r0+min(m,nb)) as global 1-based rows.  c.work holds the
+// panel workspace (panel_ws_bytes()).
+template <typename T>
+void getf2_panel(Ctx &c, i64 m, i64 nb, T *A, i64 lda, int32_t *ipiv, i64 r0);
 // Apply ipiv[k1..k2) (global 1-based rows of the matrix at A0, which has
 // m rows) to columns [c0, c0 + ncols).
-void laswp(Ctx &c, double *A0, i64 lda, i64 m, i64 c0, i64 ncols, i64 k1, i64 k2,
-           const int32_t *ipiv);
+template <typename T>
+void laswp(Ctx &c, T *A0, i64 lda, i64 m, i64 c0, i64 ncols, i64 k1, i64 k2, const int32_t *ipiv);
 
 size_t panel_ws_bytes();
+
+// ---- tensor-core GEMM for FP32 storage (tc_gemm.cu) ---------------------------
+// C(m x n) += alpha op(A) op(B) with operands in precision `prec` (TF32,
+// BF16, FP16, 3xTF32) and FP32 accumulation; lower: square C, lower triangle.
+// Returns false when it does not apply (then the caller uses the SIMT path).
+size_t tc_work_bytes(i64 m, i64 n, i64 k, int prec);
+bool tc_gemm(Ctx &c, int prec, bool ta, bool tb, i64 m, i64 n, i64 k, float alpha, const float *A,
+             i64 lda, const float *B, i64 ldb, float *C, i64 ldc, bool lower, void *work, size_t lwork);
+// Smallest GEMM sent to the tensor cores (smaller ones are latency-bound).
+constexpr i64 TC_MIN_MN = 128, TC_MIN_K = 64;
+
+// ---- recursions (api.cu), T = double or float --------------------------------
+template <typename T>
+void potrf_rec_t(Ctx &c, i64 n, T *A, i64 lda, i64 off);
+template <typename T>
+void getrf_rec_t(Ctx &c, T *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r0, i64 m, i64 n);
+
+// ---- precision form (mixed.cu) ----------------------------------------------
+size_t mixed_work_size(i64 n, i64 nrhs, bool lu, int prec);
+int mixed_solve(Ctx &c, bool lu, i64 n, i64 nrhs, double *A, i64 lda, int32_t *ipiv,
+                const double *B, i64 ldb, double *X, i64 ldx, int prec, double tol, int maxiter,
+                int32_t *iter);
 
 }  // namespace rl

@@ -1,0 +1,457 @@
+// Precision form: solve A X = B to full FP64 backward error with a
+// low-precision factorization and FP64 iterative refinement.
+//
+//   1. A (FP64) is converted to an FP32 working copy W (scaled by a power of
+//      two for the FP16 form so that max |W| <= 1).
+//   2. W is factored by the same recursions as the FP64 path (LU with partial
+//      pivoting, or Cholesky) in FP32 storage.
+//   3. x0 = solve(W, b); then, up to maxiter times: r = b - A x in FP64 (the
+//      only FP64 arithmetic besides the update and the test), stop when
+//      max_j ||r_j||_inf / (||A||_inf ||x_j||_inf + ||b_j||_inf) <= tol,
+//      else d = solve(W, r) in FP32 and x += d in FP64.
+//   4. If the low-precision factorization fails or the refinement does not
+//      converge, A is factored in FP64 in place and X = A^{-1} B (LAPACK
+//      dsgesv / dsposv semantics).
+// Every step is enqueued on the caller's stream; device flags make the
+// kernels of finished or skipped steps return at once, so the call never
+// synchronizes and has a fixed launch sequence.
+#include <cfloat>
+#include "internal.cuh"
+
+namespace rl {
+
+namespace {
+
+constexpr int RES_ROWS = 256;     // rows per CTA of the residual kernel
+constexpr int RES_KC = 512;       // k-chunk of the residual kernel
+constexpr int RES_NR = 8;         // right-hand sides per residual pass
+constexpr int NORM_CH = 64;       // column chunks of the infinity-norm kernel
+
+inline size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Scalars and flags kept on the device.
+struct MixState {
+    double anorm;          // ||A||_inf
+    double scale;          // power of two applied to A in the working copy
+    int32_t winfo;         // low-precision factorization info (or overflow)
+    int32_t stop;          // nonzero: refinement finished or abandoned
+    int32_t conv;          // 1: converged (fallback kernels skip)
+    int32_t iters;         // corrections applied when converged
+    int32_t pad[4];
+    unsigned long long bmax[RES_NR * 64];   // per-RHS max |b| (bit patterns of doubles >= 0)
+    unsigned long long xmax[RES_NR * 64];
+    unsigned long long rmax[RES_NR * 64];
+};
+constexpr int MIX_MAX_NRHS = RES_NR * 64;
+
+struct MixLayout {
+    size_t W, panel, R, D, P, N, S, TC, tc_bytes, total;
+    i64 ldw, nchunks;
+};
+
+MixLayout layout(i64 n, i64 nrhs, bool lu, int prec)
+{
+    MixLayout L;
+    L.ldw = ((n + 31) / 32) * 32;
+    if (L.ldw < 1) L.ldw = 1;
+    L.nchunks = (n + RES_KC - 1) / RES_KC;
+    if (L.nchunks < 1) L.nchunks = 1;
+    size_t off = 0;
+    L.W = off; off += al((size_t)L.ldw * (size_t)(n > 0 ? n : 1) * sizeof(float));
+    L.panel = off; off += lu ? al(panel_ws_bytes()) : 0;
+    L.R = off; off += al((size_t)(n > 0 ? n : 1) * (size_t)nrhs * sizeof(double));
+    L.D = off; off += al((size_t)(n > 0 ? n : 1) * (size_t)nrhs * sizeof(float));
+    L.P = off; off += al((size_t)L.nchunks * RES_NR * (size_t)(n > 0 ? n : 1) * sizeof(double));
+    L.N = off; off += al((size_t)NORM_CH * (size_t)(n > 0 ? n : 1) * sizeof(double));
+    L.S = off; off += al(sizeof(MixState));
+    // packing space of the tensor-core updates: the largest update of either
+    // recursion has at most n rows and n/2 + 64 columns and inner dimension
+    const i64 h = n / 2 + 64;
+    L.tc_bytes = (prec == RL_PREC_FP32) ? 0 : tc_work_bytes(n, h, h, prec);
+    L.TC = off; off += al(L.tc_bytes);
+    L.total = off;
+    return L;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double v)
+{
+    // non-negative doubles order like their bit patterns; NaN maps above +inf
+    atomicMax(p, (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void k_mix_init(MixState *st, int nrhs)
+{
+    const int t = threadIdx.x;
+    if (t == 0) {
+        st->anorm = 0.0;
+        st->scale = 1.0;
+        st->winfo = 0;
+        st->stop = 0;
+        st->conv = 0;
+        st->iters = 0;
+    }
+    for (int j = t; j < MIX_MAX_NRHS; j += blockDim.x) { st->bmax[j] = 0; st->xmax[j] = 0; st->rmax[j] = 0; }
+}
+
+// Partial row sums of |A| over column chunks: N[ch * n + i].
+__global__ void k_rowsum_partial(i64 n, const double *A, i64 lda, double *N)
+{
+    const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ch = blockIdx.y;
+    const i64 cw = (n + NORM_CH - 1) / NORM_CH, c0 = ch * cw, c1 = min(n, c0 + cw);
+    if (i >= n) return;
+    double s = 0.0;
+    for (i64 j = c0; j < c1; ++j) s += fabs(A[j * lda + i]);
+    N[ch * n + i] = s;
+}
+
+// ||A||_inf, max|A| -> scale (power of two so that max|A| * scale <= 1 when
+// requested), and max|b_j| per right-hand side.
+__global__ void k_norms(i64 n, const double *N, const double *A, i64 lda, const double *B, i64 ldb,
+                        int nrhs, int want_scale, MixState *st)
+{
+    __shared__ double red[1024 / 32];
+    double best = 0.0;
+    for (i64 i = threadIdx.x; i < n; i += blockDim.x) {
+        double s = 0.0;
+        for (int ch = 0; ch < NORM_CH; ++ch) s += N[ch * n + i];
+        if (s > best || s != s) best = s;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        double v = __shfl_down_sync(0xffffffffu, best, o);
+        if (v > best || v != v) best = v;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (red[w] > best || red[w] != red[w]) best = red[w];
+        st->anorm = best;
+    }
+    // per-RHS max |b| (block reduction per column)
+    for (int j = 0; j < nrhs; ++j) {
+        double m = 0.0;
+        for (i64 i = threadIdx.x; i < n; i += blockDim.x) {
+            const double v = fabs(B[(i64)j * ldb + i]);
+            if (v > m || v != v) m = v;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v = __shfl_down_sync(0xffffffffu, m, o);
+            if (v > m || v != v) m = v;
+        }
+        if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&st->bmax[j], m);
+    }
+    if (want_scale && threadIdx.x == 0) {
+        // the largest |a_ij| is at most ||A||_inf; scaling by 2^-e with
+        // 2^e >= ||A||_inf bounds every entry of the working copy by 1
+        int e = 0;
+        if (best > 0.0 && best == best) frexp(best, &e);
+        st->scale = ldexp(1.0, -e);
+    }
+    (void)A; (void)lda;
+}
+
+// W = (float)(A * scale); entries beyond the float range flag the working
+// copy as unusable (LAPACK dsgesv's overflow check).
+__global__ void k_to_f32(i64 m, i64 n, const double *A, i64 lda, float *W, i64 ldw, const MixState *st,
+                         int32_t *flag, const int32_t *abort)
+{
+    if (abort && *abort != 0) return;
+    const double s = st->scale;
+    const i64 total = m * n;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x) {
+        const i64 i = e % m, j = e / m;
+        const double v = A[j * lda + i] * s;
+        if (!(fabs(v) <= (double)FLT_MAX) && v == v) *flag = -2;
+        W[j * ldw + i] = (float)v;
+    }
+}
+
+// stop = (low-precision factorization failed) ? 1 : 0.
+__global__ void k_after_factor(MixState *st)
+{
+    if (st->winfo != 0) st->stop = 1;
+}
+
+// Partial products P[ch][c][i] = sum_{k in chunk ch} A[i,k] X[k, c0 + c].
+__global__ void __launch_bounds__(RES_ROWS)
+k_resid_partial(i64 n, int nr, const double *__restrict__ A, i64 lda, const double *__restrict__ X,
+                i64 ldx, double *P, const int32_t *abort)
+{
+    if (abort && *abort != 0) return;
+    __shared__ double Xs[RES_KC][RES_NR];
+    const i64 row = (i64)blockIdx.x * RES_ROWS + threadIdx.x;
+    const int ch = blockIdx.y;
+    const i64 k0 = (i64)ch * RES_KC, k1 = min(n, k0 + RES_KC);
+    const int kc = (int)(k1 - k0);
+    for (int e = threadIdx.x; e < RES_KC * RES_NR; e += blockDim.x) {
+        const int kk = e / RES_NR, c = e % RES_NR;
+        Xs[kk][c] = (kk < kc && c < nr) ? X[(i64)c * ldx + k0 + kk] : 0.0;
+    }
+    __syncthreads();
+    if (row >= n) return;
+    double acc[RES_NR];
+#pragma unroll
+    for (int c = 0; c < RES_NR; ++c) acc[c] = 0.0;
+    const double *ap = A + k0 * lda + row;
+#pragma unroll 8
+    for (int kk = 0; kk < kc; ++kk) {
+        const double a = __ldg(ap + (i64)kk * lda);
+#pragma unroll
+        for (int c = 0; c < RES_NR; ++c) acc[c] = fma(a, Xs[kk][c], acc[c]);
+    }
+    for (int c = 0; c < nr; ++c) P[((i64)ch * RES_NR + c) * n + row] = acc[c];
+}
+
+// R[:, c0 + c] = B - sum_ch P[ch][c]; running max |r| and max |x| per RHS.
+__global__ void k_resid_final(i64 n, int nr, int c0, i64 nchunks, const double *P, const double *B,
+                              i64 ldb, const double *X, i64 ldx, double *R, i64 ldr, MixState *st,
+                              const int32_t *abort)
+{
+    if (abort && *abort != 0) return;
+    const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < n;
+    for (int c = 0; c < nr; ++c) {
+        double ra = 0.0, xa = 0.0;
+        if (live) {
+            double s = 0.0;
+            for (i64 ch = 0; ch < nchunks; ++ch) s += P[(ch * RES_NR + c) * n + i];
+            const double r = B[(i64)(c0 + c) * ldb + i] - s;
+            R[(i64)(c0 + c) * ldr + i] = r;
+            ra = fabs(r);
+            xa = fabs(X[(i64)(c0 + c) * ldx + i]);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v = __shfl_down_sync(0xffffffffu, ra, o);
+            const double w = __shfl_down_sync(0xffffffffu, xa, o);
+            if (v > ra || v != v) ra = v;
+            if (w > xa || w != w) xa = w;
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomic_max_nonneg(&st->rmax[c0 + c], ra);
+            atomic_max_nonneg(&st->xmax[c0 + c], xa);
+        }
+    }
+}
+
+// Convergence test after residual number `it`: converged when every RHS has
+// ||r||_inf <= tol (||A||_inf ||x||_inf + ||b||_inf).  Clears the running
+// maxima for the next residual.
+__global__ void k_ir_test(int nrhs, int it, double tol, MixState *st)
+{
+    if (st->stop != 0) return;
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < nrhs; j += blockDim.x) {
+        const double r = __longlong_as_double((long long)st->rmax[j]);
+        const double x = __longlong_as_double((long long)st->xmax[j]);
+        const double b = __longlong_as_double((long long)st->bmax[j]);
+        const double eta = r / (st->anorm * x + b);
+        if (!(eta <= tol)) atomicExch(&bad, 1);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nrhs; j += blockDim.x) { st->rmax[j] = 0; st->xmax[j] = 0; }
+    if (threadIdx.x == 0 && !bad) {
+        st->stop = 1;
+        st->conv = 1;
+        st->iters = it;
+    }
+}
+
+// D = (float)(R * scale) for the correction solve.
+__global__ void k_r_to_f32(i64 n, int nrhs, const double *R, i64 ldr, float *D, i64 ldd,
+                           const MixState *st, const int32_t *abort)
+{
+    if (abort && *abort != 0) return;
+    const double s = st->scale;
+    const i64 total = n * nrhs;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x) {
+        const i64 i = e % n, j = e / n;
+        D[j * ldd + i] = (float)(R[j * ldr + i] * s);
+    }
+}
+
+// X (+)= D widened; first = true assigns (x0 = solve(b)).
+__global__ void k_x_update(i64 n, int nrhs, const float *D, i64 ldd, double *X, i64 ldx, int first,
+                           const int32_t *abort)
+{
+    if (abort && *abort != 0) return;
+    const i64 total = n * nrhs;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x) {
+        const i64 i = e % n, j = e / n;
+        const double d = (double)D[j * ldd + i];
+        X[j * ldx + i] = first ? d : X[j * ldx + i] + d;
+    }
+}
+
+// Fallback: X := B (before the FP64 solve), and the final iteration count.
+__global__ void k_copy_b(i64 n, int nrhs, const double *B, i64 ldb, double *X, i64 ldx,
+                         const int32_t *abort)
+{
+    if (abort && *abort != 0) return;
+    const i64 total = n * nrhs;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x) {
+        const i64 i = e % n, j = e / n;
+        X[j * ldx + i] = B[j * ldb + i];
+    }
+}
+
+__global__ void k_mix_finish(const MixState *st, int maxiter, int32_t *iter_out)
+{
+    int v;
+    if (st->conv) v = st->iters;
+    else if (st->winfo == -2) v = -2;            // conversion overflow
+    else if (st->winfo != 0) v = -3;             // low-precision factorization failed
+    else v = -31;                                // no convergence within maxiter
+    (void)maxiter;
+    *iter_out = v;
+}
+
+unsigned grid_for(i64 total, unsigned threads)
+{
+    i64 g = (total + threads - 1) / threads;
+    if (g > 4096) g = 4096;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+}  // namespace
+
+// FP32 solve of W d = P r (LU) or L L^T d = r (Cholesky) on the nrhs columns
+// of D.
+static void lowprec_solve(Ctx &c, bool lu, i64 n, i64 nrhs, const float *W, i64 ldw,
+                          const int32_t *ipiv, float *D, i64 ldd)
+{
+    if (lu) {
+        laswp<float>(c, D, ldd, n, 0, nrhs, 0, n, ipiv);
+        trsm_lln<float>(c, true, n, nrhs, 1.0f, W, ldw, D, ldd);
+        trsm_lun<float>(c, n, nrhs, 1.0f, W, ldw, D, ldd);
+    } else {
+        trsm_lln<float>(c, false, n, nrhs, 1.0f, W, ldw, D, ldd);
+        trsm_llt<float>(c, n, nrhs, 1.0f, W, ldw, D, ldd);
+    }
+}
+
+size_t mixed_work_size(i64 n, i64 nrhs, bool lu, int prec) { return layout(n, nrhs, lu, prec).total; }
+
+int mixed_solve(Ctx &c, bool lu, i64 n, i64 nrhs, double *A, i64 lda, int32_t *ipiv, const double *B,
+                i64 ldb, double *X, i64 ldx, int prec, double tol, int maxiter, int32_t *iter)
+{
+    const MixLayout Ly = layout(n, nrhs, lu, prec);
+    char *w = static_cast<char *>(c.work);
+    float *W = reinterpret_cast<float *>(w + Ly.W);
+    void *pws = w + Ly.panel;
+    double *R = reinterpret_cast<double *>(w + Ly.R);
+    float *D = reinterpret_cast<float *>(w + Ly.D);
+    double *P = reinterpret_cast<double *>(w + Ly.P);
+    double *Nn = reinterpret_cast<double *>(w + Ly.N);
+    MixState *st = reinterpret_cast<MixState *>(w + Ly.S);
+    const i64 ldw = Ly.ldw, ldr = n, ldd = n;
+    int32_t *user_info = c.info;
+    const unsigned T256 = 256;
+
+    if (tol <= 0.0) tol = 1e-14;
+    if (maxiter < 0) maxiter = 0;
+
+    { Launch L(c, K_MIX, 0.0, 0.0); k_mix_init<<<1, 256, 0, c.s>>>(st, (int)nrhs); }
+    {
+        Launch L(c, K_MIX, 0.0, (double)n * n * sizeof(double));
+        k_rowsum_partial<<<dim3((unsigned)((n + 255) / 256), NORM_CH), 256, 0, c.s>>>(n, A, lda, Nn);
+    }
+    {
+        Launch L(c, K_MIX, 0.0, 0.0);
+        k_norms<<<1, 1024, 0, c.s>>>(n, Nn, A, lda, B, ldb, (int)nrhs, prec == RL_PREC_FP16S, st);
+    }
+    {
+        Launch L(c, K_CONVERT, 0.0, (double)n * n * (sizeof(double) + sizeof(float)));
+        k_to_f32<<<grid_for(n * n, T256), T256, 0, c.s>>>(n, n, A, lda, W, ldw, st, &st->winfo, nullptr);
+    }
+
+    // low-precision factorization of W (its info lands in st->winfo)
+    {
+        Ctx f = c;
+        f.info = &st->winfo;
+        f.abort = &st->winfo;
+        f.work = pws;
+        f.prec = prec;
+        f.tcwork = w + Ly.TC;
+        f.tclwork = Ly.tc_bytes;
+        if (lu) getrf_rec_t<float>(f, W, ldw, n, ipiv, 0, n, n);
+        else potrf_rec_t<float>(f, n, W, ldw, 0);
+        if (f.err != cudaSuccess && c.err == cudaSuccess) c.err = f.err;
+    }
+    { Launch L(c, K_MIX, 0.0, 0.0); k_after_factor<<<1, 1, 0, c.s>>>(st); }
+
+    Ctx r = c;            // refinement kernels skip once st->stop is set
+    r.abort = &st->stop;
+    r.info = nullptr;
+
+    // x0 = solve(W, b)
+    {
+        Launch L(r, K_CONVERT, 0.0, (double)n * nrhs * 12.0);
+        k_r_to_f32<<<grid_for(n * nrhs, T256), T256, 0, r.s>>>(n, (int)nrhs, B, ldb, D, ldd, st, r.abort);
+    }
+    lowprec_solve(r, lu, n, nrhs, W, ldw, ipiv, D, ldd);
+    {
+        Launch L(r, K_MIX, 0.0, 0.0);
+        k_x_update<<<grid_for(n * nrhs, T256), T256, 0, r.s>>>(n, (int)nrhs, D, ldd, X, ldx, 1, r.abort);
+    }
+    // the scale of the FP16 form is undone when D is widened: A_s = s A, so
+    // A^{-1} r = s (A_s)^{-1} r, and D = (A_s)^{-1} (s r) is already A^{-1} r.
+    for (int it = 0; it <= maxiter; ++it) {
+        for (i64 c0 = 0; c0 < nrhs; c0 += RES_NR) {
+            const int nr = (int)((nrhs - c0) < RES_NR ? (nrhs - c0) : RES_NR);
+            {
+                Launch L(r, K_RESID, 2.0 * n * n * nr, (double)n * n * sizeof(double));
+                k_resid_partial<<<dim3((unsigned)((n + RES_ROWS - 1) / RES_ROWS), (unsigned)Ly.nchunks),
+                                  RES_ROWS, 0, r.s>>>(n, nr, A, lda, X + c0 * ldx, ldx, P, r.abort);
+            }
+            {
+                Launch L(r, K_RESID, (double)n * nr * Ly.nchunks, 0.0);
+                k_resid_final<<<(unsigned)((n + 255) / 256), 256, 0, r.s>>>(
+                    n, nr, (int)c0, Ly.nchunks, P, B, ldb, X, ldx, R, ldr, st, r.abort);
+            }
+        }
+        { Launch L(r, K_MIX, 0.0, 0.0); k_ir_test<<<1, 256, 0, r.s>>>((int)nrhs, it, tol, st); }
+        if (it == maxiter) break;
+        {
+            Launch L(r, K_CONVERT, 0.0, (double)n * nrhs * 12.0);
+            k_r_to_f32<<<grid_for(n * nrhs, T256), T256, 0, r.s>>>(n, (int)nrhs, R, ldr, D, ldd, st, r.abort);
+        }
+        lowprec_solve(r, lu, n, nrhs, W, ldw, ipiv, D, ldd);
+        {
+            Launch L(r, K_MIX, 0.0, 0.0);
+            k_x_update<<<grid_for(n * nrhs, T256), T256, 0, r.s>>>(n, (int)nrhs, D, ldd, X, ldx, 0, r.abort);
+        }
+        if (r.err != cudaSuccess) break;
+    }
+    if (r.err != cudaSuccess && c.err == cudaSuccess) c.err = r.err;
+
+    // FP64 fallback (skipped when converged): factor A in place, X = A^{-1} B
+    {
+        Ctx f = c;
+        f.abort = &st->conv;
+        f.info = user_info;
+        f.work = pws;
+        {
+            Launch L(f, K_MIX, 0.0, 0.0);
+            k_copy_b<<<grid_for(n * nrhs, T256), T256, 0, f.s>>>(n, (int)nrhs, B, ldb, X, ldx, f.abort);
+        }
+        if (lu) {
+            getrf_rec_t<double>(f, A, lda, n, ipiv, 0, n, n);
+            laswp<double>(f, X, ldx, n, 0, nrhs, 0, n, ipiv);
+            trsm_lln<double>(f, true, n, nrhs, 1.0, A, lda, X, ldx);
+            trsm_lun<double>(f, n, nrhs, 1.0, A, lda, X, ldx);
+        } else {
+            potrf_rec_t<double>(f, n, A, lda, 0);
+            trsm_lln<double>(f, false, n, nrhs, 1.0, A, lda, X, ldx);
+            trsm_llt<double>(f, n, nrhs, 1.0, A, lda, X, ldx);
+        }
+        if (f.err != cudaSuccess && c.err == cudaSuccess) c.err = f.err;
+    }
+    { Launch L(c, K_MIX, 0.0, 0.0); k_mix_finish<<<1, 1, 0, c.s>>>(st, maxiter, iter); }
+    return 0;
+}
+
+}  // namespace rl

@@ -1,0 +1,461 @@
+// Tensor-core (tcgen05) GEMM for the FP32 working storage of the precision
+// form: C(m x n) = C + alpha * op(A) op(B), C in FP32, the products on the
+// 5th-generation tensor cores with FP32 accumulation in tensor memory.
+//
+// Operand precision (rl_prec): TF32 (one MMA), BF16 / FP16 (one MMA on
+// 16-bit copies), or 3xTF32 (a = a_hi + a_lo split, three MMAs
+// a_hi b_hi + a_hi b_lo + a_lo b_hi, close to FP32 accuracy).
+//
+// Structure (one CTA per 128 x 256 output tile, 192 threads):
+//   * op(A) and op(B) are first packed into K-major tiles (rows of K
+//     contiguous, zero padded) of the operand type by a bandwidth-bound pack
+//     kernel; this also transposes the column-major A block.
+//   * warp 0: one lane issues TMA loads (cp.async.bulk.tensor, 128-byte
+//     swizzle) of A and B k-slices into a 4-stage shared-memory ring, each
+//     stage guarded by a "full" and an "empty" mbarrier.
+//   * warp 1: allocates 256 TMEM columns; one lane issues tcgen05.mma
+//     (M = 128, N = 256, K = 32 bytes per instruction) and tcgen05.commit to
+//     release each stage and, at the end, to signal the epilogue.
+//   * warps 2-5: read the accumulator with tcgen05.ld (each warp its own
+//     32-lane quarter) and update C with coalesced stores.
+// Every mbarrier wait is bounded; a wait that runs out sets the error word
+// (RL_INFO_DEVICE_TIMEOUT) and the CTA drains its copies, frees TMEM and
+// returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include "internal.cuh"
+
+namespace rl {
+
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int KB = 128;                     // bytes of K per stage (one swizzle row)
+constexpr int THREADS = 192;
+constexpr int A_TILE = BM * KB;             // 16 KB
+constexpr int B_TILE = BN * KB;             // 32 KB
+constexpr int TMEM_COLS = 256;
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtime()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false if it ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit_ns)
+{
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = gtime();
+    while (!mbar_try(bar, parity)) {
+        if ((long long)(gtime() - t0) >= limit_ns) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(su32(dst)), "l"(map), "r"(su32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart, tile base 1024-byte aligned.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                    // leading byte offset (unused here)
+    d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
+    d |= (uint64_t)1 << 46;                    // descriptor version
+    d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: D = F32, A/B format fmt (0 F16, 1 BF16, 2 TF32),
+// both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc(uint32_t fmt, uint32_t M, uint32_t N)
+{
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+template <bool F16KIND>
+__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc)
+{
+    if (F16KIND)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(dtmem), "l"(a), "l"(b), "r"(id), "r"(acc));
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(dtmem), "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// NSPLIT operand planes per side (1, or 2 for the hi/lo split); NMMA MMAs per
+// k-chunk (1, or 3 for hi*hi + hi*lo + lo*hi).
+// FMT: operand format of the instruction descriptor (0 FP16, 1 BF16, 2 TF32).
+template <int FMT, int NSPLIT, int STAGES, bool LOWER>
+__global__ void __launch_bounds__(THREADS, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+          const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+          int m, int n, int nkb, float alpha, float *C, i64 ldc, int tiles_m, int32_t *err,
+          long long limit_ns, const int32_t *abort)
+{
+    constexpr bool F16KIND = FMT < 2;
+    if (abort && *abort != 0) return;
+    const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+    const int m0 = tm * BM, n0 = tn * BN;
+    // lower-triangle updates: a tile entirely above the diagonal has no work
+    if (LOWER && m0 + BM <= n0) return;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte alignment of the stage ring
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr int STAGE = NSPLIT * (A_TILE + B_TILE);
+    __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_err;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+        mbar_init(&done_bar, 1);
+        s_err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer
+            int issued = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % STAGES;
+                const uint32_t par = ((kb / STAGES) & 1) ^ 1;
+                if (!mbar_wait(&empty_bar[s], par, limit_ns)) { atomicExch(&s_err, 1); break; }
+                if (s_err) break;
+                unsigned char *st = base + s * STAGE;
+                mbar_expect_tx(&full_bar[s], STAGE);
+                // K coordinate in elements: 128 bytes per stage
+                const int kx = kb * (F16KIND ? 64 : 32);
+                tma_load_2d(st, &mA0, &full_bar[s], kx, m0);
+                tma_load_2d(st + A_TILE, &mB0, &full_bar[s], kx, n0);
+                if (NSPLIT == 2) {
+                    tma_load_2d(st + A_TILE + B_TILE, &mA1, &full_bar[s], kx, m0);
+                    tma_load_2d(st + 2 * A_TILE + B_TILE, &mB1, &full_bar[s], kx, n0);
+                }
+                ++issued;
+            }
+            // drain: every issued copy has landed before the CTA can exit
+            for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+                (void)mbar_wait(&full_bar[kb % STAGES], (kb / STAGES) & 1, limit_ns);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t ID = idesc((uint32_t)FMT, BM, BN);
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % STAGES;
+                if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1, limit_ns)) { atomicExch(&s_err, 1); break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa = su32(base + s * STAGE);
+                const uint32_t sb = sa + A_TILE;
+#pragma unroll
+                for (int kk = 0; kk < KB / 32; ++kk) {
+                    const uint32_t acc = (kb | kk) ? 1u : 0u;
+                    mma<F16KIND>(tmem, sdesc(sa + kk * 32), sdesc(sb + kk * 32), ID, acc);
+                    if (NSPLIT == 2) {
+                        const uint32_t sa1 = sa + A_TILE + B_TILE, sb1 = sa + 2 * A_TILE + B_TILE;
+                        mma<F16KIND>(tmem, sdesc(sa + kk * 32), sdesc(sb1 + kk * 32), ID, 1u);
+                        mma<F16KIND>(tmem, sdesc(sa1 + kk * 32), sdesc(sb + kk * 32), ID, 1u);
+                    }
+                }
+                mma_commit(&empty_bar[s]);
+            }
+            mma_commit(&done_bar);
+        }
+    } else {
+        // epilogue: warps 2..5 -> TMEM lane quarters (warp % 4)
+        const int q = warp & 3;
+        const int row = m0 + q * 32 + lane;
+        if (!mbar_wait(&done_bar, 0, limit_ns)) atomicExch(&s_err, 1);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!s_err && nkb > 0) {
+            for (int c = 0; c < BN; c += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+                if (row < m) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = n0 + c + j;
+                        if (col < n && (!LOWER || row >= col)) {
+                            float *cp = C + (i64)col * ldc + row;
+                            *cp = fmaf(alpha, v[j], *cp);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
+    if (threadIdx.x == 0 && s_err && err) atomicExch(err, RL_INFO_DEVICE_TIMEOUT);
+}
+
+// Pack op(X) (rows x kdim, X column-major with leading dimension ldx, op =
+// transpose when TR) into P[rows_p][kp] row-major, zero padded, converted to
+// the operand type.  SPLIT: plane 0 = hi (TF32-rounded), plane 1 = lo.
+template <typename OT, bool TR, int SPLIT>
+__global__ void k_pack(int rows, int kdim, const float *X, i64 ldx, OT *P, int rows_p, int kp, i64 plane)
+{
+    __shared__ float tile[32][33];
+    const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    // load a 32 x 32 block of op(X): element (r, k)
+    for (int yy = ty; yy < 32; yy += 8) {
+        int r, k;
+        float v = 0.0f;
+        if (!TR) {            // op(X)(r,k) = X[k*ldx + r], coalesced along r
+            r = r0 + tx; k = k0 + yy;
+            if (r < rows && k < kdim) v = X[(i64)k * ldx + r];
+            tile[yy][tx] = v;                 // tile[k][r]
+        } else {              // op(X)(r,k) = X[r*ldx + k], coalesced along k
+            r = r0 + yy; k = k0 + tx;
+            if (r < rows && k < kdim) v = X[(i64)r * ldx + k];
+            tile[tx][yy] = v;                 // tile[k][r]
+        }
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int r = r0 + yy, k = k0 + tx;
+        if (r >= rows_p || k >= kp) continue;
+        const float v = tile[tx][yy];
+        const i64 o = (i64)r * kp + k;
+        if (SPLIT == 2) {
+            uint32_t hb;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v));
+            const float hi = __uint_as_float(hb);
+            P[o] = (OT)hi;
+            P[plane + o] = (OT)(v - hi);
+        } else if (sizeof(OT) == 4) {
+            uint32_t hb;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v));
+            P[o] = (OT)__uint_as_float(hb);
+        } else {
+            P[o] = (OT)v;
+        }
+    }
+}
+
+}  // namespace tc
+
+// ---- host side ----------------------------------------------------------------
+
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D map over a row-major [rows][kp] operand plane, box = one stage tile.
+static bool make_map(CUtensorMap *map, const void *base, bool f16, int rows, int kp, int box_rows)
+{
+    auto enc = tmap_encoder();
+    if (!enc) return false;
+    const int esz = f16 ? 2 : 4;
+    cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kp * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(tc::KB / esz), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    // the copy moves bytes; a 16-bit map serves both BF16 and FP16 planes
+    CUresult r = enc(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                     const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+static inline i64 rup(i64 v, i64 q) { return (v + q - 1) / q * q; }
+
+size_t tc_work_bytes(i64 m, i64 n, i64 k, int prec)
+{
+    if (prec == RL_PREC_FP32) return 0;
+    const bool f16 = (prec == RL_PREC_BF16 || prec == RL_PREC_FP16S);
+    const int esz = f16 ? 2 : 4, split = (prec == RL_PREC_TF32X3) ? 2 : 1;
+    const i64 kp = rup(k > 0 ? k : 1, tc::KB / esz);
+    const i64 mp = rup(m > 0 ? m : 1, tc::BM), np = rup(n > 0 ? n : 1, tc::BN);
+    return (size_t)split * ((size_t)mp + (size_t)np) * (size_t)kp * esz + 2048;
+}
+
+template <int FMT, int NSPLIT, int STAGES, bool LOWER>
+static cudaError_t launch_tc(const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
+                             const CUtensorMap &b1, int m, int n, int nkb, float alpha, float *C, i64 ldc,
+                             int tiles_m, unsigned grid, int32_t *err, long long lim, const int32_t *abort,
+                             cudaStream_t s)
+{
+    auto kern = tc::k_tc_gemm<FMT, NSPLIT, STAGES, LOWER>;
+    const int smem = STAGES * NSPLIT * (tc::A_TILE + tc::B_TILE) + 1024;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    kern<<<grid, tc::THREADS, smem, s>>>(a0, a1, b0, b1, m, n, nkb, alpha, C, ldc, tiles_m, err, lim, abort);
+    return cudaGetLastError();
+}
+
+// C(m x n) += alpha op(A) op(B) on the tensor cores; lower: square C, only
+// tiles on or below the diagonal and only elements i >= j are written.
+// Returns false when the operation cannot run here (caller falls back).
+bool tc_gemm(Ctx &c, int prec, bool ta, bool tb, i64 m, i64 n, i64 k, float alpha, const float *A,
+             i64 lda, const float *B, i64 ldb, float *C, i64 ldc, bool lower, void *work, size_t lwork)
+{
+    if (prec == RL_PREC_FP32 || m <= 0 || n <= 0 || k <= 0) return false;
+    if (m > INT32_MAX / 2 || n > INT32_MAX / 2 || k > INT32_MAX / 2) return false;
+    const bool f16 = (prec == RL_PREC_BF16 || prec == RL_PREC_FP16S);
+    const int esz = f16 ? 2 : 4, split = (prec == RL_PREC_TF32X3) ? 2 : 1;
+    const i64 kp = rup(k, tc::KB / esz);
+    const i64 mp = rup(m, tc::BM), np = rup(n, tc::BN);
+    if (lwork < tc_work_bytes(m, n, k, prec) || work == nullptr) return false;
+    char *w = reinterpret_cast<char *>(((uintptr_t)work + 1023) & ~(uintptr_t)1023);
+    const i64 aplane = mp * kp, bplane = np * kp;
+    char *Ap = w;
+    char *Bp = w + (size_t)split * aplane * esz;
+
+    // pack op(A) -> [mp][kp], op(B)^T -> [np][kp] (B's rows are op(B)'s columns)
+    {
+        dim3 g((unsigned)(kp / 32 + (kp % 32 ? 1 : 0)), (unsigned)(mp / 32));
+        dim3 gb((unsigned)(kp / 32 + (kp % 32 ? 1 : 0)), (unsigned)(np / 32));
+        Launch L(c, K_CONVERT, 0.0, (double)(m + n) * k * (4 + esz * split));
+        if (prec == RL_PREC_BF16) {
+            if (!ta) tc::k_pack<__nv_bfloat16, false, 1><<<g, 256, 0, c.s>>>((int)m, (int)k, A, lda, (__nv_bfloat16 *)Ap, (int)mp, (int)kp, 0);
+            else tc::k_pack<__nv_bfloat16, true, 1><<<g, 256, 0, c.s>>>((int)m, (int)k, A, lda, (__nv_bfloat16 *)Ap, (int)mp, (int)kp, 0);
+            if (!tb) tc::k_pack<__nv_bfloat16, true, 1><<<gb, 256, 0, c.s>>>((int)n, (int)k, B, ldb, (__nv_bfloat16 *)Bp, (int)np, (int)kp, 0);
+            else tc::k_pack<__nv_bfloat16, false, 1><<<gb, 256, 0, c.s>>>((int)n, (int)k, B, ldb, (__nv_bfloat16 *)Bp, (int)np, (int)kp, 0);
+        } else if (prec == RL_PREC_FP16S) {
+            if (!ta) tc::k_pack<__half, false, 1><<<g, 256, 0, c.s>>>((int)m, (int)k, A, lda, (__half *)Ap, (int)mp, (int)kp, 0);
+            else tc::k_pack<__half, true, 1><<<g, 256, 0, c.s>>>((int)m, (int)k, A, lda, (__half *)Ap, (int)mp, (int)kp, 0);
+            if (!tb) tc::k_pack<__half, true, 1><<<gb, 256, 0, c.s>>>((int)n, (int)k, B, ldb, (__half *)Bp, (int)np, (int)kp, 0);
+            else tc::k_pack<__half, false, 1><<<gb, 256, 0, c.s>>>((int)n, (int)k, B, ldb, (__half *)Bp, (int)np, (int)kp, 0);
+        } else if (split == 2) {
+            if (!ta) tc::k_pack<float, false, 2><<<g, 256, 0, c.s>>>((int)m, (int)k, A, lda, (float *)Ap, (int)mp, (int)kp, aplane);
+            else tc::k_pack<float, true, 2><<<g, 256, 0, c.s>>>((int)m, (int)k, A, lda, (float *)Ap, (int)mp, (int)kp, aplane);
+            if (!tb) tc::k_pack<float, true, 2><<<gb, 256, 0, c.s>>>((int)n, (int)k, B, ldb, (float *)Bp, (int)np, (int)kp, bplane);
+            else tc::k_pack<float, false, 2><<<gb, 256, 0, c.s>>>((int)n, (int)k, B, ldb, (float *)Bp, (int)np, (int)kp, bplane);
+        } else {
+            if (!ta) tc::k_pack<float, false, 1><<<g, 256, 0, c.s>>>((int)m, (int)k, A, lda, (float *)Ap, (int)mp, (int)kp, 0);
+            else tc::k_pack<float, true, 1><<<g, 256, 0, c.s>>>((int)m, (int)k, A, lda, (float *)Ap, (int)mp, (int)kp, 0);
+            if (!tb) tc::k_pack<float, true, 1><<<gb, 256, 0, c.s>>>((int)n, (int)k, B, ldb, (float *)Bp, (int)np, (int)kp, 0);
+            else tc::k_pack<float, false, 1><<<gb, 256, 0, c.s>>>((int)n, (int)k, B, ldb, (float *)Bp, (int)np, (int)kp, 0);
+        }
+    }
+    CUtensorMap a0, a1, b0, b1;
+    bool ok = make_map(&a0, Ap, f16, (int)mp, (int)kp, tc::BM) && make_map(&b0, Bp, f16, (int)np, (int)kp, tc::BN);
+    if (split == 2)
+        ok = ok && make_map(&a1, Ap + (size_t)aplane * esz, f16, (int)mp, (int)kp, tc::BM) &&
+             make_map(&b1, Bp + (size_t)bplane * esz, f16, (int)np, (int)kp, tc::BN);
+    else {
+        a1 = a0;
+        b1 = b0;
+    }
+    if (!ok) { note(c, cudaErrorInvalidValue); return true; }
+    const int nkb = (int)(kp / (tc::KB / esz));
+    const int tiles_m = (int)(mp / tc::BM), tiles_n = (int)(np / tc::BN);
+    // lower-triangle updates launch the full tile grid; tiles entirely above
+    // the diagonal return at once and diagonal tiles mask their stores
+    const unsigned grid = (unsigned)(tiles_m * tiles_n);
+    const double flops = lower ? (double)k * n * (n + 1) : 2.0 * m * n * k;
+    Launch L(c, lower ? K_SYRK : K_GEMM, flops, 0.0);
+    cudaError_t e;
+    const long long lim = g_params.spin_ns;
+#define RL_TC(FMT, NS, ST)                                                                                    \
+    (lower ? launch_tc<FMT, NS, ST, true>(a0, a1, b0, b1, (int)m, (int)n, nkb, alpha, C, ldc, tiles_m, grid,  \
+                                          c.info, lim, c.abort, c.s)                                        \
+           : launch_tc<FMT, NS, ST, false>(a0, a1, b0, b1, (int)m, (int)n, nkb, alpha, C, ldc, tiles_m, grid, \
+                                           c.info, lim, c.abort, c.s))
+    if (prec == RL_PREC_FP16S) e = RL_TC(0, 1, 4);
+    else if (prec == RL_PREC_BF16) e = RL_TC(1, 1, 4);
+    else if (split == 2) e = RL_TC(2, 2, 2);
+    else e = RL_TC(2, 1, 4);
+#undef RL_TC
+    note(c, e);
+    return true;
+}
+
+}  // namespace rl

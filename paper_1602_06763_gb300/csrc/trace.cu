@@ -29,8 +29,9 @@ std::vector<Rec> g_pending;
 std::vector<cudaEvent_t> g_pool;
 Totals g_tot[K_COUNT];
 
-const char *kKindNames[K_COUNT] = {"dgemm", "dsyrk", "dtrsm_base", "dtrmm_base", "dpotf2",
-                                   "dtrti2", "dlauu2", "diag_scan", "dgetf2_panel", "dlaswp"};
+const char *kKindNames[K_COUNT] = {"gemm", "syrk", "trsm_base", "trmm_base", "potf2",
+                                   "trti2", "lauu2", "diag_scan", "getf2_panel", "laswp",
+                                   "fp64_residual", "convert", "refine_control"};
 
 cudaEvent_t take_event()
 {

@@ -49,6 +49,17 @@ _SIGS = {
                                 _i64, _vp]),
     "rl_dtrmm": (ctypes.c_int, [_ch, _ch, _ch, _ch, _i64, _i64, ctypes.c_double, _vp, _i64, _vp,
                                 _i64, _vp]),
+    "rl_dgetrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp]),
+    "rl_dpotrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _i64, _vp]),
+    "rl_dsgesv_work_size": (_sz, [_i64, _i64, ctypes.c_int]),
+    "rl_dsposv_work_size": (_sz, [_i64, _i64, ctypes.c_int]),
+    "rl_dsgesv": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, ctypes.c_int,
+                                 ctypes.c_double, ctypes.c_int, _vp, _vp, _vp, _sz, _vp]),
+    "rl_dsposv": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, ctypes.c_int,
+                                 ctypes.c_double, ctypes.c_int, _vp, _vp, _vp, _sz, _vp]),
+    "rl_sgemm_tc_work_size": (_sz, [_i64, _i64, _i64, ctypes.c_int]),
+    "rl_sgemm_tc": (ctypes.c_int, [ctypes.c_int, _ch, _ch, _i64, _i64, _i64, ctypes.c_float, _vp, _i64,
+                                   _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
     "rl_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "rl_trace_kinds": (ctypes.c_int, []),
     "rl_trace_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
@@ -69,6 +80,12 @@ RL_ERR_UNSUPPORTED = 3
 RL_ERR_NULL_POINTER = 4
 RL_ERR_PARAM = 5
 RL_INFO_DEVICE_TIMEOUT = -1000
+
+RL_PREC_FP32 = 0
+RL_PREC_TF32 = 1
+RL_PREC_BF16 = 2
+RL_PREC_FP16S = 3
+RL_PREC_TF32X3 = 4
 
 RL_PARAM_POTRF_CROSSOVER = 1
 RL_PARAM_GETRF_PANEL = 2
@@ -141,6 +158,44 @@ def rl_dtrsm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream=None)
 def rl_dtrmm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream=None):
     return _lib.rl_dtrmm(_c(side), _c(uplo), _c(transa), _c(diag), m, n, alpha, _ptr(A), lda,
                          _ptr(B), ldb, _stream(stream))
+
+
+def rl_dgetrs(trans, n, nrhs, A, lda, ipiv, B, ldb, stream=None):
+    return _lib.rl_dgetrs(_c(trans), n, nrhs, _ptr(A), lda, _ptr(ipiv), _ptr(B), ldb, _stream(stream))
+
+
+def rl_dpotrs(uplo, n, nrhs, A, lda, B, ldb, stream=None):
+    return _lib.rl_dpotrs(_c(uplo), n, nrhs, _ptr(A), lda, _ptr(B), ldb, _stream(stream))
+
+
+def rl_dsgesv_work_size(n, nrhs, prec):
+    return int(_lib.rl_dsgesv_work_size(n, nrhs, prec))
+
+
+def rl_dsposv_work_size(n, nrhs, prec):
+    return int(_lib.rl_dsposv_work_size(n, nrhs, prec))
+
+
+def rl_dsgesv(n, nrhs, A, lda, ipiv, B, ldb, X, ldx, prec, tol, maxiter, iter_, info, work, lwork,
+              stream=None):
+    return _lib.rl_dsgesv(n, nrhs, _ptr(A), lda, _ptr(ipiv), _ptr(B), ldb, _ptr(X), ldx, prec, tol,
+                          maxiter, _ptr(iter_), _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_dsposv(uplo, n, nrhs, A, lda, B, ldb, X, ldx, prec, tol, maxiter, iter_, info, work, lwork,
+              stream=None):
+    return _lib.rl_dsposv(_c(uplo), n, nrhs, _ptr(A), lda, _ptr(B), ldb, _ptr(X), ldx, prec, tol,
+                          maxiter, _ptr(iter_), _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_sgemm_tc_work_size(m, n, k, prec):
+    return int(_lib.rl_sgemm_tc_work_size(m, n, k, prec))
+
+
+def rl_sgemm_tc(prec, transa, transb, m, n, k, alpha, A, lda, B, ldb, C, ldc, work, lwork,
+                stream=None):
+    return _lib.rl_sgemm_tc(prec, _c(transa), _c(transb), m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb,
+                            _ptr(C), ldc, _ptr(work), lwork, _stream(stream))
 
 
 def rl_host_work_size(routine, m, n, lda):
