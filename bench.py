@@ -211,6 +211,91 @@ def run_reference(args, rank):
 
 
 # ----------------------------------------------------------------------------
+# precision form: low-precision factorization + FP64 refinement vs FP64 solve
+# ----------------------------------------------------------------------------
+
+PRECS = {"fp32": 0, "tf32": 1, "bf16": 2, "fp16s": 3, "tf32x3": 4}
+
+
+def mixed_section(n, nrhs, cond, precs, dev, sp):
+    """Solve A X = B (A = U diag(sigma) V^T or Q diag(sigma) Q^T, sigma
+    log-spaced 1..cond, 64 Householder reflectors each side; B iid N(0,1))
+    with the FP64 path (getrf+getrs / potrf+potrs) and with rl_dsgesv /
+    rl_dsposv in each precision; reports time, the normwise backward error
+    of the returned X (computed in FP64), refinement iterations, and the
+    speedup over the FP64 path."""
+    import torch
+    from paper_1602_06763_gb300 import relgpu as r, inputs
+
+    def eta_of(A0, X, B, anorm):
+        # column-major A X is (X_t @ A0)^T with the row-major tensors used here
+        R = B - X @ A0
+        return float(torch.max(R.abs().amax(dim=1) / (anorm * X.abs().amax(dim=1) + B.abs().amax(dim=1))))
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    out = {"n": n, "nrhs": nrhs, "cond": cond, "tol": 1e-14, "reflectors": 64}
+    for kind in ("general", "spd"):
+        spd = kind == "spd"
+        A0 = inputs.spectrum_device(n, cond, inputs.seed_for(2, 30 + int(spd)), spd=spd, device=dev)
+        g = torch.Generator(device=dev)
+        g.manual_seed(inputs.seed_for(2, 40 + int(spd)))
+        B = torch.randn(nrhs, n, generator=g, device=dev, dtype=torch.float64)
+        anorm = float(A0.abs().sum(dim=0).max())
+        info = torch.zeros(2, dtype=torch.int32, device=dev)
+        ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+        lw = r.rl_dgetrf_work_size(n, n)
+        wk = torch.empty(lw, dtype=torch.uint8, device=dev)
+        res = {}
+        # FP64 path (one warm-up, then timed)
+        for rep in range(2):
+            A = A0.clone()
+            X = B.clone()
+            if spd:
+                ms = timed(lambda: (r.check(r.rl_dpotrf("L", n, A, n, info, None, 0, sp)),
+                                    r.check(r.rl_dpotrs("L", n, nrhs, A, n, X, n, sp))))
+            else:
+                ms = timed(lambda: (r.check(r.rl_dgetrf(n, n, A, n, ipiv, info, wk, lw, sp)),
+                                    r.check(r.rl_dgetrs("N", n, nrhs, A, n, ipiv, X, n, sp))))
+        res["fp64"] = {"ms": ms, "eta": eta_of(A0, X, B, anorm)}
+        del A
+        for name in precs:
+            prec = PRECS[name]
+            lwm = (r.rl_dsposv_work_size if spd else r.rl_dsgesv_work_size)(n, nrhs, prec)
+            wm = torch.empty(lwm, dtype=torch.uint8, device=dev)
+            it = torch.zeros(1, dtype=torch.int32, device=dev)
+            for rep in range(2):
+                A = A0.clone()
+                X = torch.zeros_like(B)
+                if spd:
+                    ms = timed(lambda: r.check(r.rl_dsposv("L", n, nrhs, A, n, B, n, X, n, prec, 1e-14, 30, it,
+                                                           info, wm, lwm, sp)))
+                else:
+                    ms = timed(lambda: r.check(r.rl_dsgesv(n, nrhs, A, n, ipiv, B, n, X, n, prec, 1e-14, 30, it,
+                                                           info, wm, lwm, sp)))
+            iters = int(it.item())
+            e = eta_of(A0, X, B, anorm)
+            res[name] = {"ms": ms, "eta": e, "iters": iters, "converged": iters >= 0,
+                         "speedup_vs_fp64": res["fp64"]["ms"] / ms}
+            del A, wm
+        best = [k for k in precs if res[k]["converged"] and res[k]["eta"] <= 1e-14]
+        res["best"] = max(best, key=lambda k: res[k]["speedup_vs_fp64"]) if best else None
+        res["speedup_at_equal_error"] = res[res["best"]]["speedup_vs_fp64"] if best else None
+        out[kind] = res
+        del A0
+        torch.cuda.empty_cache()
+    return out
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 
@@ -342,6 +427,13 @@ def run_gpu(args, rank, world, local_rank):
     if rank != 0:
         return 0
 
+    mixed = None
+    if args.mixed_n > 0:
+        del spd0, gen0
+        torch.cuda.empty_cache()
+        mixed = mixed_section(args.mixed_n, args.mixed_nrhs, args.mixed_cond,
+                              [p for p in args.mixed_precs.split(",") if p], dev, sp)
+
     cpu = None
     if world == 1 and args.cpu_n > 0:
         from oracle import build as obuild
@@ -368,6 +460,7 @@ def run_gpu(args, rank, world, local_rank):
                         "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["bytes"] else None}
                     for k, v in trace.items()},
         "gpu_launches": launches,
+        "mixed_solve": mixed,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clocks,
@@ -388,6 +481,11 @@ def main():
     ap.add_argument("--ref-n", type=int, default=2048,
                     help="order of the oracle's sample per step in the reference arm")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--mixed-n", type=int, default=16384,
+                    help="order of the precision-form comparison (0 skips it)")
+    ap.add_argument("--mixed-nrhs", type=int, default=16)
+    ap.add_argument("--mixed-cond", type=float, default=1e6)
+    ap.add_argument("--mixed-precs", default="fp32,tf32x3,tf32,bf16,fp16s")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

@@ -155,14 +155,17 @@ int rl_dpotrs(char uplo, int64_t n, int64_t nrhs, const double *A, int64_t lda, 
  * Updates smaller than 128 x 128 x 64 stay on the SIMT FP32 path.
  * A copy of A is converted to FP32 in `work` and factored; x0 = solve(b);
  * then r = b - A x in FP64 and x += solve(r) until, for every column,
- * ||r||_inf <= tol (||A||_inf ||x||_inf + ||b||_inf) (tol <= 0 means 1e-14)
- * or maxiter corrections were applied.  Without convergence, or when the
+ * ||r||_inf <= tol (||A||_inf ||x||_inf + ||b||_inf) (tol <= 0 means 1e-14),
+ * or maxiter corrections were applied, or a correction reduced the largest
+ * backward error by less than 10 %.  Without convergence, or when the
  * FP32 factorization fails, A is factored in FP64 in place (A then holds the
  * FP64 factors, and ipiv their pivots) and X = A^{-1} B.
  * Outputs (device, asynchronous): X (n x nrhs, ldx), ipiv (LU), *iter:
  *   >= 0  corrections applied before convergence (A unchanged)
  *   -2    an entry of A overflows FP32; -3 the FP32 factorization failed;
- *   -31   no convergence within maxiter (the FP64 fallback was used)
+ *   -31   no convergence within maxiter, or a correction that reduced the
+ *         largest backward error by less than 10 % (the FP64 fallback was
+ *         used)
  * and *info: LAPACK's info of the FP64 fallback factorization (0 otherwise).
  * nrhs <= 512.  Workspace: rl_dsgesv_work_size / rl_dsposv_work_size bytes.
  * Argument numbers (dsgesv): 1 n, 2 nrhs, 3 A, 4 lda, 5 ipiv, 6 B, 7 ldb,

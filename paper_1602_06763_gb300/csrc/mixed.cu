@@ -33,6 +33,7 @@ inline size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 struct MixState {
     double anorm;          // ||A||_inf
     double scale;          // power of two applied to A in the working copy
+    double prev_eta;       // backward error after the previous correction
     int32_t winfo;         // low-precision factorization info (or overflow)
     int32_t stop;          // nonzero: refinement finished or abandoned
     int32_t conv;          // 1: converged (fallback kernels skip)
@@ -85,6 +86,7 @@ __global__ void k_mix_init(MixState *st, int nrhs)
     if (t == 0) {
         st->anorm = 0.0;
         st->scale = 1.0;
+        st->prev_eta = 0.0;
         st->winfo = 0;
         st->stop = 0;
         st->conv = 0;
@@ -235,13 +237,17 @@ __global__ void k_resid_final(i64 n, int nr, int c0, i64 nchunks, const double *
 }
 
 // Convergence test after residual number `it`: converged when every RHS has
-// ||r||_inf <= tol (||A||_inf ||x||_inf + ||b||_inf).  Clears the running
-// maxima for the next residual.
+// ||r||_inf <= tol (||A||_inf ||x||_inf + ||b||_inf).  The refinement is
+// abandoned (fallback) once a correction fails to reduce the largest
+// backward error by 10 %: the contraction factor of the low-precision
+// factors (about kappa * u) is then near or above 1 and more iterations
+// would not reach tol.  Clears the running maxima for the next residual.
 __global__ void k_ir_test(int nrhs, int it, double tol, MixState *st)
 {
     if (st->stop != 0) return;
     __shared__ int bad;
-    if (threadIdx.x == 0) bad = 0;
+    __shared__ unsigned long long worst;
+    if (threadIdx.x == 0) { bad = 0; worst = 0; }
     __syncthreads();
     for (int j = threadIdx.x; j < nrhs; j += blockDim.x) {
         const double r = __longlong_as_double((long long)st->rmax[j]);
@@ -249,13 +255,20 @@ __global__ void k_ir_test(int nrhs, int it, double tol, MixState *st)
         const double b = __longlong_as_double((long long)st->bmax[j]);
         const double eta = r / (st->anorm * x + b);
         if (!(eta <= tol)) atomicExch(&bad, 1);
+        atomicMax(&worst, (unsigned long long)__double_as_longlong(eta == eta ? eta : INFINITY));
     }
     __syncthreads();
     for (int j = threadIdx.x; j < nrhs; j += blockDim.x) { st->rmax[j] = 0; st->xmax[j] = 0; }
-    if (threadIdx.x == 0 && !bad) {
-        st->stop = 1;
-        st->conv = 1;
-        st->iters = it;
+    if (threadIdx.x == 0) {
+        const double eta = __longlong_as_double((long long)worst);
+        if (!bad) {
+            st->stop = 1;
+            st->conv = 1;
+            st->iters = it;
+        } else if (it >= 1 && !(eta <= 0.9 * st->prev_eta)) {
+            st->stop = 1;                      // stagnation: leave for the FP64 fallback
+        }
+        st->prev_eta = eta;
     }
 }
 

@@ -209,6 +209,36 @@ def uniform_device(m: int, n: int, seed: int, device="cuda"):
     return (torch.rand(n, m, generator=g, device=device, dtype=torch.float64) * 2.0 - 1.0).contiguous()
 
 
+def spectrum_device(n: int, cond: float, seed: int, spd: bool, reflectors=64, device="cuda"):
+    """Large-n form of spd_spectrum / general_spectrum generated on the GPU
+    with torch in FP64 (input generation only): diag(sigma), sigma
+    log-spaced 1..cond, multiplied from the left by `reflectors` random
+    Householder reflectors and from the right by the same (SPD) or an
+    independent set (general).  Returns an n x n float64 tensor read as a
+    column-major matrix."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    den = max(n - 1, 1)
+    sig = torch.pow(torch.tensor(float(cond), dtype=torch.float64, device=device),
+                    torch.arange(n, device=device, dtype=torch.float64) / den)
+    A = torch.diag(sig)
+    VL = torch.randn(reflectors, n, generator=g, device=device, dtype=torch.float64)
+    VR = VL if spd else torch.randn(reflectors, n, generator=g, device=device, dtype=torch.float64)
+    for i in range(reflectors):
+        v = VL[i]
+        w = v @ A                                    # v^T A
+        A.addr_(v, w, alpha=-2.0 / float(v @ v))     # (I - 2 v v^T / v^T v) A
+    for i in range(reflectors):
+        v = VR[i]
+        w = A @ v                                    # A v
+        A.addr_(w, v, alpha=-2.0 / float(v @ v))     # A (I - 2 v v^T / v^T v)
+    if spd:
+        L = torch.tril(A)
+        A = L + torch.tril(A, -1).T
+    return A.contiguous()
+
+
 def bucket_sizes(count: int, lo: int, hi: int, seed: int):
     """Matrix orders drawn uniformly from lo..hi inclusive (batched form)."""
     return rng(seed).integers(lo, hi + 1, size=count).astype(np.int64)

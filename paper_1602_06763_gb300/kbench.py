@@ -23,7 +23,9 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", required=True,
-                    choices=["dgemm", "dsyrk", "dtrsm", "potrf", "getrf", "trtri", "lauum", "panel"])
+                    choices=["dgemm", "dsyrk", "dtrsm", "potrf", "getrf", "trtri", "lauum", "panel",
+                             "sgemm_tc"])
+    ap.add_argument("--prec", type=int, default=1, help="sgemm_tc operand precision (rl_prec)")
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--m", type=int, default=0, help="rows (panel case); default n")
     ap.add_argument("--k", type=int, default=0, help="inner dimension (dgemm/dsyrk); default n")
@@ -48,7 +50,16 @@ def main():
     s = torch.cuda.current_stream().cuda_stream
     info = torch.zeros(1, dtype=torch.int32, device=dev)
 
-    if a.case in ("dgemm", "dsyrk"):
+    if a.case == "sgemm_tc":
+        A = torch.rand(k, n, generator=g, device=dev, dtype=torch.float32)
+        B = torch.rand(n, k, generator=g, device=dev, dtype=torch.float32)
+        C = torch.rand(n, n, generator=g, device=dev, dtype=torch.float32)
+        flops = 2.0 * n * n * k
+        lw = r.rl_sgemm_tc_work_size(n, n, k, a.prec)
+        work = torch.empty(lw, dtype=torch.uint8, device=dev)
+        run = lambda: r.check(r.rl_sgemm_tc(a.prec, "N", "N", n, n, k, -1.0, A, n, B, k, C, n, work, lw, s))
+        restore = lambda: None
+    elif a.case in ("dgemm", "dsyrk"):
         A = torch.rand(k, n, generator=g, device=dev, dtype=torch.float64)
         B = torch.rand(n, k, generator=g, device=dev, dtype=torch.float64)
         C = torch.rand(n, n, generator=g, device=dev, dtype=torch.float64)
@@ -96,7 +107,7 @@ def main():
             lw = r.rl_dgetrf_work_size(rows, cols)
             work = torch.empty(lw, dtype=torch.uint8, device=dev)
             mn = min(rows, cols)
-            flops = rows * cols * mn - (rows + cols) * mn * mn / 2.0 + mn ** 3 / 3.0
+            flops = max(rows, cols) * mn * mn - mn ** 3 / 3.0   # LU of m x n, leading terms
             run = lambda: r.check(r.rl_dgetrf(rows, cols, A, rows, ipiv, info, work, lw, s))
 
     for _ in range(a.warmup):
