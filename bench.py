@@ -296,6 +296,117 @@ def mixed_section(n, nrhs, cond, precs, dev, sp):
 
 
 # ----------------------------------------------------------------------------
+# batching form: one persistent launch vs one call per matrix
+# ----------------------------------------------------------------------------
+
+def batched_section(count, baseline_count, dev, sp):
+    """count SPD (B B^T + n I) and count general (Uniform(-1,1)) matrices,
+    orders uniform in 8..256, packed 256-byte aligned; FP64 and FP32.  Times
+    one rl_*_vbatched launch against one single-matrix rl_dpotrf / rl_dgetrf
+    call per matrix (on the first baseline_count matrices, per-matrix time
+    reported and scaled to the batch)."""
+    import numpy as np
+    import torch
+    from paper_1602_06763_gb300 import relgpu as r, inputs
+
+    sizes = inputs.bucket_sizes(count, 8, 256, inputs.seed_for(3, 0))
+    out = {"count": int(count), "orders": "uniform 8..256", "sum_n3": float(np.sum(sizes.astype(np.float64) ** 3))}
+
+    def timed(fn, reps=3, before=None):
+        ts = []
+        for _ in range(reps):
+            if before:
+                before()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    for kind in ("potrf", "getrf"):
+        for prec in ("f64", "f32"):
+            dt = torch.float64 if prec == "f64" else torch.float32
+            esz = 8 if prec == "f64" else 4
+            align = 256 // esz
+            offs, off = [], 0
+            for n in sizes:
+                offs.append(off)
+                off += ((int(n) * int(n) + align - 1) // align) * align
+            pristine = torch.empty(off, dtype=dt, device=dev)
+            g = torch.Generator(device=dev)
+            g.manual_seed(inputs.seed_for(3, 10 + (kind == "getrf")))
+            for n in np.unique(sizes):
+                idx = np.nonzero(sizes == n)[0]
+                n = int(n)
+                if kind == "potrf":
+                    Bm = torch.randn(len(idx), n, n, generator=g, device=dev, dtype=torch.float64)
+                    M = torch.bmm(Bm, Bm.transpose(1, 2))
+                    M = torch.tril(M) + torch.tril(M, -1).transpose(1, 2)
+                    M.diagonal(dim1=1, dim2=2).add_(float(n))
+                else:
+                    M = torch.rand(len(idx), n, n, generator=g, device=dev, dtype=torch.float64) * 2 - 1
+                M = M.to(dt)
+                for q, b in enumerate(idx):
+                    pristine[offs[b]:offs[b] + n * n].copy_(M[q].reshape(-1))
+            work_buf = pristine.clone()
+            base = work_buf.data_ptr()
+            ptrs = torch.tensor([base + o * esz for o in offs], dtype=torch.int64, device=dev)
+            nvec = torch.tensor(sizes, dtype=torch.int32, device=dev)
+            info = torch.zeros(count, dtype=torch.int32, device=dev)
+            pstore = torch.zeros(int(np.sum(sizes)), dtype=torch.int32, device=dev)
+            pofs = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+            pptrs = torch.tensor([pstore.data_ptr() + 4 * int(q) for q in pofs], dtype=torch.int64, device=dev)
+            lw = r.rl_getrf_vbatched_work_size(count)
+            wk = torch.empty(lw, dtype=torch.uint8, device=dev)
+            restore = lambda: work_buf.copy_(pristine)
+            if kind == "potrf":
+                fn = r.rl_dpotrf_vbatched if prec == "f64" else r.rl_spotrf_vbatched
+                run = lambda: r.check(fn("L", count, nvec, ptrs, nvec, info, 256, wk, lw, sp))
+                flops = float(np.sum(sizes.astype(np.float64) ** 3)) / 3.0
+            else:
+                fn = r.rl_dgetrf_vbatched if prec == "f64" else r.rl_sgetrf_vbatched
+                run = lambda: r.check(fn(count, nvec, ptrs, nvec, pptrs, info, 256, wk, lw, sp))
+                flops = 2.0 * float(np.sum(sizes.astype(np.float64) ** 3)) / 3.0
+            restore()
+            run()
+            torch.cuda.synchronize()
+            bad = int((info != 0).sum().item())
+            ms = timed(run, reps=3, before=restore)
+            res = {"ms": ms, "gflops": flops / (ms * 1e-3) / 1e9, "launches": 2, "info_nonzero": bad}
+            if prec == "f64" and baseline_count > 0:
+                # one single-matrix call per matrix, on the first baseline_count
+                nb = min(baseline_count, count)
+                ipiv1 = torch.zeros(256, dtype=torch.int32, device=dev)
+                info1 = torch.zeros(1, dtype=torch.int32, device=dev)
+                lw1 = r.rl_dgetrf_work_size(256, 256)
+                wk1 = torch.empty(lw1, dtype=torch.uint8, device=dev)
+
+                def per_matrix():
+                    for b in range(nb):
+                        n = int(sizes[b])
+                        p = base + offs[b] * esz
+                        if kind == "potrf":
+                            r.check(r.rl_dpotrf("L", n, p, n, info1, None, 0, sp))
+                        else:
+                            r.check(r.rl_dgetrf(n, n, p, n, ipiv1, info1, wk1, lw1, sp))
+                l0 = r.rl_launch_count()
+                ms1 = timed(per_matrix, reps=1, before=restore)
+                launches = r.rl_launch_count() - l0
+                sub = float(np.sum(sizes[:nb].astype(np.float64) ** 3)) / float(np.sum(sizes.astype(np.float64) ** 3))
+                res["per_matrix_path"] = {"matrices_timed": nb, "ms_for_timed": ms1,
+                                          "ms_scaled_to_batch": ms1 / sub, "kernel_launches_timed": launches,
+                                          "speedup_batched": (ms1 / sub) / ms}
+            out[f"{kind}_{prec}"] = res
+            del pristine, work_buf
+            torch.cuda.empty_cache()
+    return out
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 
@@ -434,6 +545,10 @@ def run_gpu(args, rank, world, local_rank):
         mixed = mixed_section(args.mixed_n, args.mixed_nrhs, args.mixed_cond,
                               [p for p in args.mixed_precs.split(",") if p], dev, sp)
 
+    batched = None
+    if args.batch_count > 0:
+        batched = batched_section(args.batch_count, args.batch_baseline, dev, sp)
+
     cpu = None
     if world == 1 and args.cpu_n > 0:
         from oracle import build as obuild
@@ -461,6 +576,7 @@ def run_gpu(args, rank, world, local_rank):
                     for k, v in trace.items()},
         "gpu_launches": launches,
         "mixed_solve": mixed,
+        "batched": batched,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clocks,
@@ -486,6 +602,10 @@ def main():
     ap.add_argument("--mixed-nrhs", type=int, default=16)
     ap.add_argument("--mixed-cond", type=float, default=1e6)
     ap.add_argument("--mixed-precs", default="fp32,tf32x3,tf32,bf16,fp16s")
+    ap.add_argument("--batch-count", type=int, default=20000,
+                    help="matrices per kind in the batching-form comparison (0 skips it)")
+    ap.add_argument("--batch-baseline", type=int, default=2000,
+                    help="matrices timed through the single-matrix path for the comparison")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

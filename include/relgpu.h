@@ -211,6 +211,35 @@ int rl_dtrmm(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
              rl_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Batching form: `batch` independent factorizations of orders up to 256 in
+ * one persistent launch (the paper has no batched form; each matrix follows
+ * the Section 3 scheme with 32-column halves).  Matrix b is the n[b] x n[b]
+ * column-major array at A[b] with leading dimension lda[b]; n, A, lda, ipiv
+ * and info are DEVICE arrays of `batch` entries (A[b] and ipiv[b] device
+ * pointers).  max_n (host) bounds n[b] and must be <= 256.  info[b] follows
+ * LAPACK for matrix b (dpotrf: first non-positive minor; dgetrf: first zero
+ * pivot, factorization completed); ipiv[b] has n[b] 1-based entries.
+ * Matrices with n[b] <= 0 or n[b] > 256 are skipped with info[b] = 0.
+ * Workspace: rl_potrf_vbatched_work_size / rl_getrf_vbatched_work_size
+ * bytes (the size-sorted work list and its counter).
+ * Argument numbers: potrf 1 uplo, 2 batch; getrf 1 batch.
+ * ------------------------------------------------------------------------- */
+size_t rl_potrf_vbatched_work_size(int64_t batch);
+size_t rl_getrf_vbatched_work_size(int64_t batch);
+int rl_dpotrf_vbatched(char uplo, int64_t batch, const int32_t *n, double *const *A,
+                       const int32_t *lda, int32_t *info, int32_t max_n, void *work,
+                       size_t lwork, rl_stream_t stream);
+int rl_spotrf_vbatched(char uplo, int64_t batch, const int32_t *n, float *const *A,
+                       const int32_t *lda, int32_t *info, int32_t max_n, void *work,
+                       size_t lwork, rl_stream_t stream);
+int rl_dgetrf_vbatched(int64_t batch, const int32_t *n, double *const *A, const int32_t *lda,
+                       int32_t *const *ipiv, int32_t *info, int32_t max_n, void *work,
+                       size_t lwork, rl_stream_t stream);
+int rl_sgetrf_vbatched(int64_t batch, const int32_t *n, float *const *A, const int32_t *lda,
+                       int32_t *const *ipiv, int32_t *info, int32_t max_n, void *work,
+                       size_t lwork, rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Tensor-core GEMM on FP32 storage (the update kernel of the precision
  * form): C(m x n) := C + alpha op(A) op(B), A, B, C single precision,
  * column-major, products in `prec` (RL_PREC_TF32, _BF16, _FP16S, _TF32X3) on
@@ -257,6 +286,8 @@ int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda,
  *                              (default 2e9); 0 makes any wait that is not
  *                              already satisfied fail with
  *                              RL_INFO_DEVICE_TIMEOUT
+ *   RL_PARAM_BATCH_CTAS        CTAs per SM of the batched kernels (0 = as
+ *                              many as fit, the default; 1..8)
  * rl_set_param returns 0 or RL_ERR_PARAM; rl_get_param returns the value or
  * -1 for an unknown key.
  * ------------------------------------------------------------------------- */
@@ -264,7 +295,8 @@ enum {
     RL_PARAM_POTRF_CROSSOVER = 1,
     RL_PARAM_GETRF_PANEL = 2,
     RL_PARAM_TRTRI_CROSSOVER = 3,
-    RL_PARAM_SPIN_LIMIT_NS = 4
+    RL_PARAM_SPIN_LIMIT_NS = 4,
+    RL_PARAM_BATCH_CTAS = 5
 };
 int rl_set_param(int key, int64_t value);
 int64_t rl_get_param(int key);

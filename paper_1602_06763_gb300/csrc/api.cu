@@ -454,6 +454,72 @@ int rl_dsposv(char uplo, int64_t n, int64_t nrhs, double *A, int64_t lda, const 
     return finish(c);
 }
 
+// ---- batching form --------------------------------------------------------------
+
+size_t rl_potrf_vbatched_work_size(int64_t batch) { return batch < 0 ? 0 : batched_work_size(batch); }
+size_t rl_getrf_vbatched_work_size(int64_t batch) { return batch < 0 ? 0 : batched_work_size(batch); }
+
+}  // extern "C"
+
+template <typename T>
+static int potrf_vb(char uplo, int64_t batch, const int32_t *n, T *const *A, const int32_t *lda,
+                    int32_t *info, int32_t max_n, void *work, size_t lwork, rl_stream_t stream)
+{
+    if (!is_l(uplo) && !is_u(uplo)) return -1;
+    if (batch < 0) return -2;
+    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
+    if (max_n > BATCH_MAX_N || batch > INT32_MAX) return RL_ERR_UNSUPPORTED;
+    if (batch == 0) return RL_SUCCESS;
+    if (n == nullptr || A == nullptr || lda == nullptr || info == nullptr) return RL_ERR_NULL_POINTER;
+    if (work == nullptr || lwork < batched_work_size(batch)) return RL_ERR_WORKSPACE;
+    Ctx c = make_ctx(stream, nullptr, work, lwork);
+    batched_factor<T>(c, false, batch, n, A, lda, nullptr, info, g_params.batch_ctas);
+    return finish(c);
+}
+
+template <typename T>
+static int getrf_vb(int64_t batch, const int32_t *n, T *const *A, const int32_t *lda, int32_t *const *ipiv,
+                    int32_t *info, int32_t max_n, void *work, size_t lwork, rl_stream_t stream)
+{
+    if (batch < 0) return -1;
+    if (max_n > BATCH_MAX_N || batch > INT32_MAX) return RL_ERR_UNSUPPORTED;
+    if (batch == 0) return RL_SUCCESS;
+    if (n == nullptr || A == nullptr || lda == nullptr || ipiv == nullptr || info == nullptr)
+        return RL_ERR_NULL_POINTER;
+    if (work == nullptr || lwork < batched_work_size(batch)) return RL_ERR_WORKSPACE;
+    Ctx c = make_ctx(stream, nullptr, work, lwork);
+    batched_factor<T>(c, true, batch, n, A, lda, ipiv, info, g_params.batch_ctas);
+    return finish(c);
+}
+
+extern "C" {
+
+int rl_dpotrf_vbatched(char uplo, int64_t batch, const int32_t *n, double *const *A, const int32_t *lda,
+                       int32_t *info, int32_t max_n, void *work, size_t lwork, rl_stream_t stream)
+{
+    return potrf_vb<double>(uplo, batch, n, A, lda, info, max_n, work, lwork, stream);
+}
+
+int rl_spotrf_vbatched(char uplo, int64_t batch, const int32_t *n, float *const *A, const int32_t *lda,
+                       int32_t *info, int32_t max_n, void *work, size_t lwork, rl_stream_t stream)
+{
+    return potrf_vb<float>(uplo, batch, n, A, lda, info, max_n, work, lwork, stream);
+}
+
+int rl_dgetrf_vbatched(int64_t batch, const int32_t *n, double *const *A, const int32_t *lda,
+                       int32_t *const *ipiv, int32_t *info, int32_t max_n, void *work, size_t lwork,
+                       rl_stream_t stream)
+{
+    return getrf_vb<double>(batch, n, A, lda, ipiv, info, max_n, work, lwork, stream);
+}
+
+int rl_sgetrf_vbatched(int64_t batch, const int32_t *n, float *const *A, const int32_t *lda,
+                       int32_t *const *ipiv, int32_t *info, int32_t max_n, void *work, size_t lwork,
+                       rl_stream_t stream)
+{
+    return getrf_vb<float>(batch, n, A, lda, ipiv, info, max_n, work, lwork, stream);
+}
+
 // ---- host-buffer forms -------------------------------------------------------
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -543,6 +609,10 @@ int rl_set_param(int key, int64_t value)
         if (value < 0) return RL_ERR_PARAM;
         g_params.spin_ns = (long long)value;
         return RL_SUCCESS;
+    case RL_PARAM_BATCH_CTAS:
+        if (value < 0 || value > 8) return RL_ERR_PARAM;
+        g_params.batch_ctas = (int)value;
+        return RL_SUCCESS;
     default:
         return RL_ERR_PARAM;
     }
@@ -555,6 +625,7 @@ int64_t rl_get_param(int key)
     case RL_PARAM_GETRF_PANEL: return g_params.getrf_nb;
     case RL_PARAM_TRTRI_CROSSOVER: return g_params.trtri_c;
     case RL_PARAM_SPIN_LIMIT_NS: return g_params.spin_ns;
+    case RL_PARAM_BATCH_CTAS: return g_params.batch_ctas;
     default: return -1;
     }
 }

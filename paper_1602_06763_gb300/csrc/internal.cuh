@@ -22,6 +22,7 @@ struct Params {
     int getrf_nb = 32;       // dgetrf panel width
     int trtri_c = 64;        // dtrtri / dlauum crossover
     long long spin_ns = 2000000000LL;
+    int batch_ctas = 0;      // CTAs per SM of the batched kernels (0 = occupancy limit)
 };
 extern Params g_params;
 
@@ -48,7 +49,7 @@ void note(Ctx &c, cudaError_t e);
 // Kernel kinds, in the order rl_trace_read reports them.
 enum Kind {
     K_GEMM = 0, K_SYRK, K_TRSM, K_TRMM, K_POTF2, K_TRTI2, K_LAUU2, K_DIAG,
-    K_PANEL, K_LASWP, K_RESID, K_CONVERT, K_MIX, K_COUNT
+    K_PANEL, K_LASWP, K_RESID, K_CONVERT, K_MIX, K_BATCH, K_COUNT
 };
 extern std::atomic<int> g_trace_on;
 // Bracket one kernel launch: with tracing on, CUDA events are recorded on the
@@ -135,6 +136,13 @@ bool tc_gemm(Ctx &c, int prec, bool ta, bool tb, i64 m, i64 n, i64 k, float alph
              i64 lda, const float *B, i64 ldb, float *C, i64 ldc, bool lower, void *work, size_t lwork);
 // Smallest GEMM sent to the tensor cores (smaller ones are latency-bound).
 constexpr i64 TC_MIN_MN = 128, TC_MIN_K = 64;
+
+// ---- batching form (batched.cu) ---------------------------------------------
+size_t batched_work_size(i64 batch);
+template <typename T>
+int batched_factor(Ctx &c, bool lu, i64 batch, const int32_t *d_n, T *const *d_A, const int32_t *d_lda,
+                   int32_t *const *d_ipiv, int32_t *d_info, int per_sm);
+constexpr int BATCH_MAX_N = 256;
 
 // ---- recursions (api.cu), T = double or float --------------------------------
 template <typename T>

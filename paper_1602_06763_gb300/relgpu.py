@@ -60,6 +60,12 @@ _SIGS = {
     "rl_sgemm_tc_work_size": (_sz, [_i64, _i64, _i64, ctypes.c_int]),
     "rl_sgemm_tc": (ctypes.c_int, [ctypes.c_int, _ch, _ch, _i64, _i64, _i64, ctypes.c_float, _vp, _i64,
                                    _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
+    "rl_potrf_vbatched_work_size": (_sz, [_i64]),
+    "rl_getrf_vbatched_work_size": (_sz, [_i64]),
+    "rl_dpotrf_vbatched": (ctypes.c_int, [_ch, _i64, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _sz, _vp]),
+    "rl_spotrf_vbatched": (ctypes.c_int, [_ch, _i64, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _sz, _vp]),
+    "rl_dgetrf_vbatched": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _sz, _vp]),
+    "rl_sgetrf_vbatched": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _sz, _vp]),
     "rl_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "rl_trace_kinds": (ctypes.c_int, []),
     "rl_trace_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
@@ -91,6 +97,7 @@ RL_PARAM_POTRF_CROSSOVER = 1
 RL_PARAM_GETRF_PANEL = 2
 RL_PARAM_TRTRI_CROSSOVER = 3
 RL_PARAM_SPIN_LIMIT_NS = 4
+RL_PARAM_BATCH_CTAS = 5
 
 
 def _ptr(x):
@@ -196,6 +203,34 @@ def rl_sgemm_tc(prec, transa, transb, m, n, k, alpha, A, lda, B, ldb, C, ldc, wo
                 stream=None):
     return _lib.rl_sgemm_tc(prec, _c(transa), _c(transb), m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb,
                             _ptr(C), ldc, _ptr(work), lwork, _stream(stream))
+
+
+def rl_potrf_vbatched_work_size(batch):
+    return int(_lib.rl_potrf_vbatched_work_size(batch))
+
+
+def rl_getrf_vbatched_work_size(batch):
+    return int(_lib.rl_getrf_vbatched_work_size(batch))
+
+
+def rl_dpotrf_vbatched(uplo, batch, n, A, lda, info, max_n, work, lwork, stream=None):
+    return _lib.rl_dpotrf_vbatched(_c(uplo), batch, _ptr(n), _ptr(A), _ptr(lda), _ptr(info), max_n,
+                                   _ptr(work), lwork, _stream(stream))
+
+
+def rl_spotrf_vbatched(uplo, batch, n, A, lda, info, max_n, work, lwork, stream=None):
+    return _lib.rl_spotrf_vbatched(_c(uplo), batch, _ptr(n), _ptr(A), _ptr(lda), _ptr(info), max_n,
+                                   _ptr(work), lwork, _stream(stream))
+
+
+def rl_dgetrf_vbatched(batch, n, A, lda, ipiv, info, max_n, work, lwork, stream=None):
+    return _lib.rl_dgetrf_vbatched(batch, _ptr(n), _ptr(A), _ptr(lda), _ptr(ipiv), _ptr(info), max_n,
+                                   _ptr(work), lwork, _stream(stream))
+
+
+def rl_sgetrf_vbatched(batch, n, A, lda, ipiv, info, max_n, work, lwork, stream=None):
+    return _lib.rl_sgetrf_vbatched(batch, _ptr(n), _ptr(A), _ptr(lda), _ptr(ipiv), _ptr(info), max_n,
+                                   _ptr(work), lwork, _stream(stream))
 
 
 def rl_host_work_size(routine, m, n, lda):
