@@ -257,6 +257,7 @@ k_panel(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, Pane
     T *S = reinterpret_cast<T *>(smem_raw);
     __shared__ double wv[PANEL_THREADS / 32];
     __shared__ long long wi[PANEL_THREADS / 32];
+    __shared__ int wg[PANEL_THREADS / 32];
     __shared__ long long s_p;
     __shared__ int s_gw, s_fail;
     __shared__ T urow[PANEL_NBMAX], rowj[PANEL_NBMAX];
@@ -312,39 +313,44 @@ k_panel(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, Pane
             const unsigned long long idx = (s_p == LLONG_MAX) ? 0xFFFFFFFFFFull : (unsigned long long)s_p;
             st_release_u64(&ws->key[buf][g], ((unsigned long long)(j + 1) << 40) | idx);
         }
-        // 3. warp 0 waits for every CTA's slot of column j and picks the winner
-        if (tid < 32) {
+        // 3. thread q waits for CTA q's slot of column j (all slots in one
+        //    round trip); a block reduction picks the winner
+        {
             double v = -1.0;
             long long ix = LLONG_MAX;
-            int gw = -1, ok = 1;
-            const unsigned long long want = (unsigned long long)(j + 1);
-            for (int q = lane; q < G; q += 32) {
-                unsigned long long kq = ld_acquire_u64(&ws->key[buf][q]);
+            int gw = -1;
+            if (tid < G) {
+                const unsigned long long want = (unsigned long long)(j + 1);
+                unsigned long long kq = ld_acquire_u64(&ws->key[buf][tid]);
+                int ok = 1;
                 if ((kq >> 40) != want) {
                     const unsigned long long t0 = global_ns();
-                    while (((kq = ld_acquire_u64(&ws->key[buf][q])) >> 40) != want) {
+                    while (((kq = ld_acquire_u64(&ws->key[buf][tid])) >> 40) != want) {
                         if ((long long)(global_ns() - t0) >= spin_ns) { ok = 0; break; }
                         __nanosleep(32);
                     }
                 }
-                if (!ok) break;
-                const unsigned long long qi = kq & 0xFFFFFFFFFFull;
-                if (qi != 0xFFFFFFFFFFull) {
-                    const double qv = __ldcg(&ws->val[buf][q]);
-                    if (better(qv, (long long)qi, v, ix)) { v = qv; ix = (long long)qi; gw = q; }
+                if (!ok) {
+                    s_fail = 1;
+                } else {
+                    const unsigned long long qi = kq & 0xFFFFFFFFFFull;
+                    if (qi != 0xFFFFFFFFFFull) { v = __ldcg(&ws->val[buf][tid]); ix = (long long)qi; gw = tid; }
                 }
             }
-            ok = __all_sync(0xffffffffu, ok);
             for (int o = 16; o > 0; o >>= 1) {
                 const double ov = __shfl_down_sync(0xffffffffu, v, o);
                 const long long oi = __shfl_down_sync(0xffffffffu, ix, o);
                 const int og = __shfl_down_sync(0xffffffffu, gw, o);
                 if (og >= 0 && (gw < 0 || better(ov, oi, v, ix))) { v = ov; ix = oi; gw = og; }
             }
-            if (lane == 0) {
+            __syncthreads();                   // wv/wi of step 1 are no longer read
+            if (lane == 0) { wv[tid >> 5] = v; wi[tid >> 5] = ix; wg[tid >> 5] = gw; }
+            __syncthreads();
+            if (tid == 0) {
+                for (int w = 1; w < PANEL_THREADS / 32; ++w)
+                    if (wg[w] >= 0 && (gw < 0 || better(wv[w], wi[w], v, ix))) { v = wv[w]; ix = wi[w]; gw = wg[w]; }
                 s_p = (gw >= 0) ? ix : (long long)j;
                 s_gw = gw;
-                if (!ok) s_fail = 1;
             }
         }
         __syncthreads();

@@ -24,8 +24,10 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", required=True,
                     choices=["dgemm", "dsyrk", "dtrsm", "potrf", "getrf", "trtri", "lauum", "panel",
-                             "sgemm_tc"])
-    ap.add_argument("--prec", type=int, default=1, help="sgemm_tc operand precision (rl_prec)")
+                             "sgemm_tc", "dsgesv", "dsposv"])
+    ap.add_argument("--prec", type=int, default=1, help="operand precision (rl_prec) of sgemm_tc / dsgesv")
+    ap.add_argument("--nrhs", type=int, default=16)
+    ap.add_argument("--cond", type=float, default=1e6)
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--m", type=int, default=0, help="rows (panel case); default n")
     ap.add_argument("--k", type=int, default=0, help="inner dimension (dgemm/dsyrk); default n")
@@ -50,7 +52,26 @@ def main():
     s = torch.cuda.current_stream().cuda_stream
     info = torch.zeros(1, dtype=torch.int32, device=dev)
 
-    if a.case == "sgemm_tc":
+    if a.case in ("dsgesv", "dsposv"):
+        from . import inputs
+        spd = a.case == "dsposv"
+        A0 = inputs.spectrum_device(n, a.cond, 7, spd=spd, device=dev)
+        B = torch.randn(a.nrhs, n, generator=g, device=dev, dtype=torch.float64)
+        X = torch.zeros_like(B)
+        A = A0.clone()
+        ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+        it = torch.zeros(1, dtype=torch.int32, device=dev)
+        lw = (r.rl_dsposv_work_size if spd else r.rl_dsgesv_work_size)(n, a.nrhs, a.prec)
+        work = torch.empty(lw, dtype=torch.uint8, device=dev)
+        flops = (n ** 3 / 3.0) if spd else (2.0 * n ** 3 / 3.0)
+        restore = lambda: A.copy_(A0)
+        if spd:
+            run = lambda: r.check(r.rl_dsposv("L", n, a.nrhs, A, n, B, n, X, n, a.prec, 1e-14, 30, it, info,
+                                              work, lw, s))
+        else:
+            run = lambda: r.check(r.rl_dsgesv(n, a.nrhs, A, n, ipiv, B, n, X, n, a.prec, 1e-14, 30, it, info,
+                                              work, lw, s))
+    elif a.case == "sgemm_tc":
         A = torch.rand(k, n, generator=g, device=dev, dtype=torch.float32)
         B = torch.rand(n, k, generator=g, device=dev, dtype=torch.float32)
         C = torch.rand(n, n, generator=g, device=dev, dtype=torch.float32)
@@ -128,6 +149,9 @@ def main():
         times.append(e0.elapsed_time(e1))
     out = {"case": a.case, "n": n, "m": m, "k": k, "ms": statistics.median(times),
            "gflops": flops / (statistics.median(times) * 1e-3) / 1e9, "info": int(info.item())}
+    if a.case in ("dsgesv", "dsposv"):
+        out["iters"] = int(it.item())
+        out["prec"] = a.prec
     if a.trace:
         out["trace"] = r.trace_summary()
         r.rl_trace_enable(0)
