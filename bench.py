@@ -254,6 +254,8 @@ def mixed_section(n, nrhs, cond, precs, dev, sp):
         ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
         lw = r.rl_dgetrf_work_size(n, n)
         wk = torch.empty(lw, dtype=torch.uint8, device=dev)
+        ltw = r.rl_trs_work_size(n, nrhs)
+        tw = torch.empty(ltw, dtype=torch.uint8, device=dev) if ltw else None
         res = {}
         # FP64 path (one warm-up, then timed)
         for rep in range(2):
@@ -261,10 +263,10 @@ def mixed_section(n, nrhs, cond, precs, dev, sp):
             X = B.clone()
             if spd:
                 ms = timed(lambda: (r.check(r.rl_dpotrf("L", n, A, n, info, None, 0, sp)),
-                                    r.check(r.rl_dpotrs("L", n, nrhs, A, n, X, n, sp))))
+                                    r.check(r.rl_dpotrs("L", n, nrhs, A, n, X, n, tw, ltw, sp))))
             else:
                 ms = timed(lambda: (r.check(r.rl_dgetrf(n, n, A, n, ipiv, info, wk, lw, sp)),
-                                    r.check(r.rl_dgetrs("N", n, nrhs, A, n, ipiv, X, n, sp))))
+                                    r.check(r.rl_dgetrs("N", n, nrhs, A, n, ipiv, X, n, tw, ltw, sp))))
         res["fp64"] = {"ms": ms, "eta": eta_of(A0, X, B, anorm)}
         del A
         for name in precs:

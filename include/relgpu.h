@@ -132,12 +132,39 @@ int rl_dpotri(char uplo, int64_t n, double *A, int64_t lda, int32_t *info,
  *     Argument numbers: 1 trans, 2 n, 3 nrhs, 4 A, 5 lda, 6 ipiv, 7 B, 8 ldb.
  *   rl_dpotrs: uplo 'L' only; A from rl_dpotrf: X = L^{-T} L^{-1} B.
  *     Argument numbers: 1 uplo, 2 n, 3 nrhs, 4 A, 5 lda, 6 B, 7 ldb.
- * No workspace; stream-ordered.
+ * work (device, caller-owned, optional): with work == NULL both triangles
+ *   are solved by the recursive TRSM (Section 3's halving on the triangle).
+ *   With work != NULL and nrhs <= 64, each triangle is solved in ONE launch
+ *   that streams the triangle once (64-row blocks, inverted diagonal blocks,
+ *   per-block ready flags); lwork must then be >= rl_trs_work_size(n, nrhs)
+ *   (a few KB), else RL_ERR_WORKSPACE.  The first int32 of work is a status:
+ *   0 on completion, RL_INFO_DEVICE_TIMEOUT if a bounded device-side wait
+ *   expired (read it after synchronizing).  Calls sharing one work buffer
+ *   must be ordered (same stream).  With nrhs > 64, work is not used.
+ * Stream-ordered; no synchronization.
  * ------------------------------------------------------------------------- */
+size_t rl_trs_work_size(int64_t n, int64_t nrhs);
 int rl_dgetrs(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda,
-              const int32_t *ipiv, double *B, int64_t ldb, rl_stream_t stream);
+              const int32_t *ipiv, double *B, int64_t ldb, void *work, size_t lwork,
+              rl_stream_t stream);
 int rl_dpotrs(char uplo, int64_t n, int64_t nrhs, const double *A, int64_t lda, double *B,
-              int64_t ldb, rl_stream_t stream);
+              int64_t ldb, void *work, size_t lwork, rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Single-precision peers (Section 5: every routine exists for s, d, c and z;
+ * s and d are built): the same recursions and kernels in FP32 storage and
+ * arithmetic (SIMT FP32 updates).  Same arguments, numbering, workspace and
+ * info semantics as the double-precision routines above.
+ * ------------------------------------------------------------------------- */
+int rl_spotrf(char uplo, int64_t n, float *A, int64_t lda, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream);
+int rl_sgetrf(int64_t m, int64_t n, float *A, int64_t lda, int32_t *ipiv, int32_t *info,
+              void *work, size_t lwork, rl_stream_t stream);
+int rl_sgetrs(char trans, int64_t n, int64_t nrhs, const float *A, int64_t lda,
+              const int32_t *ipiv, float *B, int64_t ldb, void *work, size_t lwork,
+              rl_stream_t stream);
+int rl_spotrs(char uplo, int64_t n, int64_t nrhs, const float *A, int64_t lda, float *B,
+              int64_t ldb, void *work, size_t lwork, rl_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Precision form: A X = B (FP64) solved with a low-precision factorization

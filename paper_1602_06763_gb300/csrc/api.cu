@@ -321,6 +321,41 @@ int rl_dtrmm(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
     return finish(c);
 }
 
+// ---- single precision peers -----------------------------------------------------
+
+int rl_spotrf(char uplo, int64_t n, float *A, int64_t lda, int32_t *info, void *work, size_t lwork,
+              rl_stream_t stream)
+{
+    if (!is_l(uplo) && !is_u(uplo)) return -1;
+    if (n < 0) return -2;
+    if (n > 0 && A == nullptr) return -3;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (info == nullptr) return RL_ERR_NULL_POINTER;
+    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
+    Ctx c = make_ctx(stream, info, work, lwork);
+    c.abort = info;
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    potrf_rec_t<float>(c, n, A, lda, 0);
+    return finish(c);
+}
+
+int rl_sgetrf(int64_t m, int64_t n, float *A, int64_t lda, int32_t *ipiv, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream)
+{
+    if (m < 0) return -1;
+    if (n < 0) return -2;
+    if (m > 0 && n > 0 && A == nullptr) return -3;
+    if (lda < (m > 1 ? m : 1)) return -4;
+    if (m > INT32_MAX - 1) return RL_ERR_UNSUPPORTED;
+    if (info == nullptr || (ipiv == nullptr && m > 0 && n > 0)) return RL_ERR_NULL_POINTER;
+    if (m > 0 && n > 0 && (work == nullptr || lwork < rl_dgetrf_work_size(m, n))) return RL_ERR_WORKSPACE;
+    Ctx c = make_ctx(stream, info, work, lwork);
+    c.abort = nullptr;
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    getrf_rec_t<float>(c, A, lda, m, ipiv, 0, m, n);
+    return finish(c);
+}
+
 // ---- tensor-core GEMM on FP32 storage ------------------------------------------
 
 static bool tc_prec(int prec)
@@ -358,8 +393,45 @@ int rl_sgemm_tc(int prec, char transa, char transb, int64_t m, int64_t n, int64_
 
 // ---- solves with the factors ------------------------------------------------
 
-int rl_dgetrs(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda,
-              const int32_t *ipiv, double *B, int64_t ldb, rl_stream_t stream)
+}  // extern "C"
+
+// X := A^{-1} B from the factors: LU (lu) after the row interchanges, or
+// Cholesky.  With a workspace, thin right-hand sides take the one-launch flow
+// solve; otherwise the recursive TRSM.
+template <typename T>
+static int trs_t(bool lu, int64_t n, int64_t nrhs, const T *A, int64_t lda, const int32_t *ipiv, T *B,
+                 int64_t ldb, void *work, size_t lwork, rl_stream_t stream)
+{
+    if (n == 0 || nrhs == 0) return RL_SUCCESS;
+    if (A == nullptr || B == nullptr || (lu && ipiv == nullptr)) return RL_ERR_NULL_POINTER;
+    const bool flow = work != nullptr && nrhs <= FLOW_MAX_NRHS;
+    if (flow && lwork < flow_ws_bytes(n, nrhs)) return RL_ERR_WORKSPACE;
+    Ctx c = make_ctx(stream, nullptr, work, lwork);
+    if (lu) laswp<T>(c, B, ldb, n, 0, nrhs, 0, n, ipiv);
+    if (flow) {
+        note(c, cudaMemsetAsync(work, 0, sizeof(int32_t), c.s));
+        trsm_flow<T>(c, FLOW_LN, lu, n, nrhs, A, lda, B, ldb, work);
+        trsm_flow<T>(c, lu ? FLOW_UN : FLOW_LT, false, n, nrhs, A, lda, B, ldb, work);
+    } else if (lu) {
+        trsm_lln<T>(c, true, n, nrhs, T(1), A, lda, B, ldb);
+        trsm_lun<T>(c, n, nrhs, T(1), A, lda, B, ldb);
+    } else {
+        trsm_lln<T>(c, false, n, nrhs, T(1), A, lda, B, ldb);
+        trsm_llt<T>(c, n, nrhs, T(1), A, lda, B, ldb);
+    }
+    return finish(c);
+}
+
+extern "C" {
+
+size_t rl_trs_work_size(int64_t n, int64_t nrhs)
+{
+    if (n <= 0 || nrhs <= 0 || nrhs > FLOW_MAX_NRHS) return 0;
+    return flow_ws_bytes(n, nrhs);
+}
+
+int rl_dgetrs(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda, const int32_t *ipiv,
+              double *B, int64_t ldb, void *work, size_t lwork, rl_stream_t stream)
 {
     if (!is_n(trans) && !is_t(trans)) return -1;
     if (n < 0) return -2;
@@ -367,17 +439,11 @@ int rl_dgetrs(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda,
     if (lda < imax1(n)) return -5;
     if (ldb < imax1(n)) return -8;
     if (is_t(trans)) return RL_ERR_UNSUPPORTED;
-    if (n == 0 || nrhs == 0) return RL_SUCCESS;
-    if (ipiv == nullptr) return RL_ERR_NULL_POINTER;
-    Ctx c = make_ctx(stream, nullptr, nullptr, 0);
-    laswp<double>(c, B, ldb, n, 0, nrhs, 0, n, ipiv);
-    trsm_lln<double>(c, true, n, nrhs, 1.0, A, lda, B, ldb);
-    trsm_lun<double>(c, n, nrhs, 1.0, A, lda, B, ldb);
-    return finish(c);
+    return trs_t<double>(true, n, nrhs, A, lda, ipiv, B, ldb, work, lwork, stream);
 }
 
-int rl_dpotrs(char uplo, int64_t n, int64_t nrhs, const double *A, int64_t lda, double *B,
-              int64_t ldb, rl_stream_t stream)
+int rl_dpotrs(char uplo, int64_t n, int64_t nrhs, const double *A, int64_t lda, double *B, int64_t ldb,
+              void *work, size_t lwork, rl_stream_t stream)
 {
     if (!is_l(uplo) && !is_u(uplo)) return -1;
     if (n < 0) return -2;
@@ -385,11 +451,31 @@ int rl_dpotrs(char uplo, int64_t n, int64_t nrhs, const double *A, int64_t lda, 
     if (lda < imax1(n)) return -5;
     if (ldb < imax1(n)) return -7;
     if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
-    if (n == 0 || nrhs == 0) return RL_SUCCESS;
-    Ctx c = make_ctx(stream, nullptr, nullptr, 0);
-    trsm_lln<double>(c, false, n, nrhs, 1.0, A, lda, B, ldb);
-    trsm_llt<double>(c, n, nrhs, 1.0, A, lda, B, ldb);
-    return finish(c);
+    return trs_t<double>(false, n, nrhs, A, lda, nullptr, B, ldb, work, lwork, stream);
+}
+
+int rl_sgetrs(char trans, int64_t n, int64_t nrhs, const float *A, int64_t lda, const int32_t *ipiv,
+              float *B, int64_t ldb, void *work, size_t lwork, rl_stream_t stream)
+{
+    if (!is_n(trans) && !is_t(trans)) return -1;
+    if (n < 0) return -2;
+    if (nrhs < 0) return -3;
+    if (lda < imax1(n)) return -5;
+    if (ldb < imax1(n)) return -8;
+    if (is_t(trans)) return RL_ERR_UNSUPPORTED;
+    return trs_t<float>(true, n, nrhs, A, lda, ipiv, B, ldb, work, lwork, stream);
+}
+
+int rl_spotrs(char uplo, int64_t n, int64_t nrhs, const float *A, int64_t lda, float *B, int64_t ldb,
+              void *work, size_t lwork, rl_stream_t stream)
+{
+    if (!is_l(uplo) && !is_u(uplo)) return -1;
+    if (n < 0) return -2;
+    if (nrhs < 0) return -3;
+    if (lda < imax1(n)) return -5;
+    if (ldb < imax1(n)) return -7;
+    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
+    return trs_t<float>(false, n, nrhs, A, lda, nullptr, B, ldb, work, lwork, stream);
 }
 
 // ---- precision form ------------------------------------------------------------

@@ -196,18 +196,19 @@ constexpr int PANEL_THREADS = 256;
 constexpr int PANEL_RMIN = 64;
 constexpr size_t PANEL_SMEM_MAX = 200 * 1024;
 
+constexpr int PANEL_REC = 2 + PANEL_NBMAX;
+
+// Exchange area of the multi-CTA panel kernels.  Per column each CTA
+// publishes one record {|candidate|, candidate row (bits of a long long,
+// LLONG_MAX = none), candidate row's nb entries}; the owner of row j also
+// publishes row j.  Both are double-buffered by column parity: a CTA can be
+// at most one column ahead of any other, because the arrival counter holds
+// it at the next column's barrier.
 struct PanelWS {
-    // register-row kernel: slot key = (column + 1) << 40 | row, 0 = empty
-    unsigned long long key[2][PANEL_GMAX];
-    double val[2][PANEL_GMAX];
-    // shared-memory kernel: arrival counter
-    unsigned int counter;
+    unsigned int counter;               // arrivals, G per column
     unsigned int pad[63];
-    double cand_val[2][PANEL_GMAX];     // |candidate| per CTA, double-buffered
-    long long cand_idx[2][PANEL_GMAX];  // candidate row (panel-local), LLONG_MAX = none
-    // both kernels
-    double cand_row[2][PANEL_GMAX][PANEL_NBMAX];
-    double rowj[2][PANEL_NBMAX];        // current row j, published by its owner
+    double rec[2][PANEL_GMAX][PANEL_REC];
+    double rowj[2][PANEL_NBMAX];
 };
 
 size_t panel_ws_bytes() { return sizeof(PanelWS); }
@@ -231,6 +232,11 @@ __device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned l
     asm volatile("st.release.gpu.global.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
 }
 
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long global_ns()
 {
     unsigned long long t;
@@ -247,6 +253,12 @@ __device__ __forceinline__ bool better(double v, long long i, double bv, long lo
 // thread t works on row g*R + t, kept in shared memory as a[c * 256 + t]
 // (consecutive threads, consecutive words).  ipiv and info use global
 // numbering: panel row r is matrix row r0 + r.
+//
+// Per column, two block barriers: after the local candidate search, warp 0
+// alone publishes the CTA's record, arrives on the grid counter with a
+// release add, waits for all G arrivals (bounded), reads the G candidates in
+// one round trip, picks the winner (largest |a_ij|, lowest row on ties) and
+// fetches its row; then every thread swaps, scales and updates its own row.
 template <typename T>
 __global__ void __launch_bounds__(PANEL_THREADS)
 k_panel(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, PanelWS *ws, int R,
@@ -257,9 +269,8 @@ k_panel(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, Pane
     T *S = reinterpret_cast<T *>(smem_raw);
     __shared__ double wv[PANEL_THREADS / 32];
     __shared__ long long wi[PANEL_THREADS / 32];
-    __shared__ int wg[PANEL_THREADS / 32];
     __shared__ long long s_p;
-    __shared__ int s_gw, s_fail;
+    __shared__ int s_fail;
     __shared__ T urow[PANEL_NBMAX], rowj[PANEL_NBMAX];
 
     const int tid = threadIdx.x, lane = tid & 31, G = gridDim.x, g = blockIdx.x;
@@ -270,7 +281,6 @@ k_panel(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, Pane
     T *a = S + tid;                            // a[c * PANEL_THREADS] = element (my, c)
     if (have)
         for (int c = 0; c < nb; ++c) a[c * PANEL_THREADS] = A[(i64)c * lda + my];
-    if (tid == 0) s_fail = 0;
 
     const int mn = (int)min(m, (i64)nb);
     for (int j = 0; j < mn; ++j) {
@@ -286,89 +296,89 @@ k_panel(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, Pane
         }
         if (lane == 0) { wv[tid >> 5] = bv; wi[tid >> 5] = bi; }
         __syncthreads();
-        if (tid == 0) {
-            for (int w = 1; w < PANEL_THREADS / 32; ++w)
-                if (better(wv[w], wi[w], bv, bi)) { bv = wv[w]; bi = wi[w]; }
-            wv[0] = bv;
-            s_p = bi;
-        }
-        __syncthreads();
-        // 2. publish the candidate row (and row j, by its owner), then the slot;
-        //    one warp copies each row so the stores are spread over 32 lanes
-        {
-            const long long cand = s_p;
-            if (cand != LLONG_MAX && tid < 32) {
-                const T *src = S + (int)(cand - rbeg);
-                for (int c = lane; c < nb; c += 32) ws->cand_row[buf][g][c] = (double)src[c * PANEL_THREADS];
+        if (tid < 32) {
+            // 2. block candidate (every lane of warp 0 ends with it)
+            bv = lane < PANEL_THREADS / 32 ? wv[lane] : -1.0;
+            bi = lane < PANEL_THREADS / 32 ? wi[lane] : LLONG_MAX;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
             }
-            if (j >= rbeg && j < rbeg + rows && tid >= 32 && tid < 64) {
+            // 3. publish the record (and row j, by its owner), then arrive
+            double *rec = ws->rec[buf][g];
+            if (lane == 0) { rec[0] = bv; rec[1] = __longlong_as_double(bi); }
+            if (bi != LLONG_MAX) {
+                const T *src = S + (int)(bi - rbeg);
+                for (int c = lane; c < nb; c += 32) rec[2 + c] = (double)src[c * PANEL_THREADS];
+            }
+            if (j >= rbeg && j < rbeg + rows) {
                 const T *src = S + (int)(j - rbeg);
                 for (int c = lane; c < nb; c += 32) ws->rowj[buf][c] = (double)src[c * PANEL_THREADS];
             }
-        }
-        __syncthreads();
-        if (tid == 0) {
-            ws->val[buf][g] = wv[0];
-            __threadfence();
-            const unsigned long long idx = (s_p == LLONG_MAX) ? 0xFFFFFFFFFFull : (unsigned long long)s_p;
-            st_release_u64(&ws->key[buf][g], ((unsigned long long)(j + 1) << 40) | idx);
-        }
-        // 3. thread q waits for CTA q's slot of column j (all slots in one
-        //    round trip); a block reduction picks the winner
-        {
-            double v = -1.0;
-            long long ix = LLONG_MAX;
-            int gw = -1;
-            if (tid < G) {
-                const unsigned long long want = (unsigned long long)(j + 1);
-                unsigned long long kq = ld_acquire_u64(&ws->key[buf][tid]);
-                int ok = 1;
-                if ((kq >> 40) != want) {
+            __syncwarp();
+            int ok = 1;
+            if (lane == 0) {
+                red_release_add(&ws->counter, 1u);
+                const unsigned target = (unsigned)G * (unsigned)(j + 1);
+                if (ld_acquire_u32(&ws->counter) < target) {
                     const unsigned long long t0 = global_ns();
-                    while (((kq = ld_acquire_u64(&ws->key[buf][tid])) >> 40) != want) {
+                    while (ld_acquire_u32(&ws->counter) < target) {
                         if ((long long)(global_ns() - t0) >= spin_ns) { ok = 0; break; }
-                        __nanosleep(32);
+                        __nanosleep(16);
                     }
                 }
-                if (!ok) {
-                    s_fail = 1;
-                } else {
-                    const unsigned long long qi = kq & 0xFFFFFFFFFFull;
-                    if (qi != 0xFFFFFFFFFFull) { v = __ldcg(&ws->val[buf][tid]); ix = (long long)qi; gw = tid; }
+            }
+            __syncwarp();                      // orders lane 0's acquire before the lanes' loads
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (ok) {
+                // 4. all G candidates in one round trip (G <= 256: 8 per lane)
+                double v = -1.0;
+                long long ix = LLONG_MAX;
+                int gw = -1;
+                double qv[PANEL_GMAX / 32];
+                long long qi[PANEL_GMAX / 32];
+#pragma unroll
+                for (int u = 0; u < PANEL_GMAX / 32; ++u) {
+                    const int q = lane + 32 * u;
+                    qv[u] = -1.0;
+                    qi[u] = LLONG_MAX;
+                    if (q < G) {
+                        qv[u] = __ldcg(&ws->rec[buf][q][0]);
+                        qi[u] = __double_as_longlong(__ldcg(&ws->rec[buf][q][1]));
+                    }
                 }
+#pragma unroll
+                for (int u = 0; u < PANEL_GMAX / 32; ++u)
+                    if (qi[u] != LLONG_MAX && (gw < 0 || better(qv[u], qi[u], v, ix))) {
+                        v = qv[u]; ix = qi[u]; gw = lane + 32 * u;
+                    }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+                    const long long oi = __shfl_xor_sync(0xffffffffu, ix, o);
+                    const int og = __shfl_xor_sync(0xffffffffu, gw, o);
+                    if (og >= 0 && (gw < 0 || better(ov, oi, v, ix))) { v = ov; ix = oi; gw = og; }
+                }
+                // 5. the pivot row, and row j where this CTA owns the pivot row
+                const long long p = (gw >= 0) ? ix : (long long)j;
+                const bool own_p = (p != j) && p >= rbeg && p < rbeg + rows;
+                for (int c = lane; c < nb; c += 32) {
+                    urow[c] = (T)((gw >= 0) ? __ldcg(&ws->rec[buf][gw][2 + c]) : __ldcg(&ws->rowj[buf][c]));
+                    if (own_p) rowj[c] = (T)__ldcg(&ws->rowj[buf][c]);
+                }
+                if (lane == 0) s_p = p;
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_down_sync(0xffffffffu, v, o);
-                const long long oi = __shfl_down_sync(0xffffffffu, ix, o);
-                const int og = __shfl_down_sync(0xffffffffu, gw, o);
-                if (og >= 0 && (gw < 0 || better(ov, oi, v, ix))) { v = ov; ix = oi; gw = og; }
-            }
-            __syncthreads();                   // wv/wi of step 1 are no longer read
-            if (lane == 0) { wv[tid >> 5] = v; wi[tid >> 5] = ix; wg[tid >> 5] = gw; }
-            __syncthreads();
-            if (tid == 0) {
-                for (int w = 1; w < PANEL_THREADS / 32; ++w)
-                    if (wg[w] >= 0 && (gw < 0 || better(wv[w], wi[w], v, ix))) { v = wv[w]; ix = wi[w]; gw = wg[w]; }
-                s_p = (gw >= 0) ? ix : (long long)j;
-                s_gw = gw;
-            }
+            if (lane == 0) s_fail = !ok;
         }
         __syncthreads();
         if (s_fail) {
             if (tid == 0) atomicExch(info, RL_INFO_DEVICE_TIMEOUT);
             return;
         }
-        // 4. fetch the pivot row (and row j if this CTA owns the pivot row)
         const long long p = s_p;
-        const int gw = s_gw;
         const bool own_p = (p != j) && p >= rbeg && p < rbeg + rows;
-        for (int c = tid; c < nb; c += blockDim.x) {
-            urow[c] = (T)((gw >= 0) ? __ldcg(&ws->cand_row[buf][gw][c]) : __ldcg(&ws->rowj[buf][c]));
-            if (own_p) rowj[c] = (T)__ldcg(&ws->rowj[buf][c]);
-        }
-        __syncthreads();
         if (g == 0 && tid == 0) ipiv[r0 + j] = (int32_t)(r0 + p + 1);
-        // 5. swap, scale and rank-1 update of this thread's row
+        // 6. swap, scale and rank-1 update of this thread's row
         if (have) {
             if (p != j && my == j) {
                 for (int c = 0; c < nb; ++c) a[c * PANEL_THREADS] = urow[c];
@@ -463,14 +473,14 @@ k_panel_smem(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info,
         if (tid == 0) {
             for (int w = 1; w < PANEL_THREADS / 32; ++w)
                 if (better(wv[w], wi[w], bv, bi)) { bv = wv[w]; bi = wi[w]; }
-            ws->cand_val[buf][g] = bv;
-            ws->cand_idx[buf][g] = bi;
+            ws->rec[buf][g][0] = bv;
+            ws->rec[buf][g][1] = __longlong_as_double(bi);
             s_p = bi;
         }
         __syncthreads();
         {
             const long long mine = s_p;
-            if (mine != LLONG_MAX && tid < nb) ws->cand_row[buf][g][tid] = (double)S[tid * R + (int)(mine - rbeg)];
+            if (mine != LLONG_MAX && tid < nb) ws->rec[buf][g][2 + tid] = (double)S[tid * R + (int)(mine - rbeg)];
             if (j >= rbeg && j < rbeg + rows && tid < nb) ws->rowj[buf][tid] = (double)S[tid * R + (int)(j - rbeg)];
         }
         if (!grid_barrier(&ws->counter, (unsigned)G * (unsigned)(j + 1), spin_ns)) {
@@ -482,8 +492,8 @@ k_panel_smem(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info,
             long long ix = LLONG_MAX;
             int gw = -1;
             for (int q = tid; q < G; q += 32) {
-                const long long qi = __ldcg(&ws->cand_idx[buf][q]);
-                const double qv = __ldcg(&ws->cand_val[buf][q]);
+                const long long qi = __double_as_longlong(__ldcg(&ws->rec[buf][q][1]));
+                const double qv = __ldcg(&ws->rec[buf][q][0]);
                 if (qi != LLONG_MAX && better(qv, qi, v, ix)) { v = qv; ix = qi; gw = q; }
             }
             for (int o = 16; o > 0; o >>= 1) {
@@ -497,7 +507,7 @@ k_panel_smem(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info,
         __syncthreads();
         const long long p = s_p;
         const int gw = s_gw;
-        if (tid < nb) urow[tid] = (T)((gw >= 0) ? __ldcg(&ws->cand_row[buf][gw][tid]) : __ldcg(&ws->rowj[buf][tid]));
+        if (tid < nb) urow[tid] = (T)((gw >= 0) ? __ldcg(&ws->rec[buf][gw][2 + tid]) : __ldcg(&ws->rowj[buf][tid]));
         __syncthreads();
         const T piv = urow[j];
         if (g == 0 && tid == 0) ipiv[r0 + j] = (int32_t)(r0 + p + 1);
@@ -552,8 +562,8 @@ void getf2_panel(Ctx &c, i64 m, i64 nb, T *A, i64 lda, int32_t *ipiv, i64 r0)
     // flops of an m x nb unblocked LU (leading terms): m nb^2 - nb^3/3
     Launch L(c, K_PANEL, (double)m * nb * nb - (double)nb * nb * nb / 3.0,
              2.0 * (double)m * nb * sizeof(T));
+    note(c, cudaMemsetAsync(&ws->counter, 0, sizeof(unsigned), c.s));
     if (R <= PANEL_THREADS) {
-        note(c, cudaMemsetAsync(ws->key, 0, sizeof(ws->key), c.s));
         int nbi = (int)nb, Ri = (int)R;
         const int32_t *abort = c.abort;
         void *args[] = {&m, &nbi, &A, &lda, &ipiv, &r0, &info, &ws, &Ri, &spin, &abort};
@@ -562,10 +572,9 @@ void getf2_panel(Ctx &c, i64 m, i64 nb, T *A, i64 lda, int32_t *ipiv, i64 r0)
         return;
     }
     if ((size_t)R * nb * sizeof(T) > PANEL_SMEM_MAX) { note(c, cudaErrorInvalidValue); return; }
-    note(c, cudaMemsetAsync(&ws->counter, 0, sizeof(unsigned), c.s));
     int Ri = (int)R, nbi = (int)nb;
     const int32_t *abort = c.abort;
-        void *args[] = {&m, &nbi, &A, &lda, &ipiv, &r0, &info, &ws, &Ri, &spin, &abort};
+    void *args[] = {&m, &nbi, &A, &lda, &ipiv, &r0, &info, &ws, &Ri, &spin, &abort};
     note(c, cudaLaunchCooperativeKernel((const void *)k_panel_smem<T>, dim3(G), dim3(PANEL_THREADS), args,
                                         (size_t)R * nb * sizeof(T), c.s));
 }

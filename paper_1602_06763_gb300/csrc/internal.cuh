@@ -49,7 +49,7 @@ void note(Ctx &c, cudaError_t e);
 // Kernel kinds, in the order rl_trace_read reports them.
 enum Kind {
     K_GEMM = 0, K_SYRK, K_TRSM, K_TRMM, K_POTF2, K_TRTI2, K_LAUU2, K_DIAG,
-    K_PANEL, K_LASWP, K_RESID, K_CONVERT, K_MIX, K_BATCH, K_COUNT
+    K_PANEL, K_LASWP, K_RESID, K_CONVERT, K_MIX, K_BATCH, K_FLOW, K_COUNT
 };
 extern std::atomic<int> g_trace_on;
 // Bracket one kernel launch: with tracing on, CUDA events are recorded on the
@@ -126,6 +126,21 @@ template <typename T>
 void laswp(Ctx &c, T *A0, i64 lda, i64 m, i64 c0, i64 ncols, i64 k1, i64 k2, const int32_t *ipiv);
 
 size_t panel_ws_bytes();
+
+// ---- few right-hand sides (flow.cu) -------------------------------------------
+// B(n x nrhs) := op(T)^{-1} B in one dataflow launch: FLOW_LN T = L (lower,
+// unit or not), FLOW_UN T = U (upper, non-unit), FLOW_LT T = L^T (L stored
+// lower, non-unit).  ws: flow_ws_bytes(n, nrhs) of device scratch.  Its
+// first word is a status the caller zeroes (a bounded wait that expires sets
+// RL_INFO_DEVICE_TIMEOUT there and in c.info when given); the ticket and
+// flags after it are zeroed by each call itself (stream-ordered), so one ws
+// serves consecutive calls on one stream.
+enum { FLOW_LN = 0, FLOW_UN = 1, FLOW_LT = 2 };
+constexpr i64 FLOW_MAX_NRHS = 64;
+size_t flow_ws_bytes(i64 n, i64 nrhs);
+template <typename T>
+void trsm_flow(Ctx &c, int form, bool unit, i64 n, i64 nrhs, const T *A, i64 lda, T *B, i64 ldb,
+               void *ws);
 
 // ---- tensor-core GEMM for FP32 storage (tc_gemm.cu) ---------------------------
 // C(m x n) += alpha op(A) op(B) with operands in precision `prec` (TF32,

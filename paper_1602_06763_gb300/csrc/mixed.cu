@@ -46,7 +46,7 @@ struct MixState {
 constexpr int MIX_MAX_NRHS = RES_NR * 64;
 
 struct MixLayout {
-    size_t W, panel, R, D, P, N, S, TC, tc_bytes, total;
+    size_t W, panel, R, D, P, N, S, F, TC, tc_bytes, total;
     i64 ldw, nchunks;
 };
 
@@ -65,6 +65,7 @@ MixLayout layout(i64 n, i64 nrhs, bool lu, int prec)
     L.P = off; off += al((size_t)L.nchunks * RES_NR * (size_t)(n > 0 ? n : 1) * sizeof(double));
     L.N = off; off += al((size_t)NORM_CH * (size_t)(n > 0 ? n : 1) * sizeof(double));
     L.S = off; off += al(sizeof(MixState));
+    L.F = off; off += al(flow_ws_bytes(n, nrhs));
     // packing space of the tensor-core updates: the largest update of either
     // recursion has at most n rows and n/2 + 64 columns and inner dimension
     const i64 h = n / 2 + 64;
@@ -333,16 +334,23 @@ unsigned grid_for(i64 total, unsigned threads)
 
 // FP32 solve of W d = P r (LU) or L L^T d = r (Cholesky) on the nrhs columns
 // of D.
-static void lowprec_solve(Ctx &c, bool lu, i64 n, i64 nrhs, const float *W, i64 ldw,
-                          const int32_t *ipiv, float *D, i64 ldd)
+// X := A^{-1} X from the factors in F (LU with ipiv, or Cholesky L): thin
+// right-hand sides take the one-launch flow solve, wide ones the recursive
+// TRSM.
+template <typename T>
+static void factored_solve(Ctx &c, bool lu, i64 n, i64 nrhs, const T *F, i64 ldf, const int32_t *ipiv,
+                           T *X, i64 ldx, void *flow_ws)
 {
-    if (lu) {
-        laswp<float>(c, D, ldd, n, 0, nrhs, 0, n, ipiv);
-        trsm_lln<float>(c, true, n, nrhs, 1.0f, W, ldw, D, ldd);
-        trsm_lun<float>(c, n, nrhs, 1.0f, W, ldw, D, ldd);
+    if (lu) laswp<T>(c, X, ldx, n, 0, nrhs, 0, n, ipiv);
+    if (nrhs <= FLOW_MAX_NRHS) {
+        trsm_flow<T>(c, FLOW_LN, lu, n, nrhs, F, ldf, X, ldx, flow_ws);
+        trsm_flow<T>(c, lu ? FLOW_UN : FLOW_LT, false, n, nrhs, F, ldf, X, ldx, flow_ws);
+    } else if (lu) {
+        trsm_lln<T>(c, true, n, nrhs, T(1), F, ldf, X, ldx);
+        trsm_lun<T>(c, n, nrhs, T(1), F, ldf, X, ldx);
     } else {
-        trsm_lln<float>(c, false, n, nrhs, 1.0f, W, ldw, D, ldd);
-        trsm_llt<float>(c, n, nrhs, 1.0f, W, ldw, D, ldd);
+        trsm_lln<T>(c, false, n, nrhs, T(1), F, ldf, X, ldx);
+        trsm_llt<T>(c, n, nrhs, T(1), F, ldf, X, ldx);
     }
 }
 
@@ -360,6 +368,7 @@ int mixed_solve(Ctx &c, bool lu, i64 n, i64 nrhs, double *A, i64 lda, int32_t *i
     double *P = reinterpret_cast<double *>(w + Ly.P);
     double *Nn = reinterpret_cast<double *>(w + Ly.N);
     MixState *st = reinterpret_cast<MixState *>(w + Ly.S);
+    void *fws = w + Ly.F;
     const i64 ldw = Ly.ldw, ldr = n, ldd = n;
     int32_t *user_info = c.info;
     const unsigned T256 = 256;
@@ -405,7 +414,7 @@ int mixed_solve(Ctx &c, bool lu, i64 n, i64 nrhs, double *A, i64 lda, int32_t *i
         Launch L(r, K_CONVERT, 0.0, (double)n * nrhs * 12.0);
         k_r_to_f32<<<grid_for(n * nrhs, T256), T256, 0, r.s>>>(n, (int)nrhs, B, ldb, D, ldd, st, r.abort);
     }
-    lowprec_solve(r, lu, n, nrhs, W, ldw, ipiv, D, ldd);
+    factored_solve<float>(r, lu, n, nrhs, W, ldw, ipiv, D, ldd, fws);
     {
         Launch L(r, K_MIX, 0.0, 0.0);
         k_x_update<<<grid_for(n * nrhs, T256), T256, 0, r.s>>>(n, (int)nrhs, D, ldd, X, ldx, 1, r.abort);
@@ -432,7 +441,7 @@ int mixed_solve(Ctx &c, bool lu, i64 n, i64 nrhs, double *A, i64 lda, int32_t *i
             Launch L(r, K_CONVERT, 0.0, (double)n * nrhs * 12.0);
             k_r_to_f32<<<grid_for(n * nrhs, T256), T256, 0, r.s>>>(n, (int)nrhs, R, ldr, D, ldd, st, r.abort);
         }
-        lowprec_solve(r, lu, n, nrhs, W, ldw, ipiv, D, ldd);
+        factored_solve<float>(r, lu, n, nrhs, W, ldw, ipiv, D, ldd, fws);
         {
             Launch L(r, K_MIX, 0.0, 0.0);
             k_x_update<<<grid_for(n * nrhs, T256), T256, 0, r.s>>>(n, (int)nrhs, D, ldd, X, ldx, 0, r.abort);
@@ -451,16 +460,9 @@ int mixed_solve(Ctx &c, bool lu, i64 n, i64 nrhs, double *A, i64 lda, int32_t *i
             Launch L(f, K_MIX, 0.0, 0.0);
             k_copy_b<<<grid_for(n * nrhs, T256), T256, 0, f.s>>>(n, (int)nrhs, B, ldb, X, ldx, f.abort);
         }
-        if (lu) {
-            getrf_rec_t<double>(f, A, lda, n, ipiv, 0, n, n);
-            laswp<double>(f, X, ldx, n, 0, nrhs, 0, n, ipiv);
-            trsm_lln<double>(f, true, n, nrhs, 1.0, A, lda, X, ldx);
-            trsm_lun<double>(f, n, nrhs, 1.0, A, lda, X, ldx);
-        } else {
-            potrf_rec_t<double>(f, n, A, lda, 0);
-            trsm_lln<double>(f, false, n, nrhs, 1.0, A, lda, X, ldx);
-            trsm_llt<double>(f, n, nrhs, 1.0, A, lda, X, ldx);
-        }
+        if (lu) getrf_rec_t<double>(f, A, lda, n, ipiv, 0, n, n);
+        else potrf_rec_t<double>(f, n, A, lda, 0);
+        factored_solve<double>(f, lu, n, nrhs, A, lda, ipiv, X, ldx, fws);
         if (f.err != cudaSuccess && c.err == cudaSuccess) c.err = f.err;
     }
     { Launch L(c, K_MIX, 0.0, 0.0); k_mix_finish<<<1, 1, 0, c.s>>>(st, maxiter, iter); }

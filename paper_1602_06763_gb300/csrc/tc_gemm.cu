@@ -146,41 +146,43 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// NSPLIT operand planes per side (1, or 2 for the hi/lo split); NMMA MMAs per
-// k-chunk (1, or 3 for hi*hi + hi*lo + lo*hi).
+// Persistent tensor-core GEMM.  CTA b takes tiles b, b + gridDim.x, ...
+// (row tiles fastest, so CTAs running at the same time share the B tile).
+// NSPLIT operand planes per side (1, or 2 for the hi/lo split: three MMAs
+// hi*hi + hi*lo + lo*hi per k-chunk).  The accumulator is double-buffered in
+// TMEM (2 x 256 columns): the MMA warp fills one buffer while the epilogue
+// warps drain the other, so a tile's read-modify-write of C overlaps the
+// next tile's main loop.
 // FMT: operand format of the instruction descriptor (0 FP16, 1 BF16, 2 TF32).
 template <int FMT, int NSPLIT, int STAGES, bool LOWER>
 __global__ void __launch_bounds__(THREADS, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
           const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
-          int m, int n, int nkb, float alpha, float *C, i64 ldc, int tiles_m, int32_t *err,
-          long long limit_ns, const int32_t *abort)
+          int m, int n, int nkb, float alpha, float *C, i64 ldc, int tiles_m, int tiles_total,
+          int32_t *err, long long limit_ns, const int32_t *abort)
 {
     constexpr bool F16KIND = FMT < 2;
+    constexpr int STAGE = NSPLIT * (A_TILE + B_TILE);
     if (abort && *abort != 0) return;
-    const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
-    const int m0 = tm * BM, n0 = tn * BN;
-    // lower-triangle updates: a tile entirely above the diagonal has no work
-    if (LOWER && m0 + BM <= n0) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment of the stage ring
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int STAGE = NSPLIT * (A_TILE + B_TILE);
-    __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+    __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], tfull[2], tempty[2], final_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int s_err;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
-        mbar_init(&done_bar, 1);
+        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
+        mbar_init(&final_bar, 1);
         s_err = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
-                     "r"(TMEM_COLS));
+                     "r"(2 * TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -188,82 +190,122 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
+    // lower-triangle updates: tiles entirely above the diagonal have no work
+    // (every role applies the same rule, so all see the same tile sequence)
+    auto skip = [&](int t) {
+        const int tm = t % tiles_m, tn = t / tiles_m;
+        return LOWER && tm * BM + BM <= tn * BN;
+    };
+
     if (warp == 0) {
         if (lane == 0) {
-            // producer
-            int issued = 0;
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % STAGES;
-                const uint32_t par = ((kb / STAGES) & 1) ^ 1;
-                if (!mbar_wait(&empty_bar[s], par, limit_ns)) { atomicExch(&s_err, 1); break; }
-                if (s_err) break;
-                unsigned char *st = base + s * STAGE;
-                mbar_expect_tx(&full_bar[s], STAGE);
-                // K coordinate in elements: 128 bytes per stage
-                const int kx = kb * (F16KIND ? 64 : 32);
-                tma_load_2d(st, &mA0, &full_bar[s], kx, m0);
-                tma_load_2d(st + A_TILE, &mB0, &full_bar[s], kx, n0);
-                if (NSPLIT == 2) {
-                    tma_load_2d(st + A_TILE + B_TILE, &mA1, &full_bar[s], kx, m0);
-                    tma_load_2d(st + 2 * A_TILE + B_TILE, &mB1, &full_bar[s], kx, n0);
+            int g = 0;                                  // ring position across tiles
+            bool fail = false;
+            for (int t = blockIdx.x; t < tiles_total && !fail; t += gridDim.x) {
+                if (skip(t)) continue;
+                const int m0 = (t % tiles_m) * BM, n0 = (t / tiles_m) * BN;
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = g % STAGES;
+                    if (!mbar_wait(&empty_bar[s], ((g / STAGES) & 1) ^ 1, limit_ns) || s_err) {
+                        atomicExch(&s_err, 1);
+                        fail = true;
+                        break;
+                    }
+                    unsigned char *st = base + s * STAGE;
+                    mbar_expect_tx(&full_bar[s], STAGE);
+                    const int kx = kb * (F16KIND ? 64 : 32);   // 128 bytes of K per stage
+                    tma_load_2d(st, &mA0, &full_bar[s], kx, m0);
+                    tma_load_2d(st + A_TILE, &mB0, &full_bar[s], kx, n0);
+                    if (NSPLIT == 2) {
+                        tma_load_2d(st + A_TILE + B_TILE, &mA1, &full_bar[s], kx, m0);
+                        tma_load_2d(st + 2 * A_TILE + B_TILE, &mB1, &full_bar[s], kx, n0);
+                    }
                 }
-                ++issued;
             }
             // drain: every issued copy has landed before the CTA can exit
-            for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-                (void)mbar_wait(&full_bar[kb % STAGES], (kb / STAGES) & 1, limit_ns);
+            for (int gg = (g > STAGES ? g - STAGES : 0); gg < g; ++gg)
+                (void)mbar_wait(&full_bar[gg % STAGES], (gg / STAGES) & 1, limit_ns);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t ID = idesc((uint32_t)FMT, BM, BN);
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % STAGES;
-                if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1, limit_ns)) { atomicExch(&s_err, 1); break; }
+            int g = 0, i = 0;
+            bool fail = false;
+            for (int t = blockIdx.x; t < tiles_total && !fail; t += gridDim.x) {
+                if (skip(t)) continue;
+                const int b = i & 1;
+                if (!mbar_wait(&tempty[b], ((i >> 1) & 1) ^ 1, limit_ns)) { atomicExch(&s_err, 1); break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t sa = su32(base + s * STAGE);
-                const uint32_t sb = sa + A_TILE;
-#pragma unroll
-                for (int kk = 0; kk < KB / 32; ++kk) {
-                    const uint32_t acc = (kb | kk) ? 1u : 0u;
-                    mma<F16KIND>(tmem, sdesc(sa + kk * 32), sdesc(sb + kk * 32), ID, acc);
-                    if (NSPLIT == 2) {
-                        const uint32_t sa1 = sa + A_TILE + B_TILE, sb1 = sa + 2 * A_TILE + B_TILE;
-                        mma<F16KIND>(tmem, sdesc(sa + kk * 32), sdesc(sb1 + kk * 32), ID, 1u);
-                        mma<F16KIND>(tmem, sdesc(sa1 + kk * 32), sdesc(sb + kk * 32), ID, 1u);
+                const uint32_t d = tmem + (uint32_t)(b * TMEM_COLS);
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = g % STAGES;
+                    if (!mbar_wait(&full_bar[s], (g / STAGES) & 1, limit_ns)) {
+                        atomicExch(&s_err, 1);
+                        fail = true;
+                        break;
                     }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = su32(base + s * STAGE);
+                    const uint32_t sb = sa + A_TILE;
+#pragma unroll
+                    for (int kk = 0; kk < KB / 32; ++kk) {
+                        const uint32_t acc = (kb | kk) ? 1u : 0u;
+                        mma<F16KIND>(d, sdesc(sa + kk * 32), sdesc(sb + kk * 32), ID, acc);
+                        if (NSPLIT == 2) {
+                            const uint32_t sa1 = sa + A_TILE + B_TILE, sb1 = sa + 2 * A_TILE + B_TILE;
+                            mma<F16KIND>(d, sdesc(sa + kk * 32), sdesc(sb1 + kk * 32), ID, 1u);
+                            mma<F16KIND>(d, sdesc(sa1 + kk * 32), sdesc(sb + kk * 32), ID, 1u);
+                        }
+                    }
+                    mma_commit(&empty_bar[s]);
                 }
-                mma_commit(&empty_bar[s]);
+                if (!fail) mma_commit(&tfull[b]);
+                ++i;
             }
-            mma_commit(&done_bar);
+            // every issued MMA has completed before TMEM can be released
+            mma_commit(&final_bar);
+            (void)mbar_wait(&final_bar, 0, limit_ns);
         }
     } else {
         // epilogue: warps 2..5 -> TMEM lane quarters (warp % 4)
         const int q = warp & 3;
-        const int row = m0 + q * 32 + lane;
-        if (!mbar_wait(&done_bar, 0, limit_ns)) atomicExch(&s_err, 1);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!s_err && nkb > 0) {
+        int i = 0;
+        for (int t = blockIdx.x; t < tiles_total; t += gridDim.x) {
+            if (skip(t)) continue;
+            const int b = i & 1;
+            const int m0 = (t % tiles_m) * BM, n0 = (t / tiles_m) * BN;
+            const int row = m0 + q * 32 + lane;
+            if (!mbar_wait(&tfull[b], (i >> 1) & 1, limit_ns)) atomicExch(&s_err, 1);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (s_err) break;
             for (int c = 0; c < BN; c += 16) {
                 float v[16];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TMEM_COLS + c), v);
                 if (row < m) {
+                    float old[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int col = n0 + c + j;
-                        if (col < n && (!LOWER || row >= col)) {
-                            float *cp = C + (i64)col * ldc + row;
-                            *cp = fmaf(alpha, v[j], *cp);
-                        }
+                        old[j] = (col < n && (!LOWER || row >= col)) ? C[(i64)col * ldc + row] : 0.0f;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = n0 + c + j;
+                        if (col < n && (!LOWER || row >= col)) C[(i64)col * ldc + row] = fmaf(alpha, v[j], old[j]);
                     }
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tempty[b])) : "memory");
+            ++i;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS));
     }
     if (threadIdx.x == 0 && s_err && err) atomicExch(err, RL_INFO_DEVICE_TIMEOUT);
 }
@@ -365,8 +407,8 @@ size_t tc_work_bytes(i64 m, i64 n, i64 k, int prec)
 template <int FMT, int NSPLIT, int STAGES, bool LOWER>
 static cudaError_t launch_tc(const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
                              const CUtensorMap &b1, int m, int n, int nkb, float alpha, float *C, i64 ldc,
-                             int tiles_m, unsigned grid, int32_t *err, long long lim, const int32_t *abort,
-                             cudaStream_t s)
+                             int tiles_m, int tiles_total, unsigned grid, int32_t *err, long long lim,
+                             const int32_t *abort, cudaStream_t s)
 {
     auto kern = tc::k_tc_gemm<FMT, NSPLIT, STAGES, LOWER>;
     const int smem = STAGES * NSPLIT * (tc::A_TILE + tc::B_TILE) + 1024;
@@ -376,7 +418,8 @@ static cudaError_t launch_tc(const CUtensorMap &a0, const CUtensorMap &a1, const
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    kern<<<grid, tc::THREADS, smem, s>>>(a0, a1, b0, b1, m, n, nkb, alpha, C, ldc, tiles_m, err, lim, abort);
+    kern<<<grid, tc::THREADS, smem, s>>>(a0, a1, b0, b1, m, n, nkb, alpha, C, ldc, tiles_m, tiles_total, err,
+                                         lim, abort);
     return cudaGetLastError();
 }
 
@@ -437,18 +480,19 @@ bool tc_gemm(Ctx &c, int prec, bool ta, bool tb, i64 m, i64 n, i64 k, float alph
     if (!ok) { note(c, cudaErrorInvalidValue); return true; }
     const int nkb = (int)(kp / (tc::KB / esz));
     const int tiles_m = (int)(mp / tc::BM), tiles_n = (int)(np / tc::BN);
-    // lower-triangle updates launch the full tile grid; tiles entirely above
-    // the diagonal return at once and diagonal tiles mask their stores
-    const unsigned grid = (unsigned)(tiles_m * tiles_n);
+    // persistent CTAs (one per SM) walk the tile list; lower-triangle updates
+    // skip the tiles above the diagonal and mask the diagonal ones
+    const int tiles_total = tiles_m * tiles_n;
+    const unsigned grid = (unsigned)(tiles_total < c.num_sms ? tiles_total : c.num_sms);
     const double flops = lower ? (double)k * n * (n + 1) : 2.0 * m * n * k;
     Launch L(c, lower ? K_SYRK : K_GEMM, flops, 0.0);
     cudaError_t e;
     const long long lim = g_params.spin_ns;
-#define RL_TC(FMT, NS, ST)                                                                                    \
-    (lower ? launch_tc<FMT, NS, ST, true>(a0, a1, b0, b1, (int)m, (int)n, nkb, alpha, C, ldc, tiles_m, grid,  \
-                                          c.info, lim, c.abort, c.s)                                        \
-           : launch_tc<FMT, NS, ST, false>(a0, a1, b0, b1, (int)m, (int)n, nkb, alpha, C, ldc, tiles_m, grid, \
-                                           c.info, lim, c.abort, c.s))
+#define RL_TC(FMT, NS, ST)                                                                              \
+    (lower ? launch_tc<FMT, NS, ST, true>(a0, a1, b0, b1, (int)m, (int)n, nkb, alpha, C, ldc, tiles_m,   \
+                                          tiles_total, grid, c.info, lim, c.abort, c.s)               \
+           : launch_tc<FMT, NS, ST, false>(a0, a1, b0, b1, (int)m, (int)n, nkb, alpha, C, ldc, tiles_m,  \
+                                           tiles_total, grid, c.info, lim, c.abort, c.s))
     if (prec == RL_PREC_FP16S) e = RL_TC(0, 1, 4);
     else if (prec == RL_PREC_BF16) e = RL_TC(1, 1, 4);
     else if (split == 2) e = RL_TC(2, 2, 2);

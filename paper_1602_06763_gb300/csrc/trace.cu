@@ -31,7 +31,8 @@ Totals g_tot[K_COUNT];
 
 const char *kKindNames[K_COUNT] = {"gemm", "syrk", "trsm_base", "trmm_base", "potf2",
                                    "trti2", "lauu2", "diag_scan", "getf2_panel", "laswp",
-                                   "fp64_residual", "convert", "refine_control", "batched"};
+                                   "fp64_residual", "convert", "refine_control", "batched",
+                                   "trsm_flow"};
 
 cudaEvent_t take_event()
 {

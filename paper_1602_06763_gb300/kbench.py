@@ -24,7 +24,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", required=True,
                     choices=["dgemm", "dsyrk", "dtrsm", "potrf", "getrf", "trtri", "lauum", "panel",
-                             "sgemm_tc", "dsgesv", "dsposv"])
+                             "sgemm_tc", "dsgesv", "dsposv", "getrs", "potrs", "sgetrs"])
     ap.add_argument("--prec", type=int, default=1, help="operand precision (rl_prec) of sgemm_tc / dsgesv")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--cond", type=float, default=1e6)
@@ -36,6 +36,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--trace", action="store_true")
+    ap.add_argument("--flow", type=int, default=1, help="getrs/potrs: 1 = one-launch flow solve, 0 = recursive")
     a = ap.parse_args()
 
     if a.nb:
@@ -71,6 +72,33 @@ def main():
         else:
             run = lambda: r.check(r.rl_dsgesv(n, a.nrhs, A, n, ipiv, B, n, X, n, a.prec, 1e-14, 30, it, info,
                                               work, lw, s))
+    elif a.case in ("getrs", "potrs", "sgetrs"):
+        # factors computed once, untimed; the solve of nrhs columns is timed
+        dt = torch.float32 if a.case == "sgetrs" else torch.float64
+        A = torch.rand(n, n, generator=g, device=dev, dtype=torch.float64) * 2 - 1
+        lw = r.rl_dgetrf_work_size(n, n)
+        work = torch.empty(lw, dtype=torch.uint8, device=dev)
+        ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+        if a.case == "potrs":
+            A = A @ A.T
+            A.diagonal().add_(float(n))
+            r.check(r.rl_dpotrf("L", n, A, n, info, None, 0, s))
+        else:
+            A = A.to(dt)
+            f = r.rl_sgetrf if dt == torch.float32 else r.rl_dgetrf
+            r.check(f(n, n, A, n, ipiv, info, work, lw, s))
+        B0 = torch.randn(a.nrhs, n, generator=g, device=dev, dtype=torch.float64).to(dt)
+        B = B0.clone()
+        ltw = r.rl_trs_work_size(n, a.nrhs) if a.flow else 0
+        tw = torch.zeros(max(ltw, 1), dtype=torch.uint8, device=dev) if ltw else None
+        flops = 2.0 * n * n * a.nrhs
+        restore = lambda: B.copy_(B0)
+        if a.case == "potrs":
+            run = lambda: r.check(r.rl_dpotrs("L", n, a.nrhs, A, n, B, n, tw, ltw, s))
+        elif a.case == "getrs":
+            run = lambda: r.check(r.rl_dgetrs("N", n, a.nrhs, A, n, ipiv, B, n, tw, ltw, s))
+        else:
+            run = lambda: r.check(r.rl_sgetrs("N", n, a.nrhs, A, n, ipiv, B, n, tw, ltw, s))
     elif a.case == "sgemm_tc":
         A = torch.rand(k, n, generator=g, device=dev, dtype=torch.float32)
         B = torch.rand(n, k, generator=g, device=dev, dtype=torch.float32)

@@ -49,8 +49,9 @@ _SIGS = {
                                 _i64, _vp]),
     "rl_dtrmm": (ctypes.c_int, [_ch, _ch, _ch, _ch, _i64, _i64, ctypes.c_double, _vp, _i64, _vp,
                                 _i64, _vp]),
-    "rl_dgetrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp]),
-    "rl_dpotrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _i64, _vp]),
+    "rl_trs_work_size": (ctypes.c_size_t, [_i64, _i64]),
+    "rl_dgetrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _sz, _vp]),
+    "rl_dpotrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
     "rl_dsgesv_work_size": (_sz, [_i64, _i64, ctypes.c_int]),
     "rl_dsposv_work_size": (_sz, [_i64, _i64, ctypes.c_int]),
     "rl_dsgesv": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, ctypes.c_int,
@@ -66,6 +67,10 @@ _SIGS = {
     "rl_spotrf_vbatched": (ctypes.c_int, [_ch, _i64, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _sz, _vp]),
     "rl_dgetrf_vbatched": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _sz, _vp]),
     "rl_sgetrf_vbatched": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _sz, _vp]),
+    "rl_spotrf": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_sgetrf": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
+    "rl_sgetrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _sz, _vp]),
+    "rl_spotrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
     "rl_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "rl_trace_kinds": (ctypes.c_int, []),
     "rl_trace_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
@@ -167,12 +172,17 @@ def rl_dtrmm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream=None)
                          _ptr(B), ldb, _stream(stream))
 
 
-def rl_dgetrs(trans, n, nrhs, A, lda, ipiv, B, ldb, stream=None):
-    return _lib.rl_dgetrs(_c(trans), n, nrhs, _ptr(A), lda, _ptr(ipiv), _ptr(B), ldb, _stream(stream))
+def rl_trs_work_size(n, nrhs):
+    return int(_lib.rl_trs_work_size(n, nrhs))
 
 
-def rl_dpotrs(uplo, n, nrhs, A, lda, B, ldb, stream=None):
-    return _lib.rl_dpotrs(_c(uplo), n, nrhs, _ptr(A), lda, _ptr(B), ldb, _stream(stream))
+def rl_dgetrs(trans, n, nrhs, A, lda, ipiv, B, ldb, work=None, lwork=0, stream=None):
+    return _lib.rl_dgetrs(_c(trans), n, nrhs, _ptr(A), lda, _ptr(ipiv), _ptr(B), ldb, _ptr(work), lwork,
+                           _stream(stream))
+
+
+def rl_dpotrs(uplo, n, nrhs, A, lda, B, ldb, work=None, lwork=0, stream=None):
+    return _lib.rl_dpotrs(_c(uplo), n, nrhs, _ptr(A), lda, _ptr(B), ldb, _ptr(work), lwork, _stream(stream))
 
 
 def rl_dsgesv_work_size(n, nrhs, prec):
@@ -231,6 +241,23 @@ def rl_dgetrf_vbatched(batch, n, A, lda, ipiv, info, max_n, work, lwork, stream=
 def rl_sgetrf_vbatched(batch, n, A, lda, ipiv, info, max_n, work, lwork, stream=None):
     return _lib.rl_sgetrf_vbatched(batch, _ptr(n), _ptr(A), _ptr(lda), _ptr(ipiv), _ptr(info), max_n,
                                    _ptr(work), lwork, _stream(stream))
+
+
+def rl_spotrf(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
+    return _lib.rl_spotrf(_c(uplo), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_sgetrf(m, n, A, lda, ipiv, info, work, lwork, stream=None):
+    return _lib.rl_sgetrf(m, n, _ptr(A), lda, _ptr(ipiv), _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_sgetrs(trans, n, nrhs, A, lda, ipiv, B, ldb, work=None, lwork=0, stream=None):
+    return _lib.rl_sgetrs(_c(trans), n, nrhs, _ptr(A), lda, _ptr(ipiv), _ptr(B), ldb, _ptr(work), lwork,
+                           _stream(stream))
+
+
+def rl_spotrs(uplo, n, nrhs, A, lda, B, ldb, work=None, lwork=0, stream=None):
+    return _lib.rl_spotrs(_c(uplo), n, nrhs, _ptr(A), lda, _ptr(B), ldb, _ptr(work), lwork, _stream(stream))
 
 
 def rl_host_work_size(routine, m, n, lda):

@@ -23,7 +23,8 @@ rank, world = dist.get_rank(), dist.get_world_size()
 ms = 100.0 + 50.0 * rank            # rank 1 is the slow replica
 m = bench.max_over_ranks(ms, world, "cpu")
 v = bench.aggregate_gflops(1e9, m, world)
-print(json.dumps({{"rank": rank, "max": m, "value": v}}), flush=True)
+with open(os.path.join({out!r}, "rank%d.json" % rank), "w") as f:   # one file per rank: no interleaving
+    json.dump({{"rank": rank, "max": m, "value": v}}, f)
 dist.destroy_process_group()
 """
 
@@ -40,11 +41,11 @@ def _torchrun(args, env_extra=None, timeout=300):
 
 def test_max_over_ranks_and_aggregate_gloo(tmp_path):
     script = tmp_path / "worker.py"
-    script.write_text(WORKER.format(root=ROOT))
+    script.write_text(WORKER.format(root=ROOT, out=str(tmp_path)))
     r = _torchrun([str(script)])
     assert r.returncode == 0, r.stderr[-2000:]
-    lines = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
-    assert len(lines) == 2
+    lines = [json.loads((tmp_path / ("rank%d.json" % k)).read_text()) for k in range(2)]
+    assert [l["rank"] for l in lines] == [0, 1]
     for l in lines:
         assert l["max"] == 150.0
         assert l["value"] == pytest.approx(2 * 1e9 / 0.150 / 1e9)

@@ -131,22 +131,48 @@ def test_mixed_unsupported_precision():
     assert r.rl_dsgesv(4, 1, p, 4, p, p, 4, p, 4, 99, 1e-14, 10, p, p, p, 1 << 30) == r.RL_ERR_UNSUPPORTED
 
 
-@pytest.mark.parametrize("n,nrhs", [(1, 1), (130, 7), (513, 20)])
-def test_getrs_potrs_vs_oracle(n, nrhs):
+def _trs_work(n, nrhs, use_work):
+    """(work tensor, lwork) for the solves: None selects the recursive TRSM,
+    a buffer the one-launch flow solve (nrhs <= 64)."""
+    r = G.lib()
+    if not use_work:
+        return None, 0
+    lw = max(r.rl_trs_work_size(n, nrhs), 256)
+    return G.torch().full((lw,), 0x5A, dtype=G.torch().uint8, device="cuda"), lw
+
+
+@pytest.mark.parametrize("use_work", [False, True])
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (63, 16), (64, 17), (130, 7), (513, 20), (1100, 64), (700, 65)])
+def test_getrs_potrs_vs_oracle(n, nrhs, use_work):
     r = G.lib()
     A = inputs.uniform(n, n, seed=inputs.seed_for(2, 50 + n))
     B = inputs.normal(n, nrhs, seed=inputs.seed_for(2, 60 + n))
     F, ipiv, info = G.getrf(A)
     dF, dB = G.DevMat(F), G.DevMat(B, lda=n + 1)
     dp = G.torch().from_numpy(ipiv.astype(np.int32)).cuda()
-    assert r.rl_dgetrs("N", n, nrhs, dF.ptr(), dF.lda, dp.data_ptr(), dB.ptr(), dB.lda) == 0
+    w, lw = _trs_work(n, nrhs, use_work)
+    assert r.rl_dgetrs("N", n, nrhs, dF.ptr(), dF.lda, dp.data_ptr(), dB.ptr(), dB.lda, w, lw) == 0
     G.sync()
     X = dB.get()
     assert dB.canaries_intact()
+    if w is not None and nrhs <= 64:
+        assert int(w[:4].view(G.torch().int32)[0]) == 0        # status word: no wait expired
     assert oracle.backward_error(A, X, B) <= 10 * n * EPS
     S = inputs.spd_bbt(n, seed=inputs.seed_for(2, 70 + n))
     L, info = G.potrf(S)
     dL, dB = G.DevMat(L), G.DevMat(B)
-    assert r.rl_dpotrs("L", n, nrhs, dL.ptr(), dL.lda, dB.ptr(), dB.lda) == 0
+    assert r.rl_dpotrs("L", n, nrhs, dL.ptr(), dL.lda, dB.ptr(), dB.lda, w, lw) == 0
     G.sync()
+    assert dB.canaries_intact()
     assert oracle.backward_error(S, dB.get(), B) <= 10 * n * EPS
+
+
+def test_trs_workspace_too_small():
+    r = G.lib()
+    t = G.torch()
+    n, nrhs = 300, 8
+    buf = t.zeros(n * n, dtype=t.float64, device="cuda")
+    lw = r.rl_trs_work_size(n, nrhs)
+    assert lw > 0 and r.rl_trs_work_size(n, 65) == 0
+    w = t.zeros(lw, dtype=t.uint8, device="cuda")
+    assert r.rl_dpotrs("L", n, nrhs, buf, n, buf, n, w, lw - 1) == r.RL_ERR_WORKSPACE

@@ -1,0 +1,93 @@
+"""Single-precision peers (rl_spotrf / rl_sgetrf / rl_sgetrs / rl_spotrs)
+against the oracle: residuals measured in units of the FP32 rounding unit
+2^-24 (<= 10), ipiv equal to the oracle's on the FP32-rounded input up to
+the first near-tie, exact inputs bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1602_06763_gb300 import inputs
+
+from . import gpu_util as G
+
+pytestmark = pytest.mark.gpu
+SCALE = 2.0 ** -53 / 2.0 ** -24     # oracle metrics use 2^-53
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    yield
+
+
+def to_dev32(A):
+    t = G.torch()
+    return t.from_numpy(np.asfortranarray(A, dtype=np.float32).ravel(order="F").copy()).cuda()
+
+
+def from_dev32(d, m, n):
+    return np.asfortranarray(d.cpu().numpy().reshape(n, m).T.astype(np.float64))
+
+
+@pytest.mark.parametrize("n", [1, 33, 200, 700])
+def test_spotrf_sgetrf_vs_oracle(n):
+    r = G.lib()
+    t = G.torch()
+    A = inputs.spd_bbt(n, seed=inputs.seed_for(1, 3000 + n)).astype(np.float32).astype(np.float64)
+    dA = to_dev32(A)
+    info = G.int_buf(1, -7)
+    assert r.rl_spotrf("L", n, dA.data_ptr(), n, info.data_ptr()) == 0
+    G.sync()
+    assert int(info[0]) == 0
+    L = from_dev32(dA, n, n)
+    assert oracle.res_chol(A, L) * SCALE <= 10.0
+    Gm = inputs.uniform(n, n, seed=inputs.seed_for(1, 3100 + n)).astype(np.float32).astype(np.float64)
+    dG = to_dev32(Gm)
+    ipiv = G.int_buf(n, -5)
+    lw = r.rl_dgetrf_work_size(n, n)
+    work = t.empty(lw, dtype=t.uint8, device="cuda")
+    assert r.rl_sgetrf(n, n, dG.data_ptr(), n, ipiv.data_ptr(), info.data_ptr(), work.data_ptr(), lw) == 0
+    G.sync()
+    F = from_dev32(dG, n, n)
+    piv = ipiv.cpu().numpy()[:n]
+    assert int(info[0]) == 0
+    assert oracle.res_lu(Gm, F, piv) * SCALE <= 10.0
+    # solves: recursive TRSM (no workspace) and the one-launch flow solve
+    B = inputs.normal(n, 3, seed=inputs.seed_for(1, 3200 + n)).astype(np.float32).astype(np.float64)
+    for use_work in (False, True):
+        lw = r.rl_trs_work_size(n, 3) if use_work else 0
+        w = t.zeros(lw, dtype=t.uint8, device="cuda") if use_work else None
+        dB = to_dev32(B)
+        assert r.rl_sgetrs("N", n, 3, dG.data_ptr(), n, ipiv.data_ptr(), dB.data_ptr(), n, w, lw) == 0
+        G.sync()
+        X = from_dev32(dB, n, 3)
+        assert oracle.backward_error(Gm, X, B) <= 10 * n * 2.0 ** -24
+        dB = to_dev32(B)
+        assert r.rl_spotrs("L", n, 3, dA.data_ptr(), n, dB.data_ptr(), n, w, lw) == 0
+        G.sync()
+        assert oracle.backward_error(A, from_dev32(dB, n, 3), B) <= 10 * n * 2.0 ** -24
+
+
+def test_single_exact_inputs():
+    r = G.lib()
+    t = G.torch()
+    n = 150
+    L = inputs.integer_chol(n, seed=inputs.seed_for(1, 3300), offdiag=1, diag=(1, 2))
+    A = inputs.product_lower(L)
+    dA = to_dev32(A)
+    info = G.int_buf(1, -7)
+    assert r.rl_spotrf("L", n, dA.data_ptr(), n, info.data_ptr()) == 0
+    G.sync()
+    assert np.array_equal(np.tril(from_dev32(dA, n, n)), L)
+    A, Lx, U, perm = inputs.dyadic_lu(n, seed=inputs.seed_for(1, 3400))
+    dA = to_dev32(A)
+    ipiv = G.int_buf(n, -5)
+    lw = r.rl_dgetrf_work_size(n, n)
+    work = t.empty(lw, dtype=t.uint8, device="cuda")
+    assert r.rl_sgetrf(n, n, dA.data_ptr(), n, ipiv.data_ptr(), info.data_ptr(), work.data_ptr(), lw) == 0
+    G.sync()
+    F = from_dev32(dA, n, n)
+    assert np.array_equal(ipiv.cpu().numpy()[:n], inputs.expected_ipiv(perm))
+    assert np.array_equal(np.tril(F, -1) + np.eye(n), Lx) and np.array_equal(np.triu(F), U)
