@@ -267,6 +267,29 @@ int rl_sgetrf_vbatched(int64_t batch, const int32_t *n, float *const *A, const i
                        size_t lwork, rl_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * rl_dgetrf_vbatched_noalloc -- rl_dgetrf_vbatched without a workspace
+ * argument.  The paper has no counterpart: it is a calling convention for
+ * callers that cannot allocate device memory where they call (a cudaMalloc
+ * there would synchronize the device or is not permitted, e.g. inside a
+ * latency-critical loop or a host without its own device allocator).
+ * Arguments and results are those of rl_dgetrf_vbatched (argument 1 batch,
+ * 2 n, 3 A, 4 lda, 5 ipiv, 6 info, 7 max_n).
+ * Scratch: a library-owned static device array of 256 + 4 * 65536 bytes
+ *   (262,400 B) per device; batch > 65536 returns RL_ERR_UNSUPPORTED before
+ *   any device work.  The first call on a device resolves the array's
+ *   device address (set-up done once per device, with that device current),
+ *   so make the first call before any stream capture.
+ * Every call on a device shares the array: calls that may overlap in time
+ *   (different streams, or host threads without ordering) race on it and
+ *   must be serialized by the caller.  Nothing in it needs to start at zero
+ *   (each call rewrites the order list and resets its work counter).
+ * Allocates nothing (no cudaMalloc / cudaFree, no allocating library call).
+ * ------------------------------------------------------------------------- */
+int rl_dgetrf_vbatched_noalloc(int64_t batch, const int32_t *n, double *const *A,
+                               const int32_t *lda, int32_t *const *ipiv, int32_t *info,
+                               int32_t max_n, rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Tensor-core GEMM on FP32 storage (the update kernel of the precision
  * form): C(m x n) := C + alpha op(A) op(B), A, B, C single precision,
  * column-major, products in `prec` (RL_PREC_TF32, _BF16, _FP16S, _TF32X3) on

@@ -67,6 +67,7 @@ _SIGS = {
     "rl_spotrf_vbatched": (ctypes.c_int, [_ch, _i64, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _sz, _vp]),
     "rl_dgetrf_vbatched": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _sz, _vp]),
     "rl_sgetrf_vbatched": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _sz, _vp]),
+    "rl_dgetrf_vbatched_noalloc": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp]),
     "rl_spotrf": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
     "rl_sgetrf": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
     "rl_sgetrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _sz, _vp]),
@@ -241,6 +242,14 @@ def rl_dgetrf_vbatched(batch, n, A, lda, ipiv, info, max_n, work, lwork, stream=
 def rl_sgetrf_vbatched(batch, n, A, lda, ipiv, info, max_n, work, lwork, stream=None):
     return _lib.rl_sgetrf_vbatched(batch, _ptr(n), _ptr(A), _ptr(lda), _ptr(ipiv), _ptr(info), max_n,
                                    _ptr(work), lwork, _stream(stream))
+
+
+def rl_dgetrf_vbatched_noalloc(batch, n, A, lda, ipiv, info, max_n, stream=None):
+    """rl_dgetrf_vbatched with the library's static scratch (no workspace
+    argument, nothing allocated): for callers that cannot allocate device
+    memory at the call; overlapping calls on one device race on the scratch."""
+    return _lib.rl_dgetrf_vbatched_noalloc(batch, _ptr(n), _ptr(A), _ptr(lda), _ptr(ipiv), _ptr(info), max_n,
+                                           _stream(stream))
 
 
 def rl_spotrf(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
