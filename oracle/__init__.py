@@ -55,6 +55,7 @@ def _lib():
             "or_potri": (_i64, [_i64, _ptr, _i64, _i64]),
             "or_getrs": (None, [_i64, _i64, _ptr, _i64, _ptr, _ptr, _i64]),
             "or_potrs": (None, [_i64, _i64, _ptr, _i64, _ptr, _i64]),
+            "or_sygst": (_i64, [ctypes.c_int, _i64, _ptr, _i64, _ptr, _i64]),
             "or_gemm": (None, [ctypes.c_int, ctypes.c_int, _i64, _i64, _i64, _dbl,
                                _ptr, _i64, _ptr, _i64, _ptr, _i64]),
             "or_syrk_lower": (None, [ctypes.c_int, _i64, _i64, _dbl, _ptr, _i64, _ptr, _i64]),
@@ -262,6 +263,17 @@ def potrs(L, B):
         B = B.reshape(-1, 1, order="F")
     _lib().or_potrs(L.shape[0], B.shape[1], _p(L), _ld(L), _p(B), _ld(B))
     return B
+
+
+def sygst(itype, A, L):
+    """itype 1: L^{-1} A L^{-T}; itype 2/3: L^T A L (A symmetric, lower triangle
+    read and written; the strictly upper part of the result is A's)."""
+    A = _f64(A)
+    L = _f64(L, copy=False) if np.asarray(L).flags.f_contiguous else _f64(L)
+    rc = _lib().or_sygst(int(itype), A.shape[0], _p(A), _ld(A), _p(L), _ld(L))
+    if rc != 0:
+        raise ValueError("or_sygst failed: %d" % rc)
+    return A
 
 
 def _ro(a):

@@ -27,6 +27,8 @@
  *   or_getrf        Section 5, xgetrf (P L U := A, row pivoting); Section 3
  *                   halving scheme with unblocked getf2 as base case
  *   or_laswp        the row interchanges P of xgetrf
+ *   or_sygst        Section 5, xsygst (A := L^{-1} A L^{-T}, or L^T A L):
+ *                   the definition, by substitution and products
  *   metrics         normwise backward errors used by the benchmark spec's bound
  *                   ||A - LL^T|| / (n eps ||A||) <= 10, computed with the
  *                   compensated dot product Dot2 of Ogita, Rump & Oishi (2005)
@@ -484,6 +486,73 @@ void or_potrs(int64_t n, int64_t nrhs, const double *L, int64_t lda,
 {
     or_trsm_llnx(0, n, nrhs, 1.0, L, lda, B, ldb);
     or_trsm_lltn(n, nrhs, L, lda, B, ldb);
+}
+
+/* -------------------------------------------------------------------------- */
+/* sygst (Section 5, xsygst): reduction of the symmetric-definite generalized */
+/* problem to standard form with the Cholesky factor L of B, by definition:   */
+/*   itype 1:    A := L^{-1} A L^{-T}                                         */
+/*   itype 2, 3: A := L^T A L                                                 */
+/* A is symmetric with its lower triangle stored; only that triangle is read */
+/* and written.  Written out plainly on a full mirrored copy W:               */
+/*   itype 1: W := L^{-1} W by forward substitution down each column, then    */
+/*            W := W L^{-T} by forward substitution along each row;           */
+/*   itype 2: W := W L (each row times L), then W := L^T W (each column).     */
+/* -------------------------------------------------------------------------- */
+int64_t or_sygst(int itype, int64_t n, double *A, int64_t lda, const double *L, int64_t ldl)
+{
+    if (itype < 1 || itype > 3) return -1;
+    if (n <= 0) return 0;
+    double *W = (double *)malloc((size_t)n * (size_t)n * sizeof(double));
+    double *V = (double *)malloc((size_t)n * (size_t)n * sizeof(double));
+    if (!W || !V) { free(W); free(V); return -2; }
+#define WW(i, j) W[(size_t)(j) * (size_t)n + (size_t)(i)]
+#define VV(i, j) V[(size_t)(j) * (size_t)n + (size_t)(i)]
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < n; ++i)
+            WW(i, j) = (i >= j) ? AT(A, lda, i, j) : AT(A, lda, j, i);
+    if (itype == 1) {
+        /* V := L^{-1} W, column by column */
+#pragma omp parallel for schedule(static)
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = 0; i < n; ++i) {
+                double s = WW(i, j);
+                for (int64_t k = 0; k < i; ++k) s -= AT(L, ldl, i, k) * VV(k, j);
+                VV(i, j) = s / AT(L, ldl, i, i);
+            }
+        /* W := V L^{-T}, row by row: x L^T = v  <=>  L x^T = v^T */
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t j = 0; j < n; ++j) {
+                double s = VV(i, j);
+                for (int64_t k = 0; k < j; ++k) s -= WW(i, k) * AT(L, ldl, j, k);
+                WW(i, j) = s / AT(L, ldl, j, j);
+            }
+    } else {
+        /* V := W L */
+#pragma omp parallel for schedule(static)
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = 0; i < n; ++i) {
+                double s = 0.0;
+                for (int64_t k = j; k < n; ++k) s += WW(i, k) * AT(L, ldl, k, j);
+                VV(i, j) = s;
+            }
+        /* W := L^T V */
+#pragma omp parallel for schedule(static)
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = 0; i < n; ++i) {
+                double s = 0.0;
+                for (int64_t k = i; k < n; ++k) s += AT(L, ldl, k, i) * VV(k, j);
+                WW(i, j) = s;
+            }
+    }
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = j; i < n; ++i) AT(A, lda, i, j) = WW(i, j);
+#undef WW
+#undef VV
+    free(W);
+    free(V);
+    return 0;
 }
 
 /* -------------------------------------------------------------------------- */

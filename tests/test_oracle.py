@@ -461,3 +461,99 @@ def test_planted_mistakes_are_caught(oracle):
     badL = L.copy(order="F")
     badL[50, 3] = -badL[50, 3]
     assert oracle.probe_chol(A, badL, x) > 1e3
+
+
+# ----------------------------------------------------------------------------
+# sygst (Section 5, xsygst): A := L^{-1} A L^{-T} (itype 1), L^T A L (2, 3)
+# ----------------------------------------------------------------------------
+
+def test_sygst_closed_form_2x2(oracle):
+    a, b, d, p, q, r = 8.0, 5.0, 16.0, 2.0, 1.0, 4.0
+    A = np.array([[a, 99.0], [b, d]], order="F")          # the upper entry is not referenced
+    L = np.array([[p, 0.0], [q, r]], order="F")
+    X = oracle.sygst(1, A, L)
+    assert X[0, 0] == a / p ** 2 == 2.0
+    assert X[1, 0] == (p * b - q * a) / (p * p * r) == 0.125
+    assert X[1, 1] == (d - 2 * q * b / p + q * q * a / p ** 2) / r ** 2 == 0.8125
+    assert X[0, 1] == 99.0
+    for itype in (2, 3):
+        X = oracle.sygst(itype, A, L)
+        assert X[0, 0] == p * p * a + 2 * p * q * b + q * q * d == 68.0
+        assert X[1, 0] == r * (p * b + q * d) == 104.0
+        assert X[1, 1] == r * r * d == 256.0
+        assert X[0, 1] == 99.0
+
+
+def _int_sym(n, seed, lim=3):
+    r = np.random.default_rng(seed)
+    M = r.integers(-lim, lim + 1, size=(n, n)).astype(np.float64)
+    return np.asfortranarray(np.tril(M) + np.tril(M, -1).T)
+
+
+@pytest.mark.parametrize("n", [1, 3, 40, 130])
+def test_sygst_integer_exact(oracle, n):
+    L = inputs.integer_chol(n, seed=inputs.seed_for(0, 700 + n), offdiag=1, diag=(1, 1))
+    M = _int_sym(n, seed=inputs.seed_for(0, 710 + n))
+    Li, Mi = L.astype(np.int64), M.astype(np.int64)
+    A = np.asfortranarray((Li @ Mi @ Li.T).astype(np.float64))
+    # L^{-1} (L M L^T) L^{-T} = M exactly: every intermediate is an integer < 2^53
+    X = oracle.sygst(1, A, L)
+    assert np.array_equal(np.tril(X), np.tril(M))
+    X = oracle.sygst(2, M, L)
+    assert np.array_equal(np.tril(X), np.tril((Li.T @ Mi @ Li).astype(np.float64)))
+
+
+@pytest.mark.parametrize("itype", [1, 2, 3])
+@pytest.mark.parametrize("n", [1, 17, 100])
+def test_sygst_vs_lapack(oracle, itype, n):
+    Bm = inputs.spd_bbt(n, seed=inputs.seed_for(0, 720 + n))
+    L = np.asfortranarray(np.linalg.cholesky(Bm))
+    A = inputs.spd_bbt(n, seed=inputs.seed_for(0, 730 + n))
+    ref, info = lapack.dsygst(A, L, itype=itype, lower=1)
+    assert info == 0
+    X = oracle.sygst(itype, A, L)
+    scale = np.max(np.abs(np.tril(ref)))
+    assert np.max(np.abs(np.tril(X) - np.tril(ref))) <= 64 * n * 2.0 ** -53 * scale
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 5])
+def test_sygst_brute_force_rational(oracle, n):
+    Bm = inputs.spd_bbt(n, seed=inputs.seed_for(0, 740 + n))
+    L = np.asfortranarray(np.linalg.cholesky(Bm))
+    A = inputs.spd_bbt(n, seed=inputs.seed_for(0, 750 + n))
+    Lf = [[Fraction(x) for x in row] for row in L.tolist()]
+    Af = [[Fraction(x) for x in row] for row in A.tolist()]
+    # exact L^{-1} by forward substitution on the identity
+    Inv = [[Fraction(0)] * n for _ in range(n)]
+    for j in range(n):
+        for i in range(n):
+            s = Fraction(1 if i == j else 0) - sum(Lf[i][k] * Inv[k][j] for k in range(i))
+            Inv[i][j] = s / Lf[i][i]
+    for itype in (1, 2):
+        if itype == 1:
+            P = [[sum(Inv[i][k] * Af[k][l] for k in range(n)) for l in range(n)] for i in range(n)]
+            E = [[sum(P[i][l] * Inv[j][l] for l in range(n)) for j in range(n)] for i in range(n)]
+        else:
+            P = [[sum(Lf[k][i] * Af[k][l] for k in range(n)) for l in range(n)] for i in range(n)]
+            E = [[sum(P[i][l] * Lf[l][j] for l in range(n)) for j in range(n)] for i in range(n)]
+        X = oracle.sygst(itype, A, L)
+        ex = np.array([[float(E[i][j]) for j in range(n)] for i in range(n)])
+        scale = max(1.0, np.max(np.abs(ex)))
+        assert np.max(np.abs(np.tril(X) - np.tril(ex))) <= 32 * n * 2.0 ** -53 * scale
+
+
+def test_sygst_planted_mistakes_are_caught(oracle):
+    n = 60
+    Bm = inputs.spd_bbt(n, seed=inputs.seed_for(0, 760))
+    L = np.asfortranarray(np.linalg.cholesky(Bm))
+    A = inputs.spd_bbt(n, seed=inputs.seed_for(0, 770))
+    ref, _ = lapack.dsygst(A, L, itype=1, lower=1)
+    tol = 64 * n * 2.0 ** -53 * np.max(np.abs(ref))
+    Li = np.linalg.inv(L)
+    wrong_side = Li.T @ A @ Li                        # inverse applied on the wrong sides
+    assert np.max(np.abs(np.tril(wrong_side) - np.tril(ref))) > 1e6 * tol
+    X = oracle.sygst(1, A, L)
+    bad = X.copy(order="F")
+    bad[40, 7] *= -1                                  # one sign flipped
+    assert np.max(np.abs(np.tril(bad) - np.tril(ref))) > 1e3 * tol
+    assert np.max(np.abs(np.tril(X) - np.tril(ref))) <= tol
