@@ -55,6 +55,7 @@ def _lib():
             "or_potri": (_i64, [_i64, _ptr, _i64, _i64]),
             "or_getrs": (None, [_i64, _i64, _ptr, _i64, _ptr, _ptr, _i64]),
             "or_potrs": (None, [_i64, _i64, _ptr, _i64, _ptr, _i64]),
+            "or_getri": (None, [_i64, _ptr, _i64, _ptr, _ptr, _i64]),
             "or_sygst": (_i64, [ctypes.c_int, _i64, _ptr, _i64, _ptr, _i64]),
             "or_gemm": (None, [ctypes.c_int, ctypes.c_int, _i64, _i64, _i64, _dbl,
                                _ptr, _i64, _ptr, _i64, _ptr, _i64]),
@@ -263,6 +264,16 @@ def potrs(L, B):
         B = B.reshape(-1, 1, order="F")
     _lib().or_potrs(L.shape[0], B.shape[1], _p(L), _ld(L), _p(B), _ld(B))
     return B
+
+
+def getri(LU, ipiv):
+    """A^{-1} from P A = L U (LU and 1-based ipiv as or_getrf returns them)."""
+    LU = _f64(LU, copy=False) if np.asarray(LU).flags.f_contiguous else _f64(LU)
+    n = LU.shape[0]
+    X = np.zeros((n, n), order="F")
+    ipiv = np.ascontiguousarray(ipiv, dtype=np.int32)
+    _lib().or_getri(n, _p(LU), _ld(LU), _p(ipiv), _p(X), _ld(X))
+    return X
 
 
 def sygst(itype, A, L):

@@ -27,6 +27,8 @@
  *   or_getrf        Section 5, xgetrf (P L U := A, row pivoting); Section 3
  *                   halving scheme with unblocked getf2 as base case
  *   or_laswp        the row interchanges P of xgetrf
+ *   or_getri        Section 5, xtrtri as the building block of xgetri:
+ *                   the inverse by its definition, A X = I
  *   or_sygst        Section 5, xsygst (A := L^{-1} A L^{-T}, or L^T A L):
  *                   the definition, by substitution and products
  *   metrics         normwise backward errors used by the benchmark spec's bound
@@ -486,6 +488,15 @@ void or_potrs(int64_t n, int64_t nrhs, const double *L, int64_t lda,
 {
     or_trsm_llnx(0, n, nrhs, 1.0, L, lda, B, ldb);
     or_trsm_lltn(n, nrhs, L, lda, B, ldb);
+}
+
+/* getri: X := A^{-1} from P A = L U (or_getrf's LU and ipiv), by the       */
+/* definition of the inverse: the solution of A X = I, column by column.     */
+void or_getri(int64_t n, const double *LU, int64_t lda, const int32_t *ipiv, double *X, int64_t ldx)
+{
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < n; ++i) AT(X, ldx, i, j) = (i == j) ? 1.0 : 0.0;
+    or_getrs(n, n, LU, lda, ipiv, X, ldx);
 }
 
 /* -------------------------------------------------------------------------- */

@@ -557,3 +557,76 @@ def test_sygst_planted_mistakes_are_caught(oracle):
     bad[40, 7] *= -1                                  # one sign flipped
     assert np.max(np.abs(np.tril(bad) - np.tril(ref))) > 1e3 * tol
     assert np.max(np.abs(np.tril(X) - np.tril(ref))) <= tol
+
+
+# ----------------------------------------------------------------------------
+# getri (xtrtri as building block of xgetri, Section 5): A^{-1} from P L U
+# ----------------------------------------------------------------------------
+
+def test_getri_closed_form_2x2(oracle):
+    A = np.array([[1.0, 2.0], [3.0, 4.0]], order="F")
+    F, ipiv, info = oracle.getrf(A, c=1)
+    X = oracle.getri(F, ipiv)
+    det = 1.0 * 4.0 - 2.0 * 3.0
+    ex = np.array([[4.0, -2.0], [-3.0, 1.0]]) / det
+    assert np.max(np.abs(X - ex)) <= 4 * 2.0 ** -53 * 2.0
+
+
+def _unimodular_factors(n, seed):
+    """Integer unit-lower L, integer upper U with diagonal +-1 and a pivot
+    sequence: A = P^T L U has det +-1 and an integer inverse."""
+    r = np.random.default_rng(seed)
+    L = np.tril(r.integers(-1, 2, size=(n, n)).astype(np.float64), -1) + np.eye(n)
+    U = np.triu(r.integers(-1, 2, size=(n, n)).astype(np.float64), 1)
+    U[np.diag_indices(n)] = r.choice([-1.0, 1.0], size=n)
+    ipiv = np.array([r.integers(j + 1, n + 1) for j in range(n)], dtype=np.int32)
+    F = np.asfortranarray(np.tril(L, -1) + U)
+    P = np.eye(n)
+    for j in range(n):
+        p = ipiv[j] - 1
+        P[[j, p]] = P[[p, j]]
+    A = P.T @ L @ U
+    return F, ipiv, A
+
+
+@pytest.mark.parametrize("n", [1, 4, 30])
+def test_getri_integer_exact(oracle, n):
+    F, ipiv, A = _unimodular_factors(n, inputs.seed_for(0, 900 + n))
+    X = oracle.getri(F, ipiv)
+    assert np.array_equal(X, np.round(X))                       # integer inverse, exactly
+    assert np.array_equal(A @ X, np.eye(n))
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 100])
+def test_getri_vs_lapack(oracle, n):
+    A = inputs.uniform(n, n, seed=inputs.seed_for(0, 910 + n))
+    F, ipiv, info = oracle.getrf(A, c=24)
+    lu, piv, _ = lapack.dgetrf(A)
+    assert np.array_equal(piv + 1, ipiv)
+    ref, info = lapack.dgetri(lu, piv)
+    assert info == 0
+    X = oracle.getri(F, ipiv)
+    kappa = np.linalg.cond(A)
+    assert np.max(np.abs(X - ref)) <= 64 * n * 2.0 ** -53 * kappa * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("n", [1, 3, 5])
+def test_getri_brute_force_rational(oracle, n):
+    A = inputs.uniform(n, n, seed=inputs.seed_for(0, 920 + n))
+    M = [[Fraction(x) for x in row] for row in A.tolist()]
+    # exact inverse by Gauss-Jordan on [A | I] in rationals
+    aug = [M[i] + [Fraction(1 if i == j else 0) for j in range(n)] for i in range(n)]
+    for j in range(n):
+        p = next(i for i in range(j, n) if aug[i][j] != 0)
+        aug[j], aug[p] = aug[p], aug[j]
+        piv = aug[j][j]
+        aug[j] = [v / piv for v in aug[j]]
+        for i in range(n):
+            if i != j and aug[i][j] != 0:
+                f = aug[i][j]
+                aug[i] = [a - f * b for a, b in zip(aug[i], aug[j])]
+    ex = np.array([[float(aug[i][n + j]) for j in range(n)] for i in range(n)])
+    F, ipiv, info = oracle.getrf(A, c=1)
+    X = oracle.getri(F, ipiv)
+    kappa = np.linalg.cond(A)
+    assert np.max(np.abs(X - ex)) <= 16 * n * 2.0 ** -53 * kappa * np.max(np.abs(ex))
