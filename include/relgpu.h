@@ -151,6 +151,27 @@ int rl_dpotrs(char uplo, int64_t n, int64_t nrhs, const double *A, int64_t lda, 
               int64_t ldb, void *work, size_t lwork, rl_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * dsygst (Section 5, xsygst) -- reduction of the symmetric-definite
+ * generalized eigenproblem to standard form, with B's Cholesky factor L
+ * (lower, from rl_dpotrf) in B:
+ *   itype 1:    A := L^{-1} A L^{-T}      (A x = lambda B x)
+ *   itype 2, 3: A := L^T A L              (A B x = lambda x, B A x = lambda x)
+ * uplo 'L' only ('U' returns RL_ERR_UNSUPPORTED): the lower triangles of A
+ * and B are read, the lower triangle of A is overwritten, the strictly upper
+ * triangles are not referenced.  Recursive by halving (Section 3).
+ * work (device, optional): rl_dsygst_work_size(n) bytes, about n/2 x n/2
+ *   doubles, the paper's temporary buffer that saves one symmetric product
+ *   per recursion level (Section 5, xsygst user note); with work == NULL the
+ *   product is recomputed instead (no buffer).  A non-NULL work with lwork
+ *   below the query returns RL_ERR_WORKSPACE.
+ * Argument numbers: 1 itype, 2 uplo, 3 n, 4 A, 5 lda, 6 B, 7 ldb.
+ * Stream-ordered; no synchronization, no numeric info (as LAPACK's dsygst).
+ * ------------------------------------------------------------------------- */
+size_t rl_dsygst_work_size(int64_t n);
+int rl_dsygst(int itype, char uplo, int64_t n, double *A, int64_t lda, const double *B,
+              int64_t ldb, void *work, size_t lwork, rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Single-precision peers (Section 5: every routine exists for s, d, c and z;
  * s and d are built): the same recursions and kernels in FP32 storage and
  * arithmetic (SIMT FP32 updates).  Same arguments, numbering, workspace and
@@ -230,6 +251,13 @@ int rl_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, double a
              double *C, int64_t ldc, rl_stream_t stream);
 int rl_dsyrk(char uplo, char trans, int64_t n, int64_t k, double alpha, const double *A,
              int64_t lda, double beta, double *C, int64_t ldc, rl_stream_t stream);
+/* FP32 peers of rl_dgemm / rl_dsyrk (SIMT FP32 arithmetic: the update kernels
+ * of the FP32 precision form and of rl_spotrf / rl_sgetrf). */
+int rl_sgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, float alpha,
+             const float *A, int64_t lda, const float *B, int64_t ldb, float beta, float *C,
+             int64_t ldc, rl_stream_t stream);
+int rl_ssyrk(char uplo, char trans, int64_t n, int64_t k, float alpha, const float *A,
+             int64_t lda, float beta, float *C, int64_t ldc, rl_stream_t stream);
 int rl_dtrsm(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
              double alpha, const double *A, int64_t lda, double *B, int64_t ldb,
              rl_stream_t stream);
@@ -338,6 +366,10 @@ int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda,
  *                              RL_INFO_DEVICE_TIMEOUT
  *   RL_PARAM_BATCH_CTAS        CTAs per SM of the batched kernels (0 = as
  *                              many as fit, the default; 1..8)
+ *   RL_PARAM_TRI_LANES         lanes per vector of the triangle kernels at
+ *                              the TRSM/TRMM leaves: 0 (default) picks 2
+ *                              for leaves of >= 12288 vectors, else 4; 2 or
+ *                              4 force one; all give bit-identical results
  * rl_set_param returns 0 or RL_ERR_PARAM; rl_get_param returns the value or
  * -1 for an unknown key.
  * ------------------------------------------------------------------------- */
@@ -346,7 +378,8 @@ enum {
     RL_PARAM_GETRF_PANEL = 2,
     RL_PARAM_TRTRI_CROSSOVER = 3,
     RL_PARAM_SPIN_LIMIT_NS = 4,
-    RL_PARAM_BATCH_CTAS = 5
+    RL_PARAM_BATCH_CTAS = 5,
+    RL_PARAM_TRI_LANES = 6
 };
 int rl_set_param(int key, int64_t value);
 int64_t rl_get_param(int key);

@@ -242,9 +242,11 @@ static bool is_n(char t) { return t == 'N' || t == 'n'; }
 static bool is_t(char t) { return t == 'T' || t == 't' || t == 'C' || t == 'c'; }
 static i64 imax1(i64 v) { return v > 1 ? v : 1; }
 
-int rl_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
-             const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C,
-             int64_t ldc, rl_stream_t stream)
+}  // extern "C"
+
+template <typename T>
+static int gemm_api(char transa, char transb, int64_t m, int64_t n, int64_t k, T alpha, const T *A,
+                    int64_t lda, const T *B, int64_t ldb, T beta, T *C, int64_t ldc, rl_stream_t stream)
 {
     if (!is_n(transa) && !is_t(transa)) return -1;
     if (!is_n(transb) && !is_t(transb)) return -2;
@@ -256,12 +258,13 @@ int rl_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, double a
     if (ldb < imax1(tb ? n : k)) return -10;
     if (ldc < imax1(m)) return -13;
     Ctx c = make_ctx(stream, nullptr, nullptr, 0);
-    gemm(c, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, false);
+    gemm<T>(c, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, false);
     return finish(c);
 }
 
-int rl_dsyrk(char uplo, char trans, int64_t n, int64_t k, double alpha, const double *A,
-             int64_t lda, double beta, double *C, int64_t ldc, rl_stream_t stream)
+template <typename T>
+static int syrk_api(char uplo, char trans, int64_t n, int64_t k, T alpha, const T *A, int64_t lda, T beta,
+                    T *C, int64_t ldc, rl_stream_t stream)
 {
     if (!is_l(uplo) && !is_u(uplo)) return -1;
     if (!is_n(trans) && !is_t(trans)) return -2;
@@ -272,8 +275,36 @@ int rl_dsyrk(char uplo, char trans, int64_t n, int64_t k, double alpha, const do
     if (ldc < imax1(n)) return -10;
     if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
     Ctx c = make_ctx(stream, nullptr, nullptr, 0);
-    gemm(c, t, !t, n, n, k, alpha, A, lda, A, lda, beta, C, ldc, true);
+    gemm<T>(c, t, !t, n, n, k, alpha, A, lda, A, lda, beta, C, ldc, true);
     return finish(c);
+}
+
+extern "C" {
+
+int rl_dgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+             const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C,
+             int64_t ldc, rl_stream_t stream)
+{
+    return gemm_api<double>(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream);
+}
+
+int rl_dsyrk(char uplo, char trans, int64_t n, int64_t k, double alpha, const double *A,
+             int64_t lda, double beta, double *C, int64_t ldc, rl_stream_t stream)
+{
+    return syrk_api<double>(uplo, trans, n, k, alpha, A, lda, beta, C, ldc, stream);
+}
+
+int rl_sgemm(char transa, char transb, int64_t m, int64_t n, int64_t k, float alpha, const float *A,
+             int64_t lda, const float *B, int64_t ldb, float beta, float *C, int64_t ldc,
+             rl_stream_t stream)
+{
+    return gemm_api<float>(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream);
+}
+
+int rl_ssyrk(char uplo, char trans, int64_t n, int64_t k, float alpha, const float *A, int64_t lda,
+             float beta, float *C, int64_t ldc, rl_stream_t stream)
+{
+    return syrk_api<float>(uplo, trans, n, k, alpha, A, lda, beta, C, ldc, stream);
 }
 
 static int check_tr(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
@@ -423,6 +454,26 @@ static int trs_t(bool lu, int64_t n, int64_t nrhs, const T *A, int64_t lda, cons
 }
 
 extern "C" {
+
+size_t rl_dsygst_work_size(int64_t n) { return n <= 0 ? 0 : sygst_work_bytes(n); }
+
+int rl_dsygst(int itype, char uplo, int64_t n, double *A, int64_t lda, const double *B, int64_t ldb,
+              void *work, size_t lwork, rl_stream_t stream)
+{
+    if (itype < 1 || itype > 3) return -1;
+    if (!is_l(uplo) && !is_u(uplo)) return -2;
+    if (n < 0) return -3;
+    if (n > 0 && A == nullptr) return -4;
+    if (lda < imax1(n)) return -5;
+    if (n > 0 && B == nullptr) return -6;
+    if (ldb < imax1(n)) return -7;
+    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
+    if (n == 0) return RL_SUCCESS;
+    if (work != nullptr && lwork < sygst_work_bytes(n)) return RL_ERR_WORKSPACE;
+    Ctx c = make_ctx(stream, nullptr, work, lwork);
+    sygst_rec(c, itype, n, A, lda, B, ldb, static_cast<double *>(work));
+    return finish(c);
+}
 
 size_t rl_trs_work_size(int64_t n, int64_t nrhs)
 {
@@ -699,6 +750,10 @@ int rl_set_param(int key, int64_t value)
         if (value < 0 || value > 8) return RL_ERR_PARAM;
         g_params.batch_ctas = (int)value;
         return RL_SUCCESS;
+    case RL_PARAM_TRI_LANES:
+        if (value != 0 && value != 2 && value != 4) return RL_ERR_PARAM;
+        g_params.tri_lanes = (int)value;
+        return RL_SUCCESS;
     default:
         return RL_ERR_PARAM;
     }
@@ -712,6 +767,7 @@ int64_t rl_get_param(int key)
     case RL_PARAM_TRTRI_CROSSOVER: return g_params.trtri_c;
     case RL_PARAM_SPIN_LIMIT_NS: return g_params.spin_ns;
     case RL_PARAM_BATCH_CTAS: return g_params.batch_ctas;
+    case RL_PARAM_TRI_LANES: return g_params.tri_lanes;
     default: return -1;
     }
 }

@@ -25,7 +25,9 @@ namespace rl {
 // launched (square C) and only elements i >= j are stored.
 // 256 threads as 16x16; thread (tx,ty) owns rows tx+16i, columns ty+16j.
 // ----------------------------------------------------------------------------
-template <typename T, bool TA, bool TB, bool LOWER>
+// SYM: 0 plain operands; 1: A is symmetric with its lower triangle stored
+// (element (i, p) read from (max, min)); 2: the same for B.  Used by SYMM.
+template <typename T, bool TA, bool TB, bool LOWER, int SYM = 0>
 __global__ void __launch_bounds__(256)
 k_gemm(i64 m, i64 n, i64 k, T alpha, const T *__restrict__ A, i64 lda,
        const T *__restrict__ B, i64 ldb, T beta, T *C, i64 ldc,
@@ -66,7 +68,10 @@ k_gemm(i64 m, i64 n, i64 k, T alpha, const T *__restrict__ A, i64 lda,
             else     { pl = tid & 15; il = (tid >> 4) + 16 * r; }
             i64 gi = i0 + il, gp = k0 + pl;
             T v = T(0);
-            if (gi < m && gp < k) v = TA ? __ldg(A + gi * lda + gp) : __ldg(A + gp * lda + gi);
+            if (gi < m && gp < k) {
+                if (SYM == 1) v = (gi >= gp) ? __ldg(A + gp * lda + gi) : __ldg(A + gi * lda + gp);
+                else v = TA ? __ldg(A + gi * lda + gp) : __ldg(A + gp * lda + gi);
+            }
             ra[r] = v;
         }
 #pragma unroll
@@ -76,7 +81,10 @@ k_gemm(i64 m, i64 n, i64 k, T alpha, const T *__restrict__ A, i64 lda,
             else     { jl = tid & 63; pl = (tid >> 6) + 4 * r; }
             i64 gj = j0 + jl, gp = k0 + pl;
             T v = T(0);
-            if (gj < n && gp < k) v = TB ? __ldg(B + gp * ldb + gj) : __ldg(B + gj * ldb + gp);
+            if (gj < n && gp < k) {
+                if (SYM == 2) v = (gp >= gj) ? __ldg(B + gj * ldb + gp) : __ldg(B + gp * ldb + gj);
+                else v = TB ? __ldg(B + gp * ldb + gj) : __ldg(B + gj * ldb + gp);
+            }
             rb[r] = v;
         }
     };
@@ -151,6 +159,170 @@ static void launch_gemm(Ctx &c, i64 m, i64 n, i64 k, T alpha, const T *A, i64 ld
         m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, c.abort, (int)tiles_m);
 }
 
+// ----------------------------------------------------------------------------
+// FP32 SIMT GEMM with 128 x 128 CTA tiles (the FP32 updates of the precision
+// form).  FP32 FMAs issue 64x faster than FP64 ones, so the 64 x 64 tile
+// above becomes shared-memory bound; here each of the 256 threads owns an
+// 8 x 8 block (rows 4tx..4tx+3 and 64+4tx.., columns 4ty.. and 64+4ty..),
+// read as float4 from k-major tiles: 4 shared loads per 64 FMAs.
+// ----------------------------------------------------------------------------
+constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 8;
+
+template <bool TA, bool TB, bool LOWER>
+__global__ void __launch_bounds__(256)
+k_sgemm128(i64 m, i64 n, i64 k, float alpha, const float *__restrict__ A, i64 lda,
+           const float *__restrict__ B, i64 ldb, float beta, float *C, i64 ldc,
+           const int32_t *abort, int tiles_m)
+{
+    if (abort && *abort != 0) return;
+    int tm, tn;
+    if (LOWER) {
+        long long t = blockIdx.x;
+        int r = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while ((long long)(r + 1) * (r + 2) / 2 <= t) ++r;
+        while ((long long)r * (r + 1) / 2 > t) --r;
+        tm = r;
+        tn = (int)(t - (long long)r * (r + 1) / 2);
+    } else {
+        tm = blockIdx.x % tiles_m;
+        tn = blockIdx.x / tiles_m;
+    }
+    const i64 i0 = (i64)tm * SG_BM, j0 = (i64)tn * SG_BN;
+    __shared__ __align__(16) float As[2][SG_BK][SG_BM];
+    __shared__ __align__(16) float Bs[2][SG_BK][SG_BN];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+
+    // global -> register staging: 4 elements of A and 4 of B per thread
+    float ra[4], rb[4];
+    auto load = [&](i64 k0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int il, pl;
+            if (!TA) { il = tid & 127; pl = (tid >> 7) + 2 * r; }      // column-major A: rows contiguous
+            else     { pl = tid & 7; il = (tid >> 3) + 32 * r; }        // A^T: k contiguous
+            const i64 gi = i0 + il, gp = k0 + pl;
+            float v = 0.0f;
+            if (gi < m && gp < k) v = TA ? __ldg(A + gi * lda + gp) : __ldg(A + gp * lda + gi);
+            ra[r] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int jl, pl;
+            if (!TB) { pl = tid & 7; jl = (tid >> 3) + 32 * r; }        // B: k contiguous
+            else     { jl = tid & 127; pl = (tid >> 7) + 2 * r; }       // B^T: columns contiguous
+            const i64 gj = j0 + jl, gp = k0 + pl;
+            float v = 0.0f;
+            if (gj < n && gp < k) v = TB ? __ldg(B + gp * ldb + gj) : __ldg(B + gj * ldb + gp);
+            rb[r] = v;
+        }
+    };
+    auto store = [&](int st) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int il, pl;
+            if (!TA) { il = tid & 127; pl = (tid >> 7) + 2 * r; }
+            else     { pl = tid & 7; il = (tid >> 3) + 32 * r; }
+            As[st][pl][il] = ra[r];
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int jl, pl;
+            if (!TB) { pl = tid & 7; jl = (tid >> 3) + 32 * r; }
+            else     { jl = tid & 127; pl = (tid >> 7) + 2 * r; }
+            Bs[st][pl][jl] = rb[r];
+        }
+    };
+
+    const i64 nk = (k + SG_BK - 1) / SG_BK;
+    if (nk > 0) {
+        load(0);
+        store(0);
+        __syncthreads();
+        for (i64 t = 0; t < nk; ++t) {
+            const int st = (int)(t & 1);
+            if (t + 1 < nk) load((t + 1) * SG_BK);
+#pragma unroll
+            for (int kk = 0; kk < SG_BK; ++kk) {
+                const float4 a0 = *reinterpret_cast<const float4 *>(&As[st][kk][4 * tx]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&As[st][kk][64 + 4 * tx]);
+                const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[st][kk][4 * ty]);
+                const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[st][kk][64 + 4 * ty]);
+                const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            }
+            if (t + 1 < nk) store(st ^ 1);
+            __syncthreads();
+        }
+    }
+
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const i64 col = j0 + (j < 4 ? 4 * ty + j : 64 + 4 * ty + (j - 4));
+        if (col >= n) continue;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const i64 row = i0 + (i < 4 ? 4 * tx + i : 64 + 4 * tx + (i - 4));
+            if (row >= m) continue;
+            if (LOWER && row < col) continue;
+            float *cp = C + col * ldc + row;
+            const float cv = (beta == 0.0f) ? 0.0f : beta * (*cp);
+            *cp = fmaf(alpha, acc[i][j], cv);
+        }
+    }
+}
+
+template <bool TA, bool TB, bool LOWER>
+static void launch_sgemm128(Ctx &c, i64 m, i64 n, i64 k, float alpha, const float *A, i64 lda,
+                            const float *B, i64 ldb, float beta, float *C, i64 ldc)
+{
+    const i64 tiles_m = (m + SG_BM - 1) / SG_BM, tiles_n = (n + SG_BN - 1) / SG_BN;
+    const i64 grid = LOWER ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
+    const double flops = LOWER ? (double)k * (double)n * (double)(n + 1) : 2.0 * m * n * k;
+    Launch L(c, LOWER ? K_SYRK : K_GEMM, flops, 0.0);
+    k_sgemm128<TA, TB, LOWER><<<(unsigned)grid, 256, 0, c.s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                                                                c.abort, (int)tiles_m);
+}
+
+// The 128-tile kernel pays off once it still gives every SM a CTA.
+static bool sgemm128_fits(Ctx &c, i64 m, i64 n, bool lower)
+{
+    const i64 tm = (m + SG_BM - 1) / SG_BM, tn = (n + SG_BN - 1) / SG_BN;
+    const i64 tiles = lower ? tm * (tm + 1) / 2 : tm * tn;
+    return tiles >= c.num_sms;
+}
+
+template <typename T>
+static bool gemm_f32_wide(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, T alpha, const T *A, i64 lda,
+                          const T *B, i64 ldb, T beta, T *C, i64 ldc, bool lower)
+{
+    if (sizeof(T) != 4 || !sgemm128_fits(c, m, n, lower)) return false;
+    const float *a = reinterpret_cast<const float *>(A), *b = reinterpret_cast<const float *>(B);
+    float *cc = reinterpret_cast<float *>(C);
+    const float al = (float)alpha, be = (float)beta;
+    if (lower) {
+        if (!ta && tb) launch_sgemm128<false, true, true>(c, m, n, k, al, a, lda, b, ldb, be, cc, ldc);
+        else if (ta && !tb) launch_sgemm128<true, false, true>(c, m, n, k, al, a, lda, b, ldb, be, cc, ldc);
+        else if (!ta && !tb) launch_sgemm128<false, false, true>(c, m, n, k, al, a, lda, b, ldb, be, cc, ldc);
+        else launch_sgemm128<true, true, true>(c, m, n, k, al, a, lda, b, ldb, be, cc, ldc);
+        return true;
+    }
+    if (!ta && !tb) launch_sgemm128<false, false, false>(c, m, n, k, al, a, lda, b, ldb, be, cc, ldc);
+    else if (!ta && tb) launch_sgemm128<false, true, false>(c, m, n, k, al, a, lda, b, ldb, be, cc, ldc);
+    else if (ta && !tb) launch_sgemm128<true, false, false>(c, m, n, k, al, a, lda, b, ldb, be, cc, ldc);
+    else launch_sgemm128<true, true, false>(c, m, n, k, al, a, lda, b, ldb, be, cc, ldc);
+    return true;
+}
+
 template <typename T>
 void gemm(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, T alpha, const T *A, i64 lda,
           const T *B, i64 ldb, T beta, T *C, i64 ldc, bool lower)
@@ -163,6 +335,7 @@ void gemm(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, T alpha, const T *A, i6
                     (float *)C, ldc, lower, c.tcwork, c.tclwork))
             return;
     }
+    if (gemm_f32_wide<T>(c, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, lower)) return;
     if (lower) {
         if (!ta && tb) launch_gemm<T, false, true, true>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
         else if (ta && !tb) launch_gemm<T, true, false, true>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
@@ -174,6 +347,24 @@ void gemm(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, T alpha, const T *A, i6
     else if (!ta && tb) launch_gemm<T, false, true, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     else if (ta && !tb) launch_gemm<T, true, false, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     else launch_gemm<T, true, true, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+// C(m x n) := beta C + alpha S Bm (left: S m x m) or alpha Bm S (right:
+// S n x n); S symmetric, lower triangle stored.
+template <typename T>
+void symm(Ctx &c, bool left, i64 m, i64 n, T alpha, const T *S, i64 lds, const T *Bm, i64 ldb, T beta,
+          T *C, i64 ldc)
+{
+    if (m <= 0 || n <= 0) return;
+    const i64 k = left ? m : n;
+    const i64 tiles_m = (m + GEMM_BM - 1) / GEMM_BM, tiles_n = (n + GEMM_BN - 1) / GEMM_BN;
+    Launch L(c, K_GEMM, 2.0 * m * n * k, 0.0);
+    if (left)
+        k_gemm<T, false, false, false, 1><<<(unsigned)(tiles_m * tiles_n), 256, 0, c.s>>>(
+            m, n, k, alpha, S, lds, Bm, ldb, beta, C, ldc, c.abort, (int)tiles_m);
+    else
+        k_gemm<T, false, false, false, 2><<<(unsigned)(tiles_m * tiles_n), 256, 0, c.s>>>(
+            m, n, k, alpha, Bm, ldb, S, lds, beta, C, ldc, c.abort, (int)tiles_m);
 }
 
 // ----------------------------------------------------------------------------
@@ -287,6 +478,114 @@ k_tri(i64 nvec, int n, T alpha, const T *__restrict__ Tm, i64 ldt, T *B, i64 ldb
     }
 }
 
+// Two lanes per vector: lane q of a pair holds elements e = 2t + q in
+// registers.  The triangle M (order n, identity-padded to NB) is staged as a
+// full square with a padded row stride so that every access in the
+// substitution loops is a compile-time offset from a per-lane base:
+//   FWD reads M(k, j) for the lane's k: rows interleaved by parity,
+//       M(i, k) at (i & 1) * (NB/2) * RS + (i >> 1) * RS + k;
+//   BWD and MUL read M(j, k) / M(k, j) along the lane's elements: plain rows,
+//       M(i, k) at i * RS + k.
+// The loops skip, at compile time, every update that is zero for both lanes;
+// only the one element per step that belongs to one lane of the pair is
+// predicated.  Operation order per element is that of k_tri, so both
+// kernels give bit-identical results.
+template <typename T, int NB, int OP, bool ROWS, bool UNIT, bool TRANS_UPPER, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+k_tri2(i64 nvec, int n, T alpha, const T *__restrict__ Tm, i64 ldt, T *B, i64 ldb, const int32_t *abort)
+{
+    if (abort && *abort != 0) return;
+    constexpr int E = NB / 2, RS = NB + 1;
+    __shared__ T S[NB * RS];
+    for (int idx = threadIdx.x; idx < NB * NB; idx += THREADS) {
+        const int k = idx % NB, i = idx / NB;          // element M(i, k)
+        T v;
+        if (i < n && k < n) v = (k > i) ? T(0) : (TRANS_UPPER ? Tm[(i64)i * ldt + k] : Tm[(i64)k * ldt + i]);
+        else v = (i == k) ? T(1) : T(0);
+        if (UNIT && i == k) v = T(1);
+        const int a = (OP == TRI_FWD) ? ((i & 1) * E * RS + (i >> 1) * RS + k) : (i * RS + k);
+        S[a] = v;
+    }
+    __syncthreads();
+    const int q = threadIdx.x & 1;
+    const int pair = (threadIdx.x & 31) & ~1;
+    const i64 v = (i64)blockIdx.x * (THREADS / 2) + (threadIdx.x >> 1);
+    const bool live = v < nvec;
+    T x[E];
+#pragma unroll
+    for (int t = 0; t < E; ++t) {
+        const int e = 2 * t + q;
+        T b = T(0);
+        if (live && e < n) b = ROWS ? B[(i64)e * ldb + v] : B[v * ldb + e];
+        x[t] = alpha * b;
+    }
+    if (OP == TRI_FWD) {
+        const T *Sq = S + q * E * RS;                  // row 2t + q of M at Sq + t * RS
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            const int s = j >> 1, own = j & 1;
+            if (!UNIT && q == own) x[s] = x[s] / Sq[s * RS + j];
+            const T xj = __shfl_sync(0xffffffffu, x[s], pair | own);
+#pragma unroll
+            for (int t = 0; t < E; ++t) {
+                if (2 * t > j) x[t] = fma(-xj, Sq[t * RS + j], x[t]);
+                else if (2 * t == j && q == 1) x[t] = fma(-xj, Sq[t * RS + j], x[t]);
+            }
+        }
+    } else if (OP == TRI_BWD) {
+        const T *Sq = S + q;                           // M(j, 2t + q) at Sq + j * RS + 2t
+#pragma unroll
+        for (int j = NB - 1; j >= 0; --j) {
+            const int s = j >> 1, own = j & 1;
+            if (!UNIT && q == own) x[s] = x[s] / S[j * RS + j];
+            const T xj = __shfl_sync(0xffffffffu, x[s], pair | own);
+#pragma unroll
+            for (int t = 0; t < E; ++t) {
+                if (2 * t + 1 < j) x[t] = fma(-xj, Sq[j * RS + 2 * t], x[t]);
+                else if (2 * t + 1 == j && q == 0) x[t] = fma(-xj, Sq[j * RS + 2 * t], x[t]);
+            }
+        }
+    } else {
+        const T *Sq = S + q;                           // M(k, 2t + q) at Sq + k * RS + 2t
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            const int s = k >> 1, own = k & 1;
+            const T bk = __shfl_sync(0xffffffffu, x[s], pair | own);
+            if (q == own) x[s] = UNIT ? bk : bk * S[k * RS + k];
+#pragma unroll
+            for (int t = 0; t < E; ++t) {
+                if (2 * t + 1 < k) x[t] = fma(bk, Sq[k * RS + 2 * t], x[t]);
+                else if (2 * t + 1 == k && q == 0) x[t] = fma(bk, Sq[k * RS + 2 * t], x[t]);
+            }
+        }
+    }
+    if (live) {
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const int e = 2 * t + q;
+            if (e < n) {
+                if (ROWS) B[(i64)e * ldb + v] = x[t];
+                else B[v * ldb + e] = x[t];
+            }
+        }
+    }
+}
+
+constexpr i64 TRI2_MIN_VECS = 12288;
+
+template <typename T, int NB, int OP, bool ROWS, bool UNIT, bool TRANS_UPPER>
+static void launch_tri2(Ctx &c, i64 nvec, int n, T alpha, const T *Tm, i64 ldt, T *B, i64 ldb)
+{
+    // 32 vectors per CTA while that leaves fewer than two CTAs per SM of 64, else 64
+    if (nvec < (i64)c.num_sms * 2 * 64) {
+        const unsigned grid = (unsigned)((nvec + 31) / 32);
+        k_tri2<T, NB, OP, ROWS, UNIT, TRANS_UPPER, 64><<<grid, 64, 0, c.s>>>(nvec, n, alpha, Tm, ldt, B, ldb, c.abort);
+    } else {
+        const unsigned grid = (unsigned)((nvec + 63) / 64);
+        k_tri2<T, NB, OP, ROWS, UNIT, TRANS_UPPER, 128><<<grid, 128, 0, c.s>>>(nvec, n, alpha, Tm, ldt, B, ldb, c.abort);
+    }
+}
+
 template <typename T, int OP, bool ROWS, bool UNIT, bool TRANS_UPPER>
 static void launch_tri(Ctx &c, int kind, i64 nvec, int n, T alpha, const T *Tm, i64 ldt, T *B,
                        i64 ldb)
@@ -294,6 +593,15 @@ static void launch_tri(Ctx &c, int kind, i64 nvec, int n, T alpha, const T *Tm, 
     if (nvec <= 0 || n <= 0) return;
     const unsigned grid = (unsigned)((nvec + TRI_VECS - 1) / TRI_VECS);
     Launch L(c, kind, (double)nvec * n * n, 0.0);
+    // two lanes per vector halve the FP64 instructions but double each
+    // vector's dependent chain: they win only with many vectors in flight
+    const int lanes = g_params.tri_lanes ? g_params.tri_lanes : (nvec >= TRI2_MIN_VECS ? 2 : 4);
+    if (lanes == 2) {
+        if (n <= 16) launch_tri2<T, 16, OP, ROWS, UNIT, TRANS_UPPER>(c, nvec, n, alpha, Tm, ldt, B, ldb);
+        else if (n <= 32) launch_tri2<T, 32, OP, ROWS, UNIT, TRANS_UPPER>(c, nvec, n, alpha, Tm, ldt, B, ldb);
+        else launch_tri2<T, 64, OP, ROWS, UNIT, TRANS_UPPER>(c, nvec, n, alpha, Tm, ldt, B, ldb);
+        return;
+    }
     if (n <= 16)
         k_tri<T, 16, OP, ROWS, UNIT, TRANS_UPPER><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, Tm, ldt, B, ldb, c.abort);
     else if (n <= 32)
@@ -394,6 +702,7 @@ void trmm_llt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
 #define RL_INST_BLAS3(T)                                                                          \
     template void gemm<T>(Ctx &, bool, bool, i64, i64, i64, T, const T *, i64, const T *, i64, T, \
                           T *, i64, bool);                                                        \
+    template void symm<T>(Ctx &, bool, i64, i64, T, const T *, i64, const T *, i64, T, T *, i64); \
     template void trsm_lln<T>(Ctx &, bool, i64, i64, T, const T *, i64, T *, i64);                \
     template void trsm_rlt<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);                      \
     template void trsm_llt<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);                      \

@@ -53,16 +53,28 @@ k_potf2(int n, T *A, i64 lda, int32_t *info, i64 info_off, const int32_t *abort)
     for (int j = ty; j < n; j += 16)
         for (int i = j + tx; i < n; i += 16) S[i][j] = A[(i64)j * lda + i];
     __syncthreads();
-    int fail = 0;
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) s_fail = 0;
+    __syncthreads();
     for (int j = 0; j < n; ++j) {
-        // every thread evaluates the pivot of column j identically
-        const T d = S[j][j];
-        if (!(d > T(0))) { fail = j + 1; break; }
-        const T ljj = sqrt(d);
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) col[i] = S[i][j] / ljj;
+        // warp 0 alone takes the square root and divides column j (the FP64
+        // pipe is scarce: the other warps would only repeat the same work)
+        if (threadIdx.x < 32) {
+            const T d = S[j][j];
+            if (!(d > T(0))) {
+                if (threadIdx.x == 0) s_fail = j + 1;
+            } else {
+                const T ljj = sqrt(d);
+                for (int i = j + 1 + threadIdx.x; i < n; i += 32) {
+                    const T v = S[i][j] / ljj;
+                    col[i] = v;
+                    S[i][j] = v;
+                }
+                if (threadIdx.x == 0) S[j][j] = ljj;
+            }
+        }
         __syncthreads();
-        if (threadIdx.x == 0) S[j][j] = ljj;
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) S[i][j] = col[i];
+        if (s_fail) break;
         for (int ii = j + 1 + ty; ii < n; ii += 16) {
             const T lij = col[ii];
             for (int kk = j + 1 + tx; kk <= ii; kk += 16) S[ii][kk] = fma(-lij, col[kk], S[ii][kk]);
@@ -71,7 +83,7 @@ k_potf2(int n, T *A, i64 lda, int32_t *info, i64 info_off, const int32_t *abort)
     }
     for (int j = ty; j < n; j += 16)
         for (int i = j + tx; i < n; i += 16) A[(i64)j * lda + i] = S[i][j];
-    if (fail && threadIdx.x == 0) *info = (int32_t)(info_off + fail);
+    if (s_fail && threadIdx.x == 0) *info = (int32_t)(info_off + s_fail);
 }
 
 template <typename T>
@@ -199,8 +211,9 @@ constexpr size_t PANEL_SMEM_MAX = 200 * 1024;
 constexpr int PANEL_REC = 2 + PANEL_NBMAX;
 
 // Exchange area of the multi-CTA panel kernels.  Per column each CTA
-// publishes one record {|candidate|, candidate row (bits of a long long,
-// LLONG_MAX = none), candidate row's nb entries}; the owner of row j also
+// publishes one record {key of |candidate|, candidate row (PANEL_NONE =
+// none), both stored as 64-bit patterns, then the candidate row's nb
+// entries}; the owner of row j also
 // publishes row j.  Both are double-buffered by column parity: a CTA can be
 // at most one column ahead of any other, because the arrival counter holds
 // it at the next column's barrier.
@@ -244,9 +257,23 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-__device__ __forceinline__ bool better(double v, long long i, double bv, long long bi)
+// Pivot search on integer keys: the bit pattern of |v| orders like |v| for
+// non-negative doubles, so the comparisons run on the integer pipes (the
+// FP64 pipe is the scarce unit on this GPU).  NaN gets key 0 (it never wins
+// over a number; a column of NaNs and zeros takes its lowest row).  "No
+// candidate" is key 0 with row PANEL_NONE, which loses every tie.
+constexpr int PANEL_NONE = 0x7fffffff;
+
+template <typename T>
+__device__ __forceinline__ unsigned long long abs_key(T v)
 {
-    return v > bv || (v == bv && i < bi);
+    const unsigned long long b = (unsigned long long)__double_as_longlong((double)v) & 0x7fffffffffffffffull;
+    return b > 0x7ff0000000000000ull ? 0ull : b;
+}
+
+__device__ __forceinline__ bool kbetter(unsigned long long k, int i, unsigned long long bk, int bi)
+{
+    return k > bk || (k == bk && i < bi);
 }
 
 // Row-per-thread panel.  CTA g owns panel rows [g*R, g*R + R), R <= 256;
@@ -267,9 +294,9 @@ k_panel(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, Pane
     if (abort && *abort != 0) return;
     extern __shared__ unsigned char smem_raw[];
     T *S = reinterpret_cast<T *>(smem_raw);
-    __shared__ double wv[PANEL_THREADS / 32];
-    __shared__ long long wi[PANEL_THREADS / 32];
-    __shared__ long long s_p;
+    __shared__ unsigned long long wk[PANEL_THREADS / 32];
+    __shared__ int wi[PANEL_THREADS / 32];
+    __shared__ int s_p;
     __shared__ int s_fail;
     __shared__ T urow[PANEL_NBMAX], rowj[PANEL_NBMAX];
 
@@ -286,29 +313,32 @@ k_panel(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, Pane
     for (int j = 0; j < mn; ++j) {
         const int buf = j & 1;
         // 1. this CTA's candidate: largest |a_ij|, i >= j, lowest i on ties
-        double bv = -1.0;
-        long long bi = LLONG_MAX;
-        if (have && my >= j) { bv = fabs((double)a[j * PANEL_THREADS]); bi = my; }
+        unsigned long long bk = 0;
+        int bi = PANEL_NONE;
+        if (have && my >= j) { bk = abs_key(a[j * PANEL_THREADS]); bi = (int)my; }
         for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_down_sync(0xffffffffu, bv, o);
-            const long long oi = __shfl_down_sync(0xffffffffu, bi, o);
-            if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+            const unsigned long long ok = __shfl_down_sync(0xffffffffu, bk, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (kbetter(ok, oi, bk, bi)) { bk = ok; bi = oi; }
         }
-        if (lane == 0) { wv[tid >> 5] = bv; wi[tid >> 5] = bi; }
+        if (lane == 0) { wk[tid >> 5] = bk; wi[tid >> 5] = bi; }
         __syncthreads();
         if (tid < 32) {
             // 2. block candidate (every lane of warp 0 ends with it)
-            bv = lane < PANEL_THREADS / 32 ? wv[lane] : -1.0;
-            bi = lane < PANEL_THREADS / 32 ? wi[lane] : LLONG_MAX;
+            bk = lane < PANEL_THREADS / 32 ? wk[lane] : 0ull;
+            bi = lane < PANEL_THREADS / 32 ? wi[lane] : PANEL_NONE;
             for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+                const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (kbetter(ok, oi, bk, bi)) { bk = ok; bi = oi; }
             }
             // 3. publish the record (and row j, by its owner), then arrive
             double *rec = ws->rec[buf][g];
-            if (lane == 0) { rec[0] = bv; rec[1] = __longlong_as_double(bi); }
-            if (bi != LLONG_MAX) {
+            if (lane == 0) {
+                rec[0] = __longlong_as_double((long long)bk);
+                rec[1] = __longlong_as_double((long long)bi);
+            }
+            if (bi != PANEL_NONE) {
                 const T *src = S + (int)(bi - rbeg);
                 for (int c = lane; c < nb; c += 32) rec[2 + c] = (double)src[c * PANEL_THREADS];
             }
@@ -333,34 +363,33 @@ k_panel(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, Pane
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (ok) {
                 // 4. all G candidates in one round trip (G <= 256: 8 per lane)
-                double v = -1.0;
-                long long ix = LLONG_MAX;
-                int gw = -1;
-                double qv[PANEL_GMAX / 32];
-                long long qi[PANEL_GMAX / 32];
+                unsigned long long k = 0;
+                int ix = PANEL_NONE, gw = -1;
+                unsigned long long qk[PANEL_GMAX / 32];
+                int qi[PANEL_GMAX / 32];
 #pragma unroll
                 for (int u = 0; u < PANEL_GMAX / 32; ++u) {
                     const int q = lane + 32 * u;
-                    qv[u] = -1.0;
-                    qi[u] = LLONG_MAX;
+                    qk[u] = 0;
+                    qi[u] = PANEL_NONE;
                     if (q < G) {
-                        qv[u] = __ldcg(&ws->rec[buf][q][0]);
-                        qi[u] = __double_as_longlong(__ldcg(&ws->rec[buf][q][1]));
+                        qk[u] = (unsigned long long)__double_as_longlong(__ldcg(&ws->rec[buf][q][0]));
+                        qi[u] = (int)__double_as_longlong(__ldcg(&ws->rec[buf][q][1]));
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < PANEL_GMAX / 32; ++u)
-                    if (qi[u] != LLONG_MAX && (gw < 0 || better(qv[u], qi[u], v, ix))) {
-                        v = qv[u]; ix = qi[u]; gw = lane + 32 * u;
+                    if (qi[u] != PANEL_NONE && (gw < 0 || kbetter(qk[u], qi[u], k, ix))) {
+                        k = qk[u]; ix = qi[u]; gw = lane + 32 * u;
                     }
                 for (int o = 16; o > 0; o >>= 1) {
-                    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-                    const long long oi = __shfl_xor_sync(0xffffffffu, ix, o);
+                    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, k, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
                     const int og = __shfl_xor_sync(0xffffffffu, gw, o);
-                    if (og >= 0 && (gw < 0 || better(ov, oi, v, ix))) { v = ov; ix = oi; gw = og; }
+                    if (og >= 0 && (gw < 0 || kbetter(ok, oi, k, ix))) { k = ok; ix = oi; gw = og; }
                 }
                 // 5. the pivot row, and row j where this CTA owns the pivot row
-                const long long p = (gw >= 0) ? ix : (long long)j;
+                const int p = (gw >= 0) ? ix : j;
                 const bool own_p = (p != j) && p >= rbeg && p < rbeg + rows;
                 for (int c = lane; c < nb; c += 32) {
                     urow[c] = (T)((gw >= 0) ? __ldcg(&ws->rec[buf][gw][2 + c]) : __ldcg(&ws->rowj[buf][c]));
@@ -375,7 +404,7 @@ k_panel(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, Pane
             if (tid == 0) atomicExch(info, RL_INFO_DEVICE_TIMEOUT);
             return;
         }
-        const long long p = s_p;
+        const i64 p = s_p;
         const bool own_p = (p != j) && p >= rbeg && p < rbeg + rows;
         if (g == 0 && tid == 0) ipiv[r0 + j] = (int32_t)(r0 + p + 1);
         // 6. swap, scale and rank-1 update of this thread's row
@@ -438,9 +467,9 @@ k_panel_smem(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info,
     extern __shared__ unsigned char smem_raw[];
     T *S = reinterpret_cast<T *>(smem_raw);
     __shared__ T urow[PANEL_NBMAX];
-    __shared__ double wv[PANEL_THREADS / 32];
-    __shared__ long long wi[PANEL_THREADS / 32];
-    __shared__ long long s_p;
+    __shared__ unsigned long long wk[PANEL_THREADS / 32];
+    __shared__ int wi[PANEL_THREADS / 32];
+    __shared__ int s_p;
     __shared__ int s_gw;
 
     const int tid = threadIdx.x, G = gridDim.x, g = blockIdx.x;
@@ -455,32 +484,32 @@ k_panel_smem(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info,
     const int mn = (int)min(m, (i64)nb);
     for (int j = 0; j < mn; ++j) {
         const int buf = j & 1;
-        double bv = -1.0;
-        long long bi = LLONG_MAX;
+        unsigned long long bk = 0;
+        int bi = PANEL_NONE;
         for (int r = tid; r < rows; r += blockDim.x) {
             const i64 i = rbeg + r;
             if (i < j) continue;
-            const double v = fabs((double)S[j * R + r]);
-            if (better(v, i, bv, bi)) { bv = v; bi = i; }
+            const unsigned long long k = abs_key(S[j * R + r]);
+            if (kbetter(k, (int)i, bk, bi)) { bk = k; bi = (int)i; }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            double ov = __shfl_down_sync(0xffffffffu, bv, o);
-            long long oi = __shfl_down_sync(0xffffffffu, bi, o);
-            if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+            const unsigned long long ok = __shfl_down_sync(0xffffffffu, bk, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (kbetter(ok, oi, bk, bi)) { bk = ok; bi = oi; }
         }
-        if ((tid & 31) == 0) { wv[tid >> 5] = bv; wi[tid >> 5] = bi; }
+        if ((tid & 31) == 0) { wk[tid >> 5] = bk; wi[tid >> 5] = bi; }
         __syncthreads();
         if (tid == 0) {
             for (int w = 1; w < PANEL_THREADS / 32; ++w)
-                if (better(wv[w], wi[w], bv, bi)) { bv = wv[w]; bi = wi[w]; }
-            ws->rec[buf][g][0] = bv;
-            ws->rec[buf][g][1] = __longlong_as_double(bi);
+                if (kbetter(wk[w], wi[w], bk, bi)) { bk = wk[w]; bi = wi[w]; }
+            ws->rec[buf][g][0] = __longlong_as_double((long long)bk);
+            ws->rec[buf][g][1] = __longlong_as_double((long long)bi);
             s_p = bi;
         }
         __syncthreads();
         {
-            const long long mine = s_p;
-            if (mine != LLONG_MAX && tid < nb) ws->rec[buf][g][2 + tid] = (double)S[tid * R + (int)(mine - rbeg)];
+            const int mine = s_p;
+            if (mine != PANEL_NONE && tid < nb) ws->rec[buf][g][2 + tid] = (double)S[tid * R + (int)(mine - rbeg)];
             if (j >= rbeg && j < rbeg + rows && tid < nb) ws->rowj[buf][tid] = (double)S[tid * R + (int)(j - rbeg)];
         }
         if (!grid_barrier(&ws->counter, (unsigned)G * (unsigned)(j + 1), spin_ns)) {
@@ -488,24 +517,23 @@ k_panel_smem(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info,
             return;
         }
         if (tid < 32) {
-            double v = -1.0;
-            long long ix = LLONG_MAX;
-            int gw = -1;
+            unsigned long long k = 0;
+            int ix = PANEL_NONE, gw = -1;
             for (int q = tid; q < G; q += 32) {
-                const long long qi = __double_as_longlong(__ldcg(&ws->rec[buf][q][1]));
-                const double qv = __ldcg(&ws->rec[buf][q][0]);
-                if (qi != LLONG_MAX && better(qv, qi, v, ix)) { v = qv; ix = qi; gw = q; }
+                const int qi = (int)__double_as_longlong(__ldcg(&ws->rec[buf][q][1]));
+                const unsigned long long qk = (unsigned long long)__double_as_longlong(__ldcg(&ws->rec[buf][q][0]));
+                if (qi != PANEL_NONE && (gw < 0 || kbetter(qk, qi, k, ix))) { k = qk; ix = qi; gw = q; }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                double ov = __shfl_down_sync(0xffffffffu, v, o);
-                long long oi = __shfl_down_sync(0xffffffffu, ix, o);
-                int og = __shfl_down_sync(0xffffffffu, gw, o);
-                if (og >= 0 && (gw < 0 || better(ov, oi, v, ix))) { v = ov; ix = oi; gw = og; }
+                const unsigned long long ok = __shfl_down_sync(0xffffffffu, k, o);
+                const int oi = __shfl_down_sync(0xffffffffu, ix, o);
+                const int og = __shfl_down_sync(0xffffffffu, gw, o);
+                if (og >= 0 && (gw < 0 || kbetter(ok, oi, k, ix))) { k = ok; ix = oi; gw = og; }
             }
-            if (tid == 0) { s_p = (gw >= 0) ? ix : (long long)j; s_gw = gw; }
+            if (tid == 0) { s_p = (gw >= 0) ? ix : j; s_gw = gw; }
         }
         __syncthreads();
-        const long long p = s_p;
+        const i64 p = s_p;
         const int gw = s_gw;
         if (tid < nb) urow[tid] = (T)((gw >= 0) ? __ldcg(&ws->rec[buf][gw][2 + tid]) : __ldcg(&ws->rowj[buf][tid]));
         __syncthreads();

@@ -23,6 +23,7 @@ struct Params {
     int trtri_c = 64;        // dtrtri / dlauum crossover
     long long spin_ns = 2000000000LL;
     int batch_ctas = 0;      // CTAs per SM of the batched kernels (0 = occupancy limit)
+    int tri_lanes = 0;       // lanes per vector of the triangle leaf kernels (0 = by size, 2, 4)
 };
 extern Params g_params;
 
@@ -90,6 +91,11 @@ template <typename T>
 void gemm(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, T alpha, const T *A, i64 lda,
           const T *B, i64 ldb, T beta, T *C, i64 ldc, bool lower = false);
 
+// C(m x n) := beta C + alpha S B (left, S m x m) or alpha B S (right, S n x n),
+// S symmetric with its lower triangle stored.
+template <typename T>
+void symm(Ctx &c, bool left, i64 m, i64 n, T alpha, const T *S, i64 lds, const T *Bm, i64 ldb, T beta,
+          T *C, i64 ldc);
 // B(m x n) := alpha * L^{-1} B, L lower m x m (unit or not).
 template <typename T>
 void trsm_lln(Ctx &c, bool unit, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb);
@@ -164,6 +170,12 @@ template <typename T>
 void potrf_rec_t(Ctx &c, i64 n, T *A, i64 lda, i64 off);
 template <typename T>
 void getrf_rec_t(Ctx &c, T *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r0, i64 m, i64 n);
+
+// ---- sygst (sygst.cu) ----------------------------------------------------------
+// A := L^{-1} A L^{-T} (itype 1) or L^T A L (itype 2, 3), lower storage; T is
+// sygst_work_bytes(n) of scratch or nullptr (recompute instead).
+size_t sygst_work_bytes(i64 n);
+void sygst_rec(Ctx &c, int itype, i64 n, double *A, i64 lda, const double *L, i64 ldl, double *T);
 
 // ---- precision form (mixed.cu) ----------------------------------------------
 size_t mixed_work_size(i64 n, i64 nrhs, bool lu, int prec);

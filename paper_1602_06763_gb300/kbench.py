@@ -24,7 +24,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", required=True,
                     choices=["dgemm", "dsyrk", "dtrsm", "potrf", "getrf", "trtri", "lauum", "panel",
-                             "sgemm_tc", "dsgesv", "dsposv", "getrs", "potrs", "sgetrs"])
+                             "sgemm_tc", "dsgesv", "dsposv", "getrs", "potrs", "sgetrs", "sgemm"])
     ap.add_argument("--prec", type=int, default=1, help="operand precision (rl_prec) of sgemm_tc / dsgesv")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--cond", type=float, default=1e6)
@@ -36,11 +36,14 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--trace", action="store_true")
+    ap.add_argument("--tri-lanes", type=int, default=0, help="lanes per vector of the triangle leaf kernels (2 or 4)")
     ap.add_argument("--flow", type=int, default=1, help="getrs/potrs: 1 = one-launch flow solve, 0 = recursive")
     a = ap.parse_args()
 
     if a.nb:
         r.check(r.rl_set_param(r.RL_PARAM_GETRF_PANEL, a.nb))
+    if a.tri_lanes:
+        r.check(r.rl_set_param(r.RL_PARAM_TRI_LANES, a.tri_lanes))
     if a.c:
         r.check(r.rl_set_param(r.RL_PARAM_POTRF_CROSSOVER, a.c))
         r.check(r.rl_set_param(r.RL_PARAM_TRTRI_CROSSOVER, a.c))
@@ -108,6 +111,13 @@ def main():
         work = torch.empty(lw, dtype=torch.uint8, device=dev)
         run = lambda: r.check(r.rl_sgemm_tc(a.prec, "N", "N", n, n, k, -1.0, A, n, B, k, C, n, work, lw, s))
         restore = lambda: None
+    elif a.case == "sgemm":
+        A = torch.rand(k, n, generator=g, device=dev, dtype=torch.float32)
+        B = torch.rand(n, k, generator=g, device=dev, dtype=torch.float32)
+        C = torch.rand(n, n, generator=g, device=dev, dtype=torch.float32)
+        flops = 2.0 * n * n * k
+        run = lambda: r.check(r.rl_sgemm("N", "N", n, n, k, -1.0, A, n, B, k, 1.0, C, n, s))
+        restore = lambda: None
     elif a.case in ("dgemm", "dsyrk"):
         A = torch.rand(k, n, generator=g, device=dev, dtype=torch.float64)
         B = torch.rand(n, k, generator=g, device=dev, dtype=torch.float64)
@@ -120,13 +130,14 @@ def main():
             run = lambda: r.check(r.rl_dsyrk("L", "N", n, k, -1.0, A, n, 1.0, C, n, s))
         restore = lambda: None
     elif a.case == "dtrsm":
+        # B (m x n) := B L^{-T}, the TRSM of the Cholesky recursion
         L = torch.rand(n, n, generator=g, device=dev, dtype=torch.float64)
         L.diagonal().add_(float(n))
-        B0 = torch.rand(n, n, generator=g, device=dev, dtype=torch.float64)
+        B0 = torch.rand(n, m, generator=g, device=dev, dtype=torch.float64)
         B = B0.clone()
-        flops = 1.0 * n * n * n
+        flops = 1.0 * m * n * n
         restore = lambda: B.copy_(B0)
-        run = lambda: r.check(r.rl_dtrsm("R", "L", "T", "N", n, n, 1.0, L, n, B, n, s))
+        run = lambda: r.check(r.rl_dtrsm("R", "L", "T", "N", m, n, 1.0, L, n, B, m, s))
     else:
         if a.case in ("potrf", "trtri", "lauum"):
             X = torch.rand(n, n, generator=g, device=dev, dtype=torch.float64) - 0.5

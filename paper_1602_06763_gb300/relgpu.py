@@ -45,11 +45,17 @@ _SIGS = {
                                 ctypes.c_double, _vp, _i64, _vp]),
     "rl_dsyrk": (ctypes.c_int, [_ch, _ch, _i64, _i64, ctypes.c_double, _vp, _i64, ctypes.c_double,
                                 _vp, _i64, _vp]),
+    "rl_sgemm": (ctypes.c_int, [_ch, _ch, _i64, _i64, _i64, ctypes.c_float, _vp, _i64, _vp, _i64,
+                                ctypes.c_float, _vp, _i64, _vp]),
+    "rl_ssyrk": (ctypes.c_int, [_ch, _ch, _i64, _i64, ctypes.c_float, _vp, _i64, ctypes.c_float,
+                                _vp, _i64, _vp]),
     "rl_dtrsm": (ctypes.c_int, [_ch, _ch, _ch, _ch, _i64, _i64, ctypes.c_double, _vp, _i64, _vp,
                                 _i64, _vp]),
     "rl_dtrmm": (ctypes.c_int, [_ch, _ch, _ch, _ch, _i64, _i64, ctypes.c_double, _vp, _i64, _vp,
                                 _i64, _vp]),
     "rl_trs_work_size": (ctypes.c_size_t, [_i64, _i64]),
+    "rl_dsygst_work_size": (ctypes.c_size_t, [_i64]),
+    "rl_dsygst": (ctypes.c_int, [ctypes.c_int, _ch, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
     "rl_dgetrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _sz, _vp]),
     "rl_dpotrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
     "rl_dsgesv_work_size": (_sz, [_i64, _i64, ctypes.c_int]),
@@ -104,6 +110,7 @@ RL_PARAM_GETRF_PANEL = 2
 RL_PARAM_TRTRI_CROSSOVER = 3
 RL_PARAM_SPIN_LIMIT_NS = 4
 RL_PARAM_BATCH_CTAS = 5
+RL_PARAM_TRI_LANES = 6
 
 
 def _ptr(x):
@@ -163,6 +170,16 @@ def rl_dsyrk(uplo, trans, n, k, alpha, A, lda, beta, C, ldc, stream=None):
                          _stream(stream))
 
 
+def rl_sgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):
+    return _lib.rl_sgemm(_c(transa), _c(transb), m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb, beta,
+                         _ptr(C), ldc, _stream(stream))
+
+
+def rl_ssyrk(uplo, trans, n, k, alpha, A, lda, beta, C, ldc, stream=None):
+    return _lib.rl_ssyrk(_c(uplo), _c(trans), n, k, alpha, _ptr(A), lda, beta, _ptr(C), ldc,
+                         _stream(stream))
+
+
 def rl_dtrsm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream=None):
     return _lib.rl_dtrsm(_c(side), _c(uplo), _c(transa), _c(diag), m, n, alpha, _ptr(A), lda,
                          _ptr(B), ldb, _stream(stream))
@@ -171,6 +188,14 @@ def rl_dtrsm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream=None)
 def rl_dtrmm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream=None):
     return _lib.rl_dtrmm(_c(side), _c(uplo), _c(transa), _c(diag), m, n, alpha, _ptr(A), lda,
                          _ptr(B), ldb, _stream(stream))
+
+
+def rl_dsygst_work_size(n):
+    return int(_lib.rl_dsygst_work_size(n))
+
+
+def rl_dsygst(itype, uplo, n, A, lda, B, ldb, work=None, lwork=0, stream=None):
+    return _lib.rl_dsygst(itype, _c(uplo), n, _ptr(A), lda, _ptr(B), ldb, _ptr(work), lwork, _stream(stream))
 
 
 def rl_trs_work_size(n, nrhs):
