@@ -412,6 +412,137 @@ def batched_section(count, baseline_count, dev, sp):
 # GPU arm
 # ----------------------------------------------------------------------------
 
+def routines_section(n, dev, sp):
+    """The other recursive routines at order n (Section 5 list): GFLOP/s with
+    LAPACK Working Note 41 counts, median of 3 after one warm-up, inputs
+    restored before each timed call (outside its events)."""
+    import torch
+    from paper_1602_06763_gb300 import relgpu as r, inputs
+
+    def timed(fn, restore, reps=3):
+        restore()
+        fn()
+        out = []
+        for _ in range(reps):
+            restore()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return statistics.median(out)
+
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    S0 = inputs.spd_bbt_device(n, inputs.seed_for(2, 60), device=dev)
+    L0 = S0.clone()
+    r.check(r.rl_dpotrf("L", n, L0, n, info, None, 0, sp))
+    G0 = inputs.uniform_device(n, n, inputs.seed_for(2, 61), device=dev)
+    ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+    lw = r.rl_dgetrf_work_size(n, n)
+    wk = torch.empty(lw, dtype=torch.uint8, device=dev)
+    F0 = G0.clone()
+    r.check(r.rl_dgetrf(n, n, F0, n, ipiv, info, wk, lw, sp))
+    W = torch.empty_like(S0)
+    out = {}
+    n3 = float(n) ** 3
+    cases = [
+        ("dtrtri", n3 / 3.0, L0, lambda: r.check(r.rl_dtrtri("L", "N", n, W, n, info, None, 0, sp))),
+        ("dlauum", n3 / 3.0, L0, lambda: r.check(r.rl_dlauum("L", n, W, n, info, None, 0, sp))),
+        ("dpotri", 2.0 * n3 / 3.0, L0, lambda: r.check(r.rl_dpotri("L", n, W, n, info, None, 0, sp))),
+    ]
+    lg = r.rl_dgetri_work_size(n)
+    wg = torch.empty(lg, dtype=torch.uint8, device=dev)
+    cases.append(("dgetri", 4.0 * n3 / 3.0, F0,
+                  lambda: r.check(r.rl_dgetri(n, W, n, ipiv, info, wg, lg, sp))))
+    ls = r.rl_dsygst_work_size(n)
+    ws = torch.empty(max(ls, 1), dtype=torch.uint8, device=dev)
+    for it in (1, 2):
+        cases.append((f"dsygst_itype{it}", n3, S0,
+                      lambda it=it: r.check(r.rl_dsygst(it, "L", n, W, n, L0, n, ws, ls, sp))))
+    for name, flops, src, fn in cases:
+        ms = timed(fn, lambda src=src: W.copy_(src))
+        out[name] = {"gflops": flops / (ms * 1e-3) / 1e9, "ms": ms}
+    out["n"] = n
+    out["flop_counts"] = "trtri, lauum n^3/3; potri 2n^3/3; getri 4n^3/3; sygst n^3"
+    return out
+
+
+def cusolver_section(n, dev):
+    """Context only: the vendor library (cuSOLVER through torch.linalg) on the
+    same GPU and inputs (FP64), median of 3 after one warm-up."""
+    import torch
+    from paper_1602_06763_gb300 import inputs
+    res = {}
+    S = inputs.spd_bbt_device(n, inputs.seed_for(2, 10), device=dev).reshape(n, n)
+    G = inputs.uniform_device(n, n, inputs.seed_for(2, 20), device=dev).reshape(n, n)
+    for name, fn, flops in (("cholesky", lambda: torch.linalg.cholesky(S), n ** 3 / 3.0),
+                            ("lu_factor", lambda: torch.linalg.lu_factor(G), 2.0 * n ** 3 / 3.0)):
+        try:
+            fn()
+            ts = []
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                y = fn()
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+                del y
+            ms = statistics.median(ts)
+            res[name] = {"gflops": flops / (ms * 1e-3) / 1e9, "ms": ms}
+        except Exception as e:          # context figure: report, do not fail the bench
+            res[name] = {"unavailable": str(e).splitlines()[0][:200]}
+    res["what"] = "torch.linalg (cuSOLVER) FP64 on the same inputs; context, not the target"
+    return res
+
+
+def graph_section(n, dev, sp):
+    """dpotrf and dgetrf captured once into CUDA graphs and replayed: the
+    launch overhead of the ~2000 launches per factorization, measured."""
+    import torch
+    from paper_1602_06763_gb300 import relgpu as r, inputs
+    res = {}
+    S0 = inputs.spd_bbt_device(n, inputs.seed_for(2, 10), device=dev)
+    G0 = inputs.uniform_device(n, n, inputs.seed_for(2, 20), device=dev)
+    A = torch.empty_like(S0)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+    lw = r.rl_dgetrf_work_size(n, n)
+    wk = torch.empty(lw, dtype=torch.uint8, device=dev)
+    for name, src, flops, call in (
+            ("dpotrf", S0, n ** 3 / 3.0, lambda s: r.check(r.rl_dpotrf("L", n, A, n, info, None, 0, s))),
+            ("dgetrf", G0, 2.0 * n ** 3 / 3.0, lambda s: r.check(r.rl_dgetrf(n, n, A, n, ipiv, info, wk, lw, s)))):
+        try:
+            A.copy_(src)
+            call(sp)                                   # first call outside capture (one-time set-up)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            cs = torch.cuda.Stream()
+            with torch.cuda.stream(cs):
+                A.copy_(src)
+                torch.cuda.synchronize()
+                with torch.cuda.graph(g, stream=cs):
+                    call(cs.cuda_stream)
+            ts = []
+            for _ in range(3):
+                A.copy_(src)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                g.replay()
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            if int(info[0]) != 0:
+                raise RuntimeError(f"info {int(info[0])} after replay")
+            ms = statistics.median(ts)
+            res[name] = {"gflops": flops / (ms * 1e-3) / 1e9, "ms": ms}
+            del g
+        except Exception as e:
+            res[name] = {"unavailable": str(e).splitlines()[0][:200]}
+    return res
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -551,6 +682,10 @@ def run_gpu(args, rank, world, local_rank):
     if args.batch_count > 0:
         batched = batched_section(args.batch_count, args.batch_baseline, dev, sp)
 
+    others = routines_section(args.others_n, dev, sp) if args.others_n > 0 else None
+    graphs = graph_section(n, dev, sp) if args.graph else None
+    cusolver = cusolver_section(n, dev) if args.cusolver else None
+
     cpu = None
     if world == 1 and args.cpu_n > 0:
         from oracle import build as obuild
@@ -579,6 +714,9 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": launches,
         "mixed_solve": mixed,
         "batched": batched,
+        "other_routines": others,
+        "graph_replay": graphs,
+        "cusolver_context": cusolver,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clocks,
@@ -608,6 +746,10 @@ def main():
                     help="matrices per kind in the batching-form comparison (0 skips it)")
     ap.add_argument("--batch-baseline", type=int, default=2000,
                     help="matrices timed through the single-matrix path for the comparison")
+    ap.add_argument("--others-n", type=int, default=8192,
+                    help="order of the trtri/lauum/potri/getri/sygst section (0 skips it)")
+    ap.add_argument("--graph", type=int, default=1, help="time CUDA-graph replay of dpotrf/dgetrf (0 skips)")
+    ap.add_argument("--cusolver", type=int, default=1, help="time torch.linalg (cuSOLVER) as context (0 skips)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

@@ -151,6 +151,24 @@ int rl_dpotrs(char uplo, int64_t n, int64_t nrhs, const double *A, int64_t lda, 
               int64_t ldb, void *work, size_t lwork, rl_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * dgetri -- inverse of a general matrix from its LU factors (Section 5:
+ * xtrtri is the building block of xgetri).  A and ipiv from rl_dgetrf (square
+ * n); on exit A holds A^{-1} = U^{-1} L^{-1} P: U and L inverted in place by
+ * the recursive TRTRI (Fig. 4 and its upper-triangular transpose), their
+ * product formed in place by a recursion of GEMM/TRMM updates, then P's
+ * column interchanges applied in reverse order (as LAPACK's dgetri).
+ * info (device, int32): 0, or k if U(k,k) is exactly zero (A is then left
+ *   unchanged, as LAPACK's dgetri leaves it when dtrtri fails).
+ * work (device): rl_dgetri_work_size(n) bytes (about 8n), else
+ *   RL_ERR_WORKSPACE.  n <= 40960 (the permutation plan lives in one CTA's
+ *   shared memory), else RL_ERR_UNSUPPORTED.
+ * Argument numbers: 1 n, 2 A, 3 lda.  Stream-ordered; no synchronization.
+ * ------------------------------------------------------------------------- */
+size_t rl_dgetri_work_size(int64_t n);
+int rl_dgetri(int64_t n, double *A, int64_t lda, const int32_t *ipiv, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * dsygst (Section 5, xsygst) -- reduction of the symmetric-definite
  * generalized eigenproblem to standard form, with B's Cholesky factor L
  * (lower, from rl_dpotrf) in B:

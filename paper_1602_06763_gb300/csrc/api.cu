@@ -92,7 +92,7 @@ static void getrf_rec(Ctx &c, double *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64
 
 // Triangular inverse, Fig. 4: trtri(TL); BL := BL TL; BL := -BR^{-1} BL;
 // trtri(BR).
-static void trtri_rec(Ctx &c, bool unit, i64 n, double *A, i64 lda)
+void trtri_rec(Ctx &c, bool unit, i64 n, double *A, i64 lda)
 {
     if (n <= 0) return;
     if (n <= g_params.trtri_c) { trti2(c, unit, n, A, lda); return; }
@@ -454,6 +454,25 @@ static int trs_t(bool lu, int64_t n, int64_t nrhs, const T *A, int64_t lda, cons
 }
 
 extern "C" {
+
+size_t rl_dgetri_work_size(int64_t n) { return n <= 0 ? 0 : getri_work_bytes(n); }
+
+int rl_dgetri(int64_t n, double *A, int64_t lda, const int32_t *ipiv, int32_t *info, void *work, size_t lwork,
+              rl_stream_t stream)
+{
+    if (n < 0) return -1;
+    if (n > 0 && A == nullptr) return -2;
+    if (lda < imax1(n)) return -3;
+    if (info == nullptr || (n > 0 && ipiv == nullptr)) return RL_ERR_NULL_POINTER;
+    if (n > GETRI_MAX_N) return RL_ERR_UNSUPPORTED;
+    Ctx c = make_ctx(stream, info, work, lwork);
+    c.abort = info;                               // a zero diagonal of U leaves A unchanged
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    if (n == 0) return finish(c);
+    if (work == nullptr || lwork < getri_work_bytes(n)) return RL_ERR_WORKSPACE;
+    getri(c, n, A, lda, ipiv, work);
+    return finish(c);
+}
 
 size_t rl_dsygst_work_size(int64_t n) { return n <= 0 ? 0 : sygst_work_bytes(n); }
 

@@ -699,6 +699,36 @@ void trmm_llt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
     trmm_llt<T>(c, m2, n, alpha, L + m1 + m1 * ldl, ldl, B + m1, ldb);
 }
 
+template <typename T>
+void trmm_lun(Ctx &c, i64 m, i64 n, T alpha, const T *U, i64 ldu, T *B, i64 ldb)
+{
+    if (m <= 0 || n <= 0) return;
+    if (m <= TRX_NB) {
+        // columns of B times M^T with M = U^T staged as a lower triangle
+        launch_tri<T, TRI_MUL, false, false, true>(c, K_TRMM, n, (int)m, alpha, U, ldu, B, ldb);
+        return;
+    }
+    const i64 m1 = split_q(m, TRX_NB), m2 = m - m1;
+    trmm_lun<T>(c, m1, n, alpha, U, ldu, B, ldb);
+    gemm<T>(c, false, false, m1, n, m2, alpha, U + m1 * ldu, ldu, B + m1, ldb, T(1), B, ldb);
+    trmm_lun<T>(c, m2, n, alpha, U + m1 + m1 * ldu, ldu, B + m1, ldb);
+}
+
+template <typename T>
+void trsm_run(Ctx &c, i64 m, i64 n, T alpha, const T *U, i64 ldu, T *B, i64 ldb)
+{
+    if (m <= 0 || n <= 0) return;
+    if (n <= TRX_NB) {
+        // each row x^T U^{-1}: forward substitution with M = U^T
+        launch_tri<T, TRI_FWD, true, false, true>(c, K_TRSM, m, (int)n, alpha, U, ldu, B, ldb);
+        return;
+    }
+    const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
+    trsm_run<T>(c, m, n1, alpha, U, ldu, B, ldb);
+    gemm<T>(c, false, false, m, n2, n1, T(-1), B, ldb, U + n1 * ldu, ldu, alpha, B + n1 * ldb, ldb);
+    trsm_run<T>(c, m, n2, T(1), U + n1 + n1 * ldu, ldu, B + n1 * ldb, ldb);
+}
+
 #define RL_INST_BLAS3(T)                                                                          \
     template void gemm<T>(Ctx &, bool, bool, i64, i64, i64, T, const T *, i64, const T *, i64, T, \
                           T *, i64, bool);                                                        \
@@ -708,7 +738,9 @@ void trmm_llt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
     template void trsm_llt<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);                      \
     template void trsm_lun<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);                      \
     template void trmm_rln<T>(Ctx &, bool, i64, i64, T, const T *, i64, T *, i64);                \
-    template void trmm_llt<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);
+    template void trmm_llt<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);                      \
+    template void trmm_lun<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);                      \
+    template void trsm_run<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);
 RL_INST_BLAS3(double)
 RL_INST_BLAS3(float)
 #undef RL_INST_BLAS3

@@ -10,17 +10,15 @@
 //  k_lauu2        unblocked L^T L (n <= 64), one CTA.
 //  k_diag_scan    first exactly-zero diagonal entry (dtrtri's info).
 //  k_panel        fused LU panel of an m x nb block (nb <= 64): per column a
-//                 pivot search (warp-shuffle argmax, lowest row on ties), the
-//                 row swap, the division of the column by the pivot and the
-//                 rank-1 update.  The co-resident CTAs of one cooperative
-//                 launch each keep up to 256 rows in registers (one row per
-//                 thread) and exchange their pivot candidates through
-//                 flag-carrying slots in a small global workspace: a slot
-//                 holds the candidate and the column it belongs to, so
-//                 publishing a candidate is also the barrier arrival.
-//  k_panel_smem   the same algorithm with the rows in shared memory and an
-//                 arrival-counter barrier, for panels taller than 256 rows
-//                 per CTA.
+//                 pivot search (argmax on integer keys, lowest row on ties),
+//                 the row swap, the division of the column by the pivot and
+//                 the rank-1 update.  The co-resident CTAs of one cooperative
+//                 launch each keep up to 256 rows in shared memory (one row
+//                 per thread); per column one warp per CTA publishes the
+//                 CTA's candidate record, arrives on a grid counter and reads
+//                 all candidates back.
+//  k_panel_smem   the same algorithm with the rows as a column-major slab,
+//                 for panels taller than 256 rows per CTA.
 //  k_laswp        row interchanges: each CTA turns the swap sequence into the
 //                 net permutation of the touched rows (in shared memory) and
 //                 then moves every touched row of its columns with one
@@ -99,16 +97,17 @@ void potf2(Ctx &c, i64 n, T *A, i64 lda, i64 info_off)
 // L x = e_j: x_jj = 1/l_jj; x_ij = -(sum_{k=j}^{i-1} l_ik x_kj) / l_ii.
 // L packed by rows, X packed by columns (each thread owns its column).
 // ----------------------------------------------------------------------------
-template <bool UNIT>
+template <bool UNIT, bool UPPER>
 __global__ void __launch_bounds__(BASE_N)
 k_trti2(int n, double *A, i64 lda, const int32_t *abort)
 {
     if (abort && *abort != 0) return;
     __shared__ double Lp[BASE_PACK];
     __shared__ double Xp[BASE_PACK];
+    // UPPER: invert M = U^T (lower) and store X = (M^{-1})^T = U^{-1}
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         int i = e % n, k = e / n;
-        if (i >= k) Lp[tix(i, k)] = A[(i64)k * lda + i];
+        if (i >= k) Lp[tix(i, k)] = UPPER ? A[(i64)i * lda + k] : A[(i64)k * lda + i];
     }
     __syncthreads();
     const int j = threadIdx.x;
@@ -127,17 +126,23 @@ k_trti2(int n, double *A, i64 lda, const int32_t *abort)
         int i = e % n, jj = e / n;
         if (i > jj || (i == jj && !UNIT)) {
             const int cs = jj * n - jj * (jj - 1) / 2;
-            A[(i64)jj * lda + i] = Xp[cs + (i - jj)];
+            if (UPPER) A[(i64)i * lda + jj] = Xp[cs + (i - jj)];
+            else A[(i64)jj * lda + i] = Xp[cs + (i - jj)];
         }
     }
 }
 
-void trti2(Ctx &c, bool unit, i64 n, double *A, i64 lda)
+void trti2(Ctx &c, bool unit, i64 n, double *A, i64 lda, bool upper)
 {
     if (n <= 0) return;
     Launch L(c, K_TRTI2, (double)n * n * n / 3.0, 0.0);
-    if (unit) k_trti2<true><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
-    else k_trti2<false><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
+    if (upper) {
+        if (unit) k_trti2<true, true><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
+        else k_trti2<false, true><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
+    } else {
+        if (unit) k_trti2<true, false><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
+        else k_trti2<false, false><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
+    }
 }
 
 // ----------------------------------------------------------------------------

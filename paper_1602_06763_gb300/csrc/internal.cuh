@@ -108,6 +108,12 @@ void trsm_llt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
 // B(m x n) := alpha * U^{-1} B, U upper m x m, non-unit.
 template <typename T>
 void trsm_lun(Ctx &c, i64 m, i64 n, T alpha, const T *U, i64 ldu, T *B, i64 ldb);
+// B(m x n) := alpha * U B, U upper m x m, non-unit.
+template <typename T>
+void trmm_lun(Ctx &c, i64 m, i64 n, T alpha, const T *U, i64 ldu, T *B, i64 ldb);
+// B(m x n) := alpha * B U^{-1}, U upper n x n, non-unit.
+template <typename T>
+void trsm_run(Ctx &c, i64 m, i64 n, T alpha, const T *U, i64 ldu, T *B, i64 ldb);
 // B(m x n) := alpha * B L, L lower n x n (unit or not).
 template <typename T>
 void trmm_rln(Ctx &c, bool unit, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb);
@@ -118,7 +124,8 @@ void trmm_llt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
 // ---- base cases and row interchanges (factor.cu) ---------------------------
 template <typename T>
 void potf2(Ctx &c, i64 n, T *A, i64 lda, i64 info_off);
-void trti2(Ctx &c, bool unit, i64 n, double *A, i64 lda);
+// upper: invert the upper triangle instead (stored in place)
+void trti2(Ctx &c, bool unit, i64 n, double *A, i64 lda, bool upper = false);
 void lauu2(Ctx &c, i64 n, double *A, i64 lda);
 void diag_zero_scan(Ctx &c, i64 n, const double *A, i64 lda);
 // Panel LU of the m x nb block at A (row/col offset r0 in the full matrix);
@@ -170,6 +177,16 @@ template <typename T>
 void potrf_rec_t(Ctx &c, i64 n, T *A, i64 lda, i64 off);
 template <typename T>
 void getrf_rec_t(Ctx &c, T *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r0, i64 m, i64 n);
+
+// Lower triangular inverse in place (Fig. 4), unit or not (api.cu).
+void trtri_rec(Ctx &c, bool unit, i64 n, double *A, i64 lda);
+
+// ---- getri (getri.cu) -----------------------------------------------------------
+// A := A^{-1} from the LU factors in place (inv(U) inv(L) P); work holds
+// getri_work_bytes(n); n <= GETRI_MAX_N.
+constexpr i64 GETRI_MAX_N = 40960;
+size_t getri_work_bytes(i64 n);
+void getri(Ctx &c, i64 n, double *A, i64 lda, const int32_t *ipiv, void *work);
 
 // ---- sygst (sygst.cu) ----------------------------------------------------------
 // A := L^{-1} A L^{-T} (itype 1) or L^T A L (itype 2, 3), lower storage; T is

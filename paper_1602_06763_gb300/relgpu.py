@@ -54,6 +54,8 @@ _SIGS = {
     "rl_dtrmm": (ctypes.c_int, [_ch, _ch, _ch, _ch, _i64, _i64, ctypes.c_double, _vp, _i64, _vp,
                                 _i64, _vp]),
     "rl_trs_work_size": (ctypes.c_size_t, [_i64, _i64]),
+    "rl_dgetri_work_size": (ctypes.c_size_t, [_i64]),
+    "rl_dgetri": (ctypes.c_int, [_i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
     "rl_dsygst_work_size": (ctypes.c_size_t, [_i64]),
     "rl_dsygst": (ctypes.c_int, [ctypes.c_int, _ch, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
     "rl_dgetrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _sz, _vp]),
@@ -188,6 +190,14 @@ def rl_dtrsm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream=None)
 def rl_dtrmm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream=None):
     return _lib.rl_dtrmm(_c(side), _c(uplo), _c(transa), _c(diag), m, n, alpha, _ptr(A), lda,
                          _ptr(B), ldb, _stream(stream))
+
+
+def rl_dgetri_work_size(n):
+    return int(_lib.rl_dgetri_work_size(n))
+
+
+def rl_dgetri(n, A, lda, ipiv, info, work, lwork, stream=None):
+    return _lib.rl_dgetri(n, _ptr(A), lda, _ptr(ipiv), _ptr(info), _ptr(work), lwork, _stream(stream))
 
 
 def rl_dsygst_work_size(n):
