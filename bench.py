@@ -50,6 +50,12 @@ FP64_FMA_PER_SM_CLK = 2
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
+# DRAM traffic of the dominant kernel (k_gemm, the GEMM kind: 2111 launches
+# per step) per launch, from the ncu launch list of this workload in
+# profiles/launches_dpotrf_dgetrf_n16384.md (172.7 GB over 2111 launches).
+# Reset to None whenever k_gemm changes.
+GEMM_DRAM_BYTES_PER_LAUNCH = 172.704e9 / 2111
+
 
 def flops_potrf(n: int) -> float:
     return n ** 3 / 3.0 + n ** 2 / 2.0 + n / 6.0
@@ -182,6 +188,25 @@ def oracle_sample(n_cpu: int, seed_k: int = 0):
     return (flops_potrf(n_cpu) + flops_getrf(n_cpu)) / dt / 1e9, dt
 
 
+def cpu_lapack_context(n_cpu: int):
+    """Context only: the host's LAPACK (torch.linalg on CPU) on the same
+    sample, GFLOP/s of cholesky + lu_factor."""
+    try:
+        import torch
+        from paper_1602_06763_gb300 import inputs
+        A = torch.from_numpy(inputs.spd_bbt(n_cpu, seed=inputs.seed_for(2, 500)))
+        G = torch.from_numpy(inputs.uniform(n_cpu, n_cpu, seed=inputs.seed_for(2, 600)))
+        torch.linalg.cholesky(A[:64, :64])
+        t0 = time.perf_counter()
+        torch.linalg.cholesky(A)
+        torch.linalg.lu_factor(G)
+        dt = time.perf_counter() - t0
+        return {"value": (flops_potrf(n_cpu) + flops_getrf(n_cpu)) / dt / 1e9, "unit": UNIT,
+                "threads": torch.get_num_threads(), "what": "torch.linalg CPU (host LAPACK), context"}
+    except Exception as e:
+        return {"unavailable": str(e).splitlines()[0][:200]}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return 0
@@ -217,7 +242,7 @@ def run_reference(args, rank):
 PRECS = {"fp32": 0, "tf32": 1, "bf16": 2, "fp16s": 3, "tf32x3": 4}
 
 
-def mixed_section(n, nrhs, cond, precs, dev, sp):
+def mixed_section(n, nrhs, cond, precs, dev, sp, reps=2):
     """Solve A X = B (A = U diag(sigma) V^T or Q diag(sigma) Q^T, sigma
     log-spaced 1..cond, 64 Householder reflectors each side; B iid N(0,1))
     with the FP64 path (getrf+getrs / potrf+potrs) and with rl_dsgesv /
@@ -257,8 +282,8 @@ def mixed_section(n, nrhs, cond, precs, dev, sp):
         ltw = r.rl_trs_work_size(n, nrhs)
         tw = torch.empty(ltw, dtype=torch.uint8, device=dev) if ltw else None
         res = {}
-        # FP64 path (one warm-up, then timed)
-        for rep in range(2):
+        # FP64 path (warm-up(s), then timed)
+        for rep in range(reps):
             A = A0.clone()
             X = B.clone()
             if spd:
@@ -274,7 +299,7 @@ def mixed_section(n, nrhs, cond, precs, dev, sp):
             lwm = (r.rl_dsposv_work_size if spd else r.rl_dsgesv_work_size)(n, nrhs, prec)
             wm = torch.empty(lwm, dtype=torch.uint8, device=dev)
             it = torch.zeros(1, dtype=torch.int32, device=dev)
-            for rep in range(2):
+            for rep in range(reps):
                 A = A0.clone()
                 X = torch.zeros_like(B)
                 if spd:
@@ -624,9 +649,13 @@ def run_gpu(args, rank, world, local_rank):
     if dom_name:
         d = trace[dom_name]
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        alg_bytes = d["bytes"] / d["launches"] if d["launches"] else None
         roofline = {
             "bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": GEMM_DRAM_BYTES_PER_LAUNCH if dom_name == "gemm" else None,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+            "algorithmic_bytes_per_launch": alg_bytes,
             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2070 MHz",
             "launches_per_step": d["launches"] / args.steps,
             "share_of_step": d["ms"] / ms_total,
@@ -678,6 +707,12 @@ def run_gpu(args, rank, world, local_rank):
         mixed = mixed_section(args.mixed_n, args.mixed_nrhs, args.mixed_cond,
                               [p for p in args.mixed_precs.split(",") if p], dev, sp)
 
+    mixed_large = None
+    if args.mixed4_n > 0:
+        torch.cuda.empty_cache()
+        mixed_large = mixed_section(args.mixed4_n, args.mixed4_nrhs, args.mixed4_cond,
+                                    [p for p in args.mixed4_precs.split(",") if p], dev, sp, reps=1)
+
     batched = None
     if args.batch_count > 0:
         batched = batched_section(args.batch_count, args.batch_baseline, dev, sp)
@@ -692,7 +727,8 @@ def run_gpu(args, rank, world, local_rank):
         obuild.build()
         gfl, dt = oracle_sample(args.cpu_n)
         cpu = {"value": gfl, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"oracle dpotrf+dgetrf at n={args.cpu_n} (same recipes), c=24, {dt:.1f} s"}
+               "sample": f"oracle dpotrf+dgetrf at n={args.cpu_n} (same recipes), c=24, {dt:.1f} s",
+               "lapack_context": cpu_lapack_context(args.cpu_n)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -713,6 +749,7 @@ def run_gpu(args, rank, world, local_rank):
                     for k, v in trace.items()},
         "gpu_launches": launches,
         "mixed_solve": mixed,
+        "mixed_solve_large": mixed_large,
         "batched": batched,
         "other_routines": others,
         "graph_replay": graphs,
@@ -742,6 +779,11 @@ def main():
     ap.add_argument("--mixed-nrhs", type=int, default=16)
     ap.add_argument("--mixed-cond", type=float, default=1e6)
     ap.add_argument("--mixed-precs", default="fp32,tf32x3,tf32,bf16,fp16s")
+    ap.add_argument("--mixed4-n", type=int, default=32768,
+                    help="order of the large precision-form case, 1 RHS (0 skips it)")
+    ap.add_argument("--mixed4-nrhs", type=int, default=1)
+    ap.add_argument("--mixed4-cond", type=float, default=1e4)
+    ap.add_argument("--mixed4-precs", default="fp32,bf16")
     ap.add_argument("--batch-count", type=int, default=20000,
                     help="matrices per kind in the batching-form comparison (0 skips it)")
     ap.add_argument("--batch-baseline", type=int, default=2000,

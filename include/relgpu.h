@@ -199,6 +199,12 @@ int rl_spotrf(char uplo, int64_t n, float *A, int64_t lda, int32_t *info, void *
               size_t lwork, rl_stream_t stream);
 int rl_sgetrf(int64_t m, int64_t n, float *A, int64_t lda, int32_t *ipiv, int32_t *info,
               void *work, size_t lwork, rl_stream_t stream);
+int rl_strtri(char uplo, char diag, int64_t n, float *A, int64_t lda, int32_t *info,
+              void *work, size_t lwork, rl_stream_t stream);
+int rl_slauum(char uplo, int64_t n, float *A, int64_t lda, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream);
+int rl_spotri(char uplo, int64_t n, float *A, int64_t lda, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream);
 int rl_sgetrs(char trans, int64_t n, int64_t nrhs, const float *A, int64_t lda,
               const int32_t *ipiv, float *B, int64_t ldb, void *work, size_t lwork,
               rl_stream_t stream);
@@ -388,6 +394,14 @@ int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda,
  *                              the TRSM/TRMM leaves: 0 (default) picks 2
  *                              for leaves of >= 12288 vectors, else 4; 2 or
  *                              4 force one; all give bit-identical results
+ *   RL_PARAM_LOOKAHEAD         1 (default): the LU and Cholesky recursions
+ *                              run the part of each large trailing update
+ *                              that the next level needs last on an internal
+ *                              stream, beside that level's first half (same
+ *                              results, bit for bit); 0: the caller's stream
+ *                              alone.  Factorizations whose updates run on
+ *                              the tensor cores (precision form) share one
+ *                              packing workspace and run on one stream.
  * rl_set_param returns 0 or RL_ERR_PARAM; rl_get_param returns the value or
  * -1 for an unknown key.
  * ------------------------------------------------------------------------- */
@@ -397,7 +411,8 @@ enum {
     RL_PARAM_TRTRI_CROSSOVER = 3,
     RL_PARAM_SPIN_LIMIT_NS = 4,
     RL_PARAM_BATCH_CTAS = 5,
-    RL_PARAM_TRI_LANES = 6
+    RL_PARAM_TRI_LANES = 6,
+    RL_PARAM_LOOKAHEAD = 7
 };
 int rl_set_param(int key, int64_t value);
 int64_t rl_get_param(int key);

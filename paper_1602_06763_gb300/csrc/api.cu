@@ -36,47 +36,180 @@ void note(Ctx &c, cudaError_t e)
     if (e != cudaSuccess && c.err == cudaSuccess) c.err = e;
 }
 
+// ---- lookahead resources ----------------------------------------------------
+// One internal stream per device for the trailing updates that run beside
+// the recursion (created once, lowest priority so the factorization's own
+// kernels are preferred), and per host thread a pool of events indexed by
+// recursion depth: calls from different threads never share an event, and
+// calls that share the stream only serialize their side work on it.
+namespace {
+constexpr int LA_DEPTH = 48;
+cudaStream_t g_side[128];
+std::mutex g_side_mu;
+
+struct LaEvents {
+    cudaEvent_t start[LA_DEPTH] = {}, done[LA_DEPTH] = {};
+    bool ready = false, failed = false;
+};
+thread_local LaEvents t_ev[128];
+}  // namespace
+
+// Side stream and this thread's events for the current device, or false
+// (then the recursion runs on the caller's stream alone).
+static bool lookahead_resources(cudaStream_t *side, LaEvents **ev)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return false;
+    {
+        std::lock_guard<std::mutex> lock(g_side_mu);
+        if (g_side[dev] == nullptr) {
+            int lo = 0, hi = 0;
+            cudaStream_t s = nullptr;
+            if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+                cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, lo) != cudaSuccess)
+                return false;
+            g_side[dev] = s;
+        }
+        *side = g_side[dev];
+    }
+    LaEvents &e = t_ev[dev];
+    if (e.failed) return false;
+    if (!e.ready) {
+        for (int i = 0; i < LA_DEPTH; ++i)
+            if (cudaEventCreateWithFlags(&e.start[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&e.done[i], cudaEventDisableTiming) != cudaSuccess) {
+                e.failed = true;
+                return false;
+            }
+        e.ready = true;
+    }
+    *ev = &e;
+    return true;
+}
+
+// The side stream may run GEMMs concurrently with the caller's stream only
+// when no GEMM of the call stages operands in a shared workspace (the
+// tensor-core updates pack into c.tcwork).
+static bool lookahead_ok(const Ctx &c) { return g_params.lookahead && c.tcwork == nullptr; }
+
 // ---- recursions -------------------------------------------------------------
 
 // Cholesky: potrf(A11); A21 := A21 L11^{-T}; A22 -= A21 A21^T; potrf(A22).
+//
+// Lookahead (as for the LU below): the SYRK update of A22 is split at the
+// next level's split n2a; its leading n2a x n2a block runs on the caller's
+// stream, the rest (a GEMM below it and the trailing SYRK) on the side
+// stream, waited on only before the next level's TRSM.
+template <typename T>
+static void potrf_rec_la(Ctx &c, i64 n, T *A, i64 lda, i64 off, cudaEvent_t pending, int depth)
+{
+    if (n <= 0) return;
+    if (n <= g_params.potrf_c) {
+        if (pending) note(c, cudaStreamWaitEvent(c.s, pending, 0));
+        potf2<T>(c, n, A, lda, off);
+        return;
+    }
+    const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
+    T *A21 = A + n1, *A22 = A + n1 + n1 * lda;
+    potrf_rec_la<T>(c, n1, A, lda, off, nullptr, depth + 1);
+    if (pending) note(c, cudaStreamWaitEvent(c.s, pending, 0));
+    trsm_rlt<T>(c, n2, n1, T(1), A, lda, A21, lda);
+    cudaStream_t side = nullptr;
+    LaEvents *ev = nullptr;
+    cudaEvent_t next_pending = nullptr;
+    const i64 n2a = split_q(n2, TRX_NB);
+    if (lookahead_ok(c) && depth < LA_DEPTH && n2 >= LA_MIN_N && n2 > g_params.potrf_c &&
+        lookahead_resources(&side, &ev)) {
+        gemm<T>(c, false, true, n2a, n2a, n1, T(-1), A21, lda, A21, lda, T(1), A22, lda, true);
+        note(c, cudaEventRecord(ev->start[depth], c.s));
+        Ctx cs = c;
+        cs.s = side;
+        note(cs, cudaStreamWaitEvent(side, ev->start[depth], 0));
+        const i64 nr = n2 - n2a;
+        gemm<T>(cs, false, true, nr, n2a, n1, T(-1), A21 + n2a, lda, A21, lda, T(1), A22 + n2a, lda);
+        gemm<T>(cs, false, true, nr, nr, n1, T(-1), A21 + n2a, lda, A21 + n2a, lda, T(1),
+                A22 + n2a + n2a * lda, lda, true);
+        note(cs, cudaEventRecord(ev->done[depth], side));
+        if (cs.err != cudaSuccess) note(c, cs.err);
+        next_pending = ev->done[depth];
+    } else {
+        gemm<T>(c, false, true, n2, n2, n1, T(-1), A21, lda, A21, lda, T(1), A22, lda, true);
+    }
+    potrf_rec_la<T>(c, n2, A22, lda, off + n1, next_pending, depth + 1);
+}
+
 template <typename T>
 void potrf_rec_t(Ctx &c, i64 n, T *A, i64 lda, i64 off)
 {
-    if (n <= 0) return;
-    if (n <= g_params.potrf_c) { potf2<T>(c, n, A, lda, off); return; }
-    const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
-    T *A21 = A + n1, *A22 = A + n1 + n1 * lda;
-    potrf_rec_t<T>(c, n1, A, lda, off);
-    trsm_rlt<T>(c, n2, n1, T(1), A, lda, A21, lda);
-    gemm<T>(c, false, true, n2, n2, n1, T(-1), A21, lda, A21, lda, T(1), A22, lda, true);
-    potrf_rec_t<T>(c, n2, A22, lda, off + n1);
+    potrf_rec_la<T>(c, n, A, lda, off, nullptr, 0);
 }
 
 // LU of the m x n block whose top-left corner is (r0, r0) of the matrix A0
 // (m_tot rows).  Pivots are written as global 1-based rows.
+//
+// Lookahead: the trailing update A22 -= A21 A12 is split by columns at the
+// next level's own split; the left part (all the next level factors first)
+// runs on the caller's stream, the right part on the side stream, and
+// `pending` (recorded after it) is waited on only where the next level first
+// touches those columns (its row interchanges of the right half).  The
+// latency-bound panels of the left part thus overlap the right part's GEMM.
+// Every element sees the same operations in the same order either way.
 template <typename T>
-void getrf_rec_t(Ctx &c, T *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r0, i64 m, i64 n)
+static void getrf_rec_la(Ctx &c, T *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r0, i64 m, i64 n,
+                         cudaEvent_t pending, int depth)
 {
     if (m <= 0 || n <= 0) return;
     T *A = A0 + r0 + r0 * lda;
     const i64 nb = g_params.getrf_nb;
-    if (n <= nb) { getf2_panel<T>(c, m, n, A, lda, ipiv, r0); return; }
+    if (n <= nb) {
+        if (pending) note(c, cudaStreamWaitEvent(c.s, pending, 0));
+        getf2_panel<T>(c, m, n, A, lda, ipiv, r0);
+        return;
+    }
     if (m < n) {
         // wide: factor the leading m x m block, then swap and solve the rest
-        getrf_rec_t<T>(c, A0, lda, m_tot, ipiv, r0, m, m);
+        if (pending) note(c, cudaStreamWaitEvent(c.s, pending, 0));
+        getrf_rec_la<T>(c, A0, lda, m_tot, ipiv, r0, m, m, nullptr, depth + 1);
         laswp<T>(c, A0, lda, m_tot, r0 + m, n - m, r0, r0 + m, ipiv);
         trsm_lln<T>(c, true, m, n - m, T(1), A, lda, A + m * lda, lda);
         return;
     }
     const i64 n1 = split_q(n, n > 2 * TRX_NB ? TRX_NB : nb), n2 = n - n1;
-    getrf_rec_t<T>(c, A0, lda, m_tot, ipiv, r0, m, n1);
+    getrf_rec_la<T>(c, A0, lda, m_tot, ipiv, r0, m, n1, nullptr, depth + 1);
+    if (pending) note(c, cudaStreamWaitEvent(c.s, pending, 0));
     laswp<T>(c, A0, lda, m_tot, r0 + n1, n2, r0, r0 + n1, ipiv);
     trsm_lln<T>(c, true, n1, n2, T(1), A, lda, A + n1 * lda, lda);
-    gemm<T>(c, false, false, m - n1, n2, n1, T(-1), A + n1, lda, A + n1 * lda, lda, T(1),
-            A + n1 + n1 * lda, lda);
-    getrf_rec_t<T>(c, A0, lda, m_tot, ipiv, r0 + n1, m - n1, n2);
-    const i64 mn2 = (m - n1) < n2 ? (m - n1) : n2;
+    T *A21 = A + n1, *A12 = A + n1 * lda, *A22 = A + n1 + n1 * lda;
+    cudaEvent_t next_pending = nullptr;
+    cudaStream_t side = nullptr;
+    LaEvents *ev = nullptr;
+    const i64 m2 = m - n1;
+    // the next level's split of its n2 columns (the rule above, at order n2)
+    const i64 n2a = split_q(n2, n2 > 2 * TRX_NB ? TRX_NB : nb);
+    if (lookahead_ok(c) && depth < LA_DEPTH && n2 >= LA_MIN_N && m2 >= n2 &&
+        lookahead_resources(&side, &ev)) {
+        gemm<T>(c, false, false, m2, n2a, n1, T(-1), A21, lda, A12, lda, T(1), A22, lda);
+        note(c, cudaEventRecord(ev->start[depth], c.s));
+        Ctx cs = c;
+        cs.s = side;
+        note(cs, cudaStreamWaitEvent(side, ev->start[depth], 0));
+        gemm<T>(cs, false, false, m2, n2 - n2a, n1, T(-1), A21, lda, A12 + n2a * lda, lda, T(1),
+                A22 + n2a * lda, lda);
+        note(cs, cudaEventRecord(ev->done[depth], side));
+        if (cs.err != cudaSuccess) note(c, cs.err);
+        next_pending = ev->done[depth];
+    } else {
+        gemm<T>(c, false, false, m2, n2, n1, T(-1), A21, lda, A12, lda, T(1), A22, lda);
+    }
+    getrf_rec_la<T>(c, A0, lda, m_tot, ipiv, r0 + n1, m2, n2, next_pending, depth + 1);
+    const i64 mn2 = m2 < n2 ? m2 : n2;
     laswp<T>(c, A0, lda, m_tot, r0, n1, r0 + n1, r0 + n1 + mn2, ipiv);
+}
+
+template <typename T>
+void getrf_rec_t(Ctx &c, T *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r0, i64 m, i64 n)
+{
+    getrf_rec_la<T>(c, A0, lda, m_tot, ipiv, r0, m, n, nullptr, 0);
 }
 
 template void potrf_rec_t<double>(Ctx &, i64, double *, i64, i64);
@@ -92,29 +225,33 @@ static void getrf_rec(Ctx &c, double *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64
 
 // Triangular inverse, Fig. 4: trtri(TL); BL := BL TL; BL := -BR^{-1} BL;
 // trtri(BR).
-void trtri_rec(Ctx &c, bool unit, i64 n, double *A, i64 lda)
+template <typename T>
+void trtri_rec(Ctx &c, bool unit, i64 n, T *A, i64 lda)
 {
     if (n <= 0) return;
-    if (n <= g_params.trtri_c) { trti2(c, unit, n, A, lda); return; }
+    if (n <= g_params.trtri_c) { trti2<T>(c, unit, n, A, lda); return; }
     const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
-    double *BL = A + n1, *BR = A + n1 + n1 * lda;
-    trtri_rec(c, unit, n1, A, lda);
-    trmm_rln(c, unit, n2, n1, 1.0, A, lda, BL, lda);
-    trsm_lln(c, unit, n2, n1, -1.0, BR, lda, BL, lda);
-    trtri_rec(c, unit, n2, BR, lda);
+    T *BL = A + n1, *BR = A + n1 + n1 * lda;
+    trtri_rec<T>(c, unit, n1, A, lda);
+    trmm_rln<T>(c, unit, n2, n1, T(1), A, lda, BL, lda);
+    trsm_lln<T>(c, unit, n2, n1, T(-1), BR, lda, BL, lda);
+    trtri_rec<T>(c, unit, n2, BR, lda);
 }
+template void trtri_rec<double>(Ctx &, bool, i64, double *, i64);
+template void trtri_rec<float>(Ctx &, bool, i64, float *, i64);
 
 // A := L^T L: lauum(A11); A11 += A21^T A21; A21 := A22^T A21; lauum(A22).
-static void lauum_rec(Ctx &c, i64 n, double *A, i64 lda)
+template <typename T>
+static void lauum_rec(Ctx &c, i64 n, T *A, i64 lda)
 {
     if (n <= 0) return;
-    if (n <= g_params.trtri_c) { lauu2(c, n, A, lda); return; }
+    if (n <= g_params.trtri_c) { lauu2<T>(c, n, A, lda); return; }
     const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
-    double *A21 = A + n1, *A22 = A + n1 + n1 * lda;
-    lauum_rec(c, n1, A, lda);
-    gemm(c, true, false, n1, n1, n2, 1.0, A21, lda, A21, lda, 1.0, A, lda, true);
-    trmm_llt(c, n2, n1, 1.0, A22, lda, A21, lda);
-    lauum_rec(c, n2, A22, lda);
+    T *A21 = A + n1, *A22 = A + n1 + n1 * lda;
+    lauum_rec<T>(c, n1, A, lda);
+    gemm<T>(c, true, false, n1, n1, n2, T(1), A21, lda, A21, lda, T(1), A, lda, true);
+    trmm_llt<T>(c, n2, n1, T(1), A22, lda, A21, lda);
+    lauum_rec<T>(c, n2, A22, lda);
 }
 
 static bool is_l(char u) { return u == 'L' || u == 'l'; }
@@ -183,8 +320,11 @@ int rl_dgetrf(int64_t m, int64_t n, double *A, int64_t lda, int32_t *ipiv, int32
     return finish(c);
 }
 
-int rl_dtrtri(char uplo, char diag, int64_t n, double *A, int64_t lda, int32_t *info,
-              void *work, size_t lwork, rl_stream_t stream)
+}  // extern "C"
+
+template <typename T>
+static int trtri_api(char uplo, char diag, int64_t n, T *A, int64_t lda, int32_t *info, void *work,
+                     size_t lwork, rl_stream_t stream)
 {
     if (!is_l(uplo) && !is_u(uplo)) return -1;
     const bool unit = (diag == 'U' || diag == 'u');
@@ -197,43 +337,69 @@ int rl_dtrtri(char uplo, char diag, int64_t n, double *A, int64_t lda, int32_t *
     Ctx c = make_ctx(stream, info, work, lwork);
     c.abort = info;
     note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
-    if (!unit) diag_zero_scan(c, n, A, lda);
-    trtri_rec(c, unit, n, A, lda);
+    if (!unit) diag_zero_scan<T>(c, n, A, lda);
+    trtri_rec<T>(c, unit, n, A, lda);
     return finish(c);
+}
+
+// potri = false: A := L^T L (lauum); true: A := (L L^T)^{-1} = L^{-T} L^{-1}
+template <typename T>
+static int lauum_api(bool potri, char uplo, int64_t n, T *A, int64_t lda, int32_t *info, void *work,
+                     size_t lwork, rl_stream_t stream)
+{
+    if (!is_l(uplo) && !is_u(uplo)) return -1;
+    if (n < 0) return -2;
+    if (n > 0 && A == nullptr) return -3;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (info == nullptr) return RL_ERR_NULL_POINTER;
+    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
+    Ctx c = make_ctx(stream, info, work, lwork);
+    c.abort = info;
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    if (potri) {
+        diag_zero_scan<T>(c, n, A, lda);
+        trtri_rec<T>(c, false, n, A, lda);
+    }
+    lauum_rec<T>(c, n, A, lda);
+    return finish(c);
+}
+
+extern "C" {
+
+int rl_dtrtri(char uplo, char diag, int64_t n, double *A, int64_t lda, int32_t *info,
+              void *work, size_t lwork, rl_stream_t stream)
+{
+    return trtri_api<double>(uplo, diag, n, A, lda, info, work, lwork, stream);
 }
 
 int rl_dlauum(char uplo, int64_t n, double *A, int64_t lda, int32_t *info, void *work,
               size_t lwork, rl_stream_t stream)
 {
-    if (!is_l(uplo) && !is_u(uplo)) return -1;
-    if (n < 0) return -2;
-    if (n > 0 && A == nullptr) return -3;
-    if (lda < (n > 1 ? n : 1)) return -4;
-    if (info == nullptr) return RL_ERR_NULL_POINTER;
-    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
-    Ctx c = make_ctx(stream, info, work, lwork);
-    c.abort = info;
-    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
-    lauum_rec(c, n, A, lda);
-    return finish(c);
+    return lauum_api<double>(false, uplo, n, A, lda, info, work, lwork, stream);
 }
 
 int rl_dpotri(char uplo, int64_t n, double *A, int64_t lda, int32_t *info, void *work,
               size_t lwork, rl_stream_t stream)
 {
-    if (!is_l(uplo) && !is_u(uplo)) return -1;
-    if (n < 0) return -2;
-    if (n > 0 && A == nullptr) return -3;
-    if (lda < (n > 1 ? n : 1)) return -4;
-    if (info == nullptr) return RL_ERR_NULL_POINTER;
-    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
-    Ctx c = make_ctx(stream, info, work, lwork);
-    c.abort = info;
-    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
-    diag_zero_scan(c, n, A, lda);
-    trtri_rec(c, false, n, A, lda);
-    lauum_rec(c, n, A, lda);
-    return finish(c);
+    return lauum_api<double>(true, uplo, n, A, lda, info, work, lwork, stream);
+}
+
+int rl_strtri(char uplo, char diag, int64_t n, float *A, int64_t lda, int32_t *info,
+              void *work, size_t lwork, rl_stream_t stream)
+{
+    return trtri_api<float>(uplo, diag, n, A, lda, info, work, lwork, stream);
+}
+
+int rl_slauum(char uplo, int64_t n, float *A, int64_t lda, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream)
+{
+    return lauum_api<float>(false, uplo, n, A, lda, info, work, lwork, stream);
+}
+
+int rl_spotri(char uplo, int64_t n, float *A, int64_t lda, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream)
+{
+    return lauum_api<float>(true, uplo, n, A, lda, info, work, lwork, stream);
 }
 
 // ---- BLAS-3 layer ------------------------------------------------------------
@@ -773,6 +939,10 @@ int rl_set_param(int key, int64_t value)
         if (value != 0 && value != 2 && value != 4) return RL_ERR_PARAM;
         g_params.tri_lanes = (int)value;
         return RL_SUCCESS;
+    case RL_PARAM_LOOKAHEAD:
+        if (value != 0 && value != 1) return RL_ERR_PARAM;
+        g_params.lookahead = (int)value;
+        return RL_SUCCESS;
     default:
         return RL_ERR_PARAM;
     }
@@ -787,6 +957,7 @@ int64_t rl_get_param(int key)
     case RL_PARAM_SPIN_LIMIT_NS: return g_params.spin_ns;
     case RL_PARAM_BATCH_CTAS: return g_params.batch_ctas;
     case RL_PARAM_TRI_LANES: return g_params.tri_lanes;
+    case RL_PARAM_LOOKAHEAD: return g_params.lookahead;
     default: return -1;
     }
 }

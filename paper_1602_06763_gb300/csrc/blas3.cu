@@ -146,6 +146,15 @@ k_gemm(i64 m, i64 n, i64 k, T alpha, const T *__restrict__ A, i64 lda,
     }
 }
 
+// Algorithmic bytes of one GEMM/SYRK call: each operand read once, C read
+// and written once (the lower triangle only for SYRK).
+static double gemm_bytes(i64 m, i64 n, i64 k, bool lower, size_t esz)
+{
+    const double c_elems = lower ? (double)n * (double)(n + 1) / 2.0 : (double)m * (double)n;
+    const double ab = lower ? (double)n * (double)k : (double)m * (double)k + (double)k * (double)n;
+    return (ab + 2.0 * c_elems) * (double)esz;
+}
+
 template <typename T, bool TA, bool TB, bool LOWER>
 static void launch_gemm(Ctx &c, i64 m, i64 n, i64 k, T alpha, const T *A, i64 lda, const T *B,
                         i64 ldb, T beta, T *C, i64 ldc)
@@ -154,7 +163,7 @@ static void launch_gemm(Ctx &c, i64 m, i64 n, i64 k, T alpha, const T *A, i64 ld
     i64 grid = LOWER ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
     if (grid <= 0) return;
     const double flops = LOWER ? (double)k * (double)n * (double)(n + 1) : 2.0 * m * n * k;
-    Launch L(c, LOWER ? K_SYRK : K_GEMM, flops, 0.0);
+    Launch L(c, LOWER ? K_SYRK : K_GEMM, flops, gemm_bytes(m, n, k, LOWER, sizeof(T)));
     k_gemm<T, TA, TB, LOWER><<<(unsigned)grid, 256, 0, c.s>>>(
         m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, c.abort, (int)tiles_m);
 }
@@ -188,8 +197,10 @@ k_sgemm128(i64 m, i64 n, i64 k, float alpha, const float *__restrict__ A, i64 ld
         tn = blockIdx.x / tiles_m;
     }
     const i64 i0 = (i64)tm * SG_BM, j0 = (i64)tn * SG_BN;
-    __shared__ __align__(16) float As[2][SG_BK][SG_BM];
-    __shared__ __align__(16) float Bs[2][SG_BK][SG_BN];
+    // rows padded by 4 floats: the k-contiguous staging stores (8 k-values x 4
+    // rows per warp) then hit 32 distinct banks; rows stay 16-byte aligned
+    __shared__ __align__(16) float As[2][SG_BK][SG_BM + 4];
+    __shared__ __align__(16) float Bs[2][SG_BK][SG_BN + 4];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
 
     float acc[8][8];
@@ -288,7 +299,7 @@ static void launch_sgemm128(Ctx &c, i64 m, i64 n, i64 k, float alpha, const floa
     const i64 tiles_m = (m + SG_BM - 1) / SG_BM, tiles_n = (n + SG_BN - 1) / SG_BN;
     const i64 grid = LOWER ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
     const double flops = LOWER ? (double)k * (double)n * (double)(n + 1) : 2.0 * m * n * k;
-    Launch L(c, LOWER ? K_SYRK : K_GEMM, flops, 0.0);
+    Launch L(c, LOWER ? K_SYRK : K_GEMM, flops, gemm_bytes(m, n, k, LOWER, sizeof(float)));
     k_sgemm128<TA, TB, LOWER><<<(unsigned)grid, 256, 0, c.s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
                                                                 c.abort, (int)tiles_m);
 }
@@ -358,7 +369,7 @@ void symm(Ctx &c, bool left, i64 m, i64 n, T alpha, const T *S, i64 lds, const T
     if (m <= 0 || n <= 0) return;
     const i64 k = left ? m : n;
     const i64 tiles_m = (m + GEMM_BM - 1) / GEMM_BM, tiles_n = (n + GEMM_BN - 1) / GEMM_BN;
-    Launch L(c, K_GEMM, 2.0 * m * n * k, 0.0);
+    Launch L(c, K_GEMM, 2.0 * m * n * k, gemm_bytes(m, n, k, false, sizeof(T)));
     if (left)
         k_gemm<T, false, false, false, 1><<<(unsigned)(tiles_m * tiles_n), 256, 0, c.s>>>(
             m, n, k, alpha, S, lds, Bm, ldb, beta, C, ldc, c.abort, (int)tiles_m);

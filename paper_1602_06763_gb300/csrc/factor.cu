@@ -97,13 +97,13 @@ void potf2(Ctx &c, i64 n, T *A, i64 lda, i64 info_off)
 // L x = e_j: x_jj = 1/l_jj; x_ij = -(sum_{k=j}^{i-1} l_ik x_kj) / l_ii.
 // L packed by rows, X packed by columns (each thread owns its column).
 // ----------------------------------------------------------------------------
-template <bool UNIT, bool UPPER>
+template <typename T, bool UNIT, bool UPPER>
 __global__ void __launch_bounds__(BASE_N)
-k_trti2(int n, double *A, i64 lda, const int32_t *abort)
+k_trti2(int n, T *A, i64 lda, const int32_t *abort)
 {
     if (abort && *abort != 0) return;
-    __shared__ double Lp[BASE_PACK];
-    __shared__ double Xp[BASE_PACK];
+    __shared__ T Lp[BASE_PACK];
+    __shared__ T Xp[BASE_PACK];
     // UPPER: invert M = U^T (lower) and store X = (M^{-1})^T = U^{-1}
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         int i = e % n, k = e / n;
@@ -114,9 +114,9 @@ k_trti2(int n, double *A, i64 lda, const int32_t *abort)
     if (j < n) {
         // column j of X occupies Xp[cs .. cs + n - j), entry i at cs + (i - j)
         const int cs = j * n - j * (j - 1) / 2;
-        Xp[cs] = UNIT ? 1.0 : 1.0 / Lp[tix(j, j)];
+        Xp[cs] = UNIT ? T(1) : T(1) / Lp[tix(j, j)];
         for (int i = j + 1; i < n; ++i) {
-            double s = 0.0;
+            T s = T(0);
             for (int k = j; k < i; ++k) s = fma(Lp[tix(i, k)], Xp[cs + (k - j)], s);
             Xp[cs + (i - j)] = UNIT ? -s : -s / Lp[tix(i, i)];
         }
@@ -132,27 +132,31 @@ k_trti2(int n, double *A, i64 lda, const int32_t *abort)
     }
 }
 
-void trti2(Ctx &c, bool unit, i64 n, double *A, i64 lda, bool upper)
+template <typename T>
+void trti2(Ctx &c, bool unit, i64 n, T *A, i64 lda, bool upper)
 {
     if (n <= 0) return;
     Launch L(c, K_TRTI2, (double)n * n * n / 3.0, 0.0);
     if (upper) {
-        if (unit) k_trti2<true, true><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
-        else k_trti2<false, true><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
+        if (unit) k_trti2<T, true, true><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
+        else k_trti2<T, false, true><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
     } else {
-        if (unit) k_trti2<true, false><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
-        else k_trti2<false, false><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
+        if (unit) k_trti2<T, true, false><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
+        else k_trti2<T, false, false><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
     }
 }
+template void trti2<double>(Ctx &, bool, i64, double *, i64, bool);
+template void trti2<float>(Ctx &, bool, i64, float *, i64, bool);
 
 // ----------------------------------------------------------------------------
 // lauu2: (L^T L)_ij = sum_{k=i}^{n-1} l_ki l_kj for i >= j, from a staged copy.
 // ----------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(256)
-k_lauu2(int n, double *A, i64 lda, const int32_t *abort)
+k_lauu2(int n, T *A, i64 lda, const int32_t *abort)
 {
     if (abort && *abort != 0) return;
-    __shared__ double Lp[BASE_PACK];
+    __shared__ T Lp[BASE_PACK];
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         int i = e % n, k = e / n;
         if (i >= k) Lp[tix(i, k)] = A[(i64)k * lda + i];
@@ -161,29 +165,33 @@ k_lauu2(int n, double *A, i64 lda, const int32_t *abort)
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         int i = e % n, j = e / n;
         if (i < j) continue;
-        double s = 0.0;
+        T s = T(0);
         for (int k = i; k < n; ++k) s = fma(Lp[tix(k, i)], Lp[tix(k, j)], s);
         A[(i64)j * lda + i] = s;
     }
 }
 
-void lauu2(Ctx &c, i64 n, double *A, i64 lda)
+template <typename T>
+void lauu2(Ctx &c, i64 n, T *A, i64 lda)
 {
     if (n <= 0) return;
     Launch L(c, K_LAUU2, (double)n * n * n / 3.0, 0.0);
-    k_lauu2<<<1, 256, 0, c.s>>>((int)n, A, lda, c.abort);
+    k_lauu2<T><<<1, 256, 0, c.s>>>((int)n, A, lda, c.abort);
 }
+template void lauu2<double>(Ctx &, i64, double *, i64);
+template void lauu2<float>(Ctx &, i64, float *, i64);
 
 // ----------------------------------------------------------------------------
 // First exactly-zero diagonal entry -> info (dtrtri leaves A unchanged then).
 // ----------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(1024)
-k_diag_scan(i64 n, const double *A, i64 lda, int32_t *info)
+k_diag_scan(i64 n, const T *A, i64 lda, int32_t *info)
 {
     __shared__ i64 wmin[32];
     i64 best = LLONG_MAX;
     for (i64 i = threadIdx.x; i < n; i += blockDim.x)
-        if (A[i * lda + i] == 0.0 && i < best) best = i;
+        if (A[i * lda + i] == T(0) && i < best) best = i;
     for (int o = 16; o > 0; o >>= 1) {
         i64 v = __shfl_down_sync(0xffffffffu, best, o);
         if (v < best) best = v;
@@ -197,12 +205,15 @@ k_diag_scan(i64 n, const double *A, i64 lda, int32_t *info)
     }
 }
 
-void diag_zero_scan(Ctx &c, i64 n, const double *A, i64 lda)
+template <typename T>
+void diag_zero_scan(Ctx &c, i64 n, const T *A, i64 lda)
 {
     if (n <= 0) return;
-    Launch L(c, K_DIAG, 0.0, (double)n * sizeof(double));
-    k_diag_scan<<<1, 1024, 0, c.s>>>(n, A, lda, c.info);
+    Launch L(c, K_DIAG, 0.0, (double)n * sizeof(T));
+    k_diag_scan<T><<<1, 1024, 0, c.s>>>(n, A, lda, c.info);
 }
+template void diag_zero_scan<double>(Ctx &, i64, const double *, i64);
+template void diag_zero_scan<float>(Ctx &, i64, const float *, i64);
 
 // ----------------------------------------------------------------------------
 // LU panel.

@@ -4,7 +4,8 @@
 // The recursive TRSM (Section 3's halving applied to the triangle) turns a
 // thin B into many GEMMs of 16 columns, each a separate launch whose cost is
 // mostly latency.  Here the triangle is cut into 64-row blocks and every
-// (row block, 16-column chunk) is one CTA of a single launch, forming a
+// (row block, chunk of 16 columns in FP32 or 4 in FP64) is one CTA of a
+// single launch, forming a
 // dataflow: the CTA of block i
 //   1. inverts its diagonal block T_ii in shared memory (64 independent
 //      column substitutions),
@@ -31,7 +32,10 @@ namespace rl {
 namespace {
 
 constexpr int FB = 64;          // row block
-constexpr int FR = 16;          // right-hand sides per CTA
+// right-hand sides per CTA: 16 in FP32; 4 in FP64, where each block's
+// products are FP64-pipe bound and four times as many CTAs share them
+template <typename T> struct FlowCols { static constexpr int value = sizeof(T) == 8 ? 4 : 16; };
+constexpr int FR_MIN = 4;
 constexpr int FT = 256;         // threads: 64 rows x 4 groups of 4 columns
 constexpr int FP = FB + 1;      // padded column stride of the shared tiles
 
@@ -94,7 +98,7 @@ __device__ __forceinline__ void fetch_tile(T (&pre)[PER], const T *A, i64 lda, i
     }
 }
 
-template <typename T, int FORM, bool UNIT>
+template <typename T, int FORM, bool UNIT, int FR = FlowCols<T>::value>
 __global__ void __launch_bounds__(FT)
 k_flow(i64 n, int nrhs, const T *A, i64 lda, T *B, i64 ldb, unsigned *ticket, unsigned *flags,
        int32_t *status, long long spin_ns, int32_t *info, const int32_t *abort)
@@ -117,14 +121,15 @@ k_flow(i64 n, int nrhs, const T *A, i64 lda, T *B, i64 ldb, unsigned *ticket, un
     const int bi = fwd ? step : nblk - 1 - step;
     const i64 r0 = (i64)bi * FB;
     const int c0 = ch * FR;
-    const int r = tid & (FB - 1), g = tid >> 6;        // this thread: row r, columns 4g .. 4g+3
+    constexpr int CPT = FR / 4;                        // columns per thread
+    const int r = tid & (FB - 1), g = tid >> 6;        // this thread: row r, columns CPT*g ..
     unsigned *myflag = flags + (size_t)bi * nch + ch;
 
     // right-hand side block
-    T acc[4];
+    T acc[CPT];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int col = c0 + 4 * g + q;
+    for (int q = 0; q < CPT; ++q) {
+        const int col = c0 + CPT * g + q;
         acc[q] = (r0 + r < n && col < nrhs) ? B[(r0 + r) + (i64)col * ldb] : T(0);
     }
 
@@ -203,28 +208,30 @@ k_flow(i64 n, int nrhs, const T *A, i64 lda, T *B, i64 ldb, unsigned *ticket, un
 #pragma unroll 8
         for (int k = 0; k < FB; ++k) {
             const T t = Ts[k * FP + r];
-            const T *xr = Xs + k * FR + 4 * g;
+            const T *xr = Xs + k * FR + CPT * g;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = fma(-t, xr[q], acc[q]);
+            for (int q = 0; q < CPT; ++q) acc[q] = fma(-t, xr[q], acc[q]);
         }
     }
 
     // 3. X_i = T_ii^{-1} (B_i - sum T_ik X_k)
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 4; ++q) Xs[r * FR + 4 * g + q] = acc[q];
+    for (int q = 0; q < CPT; ++q) Xs[r * FR + CPT * g + q] = acc[q];
     __syncthreads();
-    T out[4] = {T(0), T(0), T(0), T(0)};
+    T out[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) out[q] = T(0);
 #pragma unroll 8
     for (int k = 0; k < FB; ++k) {
         const T t = Inv[k * FP + r];
-        const T *xr = Xs + k * FR + 4 * g;
+        const T *xr = Xs + k * FR + CPT * g;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) out[q] = fma(t, xr[q], out[q]);
+        for (int q = 0; q < CPT; ++q) out[q] = fma(t, xr[q], out[q]);
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int col = c0 + 4 * g + q;
+    for (int q = 0; q < CPT; ++q) {
+        const int col = c0 + CPT * g + q;
         if (r0 + r < n && col < nrhs) B[(r0 + r) + (i64)col * ldb] = out[q];
     }
     __syncthreads();
@@ -234,6 +241,7 @@ k_flow(i64 n, int nrhs, const T *A, i64 lda, T *B, i64 ldb, unsigned *ticket, un
 template <typename T, int FORM, bool UNIT>
 void launch_flow(Ctx &c, i64 n, i64 nrhs, const T *A, i64 lda, T *B, i64 ldb, void *ws)
 {
+    constexpr int FR = FlowCols<T>::value;
     const i64 nblk = (n + FB - 1) / FB, nch = (nrhs + FR - 1) / FR;
     int32_t *status = static_cast<int32_t *>(ws);
     unsigned *ticket = static_cast<unsigned *>(ws) + 64;
@@ -257,7 +265,8 @@ void launch_flow(Ctx &c, i64 n, i64 nrhs, const T *A, i64 lda, T *B, i64 ldb, vo
 
 size_t flow_ws_bytes(i64 n, i64 nrhs)
 {
-    const i64 nblk = (n + FB - 1) / FB, nch = (nrhs + FR - 1) / FR;
+    // flags for the narrowest chunking (either element type)
+    const i64 nblk = (n + FB - 1) / FB, nch = (nrhs + FR_MIN - 1) / FR_MIN;
     return ((65 + (size_t)(nblk > 0 ? nblk : 1) * (size_t)(nch > 0 ? nch : 1)) * sizeof(unsigned) + 255) &
            ~(size_t)255;
 }

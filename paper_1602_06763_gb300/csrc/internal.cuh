@@ -24,6 +24,7 @@ struct Params {
     long long spin_ns = 2000000000LL;
     int batch_ctas = 0;      // CTAs per SM of the batched kernels (0 = occupancy limit)
     int tri_lanes = 0;       // lanes per vector of the triangle leaf kernels (0 = by size, 2, 4)
+    int lookahead = 1;       // LU/Cholesky: trailing update split across the side stream (0 = off)
 };
 extern Params g_params;
 
@@ -65,6 +66,10 @@ struct Launch {
     Launch(Ctx &ctx, int k, double f, double b);
     ~Launch();
 };
+
+// Smallest trailing order that the LU/Cholesky recursions split across the
+// side stream.
+constexpr i64 LA_MIN_N = 512;
 
 // Largest triangle handled by the TRSM/TRMM/base kernels in shared memory.
 constexpr int TRX_NB = 64;
@@ -125,9 +130,12 @@ void trmm_llt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
 template <typename T>
 void potf2(Ctx &c, i64 n, T *A, i64 lda, i64 info_off);
 // upper: invert the upper triangle instead (stored in place)
-void trti2(Ctx &c, bool unit, i64 n, double *A, i64 lda, bool upper = false);
-void lauu2(Ctx &c, i64 n, double *A, i64 lda);
-void diag_zero_scan(Ctx &c, i64 n, const double *A, i64 lda);
+template <typename T>
+void trti2(Ctx &c, bool unit, i64 n, T *A, i64 lda, bool upper = false);
+template <typename T>
+void lauu2(Ctx &c, i64 n, T *A, i64 lda);
+template <typename T>
+void diag_zero_scan(Ctx &c, i64 n, const T *A, i64 lda);
 // Panel LU of the m x nb block at A (row/col offset r0 in the full matrix);
 // writes ipiv[r0 .. r0+min(m,nb)) as global 1-based rows.  c.work holds the
 // panel workspace (panel_ws_bytes()).
@@ -179,7 +187,8 @@ template <typename T>
 void getrf_rec_t(Ctx &c, T *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r0, i64 m, i64 n);
 
 // Lower triangular inverse in place (Fig. 4), unit or not (api.cu).
-void trtri_rec(Ctx &c, bool unit, i64 n, double *A, i64 lda);
+template <typename T>
+void trtri_rec(Ctx &c, bool unit, i64 n, T *A, i64 lda);
 
 // ---- getri (getri.cu) -----------------------------------------------------------
 // A := A^{-1} from the LU factors in place (inv(U) inv(L) P); work holds

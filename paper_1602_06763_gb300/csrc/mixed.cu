@@ -397,7 +397,7 @@ int mixed_solve(Ctx &c, bool lu, i64 n, i64 nrhs, double *A, i64 lda, int32_t *i
         f.abort = &st->winfo;
         f.work = pws;
         f.prec = prec;
-        f.tcwork = w + Ly.TC;
+        f.tcwork = prec == RL_PREC_FP32 ? nullptr : w + Ly.TC;   // no packing space in the FP32 form
         f.tclwork = Ly.tc_bytes;
         if (lu) getrf_rec_t<float>(f, W, ldw, n, ipiv, 0, n, n);
         else potrf_rec_t<float>(f, n, W, ldw, 0);

@@ -34,6 +34,9 @@ _SIGS = {
     "rl_dtrtri": (ctypes.c_int, [_ch, _ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
     "rl_dlauum": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
     "rl_dpotri": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_strtri": (ctypes.c_int, [_ch, _ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_slauum": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_spotri": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
     "rl_host_work_size": (_sz, [ctypes.c_char_p, _i64, _i64, _i64]),
     "rl_dpotrf_host": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
     "rl_dgetrf_host": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
@@ -113,6 +116,7 @@ RL_PARAM_TRTRI_CROSSOVER = 3
 RL_PARAM_SPIN_LIMIT_NS = 4
 RL_PARAM_BATCH_CTAS = 5
 RL_PARAM_TRI_LANES = 6
+RL_PARAM_LOOKAHEAD = 7
 
 
 def _ptr(x):
@@ -160,6 +164,18 @@ def rl_dlauum(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
 
 def rl_dpotri(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
     return _lib.rl_dpotri(_c(uplo), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork, _stream(stream))
+
+def rl_strtri(uplo, diag, n, A, lda, info, work=None, lwork=0, stream=None):
+    return _lib.rl_strtri(_c(uplo), _c(diag), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork,
+                          _stream(stream))
+
+
+def rl_slauum(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
+    return _lib.rl_slauum(_c(uplo), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_spotri(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
+    return _lib.rl_spotri(_c(uplo), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork, _stream(stream))
 
 
 def rl_dgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):

@@ -66,3 +66,30 @@ def test_host_logic_without_gpu(built):
     assert r.rl_set_param(r.RL_PARAM_GETRF_PANEL, 32) == 0
     assert "workspace" in r.rl_status_string(r.RL_ERR_WORKSPACE)
     assert "illegal" in r.rl_status_string(-3)
+
+
+def test_host_logic_of_the_other_routines(built):
+    from paper_1602_06763_gb300 import relgpu as r
+    # size queries are pure host arithmetic
+    assert r.rl_trs_work_size(16384, 16) > 0 and r.rl_trs_work_size(100, 65) == 0
+    assert r.rl_trs_work_size(0, 4) == 0
+    assert r.rl_dsygst_work_size(64) == 0 and r.rl_dsygst_work_size(1000) == 8 * 512 * 488   # split 512 + 488
+    assert r.rl_dgetri_work_size(1000) >= 8 * 1000
+    # argument errors come back before any device work
+    assert r.rl_dsygst(0, "L", 4, 8, 4, 8, 4, stream=0) == -1
+    assert r.rl_dsygst(1, "Q", 4, 8, 4, 8, 4, stream=0) == -2
+    assert r.rl_dsygst(1, "L", -1, 8, 4, 8, 4, stream=0) == -3
+    assert r.rl_dsygst(1, "L", 4, 8, 3, 8, 4, stream=0) == -5
+    assert r.rl_dsygst(2, "U", 4, 8, 4, 8, 4, stream=0) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_dgetri(-1, 8, 1, 8, 8, None, 0, stream=0) == -1
+    assert r.rl_dgetri(4, 8, 3, 8, 8, None, 0, stream=0) == -3
+    assert r.rl_dgetri(4, 8, 4, 8, None, None, 0, stream=0) == r.RL_ERR_NULL_POINTER
+    assert r.rl_strtri("L", "X", 4, 8, 4, 8, stream=0) == -2
+    assert r.rl_slauum("U", 4, 8, 4, 8, stream=0) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_spotri("L", 4, 8, 3, 8, stream=0) == -4
+    assert r.rl_sgemm("X", "N", 4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, stream=0) == -1
+    assert r.rl_ssyrk("U", "N", 4, 4, 1.0, 8, 4, 0.0, 8, 4, stream=0) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_dgetrs("T", 4, 1, 8, 4, 8, 8, 4, stream=0) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_dpotrs("L", 4, 1, 8, 3, 8, 4, stream=0) == -5
+    assert r.rl_set_param(r.RL_PARAM_TRI_LANES, 3) == r.RL_ERR_PARAM
+    assert r.rl_get_param(r.RL_PARAM_TRI_LANES) == 0

@@ -91,3 +91,53 @@ def test_single_exact_inputs():
     F = from_dev32(dA, n, n)
     assert np.array_equal(ipiv.cpu().numpy()[:n], inputs.expected_ipiv(perm))
     assert np.array_equal(np.tril(F, -1) + np.eye(n), Lx) and np.array_equal(np.triu(F), U)
+
+
+@pytest.mark.parametrize("n", [1, 40, 130, 300])
+def test_strtri_slauum_spotri_vs_oracle(n):
+    r = G.lib()
+    A = inputs.spd_bbt(n, seed=inputs.seed_for(1, 3500 + n)).astype(np.float32).astype(np.float64)
+    L64, info = oracle.potrf(A, c=24)
+    L = np.asfortranarray(np.tril(L64).astype(np.float32).astype(np.float64))
+    info = G.int_buf(1, -7)
+    # trtri: ||L X - I|| / (n u ||L|| ||X||) in FP32 units
+    dX = to_dev32(L)
+    assert r.rl_strtri("L", "N", n, dX.data_ptr(), n, info.data_ptr()) == 0
+    G.sync()
+    assert int(info[0]) == 0
+    X = np.tril(from_dev32(dX, n, n))
+    assert oracle.res_trtri(L, X) * SCALE <= 10.0
+    # lauum against the oracle's product
+    dX = to_dev32(L)
+    assert r.rl_slauum("L", n, dX.data_ptr(), n, info.data_ptr()) == 0
+    G.sync()
+    got = np.tril(from_dev32(dX, n, n))
+    ref = np.tril(L.T @ L)
+    assert np.max(np.abs(got - ref)) <= 4 * n * 2.0 ** -24 * np.max(np.abs(ref))
+    # potri: the inverse of A = L L^T
+    dX = to_dev32(L)
+    assert r.rl_spotri("L", n, dX.data_ptr(), n, info.data_ptr()) == 0
+    G.sync()
+    Xp = np.tril(from_dev32(dX, n, n))
+    LLt = L @ L.T
+    assert oracle.res_potri(LLt, Xp) * SCALE <= 10.0
+
+
+def test_strtri_exact_and_zero_diagonal():
+    r = G.lib()
+    n = 120
+    L = inputs.integer_trtri(n, seed=inputs.seed_for(1, 3600))
+    dX = to_dev32(L)
+    info = G.int_buf(1, -7)
+    assert r.rl_strtri("L", "N", n, dX.data_ptr(), n, info.data_ptr()) == 0
+    G.sync()
+    X = np.tril(from_dev32(dX, n, n))
+    ref, _ = oracle.trtri(L, c=24)
+    assert np.array_equal(X, np.tril(ref))
+    Z = L.copy(order="F")
+    Z[77, 77] = 0.0
+    dZ = to_dev32(Z)
+    assert r.rl_strtri("L", "N", n, dZ.data_ptr(), n, info.data_ptr()) == 0
+    G.sync()
+    assert int(info[0]) == 78
+    assert np.array_equal(from_dev32(dZ, n, n), Z)
