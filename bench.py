@@ -398,12 +398,39 @@ def batched_section(count, baseline_count, dev, sp):
                 fn = r.rl_dgetrf_vbatched if prec == "f64" else r.rl_sgetrf_vbatched
                 run = lambda: r.check(fn(count, nvec, ptrs, nvec, pptrs, info, 256, wk, lw, sp))
                 flops = 2.0 * float(np.sum(sizes.astype(np.float64) ** 3)) / 3.0
+            # autotune on this batch (restores the matrices), then time the chosen configuration
+            restore()
+            ltw = r.rl_vbatched_tune_work_size(count, int(np.sum(sizes.astype(np.int64) ** 2)), esz)
+            tw = torch.empty(ltw, dtype=torch.uint8, device=dev)
+            st, best, ms_cfg = r.rl_vbatched_tune("P" if kind == "potrf" else "G", esz, count, nvec, ptrs, nvec,
+                                                  pptrs, info, 256, tw, ltw, sp)
+            r.check(st, "rl_vbatched_tune")
+            del tw
+            cfg = r.rl_vbatched_config("P" if kind == "potrf" else "G", esz)
             restore()
             run()
             torch.cuda.synchronize()
             bad = int((info != 0).sum().item())
             ms = timed(run, reps=3, before=restore)
-            res = {"ms": ms, "gflops": flops / (ms * 1e-3) / 1e9, "launches": 2, "info_nonzero": bad}
+            res = {"ms": ms, "gflops": flops / (ms * 1e-3) / 1e9, "launches": 2, "info_nonzero": bad,
+                   "tuned": {"config": best, "nb": cfg[1], "threads": cfg[2], "ctas_per_sm": cfg[3],
+                             "ms_per_config": [round(v, 3) for v in ms_cfg]}}
+            # the same call captured once into a CUDA graph and replayed
+            try:
+                gph = torch.cuda.CUDAGraph()
+                cs = torch.cuda.Stream()
+                with torch.cuda.stream(cs):
+                    torch.cuda.synchronize()
+                    with torch.cuda.graph(gph, stream=cs):
+                        if kind == "potrf":
+                            r.check(fn("L", count, nvec, ptrs, nvec, info, 256, wk, lw, cs.cuda_stream))
+                        else:
+                            r.check(fn(count, nvec, ptrs, nvec, pptrs, info, 256, wk, lw, cs.cuda_stream))
+                msg = timed(gph.replay, reps=3, before=restore)
+                res["graph_replay_ms"] = msg
+                del gph
+            except Exception as e:
+                res["graph_replay_ms"] = {"unavailable": str(e).splitlines()[0][:200]}
             if prec == "f64" and baseline_count > 0:
                 # one single-matrix call per matrix, on the first baseline_count
                 nb = min(baseline_count, count)
@@ -490,6 +517,70 @@ def routines_section(n, dev, sp):
         out[name] = {"gflops": flops / (ms * 1e-3) / 1e9, "ms": ms}
     out["n"] = n
     out["flop_counts"] = "trtri, lauum n^3/3; potri 2n^3/3; getri 4n^3/3; sygst n^3"
+    return out
+
+
+def lowprec_section(n, dev, sp):
+    """The precision form's factorization step alone: rl_sgetrf_tc /
+    rl_spotrf_tc (FP32 storage, tcgen05 updates in each operand precision)
+    and the SIMT FP32 rl_sgetrf / rl_spotrf, GFLOP/s at order n (median of 2
+    after a warm-up, inputs restored outside the events)."""
+    import torch
+    from paper_1602_06763_gb300 import relgpu as r, inputs
+
+    G0 = inputs.uniform_device(n, n, inputs.seed_for(2, 70), device=dev).to(torch.float32)
+    S0 = inputs.spd_bbt_device(n, inputs.seed_for(2, 71), device=dev).to(torch.float32)
+    A = torch.empty_like(G0)
+    ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = {"n": n}
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        bf = float(pk.get("bf16_tflops") or 0.0)
+        peaks = {"bf16": bf, "fp16": bf, "tf32": bf / 2.0, "tf32x3": bf / 2.0 / 3.0}
+    except Exception:
+        pass
+    for name in ("fp32", "tf32", "bf16", "fp16", "tf32x3"):
+        res = {}
+        for kind, src, flops in (("getrf", G0, 2.0 * n ** 3 / 3.0), ("potrf", S0, n ** 3 / 3.0)):
+            if name == "fp32":
+                lw = r.rl_dgetrf_work_size(n, n)
+                w = torch.empty(lw, dtype=torch.uint8, device=dev)
+                if kind == "getrf":
+                    call = lambda: r.check(r.rl_sgetrf(n, n, A, n, ipiv, info, w, lw, sp))
+                else:
+                    call = lambda: r.check(r.rl_spotrf("L", n, A, n, info, None, 0, sp))
+            else:
+                p = {"tf32": r.RL_PREC_TF32, "bf16": r.RL_PREC_BF16, "fp16": r.RL_PREC_FP16S,
+                     "tf32x3": r.RL_PREC_TF32X3}[name]
+                if kind == "getrf":
+                    lw = r.rl_sgetrf_tc_work_size(n, n, p)
+                    w = torch.empty(lw, dtype=torch.uint8, device=dev)
+                    call = lambda: r.check(r.rl_sgetrf_tc(p, n, n, A, n, ipiv, info, w, lw, sp))
+                else:
+                    lw = r.rl_spotrf_tc_work_size(n, p)
+                    w = torch.empty(lw, dtype=torch.uint8, device=dev)
+                    call = lambda: r.check(r.rl_spotrf_tc(p, "L", n, A, n, info, w, lw, sp))
+            ts = []
+            for rep in range(3):
+                A.copy_(src)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                call()
+                b.record()
+                torch.cuda.synchronize()
+                if rep:
+                    ts.append(a.elapsed_time(b))
+            ms = statistics.median(ts)
+            res[kind] = {"ms": ms, "gflops": flops / (ms * 1e-3) / 1e9, "info": int(info[0])}
+            del w
+        if name in peaks and peaks[name] > 0:
+            res["update_peak_tflops"] = peaks[name]
+        out[name] = res
+    out["peaks"] = "tensor peaks from MEASURED_PEAKS.json bf16 burst (tf32 = bf16/2, 3xtf32 = tf32/3, nominal ratios)"
     return out
 
 
@@ -718,6 +809,7 @@ def run_gpu(args, rank, world, local_rank):
         batched = batched_section(args.batch_count, args.batch_baseline, dev, sp)
 
     others = routines_section(args.others_n, dev, sp) if args.others_n > 0 else None
+    lowprec = lowprec_section(args.lowprec_n, dev, sp) if args.lowprec_n > 0 else None
     graphs = graph_section(n, dev, sp) if args.graph else None
     cusolver = cusolver_section(n, dev) if args.cusolver else None
 
@@ -752,6 +844,7 @@ def run_gpu(args, rank, world, local_rank):
         "mixed_solve_large": mixed_large,
         "batched": batched,
         "other_routines": others,
+        "lowprec_factorization": lowprec,
         "graph_replay": graphs,
         "cusolver_context": cusolver,
         "e2e": e2e,
@@ -790,6 +883,8 @@ def main():
                     help="matrices timed through the single-matrix path for the comparison")
     ap.add_argument("--others-n", type=int, default=8192,
                     help="order of the trtri/lauum/potri/getri/sygst section (0 skips it)")
+    ap.add_argument("--lowprec-n", type=int, default=16384,
+                    help="order of the low-precision factorization section (0 skips it)")
     ap.add_argument("--graph", type=int, default=1, help="time CUDA-graph replay of dpotrf/dgetrf (0 skips)")
     ap.add_argument("--cusolver", type=int, default=1, help="time torch.linalg (cuSOLVER) as context (0 skips)")
     args = ap.parse_args()

@@ -143,6 +143,14 @@ int rl_dpotri(char uplo, int64_t n, double *A, int64_t lda, int32_t *info,
  *   must be ordered (same stream).  With nrhs > 64, work is not used.
  * Stream-ordered; no synchronization.
  * ------------------------------------------------------------------------- */
+/* dlaswp (the row interchanges of xgetrf): for k = k1..k2 (1-based, in
+ * order) swap rows k and ipiv[k-1] of the m x ncols matrix A.  ipiv as
+ * rl_dgetrf writes it (each target at or below its own row, <= m).  The
+ * swaps are turned into their net permutation per chunk of 4096 pivots and
+ * applied with one gather and one scatter per column.  Argument numbers:
+ * 1 m, 2 ncols, 3 A, 4 lda, 5 k1, 6 k2.  Stream-ordered. */
+int rl_dlaswp(int64_t m, int64_t ncols, double *A, int64_t lda, int64_t k1, int64_t k2,
+              const int32_t *ipiv, rl_stream_t stream);
 size_t rl_trs_work_size(int64_t n, int64_t nrhs);
 int rl_dgetrs(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda,
               const int32_t *ipiv, double *B, int64_t ldb, void *work, size_t lwork,
@@ -167,6 +175,10 @@ int rl_dpotrs(char uplo, int64_t n, int64_t nrhs, const double *A, int64_t lda, 
 size_t rl_dgetri_work_size(int64_t n);
 int rl_dgetri(int64_t n, double *A, int64_t lda, const int32_t *ipiv, int32_t *info, void *work,
               size_t lwork, rl_stream_t stream);
+/* FP32 peer, same arguments and semantics. */
+size_t rl_sgetri_work_size(int64_t n);
+int rl_sgetri(int64_t n, float *A, int64_t lda, const int32_t *ipiv, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * dsygst (Section 5, xsygst) -- reduction of the symmetric-definite
@@ -187,6 +199,10 @@ int rl_dgetri(int64_t n, double *A, int64_t lda, const int32_t *ipiv, int32_t *i
  * ------------------------------------------------------------------------- */
 size_t rl_dsygst_work_size(int64_t n);
 int rl_dsygst(int itype, char uplo, int64_t n, double *A, int64_t lda, const double *B,
+              int64_t ldb, void *work, size_t lwork, rl_stream_t stream);
+/* FP32 peer, same arguments and semantics (work in floats: rl_ssygst_work_size). */
+size_t rl_ssygst_work_size(int64_t n);
+int rl_ssygst(int itype, char uplo, int64_t n, float *A, int64_t lda, const float *B,
               int64_t ldb, void *work, size_t lwork, rl_stream_t stream);
 
 /* ---------------------------------------------------------------------------
@@ -210,6 +226,27 @@ int rl_sgetrs(char trans, int64_t n, int64_t nrhs, const float *A, int64_t lda,
               rl_stream_t stream);
 int rl_spotrs(char uplo, int64_t n, int64_t nrhs, const float *A, int64_t lda, float *B,
               int64_t ldb, void *work, size_t lwork, rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Low-precision factorizations (the factorization step of the precision
+ * form, callable on its own): rl_spotrf / rl_sgetrf on FP32 storage with
+ * every large GEMM/SYRK update on the tensor cores (tcgen05) with operands in
+ * `prec` -- RL_PREC_TF32, RL_PREC_BF16, RL_PREC_FP16S (FP16 operands; no
+ * scaling here: the caller keeps |A| in FP16 range) or RL_PREC_TF32X3 (three
+ * TF32 products, ~FP32 accuracy) -- and FP32 accumulation; panels, TRSM
+ * leaves and small updates stay FP32 SIMT.  The paper has no precision form.
+ * work (device): rl_s{potrf,getrf}_tc_work_size bytes (operand packing for the
+ *   tensor cores, plus the LU panel exchange), else RL_ERR_WORKSPACE;
+ *   prec RL_PREC_FP32 or unknown: RL_ERR_UNSUPPORTED (use rl_spotrf/rl_sgetrf).
+ * Argument numbers: 1 prec, then those of rl_spotrf / rl_sgetrf shifted by one.
+ * info as rl_spotrf / rl_sgetrf.  Stream-ordered; no synchronization.
+ * ------------------------------------------------------------------------- */
+size_t rl_spotrf_tc_work_size(int64_t n, int prec);
+size_t rl_sgetrf_tc_work_size(int64_t m, int64_t n, int prec);
+int rl_spotrf_tc(int prec, char uplo, int64_t n, float *A, int64_t lda, int32_t *info,
+                 void *work, size_t lwork, rl_stream_t stream);
+int rl_sgetrf_tc(int prec, int64_t m, int64_t n, float *A, int64_t lda, int32_t *ipiv,
+                 int32_t *info, void *work, size_t lwork, rl_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Precision form: A X = B (FP64) solved with a low-precision factorization
@@ -317,6 +354,36 @@ int rl_dgetrf_vbatched(int64_t batch, const int32_t *n, double *const *A, const 
 int rl_sgetrf_vbatched(int64_t batch, const int32_t *n, float *const *A, const int32_t *lda,
                        int32_t *const *ipiv, int32_t *info, int32_t max_n, void *work,
                        size_t lwork, rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Autotuner of the batching form.  rl_vbatched_tune times each of the
+ * RL_BATCH_CONFIGS candidate configurations of the batched kernels -- block
+ * width NB (16 or 32: matrices are factored in NB-column halves), CTA size
+ * (128 or 256 threads) and CTAs per SM -- on the caller's own batch, twice
+ * each, and keeps the fastest for later rl_{d,s}{potrf,getrf}_vbatched calls
+ * of that routine and element type (process-wide).  The matrices are saved
+ * to `work` first and restored before every run and at the end, so A is
+ * unchanged on return (ipiv and info hold the last run's values).
+ *   routine 'P' (Cholesky, lower) or 'G' (LU); elem_bytes 8 (double) or 4
+ *   (float); the batch arguments are those of the vbatched calls (ipiv may be
+ *   NULL for 'P').  work: rl_vbatched_tune_work_size(batch, sum over the batch
+ *   of n[b]^2, elem_bytes) bytes.  best (host): the chosen configuration;
+ *   ms_per_config (host, RL_BATCH_CONFIGS floats, or NULL): the best of two
+ *   times of each.  This call SYNCHRONIZES the stream (it reads the orders
+ *   back and times with events).  The paper has no batched form.
+ * rl_vbatched_config reports the configuration in use (host outputs, any may
+ *   be NULL); rl_vbatched_set_config selects one (0 .. RL_BATCH_CONFIGS-1,
+ *   else -3).  Argument numbers: 1 routine, 2 elem_bytes, 3 batch / cfg.
+ * ------------------------------------------------------------------------- */
+#define RL_BATCH_CONFIGS 8
+size_t rl_vbatched_tune_work_size(int64_t batch, int64_t sum_n2, int elem_bytes);
+int rl_vbatched_tune(char routine, int elem_bytes, int64_t batch, const int32_t *n, void *const *A,
+                     const int32_t *lda, int32_t *const *ipiv, int32_t *info, int32_t max_n,
+                     void *work, size_t lwork, int32_t *best, float *ms_per_config,
+                     rl_stream_t stream);
+int rl_vbatched_config(char routine, int elem_bytes, int32_t *cfg, int32_t *nb, int32_t *threads,
+                       int32_t *per_sm);
+int rl_vbatched_set_config(char routine, int elem_bytes, int32_t cfg);
 
 /* ---------------------------------------------------------------------------
  * rl_dgetrf_vbatched_noalloc -- rl_dgetrf_vbatched without a workspace

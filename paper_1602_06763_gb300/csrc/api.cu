@@ -9,6 +9,7 @@
 // Cholesky pivot failed or a zero diagonal was found.
 #include <cstring>
 #include <mutex>
+#include <vector>
 #include "internal.cuh"
 
 namespace rl {
@@ -520,6 +521,78 @@ int rl_dtrmm(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
 
 // ---- single precision peers -----------------------------------------------------
 
+// ---- low-precision factorizations (FP32 storage, tensor-core updates) --------
+// The factorization step of the precision form as calls of their own: the
+// recursions of rl_spotrf / rl_sgetrf with every large GEMM/SYRK update on
+// tcgen05 in precision `prec` (TF32, BF16, scaled-free FP16, 3xTF32) with
+// FP32 accumulation; panels, leaves and smaller updates in FP32 SIMT.
+
+static size_t lowprec_tc_bytes(int64_t m, int64_t n, int prec)
+{
+    const i64 h = n / 2 + 64;          // largest update: <= m rows, <= n/2 + 64 columns and depth
+    return tc_work_bytes(m > 0 ? m : 1, h, h, prec);
+}
+
+size_t rl_spotrf_tc_work_size(int64_t n, int prec)
+{
+    if (n < 0 || !(prec == RL_PREC_TF32 || prec == RL_PREC_BF16 || prec == RL_PREC_FP16S ||
+                   prec == RL_PREC_TF32X3))
+        return 0;
+    return lowprec_tc_bytes(n, n, prec);
+}
+
+size_t rl_sgetrf_tc_work_size(int64_t m, int64_t n, int prec)
+{
+    if (m < 0 || n < 0 || !(prec == RL_PREC_TF32 || prec == RL_PREC_BF16 || prec == RL_PREC_FP16S ||
+                            prec == RL_PREC_TF32X3))
+        return 0;
+    return ((panel_ws_bytes() + 255) & ~(size_t)255) + lowprec_tc_bytes(m, n, prec);
+}
+
+int rl_spotrf_tc(int prec, char uplo, int64_t n, float *A, int64_t lda, int32_t *info, void *work,
+                 size_t lwork, rl_stream_t stream)
+{
+    if (!is_l(uplo) && !is_u(uplo)) return -2;
+    if (n < 0) return -3;
+    if (n > 0 && A == nullptr) return -4;
+    if (lda < (n > 1 ? n : 1)) return -5;
+    if (info == nullptr) return RL_ERR_NULL_POINTER;
+    const size_t need = rl_spotrf_tc_work_size(n, prec);
+    if (need == 0 || is_u(uplo)) return RL_ERR_UNSUPPORTED;
+    if (work == nullptr || lwork < need) return RL_ERR_WORKSPACE;
+    Ctx c = make_ctx(stream, info, nullptr, 0);
+    c.abort = info;
+    c.prec = prec;
+    c.tcwork = work;
+    c.tclwork = lwork;
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    potrf_rec_t<float>(c, n, A, lda, 0);
+    return finish(c);
+}
+
+int rl_sgetrf_tc(int prec, int64_t m, int64_t n, float *A, int64_t lda, int32_t *ipiv, int32_t *info,
+                 void *work, size_t lwork, rl_stream_t stream)
+{
+    if (m < 0) return -2;
+    if (n < 0) return -3;
+    if (m > 0 && n > 0 && A == nullptr) return -4;
+    if (lda < (m > 1 ? m : 1)) return -5;
+    if (m > INT32_MAX - 1) return RL_ERR_UNSUPPORTED;
+    if (info == nullptr || (ipiv == nullptr && m > 0 && n > 0)) return RL_ERR_NULL_POINTER;
+    const size_t need = rl_sgetrf_tc_work_size(m, n, prec);
+    if (need == 0) return RL_ERR_UNSUPPORTED;
+    if (work == nullptr || lwork < need) return RL_ERR_WORKSPACE;
+    const size_t pw = (panel_ws_bytes() + 255) & ~(size_t)255;
+    Ctx c = make_ctx(stream, info, work, pw);
+    c.abort = nullptr;
+    c.prec = prec;
+    c.tcwork = static_cast<char *>(work) + pw;
+    c.tclwork = lwork - pw;
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    getrf_rec_t<float>(c, A, lda, m, ipiv, 0, m, n);
+    return finish(c);
+}
+
 int rl_spotrf(char uplo, int64_t n, float *A, int64_t lda, int32_t *info, void *work, size_t lwork,
               rl_stream_t stream)
 {
@@ -619,16 +692,13 @@ static int trs_t(bool lu, int64_t n, int64_t nrhs, const T *A, int64_t lda, cons
     return finish(c);
 }
 
-extern "C" {
-
-size_t rl_dgetri_work_size(int64_t n) { return n <= 0 ? 0 : getri_work_bytes(n); }
-
-int rl_dgetri(int64_t n, double *A, int64_t lda, const int32_t *ipiv, int32_t *info, void *work, size_t lwork,
-              rl_stream_t stream)
+template <typename T>
+static int getri_api(int64_t n, T *A, int64_t lda, const int32_t *ipiv, int32_t *info, void *work, size_t lwork,
+                     rl_stream_t stream)
 {
     if (n < 0) return -1;
     if (n > 0 && A == nullptr) return -2;
-    if (lda < imax1(n)) return -3;
+    if (lda < (n > 1 ? n : 1)) return -3;
     if (info == nullptr || (n > 0 && ipiv == nullptr)) return RL_ERR_NULL_POINTER;
     if (n > GETRI_MAX_N) return RL_ERR_UNSUPPORTED;
     Ctx c = make_ctx(stream, info, work, lwork);
@@ -636,14 +706,32 @@ int rl_dgetri(int64_t n, double *A, int64_t lda, const int32_t *ipiv, int32_t *i
     note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
     if (n == 0) return finish(c);
     if (work == nullptr || lwork < getri_work_bytes(n)) return RL_ERR_WORKSPACE;
-    getri(c, n, A, lda, ipiv, work);
+    getri<T>(c, n, A, lda, ipiv, work);
     return finish(c);
 }
 
-size_t rl_dsygst_work_size(int64_t n) { return n <= 0 ? 0 : sygst_work_bytes(n); }
+extern "C" {
 
-int rl_dsygst(int itype, char uplo, int64_t n, double *A, int64_t lda, const double *B, int64_t ldb,
-              void *work, size_t lwork, rl_stream_t stream)
+size_t rl_dgetri_work_size(int64_t n) { return n <= 0 ? 0 : getri_work_bytes(n); }
+size_t rl_sgetri_work_size(int64_t n) { return n <= 0 ? 0 : getri_work_bytes(n); }
+
+int rl_dgetri(int64_t n, double *A, int64_t lda, const int32_t *ipiv, int32_t *info, void *work, size_t lwork,
+              rl_stream_t stream)
+{
+    return getri_api<double>(n, A, lda, ipiv, info, work, lwork, stream);
+}
+
+int rl_sgetri(int64_t n, float *A, int64_t lda, const int32_t *ipiv, int32_t *info, void *work, size_t lwork,
+              rl_stream_t stream)
+{
+    return getri_api<float>(n, A, lda, ipiv, info, work, lwork, stream);
+}
+
+}  // extern "C"
+
+template <typename T>
+static int sygst_api(int itype, char uplo, int64_t n, T *A, int64_t lda, const T *B, int64_t ldb, void *work,
+                     size_t lwork, rl_stream_t stream)
 {
     if (itype < 1 || itype > 3) return -1;
     if (!is_l(uplo) && !is_u(uplo)) return -2;
@@ -654,9 +742,42 @@ int rl_dsygst(int itype, char uplo, int64_t n, double *A, int64_t lda, const dou
     if (ldb < imax1(n)) return -7;
     if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
     if (n == 0) return RL_SUCCESS;
-    if (work != nullptr && lwork < sygst_work_bytes(n)) return RL_ERR_WORKSPACE;
+    if (work != nullptr && lwork < sygst_work_bytes(n, sizeof(T))) return RL_ERR_WORKSPACE;
     Ctx c = make_ctx(stream, nullptr, work, lwork);
-    sygst_rec(c, itype, n, A, lda, B, ldb, static_cast<double *>(work));
+    sygst_rec<T>(c, itype, n, A, lda, B, ldb, static_cast<T *>(work));
+    return finish(c);
+}
+
+extern "C" {
+
+size_t rl_dsygst_work_size(int64_t n) { return n <= 0 ? 0 : sygst_work_bytes(n, sizeof(double)); }
+size_t rl_ssygst_work_size(int64_t n) { return n <= 0 ? 0 : sygst_work_bytes(n, sizeof(float)); }
+
+int rl_dsygst(int itype, char uplo, int64_t n, double *A, int64_t lda, const double *B, int64_t ldb,
+              void *work, size_t lwork, rl_stream_t stream)
+{
+    return sygst_api<double>(itype, uplo, n, A, lda, B, ldb, work, lwork, stream);
+}
+
+int rl_ssygst(int itype, char uplo, int64_t n, float *A, int64_t lda, const float *B, int64_t ldb,
+              void *work, size_t lwork, rl_stream_t stream)
+{
+    return sygst_api<float>(itype, uplo, n, A, lda, B, ldb, work, lwork, stream);
+}
+
+int rl_dlaswp(int64_t m, int64_t ncols, double *A, int64_t lda, int64_t k1, int64_t k2, const int32_t *ipiv,
+              rl_stream_t stream)
+{
+    if (m < 0) return -1;
+    if (ncols < 0) return -2;
+    if (m > 0 && ncols > 0 && A == nullptr) return -3;
+    if (lda < imax1(m)) return -4;
+    if (k1 < 1) return -5;
+    if (k2 > m) return -6;
+    if (ncols == 0 || k2 < k1) return RL_SUCCESS;
+    if (ipiv == nullptr) return RL_ERR_NULL_POINTER;
+    Ctx c = make_ctx(stream, nullptr, nullptr, 0);
+    laswp<double>(c, A, lda, m, 0, ncols, k1 - 1, k2, ipiv);
     return finish(c);
 }
 
@@ -795,7 +916,8 @@ static int potrf_vb(char uplo, int64_t batch, const int32_t *n, T *const *A, con
     if (n == nullptr || A == nullptr || lda == nullptr || info == nullptr) return RL_ERR_NULL_POINTER;
     if (work == nullptr || lwork < batched_work_size(batch)) return RL_ERR_WORKSPACE;
     Ctx c = make_ctx(stream, nullptr, work, lwork);
-    batched_factor<T>(c, false, batch, n, A, lda, nullptr, info, g_params.batch_ctas);
+    batched_factor<T>(c, false, batch, n, A, lda, nullptr, info, g_params.batch_cfg[sizeof(T) == 8 ? 0 : 1][0],
+                      g_params.batch_ctas);
     return finish(c);
 }
 
@@ -810,9 +932,157 @@ static int getrf_vb(int64_t batch, const int32_t *n, T *const *A, const int32_t 
         return RL_ERR_NULL_POINTER;
     if (work == nullptr || lwork < batched_work_size(batch)) return RL_ERR_WORKSPACE;
     Ctx c = make_ctx(stream, nullptr, work, lwork);
-    batched_factor<T>(c, true, batch, n, A, lda, ipiv, info, g_params.batch_ctas);
+    batched_factor<T>(c, true, batch, n, A, lda, ipiv, info, g_params.batch_cfg[sizeof(T) == 8 ? 0 : 1][1],
+                      g_params.batch_ctas);
     return finish(c);
 }
+
+// ---- autotuner of the batched form -------------------------------------------
+// Times every candidate configuration (block width, CTA size, CTAs per SM) on
+// the caller's own batch, restoring the matrices from a packed copy before
+// each run and once more at the end, and keeps the fastest for later calls
+// of the same routine and element type.
+
+template <typename T>
+__global__ void k_batch_copy(int batch, const int32_t *d_n, T *const *src, const int32_t *src_ld,
+                             T *const *dst, const int32_t *dst_ld)
+{
+    for (int b = blockIdx.x; b < batch; b += gridDim.x) {
+        const int n = d_n[b];
+        if (n <= 0) continue;
+        const T *s = src[b];
+        T *d = dst[b];
+        const int ls = src_ld[b], ld = dst_ld[b];
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int i = e % n, j = e / n;
+            d[(i64)j * ld + i] = s[(i64)j * ls + i];
+        }
+    }
+}
+
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <typename T>
+static int vb_tune(bool lu, int64_t batch, const int32_t *n, T *const *A, const int32_t *lda,
+                   int32_t *const *ipiv, int32_t *info, int32_t max_n, void *work, size_t lwork,
+                   int32_t *best, float *ms_out, rl_stream_t stream)
+{
+    if (batch < 0) return -3;
+    if (max_n > BATCH_MAX_N || batch > INT32_MAX) return RL_ERR_UNSUPPORTED;
+    if (best == nullptr) return RL_ERR_NULL_POINTER;
+    if (batch == 0) { *best = g_params.batch_cfg[sizeof(T) == 8 ? 0 : 1][lu ? 1 : 0]; return RL_SUCCESS; }
+    if (n == nullptr || A == nullptr || lda == nullptr || info == nullptr || (lu && ipiv == nullptr))
+        return RL_ERR_NULL_POINTER;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // sizes on the host (this call synchronizes)
+    std::vector<int32_t> hn((size_t)batch);
+    if (cudaMemcpyAsync(hn.data(), n, sizeof(int32_t) * batch, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return RL_ERR_CUDA;
+    size_t elems = 0;
+    for (int32_t v : hn) elems += (size_t)(v > 0 ? v : 0) * (size_t)(v > 0 ? v : 0);
+    const size_t wsb = al256(batched_work_size(batch)), pb = al256(sizeof(T *) * batch),
+                 lb = al256(sizeof(int32_t) * batch);
+    if (work == nullptr || lwork < wsb + pb + lb + elems * sizeof(T)) return RL_ERR_WORKSPACE;
+    char *w = static_cast<char *>(work);
+    T **bptr = reinterpret_cast<T **>(w + wsb);
+    int32_t *bld = reinterpret_cast<int32_t *>(w + wsb + pb);
+    T *bdata = reinterpret_cast<T *>(w + wsb + pb + lb);
+    std::vector<T *> hp((size_t)batch);
+    size_t off = 0;
+    for (int64_t b = 0; b < batch; ++b) {
+        hp[b] = bdata + off;
+        off += (size_t)(hn[b] > 0 ? hn[b] : 0) * (size_t)(hn[b] > 0 ? hn[b] : 0);
+    }
+    if (cudaMemcpyAsync(bptr, hp.data(), sizeof(T *) * batch, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(bld, n, sizeof(int32_t) * batch, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return RL_ERR_CUDA;
+    const unsigned cgrid = (unsigned)(batch < 4096 ? batch : 4096);
+    k_batch_copy<T><<<cgrid, 256, 0, s>>>((int)batch, n, A, lda, bptr, bld);       // save
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return RL_ERR_CUDA;
+    const int ti = sizeof(T) == 8 ? 0 : 1;
+    int bestc = -1;
+    float bestms = 0.0f;
+    int rc = RL_SUCCESS;
+    for (int cfg = 0; cfg < BATCH_NCFG && rc == RL_SUCCESS; ++cfg) {
+        float mn = -1.0f;
+        for (int rep = 0; rep < 2; ++rep) {
+            k_batch_copy<T><<<cgrid, 256, 0, s>>>((int)batch, n, bptr, bld, A, lda);   // restore
+            Ctx c = make_ctx(stream, nullptr, work, wsb);
+            note(c, cudaEventRecord(e0, s));
+            batched_factor<T>(c, lu, batch, n, A, lda, ipiv, info, cfg, 0);
+            note(c, cudaEventRecord(e1, s));
+            float ms = 0.0f;
+            if (c.err != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = RL_ERR_CUDA;
+                break;
+            }
+            if (mn < 0.0f || ms < mn) mn = ms;
+        }
+        if (ms_out) ms_out[cfg] = mn;
+        if (rc == RL_SUCCESS && (bestc < 0 || mn < bestms)) { bestc = cfg; bestms = mn; }
+    }
+    k_batch_copy<T><<<cgrid, 256, 0, s>>>((int)batch, n, bptr, bld, A, lda);       // the caller's data back
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = RL_ERR_CUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != RL_SUCCESS) return rc;
+    g_params.batch_cfg[ti][lu ? 1 : 0] = bestc;
+    *best = bestc;
+    return RL_SUCCESS;
+}
+
+extern "C" {
+
+size_t rl_vbatched_tune_work_size(int64_t batch, int64_t sum_n2, int elem_bytes)
+{
+    if (batch < 0 || sum_n2 < 0 || (elem_bytes != 4 && elem_bytes != 8)) return 0;
+    return al256(batched_work_size(batch)) + al256(sizeof(void *) * batch) + al256(sizeof(int32_t) * batch) +
+           (size_t)sum_n2 * (size_t)elem_bytes;
+}
+
+int rl_vbatched_tune(char routine, int elem_bytes, int64_t batch, const int32_t *n, void *const *A,
+                     const int32_t *lda, int32_t *const *ipiv, int32_t *info, int32_t max_n, void *work,
+                     size_t lwork, int32_t *best, float *ms_per_config, rl_stream_t stream)
+{
+    const bool lu = (routine == 'G' || routine == 'g');
+    if (!lu && routine != 'P' && routine != 'p') return -1;
+    if (elem_bytes == 8)
+        return vb_tune<double>(lu, batch, n, reinterpret_cast<double *const *>(A), lda, ipiv, info, max_n, work,
+                               lwork, best, ms_per_config, stream);
+    if (elem_bytes == 4)
+        return vb_tune<float>(lu, batch, n, reinterpret_cast<float *const *>(A), lda, ipiv, info, max_n, work,
+                              lwork, best, ms_per_config, stream);
+    return -2;
+}
+
+int rl_vbatched_set_config(char routine, int elem_bytes, int32_t cfg)
+{
+    const bool lu = (routine == 'G' || routine == 'g');
+    if (!lu && routine != 'P' && routine != 'p') return -1;
+    if (elem_bytes != 4 && elem_bytes != 8) return -2;
+    if (cfg < 0 || cfg >= BATCH_NCFG) return -3;
+    g_params.batch_cfg[elem_bytes == 8 ? 0 : 1][lu ? 1 : 0] = cfg;
+    return RL_SUCCESS;
+}
+
+int rl_vbatched_config(char routine, int elem_bytes, int32_t *cfg, int32_t *nb, int32_t *threads,
+                       int32_t *per_sm)
+{
+    const bool lu = (routine == 'G' || routine == 'g');
+    if (!lu && routine != 'P' && routine != 'p') return -1;
+    if (elem_bytes != 4 && elem_bytes != 8) return -2;
+    const int c = g_params.batch_cfg[elem_bytes == 8 ? 0 : 1][lu ? 1 : 0];
+    if (cfg) *cfg = c;
+    if (nb) *nb = kBatchCfgs[c].nb;
+    if (threads) *threads = kBatchCfgs[c].threads;
+    if (per_sm) *per_sm = kBatchCfgs[c].per_sm;
+    return RL_SUCCESS;
+}
+
+}  // extern "C"
 
 extern "C" {
 

@@ -1,7 +1,8 @@
 // Batching form: many independent small factorizations (orders up to 256) in
 // one persistent launch.  The paper has no batched form; each matrix is
 // factored by the paper's scheme with the halves fixed to a block of NB
-// columns, so every CTA runs: factor the NB-column block in shared memory,
+// columns (NB = 16 or 32, CTA size and CTAs per SM chosen by the autotuner,
+// rl_vbatched_tune), so every CTA runs: factor the NB-column block in shared memory,
 // update the rest with a triangular solve and a rank-NB product, continue on
 // the trailing matrix.
 //
@@ -27,9 +28,7 @@ namespace rl {
 
 namespace {
 
-constexpr int BNB = 32;            // block width
 constexpr int BMAX = 256;          // largest order handled
-constexpr int BTHREADS = 256;
 
 struct BatchWS {
     int next;                      // work counter (zeroed per launch)
@@ -75,7 +74,7 @@ __device__ __forceinline__ void tri_decode(int t, int &ti, int &tj)
 }
 
 // ---- Cholesky of one matrix by the whole CTA --------------------------------
-template <typename T>
+template <typename T, int BNB>
 __device__ void potrf_one(T *A, int n, int lda, int32_t *info, T *sm)
 {
     T *D = sm;                           // BNB x (BNB+1)
@@ -180,7 +179,7 @@ __device__ void potrf_one(T *A, int n, int lda, int32_t *info, T *sm)
 }
 
 // ---- LU with partial pivoting of one n x n matrix by the whole CTA ----------
-template <typename T>
+template <typename T, int BNB>
 __device__ void getrf_one(T *A, int n, int lda, int32_t *ipiv, int32_t *info, T *sm, double *wv,
                           int *wi, int *s_piv)
 {
@@ -311,7 +310,7 @@ __device__ void getrf_one(T *A, int n, int lda, int32_t *ipiv, int32_t *info, T 
     }
 }
 
-template <typename T, bool LU>
+template <typename T, bool LU, int BNB, int BTHREADS>
 __global__ void __launch_bounds__(BTHREADS)
 k_batched(int batch, const int32_t *d_n, T *const *d_A, const int32_t *d_lda, int32_t *const *d_ipiv,
           int32_t *d_info, BatchWS *ws)
@@ -335,39 +334,29 @@ k_batched(int batch, const int32_t *d_n, T *const *d_A, const int32_t *d_lda, in
         if (threadIdx.x == 0) d_info[b] = 0;
         __syncthreads();
         if (n <= 0 || n > BMAX) continue;
-        if (LU) getrf_one<T>(d_A[b], n, d_lda[b], d_ipiv[b], d_info + b, sm, wv, wi, s_piv);
-        else potrf_one<T>(d_A[b], n, d_lda[b], d_info + b, sm);
+        if (LU) getrf_one<T, BNB>(d_A[b], n, d_lda[b], d_ipiv[b], d_info + b, sm, wv, wi, s_piv);
+        else potrf_one<T, BNB>(d_A[b], n, d_lda[b], d_info + b, sm);
         __syncthreads();
     }
 }
 
-template <typename T>
+template <typename T, int BNB>
 size_t batch_smem(bool lu)
 {
     return lu ? (size_t)(BMAX * (BNB + 1) + BNB * (BMAX + 1)) * sizeof(T)
               : (size_t)(BNB * (BNB + 1) + BMAX * (BNB + 1)) * sizeof(T);
 }
 
-}  // namespace
-
-size_t batched_work_size(i64 batch) { return batch_ws(batch); }
-
-template <typename T>
-int batched_factor(Ctx &c, bool lu, i64 batch, const int32_t *d_n, T *const *d_A, const int32_t *d_lda,
-                   int32_t *const *d_ipiv, int32_t *d_info, int per_sm)
+template <typename T, bool LU, int BNB, int BTHREADS>
+void launch_batched(Ctx &c, i64 batch, const int32_t *d_n, T *const *d_A, const int32_t *d_lda,
+                    int32_t *const *d_ipiv, int32_t *d_info, BatchWS *ws, int per_sm)
 {
-    BatchWS *ws = reinterpret_cast<BatchWS *>(c.work);
-    {
-        Launch L(c, K_MIX, 0.0, 0.0);
-        k_batch_sort<<<1, 1024, 0, c.s>>>((int)batch, d_n, ws);
-    }
-    const size_t smem = batch_smem<T>(lu);
-    auto kern = lu ? k_batched<T, true> : k_batched<T, false>;
-    static bool attr[2][2] = {{false, false}, {false, false}};
-    bool &a = attr[sizeof(T) == 8 ? 0 : 1][lu ? 1 : 0];
-    if (!a) {
+    const size_t smem = batch_smem<T, BNB>(LU);
+    auto kern = k_batched<T, LU, BNB, BTHREADS>;
+    static bool attr = false;
+    if (!attr) {
         note(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        a = true;
+        attr = true;
     }
     int occ = 0;
     note(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BTHREADS, smem));
@@ -378,12 +367,49 @@ int batched_factor(Ctx &c, bool lu, i64 batch, const int32_t *d_n, T *const *d_A
     if (grid < 1) grid = 1;
     Launch L(c, K_BATCH, 0.0, 0.0);
     kern<<<(unsigned)grid, BTHREADS, smem, c.s>>>((int)batch, d_n, d_A, d_lda, d_ipiv, d_info, ws);
+}
+
+}  // namespace
+
+size_t batched_work_size(i64 batch) { return batch_ws(batch); }
+
+// Candidate configurations of the batched kernels: block width (the
+// recursion's cutoff: matrices are factored in blocks of NB columns), CTA
+// size, and CTAs per SM (0 = as many as fit).
+const BatchCfg kBatchCfgs[BATCH_NCFG] = {
+    {32, 256, 0}, {32, 256, 1}, {32, 256, 2}, {32, 128, 0}, {32, 128, 2},
+    {16, 256, 0}, {16, 128, 0}, {16, 128, 4},
+};
+
+template <typename T>
+int batched_factor(Ctx &c, bool lu, i64 batch, const int32_t *d_n, T *const *d_A, const int32_t *d_lda,
+                   int32_t *const *d_ipiv, int32_t *d_info, int cfg, int per_sm)
+{
+    BatchWS *ws = reinterpret_cast<BatchWS *>(c.work);
+    {
+        Launch L(c, K_MIX, 0.0, 0.0);
+        k_batch_sort<<<1, 1024, 0, c.s>>>((int)batch, d_n, ws);
+    }
+    if (cfg < 0 || cfg >= BATCH_NCFG) cfg = 0;
+    const BatchCfg k = kBatchCfgs[cfg];
+    const int ps = per_sm > 0 ? per_sm : k.per_sm;
+#define RL_BATCH_CASE(NB, TH)                                                                        \
+    if (k.nb == NB && k.threads == TH) {                                                             \
+        if (lu) launch_batched<T, true, NB, TH>(c, batch, d_n, d_A, d_lda, d_ipiv, d_info, ws, ps);  \
+        else launch_batched<T, false, NB, TH>(c, batch, d_n, d_A, d_lda, d_ipiv, d_info, ws, ps);    \
+        return 0;                                                                                     \
+    }
+    RL_BATCH_CASE(32, 256)
+    RL_BATCH_CASE(32, 128)
+    RL_BATCH_CASE(16, 256)
+    RL_BATCH_CASE(16, 128)
+#undef RL_BATCH_CASE
     return 0;
 }
 
 template int batched_factor<double>(Ctx &, bool, i64, const int32_t *, double *const *, const int32_t *,
-                                    int32_t *const *, int32_t *, int);
+                                    int32_t *const *, int32_t *, int, int);
 template int batched_factor<float>(Ctx &, bool, i64, const int32_t *, float *const *, const int32_t *,
-                                   int32_t *const *, int32_t *, int);
+                                   int32_t *const *, int32_t *, int, int);
 
 }  // namespace rl

@@ -25,23 +25,24 @@ constexpr int UL_P = UL_N + 1;
 
 // W = X Y for one block of order <= 64: X upper (with diagonal), Y unit
 // lower (strictly lower part stored), both in A; W overwrites A.
+template <typename T>
 __global__ void __launch_bounds__(256)
-k_uinv_linv(int n, double *A, i64 lda, const int32_t *abort)
+k_uinv_linv(int n, T *A, i64 lda, const int32_t *abort)
 {
     if (abort && *abort != 0) return;
-    __shared__ double S[UL_N * UL_P];            // S(i, k) at S[k * UL_P + i]
+    __shared__ T S[UL_N * UL_P];                 // S(i, k) at S[k * UL_P + i]
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e % n, k = e / n;
         S[k * UL_P + i] = A[(i64)k * lda + i];
     }
     __syncthreads();
     constexpr int PER = UL_N * UL_N / 256;
-    double w[PER];
+    T w[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int e = threadIdx.x + 256 * u;
         const int i = e % UL_N, j = e / UL_N;
-        double s = 0.0;
+        T s = T(0);
         if (i < n && j < n) {
             const int k0 = i > j ? i : j;
             // k = j: Y(j, j) = 1
@@ -59,34 +60,36 @@ k_uinv_linv(int n, double *A, i64 lda, const int32_t *abort)
     }
 }
 
-void uinv_linv_rec(Ctx &c, i64 n, double *A, i64 lda)
+template <typename T>
+void uinv_linv_rec(Ctx &c, i64 n, T *A, i64 lda)
 {
     if (n <= 0) return;
     if (n <= UL_N) {
         Launch L(c, K_TRMM, 2.0 * n * n * n / 3.0, 0.0);
-        k_uinv_linv<<<1, 256, 0, c.s>>>((int)n, A, lda, c.abort);
+        k_uinv_linv<T><<<1, 256, 0, c.s>>>((int)n, A, lda, c.abort);
         return;
     }
     const i64 n1 = split_q(n, UL_N), n2 = n - n1;
-    double *A11 = A, *A12 = A + n1 * lda, *A21 = A + n1, *A22 = A + n1 + n1 * lda;
-    uinv_linv_rec(c, n1, A11, lda);
-    gemm<double>(c, false, false, n1, n1, n2, 1.0, A12, lda, A21, lda, 1.0, A11, lda);
-    trmm_rln<double>(c, true, n1, n2, 1.0, A22, lda, A12, lda);
-    trmm_lun<double>(c, n2, n1, 1.0, A22, lda, A21, lda);
-    uinv_linv_rec(c, n2, A22, lda);
+    T *A11 = A, *A12 = A + n1 * lda, *A21 = A + n1, *A22 = A + n1 + n1 * lda;
+    uinv_linv_rec<T>(c, n1, A11, lda);
+    gemm<T>(c, false, false, n1, n1, n2, T(1), A12, lda, A21, lda, T(1), A11, lda);
+    trmm_rln<T>(c, true, n1, n2, T(1), A22, lda, A12, lda);
+    trmm_lun<T>(c, n2, n1, T(1), A22, lda, A21, lda);
+    uinv_linv_rec<T>(c, n2, A22, lda);
 }
 
 // Upper-triangular inverse, non-unit: the transpose of Fig. 4's scheme.
-void trtri_upper_rec(Ctx &c, i64 n, double *A, i64 lda)
+template <typename T>
+void trtri_upper_rec(Ctx &c, i64 n, T *A, i64 lda)
 {
     if (n <= 0) return;
-    if (n <= g_params.trtri_c) { trti2(c, false, n, A, lda, true); return; }
+    if (n <= g_params.trtri_c) { trti2<T>(c, false, n, A, lda, true); return; }
     const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
-    double *TR = A + n1 * lda, *BR = A + n1 + n1 * lda;
-    trtri_upper_rec(c, n1, A, lda);
-    trmm_lun<double>(c, n1, n2, 1.0, A, lda, TR, lda);        // TR := U11^{-1} U12
-    trsm_run<double>(c, n1, n2, -1.0, BR, lda, TR, lda);      // TR := -TR U22^{-1}
-    trtri_upper_rec(c, n2, BR, lda);
+    T *TR = A + n1 * lda, *BR = A + n1 + n1 * lda;
+    trtri_upper_rec<T>(c, n1, A, lda);
+    trmm_lun<T>(c, n1, n2, T(1), A, lda, TR, lda);        // TR := U11^{-1} U12
+    trsm_run<T>(c, n1, n2, T(-1), BR, lda, TR, lda);      // TR := -TR U22^{-1}
+    trtri_upper_rec<T>(c, n2, BR, lda);
 }
 
 // Column permutation plan.  Applying the swaps (j, ipiv[j]) for j = n-1..0
@@ -141,8 +144,9 @@ k_colperm_plan(int n, const int32_t *ipiv, PermPlan *plan, const int32_t *abort)
 // issued before its stores (the columns of one cycle are distinct).
 constexpr int CP_ROWS = 64, CP_BATCH = 16;
 
+template <typename T>
 __global__ void __launch_bounds__(CP_ROWS)
-k_colperm_apply(int n, double *A, i64 lda, const PermPlan *plan, const int32_t *abort)
+k_colperm_apply(int n, T *A, i64 lda, const PermPlan *plan, const int32_t *abort)
 {
     if (abort && *abort != 0) return;
     const i64 r = (i64)blockIdx.x * CP_ROWS + threadIdx.x;
@@ -152,11 +156,11 @@ k_colperm_apply(int n, double *A, i64 lda, const PermPlan *plan, const int32_t *
     int beg = 0;
     for (int cy = 0; cy < nc; ++cy) {
         const int end = ends[cy];
-        const double saved = A[(i64)list[beg] * lda + r];
+        const T saved = A[(i64)list[beg] * lda + r];
         int t = beg;
         while (t + 1 < end) {
             const int cnt = min(CP_BATCH, end - 1 - t);
-            double v[CP_BATCH];
+            T v[CP_BATCH];
 #pragma unroll
             for (int u = 0; u < CP_BATCH; ++u)
                 if (u < cnt) v[u] = A[(i64)list[t + 1 + u] * lda + r];
@@ -177,13 +181,14 @@ size_t getri_work_bytes(i64 n)
     return 256 + 2 * (size_t)(n > 0 ? n : 1) * sizeof(int);
 }
 
-void getri(Ctx &c, i64 n, double *A, i64 lda, const int32_t *ipiv, void *work)
+template <typename T>
+void getri(Ctx &c, i64 n, T *A, i64 lda, const int32_t *ipiv, void *work)
 {
     if (n <= 0) return;
-    diag_zero_scan(c, n, A, lda);                 // info = first zero of U's diagonal
-    trtri_upper_rec(c, n, A, lda);
-    trtri_rec(c, true, n, A, lda);              // L := L^{-1}, unit diagonal
-    uinv_linv_rec(c, n, A, lda);
+    diag_zero_scan<T>(c, n, A, lda);              // info = first zero of U's diagonal
+    trtri_upper_rec<T>(c, n, A, lda);
+    trtri_rec<T>(c, true, n, A, lda);             // L := L^{-1}, unit diagonal
+    uinv_linv_rec<T>(c, n, A, lda);
     PermPlan *plan = static_cast<PermPlan *>(work);
     const size_t smem = (size_t)n * sizeof(int) + (size_t)n;
     static bool attr = false;
@@ -196,8 +201,12 @@ void getri(Ctx &c, i64 n, double *A, i64 lda, const int32_t *ipiv, void *work)
         Launch L(c, K_LASWP, 0.0, 0.0);
         k_colperm_plan<<<1, 256, smem, c.s>>>((int)n, ipiv, plan, c.abort);
     }
-    Launch L(c, K_LASWP, 0.0, 16.0 * (double)n * n);
-    k_colperm_apply<<<(unsigned)((n + CP_ROWS - 1) / CP_ROWS), CP_ROWS, 0, c.s>>>((int)n, A, lda, plan, c.abort);
+    Launch L(c, K_LASWP, 0.0, 2.0 * sizeof(T) * (double)n * n);
+    k_colperm_apply<T><<<(unsigned)((n + CP_ROWS - 1) / CP_ROWS), CP_ROWS, 0, c.s>>>((int)n, A, lda, plan,
+                                                                                      c.abort);
 }
+
+template void getri<double>(Ctx &, i64, double *, i64, const int32_t *, void *);
+template void getri<float>(Ctx &, i64, float *, i64, const int32_t *, void *);
 
 }  // namespace rl

@@ -23,6 +23,7 @@ struct Params {
     int trtri_c = 64;        // dtrtri / dlauum crossover
     long long spin_ns = 2000000000LL;
     int batch_ctas = 0;      // CTAs per SM of the batched kernels (0 = occupancy limit)
+    int batch_cfg[2][2] = {{0, 0}, {0, 0}};   // [double/float][potrf/getrf]: tuned kBatchCfgs index
     int tri_lanes = 0;       // lanes per vector of the triangle leaf kernels (0 = by size, 2, 4)
     int lookahead = 1;       // LU/Cholesky: trailing update split across the side stream (0 = off)
 };
@@ -175,9 +176,13 @@ constexpr i64 TC_MIN_MN = 128, TC_MIN_K = 64;
 
 // ---- batching form (batched.cu) ---------------------------------------------
 size_t batched_work_size(i64 batch);
+struct BatchCfg { int nb, threads, per_sm; };
+constexpr int BATCH_NCFG = 8;
+extern const BatchCfg kBatchCfgs[BATCH_NCFG];
+// cfg: index into kBatchCfgs; per_sm > 0 overrides its CTAs per SM
 template <typename T>
 int batched_factor(Ctx &c, bool lu, i64 batch, const int32_t *d_n, T *const *d_A, const int32_t *d_lda,
-                   int32_t *const *d_ipiv, int32_t *d_info, int per_sm);
+                   int32_t *const *d_ipiv, int32_t *d_info, int cfg, int per_sm);
 constexpr int BATCH_MAX_N = 256;
 
 // ---- recursions (api.cu), T = double or float --------------------------------
@@ -195,13 +200,15 @@ void trtri_rec(Ctx &c, bool unit, i64 n, T *A, i64 lda);
 // getri_work_bytes(n); n <= GETRI_MAX_N.
 constexpr i64 GETRI_MAX_N = 40960;
 size_t getri_work_bytes(i64 n);
-void getri(Ctx &c, i64 n, double *A, i64 lda, const int32_t *ipiv, void *work);
+template <typename T>
+void getri(Ctx &c, i64 n, T *A, i64 lda, const int32_t *ipiv, void *work);
 
 // ---- sygst (sygst.cu) ----------------------------------------------------------
 // A := L^{-1} A L^{-T} (itype 1) or L^T A L (itype 2, 3), lower storage; T is
 // sygst_work_bytes(n) of scratch or nullptr (recompute instead).
-size_t sygst_work_bytes(i64 n);
-void sygst_rec(Ctx &c, int itype, i64 n, double *A, i64 lda, const double *L, i64 ldl, double *T);
+size_t sygst_work_bytes(i64 n, size_t esz);
+template <typename E>
+void sygst_rec(Ctx &c, int itype, i64 n, E *A, i64 lda, const E *L, i64 ldl, E *T);
 
 // ---- precision form (mixed.cu) ----------------------------------------------
 size_t mixed_work_size(i64 n, i64 nrhs, bool lu, int prec);

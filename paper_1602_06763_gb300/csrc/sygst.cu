@@ -33,27 +33,27 @@ namespace {
 constexpr int SG_N = 64;
 constexpr int SG_P = SG_N + 1;
 
-template <int ITYPE>
+template <typename T, int ITYPE>
 __global__ void __launch_bounds__(SG_N)
-k_sygs2(int n, double *A, i64 lda, const double *L, i64 ldl, const int32_t *abort)
+k_sygs2(int n, T *A, i64 lda, const T *L, i64 ldl, const int32_t *abort)
 {
     if (abort && *abort != 0) return;
-    extern __shared__ double sg_smem[];
-    double *W = sg_smem;                 // W(i, k) at W[k * SG_P + i]
-    double *Ls = sg_smem + SG_N * SG_P;  // L(i, k) at Ls[k * SG_P + i]
+    extern __shared__ __align__(16) unsigned char sg_raw[];
+    T *W = reinterpret_cast<T *>(sg_raw);   // W(i, k) at W[k * SG_P + i]
+    T *Ls = W + SG_N * SG_P;                // L(i, k) at Ls[k * SG_P + i]
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e % n, k = e / n;
         W[k * SG_P + i] = (i >= k) ? A[(i64)k * lda + i] : A[(i64)i * lda + k];
-        Ls[k * SG_P + i] = (i >= k) ? L[(i64)k * ldl + i] : 0.0;
+        Ls[k * SG_P + i] = (i >= k) ? L[(i64)k * ldl + i] : T(0);
     }
     __syncthreads();
     const int t = threadIdx.x;
     if (ITYPE == 1) {
         // V := L^{-1} W, thread t takes column t (in place)
         if (t < n) {
-            double *w = W + t * SG_P;
+            T *w = W + t * SG_P;
             for (int i = 0; i < n; ++i) {
-                double s = w[i];
+                T s = w[i];
                 for (int k = 0; k < i; ++k) s = fma(-Ls[k * SG_P + i], w[k], s);
                 w[i] = s / Ls[i * SG_P + i];
             }
@@ -62,7 +62,7 @@ k_sygs2(int n, double *A, i64 lda, const double *L, i64 ldl, const int32_t *abor
         // X := V L^{-T}, thread t takes row t: x_j = (v_j - sum_{k<j} x_k l_jk) / l_jj
         if (t < n) {
             for (int j = 0; j < n; ++j) {
-                double s = W[j * SG_P + t];
+                T s = W[j * SG_P + t];
                 for (int k = 0; k < j; ++k) s = fma(-W[k * SG_P + t], Ls[k * SG_P + j], s);
                 W[j * SG_P + t] = s / Ls[j * SG_P + j];
             }
@@ -71,7 +71,7 @@ k_sygs2(int n, double *A, i64 lda, const double *L, i64 ldl, const int32_t *abor
         // V := W L, thread t takes row t: v_j = sum_{k>=j} w_k l_kj, j ascending (in place)
         if (t < n) {
             for (int j = 0; j < n; ++j) {
-                double s = 0.0;
+                T s = T(0);
                 for (int k = j; k < n; ++k) s = fma(W[k * SG_P + t], Ls[j * SG_P + k], s);
                 W[j * SG_P + t] = s;
             }
@@ -79,9 +79,9 @@ k_sygs2(int n, double *A, i64 lda, const double *L, i64 ldl, const int32_t *abor
         __syncthreads();
         // X := L^T V, thread t takes column t: x_i = sum_{k>=i} l_ki v_k, i ascending
         if (t < n) {
-            double *v = W + t * SG_P;
+            T *v = W + t * SG_P;
             for (int i = 0; i < n; ++i) {
-                double s = 0.0;
+                T s = T(0);
                 for (int k = i; k < n; ++k) s = fma(Ls[i * SG_P + k], v[k], s);
                 v[i] = s;
             }
@@ -95,8 +95,8 @@ k_sygs2(int n, double *A, i64 lda, const double *L, i64 ldl, const int32_t *abor
 }
 
 // Y(m x n) += alpha X(m x n)
-__global__ void k_axpy_mat(i64 m, i64 n, double alpha, const double *X, i64 ldx, double *Y, i64 ldy,
-                           const int32_t *abort)
+template <typename T>
+__global__ void k_axpy_mat(i64 m, i64 n, T alpha, const T *X, i64 ldx, T *Y, i64 ldy, const int32_t *abort)
 {
     if (abort && *abort != 0) return;
     const i64 total = m * n;
@@ -106,78 +106,84 @@ __global__ void k_axpy_mat(i64 m, i64 n, double alpha, const double *X, i64 ldx,
     }
 }
 
-void axpy_mat(Ctx &c, i64 m, i64 n, double alpha, const double *X, i64 ldx, double *Y, i64 ldy)
+template <typename T>
+void axpy_mat(Ctx &c, i64 m, i64 n, T alpha, const T *X, i64 ldx, T *Y, i64 ldy)
 {
     if (m <= 0 || n <= 0) return;
-    Launch L(c, K_MIX, 2.0 * m * n, 24.0 * m * n);
+    Launch L(c, K_MIX, 2.0 * m * n, 3.0 * sizeof(T) * m * n);
     const i64 blocks = (m * n + 255) / 256;
     const unsigned grid = (unsigned)(blocks < (i64)c.num_sms * 16 ? blocks : (i64)c.num_sms * 16);
-    k_axpy_mat<<<grid, 256, 0, c.s>>>(m, n, alpha, X, ldx, Y, ldy, c.abort);
+    k_axpy_mat<T><<<grid, 256, 0, c.s>>>(m, n, alpha, X, ldx, Y, ldy, c.abort);
 }
 
-void sygs2(Ctx &c, int itype, i64 n, double *A, i64 lda, const double *L, i64 ldl)
+template <typename T>
+void sygs2(Ctx &c, int itype, i64 n, T *A, i64 lda, const T *L, i64 ldl)
 {
-    const size_t smem = 2 * (size_t)SG_N * SG_P * sizeof(double);
+    const size_t smem = 2 * (size_t)SG_N * SG_P * sizeof(T);
     static bool attr[2] = {false, false};
     const int ti = itype == 1 ? 0 : 1;
     if (!attr[ti]) {
-        note(c, cudaFuncSetAttribute(itype == 1 ? k_sygs2<1> : k_sygs2<2>,
+        note(c, cudaFuncSetAttribute(itype == 1 ? k_sygs2<T, 1> : k_sygs2<T, 2>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr[ti] = true;
     }
     Launch Lk(c, K_MIX, (double)n * n * n, 0.0);
-    if (itype == 1) k_sygs2<1><<<1, SG_N, smem, c.s>>>((int)n, A, lda, L, ldl, c.abort);
-    else k_sygs2<2><<<1, SG_N, smem, c.s>>>((int)n, A, lda, L, ldl, c.abort);
+    if (itype == 1) k_sygs2<T, 1><<<1, SG_N, smem, c.s>>>((int)n, A, lda, L, ldl, c.abort);
+    else k_sygs2<T, 2><<<1, SG_N, smem, c.s>>>((int)n, A, lda, L, ldl, c.abort);
 }
 
 }  // namespace
 
-size_t sygst_work_bytes(i64 n)
+size_t sygst_work_bytes(i64 n, size_t esz)
 {
     if (n <= SG_N) return 0;
     const i64 n1 = split_q(n, SG_N), n2 = n - n1;
-    return (size_t)n1 * (size_t)n2 * sizeof(double);
+    return (size_t)n1 * (size_t)n2 * esz;
 }
 
-void sygst_rec(Ctx &c, int itype, i64 n, double *A, i64 lda, const double *L, i64 ldl, double *T)
+template <typename E>
+void sygst_rec(Ctx &c, int itype, i64 n, E *A, i64 lda, const E *L, i64 ldl, E *T)
 {
     if (n <= 0) return;
     if (n <= SG_N) {
-        sygs2(c, itype, n, A, lda, L, ldl);
+        sygs2<E>(c, itype, n, A, lda, L, ldl);
         return;
     }
     const i64 n1 = split_q(n, SG_N), n2 = n - n1;
-    double *A11 = A, *A21 = A + n1, *A22 = A + n1 + n1 * lda;
-    const double *L11 = L, *L21 = L + n1, *L22 = L + n1 + n1 * ldl;
+    E *A11 = A, *A21 = A + n1, *A22 = A + n1 + n1 * lda;
+    const E *L11 = L, *L21 = L + n1, *L22 = L + n1 + n1 * ldl;
     const i64 ldt = n2;
     if (itype == 1) {
-        sygst_rec(c, 1, n1, A11, lda, L11, ldl, T);
-        trsm_rlt<double>(c, n2, n1, 1.0, L11, ldl, A21, lda);
+        sygst_rec<E>(c, 1, n1, A11, lda, L11, ldl, T);
+        trsm_rlt<E>(c, n2, n1, E(1), L11, ldl, A21, lda);
         if (T) {
-            symm<double>(c, false, n2, n1, 1.0, A11, lda, L21, ldl, 0.0, T, ldt);
-            axpy_mat(c, n2, n1, -0.5, T, ldt, A21, lda);
+            symm<E>(c, false, n2, n1, E(1), A11, lda, L21, ldl, E(0), T, ldt);
+            axpy_mat<E>(c, n2, n1, E(-0.5), T, ldt, A21, lda);
         } else {
-            symm<double>(c, false, n2, n1, -0.5, A11, lda, L21, ldl, 1.0, A21, lda);
+            symm<E>(c, false, n2, n1, E(-0.5), A11, lda, L21, ldl, E(1), A21, lda);
         }
-        gemm<double>(c, false, true, n2, n2, n1, -1.0, A21, lda, L21, ldl, 1.0, A22, lda, true);
-        gemm<double>(c, false, true, n2, n2, n1, -1.0, L21, ldl, A21, lda, 1.0, A22, lda, true);
-        if (T) axpy_mat(c, n2, n1, -0.5, T, ldt, A21, lda);
-        else symm<double>(c, false, n2, n1, -0.5, A11, lda, L21, ldl, 1.0, A21, lda);
-        trsm_lln<double>(c, false, n2, n1, 1.0, L22, ldl, A21, lda);
-        sygst_rec(c, 1, n2, A22, lda, L22, ldl, T);
+        gemm<E>(c, false, true, n2, n2, n1, E(-1), A21, lda, L21, ldl, E(1), A22, lda, true);
+        gemm<E>(c, false, true, n2, n2, n1, E(-1), L21, ldl, A21, lda, E(1), A22, lda, true);
+        if (T) axpy_mat<E>(c, n2, n1, E(-0.5), T, ldt, A21, lda);
+        else symm<E>(c, false, n2, n1, E(-0.5), A11, lda, L21, ldl, E(1), A21, lda);
+        trsm_lln<E>(c, false, n2, n1, E(1), L22, ldl, A21, lda);
+        sygst_rec<E>(c, 1, n2, A22, lda, L22, ldl, T);
     } else {
-        sygst_rec(c, itype, n1, A11, lda, L11, ldl, T);
-        if (T) symm<double>(c, true, n2, n1, 1.0, A22, lda, L21, ldl, 0.0, T, ldt);
-        trmm_rln<double>(c, false, n2, n1, 1.0, L11, ldl, A21, lda);
-        if (T) axpy_mat(c, n2, n1, 0.5, T, ldt, A21, lda);
-        else symm<double>(c, true, n2, n1, 0.5, A22, lda, L21, ldl, 1.0, A21, lda);
-        gemm<double>(c, true, false, n1, n1, n2, 1.0, L21, ldl, A21, lda, 1.0, A11, lda, true);
-        gemm<double>(c, true, false, n1, n1, n2, 1.0, A21, lda, L21, ldl, 1.0, A11, lda, true);
-        if (T) axpy_mat(c, n2, n1, 0.5, T, ldt, A21, lda);
-        else symm<double>(c, true, n2, n1, 0.5, A22, lda, L21, ldl, 1.0, A21, lda);
-        trmm_llt<double>(c, n2, n1, 1.0, L22, ldl, A21, lda);
-        sygst_rec(c, itype, n2, A22, lda, L22, ldl, T);
+        sygst_rec<E>(c, itype, n1, A11, lda, L11, ldl, T);
+        if (T) symm<E>(c, true, n2, n1, E(1), A22, lda, L21, ldl, E(0), T, ldt);
+        trmm_rln<E>(c, false, n2, n1, E(1), L11, ldl, A21, lda);
+        if (T) axpy_mat<E>(c, n2, n1, E(0.5), T, ldt, A21, lda);
+        else symm<E>(c, true, n2, n1, E(0.5), A22, lda, L21, ldl, E(1), A21, lda);
+        gemm<E>(c, true, false, n1, n1, n2, E(1), L21, ldl, A21, lda, E(1), A11, lda, true);
+        gemm<E>(c, true, false, n1, n1, n2, E(1), A21, lda, L21, ldl, E(1), A11, lda, true);
+        if (T) axpy_mat<E>(c, n2, n1, E(0.5), T, ldt, A21, lda);
+        else symm<E>(c, true, n2, n1, E(0.5), A22, lda, L21, ldl, E(1), A21, lda);
+        trmm_llt<E>(c, n2, n1, E(1), L22, ldl, A21, lda);
+        sygst_rec<E>(c, itype, n2, A22, lda, L22, ldl, T);
     }
 }
+
+template void sygst_rec<double>(Ctx &, int, i64, double *, i64, const double *, i64, double *);
+template void sygst_rec<float>(Ctx &, int, i64, float *, i64, const float *, i64, float *);
 
 }  // namespace rl

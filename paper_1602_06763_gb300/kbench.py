@@ -24,7 +24,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", required=True,
                     choices=["dgemm", "dsyrk", "dtrsm", "potrf", "getrf", "trtri", "lauum", "panel",
-                             "sgemm_tc", "dsgesv", "dsposv", "getrs", "potrs", "sgetrs", "sgemm"])
+                             "sgemm_tc", "dsgesv", "dsposv", "getrs", "potrs", "sgetrs", "sgemm", "laswp"])
     ap.add_argument("--prec", type=int, default=1, help="operand precision (rl_prec) of sgemm_tc / dsgesv")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--cond", type=float, default=1e6)
@@ -111,6 +111,20 @@ def main():
         work = torch.empty(lw, dtype=torch.uint8, device=dev)
         run = lambda: r.check(r.rl_sgemm_tc(a.prec, "N", "N", n, n, k, -1.0, A, n, B, k, C, n, work, lw, s))
         restore = lambda: None
+    elif a.case == "laswp":
+        # the top-level interchanges of an n x n LU: k = n/2 pivots (targets
+        # uniform at or below their row, as partial pivoting of random
+        # matrices gives) applied to the other n/2 columns
+        import numpy as np
+        kp = n // 2
+        rng = np.random.default_rng(7)
+        piv = np.array([rng.integers(j + 1, n + 1) for j in range(kp)], dtype=np.int32)
+        ipiv = torch.from_numpy(piv).to(dev)
+        A = torch.rand(n * n, generator=g, device=dev, dtype=torch.float64)
+        flops = 0.0
+        nbytes = 2.0 * kp * (n - kp) * 16.0          # two rows read and written per interchange per column
+        run = lambda: r.check(r.rl_dlaswp(n, n - kp, A[kp * n:], n, 1, kp, ipiv, s))
+        restore = lambda: None
     elif a.case == "sgemm":
         A = torch.rand(k, n, generator=g, device=dev, dtype=torch.float32)
         B = torch.rand(n, k, generator=g, device=dev, dtype=torch.float32)
@@ -188,6 +202,9 @@ def main():
         times.append(e0.elapsed_time(e1))
     out = {"case": a.case, "n": n, "m": m, "k": k, "ms": statistics.median(times),
            "gflops": flops / (statistics.median(times) * 1e-3) / 1e9, "info": int(info.item())}
+    if a.case == "laswp":
+        out["gbs"] = nbytes / (statistics.median(times) * 1e-3) / 1e9
+        out["bytes"] = nbytes
     if a.case in ("dsgesv", "dsposv"):
         out["iters"] = int(it.item())
         out["prec"] = a.prec

@@ -57,9 +57,18 @@ _SIGS = {
     "rl_dtrmm": (ctypes.c_int, [_ch, _ch, _ch, _ch, _i64, _i64, ctypes.c_double, _vp, _i64, _vp,
                                 _i64, _vp]),
     "rl_trs_work_size": (ctypes.c_size_t, [_i64, _i64]),
+    "rl_dlaswp": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _vp, _vp]),
+    "rl_spotrf_tc_work_size": (ctypes.c_size_t, [_i64, ctypes.c_int]),
+    "rl_sgetrf_tc_work_size": (ctypes.c_size_t, [_i64, _i64, ctypes.c_int]),
+    "rl_spotrf_tc": (ctypes.c_int, [ctypes.c_int, _ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_sgetrf_tc": (ctypes.c_int, [ctypes.c_int, _i64, _i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
     "rl_dgetri_work_size": (ctypes.c_size_t, [_i64]),
     "rl_dgetri": (ctypes.c_int, [_i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
+    "rl_sgetri_work_size": (ctypes.c_size_t, [_i64]),
+    "rl_sgetri": (ctypes.c_int, [_i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
     "rl_dsygst_work_size": (ctypes.c_size_t, [_i64]),
+    "rl_ssygst_work_size": (ctypes.c_size_t, [_i64]),
+    "rl_ssygst": (ctypes.c_int, [ctypes.c_int, _ch, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
     "rl_dsygst": (ctypes.c_int, [ctypes.c_int, _ch, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
     "rl_dgetrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _sz, _vp]),
     "rl_dpotrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
@@ -78,6 +87,11 @@ _SIGS = {
     "rl_spotrf_vbatched": (ctypes.c_int, [_ch, _i64, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _sz, _vp]),
     "rl_dgetrf_vbatched": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _sz, _vp]),
     "rl_sgetrf_vbatched": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _sz, _vp]),
+    "rl_vbatched_tune_work_size": (ctypes.c_size_t, [_i64, _i64, ctypes.c_int]),
+    "rl_vbatched_tune": (ctypes.c_int, [_ch, ctypes.c_int, _i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp,
+                                        _sz, _vp, _vp, _vp]),
+    "rl_vbatched_config": (ctypes.c_int, [_ch, ctypes.c_int, _vp, _vp, _vp, _vp]),
+    "rl_vbatched_set_config": (ctypes.c_int, [_ch, ctypes.c_int, ctypes.c_int32]),
     "rl_dgetrf_vbatched_noalloc": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp]),
     "rl_spotrf": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
     "rl_sgetrf": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
@@ -208,6 +222,31 @@ def rl_dtrmm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream=None)
                          _ptr(B), ldb, _stream(stream))
 
 
+def rl_spotrf_tc_work_size(n, prec):
+    return int(_lib.rl_spotrf_tc_work_size(n, prec))
+
+
+def rl_sgetrf_tc_work_size(m, n, prec):
+    return int(_lib.rl_sgetrf_tc_work_size(m, n, prec))
+
+
+def rl_spotrf_tc(prec, uplo, n, A, lda, info, work, lwork, stream=None):
+    return _lib.rl_spotrf_tc(prec, _c(uplo), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_sgetrf_tc(prec, m, n, A, lda, ipiv, info, work, lwork, stream=None):
+    return _lib.rl_sgetrf_tc(prec, m, n, _ptr(A), lda, _ptr(ipiv), _ptr(info), _ptr(work), lwork,
+                             _stream(stream))
+
+
+def rl_sgetri_work_size(n):
+    return int(_lib.rl_sgetri_work_size(n))
+
+
+def rl_sgetri(n, A, lda, ipiv, info, work, lwork, stream=None):
+    return _lib.rl_sgetri(n, _ptr(A), lda, _ptr(ipiv), _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
 def rl_dgetri_work_size(n):
     return int(_lib.rl_dgetri_work_size(n))
 
@@ -216,12 +255,24 @@ def rl_dgetri(n, A, lda, ipiv, info, work, lwork, stream=None):
     return _lib.rl_dgetri(n, _ptr(A), lda, _ptr(ipiv), _ptr(info), _ptr(work), lwork, _stream(stream))
 
 
+def rl_ssygst_work_size(n):
+    return int(_lib.rl_ssygst_work_size(n))
+
+
+def rl_ssygst(itype, uplo, n, A, lda, B, ldb, work=None, lwork=0, stream=None):
+    return _lib.rl_ssygst(itype, _c(uplo), n, _ptr(A), lda, _ptr(B), ldb, _ptr(work), lwork, _stream(stream))
+
+
 def rl_dsygst_work_size(n):
     return int(_lib.rl_dsygst_work_size(n))
 
 
 def rl_dsygst(itype, uplo, n, A, lda, B, ldb, work=None, lwork=0, stream=None):
     return _lib.rl_dsygst(itype, _c(uplo), n, _ptr(A), lda, _ptr(B), ldb, _ptr(work), lwork, _stream(stream))
+
+
+def rl_dlaswp(m, ncols, A, lda, k1, k2, ipiv, stream=None):
+    return _lib.rl_dlaswp(m, ncols, _ptr(A), lda, k1, k2, _ptr(ipiv), _stream(stream))
 
 
 def rl_trs_work_size(n, nrhs):
@@ -293,6 +344,35 @@ def rl_dgetrf_vbatched(batch, n, A, lda, ipiv, info, max_n, work, lwork, stream=
 def rl_sgetrf_vbatched(batch, n, A, lda, ipiv, info, max_n, work, lwork, stream=None):
     return _lib.rl_sgetrf_vbatched(batch, _ptr(n), _ptr(A), _ptr(lda), _ptr(ipiv), _ptr(info), max_n,
                                    _ptr(work), lwork, _stream(stream))
+
+
+RL_BATCH_CONFIGS = 8
+
+
+def rl_vbatched_tune_work_size(batch, sum_n2, elem_bytes):
+    return int(_lib.rl_vbatched_tune_work_size(batch, sum_n2, elem_bytes))
+
+
+def rl_vbatched_tune(routine, elem_bytes, batch, n, A, lda, ipiv, info, max_n, work, lwork, stream=None):
+    """Returns (status, best configuration, list of ms per configuration)."""
+    best = ctypes.c_int32(-1)
+    ms = (ctypes.c_float * RL_BATCH_CONFIGS)()
+    st = _lib.rl_vbatched_tune(_c(routine), elem_bytes, batch, _ptr(n), _ptr(A), _ptr(lda), _ptr(ipiv),
+                               _ptr(info), max_n, _ptr(work), lwork, ctypes.byref(best),
+                               ctypes.cast(ms, ctypes.c_void_p), _stream(stream))
+    return st, best.value, list(ms)
+
+
+def rl_vbatched_set_config(routine, elem_bytes, cfg):
+    return _lib.rl_vbatched_set_config(_c(routine), elem_bytes, cfg)
+
+
+def rl_vbatched_config(routine, elem_bytes):
+    """(cfg, nb, threads, per_sm) in use for the routine and element size."""
+    v = [ctypes.c_int32(0) for _ in range(4)]
+    st = _lib.rl_vbatched_config(_c(routine), elem_bytes, *[ctypes.byref(x) for x in v])
+    check(st, "rl_vbatched_config")
+    return tuple(x.value for x in v)
 
 
 def rl_dgetrf_vbatched_noalloc(batch, n, A, lda, ipiv, info, max_n, stream=None):

@@ -93,3 +93,23 @@ def test_host_logic_of_the_other_routines(built):
     assert r.rl_dpotrs("L", 4, 1, 8, 3, 8, 4, stream=0) == -5
     assert r.rl_set_param(r.RL_PARAM_TRI_LANES, 3) == r.RL_ERR_PARAM
     assert r.rl_get_param(r.RL_PARAM_TRI_LANES) == 0
+
+
+def test_host_logic_of_the_tuning_and_lowprec_calls(built):
+    from paper_1602_06763_gb300 import relgpu as r
+    assert r.rl_spotrf_tc_work_size(1000, r.RL_PREC_FP32) == 0
+    assert r.rl_spotrf_tc_work_size(1000, r.RL_PREC_BF16) > 0
+    assert r.rl_sgetrf_tc_work_size(1000, 1000, r.RL_PREC_TF32X3) > r.rl_sgetrf_tc_work_size(1000, 1000,
+                                                                                           r.RL_PREC_TF32)
+    assert r.rl_spotrf_tc(r.RL_PREC_FP32, "L", 4, 8, 4, 8, None, 0, stream=0) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_spotrf_tc(r.RL_PREC_BF16, "L", 4, 8, 4, 8, None, 0, stream=0) == r.RL_ERR_WORKSPACE
+    assert r.rl_sgetrf_tc(r.RL_PREC_BF16, 4, 4, 8, 3, 8, 8, None, 0, stream=0) == -5
+    assert r.rl_dlaswp(10, 4, 8, 10, 0, 5, 8, stream=0) == -5
+    assert r.rl_dlaswp(10, 4, 8, 10, 1, 11, 8, stream=0) == -6
+    assert r.rl_vbatched_set_config("G", 8, r.RL_BATCH_CONFIGS) == -3
+    assert r.rl_vbatched_set_config("X", 8, 0) == -1
+    assert r.rl_vbatched_set_config("P", 4, 3) == 0
+    assert r.rl_vbatched_config("P", 4)[:2] == (3, 32)
+    assert r.rl_vbatched_set_config("P", 4, 0) == 0
+    assert r.rl_vbatched_tune_work_size(10, 1000, 8) >= 1000 * 8
+    assert r.rl_vbatched_tune_work_size(10, 1000, 3) == 0

@@ -178,3 +178,64 @@ def test_vbatched_argument_checks():
     assert r.rl_dpotrf_vbatched("L", 1, p, p, p, p, 300, w, 1024) == r.RL_ERR_UNSUPPORTED
     assert r.rl_dgetrf_vbatched(2, p, p, p, p, p, 8, w, 4) == r.RL_ERR_WORKSPACE
     assert r.rl_dgetrf_vbatched(0, p, p, p, p, p, 8, w, 1024) == 0
+
+
+# ---- the autotuner and every configuration it chooses from -------------------
+
+@pytest.fixture
+def batch_cfg_reset():
+    yield
+    r = G.lib()
+    for k in "PG":
+        for eb in (4, 8):
+            r.rl_vbatched_set_config(k, eb, 0)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_every_batched_config_vs_oracle(prec, batch_cfg_reset):
+    r = G.lib()
+    t = G.torch()
+    sizes = [1, 15, 16, 17, 31, 33, 64, 100, 129, 200, 256]
+    eb = 8 if prec == "f64" else 4
+    dt = t.float64 if prec == "f64" else t.float32
+    scale = 1.0 if prec == "f64" else EPS64 / EPS32
+    S = [inputs.spd_bbt(n, seed=inputs.seed_for(3, 700 + i)) for i, n in enumerate(sizes)]
+    U_ = [inputs.uniform(n, n, seed=inputs.seed_for(3, 800 + i)) for i, n in enumerate(sizes)]
+    if prec == "f32":
+        S = [m.astype(np.float32).astype(np.float64) for m in S]
+        U_ = [m.astype(np.float32).astype(np.float64) for m in U_]
+    for cfg in range(r.RL_BATCH_CONFIGS):
+        assert r.rl_vbatched_set_config("P", eb, cfg) == 0 and r.rl_vbatched_set_config("G", eb, cfg) == 0
+        B = Batch(S, dt, pad=1)
+        info = run("potrf", B)
+        assert np.all(info == 0)
+        for b, A in enumerate(S):
+            assert oracle.res_chol(A, B.get(b)) * scale <= 10.0, (cfg, b)
+        B = Batch(U_, dt)
+        info = run("getrf", B)
+        assert np.all(info == 0)
+        for b, A in enumerate(U_):
+            assert oracle.res_lu(A, B.get(b), B.piv(b)) * scale <= 10.0, (cfg, b)
+
+
+def test_autotuner_restores_the_batch_and_picks_a_config(batch_cfg_reset):
+    r = G.lib()
+    t = G.torch()
+    sizes = list(inputs.bucket_sizes(300, 8, 256, inputs.seed_for(3, 900)))
+    mats = [inputs.uniform(n, n, seed=inputs.seed_for(3, 1000 + i)) for i, n in enumerate(sizes)]
+    B = Batch(mats, t.float64)
+    before = B.buf.clone()
+    lw = r.rl_vbatched_tune_work_size(len(sizes), int(sum(n * n for n in sizes)), 8)
+    w = t.empty(lw, dtype=t.uint8, device="cuda")
+    st, best, ms = r.rl_vbatched_tune("G", 8, len(sizes), B.n, B.ptrs, B.lda, B.ipiv, B.info, 256, w, lw)
+    assert st == 0, r.rl_status_string(st)
+    assert 0 <= best < r.RL_BATCH_CONFIGS and all(m > 0 for m in ms)
+    assert ms[best] == min(ms)
+    assert r.rl_vbatched_config("G", 8)[0] == best
+    assert t.equal(B.buf, before)                    # the caller's matrices are back
+    info = run("getrf", B)
+    assert np.all(info == 0)
+    for b, A in enumerate(mats):
+        assert oracle.res_lu(A, B.get(b), B.piv(b)) <= 10.0
+    assert r.rl_vbatched_tune("G", 8, len(sizes), B.n, B.ptrs, B.lda, B.ipiv, B.info, 256, w, lw - 1)[0] \
+        == r.RL_ERR_WORKSPACE

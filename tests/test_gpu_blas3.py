@@ -245,3 +245,20 @@ def test_ssyrk_lower(trans, n, k):
     lower = np.tril(np.ones((n, n), dtype=bool))
     assert np.all((np.abs(got - ref) <= bound)[lower])
     assert np.array_equal(np.triu(got, 1), np.triu(C, 1))
+
+
+def test_dlaswp_vs_oracle():
+    r = G.lib()
+    t = G.torch()
+    m, ncols, k1, k2 = 5000, 300, 3, 4700
+    rng = np.random.default_rng(inputs.seed_for(1, 5000))
+    piv = np.array([rng.integers(j + 1, m + 1) for j in range(m)], dtype=np.int32)
+    A = inputs.uniform(m, ncols, seed=inputs.seed_for(1, 5001))
+    dA = G.DevMat(A, lda=m + 2)
+    dp = t.from_numpy(piv).cuda()
+    assert r.rl_dlaswp(m, ncols, dA.ptr(), dA.lda, k1, k2, dp) == 0
+    G.sync()
+    assert dA.canaries_intact()
+    ref = oracle.laswp(A, k1 - 1, k2, piv)
+    assert np.array_equal(dA.get(), ref)
+    assert r.rl_dlaswp(m, ncols, dA.ptr(), dA.lda, 0, k2, dp) == -5

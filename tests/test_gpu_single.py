@@ -141,3 +141,37 @@ def test_strtri_exact_and_zero_diagonal():
     G.sync()
     assert int(info[0]) == 78
     assert np.array_equal(from_dev32(dZ, n, n), Z)
+
+
+@pytest.mark.parametrize("n", [1, 130, 700])
+def test_sgetri_ssygst_vs_oracle(n):
+    r = G.lib()
+    t = G.torch()
+    A = inputs.uniform(n, n, seed=inputs.seed_for(1, 3700 + n)).astype(np.float32).astype(np.float64)
+    F, ipiv, info = oracle.getrf(A, c=24)
+    F32 = F.astype(np.float32).astype(np.float64)
+    dF = to_dev32(F32)
+    dp = t.from_numpy(np.ascontiguousarray(ipiv, dtype=np.int32)).cuda()
+    info = G.int_buf(1, -7)
+    lw = r.rl_sgetri_work_size(n)
+    w = t.empty(lw, dtype=t.uint8, device="cuda")
+    assert r.rl_sgetri(n, dF, n, dp, info, w, lw) == 0
+    G.sync()
+    assert int(info[0]) == 0
+    X = from_dev32(dF, n, n)
+    ref = oracle.getri(F32, ipiv)
+    kappa = np.linalg.cond(A)
+    assert np.max(np.abs(X - ref)) <= 64 * n * 2.0 ** -24 * kappa * np.max(np.abs(ref))
+    # sygst itype 1 and 2, with the buffer
+    S = inputs.spd_bbt(n, seed=inputs.seed_for(1, 3800 + n)).astype(np.float32).astype(np.float64)
+    Bm = inputs.spd_bbt(n, seed=inputs.seed_for(1, 3900 + n))
+    L = np.tril(oracle.potrf(Bm, c=24)[0]).astype(np.float32).astype(np.float64)
+    for itype in (1, 2):
+        dS, dL = to_dev32(S), to_dev32(L)
+        lw = max(r.rl_ssygst_work_size(n), 4)
+        w = t.empty(lw, dtype=t.uint8, device="cuda")
+        assert r.rl_ssygst(itype, "L", n, dS, n, dL, n, w, lw) == 0
+        G.sync()
+        got = np.tril(from_dev32(dS, n, n))
+        ref = np.tril(oracle.sygst(itype, S, L))
+        assert np.max(np.abs(got - ref)) <= 64 * n * 2.0 ** -24 * np.max(np.abs(ref))
