@@ -56,6 +56,11 @@ def _lib():
             "or_getrs": (None, [_i64, _i64, _ptr, _i64, _ptr, _ptr, _i64]),
             "or_potrs": (None, [_i64, _i64, _ptr, _i64, _ptr, _i64]),
             "or_getri": (None, [_i64, _ptr, _i64, _ptr, _ptr, _i64]),
+            "or_zpotrf": (_i64, [_i64, _ptr, _i64, _i64]),
+            "or_zgetrf": (_i64, [_i64, _i64, _ptr, _i64, _ptr, _i64]),
+            "or_zlaswp": (None, [_i64, _ptr, _i64, _i64, _i64, _ptr]),
+            "or_res_zchol": (_dbl, [_i64, _ptr, _i64, _ptr, _i64]),
+            "or_res_zlu": (_dbl, [_i64, _i64, _ptr, _i64, _ptr, _i64, _ptr]),
             "or_sygst": (_i64, [ctypes.c_int, _i64, _ptr, _i64, _ptr, _i64]),
             "or_gemm": (None, [ctypes.c_int, ctypes.c_int, _i64, _i64, _i64, _dbl,
                                _ptr, _i64, _ptr, _i64, _ptr, _i64]),
@@ -274,6 +279,41 @@ def getri(LU, ipiv):
     ipiv = np.ascontiguousarray(ipiv, dtype=np.int32)
     _lib().or_getri(n, _p(LU), _ld(LU), _p(ipiv), _p(X), _ld(X))
     return X
+
+
+def _c128(a, copy=True):
+    a = np.asarray(a, dtype=np.complex128)
+    return np.array(a, dtype=np.complex128, order="F", copy=True) if copy else np.asfortranarray(a)
+
+
+def zpotrf(A, c=24):
+    """Recursive complex Cholesky A = L L^H (lower); returns (A with L, info)."""
+    A = _c128(A)
+    info = _lib().or_zpotrf(A.shape[0], _p(A), _ld(A), c)
+    return A, int(info)
+
+
+def zgetrf(A, c=24):
+    """Recursive complex LU with partial pivoting on |Re| + |Im|; returns
+    (LU, 1-based ipiv, info)."""
+    A = _c128(A)
+    m, n = A.shape
+    ipiv = np.zeros(max(1, min(m, n)), dtype=np.int32)
+    info = _lib().or_zgetrf(m, n, _p(A), _ld(A), _p(ipiv), c)
+    return A, ipiv[:min(m, n)], int(info)
+
+
+def res_zchol(A0, L):
+    """||A - L L^H||_1 / (n eps ||A||_1), eps = 2^-53 (lower parts used)."""
+    A0, L = _c128(A0), _c128(L)
+    return float(_lib().or_res_zchol(A0.shape[0], _p(A0), _ld(A0), _p(L), _ld(L)))
+
+
+def res_zlu(A0, LU, ipiv):
+    """||P A - L U||_1 / (n eps ||A||_1)."""
+    A0, LU = _c128(A0), _c128(LU)
+    ipiv = np.ascontiguousarray(ipiv, dtype=np.int32)
+    return float(_lib().or_res_zlu(A0.shape[0], A0.shape[1], _p(A0), _ld(A0), _p(LU), _ld(LU), _p(ipiv)))
 
 
 def sygst(itype, A, L):

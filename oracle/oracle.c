@@ -29,6 +29,8 @@
  *   or_laswp        the row interchanges P of xgetrf
  *   or_getri        Section 5, xtrtri as the building block of xgetri:
  *                   the inverse by its definition, A X = I
+ *   or_zpotrf,      complex double peers (Section 5: s, d, c and z): the
+ *   or_zgetrf       same recursions with the conjugate transpose
  *   or_sygst        Section 5, xsygst (A := L^{-1} A L^{-T}, or L^T A L):
  *                   the definition, by substitution and products
  *   metrics         normwise backward errors used by the benchmark spec's bound
@@ -979,3 +981,234 @@ double or_probe_potri(int64_t n, const double *A0, int64_t lda0, const double *X
     return r / ((double)n * ldexp(1.0, -53) * inf_norm_sym_lower(n, A0, lda0) *
                 inf_norm_sym_lower(n, X, ldx) * xn);
 }
+
+
+/* ========================================================================== */
+/* Complex double (Section 5: every routine exists for s, d, c and z).        */
+/* The same recursions with the conjugate transpose where the real ones use  */
+/* the transpose: Cholesky A = L L^H (A Hermitian, lower triangle read; the  */
+/* diagonal's imaginary part is ignored, as LAPACK's zpotrf does), LU with   */
+/* partial pivoting on |Re| + |Im| (LAPACK's izamax), lowest row on ties.     */
+/* C99 complex arithmetic; every multiply and divide is the library's.        */
+/* ========================================================================== */
+#include <complex.h>
+typedef double complex zc_t;
+#define ZT(M, ld, i, j) (M)[(size_t)(j) * (size_t)(ld) + (size_t)(i)]
+
+static double zabs1(zc_t v) { return fabs(creal(v)) + fabs(cimag(v)); }
+
+int64_t or_zpotf2(int64_t n, zc_t *A, int64_t lda)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int64_t k = 0; k < j; ++k) {
+            zc_t l = ZT(A, lda, j, k);
+            s += creal(l) * creal(l) + cimag(l) * cimag(l);
+        }
+        double d = creal(ZT(A, lda, j, j)) - s;
+        if (!(d > 0.0)) {
+            ZT(A, lda, j, j) = d;
+            return j + 1;
+        }
+        double ljj = sqrt(d);
+        ZT(A, lda, j, j) = ljj;
+        for (int64_t i = j + 1; i < n; ++i) {
+            zc_t t = 0.0;
+            for (int64_t k = 0; k < j; ++k) t += ZT(A, lda, i, k) * conj(ZT(A, lda, j, k));
+            ZT(A, lda, i, j) = (ZT(A, lda, i, j) - t) / ljj;
+        }
+    }
+    return 0;
+}
+
+/* B (m x n) := B L^{-H}: each row x solves x L^H = b by forward substitution. */
+static void or_ztrsm_rlc(int64_t m, int64_t n, const zc_t *L, int64_t ldl, zc_t *B, int64_t ldb)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            zc_t s = ZT(B, ldb, i, j);
+            for (int64_t k = 0; k < j; ++k) s -= ZT(B, ldb, i, k) * conj(ZT(L, ldl, j, k));
+            ZT(B, ldb, i, j) = s / conj(ZT(L, ldl, j, j));
+        }
+}
+
+/* C (n x n, lower) -= A A^H, A n x k. */
+static void or_zherk_lower(int64_t n, int64_t k, const zc_t *A, int64_t lda, zc_t *C, int64_t ldc)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = j; i < n; ++i) {
+            zc_t s = 0.0;
+            for (int64_t p = 0; p < k; ++p) s += ZT(A, lda, i, p) * conj(ZT(A, lda, j, p));
+            ZT(C, ldc, i, j) -= s;
+        }
+}
+
+int64_t or_zpotrf(int64_t n, zc_t *A, int64_t lda, int64_t c)
+{
+    if (n <= 0) return 0;
+    if (c < 1) c = 1;
+    if (n <= c) return or_zpotf2(n, A, lda);
+    int64_t n1 = or_split(n), n2 = n - n1;
+    zc_t *A21 = &ZT(A, lda, n1, 0), *A22 = &ZT(A, lda, n1, n1);
+    int64_t info = or_zpotrf(n1, A, lda, c);
+    if (info) return info;
+    or_ztrsm_rlc(n2, n1, A, lda, A21, lda);
+    or_zherk_lower(n2, n1, A21, lda, A22, lda);
+    info = or_zpotrf(n2, A22, lda, c);
+    return info ? info + n1 : 0;
+}
+
+void or_zlaswp(int64_t n, zc_t *A, int64_t lda, int64_t k1, int64_t k2, const int32_t *ipiv)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = k1; i < k2; ++i) {
+            int64_t p = (int64_t)ipiv[i] - 1;
+            if (p != i) {
+                zc_t t = ZT(A, lda, i, j);
+                ZT(A, lda, i, j) = ZT(A, lda, p, j);
+                ZT(A, lda, p, j) = t;
+            }
+        }
+}
+
+int64_t or_zgetf2(int64_t m, int64_t n, zc_t *A, int64_t lda, int32_t *ipiv)
+{
+    int64_t info = 0, mn = m < n ? m : n;
+    for (int64_t j = 0; j < mn; ++j) {
+        int64_t p = j;
+        double amax = zabs1(ZT(A, lda, j, j));
+        for (int64_t i = j + 1; i < m; ++i) {
+            double v = zabs1(ZT(A, lda, i, j));
+            if (v > amax) { amax = v; p = i; }
+        }
+        ipiv[j] = (int32_t)(p + 1);
+        if (ZT(A, lda, p, j) != 0.0) {
+            if (p != j)
+                for (int64_t k = 0; k < n; ++k) {
+                    zc_t t = ZT(A, lda, j, k);
+                    ZT(A, lda, j, k) = ZT(A, lda, p, k);
+                    ZT(A, lda, p, k) = t;
+                }
+            zc_t piv = ZT(A, lda, j, j);
+            for (int64_t i = j + 1; i < m; ++i) ZT(A, lda, i, j) = ZT(A, lda, i, j) / piv;
+        } else if (info == 0) {
+            info = j + 1;
+        }
+        for (int64_t k = j + 1; k < n; ++k) {
+            zc_t u = ZT(A, lda, j, k);
+            for (int64_t i = j + 1; i < m; ++i) ZT(A, lda, i, k) -= ZT(A, lda, i, j) * u;
+        }
+    }
+    return info;
+}
+
+int64_t or_zgetrf(int64_t m, int64_t n, zc_t *A, int64_t lda, int32_t *ipiv, int64_t c)
+{
+    if (m <= 0 || n <= 0) return 0;
+    if (c < 1) c = 1;
+    int64_t mn = m < n ? m : n;
+    if (n <= c || mn <= c) return or_zgetf2(m, n, A, lda, ipiv);
+    int64_t n1 = or_split(mn), n2 = n - n1;
+    zc_t *A12 = &ZT(A, lda, 0, n1), *A21 = &ZT(A, lda, n1, 0), *A22 = &ZT(A, lda, n1, n1);
+    int64_t info = or_zgetrf(m, n1, A, lda, ipiv, c);
+    or_zlaswp(n2, A12, lda, 0, n1, ipiv);
+    /* A12 := L11^{-1} A12 (unit lower), column by column */
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n2; ++j)
+        for (int64_t i = 0; i < n1; ++i) {
+            zc_t s = ZT(A12, lda, i, j);
+            for (int64_t k = 0; k < i; ++k) s -= ZT(A, lda, i, k) * ZT(A12, lda, k, j);
+            ZT(A12, lda, i, j) = s;
+        }
+    /* A22 -= A21 A12 */
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n2; ++j)
+        for (int64_t i = 0; i < m - n1; ++i) {
+            zc_t s = 0.0;
+            for (int64_t k = 0; k < n1; ++k) s += ZT(A21, lda, i, k) * ZT(A12, lda, k, j);
+            ZT(A22, lda, i, j) -= s;
+        }
+    int64_t info2 = or_zgetrf(m - n1, n2, A22, lda, ipiv + n1, c);
+    int64_t mn2 = (m - n1) < n2 ? (m - n1) : n2;
+    for (int64_t i = 0; i < mn2; ++i) ipiv[n1 + i] += (int32_t)n1;
+    if (info == 0 && info2 != 0) info = info2 + n1;
+    or_zlaswp(n1, A, lda, n1, n1 + mn2, ipiv);
+    return info;
+}
+
+/* ||A - L L^H||_1 / (n eps ||A||_1), A Hermitian (lower part read), Dot2
+ * on the real and imaginary parts of every entry. */
+double or_res_zchol(int64_t n, const zc_t *A0, int64_t lda0, const zc_t *L, int64_t ldl)
+{
+    if (n <= 0) return 0.0;
+    double rmax = 0.0, amax = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        double s = 0.0, sa = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t r = i >= j ? i : j, q = i >= j ? j : i;   /* lower entry (r, q) */
+            zc_t a = ZT(A0, lda0, r, q);
+            if (i < j) a = conj(a);
+            if (i == j) a = creal(a);
+            dot2_t re = {0.0, 0.0}, im = {0.0, 0.0};
+            dot2_add(&re, creal(a), 1.0);
+            dot2_add(&im, cimag(a), 1.0);
+            const int64_t kk = (i < j ? i : j);
+            for (int64_t k = 0; k <= kk; ++k) {
+                zc_t x = ZT(L, ldl, i, k), y = ZT(L, ldl, j, k);   /* x conj(y) */
+                dot2_add(&re, -creal(x), creal(y));
+                dot2_add(&re, -cimag(x), cimag(y));
+                dot2_add(&im, -cimag(x), creal(y));
+                dot2_add(&im, creal(x), cimag(y));
+            }
+            s += hypot(dot2_val(&re), dot2_val(&im));
+            sa += cabs(a);
+        }
+        if (s > rmax) rmax = s;
+        if (sa > amax) amax = sa;
+    }
+    return rmax / ((double)n * 0x1p-53 * amax);
+}
+
+/* ||P A - L U||_1 / (n eps ||A||_1) for an m x n LU (P from ipiv). */
+double or_res_zlu(int64_t m, int64_t n, const zc_t *A0, int64_t lda0, const zc_t *LU, int64_t ldf,
+                  const int32_t *ipiv)
+{
+    if (m <= 0 || n <= 0) return 0.0;
+    int64_t mn = m < n ? m : n;
+    int64_t *perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+    if (!perm) return -1.0;
+    for (int64_t i = 0; i < m; ++i) perm[i] = i;
+    for (int64_t i = 0; i < mn; ++i) {
+        int64_t p = ipiv[i] - 1, t = perm[i];
+        perm[i] = perm[p];
+        perm[p] = t;
+    }
+    double rmax = 0.0, amax = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        double s = 0.0, sa = 0.0;
+        for (int64_t i = 0; i < m; ++i) {
+            zc_t a = ZT(A0, lda0, perm[i], j);
+            dot2_t re = {0.0, 0.0}, im = {0.0, 0.0};
+            dot2_add(&re, creal(a), 1.0);
+            dot2_add(&im, cimag(a), 1.0);
+            const int64_t kk = i < j ? i : j;
+            for (int64_t k = 0; k <= kk && k < mn; ++k) {
+                zc_t l = (k == i) ? 1.0 : ZT(LU, ldf, i, k), u = ZT(LU, ldf, k, j);
+                dot2_add(&re, -creal(l), creal(u));
+                dot2_add(&re, cimag(l), cimag(u));
+                dot2_add(&im, -creal(l), cimag(u));
+                dot2_add(&im, -cimag(l), creal(u));
+            }
+            s += hypot(dot2_val(&re), dot2_val(&im));
+            sa += cabs(ZT(A0, lda0, i, j));
+        }
+        if (s > rmax) rmax = s;
+        if (sa > amax) amax = sa;
+    }
+    free(perm);
+    return rmax / ((double)n * 0x1p-53 * amax);
+}
+
