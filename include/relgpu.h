@@ -228,6 +228,22 @@ int rl_spotrs(char uplo, int64_t n, int64_t nrhs, const float *A, int64_t lda, f
               int64_t ldb, void *work, size_t lwork, rl_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Complex double peers (Section 5: every routine exists for s, d, c and z).
+ * rl_double_complex is LAPACK's complex*16 layout (re, im interleaved).
+ *   rl_zpotrf: A = L L^H (Hermitian positive definite, lower triangle read;
+ *     the diagonal's imaginary part is ignored), info as rl_dpotrf.
+ *   rl_zgetrf: P A = L U with partial pivoting on |Re| + |Im| (LAPACK's
+ *     izamax), lowest row on ties; ipiv, info and workspace
+ *     (rl_dgetrf_work_size) as rl_dgetrf; panels of at most 32 columns.
+ * Same recursions and argument numbering as the double-precision routines.
+ * ------------------------------------------------------------------------- */
+typedef struct { double re, im; } rl_double_complex;
+int rl_zpotrf(char uplo, int64_t n, rl_double_complex *A, int64_t lda, int32_t *info,
+              void *work, size_t lwork, rl_stream_t stream);
+int rl_zgetrf(int64_t m, int64_t n, rl_double_complex *A, int64_t lda, int32_t *ipiv,
+              int32_t *info, void *work, size_t lwork, rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Low-precision factorizations (the factorization step of the precision
  * form, callable on its own): rl_spotrf / rl_sgetrf on FP32 storage with
  * every large GEMM/SYRK update on the tensor cores (tcgen05) with operands in
@@ -469,6 +485,10 @@ int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda,
  *                              alone.  Factorizations whose updates run on
  *                              the tensor cores (precision form) share one
  *                              packing workspace and run on one stream.
+ *   RL_PARAM_PANEL_CTAS        CTAs of the LU panel kernel: low 16 bits for
+ *                              FP64 panels, high 16 bits for FP32 panels
+ *                              (0, the default: one per SM; at most 256
+ *                              rows each either way)
  * rl_set_param returns 0 or RL_ERR_PARAM; rl_get_param returns the value or
  * -1 for an unknown key.
  * ------------------------------------------------------------------------- */
@@ -479,7 +499,8 @@ enum {
     RL_PARAM_SPIN_LIMIT_NS = 4,
     RL_PARAM_BATCH_CTAS = 5,
     RL_PARAM_TRI_LANES = 6,
-    RL_PARAM_LOOKAHEAD = 7
+    RL_PARAM_LOOKAHEAD = 7,
+    RL_PARAM_PANEL_CTAS = 8
 };
 int rl_set_param(int key, int64_t value);
 int64_t rl_get_param(int key);

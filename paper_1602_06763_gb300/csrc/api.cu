@@ -161,7 +161,7 @@ static void getrf_rec_la(Ctx &c, T *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r
 {
     if (m <= 0 || n <= 0) return;
     T *A = A0 + r0 + r0 * lda;
-    const i64 nb = g_params.getrf_nb;
+    const i64 nb = is_cplx<T>::value && g_params.getrf_nb > 32 ? 32 : g_params.getrf_nb;   // complex panels <= 32
     if (n <= nb) {
         if (pending) note(c, cudaStreamWaitEvent(c.s, pending, 0));
         getf2_panel<T>(c, m, n, A, lda, ipiv, r0);
@@ -217,6 +217,8 @@ template void potrf_rec_t<double>(Ctx &, i64, double *, i64, i64);
 template void potrf_rec_t<float>(Ctx &, i64, float *, i64, i64);
 template void getrf_rec_t<double>(Ctx &, double *, i64, i64, int32_t *, i64, i64, i64);
 template void getrf_rec_t<float>(Ctx &, float *, i64, i64, int32_t *, i64, i64, i64);
+template void potrf_rec_t<cplx>(Ctx &, i64, cplx *, i64, i64);
+template void getrf_rec_t<cplx>(Ctx &, cplx *, i64, i64, int32_t *, i64, i64, i64);
 
 static void potrf_rec(Ctx &c, i64 n, double *A, i64 lda, i64 off) { potrf_rec_t<double>(c, n, A, lda, off); }
 static void getrf_rec(Ctx &c, double *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r0, i64 m, i64 n)
@@ -520,6 +522,41 @@ int rl_dtrmm(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
 }
 
 // ---- single precision peers -----------------------------------------------------
+
+// ---- complex double ------------------------------------------------------------
+
+int rl_zpotrf(char uplo, int64_t n, rl_double_complex *A, int64_t lda, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream)
+{
+    if (!is_l(uplo) && !is_u(uplo)) return -1;
+    if (n < 0) return -2;
+    if (n > 0 && A == nullptr) return -3;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (info == nullptr) return RL_ERR_NULL_POINTER;
+    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
+    Ctx c = make_ctx(stream, info, work, lwork);
+    c.abort = info;
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    potrf_rec_t<cplx>(c, n, reinterpret_cast<cplx *>(A), lda, 0);
+    return finish(c);
+}
+
+int rl_zgetrf(int64_t m, int64_t n, rl_double_complex *A, int64_t lda, int32_t *ipiv, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream)
+{
+    if (m < 0) return -1;
+    if (n < 0) return -2;
+    if (m > 0 && n > 0 && A == nullptr) return -3;
+    if (lda < (m > 1 ? m : 1)) return -4;
+    if (m > INT32_MAX - 1) return RL_ERR_UNSUPPORTED;
+    if (info == nullptr || (ipiv == nullptr && m > 0 && n > 0)) return RL_ERR_NULL_POINTER;
+    if (m > 0 && n > 0 && (work == nullptr || lwork < rl_dgetrf_work_size(m, n))) return RL_ERR_WORKSPACE;
+    Ctx c = make_ctx(stream, info, work, lwork);
+    c.abort = nullptr;
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    getrf_rec_t<cplx>(c, reinterpret_cast<cplx *>(A), lda, m, ipiv, 0, m, n);
+    return finish(c);
+}
 
 // ---- low-precision factorizations (FP32 storage, tensor-core updates) --------
 // The factorization step of the precision form as calls of their own: the
@@ -1213,6 +1250,12 @@ int rl_set_param(int key, int64_t value)
         if (value != 0 && value != 1) return RL_ERR_PARAM;
         g_params.lookahead = (int)value;
         return RL_SUCCESS;
+    case RL_PARAM_PANEL_CTAS:
+        // low 16 bits: FP64 panels, high 16 bits: FP32 panels (0 = one per SM)
+        if (value < 0 || (value & 0xffff) > 256 || (value >> 16) > 256) return RL_ERR_PARAM;
+        g_params.panel_ctas64 = (int)(value & 0xffff);
+        g_params.panel_ctas32 = (int)(value >> 16);
+        return RL_SUCCESS;
     default:
         return RL_ERR_PARAM;
     }
@@ -1228,6 +1271,7 @@ int64_t rl_get_param(int key)
     case RL_PARAM_BATCH_CTAS: return g_params.batch_ctas;
     case RL_PARAM_TRI_LANES: return g_params.tri_lanes;
     case RL_PARAM_LOOKAHEAD: return g_params.lookahead;
+    case RL_PARAM_PANEL_CTAS: return (int64_t)g_params.panel_ctas64 | ((int64_t)g_params.panel_ctas32 << 16);
     default: return -1;
     }
 }

@@ -169,6 +169,135 @@ static void launch_gemm(Ctx &c, i64 m, i64 n, i64 k, T alpha, const T *A, i64 ld
 }
 
 // ----------------------------------------------------------------------------
+// Complex GEMM (complex double): 32 x 32 tiles, 256 threads as 16 x 16, each
+// thread a 2 x 2 block; TA / TB mean the CONJUGATE transpose; LOWER as above.
+// FP64-pipe bound (4 DFMA per complex multiply-add), so small tiles and many
+// CTAs.
+// ----------------------------------------------------------------------------
+constexpr int ZG_B = 32, ZG_K = 16;
+
+template <bool TA, bool TB, bool LOWER>
+__global__ void __launch_bounds__(256)
+k_zgemm(i64 m, i64 n, i64 k, cplx alpha, const cplx *__restrict__ A, i64 lda, const cplx *__restrict__ B,
+        i64 ldb, cplx beta, cplx *C, i64 ldc, const int32_t *abort, int tiles_m)
+{
+    if (abort && *abort != 0) return;
+    int tm, tn;
+    if (LOWER) {
+        long long t = blockIdx.x;
+        int r = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while ((long long)(r + 1) * (r + 2) / 2 <= t) ++r;
+        while ((long long)r * (r + 1) / 2 > t) --r;
+        tm = r;
+        tn = (int)(t - (long long)r * (r + 1) / 2);
+    } else {
+        tm = blockIdx.x % tiles_m;
+        tn = blockIdx.x / tiles_m;
+    }
+    const i64 i0 = (i64)tm * ZG_B, j0 = (i64)tn * ZG_B;
+    __shared__ cplx As[2][ZG_K][ZG_B + 1];
+    __shared__ cplx Bs[2][ZG_K][ZG_B + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    cplx acc[2][2];
+    cplx ra[2], rb[2];
+    auto load = [&](i64 k0) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int e = tid + 256 * r;                // 512 elements of each 32 x 16 tile
+            int il, pl;
+            if (!TA) { il = e & 31; pl = e >> 5; } else { pl = e & 15; il = e >> 4; }
+            const i64 gi = i0 + il, gp = k0 + pl;
+            cplx v(0.0);
+            if (gi < m && gp < k) v = TA ? conj(A[gi * lda + gp]) : A[gp * lda + gi];
+            ra[r] = v;
+            int jl, ql;
+            if (!TB) { ql = e & 15; jl = e >> 4; } else { jl = e & 31; ql = e >> 5; }
+            const i64 gj = j0 + jl, gq = k0 + ql;
+            cplx w(0.0);
+            if (gj < n && gq < k) w = TB ? conj(B[gq * ldb + gj]) : B[gj * ldb + gq];
+            rb[r] = w;
+        }
+    };
+    auto store = [&](int st) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int e = tid + 256 * r;
+            int il, pl;
+            if (!TA) { il = e & 31; pl = e >> 5; } else { pl = e & 15; il = e >> 4; }
+            As[st][pl][il] = ra[r];
+            int jl, ql;
+            if (!TB) { ql = e & 15; jl = e >> 4; } else { jl = e & 31; ql = e >> 5; }
+            Bs[st][ql][jl] = rb[r];
+        }
+    };
+    const i64 nk = (k + ZG_K - 1) / ZG_K;
+    if (nk > 0) {
+        load(0);
+        store(0);
+        __syncthreads();
+        for (i64 t = 0; t < nk; ++t) {
+            const int st = (int)(t & 1);
+            if (t + 1 < nk) load((t + 1) * ZG_K);
+#pragma unroll
+            for (int kk = 0; kk < ZG_K; ++kk) {
+                const cplx a0 = As[st][kk][tx], a1 = As[st][kk][tx + 16];
+                const cplx b0 = Bs[st][kk][ty], b1 = Bs[st][kk][ty + 16];
+                acc[0][0] = fma(a0, b0, acc[0][0]);
+                acc[0][1] = fma(a0, b1, acc[0][1]);
+                acc[1][0] = fma(a1, b0, acc[1][0]);
+                acc[1][1] = fma(a1, b1, acc[1][1]);
+            }
+            if (t + 1 < nk) store(st ^ 1);
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const i64 col = j0 + ty + 16 * j;
+        if (col >= n) continue;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const i64 row = i0 + tx + 16 * i;
+            if (row >= m) continue;
+            if (LOWER && row < col) continue;
+            cplx *cp = C + col * ldc + row;
+            const cplx cv = (beta == cplx(0.0)) ? cplx(0.0) : beta * (*cp);
+            *cp = fma(alpha, acc[i][j], cv);
+        }
+    }
+}
+
+template <bool TA, bool TB, bool LOWER>
+static void launch_zgemm(Ctx &c, i64 m, i64 n, i64 k, cplx alpha, const cplx *A, i64 lda, const cplx *B, i64 ldb,
+                         cplx beta, cplx *C, i64 ldc)
+{
+    const i64 tiles_m = (m + ZG_B - 1) / ZG_B, tiles_n = (n + ZG_B - 1) / ZG_B;
+    const i64 grid = LOWER ? tiles_m * (tiles_m + 1) / 2 : tiles_m * tiles_n;
+    const double flops = 4.0 * (LOWER ? (double)k * (double)n * (double)(n + 1) : 2.0 * m * n * k);
+    const double c_elems = LOWER ? (double)n * (double)(n + 1) / 2.0 : (double)m * (double)n;
+    const double bytes = 16.0 * ((LOWER ? (double)n * k : (double)m * k + (double)k * n) + 2.0 * c_elems);
+    Launch L(c, LOWER ? K_SYRK : K_GEMM, flops, bytes);
+    k_zgemm<TA, TB, LOWER><<<(unsigned)grid, 256, 0, c.s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, c.abort,
+                                                            (int)tiles_m);
+}
+
+static void zgemm(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, cplx alpha, const cplx *A, i64 lda,
+                  const cplx *B, i64 ldb, cplx beta, cplx *C, i64 ldc, bool lower)
+{
+    if (lower) {
+        if (!ta && tb) launch_zgemm<false, true, true>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+        else if (ta && !tb) launch_zgemm<true, false, true>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+        else if (!ta && !tb) launch_zgemm<false, false, true>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+        else launch_zgemm<true, true, true>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+        return;
+    }
+    if (!ta && !tb) launch_zgemm<false, false, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+    else if (!ta && tb) launch_zgemm<false, true, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+    else if (ta && !tb) launch_zgemm<true, false, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+    else launch_zgemm<true, true, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+// ----------------------------------------------------------------------------
 // FP32 SIMT GEMM with 128 x 128 CTA tiles (the FP32 updates of the precision
 // form).  FP32 FMAs issue 64x faster than FP64 ones, so the 64 x 64 tile
 // above becomes shared-memory bound; here each of the 256 threads owns an
@@ -335,11 +464,9 @@ static bool gemm_f32_wide(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, T alpha
 }
 
 template <typename T>
-void gemm(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, T alpha, const T *A, i64 lda,
-          const T *B, i64 ldb, T beta, T *C, i64 ldc, bool lower)
+static void gemm_real(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, T alpha, const T *A, i64 lda,
+                      const T *B, i64 ldb, T beta, T *C, i64 ldc, bool lower)
 {
-    if (m <= 0 || n <= 0) return;
-    if (k <= 0 && beta == T(1)) return;
     if (sizeof(T) == 4 && c.prec != RL_PREC_FP32 && beta == T(1) && m >= TC_MIN_MN && n >= TC_MIN_MN &&
         k >= TC_MIN_K) {
         if (tc_gemm(c, c.prec, ta, tb, m, n, k, (float)alpha, (const float *)A, lda, (const float *)B, ldb,
@@ -358,6 +485,18 @@ void gemm(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, T alpha, const T *A, i6
     else if (!ta && tb) launch_gemm<T, false, true, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     else if (ta && !tb) launch_gemm<T, true, false, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     else launch_gemm<T, true, true, false>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+template <typename T>
+void gemm(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, T alpha, const T *A, i64 lda,
+          const T *B, i64 ldb, T beta, T *C, i64 ldc, bool lower)
+{
+    if (m <= 0 || n <= 0) return;
+    if (k <= 0 && beta == T(1)) return;
+    if constexpr (is_cplx<T>::value)
+        zgemm(c, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, lower);
+    else
+        gemm_real<T>(c, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, lower);
 }
 
 // C(m x n) := beta C + alpha S Bm (left: S m x m) or alpha Bm S (right:
@@ -404,7 +543,7 @@ __device__ __forceinline__ int tri_ix(int i, int k) { return i * (i + 1) / 2 + k
 
 // Stage the order-n triangle of Tm (lower if !TRANS_UPPER, else the upper
 // triangle stored transposed) into P, padded with identity up to NB.
-template <typename T, int NB, bool TRANS_UPPER>
+template <typename T, int NB, bool TRANS_UPPER, bool CONJ = false>
 __device__ __forceinline__ void stage_tri(T *P, const T *Tm, i64 ldt, int n, bool unit)
 {
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
@@ -414,18 +553,18 @@ __device__ __forceinline__ void stage_tri(T *P, const T *Tm, i64 ldt, int n, boo
         if (i < n && k < n) v = TRANS_UPPER ? Tm[(i64)i * ldt + k] : Tm[(i64)k * ldt + i];
         else v = (i == k) ? T(1) : T(0);
         if (unit && i == k) v = T(1);
-        P[tri_ix(i, k)] = v;
+        P[tri_ix(i, k)] = CONJ ? cj(v) : v;
     }
 }
 
-template <typename T, int NB, int OP, bool ROWS, bool UNIT, bool TRANS_UPPER>
+template <typename T, int NB, int OP, bool ROWS, bool UNIT, bool TRANS_UPPER, bool CONJ = false>
 __global__ void __launch_bounds__(TRI_THREADS)
 k_tri(i64 nvec, int n, T alpha, const T *__restrict__ Tm, i64 ldt, T *B, i64 ldb,
       const int32_t *abort)
 {
     if (abort && *abort != 0) return;
     __shared__ T P[NB * (NB + 1) / 2];
-    stage_tri<T, NB, TRANS_UPPER>(P, Tm, ldt, n, UNIT);
+    stage_tri<T, NB, TRANS_UPPER, CONJ>(P, Tm, ldt, n, UNIT);
     __syncthreads();
     constexpr int E = NB / 4;
     const int q = threadIdx.x & 3;
@@ -597,28 +736,34 @@ static void launch_tri2(Ctx &c, i64 nvec, int n, T alpha, const T *Tm, i64 ldt, 
     }
 }
 
-template <typename T, int OP, bool ROWS, bool UNIT, bool TRANS_UPPER>
+// CONJ: stage the conjugated triangle (complex solves with L^H).
+template <typename T, int OP, bool ROWS, bool UNIT, bool TRANS_UPPER, bool CONJ = false>
 static void launch_tri(Ctx &c, int kind, i64 nvec, int n, T alpha, const T *Tm, i64 ldt, T *B,
                        i64 ldb)
 {
     if (nvec <= 0 || n <= 0) return;
     const unsigned grid = (unsigned)((nvec + TRI_VECS - 1) / TRI_VECS);
-    Launch L(c, kind, (double)nvec * n * n, 0.0);
-    // two lanes per vector halve the FP64 instructions but double each
-    // vector's dependent chain: they win only with many vectors in flight
-    const int lanes = g_params.tri_lanes ? g_params.tri_lanes : (nvec >= TRI2_MIN_VECS ? 2 : 4);
-    if (lanes == 2) {
-        if (n <= 16) launch_tri2<T, 16, OP, ROWS, UNIT, TRANS_UPPER>(c, nvec, n, alpha, Tm, ldt, B, ldb);
-        else if (n <= 32) launch_tri2<T, 32, OP, ROWS, UNIT, TRANS_UPPER>(c, nvec, n, alpha, Tm, ldt, B, ldb);
-        else launch_tri2<T, 64, OP, ROWS, UNIT, TRANS_UPPER>(c, nvec, n, alpha, Tm, ldt, B, ldb);
-        return;
+    Launch L(c, kind, (double)nvec * n * n * (is_cplx<T>::value ? 4.0 : 1.0), 0.0);
+    if constexpr (!is_cplx<T>::value) {
+        // two lanes per vector halve the FP64 instructions but double each
+        // vector's dependent chain: they win only with many vectors in flight
+        const int lanes = g_params.tri_lanes ? g_params.tri_lanes : (nvec >= TRI2_MIN_VECS ? 2 : 4);
+        if (lanes == 2) {
+            if (n <= 16) launch_tri2<T, 16, OP, ROWS, UNIT, TRANS_UPPER>(c, nvec, n, alpha, Tm, ldt, B, ldb);
+            else if (n <= 32) launch_tri2<T, 32, OP, ROWS, UNIT, TRANS_UPPER>(c, nvec, n, alpha, Tm, ldt, B, ldb);
+            else launch_tri2<T, 64, OP, ROWS, UNIT, TRANS_UPPER>(c, nvec, n, alpha, Tm, ldt, B, ldb);
+            return;
+        }
     }
     if (n <= 16)
-        k_tri<T, 16, OP, ROWS, UNIT, TRANS_UPPER><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, Tm, ldt, B, ldb, c.abort);
+        k_tri<T, 16, OP, ROWS, UNIT, TRANS_UPPER, CONJ><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, Tm, ldt, B, ldb,
+                                                                                     c.abort);
     else if (n <= 32)
-        k_tri<T, 32, OP, ROWS, UNIT, TRANS_UPPER><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, Tm, ldt, B, ldb, c.abort);
+        k_tri<T, 32, OP, ROWS, UNIT, TRANS_UPPER, CONJ><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, Tm, ldt, B, ldb,
+                                                                                     c.abort);
     else
-        k_tri<T, 64, OP, ROWS, UNIT, TRANS_UPPER><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, Tm, ldt, B, ldb, c.abort);
+        k_tri<T, 64, OP, ROWS, UNIT, TRANS_UPPER, CONJ><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, Tm, ldt, B, ldb,
+                                                                                     c.abort);
 }
 
 // ----------------------------------------------------------------------------
@@ -644,7 +789,8 @@ void trsm_rlt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
 {
     if (m <= 0 || n <= 0) return;
     if (n <= TRX_NB) {
-        launch_tri<T, TRI_FWD, true, false, false>(c, K_TRSM, m, (int)n, alpha, L, ldl, B, ldb);
+        // complex: B L^{-H}, each row solves conj(L) y = x
+        launch_tri<T, TRI_FWD, true, false, false, is_cplx<T>::value>(c, K_TRSM, m, (int)n, alpha, L, ldl, B, ldb);
         return;
     }
     const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
@@ -755,5 +901,10 @@ void trsm_run(Ctx &c, i64 m, i64 n, T alpha, const T *U, i64 ldu, T *B, i64 ldb)
 RL_INST_BLAS3(double)
 RL_INST_BLAS3(float)
 #undef RL_INST_BLAS3
+// complex double: the pieces of the Cholesky and LU recursions
+template void gemm<cplx>(Ctx &, bool, bool, i64, i64, i64, cplx, const cplx *, i64, const cplx *, i64, cplx,
+                         cplx *, i64, bool);
+template void trsm_lln<cplx>(Ctx &, bool, i64, i64, cplx, const cplx *, i64, cplx *, i64);
+template void trsm_rlt<cplx>(Ctx &, i64, i64, cplx, const cplx *, i64, cplx *, i64);
 
 }  // namespace rl

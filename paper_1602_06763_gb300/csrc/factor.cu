@@ -84,6 +84,65 @@ k_potf2(int n, T *A, i64 lda, int32_t *info, i64 info_off, const int32_t *abort)
     if (s_fail && threadIdx.x == 0) *info = (int32_t)(info_off + s_fail);
 }
 
+// Complex Hermitian potf2 (A = L L^H): the real form above with l_ij / l_jj
+// and the update a_ik -= l_ij conj(l_kj); the diagonal is real (its
+// imaginary part is ignored, as LAPACK's zpotf2 does).
+__global__ void __launch_bounds__(256)
+k_zpotf2(int n, cplx *A, i64 lda, int32_t *info, i64 info_off, const int32_t *abort)
+{
+    if (abort && *abort != 0) return;
+    extern __shared__ __align__(16) unsigned char zp_raw[];       // 66.6 KB: dynamic
+    auto S = reinterpret_cast<cplx (*)[BASE_N + 1]>(zp_raw);      // S[BASE_N][BASE_N + 1]
+    cplx *col = reinterpret_cast<cplx *>(zp_raw) + BASE_N * (BASE_N + 1);
+    __shared__ int s_fail;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (int j = ty; j < n; j += 16)
+        for (int i = j + tx; i < n; i += 16) S[i][j] = A[(i64)j * lda + i];
+    if (threadIdx.x == 0) s_fail = 0;
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        if (threadIdx.x < 32) {
+            const double d = S[j][j].x;
+            if (!(d > 0.0)) {
+                if (threadIdx.x == 0) { s_fail = j + 1; S[j][j] = cplx(d); }
+            } else {
+                const double ljj = sqrt(d);
+                for (int i = j + 1 + threadIdx.x; i < n; i += 32) {
+                    const cplx v = S[i][j] / cplx(ljj);
+                    col[i] = v;
+                    S[i][j] = v;
+                }
+                if (threadIdx.x == 0) S[j][j] = cplx(ljj);
+            }
+        }
+        __syncthreads();
+        if (s_fail) break;
+        for (int ii = j + 1 + ty; ii < n; ii += 16) {
+            const cplx lij = col[ii];
+            for (int kk = j + 1 + tx; kk <= ii; kk += 16) S[ii][kk] = fma(-lij, conj(col[kk]), S[ii][kk]);
+        }
+        __syncthreads();
+    }
+    for (int j = ty; j < n; j += 16)
+        for (int i = j + tx; i < n; i += 16) A[(i64)j * lda + i] = S[i][j];
+    if (s_fail && threadIdx.x == 0) *info = (int32_t)(info_off + s_fail);
+}
+
+template <>
+void potf2<cplx>(Ctx &c, i64 n, cplx *A, i64 lda, i64 info_off)
+{
+    if (n <= 0) return;
+    if (n > BASE_N) { note(c, cudaErrorInvalidValue); return; }
+    const size_t smem = (size_t)BASE_N * (BASE_N + 2) * sizeof(cplx);
+    static bool attr = false;
+    if (!attr) {
+        note(c, cudaFuncSetAttribute(k_zpotf2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    Launch L(c, K_POTF2, 4.0 * (double)n * n * n / 3.0, 0.0);
+    k_zpotf2<<<1, 256, smem, c.s>>>((int)n, A, lda, c.info, info_off, c.abort);
+}
+
 template <typename T>
 void potf2(Ctx &c, i64 n, T *A, i64 lda, i64 info_off)
 {
@@ -223,6 +282,8 @@ constexpr int PANEL_NBMAX = 64;
 constexpr int PANEL_THREADS = 256;
 constexpr int PANEL_RMIN = 64;
 constexpr size_t PANEL_SMEM_MAX = 200 * 1024;
+// widest panel per element type (a complex row of 32 fills an exchange record)
+template <typename T> constexpr int panel_nbmax() { return sizeof(T) == 16 ? PANEL_NBMAX / 2 : PANEL_NBMAX; }
 
 constexpr int PANEL_REC = 2 + PANEL_NBMAX;
 
@@ -285,6 +346,19 @@ __device__ __forceinline__ unsigned long long abs_key(T v)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong((double)v) & 0x7fffffffffffffffull;
     return b > 0x7ff0000000000000ull ? 0ull : b;
+}
+
+// |Re| + |Im| for complex pivots (LAPACK's izamax)
+__device__ __forceinline__ unsigned long long abs_key(cplx v) { return abs_key<double>(abs1(v)); }
+
+// Rows in the exchange area are doubles: one per real entry, two (re, im)
+// per complex entry.
+template <typename T> __device__ __forceinline__ void put_row(double *row, int c, T v) { row[c] = (double)v; }
+__device__ __forceinline__ void put_row(double *row, int c, cplx v) { row[2 * c] = v.x; row[2 * c + 1] = v.y; }
+template <typename T> __device__ __forceinline__ T get_row(const double *row, int c) { return (T)__ldcg(row + c); }
+template <> __device__ __forceinline__ cplx get_row<cplx>(const double *row, int c)
+{
+    return cplx(__ldcg(row + 2 * c), __ldcg(row + 2 * c + 1));
 }
 
 __device__ __forceinline__ bool kbetter(unsigned long long k, int i, unsigned long long bk, int bi)
@@ -356,11 +430,11 @@ k_panel(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, Pane
             }
             if (bi != PANEL_NONE) {
                 const T *src = S + (int)(bi - rbeg);
-                for (int c = lane; c < nb; c += 32) rec[2 + c] = (double)src[c * PANEL_THREADS];
+                for (int c = lane; c < nb; c += 32) put_row(rec + 2, c, src[c * PANEL_THREADS]);
             }
             if (j >= rbeg && j < rbeg + rows) {
                 const T *src = S + (int)(j - rbeg);
-                for (int c = lane; c < nb; c += 32) ws->rowj[buf][c] = (double)src[c * PANEL_THREADS];
+                for (int c = lane; c < nb; c += 32) put_row(ws->rowj[buf], c, src[c * PANEL_THREADS]);
             }
             __syncwarp();
             int ok = 1;
@@ -408,8 +482,8 @@ k_panel(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, Pane
                 const int p = (gw >= 0) ? ix : j;
                 const bool own_p = (p != j) && p >= rbeg && p < rbeg + rows;
                 for (int c = lane; c < nb; c += 32) {
-                    urow[c] = (T)((gw >= 0) ? __ldcg(&ws->rec[buf][gw][2 + c]) : __ldcg(&ws->rowj[buf][c]));
-                    if (own_p) rowj[c] = (T)__ldcg(&ws->rowj[buf][c]);
+                    urow[c] = (gw >= 0) ? get_row<T>(ws->rec[buf][gw] + 2, c) : get_row<T>(ws->rowj[buf], c);
+                    if (own_p) rowj[c] = get_row<T>(ws->rowj[buf], c);
                 }
                 if (lane == 0) s_p = p;
             }
@@ -525,8 +599,8 @@ k_panel_smem(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info,
         __syncthreads();
         {
             const int mine = s_p;
-            if (mine != PANEL_NONE && tid < nb) ws->rec[buf][g][2 + tid] = (double)S[tid * R + (int)(mine - rbeg)];
-            if (j >= rbeg && j < rbeg + rows && tid < nb) ws->rowj[buf][tid] = (double)S[tid * R + (int)(j - rbeg)];
+            if (mine != PANEL_NONE && tid < nb) put_row(ws->rec[buf][g] + 2, tid, S[tid * R + (int)(mine - rbeg)]);
+            if (j >= rbeg && j < rbeg + rows && tid < nb) put_row(ws->rowj[buf], tid, S[tid * R + (int)(j - rbeg)]);
         }
         if (!grid_barrier(&ws->counter, (unsigned)G * (unsigned)(j + 1), spin_ns)) {
             if (tid == 0) atomicExch(info, RL_INFO_DEVICE_TIMEOUT);
@@ -551,13 +625,13 @@ k_panel_smem(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info,
         __syncthreads();
         const i64 p = s_p;
         const int gw = s_gw;
-        if (tid < nb) urow[tid] = (T)((gw >= 0) ? __ldcg(&ws->rec[buf][gw][2 + tid]) : __ldcg(&ws->rowj[buf][tid]));
+        if (tid < nb) urow[tid] = (gw >= 0) ? get_row<T>(ws->rec[buf][gw] + 2, tid) : get_row<T>(ws->rowj[buf], tid);
         __syncthreads();
         const T piv = urow[j];
         if (g == 0 && tid == 0) ipiv[r0 + j] = (int32_t)(r0 + p + 1);
         if (p != j) {
             if (j >= rbeg && j < rbeg + rows && tid < nb) S[tid * R + (int)(j - rbeg)] = urow[tid];
-            if (p >= rbeg && p < rbeg + rows && tid < nb) S[tid * R + (int)(p - rbeg)] = (T)__ldcg(&ws->rowj[buf][tid]);
+            if (p >= rbeg && p < rbeg + rows && tid < nb) S[tid * R + (int)(p - rbeg)] = get_row<T>(ws->rowj[buf], tid);
         }
         __syncthreads();
         if (piv != T(0)) {
@@ -586,8 +660,12 @@ template <typename T>
 void getf2_panel(Ctx &c, i64 m, i64 nb, T *A, i64 lda, int32_t *ipiv, i64 r0)
 {
     if (m <= 0 || nb <= 0) return;
+    if (nb > panel_nbmax<T>()) { note(c, cudaErrorInvalidValue); return; }
     PanelWS *ws = reinterpret_cast<PanelWS *>(c.work);
-    const int gmax = c.num_sms < PANEL_GMAX ? c.num_sms : PANEL_GMAX;
+    // CTAs: one per SM, or fewer (more rows each, fewer arrivals per column)
+    int gmax = c.num_sms < PANEL_GMAX ? c.num_sms : PANEL_GMAX;
+    const int cap = sizeof(T) == 8 ? g_params.panel_ctas64 : g_params.panel_ctas32;
+    if (cap > 0 && cap < gmax) gmax = cap;
     i64 R = (m + gmax - 1) / gmax;
     if (R < PANEL_RMIN) R = PANEL_RMIN;
     if (R > m) R = m;
@@ -598,7 +676,7 @@ void getf2_panel(Ctx &c, i64 m, i64 nb, T *A, i64 lda, int32_t *ipiv, i64 r0)
     const int ti = sizeof(T) == 8 ? 0 : 1;
     if (!attr[ti]) {
         note(c, cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(PANEL_THREADS * PANEL_NBMAX * sizeof(T))));
+                                     (int)(PANEL_THREADS * panel_nbmax<T>() * sizeof(T))));
         note(c, cudaFuncSetAttribute(k_panel_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)PANEL_SMEM_MAX));
         attr[ti] = true;
@@ -742,6 +820,8 @@ void laswp(Ctx &c, T *A0, i64 lda, i64 m, i64 c0, i64 ncols, i64 k1, i64 k2, con
     template void laswp<T>(Ctx &, T *, i64, i64, i64, i64, i64, i64, const int32_t *);
 RL_INST_FACTOR(double)
 RL_INST_FACTOR(float)
+template void getf2_panel<cplx>(Ctx &, i64, i64, cplx *, i64, int32_t *, i64);
+template void laswp<cplx>(Ctx &, cplx *, i64, i64, i64, i64, i64, i64, const int32_t *);
 #undef RL_INST_FACTOR
 
 }  // namespace rl

@@ -11,6 +11,56 @@
 namespace rl {
 
 using i64 = int64_t;
+using ::fma;   // the real overloads stay visible beside the complex one below
+
+// Complex double, interleaved (re, im) as LAPACK's complex*16.  The
+// arithmetic is written out: a * b with 4 FMAs' worth of products, division
+// by Smith's method (R. L. Smith, "Algorithm 116: Complex division", CACM
+// 1962), and |Re| + |Im| as LAPACK's izamax measures a pivot.
+struct __align__(16) cplx {
+    double x, y;
+    __host__ __device__ constexpr cplx() : x(0.0), y(0.0) {}
+    __host__ __device__ constexpr cplx(double r) : x(r), y(0.0) {}
+    __host__ __device__ constexpr cplx(double r, double i) : x(r), y(i) {}
+};
+__host__ __device__ inline cplx operator+(cplx a, cplx b) { return cplx(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline cplx operator-(cplx a, cplx b) { return cplx(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline cplx operator-(cplx a) { return cplx(-a.x, -a.y); }
+__host__ __device__ inline cplx operator*(cplx a, cplx b)
+{
+    return cplx(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__host__ __device__ inline cplx operator/(cplx a, cplx b)
+{
+    if (fabs(b.x) >= fabs(b.y)) {
+        const double r = b.y / b.x, d = b.x + b.y * r;
+        return cplx((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    }
+    const double r = b.x / b.y, d = b.x * r + b.y;
+    return cplx((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+}
+__host__ __device__ inline bool operator==(cplx a, cplx b) { return a.x == b.x && a.y == b.y; }
+__host__ __device__ inline bool operator!=(cplx a, cplx b) { return !(a == b); }
+// c + a b
+__host__ __device__ inline cplx fma(cplx a, cplx b, cplx c)
+{
+    return cplx(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__host__ __device__ inline cplx conj(cplx a) { return cplx(a.x, -a.y); }
+__host__ __device__ inline double abs1(cplx a) { return fabs(a.x) + fabs(a.y); }
+// conjugate when the element type is complex (the "transpose" of the complex
+// routines is the conjugate transpose)
+template <typename T> __host__ __device__ inline T cj(T v) { return v; }
+template <> __host__ __device__ inline cplx cj<cplx>(cplx v) { return conj(v); }
+#ifdef __CUDACC__
+using ::__shfl_sync;   // the built-in overloads stay visible beside this one
+__device__ inline cplx __shfl_sync(unsigned mask, cplx v, int src)
+{
+    return cplx(::__shfl_sync(mask, v.x, src), ::__shfl_sync(mask, v.y, src));
+}
+#endif
+template <typename T> struct is_cplx { static constexpr bool value = false; };
+template <> struct is_cplx<cplx> { static constexpr bool value = true; };
 
 // Kernel-launch accounting (host side).
 extern std::atomic<uint64_t> g_launches;
@@ -26,6 +76,8 @@ struct Params {
     int batch_cfg[2][2] = {{0, 0}, {0, 0}};   // [double/float][potrf/getrf]: tuned kBatchCfgs index
     int tri_lanes = 0;       // lanes per vector of the triangle leaf kernels (0 = by size, 2, 4)
     int lookahead = 1;       // LU/Cholesky: trailing update split across the side stream (0 = off)
+    int panel_ctas64 = 0;    // LU panel CTAs, FP64 / FP32 (0 = one per SM)
+    int panel_ctas32 = 0;
 };
 extern Params g_params;
 
@@ -105,7 +157,7 @@ void symm(Ctx &c, bool left, i64 m, i64 n, T alpha, const T *S, i64 lds, const T
 // B(m x n) := alpha * L^{-1} B, L lower m x m (unit or not).
 template <typename T>
 void trsm_lln(Ctx &c, bool unit, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb);
-// B(m x n) := alpha * B L^{-T}, L lower n x n, non-unit.
+// B(m x n) := alpha * B L^{-T}, L lower n x n, non-unit (L^{-H} for complex).
 template <typename T>
 void trsm_rlt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb);
 // B(m x n) := alpha * L^{-T} B, L lower m x m, non-unit.

@@ -116,6 +116,47 @@ def expected_ipiv(perm):
     return ipiv
 
 
+def herm_spd(n: int, seed: int):
+    """Complex A = B B^H + n I with Re B, Im B iid N(0,1), mirrored so that A
+    is exactly Hermitian (real diagonal).  Complex128, column-major."""
+    r = rng(seed)
+    B = r.standard_normal((n, n)) + 1j * r.standard_normal((n, n))
+    G = B @ B.conj().T
+    A = np.tril(G, -1) + np.tril(G, -1).conj().T + np.diag(G.diagonal().real + n)
+    return np.asfortranarray(A, dtype=np.complex128)
+
+
+def complex_uniform(m: int, n: int, seed: int):
+    """Re and Im iid Uniform(-1, 1).  Complex128, column-major."""
+    r = rng(seed)
+    return np.asfortranarray(r.uniform(-1, 1, (m, n)) + 1j * r.uniform(-1, 1, (m, n)))
+
+
+def gaussian_int_chol(n: int, seed: int):
+    """Unit lower L with Gaussian-integer off-diagonal entries a + bi,
+    a, b in {-1, 0, 1}.  A = L L^H then has Gaussian-integer entries and its
+    Cholesky factor is L exactly (every square root is sqrt(1))."""
+    r = rng(seed)
+    L = np.tril(r.integers(-1, 2, size=(n, n)) + 1j * r.integers(-1, 2, size=(n, n)), -1) + np.eye(n)
+    return np.asfortranarray(L, dtype=np.complex128)
+
+
+def complex_dyadic_lu(n: int, seed: int):
+    """A = P^T L U with L unit lower, off-diagonal (a + bi)/4 (a, b in -1..1,
+    so |Re| + |Im| <= 1/2) and U upper with Gaussian-integer entries and a
+    diagonal in {+-1, +-2, +-i, +-2i}: partial pivoting on |Re| + |Im|
+    reproduces P, and every operation (divisions by U's diagonal included)
+    is exact.  Returns (A, L, U, perm) with A[perm[i], :] = (L U)[i, :]."""
+    r = rng(seed)
+    L = np.tril((r.integers(-1, 2, size=(n, n)) + 1j * r.integers(-1, 2, size=(n, n))) / 4.0, -1) + np.eye(n)
+    U = np.triu(r.integers(-3, 4, size=(n, n)) + 1j * r.integers(-3, 4, size=(n, n)), 1).astype(complex)
+    U[np.diag_indices(n)] = r.choice(np.array([1, -1, 2, -2, 1j, -1j, 2j, -2j]), size=n)
+    perm = r.permutation(n)
+    A = np.empty((n, n), dtype=complex)
+    A[perm, :] = L @ U
+    return np.asfortranarray(A), L, U, perm
+
+
 def integer_trtri(n: int, seed: int, factors=3):
     """A lower triangular L whose inverse is exact in binary64:
     L = D (I + N_1) (I + N_2) ... with N_k = a block below the diagonal (rows

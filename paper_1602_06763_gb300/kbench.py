@@ -36,12 +36,16 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--trace", action="store_true")
+    ap.add_argument("--panel-ctas", type=int, default=0, help="LU panel CTAs (RL_PARAM_PANEL_CTAS value)")
+    ap.add_argument("--fp32", action="store_true", help="panel/getrf cases: FP32 storage (rl_sgetrf)")
     ap.add_argument("--tri-lanes", type=int, default=0, help="lanes per vector of the triangle leaf kernels (2 or 4)")
     ap.add_argument("--flow", type=int, default=1, help="getrs/potrs: 1 = one-launch flow solve, 0 = recursive")
     a = ap.parse_args()
 
     if a.nb:
         r.check(r.rl_set_param(r.RL_PARAM_GETRF_PANEL, a.nb))
+    if a.panel_ctas:
+        r.check(r.rl_set_param(r.RL_PARAM_PANEL_CTAS, a.panel_ctas))
     if a.tri_lanes:
         r.check(r.rl_set_param(r.RL_PARAM_TRI_LANES, a.tri_lanes))
     if a.c:
@@ -163,6 +167,8 @@ def main():
             rows = m
             A0 = torch.rand(n if a.case == "getrf" else n, rows, generator=g, device=dev,
                             dtype=torch.float64) * 2 - 1
+            if a.fp32:
+                A0 = A0.to(torch.float32)
         A = A0.clone()
         restore = lambda: A.copy_(A0)
         if a.case == "potrf":
@@ -182,7 +188,8 @@ def main():
             work = torch.empty(lw, dtype=torch.uint8, device=dev)
             mn = min(rows, cols)
             flops = max(rows, cols) * mn * mn - mn ** 3 / 3.0   # LU of m x n, leading terms
-            run = lambda: r.check(r.rl_dgetrf(rows, cols, A, rows, ipiv, info, work, lw, s))
+            fn = r.rl_sgetrf if a.fp32 else r.rl_dgetrf
+            run = lambda: r.check(fn(rows, cols, A, rows, ipiv, info, work, lw, s))
 
     for _ in range(a.warmup):
         restore()

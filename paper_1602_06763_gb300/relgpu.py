@@ -58,6 +58,8 @@ _SIGS = {
                                 _i64, _vp]),
     "rl_trs_work_size": (ctypes.c_size_t, [_i64, _i64]),
     "rl_dlaswp": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _vp, _vp]),
+    "rl_zpotrf": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_zgetrf": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
     "rl_spotrf_tc_work_size": (ctypes.c_size_t, [_i64, ctypes.c_int]),
     "rl_sgetrf_tc_work_size": (ctypes.c_size_t, [_i64, _i64, ctypes.c_int]),
     "rl_spotrf_tc": (ctypes.c_int, [ctypes.c_int, _ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
@@ -131,6 +133,7 @@ RL_PARAM_SPIN_LIMIT_NS = 4
 RL_PARAM_BATCH_CTAS = 5
 RL_PARAM_TRI_LANES = 6
 RL_PARAM_LOOKAHEAD = 7
+RL_PARAM_PANEL_CTAS = 8
 
 
 def _ptr(x):
@@ -220,6 +223,14 @@ def rl_dtrsm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream=None)
 def rl_dtrmm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream=None):
     return _lib.rl_dtrmm(_c(side), _c(uplo), _c(transa), _c(diag), m, n, alpha, _ptr(A), lda,
                          _ptr(B), ldb, _stream(stream))
+
+
+def rl_zpotrf(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
+    return _lib.rl_zpotrf(_c(uplo), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_zgetrf(m, n, A, lda, ipiv, info, work, lwork, stream=None):
+    return _lib.rl_zgetrf(m, n, _ptr(A), lda, _ptr(ipiv), _ptr(info), _ptr(work), lwork, _stream(stream))
 
 
 def rl_spotrf_tc_work_size(n, prec):

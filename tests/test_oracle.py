@@ -648,62 +648,33 @@ def test_complex_closed_forms_2x2(oracle):
     assert abs(F[1, 1] - (2j - 4.0 / 3.0)) <= 4 * 2.0 ** -53 * 2.0
 
 
-def _gaussian_int_chol(n, seed):
-    r = np.random.default_rng(seed)
-    L = np.tril(r.integers(-1, 2, size=(n, n)) + 1j * r.integers(-1, 2, size=(n, n)), -1) + np.eye(n)
-    return np.asfortranarray(L)
-
-
 @pytest.mark.parametrize("n,c", [(5, 1), (60, 8), (130, 24)])
 def test_zpotrf_gaussian_integers_exact(oracle, n, c):
-    L = _gaussian_int_chol(n, inputs.seed_for(0, 1100 + n))
+    L = inputs.gaussian_int_chol(n, inputs.seed_for(0, 1100 + n))
     A = np.asfortranarray(L @ L.conj().T)
     X, info = oracle.zpotrf(A, c=c)
     assert info == 0
     assert np.array_equal(np.tril(X), L)
 
 
-def complex_dyadic_lu(n, seed):
-    """P^T L U with L unit lower, off-diagonal (a + bi)/4 (a, b in -1..1, so
-    |Re| + |Im| <= 1/2) and U upper with Gaussian-integer entries and a
-    diagonal in {+-1, +-2, +-i, +-2i}: partial pivoting on |Re| + |Im|
-    reproduces P, and every operation (divisions by U's diagonal included)
-    is exact."""
-    r = np.random.default_rng(seed)
-    L = np.tril((r.integers(-1, 2, size=(n, n)) + 1j * r.integers(-1, 2, size=(n, n))) / 4.0, -1) + np.eye(n)
-    U = np.triu(r.integers(-3, 4, size=(n, n)) + 1j * r.integers(-3, 4, size=(n, n)), 1).astype(complex)
-    U[np.diag_indices(n)] = r.choice([1, -1, 2, -2, 1j, -1j, 2j, -2j], size=n)
-    perm = r.permutation(n)
-    A = np.empty((n, n), dtype=complex)
-    A[perm, :] = L @ U
-    return np.asfortranarray(A), L, U, perm
-
-
 @pytest.mark.parametrize("n,c", [(6, 1), (70, 8), (150, 24)])
 def test_zgetrf_dyadic_exact(oracle, n, c):
-    A, L, U, perm = complex_dyadic_lu(n, inputs.seed_for(0, 1200 + n))
+    A, L, U, perm = inputs.complex_dyadic_lu(n, inputs.seed_for(0, 1200 + n))
     F, ipiv, info = oracle.zgetrf(A, c=c)
     assert info == 0
     assert np.array_equal(ipiv, inputs.expected_ipiv(perm))
     assert np.array_equal(np.tril(F, -1) + np.eye(n), L) and np.array_equal(np.triu(F), U)
 
 
-def _herm_spd(n, seed):
-    r = np.random.default_rng(seed)
-    B = r.standard_normal((n, n)) + 1j * r.standard_normal((n, n))
-    return np.asfortranarray(B @ B.conj().T + n * np.eye(n))
-
-
 @pytest.mark.parametrize("n", [1, 2, 17, 100, 257])
 def test_zpotrf_zgetrf_vs_lapack(oracle, n):
-    A = _herm_spd(n, inputs.seed_for(0, 1300 + n))
+    A = inputs.herm_spd(n, inputs.seed_for(0, 1300 + n))
     L, info = oracle.zpotrf(A, c=24)
     ref, info_l = lapack.zpotrf(A, lower=1)
     assert info == info_l == 0
     assert np.max(np.abs(np.tril(L) - np.tril(ref))) <= 64 * n * 2.0 ** -53 * np.max(np.abs(ref))
     assert oracle.res_zchol(A, np.tril(L)) <= 10.0
-    r = np.random.default_rng(inputs.seed_for(0, 1400 + n))
-    G = np.asfortranarray(r.uniform(-1, 1, (n, n)) + 1j * r.uniform(-1, 1, (n, n)))
+    G = inputs.complex_uniform(n, n, inputs.seed_for(0, 1400 + n))
     F, ipiv, info = oracle.zgetrf(G, c=24)
     lu, piv, info_l = lapack.zgetrf(G)
     assert info == info_l == 0
@@ -746,7 +717,7 @@ def test_zgetrf_brute_force_gaussian_rationals(oracle, n):
 
 def test_complex_planted_mistakes_are_caught(oracle):
     n = 80
-    A = _herm_spd(n, inputs.seed_for(0, 1600))
+    A = inputs.herm_spd(n, inputs.seed_for(0, 1600))
     L, _ = oracle.zpotrf(A, c=24)
     L = np.tril(L)
     assert oracle.res_zchol(A, L) <= 10.0
@@ -754,8 +725,7 @@ def test_complex_planted_mistakes_are_caught(oracle):
     bad = L.copy(order="F")
     bad[40, 5] = -bad[40, 5]
     assert oracle.res_zchol(A, bad) > 1e3
-    r = np.random.default_rng(inputs.seed_for(0, 1601))
-    G = np.asfortranarray(r.uniform(-1, 1, (n, n)) + 1j * r.uniform(-1, 1, (n, n)))
+    G = inputs.complex_uniform(n, n, inputs.seed_for(0, 1601))
     F, ipiv, _ = oracle.zgetrf(G, c=24)
     assert oracle.res_zlu(G, F, ipiv) <= 10.0
     p2 = ipiv.copy()
