@@ -24,7 +24,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", required=True,
                     choices=["dgemm", "dsyrk", "dtrsm", "potrf", "getrf", "trtri", "lauum", "panel",
-                             "sgemm_tc", "dsgesv", "dsposv", "getrs", "potrs", "sgetrs", "sgemm", "laswp"])
+                             "sgemm_tc", "dsgesv", "dsposv", "getrs", "potrs", "sgetrs", "sgemm", "laswp",
+                             "zpotrf", "zgetrf"])
     ap.add_argument("--prec", type=int, default=1, help="operand precision (rl_prec) of sgemm_tc / dsgesv")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--cond", type=float, default=1e6)
@@ -147,6 +148,26 @@ def main():
             flops = 1.0 * k * n * (n + 1)
             run = lambda: r.check(r.rl_dsyrk("L", "N", n, k, -1.0, A, n, 1.0, C, n, s))
         restore = lambda: None
+    elif a.case in ("zpotrf", "zgetrf"):
+        # complex double; real flops: 4/3 n^3 (Cholesky), 8/3 n^3 (LU)
+        X = torch.complex(torch.rand(n, n, generator=g, device=dev, dtype=torch.float64) - 0.5,
+                          torch.rand(n, n, generator=g, device=dev, dtype=torch.float64) - 0.5)
+        if a.case == "zpotrf":
+            Z0 = X @ X.conj().T
+            Z0.diagonal().add_(float(n))
+            Z0 = Z0.transpose(0, 1).contiguous()       # column-major Hermitian: the conjugate
+            flops = 4.0 * n ** 3 / 3.0
+            Z = Z0.clone()
+            run = lambda: r.check(r.rl_zpotrf("L", n, Z, n, info, None, 0, s))
+        else:
+            Z0 = X
+            ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+            lw = r.rl_dgetrf_work_size(n, n)
+            work = torch.empty(lw, dtype=torch.uint8, device=dev)
+            flops = 8.0 * n ** 3 / 3.0
+            Z = Z0.clone()
+            run = lambda: r.check(r.rl_zgetrf(n, n, Z, n, ipiv, info, work, lw, s))
+        restore = lambda: Z.copy_(Z0)
     elif a.case == "dtrsm":
         # B (m x n) := B L^{-T}, the TRSM of the Cholesky recursion
         L = torch.rand(n, n, generator=g, device=dev, dtype=torch.float64)
