@@ -36,7 +36,16 @@
  *      RL_INFO_DEVICE_TIMEOUT  a bounded device-side wait (the grid barrier
  *                     of the LU panel kernel) ran out; outputs are invalid.
  *  - 1-based ipiv (int32): row i was interchanged with row ipiv[i]-1.
- *  - Only uplo = 'L' is built; 'U' returns RL_ERR_UNSUPPORTED.
+ *  - uplo 'L' and 'U' (Section 5: LAPACK's interface).  'U' is the lower
+ *    form of the transposed storage (A = U^T U with U = L^T; for complex
+ *    A = U^H U with U = L^H): the call swaps A's two triangles in place
+ *    (conjugating for complex), runs the lower recursion and swaps back, so
+ *    the upper triangle receives the upper result and the strictly lower
+ *    triangle comes back unchanged.  Inputs declared const that are
+ *    transposed this way (B of rl_[ds]sygst, A of rl_[ds]potrs) are
+ *    restored before the call's last kernel ends: they must be writable and
+ *    must not be read by other streams while the call runs.  The BLAS-3
+ *    layer (rl_dsyrk, rl_dtrsm, rl_dtrmm) keeps the subsets listed there.
  */
 #ifndef RELGPU_H
 #define RELGPU_H
@@ -56,7 +65,7 @@ enum {
     RL_SUCCESS = 0,
     RL_ERR_CUDA = 1,          /* a CUDA runtime call or launch failed */
     RL_ERR_WORKSPACE = 2,     /* work is NULL or lwork is below the query */
-    RL_ERR_UNSUPPORTED = 3,   /* uplo 'U', or a size beyond a kernel limit */
+    RL_ERR_UNSUPPORTED = 3,   /* an option or a size beyond a kernel limit */
     RL_ERR_NULL_POINTER = 4,  /* info (or ipiv) is NULL */
     RL_ERR_PARAM = 5          /* rl_set_param: unknown key or bad value */
 };
@@ -130,7 +139,7 @@ int rl_dpotri(char uplo, int64_t n, double *A, int64_t lda, int32_t *info,
  * building blocks of xgesv and xposv).  B (n x nrhs) is overwritten by X.
  *   rl_dgetrs: trans 'N' only; A and ipiv from rl_dgetrf: X = U^{-1} L^{-1} P B.
  *     Argument numbers: 1 trans, 2 n, 3 nrhs, 4 A, 5 lda, 6 ipiv, 7 B, 8 ldb.
- *   rl_dpotrs: uplo 'L' only; A from rl_dpotrf: X = L^{-T} L^{-1} B.
+ *   rl_dpotrs: A from rl_dpotrf: X = L^{-T} L^{-1} B ('L') or U^{-1} U^{-T} B ('U').
  *     Argument numbers: 1 uplo, 2 n, 3 nrhs, 4 A, 5 lda, 6 B, 7 ldb.
  * work (device, caller-owned, optional): with work == NULL both triangles
  *   are solved by the recursive TRSM (Section 3's halving on the triangle).
@@ -186,9 +195,10 @@ int rl_sgetri(int64_t n, float *A, int64_t lda, const int32_t *ipiv, int32_t *in
  * (lower, from rl_dpotrf) in B:
  *   itype 1:    A := L^{-1} A L^{-T}      (A x = lambda B x)
  *   itype 2, 3: A := L^T A L              (A B x = lambda x, B A x = lambda x)
- * uplo 'L' only ('U' returns RL_ERR_UNSUPPORTED): the lower triangles of A
- * and B are read, the lower triangle of A is overwritten, the strictly upper
- * triangles are not referenced.  Recursive by halving (Section 3).
+ * uplo 'L': the lower triangles of A and B are read, the lower triangle of
+ * A is overwritten, the strictly upper triangles are not referenced.  uplo
+ * 'U' (B = U^T U): A := U^{-T} A U^{-1} (itype 1) or U A U^T (2, 3) on the
+ * upper triangles.  Recursive by halving (Section 3).
  * work (device, optional): rl_dsygst_work_size(n) bytes, about n/2 x n/2
  *   doubles, the paper's temporary buffer that saves one symmetric product
  *   per recursion level (Section 5, xsygst user note); with work == NULL the

@@ -292,11 +292,13 @@ int rl_dpotrf(char uplo, int64_t n, double *A, int64_t lda, int32_t *info, void 
     if (n > 0 && A == nullptr) return -3;
     if (lda < (n > 1 ? n : 1)) return -4;
     if (info == nullptr) return RL_ERR_NULL_POINTER;
-    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
     Ctx c = make_ctx(stream, info, work, lwork);
     c.abort = info;
     note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    const bool up = is_u(uplo);
+    if (up) uplo_swap<double>(c, n, A, lda);
     potrf_rec(c, n, A, lda, 0);
+    if (up) uplo_swap<double>(c, n, A, lda);
     return finish(c);
 }
 
@@ -336,12 +338,14 @@ static int trtri_api(char uplo, char diag, int64_t n, T *A, int64_t lda, int32_t
     if (n > 0 && A == nullptr) return -4;
     if (lda < (n > 1 ? n : 1)) return -5;
     if (info == nullptr) return RL_ERR_NULL_POINTER;
-    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
     Ctx c = make_ctx(stream, info, work, lwork);
     c.abort = info;
     note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    const bool up = is_u(uplo);
+    if (up) uplo_swap<T>(c, n, A, lda);
     if (!unit) diag_zero_scan<T>(c, n, A, lda);
     trtri_rec<T>(c, unit, n, A, lda);
+    if (up) uplo_swap<T>(c, n, A, lda);
     return finish(c);
 }
 
@@ -355,15 +359,17 @@ static int lauum_api(bool potri, char uplo, int64_t n, T *A, int64_t lda, int32_
     if (n > 0 && A == nullptr) return -3;
     if (lda < (n > 1 ? n : 1)) return -4;
     if (info == nullptr) return RL_ERR_NULL_POINTER;
-    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
     Ctx c = make_ctx(stream, info, work, lwork);
     c.abort = info;
     note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    const bool up = is_u(uplo);
+    if (up) uplo_swap<T>(c, n, A, lda);
     if (potri) {
         diag_zero_scan<T>(c, n, A, lda);
         trtri_rec<T>(c, false, n, A, lda);
     }
     lauum_rec<T>(c, n, A, lda);
+    if (up) uplo_swap<T>(c, n, A, lda);
     return finish(c);
 }
 
@@ -533,11 +539,14 @@ int rl_zpotrf(char uplo, int64_t n, rl_double_complex *A, int64_t lda, int32_t *
     if (n > 0 && A == nullptr) return -3;
     if (lda < (n > 1 ? n : 1)) return -4;
     if (info == nullptr) return RL_ERR_NULL_POINTER;
-    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
     Ctx c = make_ctx(stream, info, work, lwork);
     c.abort = info;
     note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
-    potrf_rec_t<cplx>(c, n, reinterpret_cast<cplx *>(A), lda, 0);
+    cplx *Z = reinterpret_cast<cplx *>(A);
+    const bool up = is_u(uplo);
+    if (up) uplo_swap<cplx>(c, n, Z, lda);      // conjugate transposition: A = U^H U, U = L^H
+    potrf_rec_t<cplx>(c, n, Z, lda, 0);
+    if (up) uplo_swap<cplx>(c, n, Z, lda);
     return finish(c);
 }
 
@@ -595,7 +604,7 @@ int rl_spotrf_tc(int prec, char uplo, int64_t n, float *A, int64_t lda, int32_t 
     if (lda < (n > 1 ? n : 1)) return -5;
     if (info == nullptr) return RL_ERR_NULL_POINTER;
     const size_t need = rl_spotrf_tc_work_size(n, prec);
-    if (need == 0 || is_u(uplo)) return RL_ERR_UNSUPPORTED;
+    if (need == 0) return RL_ERR_UNSUPPORTED;
     if (work == nullptr || lwork < need) return RL_ERR_WORKSPACE;
     Ctx c = make_ctx(stream, info, nullptr, 0);
     c.abort = info;
@@ -603,7 +612,10 @@ int rl_spotrf_tc(int prec, char uplo, int64_t n, float *A, int64_t lda, int32_t 
     c.tcwork = work;
     c.tclwork = lwork;
     note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    const bool up = is_u(uplo);
+    if (up) uplo_swap<float>(c, n, A, lda);
     potrf_rec_t<float>(c, n, A, lda, 0);
+    if (up) uplo_swap<float>(c, n, A, lda);
     return finish(c);
 }
 
@@ -638,11 +650,13 @@ int rl_spotrf(char uplo, int64_t n, float *A, int64_t lda, int32_t *info, void *
     if (n > 0 && A == nullptr) return -3;
     if (lda < (n > 1 ? n : 1)) return -4;
     if (info == nullptr) return RL_ERR_NULL_POINTER;
-    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
     Ctx c = make_ctx(stream, info, work, lwork);
     c.abort = info;
     note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    const bool up = is_u(uplo);
+    if (up) uplo_swap<float>(c, n, A, lda);
     potrf_rec_t<float>(c, n, A, lda, 0);
+    if (up) uplo_swap<float>(c, n, A, lda);
     return finish(c);
 }
 
@@ -707,13 +721,17 @@ int rl_sgemm_tc(int prec, char transa, char transb, int64_t m, int64_t n, int64_
 // solve; otherwise the recursive TRSM.
 template <typename T>
 static int trs_t(bool lu, int64_t n, int64_t nrhs, const T *A, int64_t lda, const int32_t *ipiv, T *B,
-                 int64_t ldb, void *work, size_t lwork, rl_stream_t stream)
+                 int64_t ldb, void *work, size_t lwork, rl_stream_t stream, bool up = false)
 {
     if (n == 0 || nrhs == 0) return RL_SUCCESS;
     if (A == nullptr || B == nullptr || (lu && ipiv == nullptr)) return RL_ERR_NULL_POINTER;
     const bool flow = work != nullptr && nrhs <= FLOW_MAX_NRHS;
     if (flow && lwork < flow_ws_bytes(n, nrhs)) return RL_ERR_WORKSPACE;
     Ctx c = make_ctx(stream, nullptr, work, lwork);
+    // 'U' (Cholesky only): the factor U is transposed in place to L = U^T for
+    // the solves and restored before the call returns
+    T *Aw = const_cast<T *>(A);
+    if (up) uplo_swap<T>(c, n, Aw, lda);
     if (lu) laswp<T>(c, B, ldb, n, 0, nrhs, 0, n, ipiv);
     if (flow) {
         note(c, cudaMemsetAsync(work, 0, sizeof(int32_t), c.s));
@@ -726,6 +744,7 @@ static int trs_t(bool lu, int64_t n, int64_t nrhs, const T *A, int64_t lda, cons
         trsm_lln<T>(c, false, n, nrhs, T(1), A, lda, B, ldb);
         trsm_llt<T>(c, n, nrhs, T(1), A, lda, B, ldb);
     }
+    if (up) uplo_swap<T>(c, n, Aw, lda);
     return finish(c);
 }
 
@@ -777,11 +796,14 @@ static int sygst_api(int itype, char uplo, int64_t n, T *A, int64_t lda, const T
     if (lda < imax1(n)) return -5;
     if (n > 0 && B == nullptr) return -6;
     if (ldb < imax1(n)) return -7;
-    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
     if (n == 0) return RL_SUCCESS;
     if (work != nullptr && lwork < sygst_work_bytes(n, sizeof(T))) return RL_ERR_WORKSPACE;
     Ctx c = make_ctx(stream, nullptr, work, lwork);
+    const bool up = is_u(uplo);
+    T *Bw = const_cast<T *>(B);      // 'U': B is transposed in place and restored before the call returns
+    if (up) { uplo_swap<T>(c, n, A, lda); uplo_swap<T>(c, n, Bw, ldb); }
     sygst_rec<T>(c, itype, n, A, lda, B, ldb, static_cast<T *>(work));
+    if (up) { uplo_swap<T>(c, n, A, lda); uplo_swap<T>(c, n, Bw, ldb); }
     return finish(c);
 }
 
@@ -844,8 +866,7 @@ int rl_dpotrs(char uplo, int64_t n, int64_t nrhs, const double *A, int64_t lda, 
     if (nrhs < 0) return -3;
     if (lda < imax1(n)) return -5;
     if (ldb < imax1(n)) return -7;
-    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
-    return trs_t<double>(false, n, nrhs, A, lda, nullptr, B, ldb, work, lwork, stream);
+    return trs_t<double>(false, n, nrhs, A, lda, nullptr, B, ldb, work, lwork, stream, is_u(uplo));
 }
 
 int rl_sgetrs(char trans, int64_t n, int64_t nrhs, const float *A, int64_t lda, const int32_t *ipiv,
@@ -868,8 +889,7 @@ int rl_spotrs(char uplo, int64_t n, int64_t nrhs, const float *A, int64_t lda, f
     if (nrhs < 0) return -3;
     if (lda < imax1(n)) return -5;
     if (ldb < imax1(n)) return -7;
-    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
-    return trs_t<float>(false, n, nrhs, A, lda, nullptr, B, ldb, work, lwork, stream);
+    return trs_t<float>(false, n, nrhs, A, lda, nullptr, B, ldb, work, lwork, stream, is_u(uplo));
 }
 
 // ---- precision form ------------------------------------------------------------
@@ -920,7 +940,6 @@ int rl_dsposv(char uplo, int64_t n, int64_t nrhs, double *A, int64_t lda, const 
     if (lda < imax1(n)) return -5;
     if (ldb < imax1(n)) return -7;
     if (ldx < imax1(n)) return -9;
-    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
     if (!prec_ok(prec)) return RL_ERR_UNSUPPORTED;
     if (nrhs > 512) return RL_ERR_UNSUPPORTED;
     if (info == nullptr || iter == nullptr) return RL_ERR_NULL_POINTER;
@@ -930,7 +949,10 @@ int rl_dsposv(char uplo, int64_t n, int64_t nrhs, double *A, int64_t lda, const 
     note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
     note(c, cudaMemsetAsync(iter, 0, sizeof(int32_t), c.s));
     if (n == 0 || nrhs == 0) return finish(c);
+    const bool up = is_u(uplo);
+    if (up) uplo_swap<double>(c, n, A, lda);
     mixed_solve(c, false, n, nrhs, A, lda, nullptr, B, ldb, X, ldx, prec, tol, maxiter, iter);
+    if (up) uplo_swap<double>(c, n, A, lda);
     return finish(c);
 }
 
@@ -947,14 +969,16 @@ static int potrf_vb(char uplo, int64_t batch, const int32_t *n, T *const *A, con
 {
     if (!is_l(uplo) && !is_u(uplo)) return -1;
     if (batch < 0) return -2;
-    if (is_u(uplo)) return RL_ERR_UNSUPPORTED;
     if (max_n > BATCH_MAX_N || batch > INT32_MAX) return RL_ERR_UNSUPPORTED;
     if (batch == 0) return RL_SUCCESS;
     if (n == nullptr || A == nullptr || lda == nullptr || info == nullptr) return RL_ERR_NULL_POINTER;
     if (work == nullptr || lwork < batched_work_size(batch)) return RL_ERR_WORKSPACE;
     Ctx c = make_ctx(stream, nullptr, work, lwork);
+    const bool up = is_u(uplo);
+    if (up) uplo_swap_vbatched<T>(c, batch, n, A, lda, max_n);
     batched_factor<T>(c, false, batch, n, A, lda, nullptr, info, g_params.batch_cfg[sizeof(T) == 8 ? 0 : 1][0],
                       g_params.batch_ctas);
+    if (up) uplo_swap_vbatched<T>(c, batch, n, A, lda, max_n);
     return finish(c);
 }
 
@@ -1285,7 +1309,7 @@ const char *rl_status_string(int status)
     case RL_SUCCESS: return "success";
     case RL_ERR_CUDA: return "CUDA runtime or launch error";
     case RL_ERR_WORKSPACE: return "workspace missing or smaller than the size query";
-    case RL_ERR_UNSUPPORTED: return "unsupported option or size (only uplo='L' is built)";
+    case RL_ERR_UNSUPPORTED: return "unsupported option or size";
     case RL_ERR_NULL_POINTER: return "info or ipiv pointer is NULL";
     case RL_ERR_PARAM: return "unknown parameter key or value out of range";
     default: return "unknown status";

@@ -104,7 +104,7 @@ void note(Ctx &c, cudaError_t e);
 // Kernel kinds, in the order rl_trace_read reports them.
 enum Kind {
     K_GEMM = 0, K_SYRK, K_TRSM, K_TRMM, K_POTF2, K_TRTI2, K_LAUU2, K_DIAG,
-    K_PANEL, K_LASWP, K_RESID, K_CONVERT, K_MIX, K_BATCH, K_FLOW, K_COUNT
+    K_PANEL, K_LASWP, K_RESID, K_CONVERT, K_MIX, K_BATCH, K_FLOW, K_TRANS, K_COUNT
 };
 extern std::atomic<int> g_trace_on;
 // Bracket one kernel launch: with tracing on, CUDA events are recorded on the
@@ -261,6 +261,13 @@ void getri(Ctx &c, i64 n, T *A, i64 lda, const int32_t *ipiv, void *work);
 size_t sygst_work_bytes(i64 n, size_t esz);
 template <typename E>
 void sygst_rec(Ctx &c, int itype, i64 n, E *A, i64 lda, const E *L, i64 ldl, E *T);
+
+// uplo = 'U' by transposition (uplo.cu): swap A(i, j) <-> A(j, i) for i != j
+// (conjugated for complex), in place; never reads the abort flag.
+template <typename T>
+void uplo_swap(Ctx &c, i64 n, T *A, i64 lda);
+template <typename T>
+void uplo_swap_vbatched(Ctx &c, i64 batch, const int32_t *n, T *const *A, const int32_t *lda, int max_n);
 
 // ---- precision form (mixed.cu) ----------------------------------------------
 size_t mixed_work_size(i64 n, i64 nrhs, bool lu, int prec);

@@ -32,7 +32,7 @@ Totals g_tot[K_COUNT];
 const char *kKindNames[K_COUNT] = {"gemm", "syrk", "trsm_base", "trmm_base", "potf2",
                                    "trti2", "lauu2", "diag_scan", "getf2_panel", "laswp",
                                    "fp64_residual", "convert", "refine_control", "batched",
-                                   "trsm_flow"};
+                                   "trsm_flow", "uplo_swap"};
 
 cudaEvent_t take_event()
 {

@@ -52,7 +52,7 @@ def test_host_logic_without_gpu(built):
     assert r.rl_dtrtri("L", "N", 3, 8, 2, 8, None, 0, 0) == -5
     assert r.rl_dlauum("Q", 3, 8, 3, 8, None, 0, 0) == -1
     assert r.rl_dpotri("L", 3, 8, 3, 0, None, 0, 0) == r.RL_ERR_NULL_POINTER
-    assert r.rl_dpotrf("U", 3, 8, 3, 8, None, 0, 0) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_dpotrf("U", 3, 8, 2, 8, None, 0, 0) == -4      # 'U' accepted; lda checked
     assert r.rl_dgetrf_work_size(16384, 16384) > 0
     assert r.rl_host_work_size("dpotrf", 10, 10, 12) >= 10 * 12 * 8
     assert r.rl_host_work_size("nope", 10, 10, 10) == 0
@@ -80,12 +80,12 @@ def test_host_logic_of_the_other_routines(built):
     assert r.rl_dsygst(1, "Q", 4, 8, 4, 8, 4, stream=0) == -2
     assert r.rl_dsygst(1, "L", -1, 8, 4, 8, 4, stream=0) == -3
     assert r.rl_dsygst(1, "L", 4, 8, 3, 8, 4, stream=0) == -5
-    assert r.rl_dsygst(2, "U", 4, 8, 4, 8, 4, stream=0) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_dsygst(2, "U", 4, 8, 4, 8, 3, stream=0) == -7
     assert r.rl_dgetri(-1, 8, 1, 8, 8, None, 0, stream=0) == -1
     assert r.rl_dgetri(4, 8, 3, 8, 8, None, 0, stream=0) == -3
     assert r.rl_dgetri(4, 8, 4, 8, None, None, 0, stream=0) == r.RL_ERR_NULL_POINTER
     assert r.rl_strtri("L", "X", 4, 8, 4, 8, stream=0) == -2
-    assert r.rl_slauum("U", 4, 8, 4, 8, stream=0) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_slauum("U", 4, 8, 3, 8, stream=0) == -4
     assert r.rl_spotri("L", 4, 8, 3, 8, stream=0) == -4
     assert r.rl_sgemm("X", "N", 4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, stream=0) == -1
     assert r.rl_ssyrk("U", "N", 4, 4, 1.0, 8, 4, 0.0, 8, 4, stream=0) == r.RL_ERR_UNSUPPORTED

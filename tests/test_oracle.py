@@ -731,3 +731,42 @@ def test_complex_planted_mistakes_are_caught(oracle):
     p2 = ipiv.copy()
     p2[10] = p2[10] + 1 if p2[10] < n else p2[10] - 1
     assert oracle.res_zlu(G, F, p2) > 1e3
+
+
+# ----------------------------------------------------------------------------
+# uplo = 'U': each upper form is the lower form of the transposed storage
+# (A = U^T U with U = L^T).  The GPU path computes the upper forms that way;
+# here the identity itself is pinned against LAPACK's own upper routines.
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 5, 100, 257])
+def test_upper_forms_are_the_transposed_lower_forms(oracle, n):
+    tol = 64 * n * 2.0 ** -53
+    A = inputs.spd_bbt(n, seed=inputs.seed_for(0, 1700 + n))
+    L, info = oracle.potrf(np.asfortranarray(A.T))
+    U = np.triu(np.tril(L).T)
+    ref, info_l = lapack.dpotrf(A, lower=0)
+    assert info == info_l == 0
+    assert np.max(np.abs(U - np.triu(ref))) <= tol * np.max(np.abs(ref))
+    for unit in (False, True):
+        X, _ = oracle.trtri(np.asfortranarray(np.tril(U.T)), unit=unit)
+        ref, _ = lapack.dtrtri(U, lower=0, unitdiag=int(unit))
+        k = 1 if unit else 0                       # a unit diagonal is not referenced
+        ref = np.triu(ref, k)
+        assert np.max(np.abs(np.triu(np.tril(X).T, k) - ref), initial=0.0) <= tol * 8 * max(1.0, np.max(np.abs(ref), initial=0.0))
+    P = oracle.lauum(np.asfortranarray(np.tril(U.T)))
+    ref, _ = lapack.dlauum(U, lower=0)
+    assert np.max(np.abs(np.triu(np.tril(P).T) - np.triu(ref))) <= tol * np.max(np.abs(ref))
+    Q, _ = oracle.potri(np.asfortranarray(np.tril(U.T)))
+    ref, _ = lapack.dpotri(U, lower=0)
+    assert np.max(np.abs(np.triu(np.tril(Q).T) - np.triu(ref))) <= tol * 8 * np.max(np.abs(ref))
+    M = inputs.spd_bbt(n, seed=inputs.seed_for(0, 1710 + n))
+    for itype in (1, 2):
+        S = oracle.sygst(itype, np.asfortranarray(M.T), np.asfortranarray(np.tril(U.T)))
+        ref, _ = lapack.dsygst(M, U, itype=itype, lower=0)
+        assert np.max(np.abs(np.triu(np.tril(S).T) - np.triu(ref))) <= tol * 8 * np.max(np.abs(ref))
+    H = inputs.herm_spd(n, inputs.seed_for(0, 1720 + n))
+    Lz, info = oracle.zpotrf(np.asfortranarray(H.conj().T))
+    ref, info_l = lapack.zpotrf(H, lower=0)
+    assert info == info_l == 0
+    assert np.max(np.abs(np.triu(np.tril(Lz).conj().T) - np.triu(ref))) <= tol * np.max(np.abs(ref))
