@@ -63,7 +63,7 @@ MixLayout layout(i64 n, i64 nrhs, bool lu, int prec)
     L.R = off; off += al((size_t)(n > 0 ? n : 1) * (size_t)nrhs * sizeof(double));
     L.D = off; off += al((size_t)(n > 0 ? n : 1) * (size_t)nrhs * sizeof(float));
     L.P = off; off += al((size_t)L.nchunks * RES_NR * (size_t)(n > 0 ? n : 1) * sizeof(double));
-    L.N = off; off += al((size_t)NORM_CH * (size_t)(n > 0 ? n : 1) * sizeof(double));
+    L.N = off; off += al((size_t)(NORM_CH + 1) * (size_t)(n > 0 ? n : 1) * sizeof(double));
     L.S = off; off += al(sizeof(MixState));
     L.F = off; off += al(flow_ws_bytes(n, nrhs));
     // packing space of the tensor-core updates: the largest update of either
@@ -96,28 +96,46 @@ __global__ void k_mix_init(MixState *st, int nrhs)
     for (int j = t; j < MIX_MAX_NRHS; j += blockDim.x) { st->bmax[j] = 0; st->xmax[j] = 0; st->rmax[j] = 0; }
 }
 
-// Partial row sums of |A| over column chunks: N[ch * n + i].
+// Partial row sums of |A| over column chunks: N[ch * n + i].  SYM (the
+// Cholesky form: only the lower triangle is referenced, as LAPACK's dsposv):
+// the stored part of row i (columns j <= i) here, the rest of the row (the
+// column below the diagonal) by k_colsum_lower into N[NORM_CH * n + i].
+template <bool SYM>
 __global__ void k_rowsum_partial(i64 n, const double *A, i64 lda, double *N)
 {
     const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     const int ch = blockIdx.y;
-    const i64 cw = (n + NORM_CH - 1) / NORM_CH, c0 = ch * cw, c1 = min(n, c0 + cw);
+    const i64 cw = (n + NORM_CH - 1) / NORM_CH, c0 = ch * cw;
+    i64 c1 = min(n, c0 + cw);
     if (i >= n) return;
+    if (SYM && c1 > i + 1) c1 = i + 1;
     double s = 0.0;
     for (i64 j = c0; j < c1; ++j) s += fabs(A[j * lda + i]);
     N[ch * n + i] = s;
 }
 
+// N[i] = sum_{j > i} |A(j, i)|: one warp per column, coalesced down it.
+__global__ void k_colsum_lower(i64 n, const double *A, i64 lda, double *N)
+{
+    const i64 col = (i64)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (col >= n) return;
+    double s = 0.0;
+    for (i64 j = col + 1 + lane; j < n; j += 32) s += fabs(A[col * lda + j]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) N[col] = s;
+}
+
 // ||A||_inf, max|A| -> scale (power of two so that max|A| * scale <= 1 when
 // requested), and max|b_j| per right-hand side.
-__global__ void k_norms(i64 n, const double *N, const double *A, i64 lda, const double *B, i64 ldb,
-                        int nrhs, int want_scale, MixState *st)
+__global__ void k_norms(i64 n, const double *N, int nch, const double *B, i64 ldb, int nrhs, int want_scale,
+                        MixState *st)
 {
     __shared__ double red[1024 / 32];
     double best = 0.0;
     for (i64 i = threadIdx.x; i < n; i += blockDim.x) {
         double s = 0.0;
-        for (int ch = 0; ch < NORM_CH; ++ch) s += N[ch * n + i];
+        for (int ch = 0; ch < nch; ++ch) s += N[ch * n + i];
         if (s > best || s != s) best = s;
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -151,11 +169,12 @@ __global__ void k_norms(i64 n, const double *N, const double *A, i64 lda, const 
         if (best > 0.0 && best == best) frexp(best, &e);
         st->scale = ldexp(1.0, -e);
     }
-    (void)A; (void)lda;
 }
 
 // W = (float)(A * scale); entries beyond the float range flag the working
 // copy as unusable (LAPACK dsgesv's overflow check).
+// SYM: the lower triangle only (the upper one is neither read nor written).
+template <bool SYM>
 __global__ void k_to_f32(i64 m, i64 n, const double *A, i64 lda, float *W, i64 ldw, const MixState *st,
                          int32_t *flag, const int32_t *abort)
 {
@@ -164,6 +183,7 @@ __global__ void k_to_f32(i64 m, i64 n, const double *A, i64 lda, float *W, i64 l
     const i64 total = m * n;
     for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x) {
         const i64 i = e % m, j = e / m;
+        if (SYM && i < j) continue;
         const double v = A[j * lda + i] * s;
         if (!(fabs(v) <= (double)FLT_MAX) && v == v) *flag = -2;
         W[j * ldw + i] = (float)v;
@@ -177,6 +197,11 @@ __global__ void k_after_factor(MixState *st)
 }
 
 // Partial products P[ch][c][i] = sum_{k in chunk ch} A[i,k] X[k, c0 + c].
+// SYM: A is symmetric with its lower triangle stored, A[i,k] = A(k, i) for
+// k > i; a block above the diagonal reads its transposed tile down each
+// thread's own column (each 32-byte sector serves 4 consecutive k of one
+// thread from L1).
+template <bool SYM>
 __global__ void __launch_bounds__(RES_ROWS)
 k_resid_partial(i64 n, int nr, const double *__restrict__ A, i64 lda, const double *__restrict__ X,
                 i64 ldx, double *P, const int32_t *abort)
@@ -196,12 +221,30 @@ k_resid_partial(i64 n, int nr, const double *__restrict__ A, i64 lda, const doub
     double acc[RES_NR];
 #pragma unroll
     for (int c = 0; c < RES_NR; ++c) acc[c] = 0.0;
-    const double *ap = A + k0 * lda + row;
+    const i64 r0 = (i64)blockIdx.x * RES_ROWS;
+    if (!SYM || k1 - 1 <= r0) {                  // every k <= row: stored as A(row, k)
+        const double *ap = A + k0 * lda + row;
 #pragma unroll 8
-    for (int kk = 0; kk < kc; ++kk) {
-        const double a = __ldg(ap + (i64)kk * lda);
+        for (int kk = 0; kk < kc; ++kk) {
+            const double a = __ldg(ap + (i64)kk * lda);
 #pragma unroll
-        for (int c = 0; c < RES_NR; ++c) acc[c] = fma(a, Xs[kk][c], acc[c]);
+            for (int c = 0; c < RES_NR; ++c) acc[c] = fma(a, Xs[kk][c], acc[c]);
+        }
+    } else if (k0 > r0 + RES_ROWS - 1) {         // every k > row: stored as A(k, row)
+        const double *ap = A + row * lda + k0;
+#pragma unroll 8
+        for (int kk = 0; kk < kc; ++kk) {
+            const double a = __ldg(ap + kk);
+#pragma unroll
+            for (int c = 0; c < RES_NR; ++c) acc[c] = fma(a, Xs[kk][c], acc[c]);
+        }
+    } else {                                     // the diagonal crosses this block
+        for (int kk = 0; kk < kc; ++kk) {
+            const i64 k = k0 + kk;
+            const double a = (k <= row) ? __ldg(A + k * lda + row) : __ldg(A + row * lda + k);
+#pragma unroll
+            for (int c = 0; c < RES_NR; ++c) acc[c] = fma(a, Xs[kk][c], acc[c]);
+        }
     }
     for (int c = 0; c < nr; ++c) P[((i64)ch * RES_NR + c) * n + row] = acc[c];
 }
@@ -378,16 +421,25 @@ int mixed_solve(Ctx &c, bool lu, i64 n, i64 nrhs, double *A, i64 lda, int32_t *i
 
     { Launch L(c, K_MIX, 0.0, 0.0); k_mix_init<<<1, 256, 0, c.s>>>(st, (int)nrhs); }
     {
-        Launch L(c, K_MIX, 0.0, (double)n * n * sizeof(double));
-        k_rowsum_partial<<<dim3((unsigned)((n + 255) / 256), NORM_CH), 256, 0, c.s>>>(n, A, lda, Nn);
+        Launch L(c, K_MIX, 0.0, (lu ? 1.0 : 0.5) * n * n * sizeof(double));
+        const dim3 g((unsigned)((n + 255) / 256), NORM_CH);
+        if (lu) k_rowsum_partial<false><<<g, 256, 0, c.s>>>(n, A, lda, Nn);
+        else k_rowsum_partial<true><<<g, 256, 0, c.s>>>(n, A, lda, Nn);
+    }
+    if (!lu) {
+        Launch L(c, K_MIX, 0.0, 0.5 * n * n * sizeof(double));
+        k_colsum_lower<<<(unsigned)((n + 7) / 8), 256, 0, c.s>>>(n, A, lda, Nn + (i64)NORM_CH * n);
     }
     {
         Launch L(c, K_MIX, 0.0, 0.0);
-        k_norms<<<1, 1024, 0, c.s>>>(n, Nn, A, lda, B, ldb, (int)nrhs, prec == RL_PREC_FP16S, st);
+        k_norms<<<1, 1024, 0, c.s>>>(n, Nn, lu ? NORM_CH : NORM_CH + 1, B, ldb, (int)nrhs,
+                                     prec == RL_PREC_FP16S, st);
     }
     {
-        Launch L(c, K_CONVERT, 0.0, (double)n * n * (sizeof(double) + sizeof(float)));
-        k_to_f32<<<grid_for(n * n, T256), T256, 0, c.s>>>(n, n, A, lda, W, ldw, st, &st->winfo, nullptr);
+        Launch L(c, K_CONVERT, 0.0, (lu ? 1.0 : 0.5) * n * n * (sizeof(double) + sizeof(float)));
+        const unsigned g = grid_for(n * n, T256);
+        if (lu) k_to_f32<false><<<g, T256, 0, c.s>>>(n, n, A, lda, W, ldw, st, &st->winfo, nullptr);
+        else k_to_f32<true><<<g, T256, 0, c.s>>>(n, n, A, lda, W, ldw, st, &st->winfo, nullptr);
     }
 
     // low-precision factorization of W (its info lands in st->winfo)
@@ -426,8 +478,10 @@ int mixed_solve(Ctx &c, bool lu, i64 n, i64 nrhs, double *A, i64 lda, int32_t *i
             const int nr = (int)((nrhs - c0) < RES_NR ? (nrhs - c0) : RES_NR);
             {
                 Launch L(r, K_RESID, 2.0 * n * n * nr, (double)n * n * sizeof(double));
-                k_resid_partial<<<dim3((unsigned)((n + RES_ROWS - 1) / RES_ROWS), (unsigned)Ly.nchunks),
-                                  RES_ROWS, 0, r.s>>>(n, nr, A, lda, X + c0 * ldx, ldx, P, r.abort);
+                const dim3 g((unsigned)((n + RES_ROWS - 1) / RES_ROWS), (unsigned)Ly.nchunks);
+                const double *Xc = X + c0 * ldx;
+                if (lu) k_resid_partial<false><<<g, RES_ROWS, 0, r.s>>>(n, nr, A, lda, Xc, ldx, P, r.abort);
+                else k_resid_partial<true><<<g, RES_ROWS, 0, r.s>>>(n, nr, A, lda, Xc, ldx, P, r.abort);
             }
             {
                 Launch L(r, K_RESID, (double)n * nr * Ly.nchunks, 0.0);

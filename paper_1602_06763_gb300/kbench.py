@@ -40,6 +40,7 @@ def main():
     ap.add_argument("--panel-ctas", type=int, default=0, help="LU panel CTAs (RL_PARAM_PANEL_CTAS value)")
     ap.add_argument("--fp32", action="store_true", help="panel/getrf cases: FP32 storage (rl_sgetrf)")
     ap.add_argument("--tri-lanes", type=int, default=0, help="lanes per vector of the triangle leaf kernels (2 or 4)")
+    ap.add_argument("--uplo", default="L", help="potrf / trtri / lauum / zpotrf: triangle")
     ap.add_argument("--flow", type=int, default=1, help="getrs/potrs: 1 = one-launch flow solve, 0 = recursive")
     a = ap.parse_args()
 
@@ -158,7 +159,7 @@ def main():
             Z0 = Z0.transpose(0, 1).contiguous()       # column-major Hermitian: the conjugate
             flops = 4.0 * n ** 3 / 3.0
             Z = Z0.clone()
-            run = lambda: r.check(r.rl_zpotrf("L", n, Z, n, info, None, 0, s))
+            run = lambda: r.check(r.rl_zpotrf(a.uplo, n, Z, n, info, None, 0, s))
         else:
             Z0 = X
             ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
@@ -194,13 +195,13 @@ def main():
         restore = lambda: A.copy_(A0)
         if a.case == "potrf":
             flops = n ** 3 / 3.0
-            run = lambda: r.check(r.rl_dpotrf("L", n, A, n, info, None, 0, s))
+            run = lambda: r.check(r.rl_dpotrf(a.uplo, n, A, n, info, None, 0, s))
         elif a.case == "trtri":
             flops = n ** 3 / 3.0
-            run = lambda: r.check(r.rl_dtrtri("L", "N", n, A, n, info, None, 0, s))
+            run = lambda: r.check(r.rl_dtrtri(a.uplo, "N", n, A, n, info, None, 0, s))
         elif a.case == "lauum":
             flops = n ** 3 / 3.0
-            run = lambda: r.check(r.rl_dlauum("L", n, A, n, info, None, 0, s))
+            run = lambda: r.check(r.rl_dlauum(a.uplo, n, A, n, info, None, 0, s))
         else:
             cols = n if a.case == "getrf" else (a.nb or r.rl_get_param(r.RL_PARAM_GETRF_PANEL))
             rows = m

@@ -248,3 +248,30 @@ def test_batched_dpotrf_upper():
         X = b.cpu().numpy().reshape(n, n).T
         assert np.array_equal(np.tril(X, -1), np.tril(A0, -1))
         assert oracle.res_chol(A, tT(np.triu(X))) <= 10.0
+
+
+@pytest.mark.parametrize("prec", ["FP32", "BF16"])
+def test_dsposv_lower_ignores_the_upper_triangle(prec):
+    """LAPACK's dsposv references only the uplo triangle: a marker pattern in
+    the other one changes neither the solution nor the iteration count."""
+    r = G.lib()
+    t = G.torch()
+    n, nrhs = 900, 3
+    p = getattr(r, "RL_PREC_" + prec)
+    A = inputs.spd_bbt(n, seed=inputs.seed_for(1, 6750))
+    rng = np.random.default_rng(6751)
+    Am = np.asfortranarray(np.tril(A) + np.triu(rng.uniform(-1e30, 1e30, (n, n)), 1))
+    B = inputs.normal(n, nrhs, seed=inputs.seed_for(1, 6752))
+    out = []
+    for M in (A, Am):
+        dA, dB, dX = G.DevMat(M), G.DevMat(B), G.DevMat(np.zeros((n, nrhs)))
+        lw = r.rl_dsposv_work_size(n, nrhs, p)
+        w = t.zeros(lw, dtype=t.uint8, device="cuda")
+        it, info = G.int_buf(1, -9), G.int_buf(1, -77)
+        call(r.rl_dsposv, "L", n, nrhs, dA.ptr(), n, dB.ptr(), n, dX.ptr(), n, p, 0.0, 30,
+             it.data_ptr(), info.data_ptr(), w, lw)
+        assert int(info[0]) == 0 and int(it[0]) > 0
+        assert np.array_equal(dA.get(), M)
+        out.append((dX.get(), int(it[0])))
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
