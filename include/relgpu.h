@@ -254,6 +254,42 @@ int rl_zgetrf(int64_t m, int64_t n, rl_double_complex *A, int64_t lda, int32_t *
               int32_t *info, void *work, size_t lwork, rl_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * FP64 updates emulated on the BF16 tensor cores (the Ozaki scheme; not in
+ * the paper).  Row i of op(A) and column j of op(B) are scaled by powers of
+ * two 2^-eA_i, 2^-eB_j (max |entry| < 2^(e-1)), rounded to 8*slices-bit
+ * fixed point and cut into `slices` signed 8-bit digits (exact in BF16);
+ * the digit products of significance above 2^(-8*slices-8) are summed by
+ * tcgen05 MMAs in exact FP32 blocks of 128 values of k, then in 64-bit
+ * integers, and converted to FP64 once.  Error: below k * 2^(-8*slices)
+ * * 2^(eA_i + eB_j) per entry (normwise like an FP64 GEMM at slices = 7);
+ * integer inputs whose row and column maxima are below 2^(8*slices-1) give
+ * the exact product wherever it is below 2^53.  Inputs must be finite (a
+ * row or column holding Inf or NaN gives NaN in its row or column of C).
+ *   slices: 6, 7 (FP64-level accuracy) or 8; else argument 1 is illegal.
+ *   rl_dgemm_oz: C := beta C + alpha op(A) op(B) (transa/transb 'N'/'T');
+ *     k <= 2^21; work >= rl_oz_work_size(m, n, k, slices) bytes (device):
+ *     the digit planes, 2 * slices bytes per element of op(A) and op(B)
+ *     padded to 128 x 64 tiles.  Argument numbers: 1 slices, 2 transa,
+ *     3 transb, 4 m, 5 n, 6 k, 9 lda, 11 ldb, 14 ldc.
+ *   rl_dpotrf_oz / rl_dgetrf_oz: rl_dpotrf / rl_dgetrf with every GEMM/SYRK
+ *     update of order >= RL_PARAM_OZ_MIN (m, n and k) emulated; same
+ *     results, info and ipiv semantics (within the scheme's error);
+ *     workspace rl_dpotrf_oz_work_size(n, slices) /
+ *     rl_dgetrf_oz_work_size(m, n, slices) (the LU's includes its panel
+ *     workspace).  Argument numbers shift by one (1 = slices).
+ * ------------------------------------------------------------------------- */
+size_t rl_oz_work_size(int64_t m, int64_t n, int64_t k, int slices);
+int rl_dgemm_oz(int slices, char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C,
+                int64_t ldc, void *work, size_t lwork, rl_stream_t stream);
+size_t rl_dpotrf_oz_work_size(int64_t n, int slices);
+size_t rl_dgetrf_oz_work_size(int64_t m, int64_t n, int slices);
+int rl_dpotrf_oz(int slices, char uplo, int64_t n, double *A, int64_t lda, int32_t *info, void *work,
+                 size_t lwork, rl_stream_t stream);
+int rl_dgetrf_oz(int slices, int64_t m, int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info,
+                 void *work, size_t lwork, rl_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Low-precision factorizations (the factorization step of the precision
  * form, callable on its own): rl_spotrf / rl_sgetrf on FP32 storage with
  * every large GEMM/SYRK update on the tensor cores (tcgen05) with operands in
@@ -499,6 +535,9 @@ int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda,
  *                              FP64 panels, high 16 bits for FP32 panels
  *                              (0, the default: one per SM; at most 256
  *                              rows each either way)
+ *   RL_PARAM_OZ_MIN            smallest m, n and k of an FP64 update that
+ *                              the *_oz routines emulate on the tensor
+ *                              cores (default 256; smaller ones stay FP64)
  * rl_set_param returns 0 or RL_ERR_PARAM; rl_get_param returns the value or
  * -1 for an unknown key.
  * ------------------------------------------------------------------------- */
@@ -510,7 +549,8 @@ enum {
     RL_PARAM_BATCH_CTAS = 5,
     RL_PARAM_TRI_LANES = 6,
     RL_PARAM_LOOKAHEAD = 7,
-    RL_PARAM_PANEL_CTAS = 8
+    RL_PARAM_PANEL_CTAS = 8,
+    RL_PARAM_OZ_MIN = 9
 };
 int rl_set_param(int key, int64_t value);
 int64_t rl_get_param(int key);

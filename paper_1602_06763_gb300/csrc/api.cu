@@ -91,7 +91,10 @@ static bool lookahead_resources(cudaStream_t *side, LaEvents **ev)
 // The side stream may run GEMMs concurrently with the caller's stream only
 // when no GEMM of the call stages operands in a shared workspace (the
 // tensor-core updates pack into c.tcwork).
-static bool lookahead_ok(const Ctx &c) { return g_params.lookahead && c.tcwork == nullptr; }
+static bool lookahead_ok(const Ctx &c)
+{
+    return g_params.lookahead && c.tcwork == nullptr && c.ozwork == nullptr;   // one packing workspace per call
+}
 
 // ---- recursions -------------------------------------------------------------
 
@@ -564,6 +567,112 @@ int rl_zgetrf(int64_t m, int64_t n, rl_double_complex *A, int64_t lda, int32_t *
     c.abort = nullptr;
     note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
     getrf_rec_t<cplx>(c, reinterpret_cast<cplx *>(A), lda, m, ipiv, 0, m, n);
+    return finish(c);
+}
+
+// ---- FP64 factorizations with emulated FP64 updates ---------------------------------
+// The recursions of rl_dpotrf / rl_dgetrf with every FP64 GEMM/SYRK update of
+// order >= RL_PARAM_OZ_MIN (m, n and k) emulated on the BF16 tensor cores
+// (oz_gemm.cu); leaves, panels and smaller updates in native FP64.
+
+static bool oz_slices_ok(int s) { return s >= 6 && s <= 8; }
+
+size_t rl_oz_work_size(int64_t m, int64_t n, int64_t k, int slices)
+{
+    if (m < 0 || n < 0 || k < 0 || !oz_slices_ok(slices)) return 0;
+    return oz_work_bytes(m, n, k, slices);
+}
+
+int rl_dgemm_oz(int slices, char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
+                void *work, size_t lwork, rl_stream_t stream)
+{
+    if (!oz_slices_ok(slices)) return -1;
+    const bool ta = transa == 'T' || transa == 't' || transa == 'C' || transa == 'c';
+    const bool tb = transb == 'T' || transb == 't' || transb == 'C' || transb == 'c';
+    if (!ta && transa != 'N' && transa != 'n') return -2;
+    if (!tb && transb != 'N' && transb != 'n') return -3;
+    if (m < 0) return -4;
+    if (n < 0) return -5;
+    if (k < 0) return -6;
+    if (lda < ((ta ? k : m) > 1 ? (ta ? k : m) : 1)) return -9;
+    if (ldb < ((tb ? n : k) > 1 ? (tb ? n : k) : 1)) return -11;
+    if (ldc < (m > 1 ? m : 1)) return -14;
+    if (m == 0 || n == 0) return RL_SUCCESS;
+    if (k > (1 << 21) || m > (1 << 30) || n > (1 << 30)) return RL_ERR_UNSUPPORTED;
+    if (k > 0 && (work == nullptr || lwork < oz_work_bytes(m, n, k, slices))) return RL_ERR_WORKSPACE;
+    Ctx c = make_ctx(stream, nullptr, nullptr, 0);
+    if (k == 0) {
+        gemm<double>(c, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, false);   // C := beta C
+        return finish(c);
+    }
+    if (!oz_gemm(c, slices, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, false, work, lwork))
+        return RL_ERR_UNSUPPORTED;
+    return finish(c);
+}
+
+// largest update of the recursions: m rows (<= max(m, n)), n/2 + 64 columns
+// and inner dimension, and (wide LU) the solve of the n - m columns
+static size_t oz_factor_bytes(int64_t m, int64_t n, int slices)
+{
+    const i64 big = m > n ? m : n, h = (m < n ? m : n) / 2 + 64;
+    return oz_work_bytes(big, big, h, slices);
+}
+
+size_t rl_dpotrf_oz_work_size(int64_t n, int slices)
+{
+    if (n < 0 || !oz_slices_ok(slices)) return 0;
+    return oz_work_bytes(n / 2 + 64, n / 2 + 64, n / 2 + 64, slices);
+}
+
+size_t rl_dgetrf_oz_work_size(int64_t m, int64_t n, int slices)
+{
+    if (m < 0 || n < 0 || !oz_slices_ok(slices)) return 0;
+    return ((panel_ws_bytes() + 1023) & ~(size_t)1023) + oz_factor_bytes(m, n, slices);
+}
+
+int rl_dpotrf_oz(int slices, char uplo, int64_t n, double *A, int64_t lda, int32_t *info, void *work,
+                 size_t lwork, rl_stream_t stream)
+{
+    if (!oz_slices_ok(slices)) return -1;
+    if (!is_l(uplo) && !is_u(uplo)) return -2;
+    if (n < 0) return -3;
+    if (n > 0 && A == nullptr) return -4;
+    if (lda < (n > 1 ? n : 1)) return -5;
+    if (info == nullptr) return RL_ERR_NULL_POINTER;
+    if (n > 0 && (work == nullptr || lwork < rl_dpotrf_oz_work_size(n, slices))) return RL_ERR_WORKSPACE;
+    Ctx c = make_ctx(stream, info, nullptr, 0);
+    c.abort = info;
+    c.oz_slices = slices;
+    c.ozwork = work;
+    c.ozlwork = lwork;
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    const bool up = is_u(uplo);
+    if (up) uplo_swap<double>(c, n, A, lda);
+    potrf_rec(c, n, A, lda, 0);
+    if (up) uplo_swap<double>(c, n, A, lda);
+    return finish(c);
+}
+
+int rl_dgetrf_oz(int slices, int64_t m, int64_t n, double *A, int64_t lda, int32_t *ipiv, int32_t *info,
+                 void *work, size_t lwork, rl_stream_t stream)
+{
+    if (!oz_slices_ok(slices)) return -1;
+    if (m < 0) return -2;
+    if (n < 0) return -3;
+    if (m > 0 && n > 0 && A == nullptr) return -4;
+    if (lda < (m > 1 ? m : 1)) return -5;
+    if (m > INT32_MAX - 1) return RL_ERR_UNSUPPORTED;
+    if (info == nullptr || (ipiv == nullptr && m > 0 && n > 0)) return RL_ERR_NULL_POINTER;
+    if (m > 0 && n > 0 && (work == nullptr || lwork < rl_dgetrf_oz_work_size(m, n, slices))) return RL_ERR_WORKSPACE;
+    const size_t pw = (panel_ws_bytes() + 1023) & ~(size_t)1023;
+    Ctx c = make_ctx(stream, info, work, pw);
+    c.abort = nullptr;
+    c.oz_slices = slices;
+    c.ozwork = static_cast<char *>(work) + pw;
+    c.ozlwork = lwork > pw ? lwork - pw : 0;
+    note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
+    getrf_rec(c, A, lda, m, ipiv, 0, m, n);
     return finish(c);
 }
 
@@ -1274,6 +1383,10 @@ int rl_set_param(int key, int64_t value)
         if (value != 0 && value != 1) return RL_ERR_PARAM;
         g_params.lookahead = (int)value;
         return RL_SUCCESS;
+    case RL_PARAM_OZ_MIN:
+        if (value < 1 || value > (1 << 20)) return RL_ERR_PARAM;
+        g_params.oz_min = (int)value;
+        return RL_SUCCESS;
     case RL_PARAM_PANEL_CTAS:
         // low 16 bits: FP64 panels, high 16 bits: FP32 panels (0 = one per SM)
         if (value < 0 || (value & 0xffff) > 256 || (value >> 16) > 256) return RL_ERR_PARAM;
@@ -1295,6 +1408,7 @@ int64_t rl_get_param(int key)
     case RL_PARAM_BATCH_CTAS: return g_params.batch_ctas;
     case RL_PARAM_TRI_LANES: return g_params.tri_lanes;
     case RL_PARAM_LOOKAHEAD: return g_params.lookahead;
+    case RL_PARAM_OZ_MIN: return g_params.oz_min;
     case RL_PARAM_PANEL_CTAS: return (int64_t)g_params.panel_ctas64 | ((int64_t)g_params.panel_ctas32 << 16);
     default: return -1;
     }

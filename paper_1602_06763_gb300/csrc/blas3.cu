@@ -473,6 +473,12 @@ static void gemm_real(Ctx &c, bool ta, bool tb, i64 m, i64 n, i64 k, T alpha, co
                     (float *)C, ldc, lower, c.tcwork, c.tclwork))
             return;
     }
+    if (sizeof(T) == 8 && c.oz_slices > 0 && m >= g_params.oz_min && n >= g_params.oz_min &&
+        k >= g_params.oz_min) {
+        if (oz_gemm(c, c.oz_slices, ta, tb, m, n, k, (double)alpha, (const double *)A, lda, (const double *)B, ldb,
+                    (double)beta, (double *)C, ldc, lower, c.ozwork, c.ozlwork))
+            return;
+    }
     if (gemm_f32_wide<T>(c, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, lower)) return;
     if (lower) {
         if (!ta && tb) launch_gemm<T, false, true, true>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);

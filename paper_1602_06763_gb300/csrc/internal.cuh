@@ -78,6 +78,7 @@ struct Params {
     int lookahead = 1;       // LU/Cholesky: trailing update split across the side stream (0 = off)
     int panel_ctas64 = 0;    // LU panel CTAs, FP64 / FP32 (0 = one per SM)
     int panel_ctas32 = 0;
+    int oz_min = 256;        // smallest m, n and k that the FP64 emulation takes
 };
 extern Params g_params;
 
@@ -95,6 +96,11 @@ struct Ctx {
     int prec = RL_PREC_FP32;
     void *tcwork = nullptr;
     size_t tclwork = 0;
+    // FP64 GEMMs emulated on the BF16 tensor cores (oz_gemm.cu): digit
+    // planes (0 = native FP64) and the slicing workspace
+    int oz_slices = 0;
+    void *ozwork = nullptr;
+    size_t ozlwork = 0;
 };
 
 int device_sms();
@@ -225,6 +231,11 @@ bool tc_gemm(Ctx &c, int prec, bool ta, bool tb, i64 m, i64 n, i64 k, float alph
              i64 lda, const float *B, i64 ldb, float *C, i64 ldc, bool lower, void *work, size_t lwork);
 // Smallest GEMM sent to the tensor cores (smaller ones are latency-bound).
 constexpr i64 TC_MIN_MN = 128, TC_MIN_K = 64;
+
+// ---- FP64 GEMM emulated on the BF16 tensor cores (oz_gemm.cu) -------------------
+size_t oz_work_bytes(i64 m, i64 n, i64 k, int slices);
+bool oz_gemm(Ctx &c, int slices, bool ta, bool tb, i64 m, i64 n, i64 k, double alpha, const double *A, i64 lda,
+             const double *B, i64 ldb, double beta, double *C, i64 ldc, bool lower, void *work, size_t lwork);
 
 // ---- batching form (batched.cu) ---------------------------------------------
 size_t batched_work_size(i64 batch);

@@ -40,6 +40,8 @@ def main():
     ap.add_argument("--panel-ctas", type=int, default=0, help="LU panel CTAs (RL_PARAM_PANEL_CTAS value)")
     ap.add_argument("--fp32", action="store_true", help="panel/getrf cases: FP32 storage (rl_sgetrf)")
     ap.add_argument("--tri-lanes", type=int, default=0, help="lanes per vector of the triangle leaf kernels (2 or 4)")
+    ap.add_argument("--oz", type=int, default=0,
+                    help="dgemm / dsyrk / potrf / getrf: FP64 updates emulated with this many BF16 digit planes")
     ap.add_argument("--uplo", default="L", help="potrf / trtri / lauum / zpotrf: triangle")
     ap.add_argument("--flow", type=int, default=1, help="getrs/potrs: 1 = one-launch flow solve, 0 = recursive")
     a = ap.parse_args()
@@ -142,7 +144,12 @@ def main():
         A = torch.rand(k, n, generator=g, device=dev, dtype=torch.float64)
         B = torch.rand(n, k, generator=g, device=dev, dtype=torch.float64)
         C = torch.rand(n, n, generator=g, device=dev, dtype=torch.float64)
-        if a.case == "dgemm":
+        if a.case == "dgemm" and a.oz:
+            flops = 2.0 * n * n * k
+            lwz = r.rl_oz_work_size(n, n, k, a.oz)
+            wz = torch.empty(lwz, dtype=torch.uint8, device=dev)
+            run = lambda: r.check(r.rl_dgemm_oz(a.oz, "N", "N", n, n, k, -1.0, A, n, B, k, 1.0, C, n, wz, lwz, s))
+        elif a.case == "dgemm":
             flops = 2.0 * n * n * k
             run = lambda: r.check(r.rl_dgemm("N", "N", n, n, k, -1.0, A, n, B, k, 1.0, C, n, s))
         else:
@@ -193,7 +200,12 @@ def main():
                 A0 = A0.to(torch.float32)
         A = A0.clone()
         restore = lambda: A.copy_(A0)
-        if a.case == "potrf":
+        if a.case == "potrf" and a.oz:
+            flops = n ** 3 / 3.0
+            lwz = r.rl_dpotrf_oz_work_size(n, a.oz)
+            wz = torch.empty(lwz, dtype=torch.uint8, device=dev)
+            run = lambda: r.check(r.rl_dpotrf_oz(a.oz, a.uplo, n, A, n, info, wz, lwz, s))
+        elif a.case == "potrf":
             flops = n ** 3 / 3.0
             run = lambda: r.check(r.rl_dpotrf(a.uplo, n, A, n, info, None, 0, s))
         elif a.case == "trtri":
@@ -210,8 +222,13 @@ def main():
             work = torch.empty(lw, dtype=torch.uint8, device=dev)
             mn = min(rows, cols)
             flops = max(rows, cols) * mn * mn - mn ** 3 / 3.0   # LU of m x n, leading terms
-            fn = r.rl_sgetrf if a.fp32 else r.rl_dgetrf
-            run = lambda: r.check(fn(rows, cols, A, rows, ipiv, info, work, lw, s))
+            if a.oz and a.case == "getrf":
+                lw = r.rl_dgetrf_oz_work_size(rows, cols, a.oz)
+                work = torch.empty(lw, dtype=torch.uint8, device=dev)
+                run = lambda: r.check(r.rl_dgetrf_oz(a.oz, rows, cols, A, rows, ipiv, info, work, lw, s))
+            else:
+                fn = r.rl_sgetrf if a.fp32 else r.rl_dgetrf
+                run = lambda: r.check(fn(rows, cols, A, rows, ipiv, info, work, lw, s))
 
     for _ in range(a.warmup):
         restore()

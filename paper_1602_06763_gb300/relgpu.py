@@ -63,6 +63,13 @@ _SIGS = {
     "rl_spotrf_tc_work_size": (ctypes.c_size_t, [_i64, ctypes.c_int]),
     "rl_sgetrf_tc_work_size": (ctypes.c_size_t, [_i64, _i64, ctypes.c_int]),
     "rl_spotrf_tc": (ctypes.c_int, [ctypes.c_int, _ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_oz_work_size": (_sz, [_i64, _i64, _i64, ctypes.c_int]),
+    "rl_dgemm_oz": (ctypes.c_int, [ctypes.c_int, _ch, _ch, _i64, _i64, _i64, ctypes.c_double, _vp, _i64, _vp,
+                                   _i64, ctypes.c_double, _vp, _i64, _vp, _sz, _vp]),
+    "rl_dpotrf_oz_work_size": (_sz, [_i64, ctypes.c_int]),
+    "rl_dgetrf_oz_work_size": (_sz, [_i64, _i64, ctypes.c_int]),
+    "rl_dpotrf_oz": (ctypes.c_int, [ctypes.c_int, _ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_dgetrf_oz": (ctypes.c_int, [ctypes.c_int, _i64, _i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
     "rl_sgetrf_tc": (ctypes.c_int, [ctypes.c_int, _i64, _i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
     "rl_dgetri_work_size": (ctypes.c_size_t, [_i64]),
     "rl_dgetri": (ctypes.c_int, [_i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
@@ -134,6 +141,7 @@ RL_PARAM_BATCH_CTAS = 5
 RL_PARAM_TRI_LANES = 6
 RL_PARAM_LOOKAHEAD = 7
 RL_PARAM_PANEL_CTAS = 8
+RL_PARAM_OZ_MIN = 9
 
 
 def _ptr(x):
@@ -231,6 +239,32 @@ def rl_zpotrf(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
 
 def rl_zgetrf(m, n, A, lda, ipiv, info, work, lwork, stream=None):
     return _lib.rl_zgetrf(m, n, _ptr(A), lda, _ptr(ipiv), _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_oz_work_size(m, n, k, slices):
+    return int(_lib.rl_oz_work_size(m, n, k, slices))
+
+
+def rl_dgemm_oz(slices, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, work, lwork, stream=None):
+    return _lib.rl_dgemm_oz(slices, _c(transa), _c(transb), m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb, beta,
+                            _ptr(C), ldc, _ptr(work), lwork, _stream(stream))
+
+
+def rl_dpotrf_oz_work_size(n, slices):
+    return int(_lib.rl_dpotrf_oz_work_size(n, slices))
+
+
+def rl_dgetrf_oz_work_size(m, n, slices):
+    return int(_lib.rl_dgetrf_oz_work_size(m, n, slices))
+
+
+def rl_dpotrf_oz(slices, uplo, n, A, lda, info, work, lwork, stream=None):
+    return _lib.rl_dpotrf_oz(slices, _c(uplo), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_dgetrf_oz(slices, m, n, A, lda, ipiv, info, work, lwork, stream=None):
+    return _lib.rl_dgetrf_oz(slices, m, n, _ptr(A), lda, _ptr(ipiv), _ptr(info), _ptr(work), lwork,
+                             _stream(stream))
 
 
 def rl_spotrf_tc_work_size(n, prec):
