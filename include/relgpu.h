@@ -260,8 +260,9 @@ int rl_zgetrf(int64_t m, int64_t n, rl_double_complex *A, int64_t lda, int32_t *
  * fixed point and cut into `slices` signed 8-bit digits (exact in BF16);
  * the digit products of significance above 2^(-8*slices-8) are summed by
  * tcgen05 MMAs in exact FP32 blocks of 128 values of k, then in 64-bit
- * integers, and converted to FP64 once.  Error: below k * 2^(-8*slices)
- * * 2^(eA_i + eB_j) per entry (normwise like an FP64 GEMM at slices = 7);
+ * integers, and converted to FP64 once.  Error: below (slices + 1) * k *
+ * 2^(-8*slices-2) * 2^(eA_i + eB_j) per entry plus the final rounding
+ * (normwise like an FP64 GEMM from slices = 7 on);
  * integer inputs whose row and column maxima are below 2^(8*slices-1) give
  * the exact product wherever it is below 2^53.  Inputs must be finite (a
  * row or column holding Inf or NaN gives NaN in its row or column of C).

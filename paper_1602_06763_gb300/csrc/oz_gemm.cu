@@ -10,9 +10,10 @@
 // Scheme.  Row i of op(A) is scaled by 2^-eA_i, eA_i = the power of two with
 // max_k |a_ik| < 2^(eA_i - 1), so every scaled entry q has |q| < 1/2, and
 // rounded to the 8S-bit fixed-point integer Q = round(q 2^(8S)); the same
-// for column j of op(B) with eB_j.  Q is cut into S balanced base-256
-// digits d_1..d_S in [-128, 128] (q = sum_s d_s 2^(-8s) up to 2^(-8S-1)),
-// each exact in BF16.  Then
+// for column j of op(B) with eB_j.  Q is cut into S signed base-256 digits
+// (the low S - 1 in [-128, 127], the top one what remains, within
+// [-128, 128]), so q = sum_s d_s 2^(-8s) up to 2^(-8S-1), each exact in
+// BF16.  Then
 //     (op(A) op(B))_ij ~ 2^(eA_i + eB_j) sum_{L=2}^{S+1} 2^(-8L) T_L,
 //     T_L = sum over digit pairs (s, t), s + t = L, of sum_k dA_s dB_t,
 // the pairs with s + t > S + 1 (below 2^(-8S-8) relative) left out.  Each
@@ -23,8 +24,10 @@
 // output (levels 2..S-3 and S-2..S+1, exact), and at the end of the tile
 // converted to FP64 once.  The only roundings are the truncation of the
 // digits (2^(-8S-1) relative to the row and column maxima) and the final
-// conversion; with S = 7 the error is below k 2^-56 2^(eA_i + eB_j),
-// normwise as small as an FP64 GEMM's, and integer products are exact.
+// conversion: per term of the sum at most 2^(-8S-2) from each side's
+// truncation and (S - 1) 2^(-8S-2) from the pairs left out, so the error is
+// below (S + 1) k 2^(-8S-2) 2^(eA_i + eB_j) plus the final rounding (S = 7:
+// normwise of the order of an FP64 GEMM's), and integer products are exact.
 //
 // Kernel (one CTA per SM, persistent over 128 x 64 output tiles in groups
 // of 8 row tiles for L2 reuse; 576 threads):
@@ -127,11 +130,12 @@ __device__ __forceinline__ void digits_of(double x, int e, int *d)
         Q = (b >> 63) ? -(long long)u : (long long)u;
     }
 #pragma unroll
-    for (int s = S - 1; s >= 0; --s) {
-        const long long dd = ((Q + 128) & 255) - 128;
+    for (int s = S - 1; s >= 1; --s) {
+        const long long dd = ((Q + 128) & 255) - 128;     // in [-128, 127]
         d[s] = (int)dd;
         Q = (Q - dd) >> 8;
     }
+    d[0] = (int)Q;     // |Q| < 2^(8S-1) leaves |d[0]| <= 128 (it may be 128: no carry out)
 }
 
 // Digit planes P[s][r][k] (BF16, rows_p x kp per plane, zero padded) of the

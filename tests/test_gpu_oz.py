@@ -1,7 +1,7 @@
 """FP64 updates emulated on the BF16 tensor cores (rl_dgemm_oz, rl_dpotrf_oz,
 rl_dgetrf_oz): integer products exact bit for bit, random products within the
-scheme's error bound k 2^(-8S-1) 2^(eA_i + eB_j) against an extended-precision
-reference, every transpose combination and ragged tile edges, Inf/NaN
+scheme's error bound (S + 1) k 2^(-8S-2) 2^(eA_i + eB_j) against an
+extended-precision reference, every transpose combination and ragged tile edges, Inf/NaN
 confined to their row or column, and the factorizations held to the same
 residual bound, exact cases and pivots as the native FP64 path."""
 import numpy as np
@@ -77,7 +77,8 @@ def test_random_products_within_the_bound(S, ta, tb):
                 np.zeros((m, n)))
     eA = exp_of(np.max(np.abs(A), axis=1))[:, None]
     eB = exp_of(np.max(np.abs(B), axis=0))[None, :]
-    bound = (k + 2) * np.exp2(-8.0 * S - 1 + eA + eB) * 2 + 2.0 ** -52 * np.abs(exact.astype(np.float64))
+    # truncated digits (2^(-8S-1) each side) and the pairs left out: (S + 1) 2^(-8S-2) per term
+    bound = k * (S + 1) * np.exp2(-8.0 * S - 2 + eA + eB) + 2.0 ** -52 * np.abs(exact.astype(np.float64))
     err = np.abs((C.astype(np.longdouble) - exact).astype(np.float64))
     assert np.all(err <= bound)
     assert np.all(C[5, :] == 0.0)
