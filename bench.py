@@ -584,6 +584,105 @@ def lowprec_section(n, dev, sp):
     return out
 
 
+def emulated_section(n, slices, dev, sp):
+    """FP64 factorizations with the updates emulated on the BF16 tensor cores
+    (rl_dpotrf_oz / rl_dgetrf_oz, `slices` digit planes) next to the native
+    FP64 ones on the same inputs: GFLOP/s (LAWN 41 counts, median of 2 after
+    a warm-up) and a random-probe residual of each result,
+    ||A x - L (L^T x)|| or ||P A x - L (U x)|| / (n eps ||A||_1 ||x||_1)
+    (O(n^2) FP64 work), and an 8192^3 GEMM both ways."""
+    import torch
+    from paper_1602_06763_gb300 import relgpu as r, inputs
+
+    eps = 2.0 ** -53
+    S0 = inputs.spd_bbt_device(n, inputs.seed_for(2, 80), device=dev)
+    G0 = inputs.uniform_device(n, n, inputs.seed_for(2, 81), device=dev)
+    A = torch.empty_like(S0)
+    ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(inputs.seed_for(2, 82))
+    x = torch.rand(n, 1, generator=gen, device=dev, dtype=torch.float64) * 2 - 1
+
+    # the library reads each buffer column-major: its matrix is the transpose of the torch view
+    def probe_chol(F):
+        L = torch.tril(F.transpose(0, 1))
+        A0 = S0.transpose(0, 1)
+        y = A0 @ x - L @ (L.transpose(0, 1) @ x)
+        return float(y.abs().sum() / (n * eps * A0.abs().sum(0).max() * x.abs().sum()))
+
+    def probe_lu(F, piv):
+        Ft = F.transpose(0, 1)
+        L = torch.tril(Ft, -1) + torch.eye(n, device=dev, dtype=torch.float64)
+        U = torch.triu(Ft)
+        b = (G0.transpose(0, 1) @ x).squeeze(1)
+        p = piv.cpu().numpy() - 1
+        perm = list(range(n))
+        for i in range(n):
+            perm[i], perm[p[i]] = perm[p[i]], perm[i]
+        b = b[torch.tensor(perm, device=dev)]
+        y = b - (L @ (U @ x)).squeeze(1)
+        return float(y.abs().sum() / (n * eps * G0.transpose(0, 1).abs().sum(0).max() * x.abs().sum()))
+
+    def timed(call, src):
+        ts = []
+        for rep in range(3):
+            A.copy_(src)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            call()
+            b.record()
+            torch.cuda.synchronize()
+            if rep:
+                ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    out = {"n": n, "slices": slices}
+    lw = r.rl_dgetrf_work_size(n, n)
+    wn = torch.empty(lw, dtype=torch.uint8, device=dev)
+    lpo = r.rl_dpotrf_oz_work_size(n, slices)
+    lgo = r.rl_dgetrf_oz_work_size(n, n, slices)
+    wo = torch.empty(max(lpo, lgo), dtype=torch.uint8, device=dev)
+    for kind, emu in (("dpotrf", False), ("dpotrf", True), ("dgetrf", False), ("dgetrf", True)):
+        if kind == "dpotrf":
+            call = ((lambda: r.check(r.rl_dpotrf_oz(slices, "L", n, A, n, info, wo, lpo, sp))) if emu else
+                    (lambda: r.check(r.rl_dpotrf("L", n, A, n, info, None, 0, sp))))
+            ms = timed(call, S0)
+            res = probe_chol(A)
+            flops = n ** 3 / 3.0
+        else:
+            call = ((lambda: r.check(r.rl_dgetrf_oz(slices, n, n, A, n, ipiv, info, wo, lgo, sp))) if emu else
+                    (lambda: r.check(r.rl_dgetrf(n, n, A, n, ipiv, info, wn, lw, sp))))
+            ms = timed(call, G0)
+            res = probe_lu(A, ipiv)
+            flops = 2.0 * n ** 3 / 3.0
+        out[kind + ("_emulated" if emu else "_native")] = {
+            "ms": ms, "gflops": flops / (ms * 1e-3) / 1e9, "info": int(info[0]), "probe_residual": res}
+    del wo, wn
+    g = 8192
+    Ag = torch.rand(g, g, generator=gen, device=dev, dtype=torch.float64)
+    Bg = torch.rand(g, g, generator=gen, device=dev, dtype=torch.float64)
+    Cg = torch.zeros(g, g, device=dev, dtype=torch.float64)
+    lz = r.rl_oz_work_size(g, g, g, slices)
+    wz = torch.empty(lz, dtype=torch.uint8, device=dev)
+    for emu in (False, True):
+        call = ((lambda: r.check(r.rl_dgemm_oz(slices, "N", "N", g, g, g, 1.0, Ag, g, Bg, g, 0.0, Cg, g, wz, lz, sp)))
+                if emu else (lambda: r.check(r.rl_dgemm("N", "N", g, g, g, 1.0, Ag, g, Bg, g, 0.0, Cg, g, sp))))
+        call()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        call()
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        out["dgemm_8192_" + ("emulated" if emu else "native")] = {"ms": ms, "gflops": 2.0 * g ** 3 / (ms * 1e-3) / 1e9}
+    out["note"] = ("not in the paper: the FP64 updates as BF16 digit products on tcgen05 (Ozaki scheme); "
+                   "the headline value stays native FP64")
+    return out
+
+
 def cusolver_section(n, dev):
     """Context only: the vendor library (cuSOLVER through torch.linalg) on the
     same GPU and inputs (FP64), median of 3 after one warm-up."""
@@ -810,6 +909,7 @@ def run_gpu(args, rank, world, local_rank):
 
     others = routines_section(args.others_n, dev, sp) if args.others_n > 0 else None
     lowprec = lowprec_section(args.lowprec_n, dev, sp) if args.lowprec_n > 0 else None
+    emulated = emulated_section(args.oz_n, args.oz_slices, dev, sp) if args.oz_n > 0 else None
     graphs = graph_section(n, dev, sp) if args.graph else None
     cusolver = cusolver_section(n, dev) if args.cusolver else None
 
@@ -845,6 +945,7 @@ def run_gpu(args, rank, world, local_rank):
         "batched": batched,
         "other_routines": others,
         "lowprec_factorization": lowprec,
+        "fp64_emulated": emulated,
         "graph_replay": graphs,
         "cusolver_context": cusolver,
         "e2e": e2e,
@@ -885,6 +986,9 @@ def main():
                     help="order of the trtri/lauum/potri/getri/sygst section (0 skips it)")
     ap.add_argument("--lowprec-n", type=int, default=16384,
                     help="order of the low-precision factorization section (0 skips it)")
+    ap.add_argument("--oz-n", type=int, default=16384,
+                    help="order of the FP64-emulation section (0 skips)")
+    ap.add_argument("--oz-slices", type=int, default=7)
     ap.add_argument("--graph", type=int, default=1, help="time CUDA-graph replay of dpotrf/dgetrf (0 skips)")
     ap.add_argument("--cusolver", type=int, default=1, help="time torch.linalg (cuSOLVER) as context (0 skips)")
     args = ap.parse_args()
