@@ -30,14 +30,17 @@
 // normwise of the order of an FP64 GEMM's), and integer products are exact.
 //
 // Kernel (one CTA per SM, persistent over 128 x 64 output tiles in groups
-// of 8 row tiles for L2 reuse; 576 threads):
+// of 8 row tiles for L2 reuse; 640 threads):
 //   * warp 0, one lane: TMA loads.  Per 64-value k chunk, the S digit
 //     planes of op(B)'s 64 columns (S x 8 KB, double-buffered) and then
 //     op(A)'s S planes (16 KB each) through a 6-slot ring.
-//   * warp 1: allocates 512 TMEM columns (level L's 128 x 64 FP32
-//     accumulator at column 64 (L - 2)); one lane issues, per A plane s,
-//     the MMAs (M 128, N 64, K 16) with every B plane t <= S + 1 - s.
-//   * warps 2-17: drain the level accumulators (each warp a 32-lane quarter
+//   * warp 1 allocates 512 TMEM columns (level L's 128 x 64 FP32
+//     accumulator at column 64 (L - 2)); one lane of each of warps 1-3
+//     issues, per A plane s, the MMAs (M 128, N 64, K 16) with the B planes
+//     t <= S + 1 - s of the levels it owns (level_mask): one issuing thread
+//     does not keep the tensor pipe busy with 64-column MMAs (two are 28 %
+//     faster at 8192^3; three and four no faster than two).
+//   * warps 4-19: drain the level accumulators (each warp a 32-lane quarter
 //     and 16 columns), accumulate the integers, and write C.
 // Every mbarrier wait is bounded (RL_INFO_DEVICE_TIMEOUT on expiry).
 #include <cuda.h>
@@ -56,7 +59,9 @@ constexpr int A_TILE = BM * 128;             // 16 KB
 constexpr int B_TILE = BN * 128;             // 8 KB
 constexpr int A_SLOTS = 6;
 constexpr int EPI_WARPS = 16;
-constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr int ISSUERS = 3;                   // MMA-issuing warps (1 .. ISSUERS)
+constexpr int EPI0 = 1 + ISSUERS;            // first drain warp (0: TMA)
+constexpr int THREADS = 32 * EPI0 + 32 * EPI_WARPS;
 constexpr int TMEM_COLS = 512;
 constexpr int DRAIN = 2;                     // chunks per drain (128 values of k)
 constexpr int GROUP_M = 8;                   // row tiles per raster group
@@ -175,6 +180,27 @@ k_digits(int rows, int kdim, const double *X, i64 ldx, const unsigned long long 
     }
 }
 
+// Levels (bit L) owned by MMA-issuing thread i of ISSUERS: level L has
+// L - 1 digit pairs per chunk; largest first, each to the thread with the
+// fewest pairs so far (S = 7, 3 threads: {8, 3, 2} {7, 4} {6, 5}: 10, 9, 9).
+template <int S>
+__device__ __forceinline__ uint32_t level_mask(int i)
+{
+    int load[ISSUERS];
+    uint32_t mask = 0;
+#pragma unroll
+    for (int j = 0; j < ISSUERS; ++j) load[j] = 0;
+#pragma unroll
+    for (int L = S + 1; L >= 2; --L) {
+        int best = 0;
+#pragma unroll
+        for (int j = 1; j < ISSUERS; ++j) best = load[j] < load[best] ? j : best;
+        load[best] += L - 1;
+        if (best == i) mask |= 1u << L;
+    }
+    return mask;
+}
+
 // Tile t of the grouped raster: groups of GROUP_M row tiles, columns inside.
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int &tm, int &tn)
 {
@@ -207,11 +233,13 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtens
     const int tiles_total = tiles_m * tiles_n;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < A_SLOTS; ++i) { mbar_init(&afull[i], 1); mbar_init(&aempty[i], 1); }
-        for (int i = 0; i < 2; ++i) { mbar_init(&bfull[i], 1); mbar_init(&bempty[i], 1); }
-        mbar_init(&tfull, 1);
+        // the "empty", "full accumulator" and final barriers collect one
+        // commit from each MMA-issuing thread
+        for (int i = 0; i < A_SLOTS; ++i) { mbar_init(&afull[i], 1); mbar_init(&aempty[i], ISSUERS); }
+        for (int i = 0; i < 2; ++i) { mbar_init(&bfull[i], 1); mbar_init(&bempty[i], ISSUERS); }
+        mbar_init(&tfull, ISSUERS);
         mbar_init(&tempty, EPI_WARPS);
-        mbar_init(&final_bar, 1);
+        mbar_init(&final_bar, ISSUERS);
         s_err = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -265,9 +293,12 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtens
                 (void)mbar_wait(&afull[g % A_SLOTS], (g / A_SLOTS) & 1, limit_ns);
             for (int g = (gb > 2 ? gb - 2 : 0); g < gb; ++g) (void)mbar_wait(&bfull[g & 1], (g >> 1) & 1, limit_ns);
         }
-    } else if (warp == 1) {
+    } else if (warp <= ISSUERS) {
+        // the issuing threads split the levels (each level's MMAs stay in one
+        // thread's program order) into equal numbers of digit pairs per chunk
         if (lane == 0) {
             constexpr uint32_t ID = idesc(1u, BM, BN);      // BF16 operands, FP32 accumulators
+            const uint32_t mine = level_mask<S>(warp - 1);
             int ga = 0, gb = 0, di = 0;
             bool fail = false;
             for (int t = blockIdx.x; t < tiles_total && !fail; t += gridDim.x) {
@@ -283,7 +314,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtens
                     const int bb = gb & 1;
                     if (!mbar_wait(&bfull[bb], (gb >> 1) & 1, limit_ns)) { atomicExch(&s_err, 1); fail = true; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t sb = su32(bbuf + bb * S * B_TILE);
+                    const uint64_t db0 = sdesc(su32(bbuf + bb * S * B_TILE));
                     for (int s = 0; s < S; ++s, ++ga) {
                         const int slot = ga % A_SLOTS;
                         if (!mbar_wait(&afull[slot], (ga / A_SLOTS) & 1, limit_ns)) {
@@ -292,14 +323,17 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtens
                             break;
                         }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint32_t sa = su32(aring + slot * A_TILE);
-                        // digit pairs (s + 1, t + 1) with (s + 1) + (t + 1) <= S + 1: level L = s + t + 2
+                        const uint64_t da = sdesc(su32(aring + slot * A_TILE));
+                        // digit pairs (s + 1, t + 1) with (s + 1) + (t + 1) <= S + 1: level L = s + t + 2;
+                        // a descriptor's address field counts 16 bytes, so +2 per 16 values of k
                         for (int t2 = 0; t2 + s + 2 <= LMAX; ++t2) {
+                            if (!((mine >> (s + t2 + 2)) & 1u)) continue;
                             const uint32_t d = tmem + (uint32_t)((s + t2) * BN);
+                            const uint64_t db = db0 + (uint64_t)(t2 * (B_TILE >> 4));
 #pragma unroll
                             for (int kk = 0; kk < KC / 16; ++kk) {
                                 const uint32_t acc = (first && s == 0 && kk == 0) ? 0u : 1u;
-                                mma<true>(d, sdesc(sa + kk * 32), sdesc(sb + t2 * B_TILE + kk * 32), ID, acc);
+                                mma<true>(d, da + 2 * kk, db + 2 * kk, ID, acc);
                             }
                         }
                         mma_commit(&aempty[slot]);
@@ -318,8 +352,8 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtens
         }
     } else {
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and columns
-        // 16 ((w - 2) / 4) .. + 15 of every level
-        const int q = warp & 3, cb = (warp - 2) >> 2;
+        // 16 ((w - EPI0) / 4) .. + 15 of every level
+        const int q = warp & 3, cb = (warp - EPI0) >> 2;
         const int ndrain = (nch + DRAIN - 1) / DRAIN;
         int di = 0;
         bool fail = false;
