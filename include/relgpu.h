@@ -558,6 +558,15 @@ int64_t rl_get_param(int key);
 
 /* Number of kernels this library has launched in this process (host-side
  * count, for accounting in benchmarks). */
+/* rl_clear_cache: release what the library keeps between calls: the
+ * internal low-priority stream of each device used by the lookahead of the
+ * LU/Cholesky recursions (synchronized, then destroyed), the calling
+ * thread's lookahead events, and the trace's event pool (tracing stops).
+ * Each is created again on first use.  Not to be called while another
+ * thread has a library call in flight.  RL_SUCCESS or RL_ERR_CUDA (the first
+ * CUDA error met; the rest is released anyway).  Other host threads' event
+ * pools are not reachable from here and stay until the process ends. */
+int rl_clear_cache(void);
 uint64_t rl_launch_count(void);
 
 /* ---------------------------------------------------------------------------

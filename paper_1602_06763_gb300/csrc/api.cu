@@ -1416,6 +1416,38 @@ int64_t rl_get_param(int key)
 
 uint64_t rl_launch_count(void) { return g_launches.load(); }
 
+int rl_clear_cache(void)
+{
+    cudaError_t first = cudaSuccess;
+    auto keep = [&](cudaError_t e) { if (first == cudaSuccess && e != cudaSuccess) first = e; };
+    int cur = 0;
+    keep(cudaGetDevice(&cur));
+    {
+        std::lock_guard<std::mutex> lock(g_side_mu);
+        for (int dev = 0; dev < 128; ++dev) {
+            LaEvents &e = t_ev[dev];
+            if (g_side[dev] == nullptr && !e.ready) continue;
+            keep(cudaSetDevice(dev));
+            if (g_side[dev] != nullptr) {
+                keep(cudaStreamSynchronize(g_side[dev]));
+                keep(cudaStreamDestroy(g_side[dev]));
+                g_side[dev] = nullptr;
+            }
+            if (e.ready) {
+                for (int i = 0; i < LA_DEPTH; ++i) {
+                    keep(cudaEventDestroy(e.start[i]));
+                    keep(cudaEventDestroy(e.done[i]));
+                    e.start[i] = e.done[i] = nullptr;
+                }
+                e.ready = false;
+            }
+        }
+    }
+    keep(cudaSetDevice(cur));
+    keep(trace_release());
+    return first == cudaSuccess ? RL_SUCCESS : RL_ERR_CUDA;
+}
+
 const char *rl_status_string(int status)
 {
     if (status < 0) return "illegal argument (LAPACK numbering: argument -status)";

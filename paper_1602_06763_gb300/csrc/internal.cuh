@@ -113,6 +113,7 @@ enum Kind {
     K_PANEL, K_LASWP, K_RESID, K_CONVERT, K_MIX, K_BATCH, K_FLOW, K_TRANS, K_COUNT
 };
 extern std::atomic<int> g_trace_on;
+cudaError_t trace_release();
 // Bracket one kernel launch: with tracing on, CUDA events are recorded on the
 // launch stream around it and the launch's algorithmic flops and bytes are
 // attributed to its kind.  The destructor counts the launch and records the

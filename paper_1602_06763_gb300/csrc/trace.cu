@@ -107,6 +107,27 @@ int rl_trace_enable(int on)
 
 int rl_trace_kinds(void) { return K_COUNT; }
 
+}  // extern "C"
+
+namespace rl {
+// Tracing off, pending records read, pooled events destroyed.
+cudaError_t trace_release()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_trace_on.store(0);
+    drain_locked();
+    cudaError_t first = cudaSuccess;
+    for (cudaEvent_t e : g_pool) {
+        const cudaError_t r = cudaEventDestroy(e);
+        if (first == cudaSuccess) first = r;
+    }
+    g_pool.clear();
+    return first;
+}
+}  // namespace rl
+
+extern "C" {
+
 int rl_trace_read(int kind, const char **name, uint64_t *launches, double *ms, double *flops,
                   double *bytes)
 {

@@ -63,6 +63,7 @@ _SIGS = {
     "rl_spotrf_tc_work_size": (ctypes.c_size_t, [_i64, ctypes.c_int]),
     "rl_sgetrf_tc_work_size": (ctypes.c_size_t, [_i64, _i64, ctypes.c_int]),
     "rl_spotrf_tc": (ctypes.c_int, [ctypes.c_int, _ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_clear_cache": (ctypes.c_int, []),
     "rl_oz_work_size": (_sz, [_i64, _i64, _i64, ctypes.c_int]),
     "rl_dgemm_oz": (ctypes.c_int, [ctypes.c_int, _ch, _ch, _i64, _i64, _i64, ctypes.c_double, _vp, _i64, _vp,
                                    _i64, ctypes.c_double, _vp, _i64, _vp, _sz, _vp]),
@@ -239,6 +240,10 @@ def rl_zpotrf(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
 
 def rl_zgetrf(m, n, A, lda, ipiv, info, work, lwork, stream=None):
     return _lib.rl_zgetrf(m, n, _ptr(A), lda, _ptr(ipiv), _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_clear_cache():
+    return _lib.rl_clear_cache()
 
 
 def rl_oz_work_size(m, n, k, slices):

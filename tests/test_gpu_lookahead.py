@@ -85,3 +85,20 @@ def test_fp32_and_precision_form_lookahead_bit_identical():
     (x0, it0, f0), (x1, it1, f1) = both(dsposv)
     assert f0 == f1 == 0 and it0 == it1 >= 0
     assert np.array_equal(x0, x1)
+
+
+def test_clear_cache_releases_and_recreates_the_side_stream():
+    """rl_clear_cache destroys the lookahead stream and events and the trace
+    pool; the next call creates them again and gives the same bits."""
+    r = G.lib()
+    assert r.rl_set_param(r.RL_PARAM_LOOKAHEAD, 1) == 0
+    n = 2100
+    A = inputs.uniform(n, n, seed=inputs.seed_for(1, 1500))
+    F0, p0, _ = G.getrf(A)
+    r.rl_trace_enable(1)
+    G.getrf(A)
+    assert r.rl_clear_cache() == 0
+    F1, p1, _ = G.getrf(A)
+    assert np.array_equal(p0, p1) and np.array_equal(F0, F1)
+    assert r.rl_clear_cache() == 0
+    assert r.rl_clear_cache() == 0                # nothing left to release
