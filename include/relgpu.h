@@ -137,7 +137,9 @@ int rl_dpotri(char uplo, int64_t n, double *A, int64_t lda, int32_t *info,
 /* ---------------------------------------------------------------------------
  * Solves with computed factors (Section 5 lists xgetrf and xpotrf as the
  * building blocks of xgesv and xposv).  B (n x nrhs) is overwritten by X.
- *   rl_dgetrs: trans 'N' only; A and ipiv from rl_dgetrf: X = U^{-1} L^{-1} P B.
+ *   rl_dgetrs: A and ipiv from rl_dgetrf: X = U^{-1} L^{-1} P B (trans 'N'),
+ *     or X = P^T L^{-T} U^{-T} B (trans 'T' or 'C': A^T X = B; always the
+ *     recursive TRSM, then the interchanges last first).
  *     Argument numbers: 1 trans, 2 n, 3 nrhs, 4 A, 5 lda, 6 ipiv, 7 B, 8 ldb.
  *   rl_dpotrs: A from rl_dpotrf: X = L^{-T} L^{-1} B ('L') or U^{-1} U^{-T} B ('U').
  *     Argument numbers: 1 uplo, 2 n, 3 nrhs, 4 A, 5 lda, 6 B, 7 ldb.
@@ -252,6 +254,15 @@ int rl_zpotrf(char uplo, int64_t n, rl_double_complex *A, int64_t lda, int32_t *
               void *work, size_t lwork, rl_stream_t stream);
 int rl_zgetrf(int64_t m, int64_t n, rl_double_complex *A, int64_t lda, int32_t *ipiv,
               int32_t *info, void *work, size_t lwork, rl_stream_t stream);
+/* rl_zgetrs (trans 'N'; 'T'/'C' return RL_ERR_UNSUPPORTED) and rl_zpotrs
+ * (uplo 'L': X = L^{-H} L^{-1} B; 'U': U^{-1} U^{-H} B): the solves of
+ * rl_dgetrs / rl_dpotrs for the complex factors, by the recursive TRSM
+ * (work and lwork are accepted and ignored).  Argument numbers as there. */
+int rl_zgetrs(char trans, int64_t n, int64_t nrhs, const rl_double_complex *A, int64_t lda,
+              const int32_t *ipiv, rl_double_complex *B, int64_t ldb, void *work, size_t lwork,
+              rl_stream_t stream);
+int rl_zpotrs(char uplo, int64_t n, int64_t nrhs, const rl_double_complex *A, int64_t lda,
+              rl_double_complex *B, int64_t ldb, void *work, size_t lwork, rl_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * FP64 updates emulated on the BF16 tensor cores (the Ozaki scheme; not in

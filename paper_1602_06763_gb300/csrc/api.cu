@@ -570,6 +570,7 @@ int rl_zgetrf(int64_t m, int64_t n, rl_double_complex *A, int64_t lda, int32_t *
     return finish(c);
 }
 
+
 // ---- FP64 factorizations with emulated FP64 updates ---------------------------------
 // The recursions of rl_dpotrf / rl_dgetrf with every FP64 GEMM/SYRK update of
 // order >= RL_PARAM_OZ_MIN (m, n and k) emulated on the BF16 tensor cores
@@ -830,22 +831,32 @@ int rl_sgemm_tc(int prec, char transa, char transb, int64_t m, int64_t n, int64_
 // solve; otherwise the recursive TRSM.
 template <typename T>
 static int trs_t(bool lu, int64_t n, int64_t nrhs, const T *A, int64_t lda, const int32_t *ipiv, T *B,
-                 int64_t ldb, void *work, size_t lwork, rl_stream_t stream, bool up = false)
+                 int64_t ldb, void *work, size_t lwork, rl_stream_t stream, bool up = false, bool trans = false)
 {
     if (n == 0 || nrhs == 0) return RL_SUCCESS;
     if (A == nullptr || B == nullptr || (lu && ipiv == nullptr)) return RL_ERR_NULL_POINTER;
-    const bool flow = work != nullptr && nrhs <= FLOW_MAX_NRHS;
+    // the one-launch flow solve covers the real 'N' forms; the others recurse
+    const bool flow = !is_cplx<T>::value && !trans && work != nullptr && nrhs <= FLOW_MAX_NRHS;
     if (flow && lwork < flow_ws_bytes(n, nrhs)) return RL_ERR_WORKSPACE;
     Ctx c = make_ctx(stream, nullptr, work, lwork);
     // 'U' (Cholesky only): the factor U is transposed in place to L = U^T for
     // the solves and restored before the call returns
     T *Aw = const_cast<T *>(A);
     if (up) uplo_swap<T>(c, n, Aw, lda);
+    if (lu && trans) {
+        // A^T X = B with P A = L U: U^T Y = B, L^T Z = Y, X = P^T Z
+        trsm_lut<T>(c, n, nrhs, T(1), A, lda, B, ldb);
+        trsm_llt_u<T>(c, true, n, nrhs, T(1), A, lda, B, ldb);
+        laswp_rev<T>(c, B, ldb, n, nrhs, ipiv);
+        return finish(c);
+    }
     if (lu) laswp<T>(c, B, ldb, n, 0, nrhs, 0, n, ipiv);
     if (flow) {
-        note(c, cudaMemsetAsync(work, 0, sizeof(int32_t), c.s));
-        trsm_flow<T>(c, FLOW_LN, lu, n, nrhs, A, lda, B, ldb, work);
-        trsm_flow<T>(c, lu ? FLOW_UN : FLOW_LT, false, n, nrhs, A, lda, B, ldb, work);
+        if constexpr (!is_cplx<T>::value) {
+            note(c, cudaMemsetAsync(work, 0, sizeof(int32_t), c.s));
+            trsm_flow<T>(c, FLOW_LN, lu, n, nrhs, A, lda, B, ldb, work);
+            trsm_flow<T>(c, lu ? FLOW_UN : FLOW_LT, false, n, nrhs, A, lda, B, ldb, work);
+        }
     } else if (lu) {
         trsm_lln<T>(c, true, n, nrhs, T(1), A, lda, B, ldb);
         trsm_lun<T>(c, n, nrhs, T(1), A, lda, B, ldb);
@@ -963,8 +974,7 @@ int rl_dgetrs(char trans, int64_t n, int64_t nrhs, const double *A, int64_t lda,
     if (nrhs < 0) return -3;
     if (lda < imax1(n)) return -5;
     if (ldb < imax1(n)) return -8;
-    if (is_t(trans)) return RL_ERR_UNSUPPORTED;
-    return trs_t<double>(true, n, nrhs, A, lda, ipiv, B, ldb, work, lwork, stream);
+    return trs_t<double>(true, n, nrhs, A, lda, ipiv, B, ldb, work, lwork, stream, false, is_t(trans));
 }
 
 int rl_dpotrs(char uplo, int64_t n, int64_t nrhs, const double *A, int64_t lda, double *B, int64_t ldb,
@@ -986,8 +996,7 @@ int rl_sgetrs(char trans, int64_t n, int64_t nrhs, const float *A, int64_t lda, 
     if (nrhs < 0) return -3;
     if (lda < imax1(n)) return -5;
     if (ldb < imax1(n)) return -8;
-    if (is_t(trans)) return RL_ERR_UNSUPPORTED;
-    return trs_t<float>(true, n, nrhs, A, lda, ipiv, B, ldb, work, lwork, stream);
+    return trs_t<float>(true, n, nrhs, A, lda, ipiv, B, ldb, work, lwork, stream, false, is_t(trans));
 }
 
 int rl_spotrs(char uplo, int64_t n, int64_t nrhs, const float *A, int64_t lda, float *B, int64_t ldb,
@@ -999,6 +1008,31 @@ int rl_spotrs(char uplo, int64_t n, int64_t nrhs, const float *A, int64_t lda, f
     if (lda < imax1(n)) return -5;
     if (ldb < imax1(n)) return -7;
     return trs_t<float>(false, n, nrhs, A, lda, nullptr, B, ldb, work, lwork, stream, is_u(uplo));
+}
+
+int rl_zgetrs(char trans, int64_t n, int64_t nrhs, const rl_double_complex *A, int64_t lda, const int32_t *ipiv,
+              rl_double_complex *B, int64_t ldb, void *work, size_t lwork, rl_stream_t stream)
+{
+    if (trans != 'N' && trans != 'n' && trans != 'T' && trans != 't' && trans != 'C' && trans != 'c') return -1;
+    if (n < 0) return -2;
+    if (nrhs < 0) return -3;
+    if (lda < (n > 1 ? n : 1)) return -5;
+    if (ldb < (n > 1 ? n : 1)) return -8;
+    if (trans != 'N' && trans != 'n') return RL_ERR_UNSUPPORTED;
+    return trs_t<cplx>(true, n, nrhs, reinterpret_cast<const cplx *>(A), lda, ipiv, reinterpret_cast<cplx *>(B),
+                       ldb, work, lwork, stream);
+}
+
+int rl_zpotrs(char uplo, int64_t n, int64_t nrhs, const rl_double_complex *A, int64_t lda, rl_double_complex *B,
+              int64_t ldb, void *work, size_t lwork, rl_stream_t stream)
+{
+    if (!is_l(uplo) && !is_u(uplo)) return -1;
+    if (n < 0) return -2;
+    if (nrhs < 0) return -3;
+    if (lda < (n > 1 ? n : 1)) return -5;
+    if (ldb < (n > 1 ? n : 1)) return -7;
+    return trs_t<cplx>(false, n, nrhs, reinterpret_cast<const cplx *>(A), lda, nullptr, reinterpret_cast<cplx *>(B),
+                       ldb, work, lwork, stream, is_u(uplo));
 }
 
 // ---- precision form ------------------------------------------------------------

@@ -805,18 +805,43 @@ void trsm_rlt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
     trsm_rlt<T>(c, m, n2, T(1), L + n1 + n1 * ldl, ldl, B + n1 * ldb, ldb);
 }
 
+// B := L^{-T} B (complex: L^{-H}); unit: L's diagonal is taken as 1.
 template <typename T>
-void trsm_llt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
+void trsm_llt_u(Ctx &c, bool unit, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
 {
     if (m <= 0 || n <= 0) return;
     if (m <= TRX_NB) {
-        launch_tri<T, TRI_BWD, false, false, false>(c, K_TRSM, n, (int)m, alpha, L, ldl, B, ldb);
+        constexpr bool CJ = is_cplx<T>::value;
+        if (unit) launch_tri<T, TRI_BWD, false, true, false, CJ>(c, K_TRSM, n, (int)m, alpha, L, ldl, B, ldb);
+        else launch_tri<T, TRI_BWD, false, false, false, CJ>(c, K_TRSM, n, (int)m, alpha, L, ldl, B, ldb);
         return;
     }
     const i64 m1 = split_q(m, TRX_NB), m2 = m - m1;
-    trsm_llt<T>(c, m2, n, alpha, L + m1 + m1 * ldl, ldl, B + m1, ldb);
+    trsm_llt_u<T>(c, unit, m2, n, alpha, L + m1 + m1 * ldl, ldl, B + m1, ldb);
     gemm<T>(c, true, false, m1, n, m2, T(-1), L + m1, ldl, B + m1, ldb, alpha, B, ldb);
-    trsm_llt<T>(c, m1, n, T(1), L, ldl, B, ldb);
+    trsm_llt_u<T>(c, unit, m1, n, T(1), L, ldl, B, ldb);
+}
+
+template <typename T>
+void trsm_llt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
+{
+    trsm_llt_u<T>(c, false, m, n, alpha, L, ldl, B, ldb);
+}
+
+// B := U^{-T} B, U upper non-unit (forward substitution with U^T, staged
+// as a lower triangle by the leaf kernel).
+template <typename T>
+void trsm_lut(Ctx &c, i64 m, i64 n, T alpha, const T *U, i64 ldu, T *B, i64 ldb)
+{
+    if (m <= 0 || n <= 0) return;
+    if (m <= TRX_NB) {
+        launch_tri<T, TRI_FWD, false, false, true>(c, K_TRSM, n, (int)m, alpha, U, ldu, B, ldb);
+        return;
+    }
+    const i64 m1 = split_q(m, TRX_NB), m2 = m - m1;
+    trsm_lut<T>(c, m1, n, alpha, U, ldu, B, ldb);
+    gemm<T>(c, true, false, m2, n, m1, T(-1), U + m1 * ldu, ldu, B, ldb, alpha, B + m1, ldb);
+    trsm_lut<T>(c, m2, n, T(1), U + m1 + m1 * ldu, ldu, B + m1, ldb);
 }
 
 template <typename T>
@@ -899,6 +924,8 @@ void trsm_run(Ctx &c, i64 m, i64 n, T alpha, const T *U, i64 ldu, T *B, i64 ldb)
     template void trsm_lln<T>(Ctx &, bool, i64, i64, T, const T *, i64, T *, i64);                \
     template void trsm_rlt<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);                      \
     template void trsm_llt<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);                      \
+    template void trsm_llt_u<T>(Ctx &, bool, i64, i64, T, const T *, i64, T *, i64);              \
+    template void trsm_lut<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);                      \
     template void trsm_lun<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);                      \
     template void trmm_rln<T>(Ctx &, bool, i64, i64, T, const T *, i64, T *, i64);                \
     template void trmm_llt<T>(Ctx &, i64, i64, T, const T *, i64, T *, i64);                      \
@@ -912,5 +939,7 @@ template void gemm<cplx>(Ctx &, bool, bool, i64, i64, i64, cplx, const cplx *, i
                          cplx *, i64, bool);
 template void trsm_lln<cplx>(Ctx &, bool, i64, i64, cplx, const cplx *, i64, cplx *, i64);
 template void trsm_rlt<cplx>(Ctx &, i64, i64, cplx, const cplx *, i64, cplx *, i64);
+template void trsm_llt<cplx>(Ctx &, i64, i64, cplx, const cplx *, i64, cplx *, i64);
+template void trsm_lun<cplx>(Ctx &, i64, i64, cplx, const cplx *, i64, cplx *, i64);
 
 }  // namespace rl

@@ -814,10 +814,69 @@ void laswp(Ctx &c, T *A0, i64 lda, i64 m, i64 c0, i64 ncols, i64 k1, i64 k2, con
     }
 }
 
+// ----------------------------------------------------------------------------
+// Reverse interchanges (getrs with trans = 'T': X = P^T Z).  One CTA per
+// column: the column is staged in shared memory when it fits (n <= 24576),
+// one thread walks the interchanges last first (ipiv staged 1024 at a time),
+// then the column is written back; larger orders swap in global memory.
+// ----------------------------------------------------------------------------
+constexpr int LSR_MAX_N = 24576;
+constexpr int LSR_IPIV = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_laswp_rev(T *B, i64 ldb, int n, const int32_t *ipiv, int staged)
+{
+    extern __shared__ __align__(16) unsigned char lsr_raw[];
+    __shared__ int piv[LSR_IPIV];
+    T *col = reinterpret_cast<T *>(lsr_raw);
+    T *bj = B + (i64)blockIdx.x * ldb;
+    if (staged) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = bj[i];
+    }
+    for (int hi = n; hi > 0; hi -= LSR_IPIV) {
+        const int lo = hi - LSR_IPIV > 0 ? hi - LSR_IPIV : 0;
+        __syncthreads();
+        for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) piv[i - lo] = ipiv[i] - 1;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            T *v = staged ? col : bj;
+            for (int i = hi - 1; i >= lo; --i) {
+                const int p = piv[i - lo];
+                if (p != i && p >= 0 && p < n) { const T t = v[i]; v[i] = v[p]; v[p] = t; }
+            }
+        }
+    }
+    __syncthreads();
+    if (staged) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) bj[i] = col[i];
+    }
+}
+
+template <typename T>
+void laswp_rev(Ctx &c, T *B, i64 ldb, i64 n, i64 ncols, const int32_t *ipiv)
+{
+    if (n <= 1 || ncols <= 0) return;
+    const bool staged = n <= LSR_MAX_N;
+    const size_t smem = staged ? (size_t)n * sizeof(T) : 0;
+    static bool attr = false;
+    if (!attr) {
+        note(c, cudaFuncSetAttribute(k_laswp_rev<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(LSR_MAX_N * sizeof(T))));
+        attr = true;
+    }
+    Launch L(c, K_LASWP, 0.0, 4.0 * sizeof(T) * (double)n * ncols);
+    for (i64 c0 = 0; c0 < ncols; c0 += 65535) {
+        const i64 nc = ncols - c0 < 65535 ? ncols - c0 : 65535;
+        k_laswp_rev<T><<<(unsigned)nc, 256, smem, c.s>>>(B + c0 * ldb, ldb, (int)n, ipiv, staged ? 1 : 0);
+    }
+}
+
 #define RL_INST_FACTOR(T)                                                                   \
     template void potf2<T>(Ctx &, i64, T *, i64, i64);                                     \
     template void getf2_panel<T>(Ctx &, i64, i64, T *, i64, int32_t *, i64);               \
-    template void laswp<T>(Ctx &, T *, i64, i64, i64, i64, i64, i64, const int32_t *);
+    template void laswp<T>(Ctx &, T *, i64, i64, i64, i64, i64, i64, const int32_t *);      \
+    template void laswp_rev<T>(Ctx &, T *, i64, i64, i64, const int32_t *);
 RL_INST_FACTOR(double)
 RL_INST_FACTOR(float)
 template void getf2_panel<cplx>(Ctx &, i64, i64, cplx *, i64, int32_t *, i64);

@@ -173,6 +173,16 @@ void trsm_llt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
 // B(m x n) := alpha * U^{-1} B, U upper m x m, non-unit.
 template <typename T>
 void trsm_lun(Ctx &c, i64 m, i64 n, T alpha, const T *U, i64 ldu, T *B, i64 ldb);
+// B := L^{-T} B with a unit (unit = true) or non-unit lower L (complex: L^{-H})
+template <typename T>
+void trsm_llt_u(Ctx &c, bool unit, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb);
+// B := U^{-T} B, U upper non-unit
+template <typename T>
+void trsm_lut(Ctx &c, i64 m, i64 n, T alpha, const T *U, i64 ldu, T *B, i64 ldb);
+// Row interchanges ipiv[n-1], ..., ipiv[0] (1-based) applied to the ncols
+// columns of B, last first (P^T B for P from getrf).
+template <typename T>
+void laswp_rev(Ctx &c, T *B, i64 ldb, i64 n, i64 ncols, const int32_t *ipiv);
 // B(m x n) := alpha * U B, U upper m x m, non-unit.
 template <typename T>
 void trmm_lun(Ctx &c, i64 m, i64 n, T alpha, const T *U, i64 ldu, T *B, i64 ldb);

@@ -59,6 +59,8 @@ _SIGS = {
     "rl_trs_work_size": (ctypes.c_size_t, [_i64, _i64]),
     "rl_dlaswp": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _vp, _vp]),
     "rl_zpotrf": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_zgetrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _sz, _vp]),
+    "rl_zpotrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
     "rl_zgetrf": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
     "rl_spotrf_tc_work_size": (ctypes.c_size_t, [_i64, ctypes.c_int]),
     "rl_sgetrf_tc_work_size": (ctypes.c_size_t, [_i64, _i64, ctypes.c_int]),
@@ -236,6 +238,15 @@ def rl_dtrmm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream=None)
 
 def rl_zpotrf(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
     return _lib.rl_zpotrf(_c(uplo), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_zgetrs(trans, n, nrhs, A, lda, ipiv, B, ldb, work=None, lwork=0, stream=None):
+    return _lib.rl_zgetrs(_c(trans), n, nrhs, _ptr(A), lda, _ptr(ipiv), _ptr(B), ldb, _ptr(work), lwork,
+                          _stream(stream))
+
+
+def rl_zpotrs(uplo, n, nrhs, A, lda, B, ldb, work=None, lwork=0, stream=None):
+    return _lib.rl_zpotrs(_c(uplo), n, nrhs, _ptr(A), lda, _ptr(B), ldb, _ptr(work), lwork, _stream(stream))
 
 
 def rl_zgetrf(m, n, A, lda, ipiv, info, work, lwork, stream=None):

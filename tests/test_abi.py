@@ -89,7 +89,7 @@ def test_host_logic_of_the_other_routines(built):
     assert r.rl_spotri("L", 4, 8, 3, 8, stream=0) == -4
     assert r.rl_sgemm("X", "N", 4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, stream=0) == -1
     assert r.rl_ssyrk("U", "N", 4, 4, 1.0, 8, 4, 0.0, 8, 4, stream=0) == r.RL_ERR_UNSUPPORTED
-    assert r.rl_dgetrs("T", 4, 1, 8, 4, 8, 8, 4, stream=0) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_dgetrs("X", 4, 1, 8, 4, 8, 8, 4, stream=0) == -1
     assert r.rl_dpotrs("L", 4, 1, 8, 3, 8, 4, stream=0) == -5
     assert r.rl_set_param(r.RL_PARAM_TRI_LANES, 3) == r.RL_ERR_PARAM
     assert r.rl_get_param(r.RL_PARAM_TRI_LANES) == 0
