@@ -843,12 +843,14 @@ static int trs_t(bool lu, int64_t n, int64_t nrhs, const T *A, int64_t lda, cons
     // the solves and restored before the call returns
     T *Aw = const_cast<T *>(A);
     if (up) uplo_swap<T>(c, n, Aw, lda);
-    if (lu && trans) {
-        // A^T X = B with P A = L U: U^T Y = B, L^T Z = Y, X = P^T Z
-        trsm_lut<T>(c, n, nrhs, T(1), A, lda, B, ldb);
-        trsm_llt_u<T>(c, true, n, nrhs, T(1), A, lda, B, ldb);
-        laswp_rev<T>(c, B, ldb, n, nrhs, ipiv);
-        return finish(c);
+    if constexpr (!is_cplx<T>::value) {
+        if (lu && trans) {
+            // A^T X = B with P A = L U: U^T Y = B, L^T Z = Y, X = P^T Z
+            trsm_lut<T>(c, n, nrhs, T(1), A, lda, B, ldb);
+            trsm_llt_u<T>(c, true, n, nrhs, T(1), A, lda, B, ldb);
+            laswp_rev<T>(c, B, ldb, n, nrhs, ipiv);
+            return finish(c);
+        }
     }
     if (lu) laswp<T>(c, B, ldb, n, 0, nrhs, 0, n, ipiv);
     if (flow) {
