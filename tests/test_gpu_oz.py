@@ -196,3 +196,41 @@ def test_getrf_oz_dyadic_exact(oz_min_64):
     assert info == 0
     assert np.array_equal(ipiv, inputs.expected_ipiv(perm))
     assert np.array_equal(np.tril(F, -1) + np.eye(n), L) and np.array_equal(np.triu(F), U)
+
+
+@pytest.mark.parametrize("S,bound", [(6, 200.0), (8, 10.0)])
+def test_potrf_oz_other_slices(S, bound, oz_min_64):
+    """6 planes carry 48 bits (a bound 56 times looser than 7 planes'); 8
+    planes carry 64."""
+    n = 700
+    A = inputs.spd_bbt(n, seed=inputs.seed_for(1, 7700 + S))
+    L, info = potrf_oz(A, S=S)
+    assert info == 0
+    assert oracle.res_chol(A, np.tril(L)) <= bound
+
+
+def test_potrf_oz_upper(oz_min_64):
+    r = G.lib()
+    t = G.torch()
+    n = 600
+    Lx = inputs.integer_chol(n, seed=inputs.seed_for(1, 7800))
+    A = inputs.product_lower(Lx)
+    A0 = np.asfortranarray(np.triu(A) + np.tril(np.full((n, n), 7.5), -1))
+    d = G.DevMat(A0)
+    info = G.int_buf(1, -77)
+    lw = r.rl_dpotrf_oz_work_size(n, 7)
+    w = t.empty(lw, dtype=t.uint8, device="cuda")
+    assert r.rl_dpotrf_oz(7, "U", n, d.ptr(), n, info.data_ptr(), w, lw) == 0
+    G.sync()
+    assert int(info[0]) == 0
+    X = d.get()
+    assert np.array_equal(np.triu(X), np.triu(Lx.T))
+    assert np.array_equal(np.tril(X, -1), np.tril(A0, -1))
+
+
+def test_getrf_oz_wide(oz_min_64):
+    m, n = 400, 1000
+    A = inputs.uniform(m, n, seed=inputs.seed_for(1, 7900))
+    F, ipiv, info = getrf_oz(A)
+    assert info == 0
+    assert oracle.res_lu(A, F, ipiv) <= 10.0
