@@ -70,14 +70,16 @@ constexpr int EXP_NONFINITE = 4096;          // exponent marker of a row with In
 template <int S>
 constexpr int smem_bytes() { return 2 * S * B_TILE + A_SLOTS * A_TILE + 1024; }
 
-// Exponent e with max < 2^(e-1) from the bit pattern of max >= 0.
+// Exponent e with max < 2^(e-1) from the bit pattern of max >= 0: with max
+// in [2^(x-1), 2^x), e = x + 1 (x = E - 1022 for a normal number of biased
+// exponent E; a subnormal f 2^-1074 has x = 63 - clz(f) - 1073).
 __device__ __forceinline__ int exp_of_max(unsigned long long b)
 {
     if (b == 0) return 0;
     if (b >= 0x7FF0000000000000ull) return EXP_NONFINITE;
-    int ex;
-    (void)frexp(__longlong_as_double((long long)b), &ex);   // max in [2^(ex-1), 2^ex)
-    return ex + 1;
+    const int E = (int)(b >> 52);
+    if (E != 0) return E - 1021;
+    return -1009 - __clzll((long long)b);
 }
 
 // |X| maxima of the rows of op(X) (rows x kdim) as bit patterns, folded
@@ -152,8 +154,10 @@ k_digits(int rows, int kdim, const double *X, i64 ldx, const unsigned long long 
          int rows_p, int kp)
 {
     __shared__ double tile[32][33];
+    __shared__ int erow[32];
     const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    if (threadIdx.x < 32) erow[threadIdx.x] = (r0 + (int)threadIdx.x < rows) ? exp_of_max(mx[r0 + threadIdx.x]) : 0;
     for (int yy = ty; yy < 32; yy += 8) {
         double v = 0.0;
         if (!TR) {
@@ -171,7 +175,7 @@ k_digits(int rows, int kdim, const double *X, i64 ldx, const unsigned long long 
     for (int yy = ty; yy < 32; yy += 8) {
         const int r = r0 + yy, k = k0 + tx;
         if (r >= rows_p || k >= kp) continue;
-        const int e = r < rows ? exp_of_max(mx[r]) : 0;
+        const int e = erow[yy];
         int d[S];
         digits_of<S>(tile[tx][yy], e, d);
         const size_t o = (size_t)r * kp + k;
