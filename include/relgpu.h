@@ -288,7 +288,9 @@ int rl_zpotrs(char uplo, int64_t n, int64_t nrhs, const rl_double_complex *A, in
  *     results, info and ipiv semantics (within the scheme's error);
  *     workspace rl_dpotrf_oz_work_size(n, slices) /
  *     rl_dgetrf_oz_work_size(m, n, slices) (the LU's includes its panel
- *     workspace).  Argument numbers shift by one (1 = slices).
+ *     workspace; the Cholesky's holds two sets of digit planes, one for the
+ *     lookahead's side stream, whose updates then run beside the next
+ *     level's).  Argument numbers shift by one (1 = slices).
  * ------------------------------------------------------------------------- */
 size_t rl_oz_work_size(int64_t m, int64_t n, int64_t k, int slices);
 int rl_dgemm_oz(int slices, char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,

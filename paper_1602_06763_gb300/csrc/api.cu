@@ -93,7 +93,9 @@ static bool lookahead_resources(cudaStream_t *side, LaEvents **ev)
 // tensor-core updates pack into c.tcwork).
 static bool lookahead_ok(const Ctx &c)
 {
-    return g_params.lookahead && c.tcwork == nullptr && c.ozwork == nullptr;   // one packing workspace per call
+    // one packing workspace per stream: the tensor-core FP32 updates share
+    // one, the emulated FP64 updates may bring a second for the side stream
+    return g_params.lookahead && c.tcwork == nullptr && (c.ozwork == nullptr || c.ozwork2 != nullptr);
 }
 
 // ---- recursions -------------------------------------------------------------
@@ -128,6 +130,8 @@ static void potrf_rec_la(Ctx &c, i64 n, T *A, i64 lda, i64 off, cudaEvent_t pend
         note(c, cudaEventRecord(ev->start[depth], c.s));
         Ctx cs = c;
         cs.s = side;
+        cs.ozwork = c.ozwork2;
+        cs.ozlwork = c.ozlwork2;
         note(cs, cudaStreamWaitEvent(side, ev->start[depth], 0));
         const i64 nr = n2 - n2a;
         gemm<T>(cs, false, true, nr, n2a, n1, T(-1), A21 + n2a, lda, A21, lda, T(1), A22 + n2a, lda);
@@ -196,6 +200,8 @@ static void getrf_rec_la(Ctx &c, T *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r
         note(c, cudaEventRecord(ev->start[depth], c.s));
         Ctx cs = c;
         cs.s = side;
+        cs.ozwork = c.ozwork2;
+        cs.ozlwork = c.ozlwork2;
         note(cs, cudaStreamWaitEvent(side, ev->start[depth], 0));
         gemm<T>(cs, false, false, m2, n2 - n2a, n1, T(-1), A21, lda, A12 + n2a * lda, lda, T(1),
                 A22 + n2a * lda, lda);
@@ -620,10 +626,16 @@ static size_t oz_factor_bytes(int64_t m, int64_t n, int slices)
     return oz_work_bytes(big, big, h, slices);
 }
 
+// two halves: the caller's stream and the lookahead's side stream
+static size_t oz_potrf_half(int64_t n, int slices)
+{
+    return (oz_work_bytes(n / 2 + 64, n / 2 + 64, n / 2 + 64, slices) + 1023) & ~(size_t)1023;
+}
+
 size_t rl_dpotrf_oz_work_size(int64_t n, int slices)
 {
     if (n < 0 || !oz_slices_ok(slices)) return 0;
-    return oz_work_bytes(n / 2 + 64, n / 2 + 64, n / 2 + 64, slices);
+    return 2 * oz_potrf_half(n, slices);
 }
 
 size_t rl_dgetrf_oz_work_size(int64_t m, int64_t n, int slices)
@@ -645,8 +657,12 @@ int rl_dpotrf_oz(int slices, char uplo, int64_t n, double *A, int64_t lda, int32
     Ctx c = make_ctx(stream, info, nullptr, 0);
     c.abort = info;
     c.oz_slices = slices;
+    const size_t half = oz_potrf_half(n, slices);
     c.ozwork = work;
-    c.ozlwork = lwork;
+    c.ozlwork = half;
+    c.ozwork2 = n > 0 ? static_cast<char *>(work) + half : nullptr;
+    c.ozlwork2 = half;
+    c.oz_dynamic = true;
     note(c, cudaMemsetAsync(info, 0, sizeof(int32_t), c.s));
     const bool up = is_u(uplo);
     if (up) uplo_swap<double>(c, n, A, lda);

@@ -101,6 +101,12 @@ struct Ctx {
     int oz_slices = 0;
     void *ozwork = nullptr;
     size_t ozlwork = 0;
+    // a second slicing workspace for the lookahead's side stream (the two
+    // streams' emulated GEMMs then run at once), and one CTA per tile instead
+    // of one per SM, so that the other stream's kernels find SMs as tiles end
+    void *ozwork2 = nullptr;
+    size_t ozlwork2 = 0;
+    bool oz_dynamic = false;
 };
 
 int device_sms();

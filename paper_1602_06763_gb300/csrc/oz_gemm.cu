@@ -521,7 +521,7 @@ bool oz_gemm(Ctx &c, int S, bool ta, bool tb, i64 m, i64 n, i64 k, double alpha,
     }
     const int tiles_m = (int)(mp / oz::BM), tiles_n = (int)(np / oz::BN);
     const int tiles_total = tiles_m * tiles_n;
-    const unsigned grid = (unsigned)(tiles_total < c.num_sms ? tiles_total : c.num_sms);
+    const unsigned grid = (unsigned)(c.oz_dynamic || tiles_total < c.num_sms ? tiles_total : c.num_sms);
     const int nch = (int)(kp / oz::KC);
     const double flops = lower ? (double)k * n * (n + 1) : 2.0 * m * n * k;
     Launch L(c, lower ? K_SYRK : K_GEMM, flops, 0.0);
