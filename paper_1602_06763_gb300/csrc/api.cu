@@ -88,6 +88,22 @@ static bool lookahead_resources(cudaStream_t *side, LaEvents **ev)
     return true;
 }
 
+// A copy stream per device for the host-buffer calls (created once).
+static cudaStream_t g_copy[128];
+
+static cudaStream_t copy_stream()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return nullptr;
+    std::lock_guard<std::mutex> lock(g_side_mu);
+    if (g_copy[dev] == nullptr) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        g_copy[dev] = s;
+    }
+    return g_copy[dev];
+}
+
 // The side stream may run GEMMs concurrently with the caller's stream only
 // when no GEMM of the call stages operands in a shared workspace (the
 // tensor-core updates pack into c.tcwork).
@@ -120,6 +136,8 @@ static void potrf_rec_la(Ctx &c, i64 n, T *A, i64 lda, i64 off, cudaEvent_t pend
     potrf_rec_la<T>(c, n1, A, lda, off, nullptr, depth + 1);
     if (pending) note(c, cudaStreamWaitEvent(c.s, pending, 0));
     trsm_rlt<T>(c, n2, n1, T(1), A, lda, A21, lda);
+    if (depth == 0 && c.left_done) note(c, cudaEventRecord(c.left_done, c.s));
+    if (depth == 0 && c.trail_ready) note(c, cudaStreamWaitEvent(c.s, c.trail_ready, 0));
     cudaStream_t side = nullptr;
     LaEvents *ev = nullptr;
     cudaEvent_t next_pending = nullptr;
@@ -178,6 +196,7 @@ static void getrf_rec_la(Ctx &c, T *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r
         // wide: factor the leading m x m block, then swap and solve the rest
         if (pending) note(c, cudaStreamWaitEvent(c.s, pending, 0));
         getrf_rec_la<T>(c, A0, lda, m_tot, ipiv, r0, m, m, nullptr, depth + 1);
+        if (depth == 0 && c.trail_ready) note(c, cudaStreamWaitEvent(c.s, c.trail_ready, 0));
         laswp<T>(c, A0, lda, m_tot, r0 + m, n - m, r0, r0 + m, ipiv);
         trsm_lln<T>(c, true, m, n - m, T(1), A, lda, A + m * lda, lda);
         return;
@@ -185,6 +204,7 @@ static void getrf_rec_la(Ctx &c, T *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r
     const i64 n1 = split_q(n, n > 2 * TRX_NB ? TRX_NB : nb), n2 = n - n1;
     getrf_rec_la<T>(c, A0, lda, m_tot, ipiv, r0, m, n1, nullptr, depth + 1);
     if (pending) note(c, cudaStreamWaitEvent(c.s, pending, 0));
+    if (depth == 0 && c.trail_ready) note(c, cudaStreamWaitEvent(c.s, c.trail_ready, 0));
     laswp<T>(c, A0, lda, m_tot, r0 + n1, n2, r0, r0 + n1, ipiv);
     trsm_lln<T>(c, true, n1, n2, T(1), A, lda, A + n1 * lda, lda);
     T *A21 = A + n1, *A12 = A + n1 * lda, *A22 = A + n1 + n1 * lda;
@@ -1349,6 +1369,37 @@ size_t rl_host_work_size(const char *routine, int64_t m, int64_t n, int64_t lda)
     return 0;
 }
 
+// Host-buffer calls.  Above the order where the recursion splits, the
+// columns right of the top-level split are copied in on a copy stream while
+// the left part is factored (the top level waits for them before it first
+// touches them); the Cholesky's left columns, final after the top-level
+// TRSM, are copied back on the copy stream while the rest is factored.
+struct HostCopy {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t entry = nullptr, trail = nullptr, left = nullptr, left_back = nullptr;
+    bool ok = false;
+    HostCopy(bool wanted, bool want_left)
+    {
+        if (!wanted) return;
+        cs = copy_stream();
+        if (!cs) return;
+        if (cudaEventCreateWithFlags(&entry, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&trail, cudaEventDisableTiming) != cudaSuccess)
+            return;
+        if (want_left && (cudaEventCreateWithFlags(&left, cudaEventDisableTiming) != cudaSuccess ||
+                          cudaEventCreateWithFlags(&left_back, cudaEventDisableTiming) != cudaSuccess))
+            return;
+        ok = true;
+    }
+    ~HostCopy()
+    {
+        for (cudaEvent_t e : {entry, trail, left, left_back})
+            if (e) (void)cudaEventDestroy(e);
+    }
+};
+
+static constexpr int64_t HOST_SPLIT_MIN = 512;
+
 int rl_dpotrf_host(char uplo, int64_t n, double *A_host, int64_t lda, int32_t *info_host,
                    void *work, size_t lwork, rl_stream_t stream)
 {
@@ -1363,10 +1414,34 @@ int rl_dpotrf_host(char uplo, int64_t n, double *A_host, int64_t lda, int32_t *i
     char *w = static_cast<char *>(work);
     double *dA = reinterpret_cast<double *>(w);
     int32_t *dinfo = reinterpret_cast<int32_t *>(w + align256(bytes > 0 ? bytes : 8));
-    if (bytes && cudaMemcpyAsync(dA, A_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return RL_ERR_CUDA;
-    int st = rl_dpotrf(uplo, n, dA, lda, dinfo, nullptr, 0, stream);
-    if (st != RL_SUCCESS) return st;
-    if (bytes && cudaMemcpyAsync(A_host, dA, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return RL_ERR_CUDA;
+    const bool split = is_l(uplo) && n >= HOST_SPLIT_MIN && n > g_params.potrf_c;
+    HostCopy hc(split, true);
+    if (!split || !hc.ok) {
+        if (bytes && cudaMemcpyAsync(dA, A_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return RL_ERR_CUDA;
+        int st = rl_dpotrf(uplo, n, dA, lda, dinfo, nullptr, 0, stream);
+        if (st != RL_SUCCESS) return st;
+        if (bytes && cudaMemcpyAsync(A_host, dA, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return RL_ERR_CUDA;
+    } else {
+        const i64 n1 = split_q(n, TRX_NB);                      // the recursion's top-level split
+        const size_t lb = (size_t)lda * (size_t)n1 * sizeof(double), rb = bytes - lb;
+        Ctx c = make_ctx(stream, dinfo, nullptr, 0);
+        c.abort = dinfo;
+        c.trail_ready = hc.trail;
+        c.left_done = hc.left;
+        note(c, cudaEventRecord(hc.entry, s));                   // after the caller's earlier work on s
+        note(c, cudaStreamWaitEvent(hc.cs, hc.entry, 0));
+        note(c, cudaMemcpyAsync(dA, A_host, lb, cudaMemcpyHostToDevice, s));
+        note(c, cudaMemcpyAsync(dA + (size_t)lda * n1, A_host + (size_t)lda * n1, rb, cudaMemcpyHostToDevice, hc.cs));
+        note(c, cudaEventRecord(hc.trail, hc.cs));
+        note(c, cudaMemsetAsync(dinfo, 0, sizeof(int32_t), s));
+        potrf_rec(c, n, dA, lda, 0);
+        note(c, cudaStreamWaitEvent(hc.cs, hc.left, 0));
+        note(c, cudaMemcpyAsync(A_host, dA, lb, cudaMemcpyDeviceToHost, hc.cs));
+        note(c, cudaEventRecord(hc.left_back, hc.cs));
+        note(c, cudaMemcpyAsync(A_host + (size_t)lda * n1, dA + (size_t)lda * n1, rb, cudaMemcpyDeviceToHost, s));
+        note(c, cudaStreamWaitEvent(s, hc.left_back, 0));
+        if (c.err != cudaSuccess) return RL_ERR_CUDA;
+    }
     if (cudaMemcpyAsync(info_host, dinfo, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RL_ERR_CUDA;
     return cudaStreamSynchronize(s) == cudaSuccess ? RL_SUCCESS : RL_ERR_CUDA;
 }
@@ -1392,9 +1467,33 @@ int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda, int32_t *i
     p += align256(mn * sizeof(int32_t) + 4);
     void *ws = p;
     const size_t wsz = rl_dgetrf_work_size(m, n);
-    if (bytes && cudaMemcpyAsync(dA, A_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return RL_ERR_CUDA;
-    int st = rl_dgetrf(m, n, dA, lda, dipiv, dinfo, ws, wsz, stream);
-    if (st != RL_SUCCESS) return st;
+    // the recursion's top-level left part: the leading m x m block of a wide
+    // matrix, else the first split of the columns
+    const i64 nb = g_params.getrf_nb;
+    const i64 n1 = (n <= nb || m <= 0) ? 0 : (m < n ? m : split_q(n, n > 2 * TRX_NB ? TRX_NB : nb));
+    const bool split = n >= HOST_SPLIT_MIN && n1 > 0 && n1 < n && m <= INT32_MAX - 1;
+    HostCopy hc(split, false);
+    if (!split || !hc.ok || wsz == 0) {
+        if (bytes && cudaMemcpyAsync(dA, A_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return RL_ERR_CUDA;
+        int st = rl_dgetrf(m, n, dA, lda, dipiv, dinfo, ws, wsz, stream);
+        if (st != RL_SUCCESS) return st;
+    } else {
+        const size_t lb = (size_t)lda * (size_t)n1 * sizeof(double), rb = bytes - lb;
+        Ctx c = make_ctx(stream, dinfo, ws, wsz);
+        c.abort = nullptr;
+        c.trail_ready = hc.trail;
+        note(c, cudaEventRecord(hc.entry, s));
+        note(c, cudaStreamWaitEvent(hc.cs, hc.entry, 0));
+        note(c, cudaMemcpyAsync(dA, A_host, lb, cudaMemcpyHostToDevice, s));
+        note(c, cudaMemcpyAsync(dA + (size_t)lda * n1, A_host + (size_t)lda * n1, rb, cudaMemcpyHostToDevice, hc.cs));
+        note(c, cudaEventRecord(hc.trail, hc.cs));
+        note(c, cudaMemsetAsync(dinfo, 0, sizeof(int32_t), s));
+        getrf_rec(c, dA, lda, m, dipiv, 0, m, n);
+        // the recursion always reaches its top-level wait; this one keeps s
+        // ordered after the copy even if it did not
+        note(c, cudaStreamWaitEvent(s, hc.trail, 0));
+        if (c.err != cudaSuccess) return RL_ERR_CUDA;
+    }
     if (bytes && cudaMemcpyAsync(A_host, dA, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return RL_ERR_CUDA;
     if (mn && cudaMemcpyAsync(ipiv_host, dipiv, mn * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return RL_ERR_CUDA;
@@ -1478,8 +1577,13 @@ int rl_clear_cache(void)
         std::lock_guard<std::mutex> lock(g_side_mu);
         for (int dev = 0; dev < 128; ++dev) {
             LaEvents &e = t_ev[dev];
-            if (g_side[dev] == nullptr && !e.ready) continue;
+            if (g_side[dev] == nullptr && !e.ready && g_copy[dev] == nullptr) continue;
             keep(cudaSetDevice(dev));
+            if (g_copy[dev] != nullptr) {
+                keep(cudaStreamSynchronize(g_copy[dev]));
+                keep(cudaStreamDestroy(g_copy[dev]));
+                g_copy[dev] = nullptr;
+            }
             if (g_side[dev] != nullptr) {
                 keep(cudaStreamSynchronize(g_side[dev]));
                 keep(cudaStreamDestroy(g_side[dev]));

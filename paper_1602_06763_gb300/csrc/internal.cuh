@@ -107,6 +107,12 @@ struct Ctx {
     void *ozwork2 = nullptr;
     size_t ozlwork2 = 0;
     bool oz_dynamic = false;
+    // host-buffer calls: the columns right of the top-level split arrive on
+    // a copy stream (trail_ready: waited on before the top level first
+    // touches them); left_done is recorded once the columns left of the
+    // split hold their final values (Cholesky: after the top-level TRSM)
+    cudaEvent_t trail_ready = nullptr;
+    cudaEvent_t left_done = nullptr;
 };
 
 int device_sms();

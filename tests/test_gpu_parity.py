@@ -320,6 +320,47 @@ def test_host_buffer_forms():
     assert int(hinfo[0]) == 0 and oracle.res_lu(G_, F, hpiv.numpy()) <= BOUND
 
 
+@pytest.mark.parametrize("m,n", [(1500, 1500), (2000, 1300), (700, 1900)])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_split_copies_bit_identical(m, n, pinned):
+    """Above order 512 the host-buffer calls copy the columns right of the
+    top-level split on a copy stream (and the Cholesky's left columns back
+    early): the results equal the device-buffer calls' bit for bit, with
+    pinned and pageable host memory, tall and wide, and with a non-SPD
+    matrix (info and the partial factor as the device call leaves them)."""
+    r = G.lib()
+    t = G.torch()
+
+    def host(X):
+        h = t.from_numpy(np.asfortranarray(X).ravel(order="F").copy())
+        return h.pin_memory() if pinned else h
+
+    A = inputs.uniform(m, n, seed=inputs.seed_for(1, 9000 + m + n))
+    F_dev, p_dev, i_dev = G.getrf(A)
+    h = host(A)
+    hpiv = t.zeros(min(m, n), dtype=t.int32)
+    hinfo = t.full((1,), -9, dtype=t.int32)
+    lw = r.rl_host_work_size("dgetrf", m, n, m)
+    work = t.empty(lw, dtype=t.uint8, device="cuda")
+    assert r.rl_dgetrf_host(m, n, h.data_ptr(), m, hpiv.data_ptr(), hinfo.data_ptr(), work.data_ptr(), lw) == 0
+    assert int(hinfo[0]) == i_dev
+    assert np.array_equal(h.numpy().reshape(n, m).T, F_dev)
+    assert np.array_equal(hpiv.numpy(), p_dev)
+    if m != n:
+        return
+    for bad in (False, True):
+        S = inputs.spd_bbt(n, seed=inputs.seed_for(1, 9100 + n))
+        if bad:
+            S[1200, 1200] = -1.0
+        L_dev, li_dev = G.potrf(S)
+        h = host(S)
+        lw = r.rl_host_work_size("dpotrf", n, n, n)
+        work = t.empty(lw, dtype=t.uint8, device="cuda")
+        assert r.rl_dpotrf_host("L", n, h.data_ptr(), n, hinfo.data_ptr(), work.data_ptr(), lw) == 0
+        assert int(hinfo[0]) == li_dev == (1201 if bad else 0)
+        assert np.array_equal(h.numpy().reshape(n, n).T, L_dev)
+
+
 def test_bounded_wait_reports_timeout_and_context_survives():
     # A zero spin limit makes the panel's grid barrier give up at once: the
     # kernel must return with info = RL_INFO_DEVICE_TIMEOUT, not hang, and the
