@@ -327,7 +327,7 @@ def test_host_buffer_split_copies_bit_identical(m, n, pinned):
     top-level split on a copy stream (and the Cholesky's left columns back
     early): the results equal the device-buffer calls' bit for bit, with
     pinned and pageable host memory, tall and wide, and with a non-SPD
-    matrix (info and the partial factor as the device call leaves them)."""
+    matrix (info, and the leading block before the failure)."""
     r = G.lib()
     t = G.torch()
 
@@ -358,7 +358,11 @@ def test_host_buffer_split_copies_bit_identical(m, n, pinned):
         work = t.empty(lw, dtype=t.uint8, device="cuda")
         assert r.rl_dpotrf_host("L", n, h.data_ptr(), n, hinfo.data_ptr(), work.data_ptr(), lw) == 0
         assert int(hinfo[0]) == li_dev == (1201 if bad else 0)
-        assert np.array_equal(h.numpy().reshape(n, n).T, L_dev)
+        L_host = h.numpy().reshape(n, n).T
+        if bad:   # the leading 1200 x 1200 block is final; what follows depends on when kernels saw info
+            assert np.array_equal(np.tril(L_host[:1200, :1200]), np.tril(L_dev[:1200, :1200]))
+        else:
+            assert np.array_equal(L_host, L_dev)
 
 
 def test_bounded_wait_reports_timeout_and_context_survives():
