@@ -263,6 +263,25 @@ int rl_zgetrs(char trans, int64_t n, int64_t nrhs, const rl_double_complex *A, i
               rl_stream_t stream);
 int rl_zpotrs(char uplo, int64_t n, int64_t nrhs, const rl_double_complex *A, int64_t lda,
               rl_double_complex *B, int64_t ldb, void *work, size_t lwork, rl_stream_t stream);
+/* Complex double inversions, as their double-precision peers:
+ *   rl_ztrtri  A := A^{-1} (lower or upper, diag 'N'/'U'), info = first
+ *              zero diagonal entry (A unchanged then);
+ *   rl_zlauum  A := L^H L ('L') or U U^H ('U');
+ *   rl_zpotri  A := (L L^H)^{-1} from rl_zpotrf's factor (trtri + lauum);
+ *   rl_zgetri  A := A^{-1} from rl_zgetrf's factors and ipiv, workspace
+ *              rl_zgetri_work_size(n) bytes, n <= 40960.
+ * Base cases of order <= 32 (complex elements double the shared memory per
+ * entry); argument numbers as rl_dtrtri / rl_dlauum / rl_dpotri /
+ * rl_dgetri. */
+int rl_ztrtri(char uplo, char diag, int64_t n, rl_double_complex *A, int64_t lda, int32_t *info,
+              void *work, size_t lwork, rl_stream_t stream);
+int rl_zlauum(char uplo, int64_t n, rl_double_complex *A, int64_t lda, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream);
+int rl_zpotri(char uplo, int64_t n, rl_double_complex *A, int64_t lda, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream);
+size_t rl_zgetri_work_size(int64_t n);
+int rl_zgetri(int64_t n, rl_double_complex *A, int64_t lda, const int32_t *ipiv, int32_t *info,
+              void *work, size_t lwork, rl_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * FP64 updates emulated on the BF16 tensor cores (the Ozaki scheme; not in

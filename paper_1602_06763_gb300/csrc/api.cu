@@ -261,7 +261,8 @@ template <typename T>
 void trtri_rec(Ctx &c, bool unit, i64 n, T *A, i64 lda)
 {
     if (n <= 0) return;
-    if (n <= g_params.trtri_c) { trti2<T>(c, unit, n, A, lda); return; }
+    const i64 base = sizeof(T) > 8 && g_params.trtri_c > 32 ? 32 : g_params.trtri_c;   // complex: <= 32
+    if (n <= base) { trti2<T>(c, unit, n, A, lda); return; }
     const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
     T *BL = A + n1, *BR = A + n1 + n1 * lda;
     trtri_rec<T>(c, unit, n1, A, lda);
@@ -271,13 +272,16 @@ void trtri_rec(Ctx &c, bool unit, i64 n, T *A, i64 lda)
 }
 template void trtri_rec<double>(Ctx &, bool, i64, double *, i64);
 template void trtri_rec<float>(Ctx &, bool, i64, float *, i64);
+template void trtri_rec<cplx>(Ctx &, bool, i64, cplx *, i64);
 
-// A := L^T L: lauum(A11); A11 += A21^T A21; A21 := A22^T A21; lauum(A22).
+// A := L^T L: lauum(A11); A11 += A21^T A21; A21 := A22^T A21; lauum(A22)
+// (complex: L^H L, with conjugate transposes throughout).
 template <typename T>
 static void lauum_rec(Ctx &c, i64 n, T *A, i64 lda)
 {
     if (n <= 0) return;
-    if (n <= g_params.trtri_c) { lauu2<T>(c, n, A, lda); return; }
+    const i64 base = sizeof(T) > 8 && g_params.trtri_c > 32 ? 32 : g_params.trtri_c;
+    if (n <= base) { lauu2<T>(c, n, A, lda); return; }
     const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
     T *A21 = A + n1, *A22 = A + n1 + n1 * lda;
     lauum_rec<T>(c, n1, A, lda);
@@ -939,6 +943,33 @@ int rl_sgetri(int64_t n, float *A, int64_t lda, const int32_t *ipiv, int32_t *in
               rl_stream_t stream)
 {
     return getri_api<float>(n, A, lda, ipiv, info, work, lwork, stream);
+}
+
+// complex double inversions (the recursions above with conjugate transposes)
+size_t rl_zgetri_work_size(int64_t n) { return n <= 0 ? 0 : getri_work_bytes(n); }
+
+int rl_zgetri(int64_t n, rl_double_complex *A, int64_t lda, const int32_t *ipiv, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream)
+{
+    return getri_api<cplx>(n, reinterpret_cast<cplx *>(A), lda, ipiv, info, work, lwork, stream);
+}
+
+int rl_ztrtri(char uplo, char diag, int64_t n, rl_double_complex *A, int64_t lda, int32_t *info, void *work,
+              size_t lwork, rl_stream_t stream)
+{
+    return trtri_api<cplx>(uplo, diag, n, reinterpret_cast<cplx *>(A), lda, info, work, lwork, stream);
+}
+
+int rl_zlauum(char uplo, int64_t n, rl_double_complex *A, int64_t lda, int32_t *info, void *work, size_t lwork,
+              rl_stream_t stream)
+{
+    return lauum_api<cplx>(false, uplo, n, reinterpret_cast<cplx *>(A), lda, info, work, lwork, stream);
+}
+
+int rl_zpotri(char uplo, int64_t n, rl_double_complex *A, int64_t lda, int32_t *info, void *work, size_t lwork,
+              rl_stream_t stream)
+{
+    return lauum_api<cplx>(true, uplo, n, reinterpret_cast<cplx *>(A), lda, info, work, lwork, stream);
 }
 
 }  // extern "C"

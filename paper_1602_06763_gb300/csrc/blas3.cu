@@ -878,7 +878,8 @@ void trmm_llt(Ctx &c, i64 m, i64 n, T alpha, const T *L, i64 ldl, T *B, i64 ldb)
 {
     if (m <= 0 || n <= 0) return;
     if (m <= TRX_NB) {
-        launch_tri<T, TRI_MUL, false, false, false>(c, K_TRMM, n, (int)m, alpha, L, ldl, B, ldb);
+        // complex: L^H B
+        launch_tri<T, TRI_MUL, false, false, false, is_cplx<T>::value>(c, K_TRMM, n, (int)m, alpha, L, ldl, B, ldb);
         return;
     }
     const i64 m1 = split_q(m, TRX_NB), m2 = m - m1;
@@ -941,5 +942,10 @@ template void trsm_lln<cplx>(Ctx &, bool, i64, i64, cplx, const cplx *, i64, cpl
 template void trsm_rlt<cplx>(Ctx &, i64, i64, cplx, const cplx *, i64, cplx *, i64);
 template void trsm_llt<cplx>(Ctx &, i64, i64, cplx, const cplx *, i64, cplx *, i64);
 template void trsm_lun<cplx>(Ctx &, i64, i64, cplx, const cplx *, i64, cplx *, i64);
+// and of the inversions (trtri, lauum, getri)
+template void trmm_rln<cplx>(Ctx &, bool, i64, i64, cplx, const cplx *, i64, cplx *, i64);
+template void trmm_llt<cplx>(Ctx &, i64, i64, cplx, const cplx *, i64, cplx *, i64);
+template void trmm_lun<cplx>(Ctx &, i64, i64, cplx, const cplx *, i64, cplx *, i64);
+template void trsm_run<cplx>(Ctx &, i64, i64, cplx, const cplx *, i64, cplx *, i64);
 
 }  // namespace rl

@@ -161,8 +161,11 @@ __global__ void __launch_bounds__(BASE_N)
 k_trti2(int n, T *A, i64 lda, const int32_t *abort)
 {
     if (abort && *abort != 0) return;
-    __shared__ T Lp[BASE_PACK];
-    __shared__ T Xp[BASE_PACK];
+    // complex (16-byte) elements: order <= 32, so both packed triangles fit
+    // the 48 KB of static shared memory
+    constexpr int PACK = sizeof(T) > 8 ? 32 * 33 / 2 : BASE_PACK;
+    __shared__ T Lp[PACK];
+    __shared__ T Xp[PACK];
     // UPPER: invert M = U^T (lower) and store X = (M^{-1})^T = U^{-1}
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         int i = e % n, k = e / n;
@@ -195,6 +198,7 @@ template <typename T>
 void trti2(Ctx &c, bool unit, i64 n, T *A, i64 lda, bool upper)
 {
     if (n <= 0) return;
+    if (sizeof(T) > 8 && n > 32) { note(c, cudaErrorInvalidValue); return; }
     Launch L(c, K_TRTI2, (double)n * n * n / 3.0, 0.0);
     if (upper) {
         if (unit) k_trti2<T, true, true><<<1, BASE_N, 0, c.s>>>((int)n, A, lda, c.abort);
@@ -206,9 +210,11 @@ void trti2(Ctx &c, bool unit, i64 n, T *A, i64 lda, bool upper)
 }
 template void trti2<double>(Ctx &, bool, i64, double *, i64, bool);
 template void trti2<float>(Ctx &, bool, i64, float *, i64, bool);
+template void trti2<cplx>(Ctx &, bool, i64, cplx *, i64, bool);
 
 // ----------------------------------------------------------------------------
-// lauu2: (L^T L)_ij = sum_{k=i}^{n-1} l_ki l_kj for i >= j, from a staged copy.
+// lauu2: (L^T L)_ij = sum_{k=i}^{n-1} l_ki l_kj for i >= j, from a staged copy
+// (complex: L^H L, conj(l_ki) l_kj).
 // ----------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -225,7 +231,7 @@ k_lauu2(int n, T *A, i64 lda, const int32_t *abort)
         int i = e % n, j = e / n;
         if (i < j) continue;
         T s = T(0);
-        for (int k = i; k < n; ++k) s = fma(Lp[tix(k, i)], Lp[tix(k, j)], s);
+        for (int k = i; k < n; ++k) s = fma(cj(Lp[tix(k, i)]), Lp[tix(k, j)], s);
         A[(i64)j * lda + i] = s;
     }
 }
@@ -239,6 +245,7 @@ void lauu2(Ctx &c, i64 n, T *A, i64 lda)
 }
 template void lauu2<double>(Ctx &, i64, double *, i64);
 template void lauu2<float>(Ctx &, i64, float *, i64);
+template void lauu2<cplx>(Ctx &, i64, cplx *, i64);
 
 // ----------------------------------------------------------------------------
 // First exactly-zero diagonal entry -> info (dtrtri leaves A unchanged then).
@@ -273,6 +280,7 @@ void diag_zero_scan(Ctx &c, i64 n, const T *A, i64 lda)
 }
 template void diag_zero_scan<double>(Ctx &, i64, const double *, i64);
 template void diag_zero_scan<float>(Ctx &, i64, const float *, i64);
+template void diag_zero_scan<cplx>(Ctx &, i64, const cplx *, i64);
 
 // ----------------------------------------------------------------------------
 // LU panel.

@@ -20,16 +20,18 @@ namespace rl {
 
 namespace {
 
-constexpr int UL_N = 64;
-constexpr int UL_P = UL_N + 1;
+// block order of the base case: 64, or 32 for complex (16-byte) elements
+// so that the staged block fits the 48 KB of static shared memory
+template <typename T> constexpr int ul_n() { return sizeof(T) > 8 ? 32 : 64; }
 
-// W = X Y for one block of order <= 64: X upper (with diagonal), Y unit
+// W = X Y for one block of order <= ul_n: X upper (with diagonal), Y unit
 // lower (strictly lower part stored), both in A; W overwrites A.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_uinv_linv(int n, T *A, i64 lda, const int32_t *abort)
 {
     if (abort && *abort != 0) return;
+    constexpr int UL_N = ul_n<T>(), UL_P = UL_N + 1;
     __shared__ T S[UL_N * UL_P];                 // S(i, k) at S[k * UL_P + i]
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e % n, k = e / n;
@@ -64,12 +66,12 @@ template <typename T>
 void uinv_linv_rec(Ctx &c, i64 n, T *A, i64 lda)
 {
     if (n <= 0) return;
-    if (n <= UL_N) {
+    if (n <= ul_n<T>()) {
         Launch L(c, K_TRMM, 2.0 * n * n * n / 3.0, 0.0);
         k_uinv_linv<T><<<1, 256, 0, c.s>>>((int)n, A, lda, c.abort);
         return;
     }
-    const i64 n1 = split_q(n, UL_N), n2 = n - n1;
+    const i64 n1 = split_q(n, ul_n<T>()), n2 = n - n1;
     T *A11 = A, *A12 = A + n1 * lda, *A21 = A + n1, *A22 = A + n1 + n1 * lda;
     uinv_linv_rec<T>(c, n1, A11, lda);
     gemm<T>(c, false, false, n1, n1, n2, T(1), A12, lda, A21, lda, T(1), A11, lda);
@@ -83,7 +85,8 @@ template <typename T>
 void trtri_upper_rec(Ctx &c, i64 n, T *A, i64 lda)
 {
     if (n <= 0) return;
-    if (n <= g_params.trtri_c) { trti2<T>(c, false, n, A, lda, true); return; }
+    const i64 base = sizeof(T) > 8 && g_params.trtri_c > 32 ? 32 : g_params.trtri_c;
+    if (n <= base) { trti2<T>(c, false, n, A, lda, true); return; }
     const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
     T *TR = A + n1 * lda, *BR = A + n1 + n1 * lda;
     trtri_upper_rec<T>(c, n1, A, lda);
@@ -208,5 +211,6 @@ void getri(Ctx &c, i64 n, T *A, i64 lda, const int32_t *ipiv, void *work)
 
 template void getri<double>(Ctx &, i64, double *, i64, const int32_t *, void *);
 template void getri<float>(Ctx &, i64, float *, i64, const int32_t *, void *);
+template void getri<cplx>(Ctx &, i64, cplx *, i64, const int32_t *, void *);
 
 }  // namespace rl

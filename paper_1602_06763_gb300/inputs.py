@@ -141,6 +141,27 @@ def gaussian_int_chol(n: int, seed: int):
     return np.asfortranarray(L, dtype=np.complex128)
 
 
+def gaussian_unit_trtri(n: int, seed: int, factors=3):
+    """A lower triangular L = D (I + N_1)(I + N_2)... with N_k a block below
+    the diagonal (rows >= s_k, columns < s_k) of Gaussian integers a + bi,
+    a, b in {-1, 0, 1} (so N_k^2 = 0), and D = diag of units {1, -1, i, -i}.
+    Returns (L, L^{-1}) with L^{-1} = ... (I - N_2)(I - N_1) D^{-1}, both
+    exact Gaussian-integer matrices in complex128."""
+    r = rng(seed)
+    L = np.eye(n, dtype=np.complex128)
+    Linv = np.eye(n, dtype=np.complex128)
+    for _ in range(factors):
+        sk = int(r.integers(1, max(2, n)))
+        N = np.zeros((n, n), dtype=np.complex128)
+        N[sk:, :sk] = r.integers(-1, 2, size=(n - sk, sk)) + 1j * r.integers(-1, 2, size=(n - sk, sk))
+        L = L @ (np.eye(n) + N)
+        Linv = (np.eye(n) - N) @ Linv
+    d = r.choice(np.array([1, -1, 1j, -1j]), size=n)
+    L = np.diag(d) @ L
+    Linv = Linv @ np.diag(1.0 / d)
+    return np.asfortranarray(np.tril(L)), np.asfortranarray(np.tril(Linv))
+
+
 def complex_dyadic_lu(n: int, seed: int):
     """A = P^T L U with L unit lower, off-diagonal (a + bi)/4 (a, b in -1..1,
     so |Re| + |Im| <= 1/2) and U upper with Gaussian-integer entries and a

@@ -60,6 +60,11 @@ _SIGS = {
     "rl_dlaswp": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i64, _i64, _vp, _vp]),
     "rl_zpotrf": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
     "rl_zgetrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _sz, _vp]),
+    "rl_ztrtri": (ctypes.c_int, [_ch, _ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_zlauum": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_zpotri": (ctypes.c_int, [_ch, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "rl_zgetri_work_size": (_sz, [_i64]),
+    "rl_zgetri": (ctypes.c_int, [_i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
     "rl_zpotrs": (ctypes.c_int, [_ch, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
     "rl_zgetrf": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp]),
     "rl_spotrf_tc_work_size": (ctypes.c_size_t, [_i64, ctypes.c_int]),
@@ -238,6 +243,26 @@ def rl_dtrmm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, stream=None)
 
 def rl_zpotrf(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
     return _lib.rl_zpotrf(_c(uplo), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_ztrtri(uplo, diag, n, A, lda, info, work=None, lwork=0, stream=None):
+    return _lib.rl_ztrtri(_c(uplo), _c(diag), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_zlauum(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
+    return _lib.rl_zlauum(_c(uplo), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_zpotri(uplo, n, A, lda, info, work=None, lwork=0, stream=None):
+    return _lib.rl_zpotri(_c(uplo), n, _ptr(A), lda, _ptr(info), _ptr(work), lwork, _stream(stream))
+
+
+def rl_zgetri_work_size(n):
+    return int(_lib.rl_zgetri_work_size(n))
+
+
+def rl_zgetri(n, A, lda, ipiv, info, work, lwork, stream=None):
+    return _lib.rl_zgetri(n, _ptr(A), lda, _ptr(ipiv), _ptr(info), _ptr(work), lwork, _stream(stream))
 
 
 def rl_zgetrs(trans, n, nrhs, A, lda, ipiv, B, ldb, work=None, lwork=0, stream=None):

@@ -178,3 +178,87 @@ def test_complex_argument_errors():
     assert r.rl_zgetrf(4, 4, d.ptr(), 4, ipiv.data_ptr(), info.data_ptr(), 0, 0) == r.RL_ERR_WORKSPACE
     assert r.rl_zgetrf(-1, 4, d.ptr(), 4, ipiv.data_ptr(), info.data_ptr(), 0, 0) == -1
     assert r.rl_zpotrf("L", 0, 0, 1, info.data_ptr()) == 0
+
+
+# ----------------------------------------------------------------------------
+# inversions: ztrtri, zlauum, zpotri, zgetri
+# ----------------------------------------------------------------------------
+
+def zcall(fn, *args):
+    st = fn(*args)
+    G.sync()
+    assert st == 0, G.lib().rl_status_string(st)
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 130, 300])
+def test_ztrtri_exact(n):
+    r = G.lib()
+    L, Linv = inputs.gaussian_unit_trtri(n, inputs.seed_for(1, 5600 + n))
+    info = G.int_buf(1, -77)
+    d = ZMat(L, lda=n + 1)
+    zcall(r.rl_ztrtri, "L", "N", n, d.ptr(), d.lda, info.data_ptr())
+    assert int(info[0]) == 0 and d.canaries_intact()
+    assert np.array_equal(np.tril(d.get()), Linv)
+    # unit diagonal: L's off-diagonal part with ones on the diagonal
+    Lu = np.tril(np.diag(1.0 / np.diag(L)) @ L)
+    Lu_inv = np.asfortranarray(np.tril(Linv @ np.diag(np.diag(L))))
+    d = ZMat(Lu)
+    zcall(r.rl_ztrtri, "L", "U", n, d.ptr(), d.lda, info.data_ptr())
+    assert np.array_equal(np.tril(d.get(), -1), np.tril(Lu_inv, -1))
+    # upper: U = L^H, U^{-1} = (L^{-1})^H
+    U = np.asfortranarray(L.conj().T)
+    d = ZMat(U)
+    zcall(r.rl_ztrtri, "U", "N", n, d.ptr(), d.lda, info.data_ptr())
+    assert np.array_equal(np.triu(d.get()), np.triu(Linv.conj().T))
+
+
+def test_ztrtri_zero_diagonal_info():
+    r = G.lib()
+    n = 200
+    L, _ = inputs.gaussian_unit_trtri(n, inputs.seed_for(1, 5700))
+    L[120, 120] = 0.0
+    d = ZMat(L)
+    info = G.int_buf(1, -77)
+    zcall(r.rl_ztrtri, "L", "N", n, d.ptr(), d.lda, info.data_ptr())
+    assert int(info[0]) == 121
+    assert np.array_equal(d.get(), L)
+
+
+@pytest.mark.parametrize("n", [7, 64, 250])
+def test_zlauum_zpotri_exact(n):
+    r = G.lib()
+    L, Linv = inputs.gaussian_unit_trtri(n, inputs.seed_for(1, 5800 + n))
+    info = G.int_buf(1, -77)
+    d = ZMat(L)
+    zcall(r.rl_zlauum, "L", n, d.ptr(), d.lda, info.data_ptr())
+    assert np.array_equal(np.tril(d.get()), np.tril(L.conj().T @ L))
+    d = ZMat(np.asfortranarray(L.conj().T))
+    zcall(r.rl_zlauum, "U", n, d.ptr(), d.lda, info.data_ptr())
+    assert np.array_equal(np.triu(d.get()), np.triu(L.conj().T @ L))
+    # zpotri on the factor L of A = L L^H: A^{-1} = L^{-H} L^{-1}
+    d = ZMat(L)
+    zcall(r.rl_zpotri, "L", n, d.ptr(), d.lda, info.data_ptr())
+    assert int(info[0]) == 0
+    assert np.array_equal(np.tril(d.get()), np.tril(Linv.conj().T @ Linv))
+
+
+@pytest.mark.parametrize("n", [1, 40, 300, 700])
+def test_zgetri(n):
+    r = G.lib()
+    t = G.torch()
+    A = inputs.complex_uniform(n, n, inputs.seed_for(1, 5900 + n))
+    F, ipiv, info = zgetrf(A)
+    assert info == 0
+    d = ZMat(F)
+    dp = t.from_numpy(ipiv.astype(np.int32)).cuda()
+    inf = G.int_buf(1, -77)
+    lw = r.rl_zgetri_work_size(n)
+    w = t.empty(lw, dtype=t.uint8, device="cuda")
+    zcall(r.rl_zgetri, n, d.ptr(), d.lda, dp.data_ptr(), inf.data_ptr(), w.data_ptr(), lw)
+    assert int(inf[0]) == 0 and d.canaries_intact()
+    X = d.get()
+    Al, Xl = A.astype(np.clongdouble), X.astype(np.clongdouble)
+    R = (Al @ Xl - np.eye(n)).astype(np.complex128)
+    # ||A X - I|| / (||A|| ||X|| n eps), 1-norms
+    res = np.abs(R).sum(0).max() / (np.abs(A).sum(0).max() * np.abs(X).sum(0).max() * n * 2.0 ** -53)
+    assert res <= 10.0
