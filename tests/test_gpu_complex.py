@@ -3,7 +3,9 @@
 are exact in binary64 bit for bit (Gaussian-integer Cholesky, dyadic
 complex LU with a planted permutation), ipiv equal to the oracle's up to the
 first near-tie of the |Re| + |Im| pivot search, info on singular and
-indefinite inputs, and canaries around every buffer."""
+indefinite inputs, and canaries around every buffer; the inversions
+(ztrtri lower/upper/unit, zlauum, zpotri) bit for bit on Gaussian-integer
+triangles whose inverses are Gaussian integers, zgetri by ||A X - I||."""
 import numpy as np
 import pytest
 
