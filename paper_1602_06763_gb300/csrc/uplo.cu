@@ -5,9 +5,9 @@
 //   lauum:  U U^T = L^T L               potri:  (U^T U)^{-1} = (L L^T)^{-1}
 //   sygst:  U^{-T} A U^{-1} = L^{-1} A L^{-T},  U A U^T = L^T A L
 // so an upper call swaps the two triangles of its square operands in place
-// (conjugating for the complex Hermitian forms), runs the lower recursion,
-// and swaps back: the strictly lower part comes back unchanged, as LAPACK
-// leaves the unreferenced triangle.  A swap moves 2 * 16 B per off-diagonal
+// (for complex, A := A^H: conjugating, the diagonal included), runs the
+// lower recursion, and swaps back: the strictly lower part comes back
+// unchanged, as LAPACK leaves the unreferenced triangle.  A swap moves 2 * 16 B per off-diagonal
 // element pair (read and write of both), about 0.1 % of a factorization's
 // time at n = 16384, against a second copy of every kernel.
 //
@@ -50,9 +50,11 @@ __device__ inline void swap_pair(int n, T *A, i64 lda, int I, int J, T (*s1)[SW_
     }
     __syncthreads();
     for (int k = ty; k < SW_T; k += SW_ROWS) {
-        // tile 1 element (r1 + tx, c1 + k) := old A(c1 + k, r1 + tx) = s2[tx][k]
+        // tile 1 element (r1 + tx, c1 + k) := old A(c1 + k, r1 + tx) = s2[tx][k];
+        // complex: the diagonal is conjugated too (a triangle's transpose-
+        // conjugate; twice is the identity)
         const int i = r1 + tx, j = c1 + k;
-        if (i < n && j < n && i != j) {
+        if (i < n && j < n && (CONJ || i != j)) {
             const T v = s2[tx][k];
             A[(i64)j * lda + i] = CONJ ? cj(v) : v;
         }
