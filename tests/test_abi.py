@@ -113,3 +113,42 @@ def test_host_logic_of_the_tuning_and_lowprec_calls(built):
     assert r.rl_vbatched_set_config("P", 4, 0) == 0
     assert r.rl_vbatched_tune_work_size(10, 1000, 8) >= 1000 * 8
     assert r.rl_vbatched_tune_work_size(10, 1000, 3) == 0
+
+
+def test_host_logic_of_the_complex_upper_and_emulated_calls(built):
+    """Argument checks and size queries of the complex, transposed-solve and
+    emulated-FP64 entry points return before any device work."""
+    from paper_1602_06763_gb300 import relgpu as r
+    # complex: LAPACK argument numbering
+    assert r.rl_zpotrf("X", 4, 8, 4, 8, stream=0) == -1
+    assert r.rl_zgetrf(4, -1, 8, 4, 8, 8, None, 0, stream=0) == -2
+    assert r.rl_ztrtri("L", "Q", 4, 8, 4, 8, stream=0) == -2
+    assert r.rl_zlauum("L", 4, 8, 3, 8, stream=0) == -4
+    assert r.rl_zpotri("Q", 4, 8, 4, 8, stream=0) == -1
+    assert r.rl_zgetri(-1, 8, 1, 8, 8, None, 0, stream=0) == -1
+    assert r.rl_zgetri_work_size(1000) == r.rl_dgetri_work_size(1000)
+    assert r.rl_zgetrs("Q", 4, 1, 8, 4, 8, 8, 4, stream=0) == -1
+    assert r.rl_zgetrs("N", 4, 1, 8, 3, 8, 8, 4, stream=0) == -5
+    assert r.rl_zgetrs("T", 4, 1, 8, 4, 8, 8, 4, stream=0) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_zpotrs("L", 4, 1, 8, 4, 8, 3, stream=0) == -7
+    # transposed real solves: argument checks
+    assert r.rl_sgetrs("Q", 4, 1, 8, 4, 8, 8, 4, stream=0) == -1
+    assert r.rl_dgetrs("T", 4, -1, 8, 4, 8, 8, 4, stream=0) == -3
+    # emulated FP64: slices, arguments, workspace queries
+    assert r.rl_oz_work_size(100, 100, 100, 5) == 0 and r.rl_oz_work_size(100, 100, 100, 9) == 0
+    w7 = r.rl_oz_work_size(1000, 500, 300, 7)
+    # digit planes: 7 planes x 2 bytes x (rows padded to 128 + columns padded to 64) x k padded to 64
+    assert w7 >= 7 * 2 * (1024 + 512) * 320
+    assert r.rl_oz_work_size(1000, 500, 300, 8) > w7 > r.rl_oz_work_size(1000, 500, 300, 6)
+    assert r.rl_dpotrf_oz_work_size(4096, 7) >= 2 * r.rl_oz_work_size(2112, 2112, 2112, 7)
+    assert r.rl_dgetrf_oz_work_size(4096, 4096, 7) > r.rl_oz_work_size(4096, 4096, 2112, 7)
+    assert r.rl_dgemm_oz(7, "N", "X", 4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, None, 0, stream=0) == -3
+    assert r.rl_dgemm_oz(7, "N", "N", -1, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 4, None, 0, stream=0) == -4
+    assert r.rl_dgemm_oz(7, "N", "N", 4, 4, 4, 1.0, 8, 4, 8, 4, 0.0, 8, 3, None, 0, stream=0) == -14
+    assert r.rl_dgemm_oz(7, "N", "N", 4, 4, 1 << 22, 1.0, 8, 4, 8, 1 << 22, 0.0, 8, 4, None, 0,
+                         stream=0) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_dpotrf_oz(9, "L", 4, 8, 4, 8, None, 0, stream=0) == -1
+    assert r.rl_dpotrf_oz(7, "L", 4, 8, 3, 8, None, 0, stream=0) == -5
+    assert r.rl_dgetrf_oz(7, 4, 4, 8, 4, 8, 8, None, 0, stream=0) == r.RL_ERR_WORKSPACE
+    assert r.rl_set_param(r.RL_PARAM_OZ_MIN, 0) == r.RL_ERR_PARAM
+    assert r.rl_get_param(r.RL_PARAM_OZ_MIN) == 256
