@@ -570,7 +570,7 @@ int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda,
  *                              rows each either way)
  *   RL_PARAM_OZ_MIN            smallest m, n and k of an FP64 update that
  *                              the *_oz routines emulate on the tensor
- *                              cores (default 256; smaller ones stay FP64)
+ *                              cores (default 128; smaller ones stay FP64)
  * rl_set_param returns 0 or RL_ERR_PARAM; rl_get_param returns the value or
  * -1 for an unknown key.
  * ------------------------------------------------------------------------- */

@@ -78,7 +78,7 @@ struct Params {
     int lookahead = 1;       // LU/Cholesky: trailing update split across the side stream (0 = off)
     int panel_ctas64 = 0;    // LU panel CTAs, FP64 / FP32 (0 = one per SM)
     int panel_ctas32 = 0;
-    int oz_min = 256;        // smallest m, n and k that the FP64 emulation takes
+    int oz_min = 128;        // smallest m, n and k that the FP64 emulation takes
 };
 extern Params g_params;
 

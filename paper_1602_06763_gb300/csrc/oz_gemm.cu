@@ -454,7 +454,8 @@ static void oz_split(Ctx &c, bool tr, int rows, int kdim, const double *X, i64 l
         if (tr) {
             oz::k_absmax<true><<<(unsigned)((rows + 7) / 8), 256, 0, c.s>>>(rows, kdim, X, ldx, mx);
         } else {
-            const int kch = kdim >= 4096 ? 32 : (kdim >= 512 ? 8 : 1);
+            // 64 values of k per thread: rows x k / 64 threads in flight
+            const int kch = (kdim + 63) / 64 < 4096 ? (kdim + 63) / 64 : 4096;
             const dim3 g((unsigned)((rows + 255) / 256), (unsigned)kch);
             oz::k_absmax<false><<<g, 256, 0, c.s>>>(rows, kdim, X, ldx, mx);
         }

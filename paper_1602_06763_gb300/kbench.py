@@ -42,12 +42,15 @@ def main():
     ap.add_argument("--tri-lanes", type=int, default=0, help="lanes per vector of the triangle leaf kernels (2 or 4)")
     ap.add_argument("--oz", type=int, default=0,
                     help="dgemm / dsyrk / potrf / getrf: FP64 updates emulated with this many BF16 digit planes")
+    ap.add_argument("--oz-min", type=int, default=0, help="RL_PARAM_OZ_MIN value for the --oz cases")
     ap.add_argument("--uplo", default="L", help="potrf / trtri / lauum / zpotrf: triangle")
     ap.add_argument("--flow", type=int, default=1, help="getrs/potrs: 1 = one-launch flow solve, 0 = recursive")
     a = ap.parse_args()
 
     if a.nb:
         r.check(r.rl_set_param(r.RL_PARAM_GETRF_PANEL, a.nb))
+    if a.oz_min:
+        r.check(r.rl_set_param(r.RL_PARAM_OZ_MIN, a.oz_min))
     if a.panel_ctas:
         r.check(r.rl_set_param(r.RL_PARAM_PANEL_CTAS, a.panel_ctas))
     if a.tri_lanes:

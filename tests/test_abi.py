@@ -151,4 +151,4 @@ def test_host_logic_of_the_complex_upper_and_emulated_calls(built):
     assert r.rl_dpotrf_oz(7, "L", 4, 8, 3, 8, None, 0, stream=0) == -5
     assert r.rl_dgetrf_oz(7, 4, 4, 8, 4, 8, 8, None, 0, stream=0) == r.RL_ERR_WORKSPACE
     assert r.rl_set_param(r.RL_PARAM_OZ_MIN, 0) == r.RL_ERR_PARAM
-    assert r.rl_get_param(r.RL_PARAM_OZ_MIN) == 256
+    assert r.rl_get_param(r.RL_PARAM_OZ_MIN) == 128
