@@ -7,7 +7,9 @@ CPU-baseline leg of ``bench.py`` may import this package.  The library's
 product path never does; it shares no code with the CUDA implementation.
 
 The arithmetic lives in ``oracle.c`` (compiled to ``liboracle.so`` by
-``oracle/build.py``); this module only marshals numpy arrays.  Matrices are
+``oracle/build.py``); this module only marshals numpy arrays.  The oracle of
+the emulated FP64 GEMM (not in the paper) is ``oracle/ozaki.py``, exact
+integer arithmetic in Python and numpy.  Matrices are
 numpy float64 arrays in Fortran (column-major) order, as LAPACK stores them;
 each call works on a copy unless ``inplace=True``.
 

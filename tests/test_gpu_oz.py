@@ -234,3 +234,22 @@ def test_getrf_oz_wide(oz_min_64):
     F, ipiv, info = getrf_oz(A)
     assert info == 0
     assert oracle.res_lu(A, F, ipiv) <= 10.0
+
+
+@pytest.mark.parametrize("S", [6, 7, 8])
+@pytest.mark.parametrize("ta,tb,m,n,k", [(False, False, 150, 70, 300), (True, False, 129, 64, 200),
+                                         (False, True, 40, 130, 513), (True, True, 200, 33, 64)])
+def test_bit_identical_to_the_oracle(S, ta, tb, m, n, k):
+    """Every intermediate sum of the scheme is exact and the result is rounded
+    once, so the GPU returns the oracle's binary64 values bit for bit (k <=
+    600 keeps the integer accumulators below 2^53 before that rounding)."""
+    from oracle import ozaki
+    rng = np.random.default_rng(7400 + S + m + k)
+    opA = rng.standard_normal((m, k)) * np.exp2(rng.integers(-25, 25, size=(m, 1)))
+    opB = rng.standard_normal((k, n)) * np.exp2(rng.integers(-25, 25, size=(1, n)))
+    opA[m // 3, :] = 0.0
+    A = np.asfortranarray(opA.T) if ta else opA
+    B = np.asfortranarray(opB.T) if tb else opB
+    ref = ozaki.gemm(A, B, S, ta, tb)
+    C = oz_gemm(S, ta, tb, A, B, np.zeros((m, n)))
+    assert np.array_equal(C, ref)

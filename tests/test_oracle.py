@@ -770,3 +770,105 @@ def test_upper_forms_are_the_transposed_lower_forms(oracle, n):
     ref, info_l = lapack.zpotrf(H, lower=0)
     assert info == info_l == 0
     assert np.max(np.abs(np.triu(np.tril(Lz).conj().T) - np.triu(ref))) <= tol * np.max(np.abs(ref))
+
+
+# ----------------------------------------------------------------------------
+# the emulated FP64 GEMM (oracle/ozaki.py): not in the paper; pinned by the
+# exact product of integers, the scheme's error bound against exact rational
+# products, the digit identity, and planted mistakes that the bound catches
+# ----------------------------------------------------------------------------
+
+from fractions import Fraction  # noqa: E402
+
+from oracle import ozaki  # noqa: E402
+
+
+def test_ozaki_digits_reconstruct_and_stay_in_range():
+    rng = np.random.default_rng(11)
+    for S in (6, 7, 8):
+        for _ in range(2000):
+            q = rng.uniform(-0.5, 0.5) * 2.0 ** int(rng.integers(-40, 1))
+            Q = ozaki.fixed_point(q, 0, S)
+            d = ozaki.digits(Q, S)
+            assert sum(ds * 256 ** (S - 1 - i) for i, ds in enumerate(d)) == Q
+            assert all(-128 <= x <= 127 for x in d[1:]) and -128 <= d[0] <= 128
+        # near 1/2 the top digit reaches 128 (no carry out)
+        Q = ozaki.fixed_point(0.5 - 2.0 ** -54, 0, S)
+        assert ozaki.digits(Q, S)[0] == 128
+    # ties round away from zero
+    assert ozaki.fixed_point(2.0 ** -57 * 3, 0, 7) == 2 and ozaki.fixed_point(-(2.0 ** -57) * 3, 0, 7) == -2
+    assert ozaki.exponent_of_max(1.0) == 2 and ozaki.exponent_of_max(0.75) == 1
+    assert ozaki.exponent_of_max(5e-324) == -1072 and ozaki.exponent_of_max(0.0) == 0
+
+
+@pytest.mark.parametrize("S", [6, 7, 8])
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, True), (False, True)])
+def test_ozaki_integer_products_exact(S, ta, tb):
+    rng = np.random.default_rng(12 + S)
+    A = rng.integers(-1000, 1001, size=(40, 23)).astype(np.float64)
+    B = rng.integers(-1000, 1001, size=(40, 17)).astype(np.float64)
+    A = A if ta else np.asfortranarray(A.T)                   # op(A): 23 x 40
+    B = np.asfortranarray(B.T) if tb else B                   # op(B): 40 x 17
+    exact = (A.T if ta else A).astype(np.int64) @ (B.T if tb else B).astype(np.int64)
+    assert np.array_equal(ozaki.gemm(A, B, S, ta, tb), exact.astype(np.float64))
+
+
+def _exact_product(A, B):
+    m, k = A.shape
+    n = B.shape[1]
+    Af = [[Fraction(float(v)) for v in row] for row in A]
+    Bf = [[Fraction(float(B[kk, j])) for kk in range(k)] for j in range(n)]
+    return [[sum(a * b for a, b in zip(Af[i], Bf[j])) for j in range(n)] for i in range(m)]
+
+
+def _bound_ok(C, A, B, S, exact, levels_dropped=0):
+    m, k = A.shape
+    ok = True
+    for i in range(m):
+        ea = ozaki.exponent_of_max(float(np.max(np.abs(A[i]))))
+        for j in range(B.shape[1]):
+            eb = ozaki.exponent_of_max(float(np.max(np.abs(B[:, j]))))
+            bound = Fraction(k * (S + 1)) * Fraction(2) ** (-8 * S - 2 + ea + eb)
+            bound += abs(exact[i][j]) * Fraction(2) ** -53
+            ok &= abs(Fraction(float(C[i, j])) - exact[i][j]) <= bound
+    return ok
+
+
+@pytest.mark.parametrize("S", [6, 7, 8])
+def test_ozaki_error_bound_against_exact_rationals(S):
+    rng = np.random.default_rng(13 + S)
+    A = rng.standard_normal((6, 40)) * np.exp2(rng.integers(-20, 20, size=(6, 1)))
+    B = rng.standard_normal((40, 5)) * np.exp2(rng.integers(-20, 20, size=(1, 5)))
+    A[2, :] = 0.0
+    exact = _exact_product(A, B)
+    C = ozaki.gemm(A, B, S)
+    assert _bound_ok(C, A, B, S, exact)
+    assert np.all(C[2, :] == 0.0)
+
+
+def test_ozaki_planted_mistakes_break_the_bound():
+    """A dropped top level, or digit planes taken in reverse order, leave the
+    derived bound by orders of magnitude."""
+    S = 7
+    rng = np.random.default_rng(14)
+    A = rng.standard_normal((5, 30))
+    B = rng.standard_normal((30, 4))
+    exact = _exact_product(A, B)
+    eA, DA = ozaki.slice_rows(A, S)
+    eB, DB = ozaki.slice_rows(B.T, S)
+
+    def combine(T):
+        C = np.zeros((5, 4))
+        for i in range(5):
+            for j in range(4):
+                V = sum(int(T[L][i, j]) << (8 * (S + 1 - L)) for L in T)
+                C[i, j] = np.ldexp(float(V), eA[i] + eB[j] - 8 * (S + 1))
+        return C
+
+    T = ozaki.level_sums(DA, DB, S)
+    assert _bound_ok(combine(T), A, B, S, exact)
+    T_drop = dict(T)
+    del T_drop[S + 1]
+    assert not _bound_ok(combine(T_drop), A, B, S, exact)
+    T_rev = ozaki.level_sums(DA[::-1], DB, S)
+    assert not _bound_ok(combine(T_rev), A, B, S, exact)
