@@ -63,6 +63,10 @@ def _lib():
             "or_zlaswp": (None, [_i64, _ptr, _i64, _i64, _i64, _ptr]),
             "or_res_zchol": (_dbl, [_i64, _ptr, _i64, _ptr, _i64]),
             "or_res_zlu": (_dbl, [_i64, _i64, _ptr, _i64, _ptr, _i64, _ptr]),
+            "or_ztrtri": (_i64, [ctypes.c_int, _i64, _ptr, _i64]),
+            "or_zlauum": (None, [_i64, _ptr, _i64]),
+            "or_zpotri": (_i64, [_i64, _ptr, _i64]),
+            "or_zgetri": (None, [_i64, _ptr, _i64, _ptr, _ptr, _i64]),
             "or_sygst": (_i64, [ctypes.c_int, _i64, _ptr, _i64, _ptr, _i64]),
             "or_gemm": (None, [ctypes.c_int, ctypes.c_int, _i64, _i64, _i64, _dbl,
                                _ptr, _i64, _ptr, _i64, _ptr, _i64]),
@@ -303,6 +307,37 @@ def zgetrf(A, c=24):
     ipiv = np.zeros(max(1, min(m, n)), dtype=np.int32)
     info = _lib().or_zgetrf(m, n, _p(A), _ld(A), _p(ipiv), c)
     return A, ipiv[:min(m, n)], int(info)
+
+
+def ztrtri(L, unit=False):
+    """L^{-1} (lower, complex), by substitution; returns (A, info)."""
+    L = _c128(L)
+    info = _lib().or_ztrtri(int(unit), L.shape[0], _p(L), _ld(L))
+    return L, int(info)
+
+
+def zlauum(L):
+    """L^H L (lower triangle written)."""
+    L = _c128(L)
+    _lib().or_zlauum(L.shape[0], _p(L), _ld(L))
+    return L
+
+
+def zpotri(L):
+    """(L L^H)^{-1} from the factor L; returns (A, info)."""
+    L = _c128(L)
+    info = _lib().or_zpotri(L.shape[0], _p(L), _ld(L))
+    return L, int(info)
+
+
+def zgetri(LU, ipiv):
+    """A^{-1} from P A = L U (complex)."""
+    LU = _c128(LU)
+    n = LU.shape[0]
+    X = np.zeros((n, n), dtype=np.complex128, order="F")
+    piv = np.ascontiguousarray(ipiv, dtype=np.int32)
+    _lib().or_zgetri(n, _p(LU), _ld(LU), _p(piv), _p(X), _ld(X))
+    return X
 
 
 def res_zchol(A0, L):

@@ -31,6 +31,10 @@
  *                   the inverse by its definition, A X = I
  *   or_zpotrf,      complex double peers (Section 5: s, d, c and z): the
  *   or_zgetrf       same recursions with the conjugate transpose
+ *   or_ztrtri,      complex inversions, each its definition written out
+ *   or_zlauum,      (substitution on L X = I; L^H L; L^{-H} L^{-1}; A X = I
+ *   or_zpotri,      on the factors)
+ *   or_zgetri
  *   or_sygst        Section 5, xsygst (A := L^{-1} A L^{-T}, or L^T A L):
  *                   the definition, by substitution and products
  *   metrics         normwise backward errors used by the benchmark spec's bound
@@ -1212,3 +1216,90 @@ double or_res_zlu(int64_t m, int64_t n, const zc_t *A0, int64_t lda0, const zc_t
     return rmax / ((double)n * 0x1p-53 * amax);
 }
 
+
+/* -------------------------------------------------------------------------- */
+/* Complex double inversions (Section 5: the c/z peers of xtrtri, xlauum,    */
+/* xpotri, xgetri), each its definition written out.                          */
+/* -------------------------------------------------------------------------- */
+
+/* X = L^{-1} (lower; unit: diagonal taken as 1) by forward substitution on
+ * L x = e_j, column by column; info = first exactly-zero diagonal entry
+ * (1-based, A unchanged then).  Sums accumulated in increasing k. */
+int64_t or_ztrtri(int unit, int64_t n, zc_t *A, int64_t lda)
+{
+    if (n <= 0) return 0;
+    if (!unit)
+        for (int64_t i = 0; i < n; ++i)
+            if (ZT(A, lda, i, i) == 0.0) return i + 1;
+    zc_t *X = (zc_t *)calloc((size_t)n * (size_t)n, sizeof(zc_t));
+    if (!X) return -1;
+    for (int64_t j = 0; j < n; ++j) {
+        X[(size_t)j * n + j] = unit ? 1.0 : 1.0 / ZT(A, lda, j, j);
+        for (int64_t i = j + 1; i < n; ++i) {
+            zc_t s = 0.0;
+            for (int64_t k = j; k < i; ++k) s += ZT(A, lda, i, k) * X[(size_t)j * n + k];
+            X[(size_t)j * n + i] = unit ? -s : -s / ZT(A, lda, i, i);
+        }
+    }
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = j; i < n; ++i)
+            if (!(unit && i == j)) ZT(A, lda, i, j) = X[(size_t)j * n + i];
+    free(X);
+    return 0;
+}
+
+/* A := L^H L (lower triangle written): (L^H L)_ij = sum_{k >= i} conj(l_ki) l_kj. */
+void or_zlauum(int64_t n, zc_t *A, int64_t lda)
+{
+    if (n <= 0) return;
+    zc_t *T = (zc_t *)malloc(sizeof(zc_t) * (size_t)n * (size_t)n);
+    if (!T) return;
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = j; i < n; ++i) {
+            zc_t s = 0.0;
+            for (int64_t k = i; k < n; ++k) s += conj(ZT(A, lda, k, i)) * ZT(A, lda, k, j);
+            T[(size_t)j * n + i] = s;
+        }
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = j; i < n; ++i) ZT(A, lda, i, j) = T[(size_t)j * n + i];
+    free(T);
+}
+
+/* A^{-1} = (L L^H)^{-1} = L^{-H} L^{-1}: ztrtri then zlauum on the factor. */
+int64_t or_zpotri(int64_t n, zc_t *A, int64_t lda)
+{
+    int64_t info = or_ztrtri(0, n, A, lda);
+    if (info) return info;
+    or_zlauum(n, A, lda);
+    return 0;
+}
+
+/* X := A^{-1} from P A = L U (factors and 1-based ipiv as or_zgetrf returns
+ * them), by its definition A X = I: X = I with P applied, then L Y = P,
+ * then U X = Y, column by column. */
+void or_zgetri(int64_t n, const zc_t *LU, int64_t lda, const int32_t *ipiv, zc_t *X, int64_t ldx)
+{
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < n; ++i) ZT(X, ldx, i, j) = (i == j) ? 1.0 : 0.0;
+    for (int64_t i = 0; i < n; ++i) {            /* row interchanges in order */
+        int64_t p = ipiv[i] - 1;
+        if (p != i)
+            for (int64_t j = 0; j < n; ++j) {
+                zc_t t = ZT(X, ldx, i, j);
+                ZT(X, ldx, i, j) = ZT(X, ldx, p, j);
+                ZT(X, ldx, p, j) = t;
+            }
+    }
+    for (int64_t j = 0; j < n; ++j) {
+        for (int64_t i = 0; i < n; ++i) {        /* L unit lower */
+            zc_t s = ZT(X, ldx, i, j);
+            for (int64_t k = 0; k < i; ++k) s -= ZT(LU, lda, i, k) * ZT(X, ldx, k, j);
+            ZT(X, ldx, i, j) = s;
+        }
+        for (int64_t i = n - 1; i >= 0; --i) {   /* U upper */
+            zc_t s = ZT(X, ldx, i, j);
+            for (int64_t k = i + 1; k < n; ++k) s -= ZT(LU, lda, i, k) * ZT(X, ldx, k, j);
+            ZT(X, ldx, i, j) = s / ZT(LU, lda, i, i);
+        }
+    }
+}

@@ -264,3 +264,31 @@ def test_zgetri(n):
     # ||A X - I|| / (||A|| ||X|| n eps), 1-norms
     res = np.abs(R).sum(0).max() / (np.abs(A).sum(0).max() * np.abs(X).sum(0).max() * n * 2.0 ** -53)
     assert res <= 10.0
+
+
+@pytest.mark.parametrize("n", [65, 300])
+def test_complex_inversions_vs_oracle(n):
+    """Random well-conditioned inputs against the oracle's definitions (the
+    tolerances the oracle itself meets against LAPACK)."""
+    r = G.lib()
+    t = G.torch()
+    tol = 64 * n * 2.0 ** -53
+    H = inputs.herm_spd(n, inputs.seed_for(1, 6000 + n))
+    L = np.asfortranarray(np.tril(oracle.zpotrf(H)[0]))
+    info = G.int_buf(1, -77)
+    for fn, ref in ((lambda d: r.rl_ztrtri("L", "N", n, d.ptr(), n, info.data_ptr()), oracle.ztrtri(L)[0]),
+                    (lambda d: r.rl_zlauum("L", n, d.ptr(), n, info.data_ptr()), oracle.zlauum(L)),
+                    (lambda d: r.rl_zpotri("L", n, d.ptr(), n, info.data_ptr()), oracle.zpotri(L)[0])):
+        d = ZMat(L)
+        zcall(fn, d)
+        assert int(info[0]) == 0
+        assert np.max(np.abs(np.tril(d.get()) - np.tril(ref))) <= tol * 8 * np.max(np.abs(ref))
+    A = inputs.complex_uniform(n, n, inputs.seed_for(1, 6100 + n))
+    F, ipiv, _ = zgetrf(A)
+    d = ZMat(F)
+    dp = t.from_numpy(ipiv.astype(np.int32)).cuda()
+    lw = r.rl_zgetri_work_size(n)
+    w = t.empty(lw, dtype=t.uint8, device="cuda")
+    zcall(r.rl_zgetri, n, d.ptr(), n, dp.data_ptr(), info.data_ptr(), w.data_ptr(), lw)
+    ref = oracle.zgetri(F, ipiv)
+    assert np.max(np.abs(d.get() - ref)) <= tol * 8 * np.linalg.cond(A) * np.max(np.abs(ref))

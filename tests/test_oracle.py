@@ -872,3 +872,57 @@ def test_ozaki_planted_mistakes_break_the_bound():
     assert not _bound_ok(combine(T_drop), A, B, S, exact)
     T_rev = ozaki.level_sums(DA[::-1], DB, S)
     assert not _bound_ok(combine(T_rev), A, B, S, exact)
+
+
+# ----------------------------------------------------------------------------
+# complex inversions (oracle ztrtri / zlauum / zpotri / zgetri)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 6, 40, 100])
+def test_complex_inversions_exact_on_gaussian_integers(oracle, n):
+    L, Linv = inputs.gaussian_unit_trtri(n, inputs.seed_for(0, 1800 + n))
+    X, info = oracle.ztrtri(L)
+    assert info == 0 and np.array_equal(np.tril(X), Linv)
+    Lu = np.asfortranarray(np.tril(np.diag(1.0 / np.diag(L)) @ L))
+    X, _ = oracle.ztrtri(Lu, unit=True)
+    assert np.array_equal(np.tril(X, -1), np.tril(Linv @ np.diag(np.diag(L)), -1))
+    P = oracle.zlauum(L)
+    assert np.array_equal(np.tril(P), np.tril(L.conj().T @ L))
+    Q, info = oracle.zpotri(L)
+    assert info == 0 and np.array_equal(np.tril(Q), np.tril(Linv.conj().T @ Linv))
+
+
+@pytest.mark.parametrize("n", [1, 17, 120])
+def test_complex_inversions_vs_lapack(oracle, n):
+    tol = 64 * n * 2.0 ** -53
+    H = inputs.herm_spd(n, inputs.seed_for(0, 1900 + n))
+    L = np.asfortranarray(np.tril(oracle.zpotrf(H)[0]))
+    X, info = oracle.ztrtri(L)
+    ref, info_l = lapack.ztrtri(L, lower=1)
+    assert info == info_l == 0
+    assert np.max(np.abs(np.tril(X) - np.tril(ref))) <= tol * 8 * np.max(np.abs(ref))
+    P = oracle.zlauum(L)
+    ref, _ = lapack.zlauum(L, lower=1)
+    assert np.max(np.abs(np.tril(P) - np.tril(ref))) <= tol * np.max(np.abs(ref))
+    Q, info = oracle.zpotri(L)
+    ref, _ = lapack.zpotri(L, lower=1)
+    assert np.max(np.abs(np.tril(Q) - np.tril(ref))) <= tol * 8 * np.max(np.abs(ref))
+    G = inputs.complex_uniform(n, n, inputs.seed_for(0, 1950 + n))
+    F, ipiv, info = oracle.zgetrf(G)
+    Xg = oracle.zgetri(F, ipiv)
+    ref, info_l = lapack.zgetri(*lapack.zgetrf(G)[:2])
+    kappa = np.linalg.cond(G)
+    assert np.max(np.abs(Xg - ref)) <= tol * 8 * kappa * np.max(np.abs(ref))
+    assert np.max(np.abs(G @ Xg - np.eye(n))) <= tol * 8 * kappa
+
+
+def test_complex_inversion_planted_mistakes(oracle):
+    """Dropping the conjugate in L^H L, or the interchanges in getri, is seen."""
+    n = 30
+    L, Linv = inputs.gaussian_unit_trtri(n, inputs.seed_for(0, 1990))
+    P = oracle.zlauum(L)
+    assert not np.array_equal(np.tril(P), np.tril(L.T @ L))
+    G = inputs.complex_uniform(n, n, inputs.seed_for(0, 1991))
+    F, ipiv, _ = oracle.zgetrf(G)
+    assert np.max(np.abs(G @ oracle.zgetri(F, ipiv) - np.eye(n))) < 1e-10
+    assert np.max(np.abs(G @ oracle.zgetri(F, np.arange(1, n + 1)) - np.eye(n))) > 1e-3
