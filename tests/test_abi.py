@@ -152,3 +152,13 @@ def test_host_logic_of_the_complex_upper_and_emulated_calls(built):
     assert r.rl_dgetrf_oz(7, 4, 4, 8, 4, 8, 8, None, 0, stream=0) == r.RL_ERR_WORKSPACE
     assert r.rl_set_param(r.RL_PARAM_OZ_MIN, 0) == r.RL_ERR_PARAM
     assert r.rl_get_param(r.RL_PARAM_OZ_MIN) == 128
+
+
+def test_binding_has_every_declared_entry_point(built):
+    """The Python binding carries the same names as the C ABI: a ctypes
+    signature and a wrapper function for each declared routine."""
+    from paper_1602_06763_gb300 import relgpu as r
+    src = open(os.path.join(ROOT, "paper_1602_06763_gb300", "relgpu.py")).read()
+    for name in declared_functions():
+        assert f'"{name}"' in src, name
+        assert callable(getattr(r, name, None)), name
