@@ -77,7 +77,9 @@ enum {
  * Section 3).  With n1 ~ n/2: potrf(A11); A21 := A21 L11^{-T} (TRSM);
  * A22 := A22 - A21 A21^T (SYRK, lower triangle); potrf(A22).  Base case: an
  * unblocked Cholesky of a diagonal block in shared memory (IEEE sqrt and
- * division).  A: n x n, lower triangle overwritten by L.
+ * division).  A: n x n, lower triangle overwritten by L (uplo 'L'), or
+ * upper triangle by U with A = U^T U (uplo 'U', the transposed-storage form
+ * described at the top of this file).
  * Argument numbers: 1 uplo, 2 n, 3 A, 4 lda, 5 info.
  * Workspace: none (work may be NULL, lwork 0).
  * ------------------------------------------------------------------------- */
@@ -104,10 +106,11 @@ int rl_dgetrf(int64_t m, int64_t n, double *A, int64_t lda, int32_t *ipiv,
 size_t rl_dgetrf_work_size(int64_t m, int64_t n);
 
 /* ---------------------------------------------------------------------------
- * dtrtri -- recursive inverse of a lower triangular matrix in place
+ * dtrtri -- recursive inverse of a triangular matrix in place
  * (Section 3, Fig. 4): trtri(A_TL); A_BL := A_BL A_TL (TRMM, A_TL already
  * inverted); A_BL := -A_BR^{-1} A_BL (TRSM with the not yet inverted A_BR);
  * trtri(A_BR).  Base case: an unblocked inverse in shared memory.
+ * uplo 'U': the upper triangular matrix is inverted in its triangle.
  * diag: 'N' (non-unit) or 'U' (unit diagonal, not referenced).
  * Argument numbers: 1 uplo, 2 diag, 3 n, 4 A, 5 lda, 6 info.
  * Workspace: none.
@@ -119,7 +122,8 @@ int rl_dtrtri(char uplo, char diag, int64_t n, double *A, int64_t lda,
  * dlauum -- A := L^T L for lower triangular L in place (Section 5, xlauum),
  * recursively: lauum(A11); A11 := A11 + A21^T A21 (SYRK); A21 := A22^T A21
  * (TRMM); lauum(A22).  The lower triangle of the symmetric result is
- * written.  Argument numbers: 1 uplo, 2 n, 3 A, 4 lda, 5 info.
+ * written (uplo 'U': A := U U^T in the upper triangle).
+ * Argument numbers: 1 uplo, 2 n, 3 A, 4 lda, 5 info.
  * Workspace: none.  *info is always 0.
  * ------------------------------------------------------------------------- */
 int rl_dlauum(char uplo, int64_t n, double *A, int64_t lda, int32_t *info,
@@ -129,7 +133,8 @@ int rl_dlauum(char uplo, int64_t n, double *A, int64_t lda, int32_t *info,
  * dpotri -- inverse of an SPD matrix from its Cholesky factor: dtrtri then
  * dlauum on L (Section 5: xtrtri is the building block of xpotri), since
  * A^{-1} = L^{-T} L^{-1}.  A holds L on entry and the lower triangle of
- * A^{-1} on exit.  Argument numbers: 1 uplo, 2 n, 3 A, 4 lda, 5 info.
+ * A^{-1} on exit (uplo 'U': U from A = U^T U, and the upper triangle).
+ * Argument numbers: 1 uplo, 2 n, 3 A, 4 lda, 5 info.
  * ------------------------------------------------------------------------- */
 int rl_dpotri(char uplo, int64_t n, double *A, int64_t lda, int32_t *info,
               void *work, size_t lwork, rl_stream_t stream);
@@ -243,7 +248,8 @@ int rl_spotrs(char uplo, int64_t n, int64_t nrhs, const float *A, int64_t lda, f
  * Complex double peers (Section 5: every routine exists for s, d, c and z).
  * rl_double_complex is LAPACK's complex*16 layout (re, im interleaved).
  *   rl_zpotrf: A = L L^H (Hermitian positive definite, lower triangle read;
- *     the diagonal's imaginary part is ignored), info as rl_dpotrf.
+ *     the diagonal's imaginary part is ignored), or A = U^H U (uplo 'U'),
+ *     info as rl_dpotrf.
  *   rl_zgetrf: P A = L U with partial pivoting on |Re| + |Im| (LAPACK's
  *     izamax), lowest row on ties; ipiv, info and workspace
  *     (rl_dgetrf_work_size) as rl_dgetrf; panels of at most 32 columns.
