@@ -577,6 +577,10 @@ int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda,
  *   RL_PARAM_OZ_MIN            smallest m, n and k of an FP64 update that
  *                              the *_oz routines emulate on the tensor
  *                              cores (default 128; smaller ones stay FP64)
+ *   RL_PARAM_NVTX              1: every recursion node (potrf, getrf,
+ *                              trtri, lauum) pushes an NVTX range named by
+ *                              routine, order and depth, for timeline
+ *                              tools; 0 (default): none
  * rl_set_param returns 0 or RL_ERR_PARAM; rl_get_param returns the value or
  * -1 for an unknown key.
  * ------------------------------------------------------------------------- */
@@ -589,7 +593,8 @@ enum {
     RL_PARAM_TRI_LANES = 6,
     RL_PARAM_LOOKAHEAD = 7,
     RL_PARAM_PANEL_CTAS = 8,
-    RL_PARAM_OZ_MIN = 9
+    RL_PARAM_OZ_MIN = 9,
+    RL_PARAM_NVTX = 10
 };
 int rl_set_param(int key, int64_t value);
 int64_t rl_get_param(int key);

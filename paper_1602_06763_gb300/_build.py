@@ -68,7 +68,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
                     raise RuntimeError(f"nvcc failed: {' '.join(cmd)}")
     if _stale(OUT, objs):
         tmp = OUT + f".tmp{os.getpid()}"
-        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
+        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-ldl"]      # libdl: NVTX's tool loader
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.run(cmd, check=True)

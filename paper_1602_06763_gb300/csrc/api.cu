@@ -12,6 +12,9 @@
 #include <vector>
 #include "internal.cuh"
 
+#include <cstdio>
+#include <nvtx3/nvToolsExt.h>
+
 namespace rl {
 
 std::atomic<uint64_t> g_launches{0};
@@ -114,6 +117,24 @@ static bool lookahead_ok(const Ctx &c)
     return g_params.lookahead && c.tcwork == nullptr && (c.ozwork == nullptr || c.ozwork2 != nullptr);
 }
 
+// NVTX range of one recursion node ("potrf n=4096 d=1") when RL_PARAM_NVTX
+// is set, for timeline tools (Figs. 2 and 5 break the time down per call and
+// per recursion level); nothing is pushed otherwise.
+struct NvtxNode {
+    bool on;
+    NvtxNode(const char *routine, i64 n, int depth) : on(g_params.nvtx != 0)
+    {
+        if (!on) return;
+        char buf[64];
+        snprintf(buf, sizeof buf, "%s n=%lld d=%d", routine, (long long)n, depth);
+        nvtxRangePushA(buf);
+    }
+    ~NvtxNode()
+    {
+        if (on) nvtxRangePop();
+    }
+};
+
 // ---- recursions -------------------------------------------------------------
 
 // Cholesky: potrf(A11); A21 := A21 L11^{-T}; A22 -= A21 A21^T; potrf(A22).
@@ -126,6 +147,7 @@ template <typename T>
 static void potrf_rec_la(Ctx &c, i64 n, T *A, i64 lda, i64 off, cudaEvent_t pending, int depth)
 {
     if (n <= 0) return;
+    NvtxNode nv("potrf", n, depth);
     if (n <= g_params.potrf_c) {
         if (pending) note(c, cudaStreamWaitEvent(c.s, pending, 0));
         potf2<T>(c, n, A, lda, off);
@@ -185,6 +207,7 @@ static void getrf_rec_la(Ctx &c, T *A0, i64 lda, i64 m_tot, int32_t *ipiv, i64 r
                          cudaEvent_t pending, int depth)
 {
     if (m <= 0 || n <= 0) return;
+    NvtxNode nv("getrf", n, depth);
     T *A = A0 + r0 + r0 * lda;
     const i64 nb = is_cplx<T>::value && g_params.getrf_nb > 32 ? 32 : g_params.getrf_nb;   // complex panels <= 32
     if (n <= nb) {
@@ -261,6 +284,7 @@ template <typename T>
 void trtri_rec(Ctx &c, bool unit, i64 n, T *A, i64 lda)
 {
     if (n <= 0) return;
+    NvtxNode nv("trtri", n, -1);
     const i64 base = sizeof(T) > 8 && g_params.trtri_c > 32 ? 32 : g_params.trtri_c;   // complex: <= 32
     if (n <= base) { trti2<T>(c, unit, n, A, lda); return; }
     const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
@@ -280,6 +304,7 @@ template <typename T>
 static void lauum_rec(Ctx &c, i64 n, T *A, i64 lda)
 {
     if (n <= 0) return;
+    NvtxNode nv("lauum", n, -1);
     const i64 base = sizeof(T) > 8 && g_params.trtri_c > 32 ? 32 : g_params.trtri_c;
     if (n <= base) { lauu2<T>(c, n, A, lda); return; }
     const i64 n1 = split_q(n, TRX_NB), n2 = n - n1;
@@ -1565,6 +1590,10 @@ int rl_set_param(int key, int64_t value)
         if (value != 0 && value != 1) return RL_ERR_PARAM;
         g_params.lookahead = (int)value;
         return RL_SUCCESS;
+    case RL_PARAM_NVTX:
+        if (value != 0 && value != 1) return RL_ERR_PARAM;
+        g_params.nvtx = (int)value;
+        return RL_SUCCESS;
     case RL_PARAM_OZ_MIN:
         if (value < 1 || value > (1 << 20)) return RL_ERR_PARAM;
         g_params.oz_min = (int)value;
@@ -1591,6 +1620,7 @@ int64_t rl_get_param(int key)
     case RL_PARAM_TRI_LANES: return g_params.tri_lanes;
     case RL_PARAM_LOOKAHEAD: return g_params.lookahead;
     case RL_PARAM_OZ_MIN: return g_params.oz_min;
+    case RL_PARAM_NVTX: return g_params.nvtx;
     case RL_PARAM_PANEL_CTAS: return (int64_t)g_params.panel_ctas64 | ((int64_t)g_params.panel_ctas32 << 16);
     default: return -1;
     }

@@ -79,6 +79,7 @@ struct Params {
     int panel_ctas64 = 0;    // LU panel CTAs, FP64 / FP32 (0 = one per SM)
     int panel_ctas32 = 0;
     int oz_min = 128;        // smallest m, n and k that the FP64 emulation takes
+    int nvtx = 0;            // 1: an NVTX range per recursion node (routine, order, depth)
 };
 extern Params g_params;
 

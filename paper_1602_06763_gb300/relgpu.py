@@ -150,6 +150,7 @@ RL_PARAM_TRI_LANES = 6
 RL_PARAM_LOOKAHEAD = 7
 RL_PARAM_PANEL_CTAS = 8
 RL_PARAM_OZ_MIN = 9
+RL_PARAM_NVTX = 10
 
 
 def _ptr(x):

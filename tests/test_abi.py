@@ -152,6 +152,10 @@ def test_host_logic_of_the_complex_upper_and_emulated_calls(built):
     assert r.rl_dgetrf_oz(7, 4, 4, 8, 4, 8, 8, None, 0, stream=0) == r.RL_ERR_WORKSPACE
     assert r.rl_set_param(r.RL_PARAM_OZ_MIN, 0) == r.RL_ERR_PARAM
     assert r.rl_get_param(r.RL_PARAM_OZ_MIN) == 128
+    assert r.rl_get_param(r.RL_PARAM_NVTX) == 0
+    assert r.rl_set_param(r.RL_PARAM_NVTX, 2) == r.RL_ERR_PARAM
+    assert r.rl_set_param(r.RL_PARAM_NVTX, 1) == 0 and r.rl_get_param(r.RL_PARAM_NVTX) == 1
+    assert r.rl_set_param(r.RL_PARAM_NVTX, 0) == 0
 
 
 def test_binding_has_every_declared_entry_point(built):

@@ -102,3 +102,23 @@ def test_clear_cache_releases_and_recreates_the_side_stream():
     assert np.array_equal(p0, p1) and np.array_equal(F0, F1)
     assert r.rl_clear_cache() == 0
     assert r.rl_clear_cache() == 0                # nothing left to release
+
+
+def test_nvtx_ranges_change_nothing():
+    """With RL_PARAM_NVTX on, every recursion node pushes a named NVTX range
+    (a no-op without a timeline tool attached): the same bits come out."""
+    r = G.lib()
+    n = 1100
+    A = inputs.spd_bbt(n, seed=inputs.seed_for(1, 1600))
+    L0, _ = G.potrf(A)
+    F0, p0, _ = G.getrf(A)
+    assert r.rl_set_param(r.RL_PARAM_NVTX, 1) == 0
+    try:
+        L1, _ = G.potrf(A)
+        F1, p1, _ = G.getrf(A)
+        X1, _ = G.trtri(np.tril(L0))
+    finally:
+        assert r.rl_set_param(r.RL_PARAM_NVTX, 0) == 0
+    assert np.array_equal(L0, L1) and np.array_equal(F0, F1) and np.array_equal(p0, p1)
+    X0, _ = G.trtri(np.tril(L0))
+    assert np.array_equal(X0, X1)
