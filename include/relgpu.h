@@ -436,7 +436,10 @@ int rl_dtrmm(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
  * pointers).  max_n (host) bounds n[b] and must be <= 256.  info[b] follows
  * LAPACK for matrix b (dpotrf: first non-positive minor; dgetrf: first zero
  * pivot, factorization completed); ipiv[b] has n[b] 1-based entries.
- * Matrices with n[b] <= 0 or n[b] > 256 are skipped with info[b] = 0.
+ * A matrix with n[b] = 0 is left alone with info[b] = 0; one with n[b] < 0
+ * or n[b] > 256 gets info[b] = -3 (potrf) / -2 (getrf), one with
+ * lda[b] < max(1, n[b]) gets info[b] = -5 / -4 (LAPACK's argument numbers
+ * of the order and leading-dimension arrays), and is not touched.
  * Workspace: rl_potrf_vbatched_work_size / rl_getrf_vbatched_work_size
  * bytes (the size-sorted work list and its counter).
  * Argument numbers: potrf 1 uplo, 2 batch; getrf 1 batch.
@@ -555,7 +558,11 @@ int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda,
  *   RL_PARAM_SPIN_LIMIT_NS     bound on every device-side wait, in ns
  *                              (default 2e9); 0 makes any wait that is not
  *                              already satisfied fail with
- *                              RL_INFO_DEVICE_TIMEOUT
+ *                              RL_INFO_DEVICE_TIMEOUT.  The tensor-core
+ *                              kernels' final waits for their own copies
+ *                              and MMAs in flight (before a CTA frees its
+ *                              tensor memory and exits) are never shorter
+ *                              than 1 s, whatever this value
  *   RL_PARAM_BATCH_CTAS        CTAs per SM of the batched kernels (0 = as
  *                              many as fit, the default; 1..8)
  *   RL_PARAM_TRI_LANES         lanes per vector of the triangle kernels at

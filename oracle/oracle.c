@@ -780,7 +780,8 @@ double or_res_potri(int64_t n, const double *A0, int64_t lda0, const double *X,
 /* Random-probe residuals for large n (O(n^2) per probe vector x):
  *   chol:  ||A x - L (L^T x)||_inf / (n eps ||A||_inf ||x||_inf)
  *   lu:    ||P A x - L (U x)||_inf / (n eps ||A||_inf ||x||_inf)
- * A symmetric lower-stored for chol; general for lu.  All sums Dot2. */
+ * A symmetric lower-stored for chol; general for lu.  All sums Dot2; the
+ * intermediate y = L^T x (U x) is stored in binary64, one rounding. */
 static double inf_norm_sym_lower(int64_t n, const double *A, int64_t lda)
 {
     double best = 0.0;

@@ -13,6 +13,7 @@
 #include "internal.cuh"
 
 #include <cstdio>
+#include <map>
 #include <nvtx3/nvToolsExt.h>
 
 namespace rl {
@@ -38,6 +39,22 @@ int device_sms()
 void note(Ctx &c, cudaError_t e)
 {
     if (e != cudaSuccess && c.err == cudaSuccess) c.err = e;
+}
+
+cudaError_t smem_optin(const void *func, int bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, int> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(dev, func);
+    auto it = done.find(key);
+    if (it != done.end() && it->second >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done[key] = bytes;
+    return e;
 }
 
 // ---- lookahead resources ----------------------------------------------------
@@ -1447,6 +1464,16 @@ struct HostCopy {
             return;
         ok = true;
     }
+    // An error after the first copy was queued: wait for everything already
+    // queued on the caller's stream and the copy stream (their status is
+    // not looked at) so that no copy from or to the caller's host buffer is
+    // still running when the error is returned.
+    int fail(cudaStream_t s, int st)
+    {
+        (void)cudaStreamSynchronize(s);
+        if (cs) (void)cudaStreamSynchronize(cs);
+        return st;
+    }
     ~HostCopy()
     {
         for (cudaEvent_t e : {entry, trail, left, left_back})
@@ -1473,10 +1500,10 @@ int rl_dpotrf_host(char uplo, int64_t n, double *A_host, int64_t lda, int32_t *i
     const bool split = is_l(uplo) && n >= HOST_SPLIT_MIN && n > g_params.potrf_c;
     HostCopy hc(split, true);
     if (!split || !hc.ok) {
-        if (bytes && cudaMemcpyAsync(dA, A_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return RL_ERR_CUDA;
+        if (bytes && cudaMemcpyAsync(dA, A_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return hc.fail(s, RL_ERR_CUDA);
         int st = rl_dpotrf(uplo, n, dA, lda, dinfo, nullptr, 0, stream);
-        if (st != RL_SUCCESS) return st;
-        if (bytes && cudaMemcpyAsync(A_host, dA, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return RL_ERR_CUDA;
+        if (st != RL_SUCCESS) return hc.fail(s, st);
+        if (bytes && cudaMemcpyAsync(A_host, dA, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return hc.fail(s, RL_ERR_CUDA);
     } else {
         const i64 n1 = split_q(n, TRX_NB);                      // the recursion's top-level split
         const size_t lb = (size_t)lda * (size_t)n1 * sizeof(double), rb = bytes - lb;
@@ -1496,10 +1523,10 @@ int rl_dpotrf_host(char uplo, int64_t n, double *A_host, int64_t lda, int32_t *i
         note(c, cudaEventRecord(hc.left_back, hc.cs));
         note(c, cudaMemcpyAsync(A_host + (size_t)lda * n1, dA + (size_t)lda * n1, rb, cudaMemcpyDeviceToHost, s));
         note(c, cudaStreamWaitEvent(s, hc.left_back, 0));
-        if (c.err != cudaSuccess) return RL_ERR_CUDA;
+        if (c.err != cudaSuccess) return hc.fail(s, RL_ERR_CUDA);
     }
-    if (cudaMemcpyAsync(info_host, dinfo, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RL_ERR_CUDA;
-    return cudaStreamSynchronize(s) == cudaSuccess ? RL_SUCCESS : RL_ERR_CUDA;
+    if (cudaMemcpyAsync(info_host, dinfo, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return hc.fail(s, RL_ERR_CUDA);
+    return cudaStreamSynchronize(s) == cudaSuccess ? RL_SUCCESS : hc.fail(s, RL_ERR_CUDA);
 }
 
 int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda, int32_t *ipiv_host,
@@ -1530,9 +1557,9 @@ int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda, int32_t *i
     const bool split = n >= HOST_SPLIT_MIN && n1 > 0 && n1 < n && m <= INT32_MAX - 1;
     HostCopy hc(split, false);
     if (!split || !hc.ok || wsz == 0) {
-        if (bytes && cudaMemcpyAsync(dA, A_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return RL_ERR_CUDA;
+        if (bytes && cudaMemcpyAsync(dA, A_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return hc.fail(s, RL_ERR_CUDA);
         int st = rl_dgetrf(m, n, dA, lda, dipiv, dinfo, ws, wsz, stream);
-        if (st != RL_SUCCESS) return st;
+        if (st != RL_SUCCESS) return hc.fail(s, st);
     } else {
         const size_t lb = (size_t)lda * (size_t)n1 * sizeof(double), rb = bytes - lb;
         Ctx c = make_ctx(stream, dinfo, ws, wsz);
@@ -1548,13 +1575,13 @@ int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda, int32_t *i
         // the recursion always reaches its top-level wait; this one keeps s
         // ordered after the copy even if it did not
         note(c, cudaStreamWaitEvent(s, hc.trail, 0));
-        if (c.err != cudaSuccess) return RL_ERR_CUDA;
+        if (c.err != cudaSuccess) return hc.fail(s, RL_ERR_CUDA);
     }
-    if (bytes && cudaMemcpyAsync(A_host, dA, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return RL_ERR_CUDA;
+    if (bytes && cudaMemcpyAsync(A_host, dA, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return hc.fail(s, RL_ERR_CUDA);
     if (mn && cudaMemcpyAsync(ipiv_host, dipiv, mn * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return RL_ERR_CUDA;
-    if (cudaMemcpyAsync(info_host, dinfo, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RL_ERR_CUDA;
-    return cudaStreamSynchronize(s) == cudaSuccess ? RL_SUCCESS : RL_ERR_CUDA;
+        return hc.fail(s, RL_ERR_CUDA);
+    if (cudaMemcpyAsync(info_host, dinfo, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return hc.fail(s, RL_ERR_CUDA);
+    return cudaStreamSynchronize(s) == cudaSuccess ? RL_SUCCESS : hc.fail(s, RL_ERR_CUDA);
 }
 
 // ---- parameters, accounting, status ------------------------------------------

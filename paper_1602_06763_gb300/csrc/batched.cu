@@ -331,9 +331,14 @@ k_batched(int batch, const int32_t *d_n, T *const *d_A, const int32_t *d_lda, in
         __syncthreads();
         if (b < 0) break;
         const int n = d_n[b];
-        if (threadIdx.x == 0) d_info[b] = 0;
+        const int ld = d_lda[b];
+        // an order outside 0..256 or a leading dimension below max(1, n) is
+        // an argument error of that matrix (LAPACK's -i for argument i: the
+        // order array is argument 3 of potrf and 2 of getrf, lda 5 and 4)
+        const int bad = (n < 0 || n > BMAX) ? (LU ? -2 : -3) : (ld < (n > 1 ? n : 1) ? (LU ? -4 : -5) : 0);
+        if (threadIdx.x == 0) d_info[b] = bad;
         __syncthreads();
-        if (n <= 0 || n > BMAX) continue;
+        if (bad != 0 || n == 0) continue;
         if (LU) getrf_one<T, BNB>(d_A[b], n, d_lda[b], d_ipiv[b], d_info + b, sm, wv, wi, s_piv);
         else potrf_one<T, BNB>(d_A[b], n, d_lda[b], d_info + b, sm);
         __syncthreads();
@@ -353,11 +358,7 @@ void launch_batched(Ctx &c, i64 batch, const int32_t *d_n, T *const *d_A, const 
 {
     const size_t smem = batch_smem<T, BNB>(LU);
     auto kern = k_batched<T, LU, BNB, BTHREADS>;
-    static bool attr = false;
-    if (!attr) {
-        note(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    note(c, smem_optin(kern, smem));
     int occ = 0;
     note(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BTHREADS, smem));
     if (occ < 1) occ = 1;

@@ -134,11 +134,7 @@ void potf2<cplx>(Ctx &c, i64 n, cplx *A, i64 lda, i64 info_off)
     if (n <= 0) return;
     if (n > BASE_N) { note(c, cudaErrorInvalidValue); return; }
     const size_t smem = (size_t)BASE_N * (BASE_N + 2) * sizeof(cplx);
-    static bool attr = false;
-    if (!attr) {
-        note(c, cudaFuncSetAttribute(k_zpotf2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    note(c, smem_optin(k_zpotf2, smem));
     Launch L(c, K_POTF2, 4.0 * (double)n * n * n / 3.0, 0.0);
     k_zpotf2<<<1, 256, smem, c.s>>>((int)n, A, lda, c.info, info_off, c.abort);
 }
@@ -680,15 +676,8 @@ void getf2_panel(Ctx &c, i64 m, i64 nb, T *A, i64 lda, int32_t *ipiv, i64 r0)
     const int G = (int)((m + R - 1) / R);
     long long spin = g_params.spin_ns;
     int32_t *info = c.info;
-    static bool attr[2] = {false, false};
-    const int ti = sizeof(T) == 8 ? 0 : 1;
-    if (!attr[ti]) {
-        note(c, cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(PANEL_THREADS * panel_nbmax<T>() * sizeof(T))));
-        note(c, cudaFuncSetAttribute(k_panel_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)PANEL_SMEM_MAX));
-        attr[ti] = true;
-    }
+    note(c, smem_optin(k_panel<T>, PANEL_THREADS * panel_nbmax<T>() * sizeof(T)));
+    note(c, smem_optin(k_panel_smem<T>, (size_t)PANEL_SMEM_MAX));
     // flops of an m x nb unblocked LU (leading terms): m nb^2 - nb^3/3
     Launch L(c, K_PANEL, (double)m * nb * nb - (double)nb * nb * nb / 3.0,
              2.0 * (double)m * nb * sizeof(T));
@@ -797,13 +786,7 @@ template <typename T>
 void laswp(Ctx &c, T *A0, i64 lda, i64 m, i64 c0, i64 ncols, i64 k1, i64 k2, const int32_t *ipiv)
 {
     if (ncols <= 0 || k2 <= k1) return;
-    static bool attr[2] = {false, false};
-    const int ti = sizeof(T) == 8 ? 0 : 1;
-    if (!attr[ti]) {
-        note(c, cudaFuncSetAttribute(k_laswp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)LASWP_SMEM_MAX));
-        attr[ti] = true;
-    }
+    note(c, smem_optin(k_laswp<T>, (size_t)LASWP_SMEM_MAX));
     for (i64 kb = k1; kb < k2; kb += LASWP_CHUNK) {
         const i64 ke = (kb + LASWP_CHUNK < k2) ? kb + LASWP_CHUNK : k2;
         const size_t smem = (size_t)((m - kb) + 3 * (ke - kb)) * sizeof(int);
@@ -867,12 +850,7 @@ void laswp_rev(Ctx &c, T *B, i64 ldb, i64 n, i64 ncols, const int32_t *ipiv)
     if (n <= 1 || ncols <= 0) return;
     const bool staged = n <= LSR_MAX_N;
     const size_t smem = staged ? (size_t)n * sizeof(T) : 0;
-    static bool attr = false;
-    if (!attr) {
-        note(c, cudaFuncSetAttribute(k_laswp_rev<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(LSR_MAX_N * sizeof(T))));
-        attr = true;
-    }
+    note(c, smem_optin(k_laswp_rev<T>, LSR_MAX_N * sizeof(T)));
     Launch L(c, K_LASWP, 0.0, 4.0 * sizeof(T) * (double)n * ncols);
     for (i64 c0 = 0; c0 < ncols; c0 += 65535) {
         const i64 nc = ncols - c0 < 65535 ? ncols - c0 : 65535;

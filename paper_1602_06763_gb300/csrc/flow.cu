@@ -247,12 +247,7 @@ void launch_flow(Ctx &c, i64 n, i64 nrhs, const T *A, i64 lda, T *B, i64 ldb, vo
     unsigned *ticket = static_cast<unsigned *>(ws) + 64;
     unsigned *flags = ticket + 1;
     const size_t smem = (2 * (size_t)FB * FP + (size_t)FB * FR) * sizeof(T);
-    static bool attr = false;
-    if (!attr) {
-        note(c, cudaFuncSetAttribute(k_flow<T, FORM, UNIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-        attr = true;
-    }
+    note(c, smem_optin(k_flow<T, FORM, UNIT>, smem));
     note(c, cudaMemsetAsync(ticket, 0, (1 + (size_t)nblk * nch) * sizeof(unsigned), c.s));
     // n^2 nrhs flops; the triangle is read once, B read and written once
     Launch L(c, K_TRSM, (double)n * n * nrhs,

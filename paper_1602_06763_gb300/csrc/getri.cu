@@ -194,12 +194,7 @@ void getri(Ctx &c, i64 n, T *A, i64 lda, const int32_t *ipiv, void *work)
     uinv_linv_rec<T>(c, n, A, lda);
     PermPlan *plan = static_cast<PermPlan *>(work);
     const size_t smem = (size_t)n * sizeof(int) + (size_t)n;
-    static bool attr = false;
-    if (!attr) {
-        note(c, cudaFuncSetAttribute(k_colperm_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)((size_t)GETRI_MAX_N * 5)));
-        attr = true;
-    }
+    note(c, smem_optin(k_colperm_plan, (size_t)GETRI_MAX_N * 5));
     {
         Launch L(c, K_LASWP, 0.0, 0.0);
         k_colperm_plan<<<1, 256, smem, c.s>>>((int)n, ipiv, plan, c.abort);

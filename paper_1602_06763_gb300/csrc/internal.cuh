@@ -118,6 +118,16 @@ struct Ctx {
 
 int device_sms();
 void note(Ctx &c, cudaError_t e);
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device.  The attribute belongs to the device, so it is set once per
+// (device, kernel) and again only if a larger size is asked for; safe to
+// call from several host threads.
+cudaError_t smem_optin(const void *func, int bytes);
+template <typename F>
+inline cudaError_t smem_optin(F *func, size_t bytes)
+{
+    return smem_optin(reinterpret_cast<const void *>(func), (int)bytes);
+}
 
 // ---- per-kernel tracing (trace.cu) -----------------------------------------
 // Kernel kinds, in the order rl_trace_read reports them.

@@ -294,8 +294,8 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtens
             }
             // drain: every issued copy has landed before the CTA can exit
             for (int g = (ga > A_SLOTS ? ga - A_SLOTS : 0); g < ga; ++g)
-                (void)mbar_wait(&afull[g % A_SLOTS], (g / A_SLOTS) & 1, limit_ns);
-            for (int g = (gb > 2 ? gb - 2 : 0); g < gb; ++g) (void)mbar_wait(&bfull[g & 1], (g >> 1) & 1, limit_ns);
+                (void)mbar_wait(&afull[g % A_SLOTS], (g / A_SLOTS) & 1, drain_limit(limit_ns));
+            for (int g = (gb > 2 ? gb - 2 : 0); g < gb; ++g) (void)mbar_wait(&bfull[g & 1], (g >> 1) & 1, drain_limit(limit_ns));
         }
     } else if (warp <= ISSUERS) {
         // the issuing threads split the levels (each level's MMAs stay in one
@@ -352,7 +352,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtens
                 }
             }
             mma_commit(&final_bar);
-            (void)mbar_wait(&final_bar, 0, limit_ns);
+            (void)mbar_wait(&final_bar, 0, drain_limit(limit_ns));
         }
     } else {
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and columns
@@ -474,12 +474,8 @@ static cudaError_t launch_oz(const CUtensorMap &a, const CUtensorMap &b, int m, 
 {
     auto kern = oz::k_oz_gemm<S, LOWER>;
     constexpr int smem = oz::smem_bytes<S>();
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = smem_optin(kern, (size_t)smem);
+    if (e != cudaSuccess) return e;
     kern<<<grid, oz::THREADS, smem, s>>>(a, b, m, n, nch, alpha, beta, C, ldc, mxA, mxB, tiles_m, tiles_n, err, lim,
                                          abort);
     return cudaGetLastError();

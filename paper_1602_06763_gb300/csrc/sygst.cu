@@ -120,13 +120,7 @@ template <typename T>
 void sygs2(Ctx &c, int itype, i64 n, T *A, i64 lda, const T *L, i64 ldl)
 {
     const size_t smem = 2 * (size_t)SG_N * SG_P * sizeof(T);
-    static bool attr[2] = {false, false};
-    const int ti = itype == 1 ? 0 : 1;
-    if (!attr[ti]) {
-        note(c, cudaFuncSetAttribute(itype == 1 ? k_sygs2<T, 1> : k_sygs2<T, 2>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr[ti] = true;
-    }
+    note(c, smem_optin(itype == 1 ? k_sygs2<T, 1> : k_sygs2<T, 2>, smem));
     Launch Lk(c, K_MIX, (double)n * n * n, 0.0);
     if (itype == 1) k_sygs2<T, 1><<<1, SG_N, smem, c.s>>>((int)n, A, lda, L, ldl, c.abort);
     else k_sygs2<T, 2><<<1, SG_N, smem, c.s>>>((int)n, A, lda, L, ldl, c.abort);

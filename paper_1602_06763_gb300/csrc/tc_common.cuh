@@ -59,6 +59,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
     return true;
 }
 
+// The waits that drain a CTA before it exits (copies still landing in shared
+// memory, MMAs still writing tensor memory) are never shorter than this,
+// whatever the caller's wait bound: a CTA must not free tensor memory or end
+// while the asynchronous units still write into it.
+constexpr long long DRAIN_FLOOR_NS = 1000000000LL;
+
+__device__ __forceinline__ long long drain_limit(long long limit_ns)
+{
+    return limit_ns > DRAIN_FLOOR_NS ? limit_ns : DRAIN_FLOOR_NS;
+}
+
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z)
 {
     asm volatile(

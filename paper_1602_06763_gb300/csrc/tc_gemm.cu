@@ -118,7 +118,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
             }
             // drain: every issued copy has landed before the CTA can exit
             for (int gg = (g > STAGES ? g - STAGES : 0); gg < g; ++gg)
-                (void)mbar_wait(&full_bar[gg % STAGES], (gg / STAGES) & 1, limit_ns);
+                (void)mbar_wait(&full_bar[gg % STAGES], (gg / STAGES) & 1, drain_limit(limit_ns));
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -158,7 +158,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
             }
             // every issued MMA has completed before TMEM can be released
             mma_commit(&final_bar);
-            (void)mbar_wait(&final_bar, 0, limit_ns);
+            (void)mbar_wait(&final_bar, 0, drain_limit(limit_ns));
         }
     } else {
         // epilogue: warps 2..5 -> TMEM lane quarters (warp % 4)
@@ -306,12 +306,8 @@ static cudaError_t launch_tc(const CUtensorMap &a0, const CUtensorMap &a1, const
 {
     auto kern = tc::k_tc_gemm<FMT, NSPLIT, STAGES, LOWER>;
     const int smem = STAGES * NSPLIT * (tc::A_TILE + tc::B_TILE) + 1024;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = smem_optin(kern, (size_t)smem);
+    if (e != cudaSuccess) return e;
     kern<<<grid, tc::THREADS, smem, s>>>(a0, a1, b0, b1, m, n, nkb, alpha, C, ldc, tiles_m, tiles_total, err,
                                          lim, abort);
     return cudaGetLastError();
