@@ -868,7 +868,9 @@ double or_probe_lu(int64_t n, const double *A0, int64_t lda0, const double *LU,
 
 /* Normwise backward error of a computed solution X of A X = B (general A),
  * per right-hand side, returning the maximum over columns:
- *   eta = ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf). */
+ *   eta = ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)
+ * (Rigal and Gaches' formula for the smallest relative perturbation of A
+ * and b that x solves exactly; 0 when the residual is 0). */
 double or_backward_error(int64_t n, int64_t nrhs, const double *A, int64_t lda,
                          const double *X, int64_t ldx, const double *B,
                          int64_t ldb)
@@ -894,7 +896,10 @@ double or_backward_error(int64_t n, int64_t nrhs, const double *A, int64_t lda,
             if (fabs(AT(X, ldx, i, j)) > xn) xn = fabs(AT(X, ldx, i, j));
             if (fabs(AT(B, ldb, i, j)) > bn) bn = fabs(AT(B, ldb, i, j));
         }
-        double eta = rn / (an * xn + bn);
+        /* r = 0 is an exact solution: its backward error (the smallest
+         * relative perturbation of A and b that x solves) is 0, also when
+         * x = b = 0 makes the quotient 0/0 */
+        double eta = (rn == 0.0) ? 0.0 : rn / (an * xn + bn);
         if (eta > worst || eta != eta) worst = eta;
     }
     return worst;

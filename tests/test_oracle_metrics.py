@@ -77,8 +77,15 @@ def test_backward_error_closed_form(oracle):
         assert abs(got - wrong) > 1e-3
     # one right-hand side given as a vector
     assert oracle.backward_error(A, X[:, 0], B[:, 0]) == pytest.approx(1.0 / 57.0, rel=1e-15)
-    # an exact solution has eta = 0
+    # an exact solution has eta = 0, also a zero right-hand side with x = 0
+    # (no perturbation is needed; the quotient would be 0/0)
     assert oracle.backward_error(A, X, A @ X) == 0.0
+    Z = X.copy(order="F")
+    Z[:, 0] = 0.0
+    assert oracle.backward_error(A, Z, A @ Z) == 0.0
+    Bz = B.copy(order="F")
+    Bz[:, 0] = 0.0
+    assert oracle.backward_error(A, Z, Bz) == pytest.approx(2.0 / 59.0, rel=1e-15)
 
 
 def test_backward_error_exact_rational(oracle):
