@@ -49,12 +49,30 @@ SMS = 152
 FP64_FMA_PER_SM_CLK = 2
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# FP32 SIMT: 128 FFMA lanes per SM (4 sub-partitions x 32) -> 80.5 TFLOP/s
+FP32_FMA_PER_SM_CLK = 128
+FP32_PEAK_TFLOPS = SMS * FP32_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def measured_hbm_gbs():
+    """The measured copy bandwidth of the GB300s (MEASURED_PEAKS.json),
+    or None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f).get("hbm_gbs") or 0.0) or None
+    except Exception:
+        return None
 
 # DRAM traffic of the dominant kernel (k_gemm, the GEMM kind: 2111 launches
-# per step) per launch, from the ncu launch list of this workload in
-# profiles/launches_dpotrf_dgetrf_n16384.md (172.7 GB over 2111 launches).
-# Reset to None whenever k_gemm changes.
+# per step) per launch: dram__bytes_read.sum + dram__bytes_write.sum summed
+# over the k_gemm launches of one step (172.7 GB over 2111 launches), from
+#   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
+#       --clock-control none -c 9000 --csv python bench.py --steps 1 --warmup 0
+#       --e2e-steps 0 --mixed-n 0 --batch-count 0 --cpu-n 0 --others-n 0 --graph 0 --cusolver 0
+# on commit f7f7de1 ("Lookahead in the LU and Cholesky recursions ...").  The
+# real-valued k_gemm has not changed since; set this to None when it does.
 GEMM_DRAM_BYTES_PER_LAUNCH = 172.704e9 / 2111
+GEMM_DRAM_SOURCE = "ncu capture of one n=16384 step on commit f7f7de1 (k_gemm unchanged since)"
 
 
 def flops_potrf(n: int) -> float:
@@ -173,6 +191,27 @@ def cpu_cores():
     return min(n, int(omp)) if omp and omp.isdigit() else n
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the
+    machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
 def oracle_sample(n_cpu: int, seed_k: int = 0):
     """Time the oracle's recursive dpotrf + dgetrf on an n_cpu sample of the
     same recipes; returns (GFLOP/s, seconds)."""
@@ -221,14 +260,19 @@ def run_reference(args, rank):
         times.append(dt)
     tot = sum(times)
     value = args.steps * (flops_potrf(n_ref) + flops_getrf(n_ref)) / tot / 1e9
-    sample = f"oracle dpotrf+dgetrf at n={n_ref} (same recipes) per step, c=24"
+    sample = (f"oracle dpotrf+dgetrf at n={n_ref} (same recipes as the n={args.n} workload) per step, "
+              f"c=24; GFLOP/s of that order")
+    cfg = workload_config(args.n)
+    cfg["timed_order"] = n_ref
+    cfg["timed_note"] = (f"each step times the oracle at order {n_ref}, a bounded sample of the n={args.n} "
+                         f"workload; the GFLOP/s is that of order {n_ref}")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "impl": "reference", "config": workload_config(args.n),
+        "data": "synthetic", "impl": "reference", "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "sample_n": n_ref, "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -242,13 +286,16 @@ def run_reference(args, rank):
 PRECS = {"fp32": 0, "tf32": 1, "bf16": 2, "fp16s": 3, "tf32x3": 4}
 
 
-def mixed_section(n, nrhs, cond, precs, dev, sp, reps=2):
+def mixed_section(n, nrhs, cond, precs, dev, sp, reps=2, gmres_budget=300):
     """Solve A X = B (A = U diag(sigma) V^T or Q diag(sigma) Q^T, sigma
     log-spaced 1..cond, 64 Householder reflectors each side; B iid N(0,1))
     with the FP64 path (getrf+getrs / potrf+potrs) and with rl_dsgesv /
-    rl_dsposv in each precision; reports time, the normwise backward error
-    of the returned X (computed in FP64), refinement iterations, and the
-    speedup over the FP64 path."""
+    rl_dsposv in each precision, with the classic refinement and with the
+    GMRES refinement ("<prec>+gmres", budget gmres_budget GMRES iterations,
+    one timed run after the classic runs of the same precision); reports
+    time, the normwise backward error of the returned X (computed in FP64),
+    refinement iterations (GMRES iterations for "+gmres"; negative: the FP64
+    fallback ran), and the speedup over the FP64 path."""
     import torch
     from paper_1602_06763_gb300 import relgpu as r, inputs
 
@@ -294,26 +341,32 @@ def mixed_section(n, nrhs, cond, precs, dev, sp, reps=2):
                                     r.check(r.rl_dgetrs("N", n, nrhs, A, n, ipiv, X, n, tw, ltw, sp))))
         res["fp64"] = {"ms": ms, "eta": eta_of(A0, X, B, anorm)}
         del A
-        for name in precs:
-            prec = PRECS[name]
+        variants = [(name, PRECS[name], 30, reps) for name in precs]
+        if gmres_budget > 0:
+            variants += [(name + "+gmres", PRECS[name] | r.RL_REFINE_GMRES, gmres_budget, 1) for name in precs]
+        for name, prec, maxit, nrep in variants:
             lwm = (r.rl_dsposv_work_size if spd else r.rl_dsgesv_work_size)(n, nrhs, prec)
             wm = torch.empty(lwm, dtype=torch.uint8, device=dev)
             it = torch.zeros(1, dtype=torch.int32, device=dev)
-            for rep in range(reps):
+            for rep in range(nrep):
                 A = A0.clone()
                 X = torch.zeros_like(B)
                 if spd:
-                    ms = timed(lambda: r.check(r.rl_dsposv("L", n, nrhs, A, n, B, n, X, n, prec, 1e-14, 30, it,
+                    ms = timed(lambda: r.check(r.rl_dsposv("L", n, nrhs, A, n, B, n, X, n, prec, 1e-14, maxit, it,
                                                            info, wm, lwm, sp)))
                 else:
-                    ms = timed(lambda: r.check(r.rl_dsgesv(n, nrhs, A, n, ipiv, B, n, X, n, prec, 1e-14, 30, it,
+                    ms = timed(lambda: r.check(r.rl_dsgesv(n, nrhs, A, n, ipiv, B, n, X, n, prec, 1e-14, maxit, it,
                                                            info, wm, lwm, sp)))
             iters = int(it.item())
             e = eta_of(A0, X, B, anorm)
-            res[name] = {"ms": ms, "eta": e, "iters": iters, "converged": iters >= 0,
-                         "speedup_vs_fp64": res["fp64"]["ms"] / ms}
+            res[name] = {"ms": round(ms, 2), "eta": e, "iters": iters, "converged": iters >= 0,
+                         "speedup_vs_fp64": round(res["fp64"]["ms"] / ms, 3)}
+            if iters < 0:
+                res[name]["note"] = {-2: "FP32 overflow: FP64 fallback", -3: "low-precision factorization failed: "
+                                     "FP64 fallback"}.get(iters, "refinement did not converge: FP64 fallback")
             del A, wm
-        best = [k for k in precs if res[k]["converged"] and res[k]["eta"] <= 1e-14]
+        keys = [v[0] for v in variants]
+        best = [k for k in keys if res[k]["converged"] and res[k]["eta"] <= 1e-14]
         res["best"] = max(best, key=lambda k: res[k]["speedup_vs_fp64"]) if best else None
         res["speedup_at_equal_error"] = res[res["best"]]["speedup_vs_fp64"] if best else None
         out[kind] = res
@@ -412,7 +465,17 @@ def batched_section(count, baseline_count, dev, sp):
             torch.cuda.synchronize()
             bad = int((info != 0).sum().item())
             ms = timed(run, reps=3, before=restore)
+            # roofline of the batched form: the arithmetic pipe (FP64 DFMA or
+            # FP32 FFMA, derived from unit counts and the maximum clock) and
+            # HBM (every matrix read and written once: 2 n^2 elements)
+            pipe = FP64_PEAK_TFLOPS if prec == "f64" else FP32_PEAK_TFLOPS
+            alg_bytes = 2.0 * esz * float(np.sum(sizes.astype(np.float64) ** 2))
+            hbm = measured_hbm_gbs()
             res = {"ms": ms, "gflops": flops / (ms * 1e-3) / 1e9, "launches": 2, "info_nonzero": bad,
+                   "pct_flop_peak": round(100.0 * flops / (ms * 1e-3) / (pipe * 1e12), 2),
+                   "flop_peak_tflops": round(pipe, 2),
+                   "gbs_algorithmic": round(alg_bytes / (ms * 1e-3) / 1e9, 1),
+                   "pct_hbm": round(100.0 * alg_bytes / (ms * 1e-3) / 1e9 / hbm, 2) if hbm else None,
                    "tuned": {"config": best, "nb": cfg[1], "threads": cfg[2], "ctas_per_sm": cfg[3],
                              "ms_per_config": [round(v, 3) for v in ms_cfg]}}
             # the same call captured once into a CUDA graph and replayed
@@ -517,6 +580,95 @@ def routines_section(n, dev, sp):
         out[name] = {"gflops": flops / (ms * 1e-3) / 1e9, "ms": ms}
     out["n"] = n
     out["flop_counts"] = "trtri, lauum n^3/3; potri 2n^3/3; getri 4n^3/3; sygst n^3"
+    return out
+
+
+def large_section(n, dev, sp):
+    """The large FP64 case at order n (32768): dgetrf on the general matrix
+    U diag(sigma) V^T with sigma log-spaced 1..1e4 (the matrix the large
+    precision-form case solves), dpotrf and then POTRI (dtrtri + dlauum on the
+    Cholesky factor, Section 5: xpotri from xtrtri and xlauum) on the SPD
+    Q diag(sigma) Q^T with sigma log-spaced 1..1e6; 64 Householder
+    reflectors per side.  One timed call each (a call takes seconds, far
+    above any launch or clock effect), GFLOP/s with LAPACK Working Note 41
+    counts and % of the derived FP64 peak, and a random-probe residual of
+    each result in units of n eps ||A||_1 ||x||_1, computed with plain FP64
+    torch products on the device: ||P A x - L (U x)||, ||A x - L (L^T x)||,
+    ||A (X x) - x|| / ||X||_1 for the inverse X (symmetric, lower stored)."""
+    import torch
+    from paper_1602_06763_gb300 import relgpu as r, inputs
+
+    eps = 2.0 ** -53
+    out = {"n": n}
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(inputs.seed_for(4, 90))
+    x = torch.rand(n, 1, generator=g, device=dev, dtype=torch.float64) * 2 - 1
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    def entry(name, flops, ms, res):
+        out[name] = {"ms": round(ms, 2), "gflops": round(flops / (ms * 1e-3) / 1e9, 1),
+                     "pct_fp64_peak": round(100.0 * flops / (ms * 1e-3) / (FP64_PEAK_TFLOPS * 1e12), 1),
+                     "info": int(info[0]), "probe_residual": res}
+
+    # general, sigma 1..1e4: dgetrf
+    A0 = inputs.spectrum_device(n, 1e4, inputs.seed_for(4, 91), spd=False, device=dev)
+    A = A0.clone()
+    ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+    lw = r.rl_dgetrf_work_size(n, n)
+    wk = torch.empty(lw, dtype=torch.uint8, device=dev)
+    ms = timed(lambda: r.check(r.rl_dgetrf(n, n, A, n, ipiv, info, wk, lw, sp), "rl_dgetrf"))
+    # the library reads the buffers column-major: its matrices are the transposes of the torch views
+    Ft, Gt = A.t(), A0.t()
+    b = (Gt @ x).squeeze(1)
+    p = ipiv.cpu().numpy() - 1
+    perm = list(range(n))
+    for i in range(n):
+        perm[i], perm[p[i]] = perm[p[i]], perm[i]
+    b = b[torch.tensor(perm, device=dev)]
+    y = torch.triu(Ft) @ x
+    y = (torch.tril(Ft, -1) @ y + y).squeeze(1)
+    res = float((b - y).abs().sum() / (n * eps * Gt.abs().sum(0).max() * x.abs().sum()))
+    entry("dgetrf", flops_getrf(n), ms, res)
+    del A, A0, Ft, Gt, y, wk
+    torch.cuda.empty_cache()
+
+    # SPD, sigma 1..1e6: dpotrf, then dtrtri + dlauum = dpotri on the factor
+    S0 = inputs.spectrum_device(n, 1e6, inputs.seed_for(4, 92), spd=True, device=dev)
+    L = S0.clone()
+    ms = timed(lambda: r.check(r.rl_dpotrf("L", n, L, n, info, None, 0, sp), "rl_dpotrf"))
+    Lt = torch.tril(L.t())
+    St = S0.t()
+    y = St @ x - Lt @ (Lt.t() @ x)
+    anorm = St.abs().sum(0).max()
+    res = float(y.abs().sum() / (n * eps * anorm * x.abs().sum()))
+    entry("dpotrf", flops_potrf(n), ms, res)
+    del Lt, y
+    torch.cuda.empty_cache()
+    X = L
+    ms1 = timed(lambda: r.check(r.rl_dtrtri("L", "N", n, X, n, info, None, 0, sp), "rl_dtrtri"))
+    ms2 = timed(lambda: r.check(r.rl_dlauum("L", n, X, n, info, None, 0, sp), "rl_dlauum"))
+    Xl = torch.tril(X.t())
+    Xx = Xl @ x + torch.tril(X.t(), -1).t() @ x
+    xnorm = (Xl.abs().sum(0) + torch.tril(X.t(), -1).abs().sum(1)).max()
+    del Xl
+    y = St @ Xx - x
+    res = float(y.abs().sum() / (n * eps * anorm * xnorm * x.abs().sum()))
+    n3 = float(n) ** 3
+    out["dtrtri"] = {"ms": round(ms1, 2), "gflops": round(n3 / 3.0 / (ms1 * 1e-3) / 1e9, 1)}
+    out["dlauum"] = {"ms": round(ms2, 2), "gflops": round(n3 / 3.0 / (ms2 * 1e-3) / 1e9, 1)}
+    entry("dpotri", 2.0 * n3 / 3.0, ms1 + ms2, res)
+    out["inputs"] = "dgetrf: U diag(sigma) V^T, sigma 1..1e4; dpotrf/dpotri: Q diag(sigma) Q^T, sigma 1..1e6"
+    del X, L, S0, St, Xx, y
+    torch.cuda.empty_cache()
     return out
 
 
@@ -712,6 +864,35 @@ def cusolver_section(n, dev):
     return res
 
 
+def probe_chol_dev(S0, F, x):
+    """||A x - L (L^T x)||_1 / (n eps ||A||_1 ||x||_1) for the Cholesky factor
+    in F; S0 and F are column-major buffers (their torch views are the
+    transposes), plain FP64 torch products."""
+    import torch
+    n = S0.shape[0]
+    L = torch.tril(F.t())
+    A0 = S0.t()
+    y = A0 @ x - L @ (L.t() @ x)
+    return float(y.abs().sum() / (n * 2.0 ** -53 * A0.abs().sum(0).max() * x.abs().sum()))
+
+
+def probe_lu_dev(G0, F, piv, x):
+    """||P A x - L (U x)||_1 / (n eps ||A||_1 ||x||_1) for the LU factors in F
+    with the 1-based interchanges piv (column-major buffers, as above)."""
+    import torch
+    n = G0.shape[0]
+    Ft = F.t()
+    b = (G0.t() @ x).squeeze(1)
+    p = piv.cpu().numpy() - 1
+    perm = list(range(n))
+    for i in range(n):
+        perm[i], perm[p[i]] = perm[p[i]], perm[i]
+    b = b[torch.tensor(perm, device=b.device)]
+    y = torch.triu(Ft) @ x
+    y = (torch.tril(Ft, -1) @ y + y).squeeze(1)
+    return float((b - y).abs().sum() / (n * 2.0 ** -53 * G0.t().abs().sum(0).max() * x.abs().sum()))
+
+
 def graph_section(n, dev, sp):
     """dpotrf and dgetrf captured once into CUDA graphs and replayed: the
     launch overhead of the ~2000 launches per factorization, measured."""
@@ -751,11 +932,48 @@ def graph_section(n, dev, sp):
             if int(info[0]) != 0:
                 raise RuntimeError(f"info {int(info[0])} after replay")
             ms = statistics.median(ts)
-            res[name] = {"gflops": flops / (ms * 1e-3) / 1e9, "ms": ms}
+            gen = torch.Generator(device=dev)
+            gen.manual_seed(inputs.seed_for(2, 11))
+            x = torch.rand(n, 1, generator=gen, device=dev, dtype=torch.float64) * 2 - 1
+            res[name] = {"gflops": flops / (ms * 1e-3) / 1e9, "ms": ms,
+                         "probe_residual_of_replayed_factors": probe_chol_dev(src, A, x) if name == "dpotrf"
+                         else probe_lu_dev(src, A, ipiv, x)}
             del g
         except Exception as e:
             res[name] = {"unavailable": str(e).splitlines()[0][:200]}
     return res
+
+
+def summarize_mixed(*sections):
+    """Per precision-form case: order, condition, right-hand sides, the FP64
+    time, and per variant the refinement iterations (negative: the FP64
+    fallback ran) and the speedup over FP64."""
+    out = []
+    for sec in sections:
+        if not sec:
+            continue
+        for kind in ("general", "spd"):
+            res = sec.get(kind)
+            if not res:
+                continue
+            row = {"case": f"{kind} n={sec['n']} cond={sec['cond']:g} nrhs={sec['nrhs']}",
+                   "fp64_ms": round(res["fp64"]["ms"], 1), "best": res.get("best"),
+                   "speedup_at_equal_error": res.get("speedup_at_equal_error")}
+            for k, v in res.items():
+                if isinstance(v, dict) and "iters" in v:
+                    row[k] = [v["iters"], v["speedup_vs_fp64"]]
+            out.append(row)
+    return {"format": "variant: [iterations (negative: FP64 fallback), speedup vs FP64]", "cases": out} if out else None
+
+
+def summarize_batched(sec):
+    if not sec:
+        return None
+    out = {}
+    for k, v in sec.items():
+        if isinstance(v, dict) and "ms" in v:
+            out[k] = {"ms": round(v["ms"], 2), "pct_flop_peak": v.get("pct_flop_peak"), "pct_hbm": v.get("pct_hbm")}
+    return out
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -845,6 +1063,7 @@ def run_gpu(args, rank, world, local_rank):
             "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
             "traffic": GEMM_DRAM_BYTES_PER_LAUNCH if dom_name == "gemm" else None,
             "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+            "traffic_source": GEMM_DRAM_SOURCE if dom_name == "gemm" else None,
             "algorithmic_bytes_per_launch": alg_bytes,
             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2070 MHz",
             "launches_per_step": d["launches"] / args.steps,
@@ -895,13 +1114,20 @@ def run_gpu(args, rank, world, local_rank):
         del spd0, gen0
         torch.cuda.empty_cache()
         mixed = mixed_section(args.mixed_n, args.mixed_nrhs, args.mixed_cond,
-                              [p for p in args.mixed_precs.split(",") if p], dev, sp)
+                              [p for p in args.mixed_precs.split(",") if p], dev, sp,
+                              gmres_budget=args.gmres_budget)
 
     mixed_large = None
     if args.mixed4_n > 0:
         torch.cuda.empty_cache()
         mixed_large = mixed_section(args.mixed4_n, args.mixed4_nrhs, args.mixed4_cond,
-                                    [p for p in args.mixed4_precs.split(",") if p], dev, sp, reps=1)
+                                    [p for p in args.mixed4_precs.split(",") if p], dev, sp, reps=1,
+                                    gmres_budget=args.gmres_budget)
+
+    large = None
+    if args.large_n > 0:
+        torch.cuda.empty_cache()
+        large = large_section(args.large_n, dev, sp)
 
     batched = None
     if args.batch_count > 0:
@@ -919,8 +1145,10 @@ def run_gpu(args, rank, world, local_rank):
         obuild.build()
         gfl, dt = oracle_sample(args.cpu_n)
         cpu = {"value": gfl, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"oracle dpotrf+dgetrf at n={args.cpu_n} (same recipes), c=24, {dt:.1f} s",
-               "lapack_context": cpu_lapack_context(args.cpu_n)}
+               "sample": f"oracle dpotrf+dgetrf once at n={args.cpu_n} (same recipes as the n={n} workload), "
+                         f"c=24, {dt:.1f} s; GFLOP/s of that order",
+               "sample_n": args.cpu_n, "cpu_model": cpu_model(),
+               "lapack_context": cpu_lapack_context(min(args.cpu_n, 4096))}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -940,6 +1168,12 @@ def run_gpu(args, rank, world, local_rank):
                         "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["bytes"] else None}
                     for k, v in trace.items()},
         "gpu_launches": launches,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        # detailed sections, then (last, so that they stay in view at the end
+        # of the line) compact summaries of the precision, batching and
+        # large-order sections
         "mixed_solve": mixed,
         "mixed_solve_large": mixed_large,
         "batched": batched,
@@ -948,9 +1182,9 @@ def run_gpu(args, rank, world, local_rank):
         "fp64_emulated": emulated,
         "graph_replay": graphs,
         "cusolver_context": cusolver,
-        "e2e": e2e,
-        "cpu_baseline": cpu,
-        "clocks": clocks,
+        "summary_mixed": summarize_mixed(mixed, mixed_large),
+        "summary_batched": summarize_batched(batched),
+        "large": large,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -963,9 +1197,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=16384)
-    ap.add_argument("--cpu-n", type=int, default=3072,
-                    help="order of the oracle's timed sample for cpu_baseline (about 10 s)")
-    ap.add_argument("--ref-n", type=int, default=2048,
+    ap.add_argument("--cpu-n", type=int, default=8192,
+                    help="order of the oracle's timed sample for cpu_baseline (about 20 s on 16 cores)")
+    ap.add_argument("--ref-n", type=int, default=3072,
                     help="order of the oracle's sample per step in the reference arm")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--mixed-n", type=int, default=16384,
@@ -977,7 +1211,11 @@ def main():
                     help="order of the large precision-form case, 1 RHS (0 skips it)")
     ap.add_argument("--mixed4-nrhs", type=int, default=1)
     ap.add_argument("--mixed4-cond", type=float, default=1e4)
-    ap.add_argument("--mixed4-precs", default="fp32,bf16")
+    ap.add_argument("--mixed4-precs", default="fp32,bf16,fp16s")
+    ap.add_argument("--large-n", type=int, default=32768,
+                    help="order of the large FP64 section: dgetrf, dpotrf, dpotri (0 skips it)")
+    ap.add_argument("--gmres-budget", type=int, default=300,
+                    help="GMRES iterations allowed to the '+gmres' precision-form variants (0 skips them)")
     ap.add_argument("--batch-count", type=int, default=20000,
                     help="matrices per kind in the batching-form comparison (0 skips it)")
     ap.add_argument("--batch-baseline", type=int, default=2000,

@@ -378,11 +378,30 @@ int rl_sgetrf_tc(int prec, int64_t m, int64_t n, float *A, int64_t lda, int32_t 
  *         used)
  * and *info: LAPACK's info of the FP64 fallback factorization (0 otherwise).
  * nrhs <= 512.  Workspace: rl_dsgesv_work_size / rl_dsposv_work_size bytes.
+ *
+ * prec | RL_REFINE_GMRES selects GMRES-based refinement (not in the paper;
+ * E. Carson and N. J. Higham, SIAM J. Sci. Comput. 2017/2018, in the
+ * flexible form of A. Haidar et al., SC18) for factorizations too inexact
+ * for the classic loop (kappa(A) u >= 1, e.g. BF16 or FP16 updates at
+ * kappa = 1e6): after x0 = solve(b), each refinement step solves the
+ * correction equation A d = r by restarted flexible GMRES, right
+ * preconditioned by the low-precision factors (applied in FP32), with the
+ * Krylov basis, the products A z (A in FP64) and the least-squares problem
+ * in FP64; a cycle ends for a column once its residual is below 1e-4 of
+ * the cycle's start (or below half of what tol allows), after
+ * RL_PARAM_GMRES_RESTART iterations, or when the budget is spent.  maxiter
+ * then bounds the total number of GMRES iterations (preconditioner
+ * applications) and *iter >= 0 reports that number; the refinement is
+ * abandoned for the FP64 fallback (*iter = -31) when the budget is spent or
+ * a cycle reduces the largest backward error by less than half.  nrhs <= 64
+ * with this flag; the work size depends on the flag and on the restart
+ * length in force when it is queried.
  * Argument numbers (dsgesv): 1 n, 2 nrhs, 3 A, 4 lda, 5 ipiv, 6 B, 7 ldb,
  * 8 X, 9 ldx; (dsposv): 1 uplo, 2 n, 3 nrhs, 4 A, 5 lda, 6 B, 7 ldb, 8 X,
  * 9 ldx.
  * ------------------------------------------------------------------------- */
 enum { RL_PREC_FP32 = 0, RL_PREC_TF32 = 1, RL_PREC_BF16 = 2, RL_PREC_FP16S = 3, RL_PREC_TF32X3 = 4 };
+enum { RL_PREC_MASK = 0xff, RL_REFINE_GMRES = 0x100 };
 size_t rl_dsgesv_work_size(int64_t n, int64_t nrhs, int prec);
 size_t rl_dsposv_work_size(int64_t n, int64_t nrhs, int prec);
 int rl_dsgesv(int64_t n, int64_t nrhs, double *A, int64_t lda, int32_t *ipiv, const double *B,
@@ -584,6 +603,8 @@ int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda,
  *   RL_PARAM_OZ_MIN            smallest m, n and k of an FP64 update that
  *                              the *_oz routines emulate on the tensor
  *                              cores (default 128; smaller ones stay FP64)
+ *   RL_PARAM_GMRES_RESTART     restart length of the GMRES refinement of
+ *                              rl_dsgesv / rl_dsposv (1..64, default 50)
  *   RL_PARAM_NVTX              1: every recursion node (potrf, getrf,
  *                              trtri, lauum) pushes an NVTX range named by
  *                              routine, order and depth, for timeline
@@ -601,7 +622,8 @@ enum {
     RL_PARAM_LOOKAHEAD = 7,
     RL_PARAM_PANEL_CTAS = 8,
     RL_PARAM_OZ_MIN = 9,
-    RL_PARAM_NVTX = 10
+    RL_PARAM_NVTX = 10,
+    RL_PARAM_GMRES_RESTART = 11
 };
 int rl_set_param(int key, int64_t value);
 int64_t rl_get_param(int key);

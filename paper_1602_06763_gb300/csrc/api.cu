@@ -1148,7 +1148,16 @@ int rl_zpotrs(char uplo, int64_t n, int64_t nrhs, const rl_double_complex *A, in
 
 // ---- precision form ------------------------------------------------------------
 
-static bool prec_ok(int prec) { return prec == RL_PREC_FP32 || tc_prec(prec); }
+// a precision, optionally with the GMRES refinement flag
+static bool prec_ok(int prec)
+{
+    if ((prec & ~(RL_PREC_MASK | RL_REFINE_GMRES)) != 0) return false;
+    const int p = prec & RL_PREC_MASK;
+    return p == RL_PREC_FP32 || tc_prec(p);
+}
+
+// largest nrhs of each refinement
+static int64_t mixed_max_nrhs(int prec) { return (prec & RL_REFINE_GMRES) ? 64 : 512; }
 
 size_t rl_dsgesv_work_size(int64_t n, int64_t nrhs, int prec)
 {
@@ -1172,7 +1181,7 @@ int rl_dsgesv(int64_t n, int64_t nrhs, double *A, int64_t lda, int32_t *ipiv, co
     if (ldb < imax1(n)) return -7;
     if (ldx < imax1(n)) return -9;
     if (!prec_ok(prec)) return RL_ERR_UNSUPPORTED;
-    if (nrhs > 512) return RL_ERR_UNSUPPORTED;
+    if (nrhs > mixed_max_nrhs(prec)) return RL_ERR_UNSUPPORTED;
     if (info == nullptr || iter == nullptr || (ipiv == nullptr && n > 0)) return RL_ERR_NULL_POINTER;
     if (n > 0 && nrhs > 0 && (work == nullptr || lwork < rl_dsgesv_work_size(n, nrhs, prec)))
         return RL_ERR_WORKSPACE;
@@ -1195,7 +1204,7 @@ int rl_dsposv(char uplo, int64_t n, int64_t nrhs, double *A, int64_t lda, const 
     if (ldb < imax1(n)) return -7;
     if (ldx < imax1(n)) return -9;
     if (!prec_ok(prec)) return RL_ERR_UNSUPPORTED;
-    if (nrhs > 512) return RL_ERR_UNSUPPORTED;
+    if (nrhs > mixed_max_nrhs(prec)) return RL_ERR_UNSUPPORTED;
     if (info == nullptr || iter == nullptr) return RL_ERR_NULL_POINTER;
     if (n > 0 && nrhs > 0 && (work == nullptr || lwork < rl_dsposv_work_size(n, nrhs, prec)))
         return RL_ERR_WORKSPACE;
@@ -1625,6 +1634,10 @@ int rl_set_param(int key, int64_t value)
         if (value < 1 || value > (1 << 20)) return RL_ERR_PARAM;
         g_params.oz_min = (int)value;
         return RL_SUCCESS;
+    case RL_PARAM_GMRES_RESTART:
+        if (value < 1 || value > 64) return RL_ERR_PARAM;
+        g_params.gmres_m = (int)value;
+        return RL_SUCCESS;
     case RL_PARAM_PANEL_CTAS:
         // low 16 bits: FP64 panels, high 16 bits: FP32 panels (0 = one per SM)
         if (value < 0 || (value & 0xffff) > 256 || (value >> 16) > 256) return RL_ERR_PARAM;
@@ -1648,6 +1661,7 @@ int64_t rl_get_param(int key)
     case RL_PARAM_LOOKAHEAD: return g_params.lookahead;
     case RL_PARAM_OZ_MIN: return g_params.oz_min;
     case RL_PARAM_NVTX: return g_params.nvtx;
+    case RL_PARAM_GMRES_RESTART: return g_params.gmres_m;
     case RL_PARAM_PANEL_CTAS: return (int64_t)g_params.panel_ctas64 | ((int64_t)g_params.panel_ctas32 << 16);
     default: return -1;
     }

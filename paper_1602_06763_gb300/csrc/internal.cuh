@@ -80,6 +80,7 @@ struct Params {
     int panel_ctas32 = 0;
     int oz_min = 128;        // smallest m, n and k that the FP64 emulation takes
     int nvtx = 0;            // 1: an NVTX range per recursion node (routine, order, depth)
+    int gmres_m = 50;        // restart length of the GMRES refinement
 };
 extern Params g_params;
 

@@ -15,6 +15,20 @@
 // Every step is enqueued on the caller's stream; device flags make the
 // kernels of finished or skipped steps return at once, so the call never
 // synchronizes and has a fixed launch sequence.
+//
+// With RL_REFINE_GMRES the correction equation A d = r of each refinement
+// step is solved by flexible GMRES (right preconditioned, restarted) instead
+// of one solve with the low-precision factors: the factors precondition,
+// applied in FP32 (z = M^{-1} v), while the Krylov basis, the products
+// w = A z and the Hessenberg least-squares problem stay in FP64.  Flexible
+// GMRES keeps the FP64 relation A Z = V H however inexactly the FP32 solve
+// applies M^{-1}, so each cycle reduces the true residual of the correction
+// equation to its tolerance; the low-precision factors only decide how many
+// iterations that takes.  This is GMRES-based iterative refinement
+// (E. Carson, N. J. Higham, SIAM J. Sci. Comput. 39, 2017 and 40, 2018) in
+// the flexible form used with half-precision tensor-core factorizations
+// (A. Haidar, S. Tomov, J. Dongarra, N. J. Higham, SC18): it converges where
+// kappa(A) u_f >= 1 stops the classic loop.
 #include <cfloat>
 #include "internal.cuh"
 
@@ -46,13 +60,43 @@ struct MixState {
 constexpr int MIX_MAX_NRHS = RES_NR * 64;
 
 struct MixLayout {
-    size_t W, panel, R, D, P, N, S, F, TC, tc_bytes, total;
+    size_t W, panel, R, D, P, N, S, F, TC, tc_bytes, V, Z, ZC, WV, GS, total;
     i64 ldw, nchunks;
+    int m;                 // GMRES restart length (0: classic refinement)
+};
+
+// ---- GMRES-IR state ----------------------------------------------------------
+constexpr int GM_MAX_NRHS = 64;
+constexpr int GM_MAX_M = 64;
+// a column's cycle ends once its least-squares residual is below this
+// fraction of the cycle's starting residual (or below what the requested
+// backward error needs)
+constexpr double GM_TAU_REL = 1e-4;
+
+struct GmCol {
+    double beta;           // ||r||_2 at the start of the cycle
+    double tau;            // the cycle's residual target
+    double tau_abs;        // half the residual the requested backward error allows
+    int32_t done, k;       // cycle finished for this column; its iterations
+    double g[GM_MAX_M + 1], cs[GM_MAX_M], sn[GM_MAX_M], y[GM_MAX_M];
+    double H[(GM_MAX_M + 1) * GM_MAX_M];   // R of the rotated Hessenberg, column j at j (m + 1)
+};
+struct GmState {
+    int32_t j;             // next iteration of the open cycle
+    int32_t open;          // a cycle is running
+    int32_t has_cycle;     // a cycle ran since the last update of X
+    int32_t total;         // preconditioner applications so far (all cycles)
+    int32_t no_outer;      // this slot skips the update / residual / test / start block
+    int32_t pad[11];
+    GmCol col[GM_MAX_NRHS];
 };
 
 MixLayout layout(i64 n, i64 nrhs, bool lu, int prec)
 {
     MixLayout L;
+    const bool gm = (prec & RL_REFINE_GMRES) != 0;
+    prec &= RL_PREC_MASK;
+    L.m = gm ? g_params.gmres_m : 0;
     L.ldw = ((n + 31) / 32) * 32;
     if (L.ldw < 1) L.ldw = 1;
     L.nchunks = (n + RES_KC - 1) / RES_KC;
@@ -71,6 +115,15 @@ MixLayout layout(i64 n, i64 nrhs, bool lu, int prec)
     const i64 h = n / 2 + 64;
     L.tc_bytes = (prec == RL_PREC_FP32) ? 0 : tc_work_bytes(n, h, h, prec);
     L.TC = off; off += al(L.tc_bytes);
+    // GMRES-IR: per right-hand side m + 1 basis vectors V and m
+    // preconditioned vectors Z (FP64, n each, column after column), the
+    // current z and w = A z for all right-hand sides, and the cycle state
+    const size_t nn = (size_t)(n > 0 ? n : 1), nr = (size_t)nrhs;
+    L.V = off; off += gm ? al(nr * (size_t)(L.m + 1) * nn * sizeof(double)) : 0;
+    L.Z = off; off += gm ? al(nr * (size_t)L.m * nn * sizeof(double)) : 0;
+    L.ZC = off; off += gm ? al(nr * nn * sizeof(double)) : 0;
+    L.WV = off; off += gm ? al(nr * nn * sizeof(double)) : 0;
+    L.GS = off; off += gm ? al(sizeof(GmState)) : 0;
     L.total = off;
     return L;
 }
@@ -297,8 +350,11 @@ __global__ void k_ir_test(int nrhs, int it, double tol, MixState *st)
         const double r = __longlong_as_double((long long)st->rmax[j]);
         const double x = __longlong_as_double((long long)st->xmax[j]);
         const double b = __longlong_as_double((long long)st->bmax[j]);
-        const double eta = r / (st->anorm * x + b);
-        if (!(eta <= tol)) atomicExch(&bad, 1);
+        // r <= tol (||A|| ||x|| + ||b||) without the division: a zero
+        // right-hand side (r = x = b = 0) has converged
+        const double den = st->anorm * x + b;
+        const double eta = (r == 0.0) ? 0.0 : r / den;
+        if (!(r <= tol * den)) atomicExch(&bad, 1);
         atomicMax(&worst, (unsigned long long)__double_as_longlong(eta == eta ? eta : INFINITY));
     }
     __syncthreads();
@@ -365,6 +421,248 @@ __global__ void k_mix_finish(const MixState *st, int maxiter, int32_t *iter_out)
     *iter_out = v;
 }
 
+// ---- GMRES-IR kernels -----------------------------------------------------------
+
+__global__ void k_gm_init(GmState *gs)
+{
+    gs->j = 0;
+    gs->open = 0;
+    gs->has_cycle = 0;
+    gs->total = 0;
+    gs->no_outer = 0;
+}
+
+// Start of a slot: the update / residual / test / start block runs when no
+// cycle is open (and the solve has not stopped).
+__global__ void k_gm_slot_begin(const MixState *st, GmState *gs)
+{
+    gs->no_outer = (st->stop != 0 || gs->open != 0) ? 1 : 0;
+}
+
+// X[:, c] += sum_l y_c[l] Z_c[l] after a cycle (each column's own k).
+__global__ void k_gm_update(i64 n, int nrhs, int m, const double *Z, double *X, i64 ldx, const GmState *gs)
+{
+    if (gs->no_outer || !gs->has_cycle) return;
+    const i64 total = n * nrhs;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x) {
+        const i64 i = e % n;
+        const int c = (int)(e / n);
+        const GmCol &col = gs->col[c];
+        const double *zc = Z + (i64)c * m * n + i;
+        double d = 0.0;
+        for (int l = 0; l < col.k; ++l) d = fma(col.y[l], zc[(i64)l * n], d);
+        X[(i64)c * ldx + i] += d;
+    }
+}
+
+// Backward error of every column after a residual: per-column targets for
+// the next cycle, convergence (all columns at tol), budget and stagnation
+// (a cycle that reduced the largest backward error by less than half: the
+// FP64 fallback takes over).  Clears the running maxima.
+__global__ void k_gm_test(int nrhs, double tol, int maxiter, MixState *st, GmState *gs)
+{
+    if (gs->no_outer) return;
+    __shared__ int bad;
+    __shared__ unsigned long long worst;
+    if (threadIdx.x == 0) { bad = 0; worst = 0; }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nrhs; j += blockDim.x) {
+        const double r = __longlong_as_double((long long)st->rmax[j]);
+        const double x = __longlong_as_double((long long)st->xmax[j]);
+        const double b = __longlong_as_double((long long)st->bmax[j]);
+        const double den = st->anorm * x + b;
+        const double eta = (r == 0.0) ? 0.0 : r / den;
+        const bool ok = r <= tol * den;         // a zero column (r = x = b = 0) has converged
+        GmCol &col = gs->col[j];
+        col.tau_abs = 0.5 * tol * den;
+        col.done = ok ? 1 : 0;
+        if (!ok) atomicExch(&bad, 1);
+        atomicMax(&worst, (unsigned long long)__double_as_longlong(eta == eta ? eta : INFINITY));
+        st->rmax[j] = 0;
+        st->xmax[j] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double eta = __longlong_as_double((long long)worst);
+        if (!bad) {
+            st->stop = 1;
+            st->conv = 1;
+            st->iters = gs->total;
+        } else if (gs->total >= maxiter || (gs->has_cycle && !(eta <= 0.5 * st->prev_eta))) {
+            st->stop = 1;                        // budget spent or stagnation: FP64 fallback
+        }
+        st->prev_eta = eta;
+        gs->has_cycle = 0;
+    }
+}
+
+__device__ double block_sum(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int i = 0; i < nw; ++i) s += red[i];      // same order in every thread
+    return s;
+}
+
+// Start of a cycle (one CTA per right-hand side): beta = ||r||_2,
+// v_0 = r / beta, g = beta e_1; columns already at tol take no part.
+__global__ void k_gm_start(i64 n, int m, const double *R, i64 ldr, double *V, MixState *st, GmState *gs)
+{
+    if (gs->no_outer || st->stop) return;
+    __shared__ double red[32];
+    const int c = blockIdx.x;
+    GmCol &col = gs->col[c];
+    if (c == 0 && threadIdx.x == 0) {
+        gs->j = 0;
+        gs->open = 1;
+        gs->has_cycle = 1;
+    }
+    if (threadIdx.x == 0) col.k = 0;
+    if (col.done) return;
+    const double *r = R + (i64)c * ldr;
+    double s = 0.0;
+    for (i64 i = threadIdx.x; i < n; i += blockDim.x) s = fma(r[i], r[i], s);
+    const double beta = sqrt(block_sum(s, red));
+    double *v = V + (i64)c * (m + 1) * n;
+    if (threadIdx.x == 0) {
+        col.beta = beta;
+        col.g[0] = beta;
+        col.tau = fmax(GM_TAU_REL * beta, col.tau_abs);
+        if (!(beta > 0.0)) col.done = 1;
+    }
+    if (!(beta > 0.0)) return;
+    const double inv = 1.0 / beta;
+    for (i64 i = threadIdx.x; i < n; i += blockDim.x) v[i] = r[i] * inv;
+}
+
+// D[:, c] = (float)(s v_j) for the preconditioner solve (0 for columns that
+// are done).
+__global__ void k_gm_prep(i64 n, int nrhs, int m, const double *V, float *D, i64 ldd, const MixState *st,
+                          const GmState *gs)
+{
+    if (st->stop) return;
+    const int j = gs->j;
+    const double sc = st->scale;
+    const i64 total = n * nrhs;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x) {
+        const i64 i = e % n;
+        const int c = (int)(e / n);
+        const double v = gs->col[c].done ? 0.0 : V[((i64)c * (m + 1) + j) * n + i];
+        D[(i64)c * ldd + i] = (float)(v * sc);
+    }
+}
+
+// z_j = (double) D (the FP32 solve's result); also into ZC, the operand of
+// the product w = A z.
+__global__ void k_gm_widen(i64 n, int nrhs, int m, const float *D, i64 ldd, double *Z, double *ZC,
+                           const MixState *st, const GmState *gs)
+{
+    if (st->stop) return;
+    const int j = gs->j;
+    const i64 total = n * nrhs;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (i64)gridDim.x * blockDim.x) {
+        const i64 i = e % n;
+        const int c = (int)(e / n);
+        const double z = gs->col[c].done ? 0.0 : (double)D[(i64)c * ldd + i];
+        Z[((i64)c * m + j) * n + i] = z;
+        ZC[(i64)c * n + i] = z;
+    }
+}
+
+// W[:, c0 + c] = sum_ch P[ch][c] (the product A z, from the residual
+// kernel's partial sums).
+__global__ void k_mv_final(i64 n, int nr, int c0, i64 nchunks, const double *P, double *W, const int32_t *abort)
+{
+    if (abort && *abort != 0) return;
+    const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int c = 0; c < nr; ++c) {
+        double s = 0.0;
+        for (i64 ch = 0; ch < nchunks; ++ch) s += P[(ch * RES_NR + c) * n + i];
+        W[(i64)(c0 + c) * n + i] = s;
+    }
+}
+
+// One Arnoldi step per right-hand side (one CTA each): modified Gram-Schmidt
+// of w against v_0..v_j, h_{j+1,j} = ||w||_2, v_{j+1} = w / h_{j+1,j}; the
+// previous Givens rotations and a new one reduce the Hessenberg column to
+// triangular form, and |g_{j+1}| is the least-squares residual.  A column
+// whose residual meets its target (or whose basis breaks down, or whose
+// cycle reaches m iterations or the budget) solves R y = g for its update.
+__global__ void __launch_bounds__(1024)
+k_gm_arnoldi(i64 n, int m, int maxiter, double *V, double *W, MixState *st, GmState *gs)
+{
+    if (st->stop) return;
+    __shared__ double red[32];
+    __shared__ double h[GM_MAX_M + 1];
+    const int c = blockIdx.x;
+    GmCol &col = gs->col[c];
+    if (col.done) return;
+    const int j = gs->j;
+    double *w = W + (i64)c * n;
+    double *Vc = V + (i64)c * (m + 1) * n;
+    for (int i = 0; i <= j; ++i) {
+        const double *vi = Vc + (i64)i * n;
+        double s = 0.0;
+        for (i64 r = threadIdx.x; r < n; r += blockDim.x) s = fma(vi[r], w[r], s);
+        const double hi = block_sum(s, red);
+        for (i64 r = threadIdx.x; r < n; r += blockDim.x) w[r] = fma(-hi, vi[r], w[r]);
+        if (threadIdx.x == 0) h[i] = hi;
+        __syncthreads();
+    }
+    double s = 0.0;
+    for (i64 r = threadIdx.x; r < n; r += blockDim.x) s = fma(w[r], w[r], s);
+    const double hn = sqrt(block_sum(s, red));
+    if (hn > 0.0) {
+        const double inv = 1.0 / hn;
+        double *vn = Vc + (i64)(j + 1) * n;
+        for (i64 r = threadIdx.x; r < n; r += blockDim.x) vn[r] = w[r] * inv;
+    }
+    if (threadIdx.x != 0) return;
+    h[j + 1] = hn;
+    for (int l = 0; l < j; ++l) {                       // earlier rotations
+        const double t = col.cs[l] * h[l] + col.sn[l] * h[l + 1];
+        h[l + 1] = -col.sn[l] * h[l] + col.cs[l] * h[l + 1];
+        h[l] = t;
+    }
+    const double rr = hypot(h[j], h[j + 1]);
+    const double cj = rr > 0.0 ? h[j] / rr : 1.0, sj = rr > 0.0 ? h[j + 1] / rr : 0.0;
+    col.cs[j] = cj;
+    col.sn[j] = sj;
+    h[j] = rr;
+    col.g[j + 1] = -sj * col.g[j];
+    col.g[j] = cj * col.g[j];
+    double *Hj = col.H + (i64)j * (m + 1);
+    for (int l = 0; l <= j; ++l) Hj[l] = h[l];
+    const int k = j + 1;
+    col.k = k;
+    const bool fin = fabs(col.g[k]) <= col.tau || !(hn > 0.0) || k == m || gs->total + 1 >= maxiter;
+    if (!fin) return;
+    for (int l = k - 1; l >= 0; --l) {                  // R y = g
+        double t = col.g[l];
+        for (int q = l + 1; q < k; ++q) t -= col.H[(i64)q * (m + 1) + l] * col.y[q];
+        const double d = col.H[(i64)l * (m + 1) + l];
+        col.y[l] = d != 0.0 ? t / d : 0.0;
+    }
+    col.done = 1;
+}
+
+// End of a slot: count the iteration; close the cycle when every column is
+// done, at m iterations, or when the budget is spent.
+__global__ void k_gm_slot_end(int nrhs, int m, int maxiter, const MixState *st, GmState *gs)
+{
+    if (st->stop || !gs->open) return;
+    gs->j += 1;
+    gs->total += 1;
+    bool all = true;
+    for (int c = 0; c < nrhs; ++c) all = all && gs->col[c].done;
+    if (all || gs->j >= m || gs->total >= maxiter) gs->open = 0;
+}
+
 unsigned grid_for(i64 total, unsigned threads)
 {
     i64 g = (total + threads - 1) / threads;
@@ -399,6 +697,91 @@ static void factored_solve(Ctx &c, bool lu, i64 n, i64 nrhs, const T *F, i64 ldf
 
 size_t mixed_work_size(i64 n, i64 nrhs, bool lu, int prec) { return layout(n, nrhs, lu, prec).total; }
 
+// R[:, c0..] = B - A X (FP64) for every block of RES_NR right-hand sides,
+// with the running maxima of |r| and |x| per column; or, with B null,
+// OUT = A X.
+static void residual_blocks(Ctx &r, bool lu, i64 n, i64 nrhs, const double *A, i64 lda, const double *X,
+                            i64 ldx, const double *B, i64 ldb, double *OUT, i64 ldo, double *P, i64 nchunks,
+                            MixState *st)
+{
+    for (i64 c0 = 0; c0 < nrhs; c0 += RES_NR) {
+        const int nr = (int)((nrhs - c0) < RES_NR ? (nrhs - c0) : RES_NR);
+        {
+            Launch L(r, K_RESID, 2.0 * n * n * nr, (double)n * n * sizeof(double));
+            const dim3 g((unsigned)((n + RES_ROWS - 1) / RES_ROWS), (unsigned)nchunks);
+            const double *Xc = X + c0 * ldx;
+            if (lu) k_resid_partial<false><<<g, RES_ROWS, 0, r.s>>>(n, nr, A, lda, Xc, ldx, P, r.abort);
+            else k_resid_partial<true><<<g, RES_ROWS, 0, r.s>>>(n, nr, A, lda, Xc, ldx, P, r.abort);
+        }
+        {
+            Launch L(r, K_RESID, (double)n * nr * nchunks, 0.0);
+            if (B)
+                k_resid_final<<<(unsigned)((n + 255) / 256), 256, 0, r.s>>>(n, nr, (int)c0, nchunks, P, B, ldb, X,
+                                                                             ldx, OUT, ldo, st, r.abort);
+            else
+                k_mv_final<<<(unsigned)((n + 255) / 256), 256, 0, r.s>>>(n, nr, (int)c0, nchunks, P, OUT, r.abort);
+        }
+    }
+}
+
+// GMRES-IR: maxiter slots, each an optional block (update X from the last
+// cycle, residual, backward-error test, start of a new cycle: it runs when
+// no cycle is open) and one flexible-GMRES iteration; then a last update,
+// residual and test.  Device flags decide which parts run, so the launch
+// sequence is fixed.
+static void gmres_refine(Ctx &r, bool lu, i64 n, i64 nrhs, const double *A, i64 lda, const int32_t *ipiv,
+                         const double *B, i64 ldb, double *X, i64 ldx, const float *W, i64 ldw, float *D,
+                         i64 ldd, double *R, i64 ldr, double *P, MixState *st, void *fws, const MixLayout &Ly,
+                         double tol, int maxiter)
+{
+    char *w = static_cast<char *>(r.work);
+    double *V = reinterpret_cast<double *>(w + Ly.V);
+    double *Z = reinterpret_cast<double *>(w + Ly.Z);
+    double *ZC = reinterpret_cast<double *>(w + Ly.ZC);
+    double *WV = reinterpret_cast<double *>(w + Ly.WV);
+    GmState *gs = reinterpret_cast<GmState *>(w + Ly.GS);
+    const int m = Ly.m, nr = (int)nrhs;
+    const unsigned T256 = 256;
+    const unsigned gel = grid_for(n * nrhs, T256);
+    { Launch L(r, K_MIX, 0.0, 0.0); k_gm_init<<<1, 1, 0, r.s>>>(gs); }
+    Ctx ro = r;                                  // the update / residual / test / start block
+    ro.abort = &gs->no_outer;
+    auto outer = [&]() {
+        { Launch L(r, K_MIX, 0.0, 0.0); k_gm_slot_begin<<<1, 1, 0, r.s>>>(st, gs); }
+        {
+            Launch L(ro, K_MIX, 2.0 * n * nrhs * m, (double)n * nrhs * m * sizeof(double));
+            k_gm_update<<<gel, T256, 0, r.s>>>(n, nr, m, Z, X, ldx, gs);
+        }
+        residual_blocks(ro, lu, n, nrhs, A, lda, X, ldx, B, ldb, R, ldr, P, Ly.nchunks, st);
+        { Launch L(ro, K_MIX, 0.0, 0.0); k_gm_test<<<1, 256, 0, r.s>>>(nr, tol, maxiter, st, gs); }
+        {
+            Launch L(ro, K_MIX, 0.0, (double)n * nrhs * 16.0);
+            k_gm_start<<<nr, 1024, 0, r.s>>>(n, m, R, ldr, V, st, gs);
+        }
+        if (ro.err != cudaSuccess && r.err == cudaSuccess) r.err = ro.err;
+    };
+    for (int slot = 0; slot < maxiter; ++slot) {
+        outer();
+        {
+            Launch L(r, K_CONVERT, 0.0, (double)n * nrhs * 12.0);
+            k_gm_prep<<<gel, T256, 0, r.s>>>(n, nr, m, V, D, ldd, st, gs);
+        }
+        factored_solve<float>(r, lu, n, nrhs, W, ldw, ipiv, D, ldd, fws);
+        {
+            Launch L(r, K_CONVERT, 0.0, (double)n * nrhs * 20.0);
+            k_gm_widen<<<gel, T256, 0, r.s>>>(n, nr, m, D, ldd, Z, ZC, st, gs);
+        }
+        residual_blocks(r, lu, n, nrhs, A, lda, ZC, n, nullptr, 0, WV, n, P, Ly.nchunks, st);
+        {
+            Launch L(r, K_MIX, 4.0 * n * nrhs * m, (double)n * nrhs * m * 3 * sizeof(double));
+            k_gm_arnoldi<<<nr, 1024, 0, r.s>>>(n, m, maxiter, V, WV, st, gs);
+        }
+        { Launch L(r, K_MIX, 0.0, 0.0); k_gm_slot_end<<<1, 1, 0, r.s>>>(nr, m, maxiter, st, gs); }
+        if (r.err != cudaSuccess) return;
+    }
+    outer();
+}
+
 int mixed_solve(Ctx &c, bool lu, i64 n, i64 nrhs, double *A, i64 lda, int32_t *ipiv, const double *B,
                 i64 ldb, double *X, i64 ldx, int prec, double tol, int maxiter, int32_t *iter)
 {
@@ -415,6 +798,8 @@ int mixed_solve(Ctx &c, bool lu, i64 n, i64 nrhs, double *A, i64 lda, int32_t *i
     const i64 ldw = Ly.ldw, ldr = n, ldd = n;
     int32_t *user_info = c.info;
     const unsigned T256 = 256;
+    const bool gm = (prec & RL_REFINE_GMRES) != 0;
+    prec &= RL_PREC_MASK;
 
     if (tol <= 0.0) tol = 1e-14;
     if (maxiter < 0) maxiter = 0;
@@ -473,6 +858,11 @@ int mixed_solve(Ctx &c, bool lu, i64 n, i64 nrhs, double *A, i64 lda, int32_t *i
     }
     // the scale of the FP16 form is undone when D is widened: A_s = s A, so
     // A^{-1} r = s (A_s)^{-1} r, and D = (A_s)^{-1} (s r) is already A^{-1} r.
+    if (gm) {
+        gmres_refine(r, lu, n, nrhs, A, lda, ipiv, B, ldb, X, ldx, W, ldw, D, ldd, R, ldr, P, st, fws, Ly, tol,
+                     maxiter);
+        maxiter = -1;                        // the classic loop below does not run
+    }
     for (int it = 0; it <= maxiter; ++it) {
         for (i64 c0 = 0; c0 < nrhs; c0 += RES_NR) {
             const int nr = (int)((nrhs - c0) < RES_NR ? (nrhs - c0) : RES_NR);

@@ -25,7 +25,7 @@ def main():
     ap.add_argument("--case", required=True,
                     choices=["dgemm", "dsyrk", "dtrsm", "potrf", "getrf", "trtri", "lauum", "panel",
                              "sgemm_tc", "dsgesv", "dsposv", "getrs", "potrs", "sgetrs", "sgemm", "laswp",
-                             "zpotrf", "zgetrf"])
+                             "zpotrf", "zgetrf", "sgetrf_tc", "spotrf_tc"])
     ap.add_argument("--prec", type=int, default=1, help="operand precision (rl_prec) of sgemm_tc / dsgesv")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--cond", type=float, default=1e6)
@@ -179,6 +179,33 @@ def main():
             Z = Z0.clone()
             run = lambda: r.check(r.rl_zgetrf(n, n, Z, n, ipiv, info, work, lw, s))
         restore = lambda: Z.copy_(Z0)
+    elif a.case in ("sgetrf_tc", "spotrf_tc"):
+        # the precision form's factorization alone: FP32 storage, tcgen05
+        # updates in operand precision --prec (0: SIMT FP32 rl_sgetrf / rl_spotrf)
+        if a.case == "spotrf_tc":
+            X = torch.rand(n, n, generator=g, device=dev, dtype=torch.float64) - 0.5
+            A0 = (X @ X.T)
+            A0.diagonal().add_(float(n))
+            A0 = A0.to(torch.float32)
+            flops = n ** 3 / 3.0
+        else:
+            A0 = (torch.rand(n, n, generator=g, device=dev, dtype=torch.float64) * 2 - 1).to(torch.float32)
+            flops = 2.0 * n ** 3 / 3.0
+        A = A0.clone()
+        ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+        if a.prec == 0:
+            lw = r.rl_dgetrf_work_size(n, n)
+        else:
+            lw = (r.rl_spotrf_tc_work_size(n, a.prec) if a.case == "spotrf_tc"
+                  else r.rl_sgetrf_tc_work_size(n, n, a.prec))
+        work = torch.empty(max(lw, 1), dtype=torch.uint8, device=dev)
+        if a.case == "spotrf_tc":
+            run = ((lambda: r.check(r.rl_spotrf("L", n, A, n, info, None, 0, s))) if a.prec == 0 else
+                   (lambda: r.check(r.rl_spotrf_tc(a.prec, "L", n, A, n, info, work, lw, s))))
+        else:
+            run = ((lambda: r.check(r.rl_sgetrf(n, n, A, n, ipiv, info, work, lw, s))) if a.prec == 0 else
+                   (lambda: r.check(r.rl_sgetrf_tc(a.prec, n, n, A, n, ipiv, info, work, lw, s))))
+        restore = lambda: A.copy_(A0)
     elif a.case == "dtrsm":
         # B (m x n) := B L^{-T}, the TRSM of the Cholesky recursion
         L = torch.rand(n, n, generator=g, device=dev, dtype=torch.float64)

@@ -140,6 +140,8 @@ RL_PREC_TF32 = 1
 RL_PREC_BF16 = 2
 RL_PREC_FP16S = 3
 RL_PREC_TF32X3 = 4
+RL_PREC_MASK = 0xFF
+RL_REFINE_GMRES = 0x100
 
 RL_PARAM_POTRF_CROSSOVER = 1
 RL_PARAM_GETRF_PANEL = 2
@@ -151,6 +153,7 @@ RL_PARAM_LOOKAHEAD = 7
 RL_PARAM_PANEL_CTAS = 8
 RL_PARAM_OZ_MIN = 9
 RL_PARAM_NVTX = 10
+RL_PARAM_GMRES_RESTART = 11
 
 
 def _ptr(x):

@@ -166,3 +166,31 @@ def test_binding_has_every_declared_entry_point(built):
     for name in declared_functions():
         assert f'"{name}"' in src, name
         assert callable(getattr(r, name, None)), name
+
+
+def test_host_logic_of_the_gmres_refinement(built):
+    from paper_1602_06763_gb300 import relgpu as r
+    g = r.RL_REFINE_GMRES
+    n, nrhs = 1000, 16
+    for prec in (r.RL_PREC_FP32, r.RL_PREC_BF16, r.RL_PREC_TF32X3):
+        base = r.rl_dsgesv_work_size(n, nrhs, prec)
+        gm = r.rl_dsgesv_work_size(n, nrhs, prec | g)
+        m = r.rl_get_param(r.RL_PARAM_GMRES_RESTART)
+        # the basis V (m + 1 vectors) and Z (m vectors) per right-hand side, FP64
+        assert gm - base >= nrhs * (2 * m + 1) * n * 8
+        assert r.rl_dsposv_work_size(n, nrhs, prec | g) > r.rl_dsposv_work_size(n, nrhs, prec)
+    assert r.rl_dsgesv_work_size(n, nrhs, 0x200) == 0                # unknown flag bits
+    assert r.rl_dsgesv_work_size(n, nrhs, 7 | g) == 0                # unknown precision
+    # the restart length sizes the workspace and is range-checked
+    assert r.rl_get_param(r.RL_PARAM_GMRES_RESTART) == 50
+    w50 = r.rl_dsgesv_work_size(n, nrhs, g)
+    assert r.rl_set_param(r.RL_PARAM_GMRES_RESTART, 10) == 0
+    assert r.rl_dsgesv_work_size(n, nrhs, g) < w50
+    assert r.rl_set_param(r.RL_PARAM_GMRES_RESTART, 0) == r.RL_ERR_PARAM
+    assert r.rl_set_param(r.RL_PARAM_GMRES_RESTART, 65) == r.RL_ERR_PARAM
+    assert r.rl_set_param(r.RL_PARAM_GMRES_RESTART, 50) == 0
+    # more than 64 right-hand sides with the GMRES refinement: unsupported
+    # (checked on the host before any launch)
+    assert r.rl_dsgesv(n, 65, 8, n, 8, 8, n, 8, n, g, 1e-14, 30, 8, 8, 8, 1 << 40, 0) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_dsposv("L", n, 65, 8, n, 8, n, 8, n, g, 1e-14, 30, 8, 8, 8, 1 << 40, 0) == r.RL_ERR_UNSUPPORTED
+    assert r.rl_dsgesv(n, 65, 8, n, 8, 8, n, 8, n, 0, 1e-14, 30, 8, 8, None, 0, 0) == r.RL_ERR_WORKSPACE

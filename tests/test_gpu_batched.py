@@ -239,3 +239,33 @@ def test_autotuner_restores_the_batch_and_picks_a_config(batch_cfg_reset):
         assert oracle.res_lu(A, B.get(b), B.piv(b)) <= 10.0
     assert r.rl_vbatched_tune("G", 8, len(sizes), B.n, B.ptrs, B.lda, B.ipiv, B.info, 256, w, lw - 1)[0] \
         == r.RL_ERR_WORKSPACE
+
+
+@pytest.mark.parametrize("kind", ["potrf", "getrf"])
+def test_out_of_range_orders_report_argument_errors(kind):
+    """A matrix whose order is negative or above 256, or whose leading
+    dimension is below its order, gets LAPACK's argument error in its info
+    entry (-3 / -5 for potrf's order and lda arrays, -2 / -4 for getrf's) and
+    is not touched; the rest of the batch is factored as usual."""
+    t = G.torch()
+    sizes = [40, 12, 60, 33]
+    mats = [inputs.spd_bbt(n, seed=inputs.seed_for(3, 1500 + i)) if kind == "potrf"
+            else inputs.uniform(n, n, seed=inputs.seed_for(3, 1600 + i)) for i, n in enumerate(sizes)]
+    B = Batch(mats, t.float64)
+    before = B.buf.cpu().numpy().copy()
+    # matrix 1: order 300 (> 256); matrix 3: order -1; matrix 2: lda 59 < 60
+    B.n[1] = 300
+    B.n[3] = -1
+    B.lda[2] = 59
+    info = run(kind, B)
+    e_n, e_lda = (-3, -5) if kind == "potrf" else (-2, -4)
+    assert info.tolist() == [0, e_n, e_lda, e_n]
+    after = B.buf.cpu().numpy()
+    for b in (1, 2, 3):
+        o, n = B.offs[b], sizes[b]
+        assert np.array_equal(after[o:o + n * n], before[o:o + n * n]), b
+    F = B.get(0)
+    if kind == "potrf":
+        assert oracle.res_chol(mats[0], F) <= 10.0
+    else:
+        assert oracle.res_lu(mats[0], F, B.piv(0)) <= 10.0

@@ -176,3 +176,16 @@ def test_trs_workspace_too_small():
     assert lw > 0 and r.rl_trs_work_size(n, 65) == 0
     w = t.zeros(lw, dtype=t.uint8, device="cuda")
     assert r.rl_dpotrs("L", n, nrhs, buf, n, buf, n, w, lw - 1) == r.RL_ERR_WORKSPACE
+
+
+def test_mixed_zero_rhs_column_converges():
+    """A zero right-hand side next to ordinary ones: its residual, x and b
+    are all zero, which counts as converged (no division by a zero norm)."""
+    n = 300
+    A = inputs.general_spectrum(n, 1e3, seed=inputs.seed_for(2, 790))
+    B = inputs.normal(n, 3, seed=inputs.seed_for(2, 791))
+    B[:, 0] = 0.0
+    X, Aout, it, info, ipiv = run_mixed(A, B, prec=0)
+    assert it >= 0 and info == 0
+    assert np.all(X[:, 0] == 0.0)
+    assert oracle.backward_error(A, X, B) <= 1e-14
