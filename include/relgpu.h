@@ -603,6 +603,14 @@ int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda,
  *   RL_PARAM_OZ_MIN            smallest m, n and k of an FP64 update that
  *                              the *_oz routines emulate on the tensor
  *                              cores (default 128; smaller ones stay FP64)
+ *   RL_PARAM_PANEL_CLUSTER     1 (default): FP32 LU panels (width <= 32,
+ *                              at most 16384 rows) run on one cluster of
+ *                              2, 4, 8 or 16 CTAs that holds the panel in
+ *                              registers and exchanges the pivot candidates
+ *                              through distributed shared memory (one
+ *                              hardware cluster barrier per column); 0: the
+ *                              cooperative one-CTA-per-SM panel kernel.
+ *                              Both give the same bits.
  *   RL_PARAM_GMRES_RESTART     restart length of the GMRES refinement of
  *                              rl_dsgesv / rl_dsposv (1..64, default 50)
  *   RL_PARAM_NVTX              1: every recursion node (potrf, getrf,
@@ -623,7 +631,8 @@ enum {
     RL_PARAM_PANEL_CTAS = 8,
     RL_PARAM_OZ_MIN = 9,
     RL_PARAM_NVTX = 10,
-    RL_PARAM_GMRES_RESTART = 11
+    RL_PARAM_GMRES_RESTART = 11,
+    RL_PARAM_PANEL_CLUSTER = 12
 };
 int rl_set_param(int key, int64_t value);
 int64_t rl_get_param(int key);

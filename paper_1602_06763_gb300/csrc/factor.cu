@@ -19,6 +19,9 @@
 //                 all candidates back.
 //  k_panel_smem   the same algorithm with the rows as a column-major slab,
 //                 for panels taller than 256 rows per CTA.
+//  k_panel_cluster  FP32 panels of up to 16384 rows on one thread-block
+//                 cluster, the panel in registers, the candidates exchanged
+//                 through distributed shared memory.
 //  k_laswp        row interchanges: each CTA turns the swap sequence into the
 //                 net permutation of the touched rows (in shared memory) and
 //                 then moves every touched row of its columns with one
@@ -26,6 +29,8 @@
 // Every device-side wait is bounded (RL_PARAM_SPIN_LIMIT_NS); a wait that
 // runs out sets *info = RL_INFO_DEVICE_TIMEOUT and the kernel returns.
 #include <climits>
+#include <mutex>
+#include <cooperative_groups.h>
 #include "internal.cuh"
 
 namespace rl {
@@ -660,6 +665,227 @@ k_panel_smem(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info,
     }
 }
 
+// Cluster panel: the same algorithm on one thread-block cluster of CL CTAs
+// (CL = 2, 4, 8 or 16) with the panel held in registers: thread t of CTA q
+// keeps rows q R + t + k TH (k < RPT, R = RPT TH, TH threads per CTA), all
+// PCL_NB columns of each, and every column index is a compile-time constant
+// (the column loop is unrolled), so the update never touches shared memory.
+// Per column: each warp reduces its candidate, one block barrier, every
+// thread picks the CTA's candidate from the warp records, the owner thread
+// publishes the candidate's row and rank 0's owner of row j that row; one
+// cluster barrier (hardware, not a spin) makes the records visible; each
+// warp reads the CL candidates and the two rows through distributed shared
+// memory (lane c reads column c) and shares them by shuffles; the owners of
+// rows j and p swap, and every thread divides and updates its own rows.
+// The records are double-buffered: a CTA writes buffer j & 1 only after the
+// cluster barrier of column j - 1, which every CTA reaches after its reads
+// of column j - 2.  Same arithmetic per element as k_panel (bit-identical).
+constexpr int PCL_NB = 32;
+
+template <typename T, int CL, int RPT, int TH>
+__global__ void __launch_bounds__(TH)
+k_panel_cluster(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, const int32_t *abort)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    constexpr int R = RPT * TH;
+    constexpr int NW = TH / 32;
+    __shared__ unsigned long long ckey[2];
+    __shared__ int crow[2];
+    __shared__ T crowv[2][PCL_NB];                // this CTA's candidate row
+    __shared__ T rowjv[2][PCL_NB];                // row j (rank 0 only)
+    __shared__ unsigned long long wk[2][NW];
+    __shared__ int wi[2][NW];
+    __shared__ int s_skip;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int q = (int)cl.block_rank();
+    if (q == 0 && tid == 0) s_skip = (abort && *abort != 0) ? 1 : 0;
+    cl.sync();
+    if (*cl.map_shared_rank(&s_skip, 0)) {
+        cl.sync();                                // rank 0's word is read before it exits
+        return;
+    }
+    const i64 rbeg = (i64)q * R;
+    T a[RPT][PCL_NB];
+    i64 gi[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        gi[k] = rbeg + tid + (i64)k * TH;
+#pragma unroll
+        for (int c = 0; c < PCL_NB; ++c)
+            a[k][c] = (gi[k] < m && c < nb) ? A[(i64)c * lda + gi[k]] : T(0);
+    }
+    const int mn = (int)min(m, (i64)nb);
+    // the column loop is unrolled: every register column is addressed by a
+    // compile-time index
+#pragma unroll
+    for (int j = 0; j < PCL_NB; ++j) {
+        if (j < mn) {
+        const int buf = j & 1;
+        // 1. the warp's candidate: largest |a_ij| over rows i >= j, lowest i on ties
+        unsigned long long bk = 0;
+        int bi = PANEL_NONE;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+            if (gi[k] < m && gi[k] >= j) {
+                const unsigned long long key = abs_key(a[k][j]);
+                if (kbetter(key, (int)gi[k], bk, bi)) { bk = key; bi = (int)gi[k]; }
+            }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (kbetter(ok, oi, bk, bi)) { bk = ok; bi = oi; }
+        }
+        if (lane == 0) { wk[buf][warp] = bk; wi[buf][warp] = bi; }
+        __syncthreads();
+        // 2. the CTA's candidate (every thread reduces the warp records the same way)
+        bk = wk[buf][0];
+        bi = wi[buf][0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w)
+            if (kbetter(wk[buf][w], wi[buf][w], bk, bi)) { bk = wk[buf][w]; bi = wi[buf][w]; }
+        if (tid == 0) { ckey[buf] = bk; crow[buf] = bi; }
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (bi != PANEL_NONE && gi[k] == bi) {
+#pragma unroll
+                for (int c = 0; c < PCL_NB; ++c) crowv[buf][c] = a[k][c];
+            }
+            if (gi[k] == j) {
+#pragma unroll
+                for (int c = 0; c < PCL_NB; ++c) rowjv[buf][c] = a[k][c];
+            }
+        }
+        cl.sync();
+        // 3. the winner over the cluster (every warp), the pivot row and row j
+        unsigned long long k2 = 0;
+        int ix = PANEL_NONE, gw = -1;
+        if (lane < CL) {
+            const int qi = *cl.map_shared_rank(&crow[buf], lane);
+            if (qi != PANEL_NONE) { k2 = *cl.map_shared_rank(&ckey[buf], lane); ix = qi; gw = lane; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, k2, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
+            const int og = __shfl_xor_sync(0xffffffffu, gw, o);
+            if (og >= 0 && (gw < 0 || kbetter(ok, oi, k2, ix))) { k2 = ok; ix = oi; gw = og; }
+        }
+        const int p = (gw >= 0) ? ix : j;
+        // row j sits in rank 0 (j < nb <= R); lane c holds column c of each row
+        const T rjl = *cl.map_shared_rank(&rowjv[buf][lane], 0);
+        const T upl = gw >= 0 ? *cl.map_shared_rank(&crowv[buf][lane], gw) : rjl;
+        if (q == 0 && tid == 0) ipiv[r0 + j] = (int32_t)(r0 + p + 1);
+        const T piv = __shfl_sync(0xffffffffu, upl, j);
+        // 4. swap (the owners of rows j and p), divide, update; every lane
+        // takes part in every shuffle, only the owners keep the values
+        if (p != j) {
+#pragma unroll
+            for (int c = 0; c < PCL_NB; ++c) {
+                const T vu = __shfl_sync(0xffffffffu, upl, c);
+                const T vj = __shfl_sync(0xffffffffu, rjl, c);
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) {
+                    if (gi[k] == j) a[k][c] = vu;
+                    else if (gi[k] == p) a[k][c] = vj;
+                }
+            }
+        }
+        if (piv != T(0)) {
+            T l[RPT];
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const bool below = gi[k] < m && gi[k] > j;
+                l[k] = below ? a[k][j] / piv : T(0);
+                if (below) a[k][j] = l[k];
+            }
+#pragma unroll
+            for (int c = j + 1; c < PCL_NB; ++c) {
+                const T u = __shfl_sync(0xffffffffu, upl, c);
+#pragma unroll
+                for (int k = 0; k < RPT; ++k)
+                    if (gi[k] < m && gi[k] > j) a[k][c] = fma(-l[k], u, a[k][c]);
+            }
+        } else if (q == 0 && tid == 0 && *info == 0) {
+            *info = (int32_t)(r0 + j + 1);
+        }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+        if (gi[k] < m) {
+#pragma unroll
+            for (int c = 0; c < PCL_NB; ++c)
+                if (c < nb) A[(i64)c * lda + gi[k]] = a[k][c];
+        }
+    cl.sync();                                    // no CTA leaves while others may read its records
+}
+
+// Launch of the cluster panel with CL CTAs; false if this device cannot
+// place such a cluster (the caller then takes the cooperative kernel).
+template <typename T, int CL, int RPT, int TH>
+static bool launch_panel_cluster(Ctx &c, i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0)
+{
+    auto kern = k_panel_cluster<T, CL, RPT, TH>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(TH);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = c.s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    // once per device: the cluster-size attribute and whether such a
+    // cluster can be placed at all
+    static std::mutex mu;
+    static int state[128];                       // 0 unknown, 1 usable, 2 not
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return false;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (state[dev] == 0) {
+            state[dev] = 2;
+            int clusters = 0;
+            if ((CL <= 8 || cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                                cudaSuccess) &&
+                cudaOccupancyMaxActiveClusters(&clusters, (void *)kern, &cfg) == cudaSuccess && clusters >= 1)
+                state[dev] = 1;
+            (void)cudaGetLastError();
+        }
+        if (state[dev] != 1) return false;
+    }
+    int32_t *info = c.info;
+    const int32_t *abort = c.abort;
+    note(c, cudaLaunchKernelEx(&cfg, kern, m, nb, A, lda, ipiv, r0, info, abort));
+    return true;
+}
+
+// The register-resident cluster panel serves FP32 panels: 256 threads per
+// CTA, four rows of 32 floats per thread.  (FP64 panels measured slower on it
+// than on the cooperative kernel and keep that one.)
+constexpr int PCL_TH = 256;
+
+template <typename T>
+static bool panel_cluster(Ctx &c, i64 m, i64 nb, T *A, i64 lda, int32_t *ipiv, i64 r0)
+{
+    if constexpr (sizeof(T) != 4) {
+        return false;
+    } else {
+    constexpr int RPT = 4;
+    constexpr i64 R = (i64)RPT * PCL_TH;
+    if (nb > PCL_NB || m > 16 * R || m <= 0) return false;
+    const int ni = (int)nb;
+    if (m <= 2 * R) return launch_panel_cluster<T, 2, RPT, PCL_TH>(c, m, ni, A, lda, ipiv, r0);
+    if (m <= 4 * R) return launch_panel_cluster<T, 4, RPT, PCL_TH>(c, m, ni, A, lda, ipiv, r0);
+    if (m <= 8 * R) return launch_panel_cluster<T, 8, RPT, PCL_TH>(c, m, ni, A, lda, ipiv, r0);
+    return launch_panel_cluster<T, 16, RPT, PCL_TH>(c, m, ni, A, lda, ipiv, r0);
+    }
+}
+
 template <typename T>
 void getf2_panel(Ctx &c, i64 m, i64 nb, T *A, i64 lda, int32_t *ipiv, i64 r0)
 {
@@ -681,6 +907,10 @@ void getf2_panel(Ctx &c, i64 m, i64 nb, T *A, i64 lda, int32_t *ipiv, i64 r0)
     // flops of an m x nb unblocked LU (leading terms): m nb^2 - nb^3/3
     Launch L(c, K_PANEL, (double)m * nb * nb - (double)nb * nb * nb / 3.0,
              2.0 * (double)m * nb * sizeof(T));
+    // panels whose rows fit the registers of one cluster take the cluster kernel
+    if constexpr (!is_cplx<T>::value) {
+        if (g_params.panel_cluster && panel_cluster<T>(c, m, nb, A, lda, ipiv, r0)) return;
+    }
     note(c, cudaMemsetAsync(&ws->counter, 0, sizeof(unsigned), c.s));
     if (R <= PANEL_THREADS) {
         int nbi = (int)nb, Ri = (int)R;

@@ -81,6 +81,7 @@ struct Params {
     int oz_min = 128;        // smallest m, n and k that the FP64 emulation takes
     int nvtx = 0;            // 1: an NVTX range per recursion node (routine, order, depth)
     int gmres_m = 50;        // restart length of the GMRES refinement
+    int panel_cluster = 1;   // LU panels that fit a cluster's shared memory take the cluster kernel
 };
 extern Params g_params;
 

@@ -25,7 +25,8 @@ def main():
     ap.add_argument("--case", required=True,
                     choices=["dgemm", "dsyrk", "dtrsm", "potrf", "getrf", "trtri", "lauum", "panel",
                              "sgemm_tc", "dsgesv", "dsposv", "getrs", "potrs", "sgetrs", "sgemm", "laswp",
-                             "zpotrf", "zgetrf", "sgetrf_tc", "spotrf_tc"])
+                             "zpotrf", "zgetrf", "sgetrf_tc", "spotrf_tc", "vbatched_potrf", "vbatched_getrf"])
+    ap.add_argument("--count", type=int, default=20000, help="vbatched cases: matrices (orders uniform 8..256)")
     ap.add_argument("--prec", type=int, default=1, help="operand precision (rl_prec) of sgemm_tc / dsgesv")
     ap.add_argument("--nrhs", type=int, default=16)
     ap.add_argument("--cond", type=float, default=1e6)
@@ -45,10 +46,15 @@ def main():
     ap.add_argument("--oz-min", type=int, default=0, help="RL_PARAM_OZ_MIN value for the --oz cases")
     ap.add_argument("--uplo", default="L", help="potrf / trtri / lauum / zpotrf: triangle")
     ap.add_argument("--flow", type=int, default=1, help="getrs/potrs: 1 = one-launch flow solve, 0 = recursive")
+    ap.add_argument("--panel-cluster", type=int, default=-1, help="RL_PARAM_PANEL_CLUSTER value (0 or 1)")
+    ap.add_argument("--graph", action="store_true",
+                    help="time replays of the call captured once into a CUDA graph (after an eager warm-up)")
     a = ap.parse_args()
 
     if a.nb:
         r.check(r.rl_set_param(r.RL_PARAM_GETRF_PANEL, a.nb))
+    if a.panel_cluster >= 0:
+        r.check(r.rl_set_param(r.RL_PARAM_PANEL_CLUSTER, a.panel_cluster))
     if a.oz_min:
         r.check(r.rl_set_param(r.RL_PARAM_OZ_MIN, a.oz_min))
     if a.panel_ctas:
@@ -179,6 +185,51 @@ def main():
             Z = Z0.clone()
             run = lambda: r.check(r.rl_zgetrf(n, n, Z, n, ipiv, info, work, lw, s))
         restore = lambda: Z.copy_(Z0)
+    elif a.case in ("vbatched_potrf", "vbatched_getrf"):
+        # the batching form: `count` matrices with orders uniform on 8..256,
+        # packed 256-byte aligned (SPD B B^T + n I for potrf, U(-1, 1) for getrf)
+        import numpy as np
+        from . import inputs
+        sizes = inputs.bucket_sizes(a.count, 8, 256, inputs.seed_for(3, 0))
+        dt = torch.float32 if a.fp32 else torch.float64
+        esz = 4 if a.fp32 else 8
+        align = 256 // esz
+        offs, off = [], 0
+        for nn in sizes:
+            offs.append(off)
+            off += ((int(nn) * int(nn) + align - 1) // align) * align
+        A0 = torch.empty(off, dtype=dt, device=dev)
+        for nn in np.unique(sizes):
+            idx = np.nonzero(sizes == nn)[0]
+            nn = int(nn)
+            if a.case == "vbatched_potrf":
+                Bm = torch.randn(len(idx), nn, nn, generator=g, device=dev, dtype=torch.float64)
+                M = torch.bmm(Bm, Bm.transpose(1, 2))
+                M.diagonal(dim1=1, dim2=2).add_(float(nn))
+            else:
+                M = torch.rand(len(idx), nn, nn, generator=g, device=dev, dtype=torch.float64) * 2 - 1
+            M = M.to(dt)
+            for qq, b in enumerate(idx):
+                A0[offs[b]:offs[b] + nn * nn].copy_(M[qq].reshape(-1))
+        A = A0.clone()
+        ptrs = torch.tensor([A.data_ptr() + o * esz for o in offs], dtype=torch.int64, device=dev)
+        nvec = torch.tensor(sizes, dtype=torch.int32, device=dev)
+        binfo = torch.zeros(a.count, dtype=torch.int32, device=dev)
+        pstore = torch.zeros(int(np.sum(sizes)), dtype=torch.int32, device=dev)
+        pofs = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+        pptrs = torch.tensor([pstore.data_ptr() + 4 * int(qq) for qq in pofs], dtype=torch.int64, device=dev)
+        lw = r.rl_getrf_vbatched_work_size(a.count)
+        work = torch.empty(lw, dtype=torch.uint8, device=dev)
+        n3 = float(np.sum(sizes.astype(np.float64) ** 3))
+        if a.case == "vbatched_potrf":
+            fn = r.rl_spotrf_vbatched if a.fp32 else r.rl_dpotrf_vbatched
+            flops = n3 / 3.0
+            run = lambda: r.check(fn("L", a.count, nvec, ptrs, nvec, binfo, 256, work, lw, s))
+        else:
+            fn = r.rl_sgetrf_vbatched if a.fp32 else r.rl_dgetrf_vbatched
+            flops = 2.0 * n3 / 3.0
+            run = lambda: r.check(fn(a.count, nvec, ptrs, nvec, pptrs, binfo, 256, work, lw, s))
+        restore = lambda: A.copy_(A0)
     elif a.case in ("sgetrf_tc", "spotrf_tc"):
         # the precision form's factorization alone: FP32 storage, tcgen05
         # updates in operand precision --prec (0: SIMT FP32 rl_sgetrf / rl_spotrf)
@@ -264,6 +315,19 @@ def main():
         restore()
         run()
     torch.cuda.synchronize()
+    if a.graph:
+        # capture on a side stream (the calls take the current stream's handle)
+        gph = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream()
+        s_eager = s
+        with torch.cuda.stream(cs):
+            s = cs.cuda_stream
+            restore()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(gph, stream=cs):
+                run()
+        s = s_eager
+        run = gph.replay
     times = []
     if a.trace:
         r.rl_trace_enable(1)

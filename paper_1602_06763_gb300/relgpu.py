@@ -154,6 +154,7 @@ RL_PARAM_PANEL_CTAS = 8
 RL_PARAM_OZ_MIN = 9
 RL_PARAM_NVTX = 10
 RL_PARAM_GMRES_RESTART = 11
+RL_PARAM_PANEL_CLUSTER = 12
 
 
 def _ptr(x):
