@@ -37,7 +37,7 @@
  *   or_zgetri
  *   or_sygst        Section 5, xsygst (A := L^{-1} A L^{-T}, or L^T A L):
  *                   the definition, by substitution and products
- *   metrics         normwise backward errors used by the benchmark spec's bound
+ *   metrics         normwise backward errors of the pass bound (<= 10)
  *                   ||A - LL^T|| / (n eps ||A||) <= 10, computed with the
  *                   compensated dot product Dot2 of Ogita, Rump & Oishi (2005)
  *

@@ -29,6 +29,9 @@ namespace rl {
 namespace {
 
 constexpr int BMAX = 256;          // largest order handled
+// columns per pass of the batched LU's interchanges: (2 NB moved rows) x
+// BPERM_COLS elements staged in the U buffer (NB x (BMAX + 1) elements)
+constexpr int BPERM_COLS = 128;
 
 struct BatchWS {
     int next;                      // work counter (zeroed per launch)
@@ -77,6 +80,7 @@ __device__ __forceinline__ void tri_decode(int t, int &ti, int &tj)
 template <typename T, int BNB>
 __device__ void potrf_one(T *A, int n, int lda, int32_t *info, T *sm)
 {
+    __shared__ int s_fail;
     T *D = sm;                           // BNB x (BNB+1)
     T *P = sm + BNB * (BNB + 1);         // (BMAX) x (BNB+1), row-major
     const int tid = threadIdx.x, bd = blockDim.x;
@@ -88,22 +92,48 @@ __device__ void potrf_one(T *A, int n, int lda, int32_t *info, T *sm)
             if (i >= j) D[i * LD + j] = A[(i64)(k0 + j) * lda + k0 + i];
         }
         __syncthreads();
-        int fail = 0;
-        for (int j = 0; j < kb; ++j) {
-            const T d = D[j * LD + j];
-            if (!(d > T(0))) { fail = j + 1; break; }
-            const T ljj = sqrt(d);
-            __syncthreads();
-            if (tid == 0) D[j * LD + j] = ljj;
-            for (int i = j + 1 + tid; i < kb; i += bd) D[i * LD + j] = D[i * LD + j] / ljj;
-            __syncthreads();
-            const int t = kb - j - 1;
-            for (int e = tid; e < t * t; e += bd) {
-                const int ii = j + 1 + e % t, kk = j + 1 + e / t;
-                if (ii >= kk) D[ii * LD + kk] = fma(-D[ii * LD + j], D[kk * LD + j], D[ii * LD + kk]);
+        // unblocked Cholesky of the diagonal block: FP64 by warp 0 alone (warp
+        // barriers only; the other warps wait at the block barrier below),
+        // FP32 by the whole CTA (measured faster there)
+        if constexpr (sizeof(T) == 4) {
+            int f = 0;
+            for (int j = 0; j < kb; ++j) {
+                const T d = D[j * LD + j];
+                if (!(d > T(0))) { f = j + 1; break; }
+                const T ljj = sqrt(d);
+                __syncthreads();
+                if (tid == 0) D[j * LD + j] = ljj;
+                for (int i = j + 1 + tid; i < kb; i += bd) D[i * LD + j] = D[i * LD + j] / ljj;
+                __syncthreads();
+                const int t = kb - j - 1;
+                for (int e = tid; e < t * t; e += bd) {
+                    const int ii = j + 1 + e % t, kk = j + 1 + e / t;
+                    if (ii >= kk) D[ii * LD + kk] = fma(-D[ii * LD + j], D[kk * LD + j], D[ii * LD + kk]);
+                }
+                __syncthreads();
             }
-            __syncthreads();
+            if (tid == 0) s_fail = f;
+        } else if (tid < 32) {
+            int f = 0;
+            for (int j = 0; j < kb; ++j) {
+                const T d = D[j * LD + j];
+                if (!(d > T(0))) { f = j + 1; break; }
+                const T ljj = sqrt(d);
+                __syncwarp();
+                if (tid == 0) D[j * LD + j] = ljj;
+                for (int i = j + 1 + tid; i < kb; i += 32) D[i * LD + j] = D[i * LD + j] / ljj;
+                __syncwarp();
+                const int t = kb - j - 1;
+                for (int e = tid; e < t * t; e += 32) {
+                    const int ii = j + 1 + e % t, kk = j + 1 + e / t;
+                    if (ii >= kk) D[ii * LD + kk] = fma(-D[ii * LD + j], D[kk * LD + j], D[ii * LD + kk]);
+                }
+                __syncwarp();
+            }
+            if (tid == 0) s_fail = f;
         }
+        __syncthreads();
+        const int fail = s_fail;
         for (int e = tid; e < kb * kb; e += bd) {
             const int i = e % kb, j = e / kb;
             if (i >= j) A[(i64)(k0 + j) * lda + k0 + i] = D[i * LD + j];
@@ -183,10 +213,14 @@ template <typename T, int BNB>
 __device__ void getrf_one(T *A, int n, int lda, int32_t *ipiv, int32_t *info, T *sm, double *wv,
                           int *wi, int *s_piv)
 {
+    __shared__ int s_perm[BMAX];                 // net permutation of the block's interchanges
+    __shared__ int s_tl[2 * BNB];                // the rows it moves
+    __shared__ int s_nt;
     constexpr int LD = BNB + 1;          // panel row stride
     constexpr int LU = BMAX + 1;         // U block row stride
     T *P = sm;                           // BMAX x LD, row-major: P[i*LD + c]
     T *U = sm + BMAX * LD;               // BNB x LU: U[c*LU + col]
+    T *stage = U;                        // the interchanges' staging (U is free until the solve)
     const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5;
     for (int k0 = 0; k0 < n; k0 += BNB) {
         const int kb = min(BNB, n - k0), mp = n - k0;
@@ -195,63 +229,139 @@ __device__ void getrf_one(T *A, int n, int lda, int32_t *ipiv, int32_t *info, T 
             P[i * LD + c] = A[(i64)(k0 + c) * lda + k0 + i];
         }
         __syncthreads();
-        for (int j = 0; j < kb; ++j) {
-            // block argmax of |P[i][j]|, i >= j, lowest i on ties
-            double bv = -1.0;
-            int bi = INT_MAX;
-            for (int i = j + tid; i < mp; i += bd) {
-                const double v = fabs((double)P[i * LD + j]);
-                if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_down_sync(0xffffffffu, bv, o);
-                const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-            }
-            if (lane == 0) { wv[warp] = bv; wi[warp] = bi; }
-            __syncthreads();
-            if (tid == 0) {
-                for (int w = 1; w < (bd >> 5); ++w)
-                    if (wv[w] > bv || (wv[w] == bv && wi[w] < bi)) { bv = wv[w]; bi = wi[w]; }
-                const int p = (bi == INT_MAX) ? j : bi;
-                s_piv[j] = p;
-                ipiv[k0 + j] = k0 + p + 1;
-            }
-            __syncthreads();
-            const int p = s_piv[j];
-            if (p != j)
-                for (int c = tid; c < kb; c += bd) {
-                    const T t = P[j * LD + c];
-                    P[j * LD + c] = P[p * LD + c];
-                    P[p * LD + c] = t;
+        // the panel: per column an argmax of |P[i][j]|, i >= j (lowest i on
+        // ties), the swap, the division by the pivot and the rank-1 update --
+        // FP32: by warp 0 alone, separated by warp barriers only; then (warp
+        // 0) the net row permutation of the block's interchanges (final row r
+        // holds original row s_perm[r]) and the list of the rows it moves
+        if constexpr (sizeof(T) == 8) {
+            // FP64: the panel's arithmetic (one FP64 unit per quarter of the
+            // SM) needs every warp; a block argmax and block barriers
+            for (int j = 0; j < kb; ++j) {
+                double bv = -1.0;
+                int bi = INT_MAX;
+                for (int i = j + tid; i < mp; i += bd) {
+                    const double v = fabs((double)P[i * LD + j]);
+                    if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
                 }
-            __syncthreads();
-            const T piv = P[j * LD + j];
-            if (piv != T(0)) {
-                for (int i = j + 1 + tid; i < mp; i += bd) {
-                    const T l = P[i * LD + j] / piv;
-                    P[i * LD + j] = l;
-                    for (int c = j + 1; c < kb; ++c) P[i * LD + c] = fma(-l, P[j * LD + c], P[i * LD + c]);
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+                    const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
                 }
-            } else if (tid == 0 && *info == 0) {
-                *info = k0 + j + 1;
+                if (lane == 0) { wv[warp] = bv; wi[warp] = bi; }
+                __syncthreads();
+                if (tid == 0) {
+                    for (int w = 1; w < (bd >> 5); ++w)
+                        if (wv[w] > bv || (wv[w] == bv && wi[w] < bi)) { bv = wv[w]; bi = wi[w]; }
+                    const int p = (bi == INT_MAX) ? j : bi;
+                    s_piv[j] = p;
+                    ipiv[k0 + j] = k0 + p + 1;
+                }
+                __syncthreads();
+                const int p = s_piv[j];
+                if (p != j)
+                    for (int c = tid; c < kb; c += bd) {
+                        const T t = P[j * LD + c];
+                        P[j * LD + c] = P[p * LD + c];
+                        P[p * LD + c] = t;
+                    }
+                __syncthreads();
+                const T piv = P[j * LD + j];
+                if (piv != T(0)) {
+                    for (int i = j + 1 + tid; i < mp; i += bd) {
+                        const T l = P[i * LD + j] / piv;
+                        P[i * LD + j] = l;
+                        for (int c = j + 1; c < kb; ++c) P[i * LD + c] = fma(-l, P[j * LD + c], P[i * LD + c]);
+                    }
+                } else if (tid == 0 && *info == 0) {
+                    *info = k0 + j + 1;
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
+        if (warp == 0) {
+            if constexpr (sizeof(T) != 8)
+            for (int j = 0; j < kb; ++j) {
+                double bv = -1.0;
+                int bi = INT_MAX;
+                for (int i = j + lane; i < mp; i += 32) {
+                    const double v = fabs((double)P[i * LD + j]);
+                    if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+                }
+                const int p = (bi == INT_MAX) ? j : bi;
+                if (lane == 0) {
+                    s_piv[j] = p;
+                    ipiv[k0 + j] = k0 + p + 1;
+                }
+                if (p != j)
+                    for (int c = lane; c < kb; c += 32) {
+                        const T t = P[j * LD + c];
+                        P[j * LD + c] = P[p * LD + c];
+                        P[p * LD + c] = t;
+                    }
+                __syncwarp();
+                const T piv = P[j * LD + j];
+                if (piv != T(0)) {
+                    for (int i = j + 1 + lane; i < mp; i += 32) {
+                        const T l = P[i * LD + j] / piv;
+                        P[i * LD + j] = l;
+                        for (int c = j + 1; c < kb; ++c) P[i * LD + c] = fma(-l, P[j * LD + c], P[i * LD + c]);
+                    }
+                } else if (lane == 0 && *info == 0) {
+                    *info = k0 + j + 1;
+                }
+                __syncwarp();
+            }
+            for (int i = lane; i < mp; i += 32) s_perm[i] = i;
+            __syncwarp();
+            if (lane == 0)
+                for (int j = 0; j < kb; ++j) {
+                    const int p = s_piv[j], t = s_perm[j];
+                    s_perm[j] = s_perm[p];
+                    s_perm[p] = t;
+                }
+            __syncwarp();
+            int nt = 0;
+            for (int base = 0; base < mp; base += 32) {
+                const int i = base + lane;
+                const bool moved = i < mp && s_perm[i] != i;
+                const unsigned mk = __ballot_sync(0xffffffffu, moved);
+                if (moved) s_tl[nt + __popc(mk & ((1u << lane) - 1u))] = i;
+                nt += __popc(mk);
+            }
+            if (lane == 0) s_nt = nt;
+        }
+        __syncthreads();
         for (int e = tid; e < mp * kb; e += bd) {
             const int i = e % mp, c = e / mp;
             A[(i64)(k0 + c) * lda + k0 + i] = P[i * LD + c];
         }
-        // interchanges on the columns outside the panel, in pivot order
-        for (int col = tid; col < n - kb; col += bd) {
-            const int cc = (col < k0) ? col : col + kb;
-            T *cp = A + (i64)cc * lda + k0;
-            for (int j = 0; j < kb; ++j) {
-                const int p = s_piv[j];
-                if (p != j) { const T t = cp[j]; cp[j] = cp[p]; cp[p] = t; }
+        // the interchanges on the columns outside the panel: (moved row,
+        // column) pairs spread over the threads, every moved element read
+        // into shared memory, then written to its final place
+        const int nt = s_nt;
+        const int nc_out = n - kb;
+        for (int c0 = 0; c0 < nc_out; c0 += BPERM_COLS) {
+            const int cw = min(BPERM_COLS, nc_out - c0);
+            for (int e = tid; e < nt * cw; e += bd) {
+                const int t = e % nt, col = c0 + e / nt;
+                const int cc = (col < k0) ? col : col + kb;
+                stage[e] = A[(i64)cc * lda + k0 + s_perm[s_tl[t]]];
             }
+            __syncthreads();
+            for (int e = tid; e < nt * cw; e += bd) {
+                const int t = e % nt, col = c0 + e / nt;
+                const int cc = (col < k0) ? col : col + kb;
+                A[(i64)cc * lda + k0 + s_tl[t]] = stage[e];
+            }
+            __syncthreads();
         }
-        __syncthreads();
         // U block row: L11^{-1} A12 (unit lower), one column per thread
         const int nc = n - k0 - kb;
         for (int col = tid; col < nc; col += bd) {

@@ -1,7 +1,7 @@
 """Batching form (rl_[ds]potrf_vbatched, rl_[ds]getrf_vbatched) against the
 oracle, matrix by matrix.
 
-FP64: the benchmark spec's bound (residual / (n eps ||A||) <= 10, eps = 2^-53) and
+FP64: the pass bound (residual / (n eps ||A||) <= 10, eps = 2^-53) and
 ipiv equal to the oracle's up to the first near-tie; integer / dyadic
 matrices bit-exact.  FP32: the same residual measured in units of the FP32
 rounding unit 2^-24 on the FP32-rounded input.

@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-Bar (the benchmark spec): backward errors ||A - L L^T|| / (n eps ||A||) and
+Bar: backward errors ||A - L L^T|| / (n eps ||A||) and
 ||P A - L U|| / (n eps ||A||) <= 10, and the analogous TRTRI / POTRI
 residuals; ipiv equal to the oracle's up to the first pivot near-tie (relative
 gap < 1e-12); factors that are exact in binary64 (integer / dyadic inputs)

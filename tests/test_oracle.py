@@ -4,7 +4,7 @@ Each test ties the oracle to something other than itself: the paper's printed
 per-level flop shares (Section 3, Fig. 5), closed forms of 2x2 cases, factors
 that are exact in binary64 (integer / dyadic constructions), exact rational
 brute force on tiny inputs, LAPACK through scipy, and the backward-error bound
-of the benchmark spec (residual / (n eps ||A||) <= 10).  The planted-mistake
+of the required accuracy (residual / (n eps ||A||) <= 10).  The planted-mistake
 tests show that each check fails when a plausible error (a dropped update, a
 wrong sign, a transposed block, a swapped pivot) is put into the oracle's
 output.
@@ -355,7 +355,7 @@ def test_trtri_info_zero_diagonal(oracle):
 
 
 # ----------------------------------------------------------------------------
-# random residual bounds and crossover invariance (spec bound <= 10)
+# random residual bounds and crossover invariance (bound <= 10)
 # ----------------------------------------------------------------------------
 
 @pytest.mark.parametrize("n", [3, 64, 129, 300, 512])
