@@ -1109,46 +1109,46 @@ def run_gpu(args, rank, world, local_rank):
     if rank != 0:
         return 0
 
-    mixed = None
-    if args.mixed_n > 0:
-        del spd0, gen0
-        torch.cuda.empty_cache()
-        mixed = mixed_section(args.mixed_n, args.mixed_nrhs, args.mixed_cond,
-                              [p for p in args.mixed_precs.split(",") if p], dev, sp,
-                              gmres_budget=args.gmres_budget)
+    secs = {}
 
-    mixed_large = None
-    if args.mixed4_n > 0:
-        torch.cuda.empty_cache()
-        mixed_large = mixed_section(args.mixed4_n, args.mixed4_nrhs, args.mixed4_cond,
-                                    [p for p in args.mixed4_precs.split(",") if p], dev, sp, reps=1,
-                                    gmres_budget=args.gmres_budget)
+    def section(name, fn):
+        t0 = time.perf_counter()
+        out = fn()
+        secs[name] = round(time.perf_counter() - t0, 1)
+        return out
 
-    large = None
-    if args.large_n > 0:
-        torch.cuda.empty_cache()
-        large = large_section(args.large_n, dev, sp)
-
-    batched = None
-    if args.batch_count > 0:
-        batched = batched_section(args.batch_count, args.batch_baseline, dev, sp)
-
-    others = routines_section(args.others_n, dev, sp) if args.others_n > 0 else None
-    lowprec = lowprec_section(args.lowprec_n, dev, sp) if args.lowprec_n > 0 else None
-    emulated = emulated_section(args.oz_n, args.oz_slices, dev, sp) if args.oz_n > 0 else None
-    graphs = graph_section(n, dev, sp) if args.graph else None
-    cusolver = cusolver_section(n, dev) if args.cusolver else None
+    del spd0, gen0
+    torch.cuda.empty_cache()
+    mixed = section("mixed_solve", lambda: mixed_section(
+        args.mixed_n, args.mixed_nrhs, args.mixed_cond, [p for p in args.mixed_precs.split(",") if p], dev, sp,
+        gmres_budget=args.gmres_budget)) if args.mixed_n > 0 else None
+    torch.cuda.empty_cache()
+    mixed_large = section("mixed_solve_large", lambda: mixed_section(
+        args.mixed4_n, args.mixed4_nrhs, args.mixed4_cond, [p for p in args.mixed4_precs.split(",") if p], dev,
+        sp, reps=1, gmres_budget=args.gmres_budget)) if args.mixed4_n > 0 else None
+    torch.cuda.empty_cache()
+    large = section("large", lambda: large_section(args.large_n, dev, sp)) if args.large_n > 0 else None
+    batched = section("batched", lambda: batched_section(args.batch_count, args.batch_baseline, dev, sp)) \
+        if args.batch_count > 0 else None
+    others = section("other_routines", lambda: routines_section(args.others_n, dev, sp)) if args.others_n > 0 else None
+    lowprec = section("lowprec", lambda: lowprec_section(args.lowprec_n, dev, sp)) if args.lowprec_n > 0 else None
+    emulated = section("fp64_emulated", lambda: emulated_section(args.oz_n, args.oz_slices, dev, sp)) \
+        if args.oz_n > 0 else None
+    graphs = section("graph_replay", lambda: graph_section(n, dev, sp)) if args.graph else None
+    cusolver = section("cusolver", lambda: cusolver_section(n, dev)) if args.cusolver else None
 
     cpu = None
     if world == 1 and args.cpu_n > 0:
         from oracle import build as obuild
         obuild.build()
+        t0 = time.perf_counter()
         gfl, dt = oracle_sample(args.cpu_n)
         cpu = {"value": gfl, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                "sample": f"oracle dpotrf+dgetrf once at n={args.cpu_n} (same recipes as the n={n} workload), "
                          f"c=24, {dt:.1f} s; GFLOP/s of that order",
                "sample_n": args.cpu_n, "cpu_model": cpu_model(),
                "lapack_context": cpu_lapack_context(min(args.cpu_n, 4096))}
+        secs["cpu_baseline"] = round(time.perf_counter() - t0, 1)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1182,6 +1182,7 @@ def run_gpu(args, rank, world, local_rank):
         "fp64_emulated": emulated,
         "graph_replay": graphs,
         "cusolver_context": cusolver,
+        "section_seconds": secs,
         "summary_mixed": summarize_mixed(mixed, mixed_large),
         "summary_batched": summarize_batched(batched),
         "large": large,
@@ -1197,8 +1198,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=16384)
-    ap.add_argument("--cpu-n", type=int, default=8192,
-                    help="order of the oracle's timed sample for cpu_baseline (about 20 s on 16 cores)")
+    ap.add_argument("--cpu-n", type=int, default=6144,
+                    help="order of the oracle's timed sample for cpu_baseline (about 15 s on 16 cores)")
     ap.add_argument("--ref-n", type=int, default=3072,
                     help="order of the oracle's sample per step in the reference arm")
     ap.add_argument("--e2e-steps", type=int, default=2)
