@@ -611,6 +611,11 @@ int rl_dgetrf_host(int64_t m, int64_t n, double *A_host, int64_t lda,
  *                              hardware cluster barrier per column); 0: the
  *                              cooperative one-CTA-per-SM panel kernel.
  *                              Both give the same bits.
+ *   RL_PARAM_TC_PAIRS          1 (default): the tensor-core GEMM of the
+ *                              precision form runs pairs of row tiles on
+ *                              clusters of two CTAs that share the B tile
+ *                              (each loads half and multicasts it); 0: one
+ *                              CTA per tile.  Both give the same bits.
  *   RL_PARAM_GMRES_RESTART     restart length of the GMRES refinement of
  *                              rl_dsgesv / rl_dsposv (1..64, default 50)
  *   RL_PARAM_NVTX              1: every recursion node (potrf, getrf,
@@ -632,7 +637,8 @@ enum {
     RL_PARAM_OZ_MIN = 9,
     RL_PARAM_NVTX = 10,
     RL_PARAM_GMRES_RESTART = 11,
-    RL_PARAM_PANEL_CLUSTER = 12
+    RL_PARAM_PANEL_CLUSTER = 12,
+    RL_PARAM_TC_PAIRS = 13
 };
 int rl_set_param(int key, int64_t value);
 int64_t rl_get_param(int key);

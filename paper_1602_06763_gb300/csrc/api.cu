@@ -1642,6 +1642,10 @@ int rl_set_param(int key, int64_t value)
         if (value != 0 && value != 1) return RL_ERR_PARAM;
         g_params.panel_cluster = (int)value;
         return RL_SUCCESS;
+    case RL_PARAM_TC_PAIRS:
+        if (value != 0 && value != 1) return RL_ERR_PARAM;
+        g_params.tc_pairs = (int)value;
+        return RL_SUCCESS;
     case RL_PARAM_PANEL_CTAS:
         // low 16 bits: FP64 panels, high 16 bits: FP32 panels (0 = one per SM)
         if (value < 0 || (value & 0xffff) > 256 || (value >> 16) > 256) return RL_ERR_PARAM;
@@ -1667,6 +1671,7 @@ int64_t rl_get_param(int key)
     case RL_PARAM_NVTX: return g_params.nvtx;
     case RL_PARAM_GMRES_RESTART: return g_params.gmres_m;
     case RL_PARAM_PANEL_CLUSTER: return g_params.panel_cluster;
+    case RL_PARAM_TC_PAIRS: return g_params.tc_pairs;
     case RL_PARAM_PANEL_CTAS: return (int64_t)g_params.panel_ctas64 | ((int64_t)g_params.panel_ctas32 << 16);
     default: return -1;
     }

@@ -82,6 +82,7 @@ struct Params {
     int nvtx = 0;            // 1: an NVTX range per recursion node (routine, order, depth)
     int gmres_m = 50;        // restart length of the GMRES refinement
     int panel_cluster = 1;   // LU panels that fit a cluster's shared memory take the cluster kernel
+    int tc_pairs = 1;        // tensor-core GEMM: row-tile pairs on 2-CTA clusters sharing B
 };
 extern Params g_params;
 

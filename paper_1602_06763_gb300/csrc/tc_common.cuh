@@ -86,6 +86,27 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// TMA load multicast to the CTAs of this cluster in cta_mask: the tile lands
+// at the same shared-memory offset in each, and each one's mbarrier at the
+// same offset receives the byte count.
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y,
+                                               uint16_t cta_mask)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%3, %4}], [%2], %5;"
+        ::"r"(su32(dst)), "l"(map), "r"(su32(bar)), "r"(x), "r"(y), "h"(cta_mask)
+        : "memory");
+}
+
+// Cluster-wide barrier of every thread of every CTA in the cluster (the
+// warp converges first: the barrier is the aligned form).
+__device__ __forceinline__ void cluster_sync_all()
+{
+    __syncwarp();
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart, tile base 1024-byte aligned.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
@@ -124,6 +145,15 @@ __device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+// Arrive (when the MMAs issued so far complete) on the mbarrier at this
+// offset in every CTA of cta_mask.
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t cta_mask)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 ::"r"(su32(bar)), "h"(cta_mask)
                  : "memory");
 }
 

@@ -21,6 +21,7 @@
 // Every mbarrier wait is bounded; a wait that runs out sets the error word
 // (RL_INFO_DEVICE_TIMEOUT) and the CTA drains its copies, frees TMEM and
 // returns.
+#include <mutex>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -48,7 +49,14 @@ constexpr int TMEM_COLS = 256;
 // warps drain the other, so a tile's read-modify-write of C overlaps the
 // next tile's main loop.
 // FMT: operand format of the instruction descriptor (0 FP16, 1 BF16, 2 TF32).
-template <int FMT, int NSPLIT, int STAGES, bool LOWER>
+//
+// CL = 2: the CTAs run as clusters of two that take pairs of row tiles
+// (2p, 2p + 1) of one column tile, so both need the same B tile: each CTA
+// loads its own A tile and one half (128 rows) of B, multicast into both
+// CTAs' shared memory; a stage is free again only when the MMAs of both CTAs
+// have read it (each CTA's MMA commits to the "empty" barriers of both).
+// Each CTA reads 32 KB instead of 48 KB of operands per 128 bytes of K.
+template <int FMT, int NSPLIT, int STAGES, bool LOWER, int CL>
 __global__ void __launch_bounds__(THREADS, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
           const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
@@ -67,7 +75,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], CL); }
         for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
         mbar_init(&final_bar, 1);
         s_err = 0;
@@ -80,24 +88,41 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+    if (CL > 1) cluster_sync_all();          // the peer's barriers are initialised before any remote arrive
+    else __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
-    // lower-triangle updates: tiles entirely above the diagonal have no work
-    // (every role applies the same rule, so all see the same tile sequence)
-    auto skip = [&](int t) {
-        const int tm = t % tiles_m, tn = t / tiles_m;
-        return LOWER && tm * BM + BM <= tn * BN;
+    // The work list: single tiles (CL = 1; row tiles fastest, so CTAs
+    // running at the same time share the B tile) or row-tile pairs (CL = 2;
+    // this CTA takes the pair's row tile of its rank).  A pair's second row
+    // tile may lie past the last one: it is computed on the zero fill of the
+    // A copies and writes nothing.
+    const int rank = CL > 1 ? (int)(blockIdx.x % CL) : 0;
+    const int pairs_m = (tiles_m + CL - 1) / CL;
+    const int utotal = pairs_m * (tiles_total / tiles_m);
+    const int ustart = (int)blockIdx.x / CL, ustep = (int)gridDim.x / CL;
+    auto coords = [&](int u, int &tm, int &tn) {
+        tm = CL * (u % pairs_m) + rank;
+        tn = u / pairs_m;
+    };
+    // lower-triangle updates: work units entirely above the diagonal have no
+    // work (every role of both CTAs applies the same rule on the unit's last
+    // row tile, so all see the same sequence)
+    auto skip = [&](int u) {
+        const int tmax = CL * (u % pairs_m) + CL - 1, tn = u / pairs_m;
+        return LOWER && tmax * BM + BM <= tn * BN;
     };
 
     if (warp == 0) {
         if (lane == 0) {
             int g = 0;                                  // ring position across tiles
             bool fail = false;
-            for (int t = blockIdx.x; t < tiles_total && !fail; t += gridDim.x) {
-                if (skip(t)) continue;
-                const int m0 = (t % tiles_m) * BM, n0 = (t / tiles_m) * BN;
+            for (int u = ustart; u < utotal && !fail; u += ustep) {
+                if (skip(u)) continue;
+                int tm, tn;
+                coords(u, tm, tn);
+                const int m0 = tm * BM, n0 = tn * BN;
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
                     const int s = g % STAGES;
                     if (!mbar_wait(&empty_bar[s], ((g / STAGES) & 1) ^ 1, limit_ns) || s_err) {
@@ -109,10 +134,22 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                     mbar_expect_tx(&full_bar[s], STAGE);
                     const int kx = kb * (F16KIND ? 64 : 32);   // 128 bytes of K per stage
                     tma_load_2d(st, &mA0, &full_bar[s], kx, m0);
-                    tma_load_2d(st + A_TILE, &mB0, &full_bar[s], kx, n0);
+                    if (CL == 1) {
+                        tma_load_2d(st + A_TILE, &mB0, &full_bar[s], kx, n0);
+                    } else {
+                        // this CTA's half of B (the maps' box is BN / 2 rows), into both CTAs
+                        constexpr int HB = B_TILE / 2;
+                        tma_load_2d_mc(st + A_TILE + rank * HB, &mB0, &full_bar[s], kx, n0 + rank * (BN / 2), 0x3);
+                    }
                     if (NSPLIT == 2) {
                         tma_load_2d(st + A_TILE + B_TILE, &mA1, &full_bar[s], kx, m0);
-                        tma_load_2d(st + 2 * A_TILE + B_TILE, &mB1, &full_bar[s], kx, n0);
+                        if (CL == 1) {
+                            tma_load_2d(st + 2 * A_TILE + B_TILE, &mB1, &full_bar[s], kx, n0);
+                        } else {
+                            constexpr int HB = B_TILE / 2;
+                            tma_load_2d_mc(st + 2 * A_TILE + B_TILE + rank * HB, &mB1, &full_bar[s], kx,
+                                           n0 + rank * (BN / 2), 0x3);
+                        }
                     }
                 }
             }
@@ -125,8 +162,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
             constexpr uint32_t ID = idesc((uint32_t)FMT, BM, BN);
             int g = 0, i = 0;
             bool fail = false;
-            for (int t = blockIdx.x; t < tiles_total && !fail; t += gridDim.x) {
-                if (skip(t)) continue;
+            for (int u = ustart; u < utotal && !fail; u += ustep) {
+                if (skip(u)) continue;
                 const int b = i & 1;
                 if (!mbar_wait(&tempty[b], ((i >> 1) & 1) ^ 1, limit_ns)) { atomicExch(&s_err, 1); break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -151,7 +188,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
                             mma<F16KIND>(d, sdesc(sa1 + kk * 32), sdesc(sb + kk * 32), ID, 1u);
                         }
                     }
-                    mma_commit(&empty_bar[s]);
+                    if (CL == 1) mma_commit(&empty_bar[s]);
+                    else mma_commit_mc(&empty_bar[s], 0x3);    // the stage holds B halves of both CTAs
                 }
                 if (!fail) mma_commit(&tfull[b]);
                 ++i;
@@ -164,10 +202,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         // epilogue: warps 2..5 -> TMEM lane quarters (warp % 4)
         const int q = warp & 3;
         int i = 0;
-        for (int t = blockIdx.x; t < tiles_total; t += gridDim.x) {
-            if (skip(t)) continue;
+        for (int u = ustart; u < utotal; u += ustep) {
+            if (skip(u)) continue;
             const int b = i & 1;
-            const int m0 = (t % tiles_m) * BM, n0 = (t / tiles_m) * BN;
+            int tm, tn;
+            coords(u, tm, tn);
+            const int m0 = tm * BM, n0 = tn * BN;
             const int row = m0 + q * 32 + lane;
             if (!mbar_wait(&tfull[b], (i >> 1) & 1, limit_ns)) atomicExch(&s_err, 1);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -196,7 +236,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUten
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+    // a CTA leaves only when its peer no longer copies into it or arrives on its barriers
+    if (CL > 1) cluster_sync_all();
+    else __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS));
@@ -298,19 +340,68 @@ size_t tc_work_bytes(i64 m, i64 n, i64 k, int prec)
     return (size_t)split * ((size_t)mp + (size_t)np) * (size_t)kp * esz + 2048;
 }
 
-template <int FMT, int NSPLIT, int STAGES, bool LOWER>
+template <int FMT, int NSPLIT, int STAGES, bool LOWER, int CL>
 static cudaError_t launch_tc(const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
                              const CUtensorMap &b1, int m, int n, int nkb, float alpha, float *C, i64 ldc,
                              int tiles_m, int tiles_total, unsigned grid, int32_t *err, long long lim,
                              const int32_t *abort, cudaStream_t s)
 {
-    auto kern = tc::k_tc_gemm<FMT, NSPLIT, STAGES, LOWER>;
+    auto kern = tc::k_tc_gemm<FMT, NSPLIT, STAGES, LOWER, CL>;
     const int smem = STAGES * NSPLIT * (tc::A_TILE + tc::B_TILE) + 1024;
     cudaError_t e = smem_optin(kern, (size_t)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, tc::THREADS, smem, s>>>(a0, a1, b0, b1, m, n, nkb, alpha, C, ldc, tiles_m, tiles_total, err,
-                                         lim, abort);
-    return cudaGetLastError();
+    if (CL == 1) {
+        kern<<<grid, tc::THREADS, smem, s>>>(a0, a1, b0, b1, m, n, nkb, alpha, C, ldc, tiles_m, tiles_total, err,
+                                             lim, abort);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(tc::THREADS);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a0, a1, b0, b1, m, n, nkb, alpha, C, ldc, tiles_m, tiles_total, err,
+                              lim, abort);
+}
+
+// Whether clusters of two CTAs of the tensor-core GEMM (largest shared-memory
+// footprint) can be placed on this device; asked once per device.
+static bool tc_pairs_ok()
+{
+    static std::mutex mu;
+    static int state[128];                   // 0 unknown, 1 yes, 2 no
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (state[dev] == 0) {
+        state[dev] = 2;
+        auto kern = tc::k_tc_gemm<1, 1, 4, false, 2>;
+        const int smem = 4 * (tc::A_TILE + tc::B_TILE) + 1024;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2);
+        cfg.blockDim = dim3(tc::THREADS);
+        cfg.dynamicSmemBytes = (size_t)smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (smem_optin(kern, (size_t)smem) == cudaSuccess &&
+            cudaOccupancyMaxActiveClusters(&clusters, (void *)kern, &cfg) == cudaSuccess && clusters >= 1)
+            state[dev] = 1;
+        (void)cudaGetLastError();
+    }
+    return state[dev] == 1;
 }
 
 // C(m x n) += alpha op(A) op(B) on the tensor cores; lower: square C, only
@@ -358,36 +449,45 @@ bool tc_gemm(Ctx &c, int prec, bool ta, bool tb, i64 m, i64 n, i64 k, float alph
             else tc::k_pack<float, false, 1><<<gb, 256, 0, c.s>>>((int)n, (int)k, B, ldb, (float *)Bp, (int)np, (int)kp, 0);
         }
     }
+    const int nkb = (int)(kp / (tc::KB / esz));
+    const int tiles_m = (int)(mp / tc::BM), tiles_n = (int)(np / tc::BN);
+    const int tiles_total = tiles_m * tiles_n;
+    // row-tile pairs on clusters of two when there are pairs to share B and
+    // enough of them to fill the GPU
+    const int pairs = ((tiles_m + 1) / 2) * tiles_n;
+    const int CLn = (g_params.tc_pairs && tiles_m >= 2 && 2 * pairs >= c.num_sms && tc_pairs_ok()) ? 2 : 1;
     CUtensorMap a0, a1, b0, b1;
-    bool ok = make_map(&a0, Ap, f16, (int)mp, (int)kp, tc::BM) && make_map(&b0, Bp, f16, (int)np, (int)kp, tc::BN);
+    bool ok = make_map(&a0, Ap, f16, (int)mp, (int)kp, tc::BM) &&
+              make_map(&b0, Bp, f16, (int)np, (int)kp, tc::BN / CLn);
     if (split == 2)
         ok = ok && make_map(&a1, Ap + (size_t)aplane * esz, f16, (int)mp, (int)kp, tc::BM) &&
-             make_map(&b1, Bp + (size_t)bplane * esz, f16, (int)np, (int)kp, tc::BN);
+             make_map(&b1, Bp + (size_t)bplane * esz, f16, (int)np, (int)kp, tc::BN / CLn);
     else {
         a1 = a0;
         b1 = b0;
     }
     if (!ok) { note(c, cudaErrorInvalidValue); return true; }
-    const int nkb = (int)(kp / (tc::KB / esz));
-    const int tiles_m = (int)(mp / tc::BM), tiles_n = (int)(np / tc::BN);
-    // persistent CTAs (one per SM) walk the tile list; lower-triangle updates
+    // persistent CTAs (one per SM) walk the work list; lower-triangle updates
     // skip the tiles above the diagonal and mask the diagonal ones
-    const int tiles_total = tiles_m * tiles_n;
-    const unsigned grid = (unsigned)(tiles_total < c.num_sms ? tiles_total : c.num_sms);
+    unsigned grid;
+    if (CLn == 1) grid = (unsigned)(tiles_total < c.num_sms ? tiles_total : c.num_sms);
+    else grid = 2u * (unsigned)(pairs < c.num_sms / 2 ? pairs : c.num_sms / 2);
     const double flops = lower ? (double)k * n * (n + 1) : 2.0 * m * n * k;
     Launch L(c, lower ? K_SYRK : K_GEMM, flops, 0.0);
     cudaError_t e;
     const long long lim = g_params.spin_ns;
-#define RL_TC(FMT, NS, ST)                                                                              \
-    (lower ? launch_tc<FMT, NS, ST, true>(a0, a1, b0, b1, (int)m, (int)n, nkb, alpha, C, ldc, tiles_m,   \
-                                          tiles_total, grid, c.info, lim, c.abort, c.s)               \
-           : launch_tc<FMT, NS, ST, false>(a0, a1, b0, b1, (int)m, (int)n, nkb, alpha, C, ldc, tiles_m,  \
-                                           tiles_total, grid, c.info, lim, c.abort, c.s))
+#define RL_TC1(FMT, NS, ST, CLX)                                                                        \
+    (lower ? launch_tc<FMT, NS, ST, true, CLX>(a0, a1, b0, b1, (int)m, (int)n, nkb, alpha, C, ldc, tiles_m, \
+                                               tiles_total, grid, c.info, lim, c.abort, c.s)           \
+           : launch_tc<FMT, NS, ST, false, CLX>(a0, a1, b0, b1, (int)m, (int)n, nkb, alpha, C, ldc,      \
+                                                tiles_m, tiles_total, grid, c.info, lim, c.abort, c.s))
+#define RL_TC(FMT, NS, ST) (CLn == 2 ? RL_TC1(FMT, NS, ST, 2) : RL_TC1(FMT, NS, ST, 1))
     if (prec == RL_PREC_FP16S) e = RL_TC(0, 1, 4);
     else if (prec == RL_PREC_BF16) e = RL_TC(1, 1, 4);
     else if (split == 2) e = RL_TC(2, 2, 2);
     else e = RL_TC(2, 1, 4);
 #undef RL_TC
+#undef RL_TC1
     note(c, e);
     return true;
 }

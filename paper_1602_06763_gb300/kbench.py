@@ -47,6 +47,7 @@ def main():
     ap.add_argument("--uplo", default="L", help="potrf / trtri / lauum / zpotrf: triangle")
     ap.add_argument("--flow", type=int, default=1, help="getrs/potrs: 1 = one-launch flow solve, 0 = recursive")
     ap.add_argument("--panel-cluster", type=int, default=-1, help="RL_PARAM_PANEL_CLUSTER value (0 or 1)")
+    ap.add_argument("--tc-pairs", type=int, default=-1, help="RL_PARAM_TC_PAIRS value (0 or 1)")
     ap.add_argument("--graph", action="store_true",
                     help="time replays of the call captured once into a CUDA graph (after an eager warm-up)")
     a = ap.parse_args()
@@ -55,6 +56,8 @@ def main():
         r.check(r.rl_set_param(r.RL_PARAM_GETRF_PANEL, a.nb))
     if a.panel_cluster >= 0:
         r.check(r.rl_set_param(r.RL_PARAM_PANEL_CLUSTER, a.panel_cluster))
+    if a.tc_pairs >= 0:
+        r.check(r.rl_set_param(r.RL_PARAM_TC_PAIRS, a.tc_pairs))
     if a.oz_min:
         r.check(r.rl_set_param(r.RL_PARAM_OZ_MIN, a.oz_min))
     if a.panel_ctas:

@@ -155,6 +155,7 @@ RL_PARAM_OZ_MIN = 9
 RL_PARAM_NVTX = 10
 RL_PARAM_GMRES_RESTART = 11
 RL_PARAM_PANEL_CLUSTER = 12
+RL_PARAM_TC_PAIRS = 13
 
 
 def _ptr(x):
