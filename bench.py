@@ -286,13 +286,15 @@ def run_reference(args, rank):
 PRECS = {"fp32": 0, "tf32": 1, "bf16": 2, "fp16s": 3, "tf32x3": 4}
 
 
-def mixed_section(n, nrhs, cond, precs, dev, sp, reps=2, gmres_budget=300):
+def mixed_section(n, nrhs, cond, precs, dev, sp, reps=2, gmres_budget=300, oz_precs=()):
     """Solve A X = B (A = U diag(sigma) V^T or Q diag(sigma) Q^T, sigma
     log-spaced 1..cond, 64 Householder reflectors each side; B iid N(0,1))
     with the FP64 path (getrf+getrs / potrf+potrs) and with rl_dsgesv /
     rl_dsposv in each precision, with the classic refinement and with the
     GMRES refinement ("<prec>+gmres", budget gmres_budget GMRES iterations,
-    one timed run after the classic runs of the same precision); reports
+    one timed run after the classic runs of the same precision) and, for the
+    precisions in oz_precs, the classic refinement with its FP64 products
+    emulated on the BF16 tensor cores ("<prec>+oz"); reports
     time, the normwise backward error of the returned X (computed in FP64),
     refinement iterations (GMRES iterations for "+gmres"; negative: the FP64
     fallback ran), and the speedup over the FP64 path."""
@@ -344,6 +346,7 @@ def mixed_section(n, nrhs, cond, precs, dev, sp, reps=2, gmres_budget=300):
         variants = [(name, PRECS[name], 30, reps) for name in precs]
         if gmres_budget > 0:
             variants += [(name + "+gmres", PRECS[name] | r.RL_REFINE_GMRES, gmres_budget, 1) for name in precs]
+        variants += [(name + "+oz", PRECS[name] | r.RL_REFINE_OZRES, 30, reps) for name in oz_precs]
         for name, prec, maxit, nrep in variants:
             lwm = (r.rl_dsposv_work_size if spd else r.rl_dsgesv_work_size)(n, nrhs, prec)
             wm = torch.empty(lwm, dtype=torch.uint8, device=dev)
@@ -1121,7 +1124,8 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.empty_cache()
     mixed = section("mixed_solve", lambda: mixed_section(
         args.mixed_n, args.mixed_nrhs, args.mixed_cond, [p for p in args.mixed_precs.split(",") if p], dev, sp,
-        gmres_budget=args.gmres_budget)) if args.mixed_n > 0 else None
+        gmres_budget=args.gmres_budget, oz_precs=[p for p in args.mixed_oz.split(",") if p])) \
+        if args.mixed_n > 0 else None
     torch.cuda.empty_cache()
     mixed_large = section("mixed_solve_large", lambda: mixed_section(
         args.mixed4_n, args.mixed4_nrhs, args.mixed4_cond, [p for p in args.mixed4_precs.split(",") if p], dev,
@@ -1208,6 +1212,8 @@ def main():
     ap.add_argument("--mixed-nrhs", type=int, default=16)
     ap.add_argument("--mixed-cond", type=float, default=1e6)
     ap.add_argument("--mixed-precs", default="fp32,tf32x3,tf32,bf16,fp16s")
+    ap.add_argument("--mixed-oz", default="fp32,tf32x3",
+                    help="precisions also run with emulated FP64 residual products (+oz) in the n=16384 case")
     ap.add_argument("--mixed4-n", type=int, default=32768,
                     help="order of the large precision-form case, 1 RHS (0 skips it)")
     ap.add_argument("--mixed4-nrhs", type=int, default=1)

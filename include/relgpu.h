@@ -396,12 +396,23 @@ int rl_sgetrf_tc(int prec, int64_t m, int64_t n, float *A, int64_t lda, int32_t 
  * a cycle reduces the largest backward error by less than half.  nrhs <= 64
  * with this flag; the work size depends on the flag and on the restart
  * length in force when it is queried.
+ *
+ * prec | RL_REFINE_OZRES (with either refinement; not in the paper): the
+ * FP64 products of the refinement -- the residuals b - A x and GMRES's
+ * A z -- are emulated on the BF16 tensor cores (the Ozaki scheme with 7
+ * digit planes, as rl_dgemm_oz): A's planes are made once per call (14 bytes
+ * per element of A in the workspace) and each product slices only x.  The
+ * products are exact in the digits kept: per entry the error is below
+ * 8 n 2^-58 2^(e_i + e_x) (2^e_i, 2^e_x: powers of two just above the
+ * largest |a_ik| of row i and the largest |x_k|), normwise the accuracy of
+ * an FP64 product, so the backward-error test and the corrections keep FP64
+ * accuracy; the products run at tensor-core rather than FP64-pipe rates.
  * Argument numbers (dsgesv): 1 n, 2 nrhs, 3 A, 4 lda, 5 ipiv, 6 B, 7 ldb,
  * 8 X, 9 ldx; (dsposv): 1 uplo, 2 n, 3 nrhs, 4 A, 5 lda, 6 B, 7 ldb, 8 X,
  * 9 ldx.
  * ------------------------------------------------------------------------- */
 enum { RL_PREC_FP32 = 0, RL_PREC_TF32 = 1, RL_PREC_BF16 = 2, RL_PREC_FP16S = 3, RL_PREC_TF32X3 = 4 };
-enum { RL_PREC_MASK = 0xff, RL_REFINE_GMRES = 0x100 };
+enum { RL_PREC_MASK = 0xff, RL_REFINE_GMRES = 0x100, RL_REFINE_OZRES = 0x200 };
 size_t rl_dsgesv_work_size(int64_t n, int64_t nrhs, int prec);
 size_t rl_dsposv_work_size(int64_t n, int64_t nrhs, int prec);
 int rl_dsgesv(int64_t n, int64_t nrhs, double *A, int64_t lda, int32_t *ipiv, const double *B,

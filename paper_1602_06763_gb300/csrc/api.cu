@@ -1151,7 +1151,7 @@ int rl_zpotrs(char uplo, int64_t n, int64_t nrhs, const rl_double_complex *A, in
 // a precision, optionally with the GMRES refinement flag
 static bool prec_ok(int prec)
 {
-    if ((prec & ~(RL_PREC_MASK | RL_REFINE_GMRES)) != 0) return false;
+    if ((prec & ~(RL_PREC_MASK | RL_REFINE_GMRES | RL_REFINE_OZRES)) != 0) return false;
     const int p = prec & RL_PREC_MASK;
     return p == RL_PREC_FP32 || tc_prec(p);
 }

@@ -271,6 +271,10 @@ constexpr i64 TC_MIN_MN = 128, TC_MIN_K = 64;
 
 // ---- FP64 GEMM emulated on the BF16 tensor cores (oz_gemm.cu) -------------------
 size_t oz_work_bytes(i64 m, i64 n, i64 k, int slices);
+size_t oz_planes_bytes(i64 m, i64 k, int slices);
+bool oz_prepare(Ctx &c, int slices, bool sym, i64 m, i64 k, const double *A, i64 lda, void *planes);
+bool oz_gemm_planes(Ctx &c, int slices, i64 m, i64 n, i64 k, double alpha, const void *planes, const double *B,
+                    i64 ldb, double beta, double *C, i64 ldc, void *work, size_t lwork);
 bool oz_gemm(Ctx &c, int slices, bool ta, bool tb, i64 m, i64 n, i64 k, double alpha, const double *A, i64 lda,
              const double *B, i64 ldb, double beta, double *C, i64 ldc, bool lower, void *work, size_t lwork);
 

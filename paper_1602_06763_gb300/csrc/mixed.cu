@@ -60,12 +60,14 @@ struct MixState {
 constexpr int MIX_MAX_NRHS = RES_NR * 64;
 
 struct MixLayout {
-    size_t W, panel, R, D, P, N, S, F, TC, tc_bytes, V, Z, ZC, WV, GS, total;
+    size_t W, panel, R, D, P, N, S, F, TC, tc_bytes, V, Z, ZC, WV, GS, OZP, OZW, ozw_bytes, total;
     i64 ldw, nchunks;
     int m;                 // GMRES restart length (0: classic refinement)
 };
 
 // ---- GMRES-IR state ----------------------------------------------------------
+// digit planes of the emulated residual products
+constexpr int OZ_RES_SLICES = 7;
 constexpr int GM_MAX_NRHS = 64;
 constexpr int GM_MAX_M = 64;
 // a column's cycle ends once its least-squares residual is below this
@@ -95,6 +97,7 @@ MixLayout layout(i64 n, i64 nrhs, bool lu, int prec)
 {
     MixLayout L;
     const bool gm = (prec & RL_REFINE_GMRES) != 0;
+    const bool oz = (prec & RL_REFINE_OZRES) != 0;
     prec &= RL_PREC_MASK;
     L.m = gm ? g_params.gmres_m : 0;
     L.ldw = ((n + 31) / 32) * 32;
@@ -124,6 +127,11 @@ MixLayout layout(i64 n, i64 nrhs, bool lu, int prec)
     L.ZC = off; off += gm ? al(nr * nn * sizeof(double)) : 0;
     L.WV = off; off += gm ? al(nr * nn * sizeof(double)) : 0;
     L.GS = off; off += gm ? al(sizeof(GmState)) : 0;
+    // emulated FP64 products: A's digit planes (made once) and the slicing
+    // space of the thin operand
+    L.ozw_bytes = oz ? oz_work_bytes(1, nrhs, n > 0 ? n : 1, OZ_RES_SLICES) : 0;
+    L.OZP = off; off += oz ? al(oz_planes_bytes(n > 0 ? n : 1, n > 0 ? n : 1, OZ_RES_SLICES)) : 0;
+    L.OZW = off; off += oz ? al(L.ozw_bytes) : 0;
     L.total = off;
     return L;
 }
@@ -663,6 +671,29 @@ __global__ void k_gm_slot_end(int nrhs, int m, int maxiter, const MixState *st, 
     if (all || gs->j >= m || gs->total >= maxiter) gs->open = 0;
 }
 
+// Running maxima of |r| and |x| per column after an emulated residual.
+__global__ void k_resid_stats(i64 n, int nrhs, const double *R, i64 ldr, const double *X, i64 ldx, MixState *st,
+                              const int32_t *abort)
+{
+    if (abort && *abort != 0) return;
+    const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < n;
+    for (int c = 0; c < nrhs; ++c) {
+        double ra = live ? fabs(R[(i64)c * ldr + i]) : 0.0;
+        double xa = live ? fabs(X[(i64)c * ldx + i]) : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v = __shfl_down_sync(0xffffffffu, ra, o);
+            const double w = __shfl_down_sync(0xffffffffu, xa, o);
+            if (v > ra || v != v) ra = v;
+            if (w > xa || w != w) xa = w;
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomic_max_nonneg(&st->rmax[c], ra);
+            atomic_max_nonneg(&st->xmax[c], xa);
+        }
+    }
+}
+
 unsigned grid_for(i64 total, unsigned threads)
 {
     i64 g = (total + threads - 1) / threads;
@@ -700,10 +731,34 @@ size_t mixed_work_size(i64 n, i64 nrhs, bool lu, int prec) { return layout(n, nr
 // R[:, c0..] = B - A X (FP64) for every block of RES_NR right-hand sides,
 // with the running maxima of |r| and |x| per column; or, with B null,
 // OUT = A X.
+// Emulated FP64 products of the refinement: A's digit planes (made once per
+// call) and the slicing space of the thin operand.
+struct OzRes {
+    const void *planes;
+    void *work;
+    size_t lwork;
+};
+
 static void residual_blocks(Ctx &r, bool lu, i64 n, i64 nrhs, const double *A, i64 lda, const double *X,
                             i64 ldx, const double *B, i64 ldb, double *OUT, i64 ldo, double *P, i64 nchunks,
-                            MixState *st)
+                            MixState *st, const OzRes *oz = nullptr)
 {
+    if (oz) {
+        // OUT = B - A X (one product, alpha -1 onto a copy of B) or OUT = A X,
+        // the product emulated on the BF16 tensor cores with A's planes
+        const unsigned T256 = 256;
+        if (B) {
+            Launch L(r, K_MIX, 0.0, 16.0 * n * nrhs);
+            k_copy_b<<<grid_for(n * nrhs, T256), T256, 0, r.s>>>(n, (int)nrhs, B, ldb, OUT, ldo, r.abort);
+        }
+        oz_gemm_planes(r, OZ_RES_SLICES, n, nrhs, n, B ? -1.0 : 1.0, oz->planes, X, ldx, B ? 1.0 : 0.0, OUT, ldo,
+                       oz->work, oz->lwork);
+        if (B) {
+            Launch L(r, K_RESID, 0.0, 16.0 * n * nrhs);
+            k_resid_stats<<<(unsigned)((n + 255) / 256), 256, 0, r.s>>>(n, (int)nrhs, OUT, ldo, X, ldx, st, r.abort);
+        }
+        return;
+    }
     for (i64 c0 = 0; c0 < nrhs; c0 += RES_NR) {
         const int nr = (int)((nrhs - c0) < RES_NR ? (nrhs - c0) : RES_NR);
         {
@@ -732,7 +787,7 @@ static void residual_blocks(Ctx &r, bool lu, i64 n, i64 nrhs, const double *A, i
 static void gmres_refine(Ctx &r, bool lu, i64 n, i64 nrhs, const double *A, i64 lda, const int32_t *ipiv,
                          const double *B, i64 ldb, double *X, i64 ldx, const float *W, i64 ldw, float *D,
                          i64 ldd, double *R, i64 ldr, double *P, MixState *st, void *fws, const MixLayout &Ly,
-                         double tol, int maxiter)
+                         double tol, int maxiter, const OzRes *oz)
 {
     char *w = static_cast<char *>(r.work);
     double *V = reinterpret_cast<double *>(w + Ly.V);
@@ -752,7 +807,7 @@ static void gmres_refine(Ctx &r, bool lu, i64 n, i64 nrhs, const double *A, i64 
             Launch L(ro, K_MIX, 2.0 * n * nrhs * m, (double)n * nrhs * m * sizeof(double));
             k_gm_update<<<gel, T256, 0, r.s>>>(n, nr, m, Z, X, ldx, gs);
         }
-        residual_blocks(ro, lu, n, nrhs, A, lda, X, ldx, B, ldb, R, ldr, P, Ly.nchunks, st);
+        residual_blocks(ro, lu, n, nrhs, A, lda, X, ldx, B, ldb, R, ldr, P, Ly.nchunks, st, oz);
         { Launch L(ro, K_MIX, 0.0, 0.0); k_gm_test<<<1, 256, 0, r.s>>>(nr, tol, maxiter, st, gs); }
         {
             Launch L(ro, K_MIX, 0.0, (double)n * nrhs * 16.0);
@@ -771,7 +826,7 @@ static void gmres_refine(Ctx &r, bool lu, i64 n, i64 nrhs, const double *A, i64 
             Launch L(r, K_CONVERT, 0.0, (double)n * nrhs * 20.0);
             k_gm_widen<<<gel, T256, 0, r.s>>>(n, nr, m, D, ldd, Z, ZC, st, gs);
         }
-        residual_blocks(r, lu, n, nrhs, A, lda, ZC, n, nullptr, 0, WV, n, P, Ly.nchunks, st);
+        residual_blocks(r, lu, n, nrhs, A, lda, ZC, n, nullptr, 0, WV, n, P, Ly.nchunks, st, oz);
         {
             Launch L(r, K_MIX, 4.0 * n * nrhs * m, (double)n * nrhs * m * 3 * sizeof(double));
             k_gm_arnoldi<<<nr, 1024, 0, r.s>>>(n, m, maxiter, V, WV, st, gs);
@@ -799,6 +854,7 @@ int mixed_solve(Ctx &c, bool lu, i64 n, i64 nrhs, double *A, i64 lda, int32_t *i
     int32_t *user_info = c.info;
     const unsigned T256 = 256;
     const bool gm = (prec & RL_REFINE_GMRES) != 0;
+    const bool ozr = (prec & RL_REFINE_OZRES) != 0;
     prec &= RL_PREC_MASK;
 
     if (tol <= 0.0) tol = 1e-14;
@@ -858,27 +914,22 @@ int mixed_solve(Ctx &c, bool lu, i64 n, i64 nrhs, double *A, i64 lda, int32_t *i
     }
     // the scale of the FP16 form is undone when D is widened: A_s = s A, so
     // A^{-1} r = s (A_s)^{-1} r, and D = (A_s)^{-1} (s r) is already A^{-1} r.
+    OzRes ozs{w + Ly.OZP, w + Ly.OZW, Ly.ozw_bytes};
+    const OzRes *oz = nullptr;
+    if (ozr) {
+        // A's digit planes, once, for every residual (and GMRES product)
+        Ctx o = r;
+        oz_prepare(o, OZ_RES_SLICES, !lu, n, n, A, lda, w + Ly.OZP);
+        if (o.err != cudaSuccess && c.err == cudaSuccess) c.err = o.err;
+        oz = &ozs;
+    }
     if (gm) {
         gmres_refine(r, lu, n, nrhs, A, lda, ipiv, B, ldb, X, ldx, W, ldw, D, ldd, R, ldr, P, st, fws, Ly, tol,
-                     maxiter);
+                     maxiter, oz);
         maxiter = -1;                        // the classic loop below does not run
     }
     for (int it = 0; it <= maxiter; ++it) {
-        for (i64 c0 = 0; c0 < nrhs; c0 += RES_NR) {
-            const int nr = (int)((nrhs - c0) < RES_NR ? (nrhs - c0) : RES_NR);
-            {
-                Launch L(r, K_RESID, 2.0 * n * n * nr, (double)n * n * sizeof(double));
-                const dim3 g((unsigned)((n + RES_ROWS - 1) / RES_ROWS), (unsigned)Ly.nchunks);
-                const double *Xc = X + c0 * ldx;
-                if (lu) k_resid_partial<false><<<g, RES_ROWS, 0, r.s>>>(n, nr, A, lda, Xc, ldx, P, r.abort);
-                else k_resid_partial<true><<<g, RES_ROWS, 0, r.s>>>(n, nr, A, lda, Xc, ldx, P, r.abort);
-            }
-            {
-                Launch L(r, K_RESID, (double)n * nr * Ly.nchunks, 0.0);
-                k_resid_final<<<(unsigned)((n + 255) / 256), 256, 0, r.s>>>(
-                    n, nr, (int)c0, Ly.nchunks, P, B, ldb, X, ldx, R, ldr, st, r.abort);
-            }
-        }
+        residual_blocks(r, lu, n, nrhs, A, lda, X, ldx, B, ldb, R, ldr, P, Ly.nchunks, st, oz);
         { Launch L(r, K_MIX, 0.0, 0.0); k_ir_test<<<1, 256, 0, r.s>>>((int)nrhs, it, tol, st); }
         if (it == maxiter) break;
         {

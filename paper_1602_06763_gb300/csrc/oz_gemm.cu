@@ -86,7 +86,7 @@ __device__ __forceinline__ int exp_of_max(unsigned long long b)
 // with atomicMax into mx (zeroed by the caller).  TR: op(X)(r, k) =
 // X[r ldx + k] (one warp per row); else X[k ldx + r] (one thread per row,
 // blockIdx.y a chunk of k).
-template <bool TR>
+template <bool TR, bool SYM = false>
 __global__ void k_absmax(int rows, int kdim, const double *X, i64 ldx, unsigned long long *mx)
 {
     if (TR) {
@@ -110,7 +110,9 @@ __global__ void k_absmax(int rows, int kdim, const double *X, i64 ldx, unsigned 
         const i64 k0 = (i64)blockIdx.y * kw, k1 = min((i64)kdim, k0 + kw);
         unsigned long long best = 0;
         for (i64 k = k0; k < k1; ++k) {
-            const unsigned long long v = (unsigned long long)__double_as_longlong(X[k * ldx + r]) & 0x7FFFFFFFFFFFFFFFull;
+            // SYM: X symmetric with its lower triangle stored, X(r, k) = X(k, r) above it
+            const double x = (!SYM || k <= r) ? X[k * ldx + r] : X[r * ldx + k];
+            const unsigned long long v = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
             best = v > best ? v : best;
         }
         if (k1 > k0) atomicMax(&mx[r], best);
@@ -148,7 +150,7 @@ __device__ __forceinline__ void digits_of(double x, int e, int *d)
 // Digit planes P[s][r][k] (BF16, rows_p x kp per plane, zero padded) of the
 // rows of op(X); TR as k_absmax.  32 x 32 tiles through shared memory so
 // that the reads run along X's columns and the writes along k.
-template <bool TR, int S>
+template <bool TR, int S, bool SYM = false>
 __global__ void __launch_bounds__(256)
 k_digits(int rows, int kdim, const double *X, i64 ldx, const unsigned long long *mx, __nv_bfloat16 *P,
          int rows_p, int kp)
@@ -160,9 +162,15 @@ k_digits(int rows, int kdim, const double *X, i64 ldx, const unsigned long long 
     if (threadIdx.x < 32) erow[threadIdx.x] = (r0 + (int)threadIdx.x < rows) ? exp_of_max(mx[r0 + threadIdx.x]) : 0;
     for (int yy = ty; yy < 32; yy += 8) {
         double v = 0.0;
-        if (!TR) {
+        if (!TR && SYM && k0 > r0 + 31) {
+            // a tile above the diagonal of a lower-stored symmetric X: X(r, k)
+            // = X(k, r), read along k
+            const int r = r0 + yy, k = k0 + tx;
+            if (r < rows && k < kdim) v = X[(i64)r * ldx + k];
+            tile[tx][yy] = v;                          // tile[k][r]
+        } else if (!TR) {
             const int r = r0 + tx, k = k0 + yy;
-            if (r < rows && k < kdim) v = X[(i64)k * ldx + r];
+            if (r < rows && k < kdim) v = (!SYM || k <= r) ? X[(i64)k * ldx + r] : X[(i64)r * ldx + k];
             tile[yy][tx] = v;                          // tile[k][r]
         } else {
             const int r = r0 + yy, k = k0 + tx;
@@ -447,7 +455,7 @@ static bool make_map3(CUtensorMap *map, const void *base, int rows, int kp, int 
 
 template <int S>
 static void oz_split(Ctx &c, bool tr, int rows, int kdim, const double *X, i64 ldx, unsigned long long *mx,
-                     __nv_bfloat16 *P, int rows_p, int kp)
+                     __nv_bfloat16 *P, int rows_p, int kp, bool sym = false)
 {
     {
         Launch L(c, K_CONVERT, 0.0, 8.0 * rows * kdim);
@@ -457,12 +465,14 @@ static void oz_split(Ctx &c, bool tr, int rows, int kdim, const double *X, i64 l
             // 64 values of k per thread: rows x k / 64 threads in flight
             const int kch = (kdim + 63) / 64 < 4096 ? (kdim + 63) / 64 : 4096;
             const dim3 g((unsigned)((rows + 255) / 256), (unsigned)kch);
-            oz::k_absmax<false><<<g, 256, 0, c.s>>>(rows, kdim, X, ldx, mx);
+            if (sym) oz::k_absmax<false, true><<<g, 256, 0, c.s>>>(rows, kdim, X, ldx, mx);
+            else oz::k_absmax<false><<<g, 256, 0, c.s>>>(rows, kdim, X, ldx, mx);
         }
     }
     Launch L(c, K_CONVERT, 0.0, (8.0 + 2.0 * S) * rows * kdim);
     const dim3 g((unsigned)(kp / 32), (unsigned)(rows_p / 32));
     if (tr) oz::k_digits<true, S><<<g, 256, 0, c.s>>>(rows, kdim, X, ldx, mx, P, rows_p, kp);
+    else if (sym) oz::k_digits<false, S, true><<<g, 256, 0, c.s>>>(rows, kdim, X, ldx, mx, P, rows_p, kp);
     else oz::k_digits<false, S><<<g, 256, 0, c.s>>>(rows, kdim, X, ldx, mx, P, rows_p, kp);
 }
 
@@ -533,6 +543,82 @@ bool oz_gemm(Ctx &c, int S, bool ta, bool tb, i64 m, i64 n, i64 k, double alpha,
     else if (S == 7) e = RL_OZ(7);
     else e = RL_OZ(8);
 #undef RL_OZ
+    note(c, e);
+    return true;
+}
+
+// ---- products with a matrix sliced once ----------------------------------------
+// The precision form multiplies the same A by many right-hand-side blocks:
+// its digit planes and row exponents are made once (oz_prepare) and reused
+// by every product (oz_gemm_planes), which slices only the thin operand.
+
+size_t oz_planes_bytes(i64 m, i64 k, int S)
+{
+    const i64 mp = rup_oz(m > 0 ? m : 1, oz::BM), kp = rup_oz(k > 0 ? k : 1, oz::KC);
+    return al1k((size_t)S * (size_t)mp * (size_t)kp * 2) + al1k((size_t)mp * 8) + 1024;
+}
+
+// Digit planes of the m x k matrix A (its rows); sym: A symmetric with the
+// lower triangle stored (m = k), each row read across the diagonal.
+bool oz_prepare(Ctx &c, int S, bool sym, i64 m, i64 k, const double *A, i64 lda, void *planes)
+{
+    if (S < 6 || S > 8 || m <= 0 || k <= 0 || m > (1 << 30) || k > (1 << 21) || planes == nullptr) return false;
+    const i64 mp = rup_oz(m, oz::BM), kp = rup_oz(k, oz::KC);
+    char *w = reinterpret_cast<char *>(((uintptr_t)planes + 1023) & ~(uintptr_t)1023);
+    __nv_bfloat16 *Ap = reinterpret_cast<__nv_bfloat16 *>(w);
+    unsigned long long *mxA = reinterpret_cast<unsigned long long *>(w + al1k((size_t)S * mp * kp * 2));
+    note(c, cudaMemsetAsync(mxA, 0, (size_t)mp * 8, c.s));
+    switch (S) {
+    case 6: oz_split<6>(c, false, (int)m, (int)k, A, lda, mxA, Ap, (int)mp, (int)kp, sym); break;
+    case 7: oz_split<7>(c, false, (int)m, (int)k, A, lda, mxA, Ap, (int)mp, (int)kp, sym); break;
+    default: oz_split<8>(c, false, (int)m, (int)k, A, lda, mxA, Ap, (int)mp, (int)kp, sym); break;
+    }
+    return true;
+}
+
+// C (m x n) := beta C + alpha A B with A's planes from oz_prepare (m x k) and
+// B (k x n, column-major) sliced into work (oz_work_bytes(0, n, k, S)).
+bool oz_gemm_planes(Ctx &c, int S, i64 m, i64 n, i64 k, double alpha, const void *planes, const double *B,
+                    i64 ldb, double beta, double *C, i64 ldc, void *work, size_t lwork)
+{
+    if (S < 6 || S > 8 || m <= 0 || n <= 0 || k <= 0 || m > (1 << 30) || n > (1 << 30) || k > (1 << 21))
+        return false;
+    if (work == nullptr || lwork < oz_work_bytes(1, n, k, S) || planes == nullptr) return false;
+    const i64 mp = rup_oz(m, oz::BM), np = rup_oz(n, oz::BN), kp = rup_oz(k, oz::KC);
+    const char *pa = reinterpret_cast<const char *>(((uintptr_t)planes + 1023) & ~(uintptr_t)1023);
+    const __nv_bfloat16 *Ap = reinterpret_cast<const __nv_bfloat16 *>(pa);
+    const unsigned long long *mxA =
+        reinterpret_cast<const unsigned long long *>(pa + al1k((size_t)S * mp * kp * 2));
+    char *w = reinterpret_cast<char *>(((uintptr_t)work + 1023) & ~(uintptr_t)1023);
+    __nv_bfloat16 *Bp = reinterpret_cast<__nv_bfloat16 *>(w);
+    unsigned long long *mxB = reinterpret_cast<unsigned long long *>(w + al1k((size_t)S * np * kp * 2));
+    note(c, cudaMemsetAsync(mxB, 0, (size_t)np * 8, c.s));
+    switch (S) {
+    case 6: oz_split<6>(c, true, (int)n, (int)k, B, ldb, mxB, Bp, (int)np, (int)kp); break;
+    case 7: oz_split<7>(c, true, (int)n, (int)k, B, ldb, mxB, Bp, (int)np, (int)kp); break;
+    default: oz_split<8>(c, true, (int)n, (int)k, B, ldb, mxB, Bp, (int)np, (int)kp); break;
+    }
+    CUtensorMap ma, mb;
+    if (!make_map3(&ma, Ap, (int)mp, (int)kp, S, oz::BM) || !make_map3(&mb, Bp, (int)np, (int)kp, S, oz::BN)) {
+        note(c, cudaErrorInvalidValue);
+        return true;
+    }
+    const int tiles_m = (int)(mp / oz::BM), tiles_n = (int)(np / oz::BN);
+    const int tiles_total = tiles_m * tiles_n;
+    const unsigned grid = (unsigned)(tiles_total < c.num_sms ? tiles_total : c.num_sms);
+    const int nch = (int)(kp / oz::KC);
+    Launch L(c, K_RESID, 2.0 * m * n * k, 2.0 * S * (double)m * k);
+    const long long lim = g_params.spin_ns;
+    cudaError_t e;
+    if (S == 6)
+        e = launch_oz<6, false>(ma, mb, (int)m, (int)n, nch, alpha, beta, C, ldc, mxA, mxB, tiles_m, tiles_n, grid,
+                                c.info, lim, c.abort, c.s);
+    else if (S == 7)
+        e = launch_oz<7, false>(ma, mb, (int)m, (int)n, nch, alpha, beta, C, ldc, mxA, mxB, tiles_m, tiles_n, grid,
+                                c.info, lim, c.abort, c.s);
+    else
+        e = launch_oz<8, false>(ma, mb, (int)m, (int)n, nch, alpha, beta, C, ldc, mxA, mxB, tiles_m, tiles_n, grid,
+                                c.info, lim, c.abort, c.s);
     note(c, e);
     return true;
 }

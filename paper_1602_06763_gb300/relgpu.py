@@ -142,6 +142,7 @@ RL_PREC_FP16S = 3
 RL_PREC_TF32X3 = 4
 RL_PREC_MASK = 0xFF
 RL_REFINE_GMRES = 0x100
+RL_REFINE_OZRES = 0x200
 
 RL_PARAM_POTRF_CROSSOVER = 1
 RL_PARAM_GETRF_PANEL = 2

@@ -179,7 +179,11 @@ def test_host_logic_of_the_gmres_refinement(built):
         # the basis V (m + 1 vectors) and Z (m vectors) per right-hand side, FP64
         assert gm - base >= nrhs * (2 * m + 1) * n * 8
         assert r.rl_dsposv_work_size(n, nrhs, prec | g) > r.rl_dsposv_work_size(n, nrhs, prec)
-    assert r.rl_dsgesv_work_size(n, nrhs, 0x200) == 0                # unknown flag bits
+    assert r.rl_dsgesv_work_size(n, nrhs, 0x400) == 0                # unknown flag bits
+    # emulated residual products: A's digit planes (7 x 2 bytes per element) in the workspace
+    oz = r.rl_dsgesv_work_size(n, nrhs, r.RL_REFINE_OZRES) - r.rl_dsgesv_work_size(n, nrhs, 0)
+    assert oz >= 14 * n * n
+    assert r.rl_dsposv_work_size(n, nrhs, r.RL_REFINE_OZRES | g) > r.rl_dsposv_work_size(n, nrhs, g)
     assert r.rl_dsgesv_work_size(n, nrhs, 7 | g) == 0                # unknown precision
     # the restart length sizes the workspace and is range-checked
     assert r.rl_get_param(r.RL_PARAM_GMRES_RESTART) == 50
