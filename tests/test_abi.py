@@ -198,3 +198,13 @@ def test_host_logic_of_the_gmres_refinement(built):
     assert r.rl_dsgesv(n, 65, 8, n, 8, 8, n, 8, n, g, 1e-14, 30, 8, 8, 8, 1 << 40, 0) == r.RL_ERR_UNSUPPORTED
     assert r.rl_dsposv("L", n, 65, 8, n, 8, n, 8, n, g, 1e-14, 30, 8, 8, 8, 1 << 40, 0) == r.RL_ERR_UNSUPPORTED
     assert r.rl_dsgesv(n, 65, 8, n, 8, 8, n, 8, n, 0, 1e-14, 30, 8, 8, None, 0, 0) == r.RL_ERR_WORKSPACE
+
+
+def test_host_logic_of_the_cluster_parameters(built):
+    from paper_1602_06763_gb300 import relgpu as r
+    for key in (r.RL_PARAM_PANEL_CLUSTER, r.RL_PARAM_TC_PAIRS):
+        assert r.rl_get_param(key) == 1                  # on by default
+        assert r.rl_set_param(key, 0) == 0 and r.rl_get_param(key) == 0
+        assert r.rl_set_param(key, 2) == r.RL_ERR_PARAM
+        assert r.rl_set_param(key, -1) == r.RL_ERR_PARAM
+        assert r.rl_set_param(key, 1) == 0 and r.rl_get_param(key) == 1
