@@ -32,6 +32,7 @@
 #include <mutex>
 #include <cooperative_groups.h>
 #include "internal.cuh"
+#include "tc_common.cuh"
 
 namespace rl {
 
@@ -666,42 +667,150 @@ k_panel_smem(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info,
 }
 
 // Cluster panel: the same algorithm on one thread-block cluster of CL CTAs
-// (CL = 2, 4, 8 or 16) with the panel held in registers: thread t of CTA q
-// keeps rows q R + t + k TH (k < RPT, R = RPT TH, TH threads per CTA), all
-// PCL_NB columns of each, and every column index is a compile-time constant
-// (the column loop is unrolled), so the update never touches shared memory.
+// (CL = 2, 4, 8 or 16), FP32 storage.  Thread t of CTA q owns rows
+// q R + t + k TH (k < RPT, R = RPT TH, TH threads per CTA).  The columns not
+// yet finished live in registers as a window that shifts by one column per
+// step: before step j, register column c holds column j + c, so the current
+// column is always register 0, every register index is a compile-time
+// constant and the column loop stays rolled (a body the instruction cache
+// holds).  A finished column goes straight to A.
 // Per column: each warp reduces its candidate, one block barrier, every
-// thread picks the CTA's candidate from the warp records, the owner thread
-// publishes the candidate's row and rank 0's owner of row j that row; one
-// cluster barrier (hardware, not a spin) makes the records visible; each
-// warp reads the CL candidates and the two rows through distributed shared
-// memory (lane c reads column c) and shares them by shuffles; the owners of
-// rows j and p swap, and every thread divides and updates its own rows.
-// The records are double-buffered: a CTA writes buffer j & 1 only after the
-// cluster barrier of column j - 1, which every CTA reaches after its reads
-// of column j - 2.  Same arithmetic per element as k_panel (bit-identical).
+// thread picks the CTA's candidate from the warp records, and the owner's
+// warp pushes the record {key, row, the row's window} into every CTA of the
+// cluster with st.async, which completes bytes on the receiver's mbarrier
+// (rank 0 pushes row j the same way).  A CTA waits on its own mbarrier only:
+// no cluster barrier and no remote read per column.  Each warp then picks the
+// winner from the CL local records, the owners of rows j and p swap their
+// windows, and every thread divides and updates its rows.  The interchange of
+// the finished columns of rows j and p is deferred: after the last column,
+// rank 0 applies the interchanges of the steps after each column to that
+// column's entries, which yields the same matrix as interchanging whole rows
+// at every step.  Same arithmetic per element as k_panel (bit-identical).
+// Records and mbarriers are double-buffered by column parity: a CTA pushes
+// column j only after it received every CTA's record of column j - 1, which
+// each CTA sends after its block barrier of column j - 1, after its reads of
+// the buffer of column j - 2.  All waits are bounded (RL_INFO_DEVICE_TIMEOUT).
 constexpr int PCL_NB = 32;
 
-template <typename T, int CL, int RPT, int TH>
+struct alignas(16) PclRec {
+    uint32_t key;                                 // pcl_key of the candidate
+    int row;
+    int pad[2];
+    float v[PCL_NB];                              // the row's window: columns j .. j + 31
+};
+static_assert(sizeof(PclRec) == 144, "record of 9 16-byte chunks");
+
+// Pivot key of an FP32 entry: the bits of |v| (ordered like |v|), NaN 0 --
+// the same order as abs_key on the exact double of v, in 32 bits.
+__device__ __forceinline__ uint32_t pcl_key(float v)
+{
+    const uint32_t b = __float_as_uint(v) & 0x7fffffffu;
+    return b > 0x7f800000u ? 0u : b;
+}
+
+// Largest key, lowest row among equal keys, over the warp (the order of
+// kbetter); every lane gets the result.  No candidate: key 0, PANEL_NONE.
+__device__ __forceinline__ void pcl_warp_best(uint32_t &key, int &row)
+{
+    const uint32_t kmax = __reduce_max_sync(0xffffffffu, key);
+    row = (int)__reduce_min_sync(0xffffffffu, key == kmax ? (uint32_t)row : 0xffffffffu);
+    key = kmax;
+}
+
+__device__ __forceinline__ uint32_t pcl_mapa(const void *p, int rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(tc::su32(p)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void pcl_push16(uint32_t raddr, uint4 v, uint32_t rbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
+                 ::"r"(raddr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(rbar) : "memory");
+}
+
+__device__ __forceinline__ bool pcl_try(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(tc::su32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait of a whole warp on a local mbarrier phase; the result is the
+// same in every lane.
+__device__ __forceinline__ bool pcl_wait(uint64_t *bar, uint32_t parity, long long limit_ns)
+{
+    if (__all_sync(0xffffffffu, pcl_try(bar, parity))) return true;
+    const unsigned long long t0 = tc::gtime();
+    for (;;) {
+        if (__all_sync(0xffffffffu, pcl_try(bar, parity))) return true;
+        if (__any_sync(0xffffffffu, (long long)(tc::gtime() - t0) >= limit_ns)) return false;
+    }
+}
+
+// The warp pushes the NCH 16-byte chunks at src (a slot of this CTA's
+// shared memory) into the same slot of every other CTA of the cluster,
+// completing bytes on each one's bar.  (Its own CTA's copy is written with
+// plain stores and announced by an ordinary arrive.)
+template <int CL, int NCH>
+__device__ __forceinline__ void pcl_push_peers(const void *src, uint64_t *bar, int q, int lane)
+{
+    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    for (int it = lane; it < (CL - 1) * NCH; it += 32) {
+        const int rr = it / NCH, ch = it % NCH;
+        const int r = rr + (rr >= q ? 1 : 0);
+        pcl_push16(pcl_mapa(src, r) + 16u * (uint32_t)ch, s[ch], pcl_mapa(bar, r));
+    }
+}
+
+__device__ __forceinline__ void pcl_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::su32(bar)) : "memory");
+}
+
+template <int CL, int RPT, int TH>
 __global__ void __launch_bounds__(TH)
-k_panel_cluster(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, const int32_t *abort)
+k_panel_cluster(i64 m, int nb, float *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *info, long long spin_ns,
+                const int32_t *abort)
 {
     namespace cg = cooperative_groups;
+    using T = float;
     cg::cluster_group cl = cg::this_cluster();
     constexpr int R = RPT * TH;
     constexpr int NW = TH / 32;
-    __shared__ unsigned long long ckey[2];
-    __shared__ int crow[2];
-    __shared__ T crowv[2][PCL_NB];                // this CTA's candidate row
-    __shared__ T rowjv[2][PCL_NB];                // row j (rank 0 only)
-    __shared__ unsigned long long wk[2][NW];
+    static_assert(NW <= 32 && PCL_NB <= TH, "one warp reduces the warp records; row j < TH");
+    __shared__ PclRec recs[2][CL];                // slot r: rank r's candidate of the column
+    __shared__ alignas(16) T rowj[2][PCL_NB];     // row j's window (pushed by rank 0)
+    __shared__ alignas(8) uint64_t bar[2];
+    __shared__ uint32_t wk[2][NW];
     __shared__ int wi[2][NW];
-    __shared__ int s_skip;
+    __shared__ int s_p[PCL_NB];                   // p_j (rank 0, for the deferred interchanges)
+    __shared__ int s_slot[PCL_NB];                // fix-up slot of row p_j
+    __shared__ int s_row[2 * PCL_NB];             // fix-up slot -> row (-1: unused)
+    __shared__ T fix[2 * PCL_NB][PCL_NB + 1];
+    __shared__ int s_skip, s_tmo;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int q = (int)cl.block_rank();
+    // per column: the bytes of the other CTAs' records (and of row j) arrive
+    // on bar; the arrivals are tid 0's expect_tx, the local record's and (rank
+    // 0) the local row j's
+    const uint32_t TX = (CL - 1) * (uint32_t)sizeof(PclRec) + (q != 0 ? PCL_NB * (uint32_t)sizeof(T) : 0u);
+    if (tid == 0) {
+        tc::mbar_init(&bar[0], q == 0 ? 3 : 2);
+        tc::mbar_init(&bar[1], q == 0 ? 3 : 2);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_tmo = 0;
+    }
     if (q == 0 && tid == 0) s_skip = (abort && *abort != 0) ? 1 : 0;
-    cl.sync();
+    cl.sync();                                    // mbarriers initialised cluster-wide
     if (*cl.map_shared_rank(&s_skip, 0)) {
         cl.sync();                                // rank 0's word is read before it exits
         return;
@@ -717,116 +826,185 @@ k_panel_cluster(i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0, int32_t *in
             a[k][c] = (gi[k] < m && c < nb) ? A[(i64)c * lda + gi[k]] : T(0);
     }
     const int mn = (int)min(m, (i64)nb);
-    // the column loop is unrolled: every register column is addressed by a
-    // compile-time index
-#pragma unroll
-    for (int j = 0; j < PCL_NB; ++j) {
-        if (j < mn) {
-        const int buf = j & 1;
-        // 1. the warp's candidate: largest |a_ij| over rows i >= j, lowest i on ties
-        unsigned long long bk = 0;
+    int tmo = 0;
+    int j = 0;
+#pragma unroll 1
+    for (; j < mn; ++j) {
+        const int b = j & 1;
+        if (tid == 0) tc::mbar_expect_tx(&bar[b], TX);
+        // 1. the warp's candidate: largest |a_ij| over rows i >= j, lowest i
+        // on ties (a thread's rows ascend with k)
+        uint32_t bk = 0;
         int bi = PANEL_NONE;
 #pragma unroll
         for (int k = 0; k < RPT; ++k)
             if (gi[k] < m && gi[k] >= j) {
-                const unsigned long long key = abs_key(a[k][j]);
-                if (kbetter(key, (int)gi[k], bk, bi)) { bk = key; bi = (int)gi[k]; }
+                const uint32_t key = pcl_key(a[k][0]);
+                if (key > bk || bi == PANEL_NONE) { bk = key; bi = (int)gi[k]; }
             }
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (kbetter(ok, oi, bk, bi)) { bk = ok; bi = oi; }
-        }
-        if (lane == 0) { wk[buf][warp] = bk; wi[buf][warp] = bi; }
-        __syncthreads();
-        // 2. the CTA's candidate (every thread reduces the warp records the same way)
-        bk = wk[buf][0];
-        bi = wi[buf][0];
+        pcl_warp_best(bk, bi);
+        if (lane == 0) { wk[b][warp] = bk; wi[b][warp] = bi; }
+        if (__syncthreads_or(tmo)) break;         // a warp ran out of its wait: every thread leaves
+        // 2. the CTA's candidate (every warp reduces the warp records); the
+        // owner's warp pushes its record, rank 0's warp 0 row j
+        bk = lane < NW ? wk[b][lane] : 0u;
+        bi = lane < NW ? wi[b][lane] : PANEL_NONE;
+        pcl_warp_best(bk, bi);
+        const int lr = bi != PANEL_NONE ? (int)(bi - rbeg) : 0;   // owner: thread lr % TH, window lr / TH
+        if (warp == (lr % TH) >> 5) {
+            PclRec &mine = recs[b][q];
+            if (lane == 0) { mine.key = bk; mine.row = bi; }
+            if (bi != PANEL_NONE && lane == (lr & 31)) {
+                const int kk = lr / TH;
 #pragma unroll
-        for (int w = 1; w < NW; ++w)
-            if (kbetter(wk[buf][w], wi[buf][w], bk, bi)) { bk = wk[buf][w]; bi = wi[buf][w]; }
-        if (tid == 0) { ckey[buf] = bk; crow[buf] = bi; }
+                for (int k = 0; k < RPT; ++k)
+                    if (k == kk) {
+#pragma unroll
+                        for (int c4 = 0; c4 < PCL_NB / 4; ++c4)
+                            reinterpret_cast<float4 *>(mine.v)[c4] =
+                                make_float4(a[k][4 * c4], a[k][4 * c4 + 1], a[k][4 * c4 + 2], a[k][4 * c4 + 3]);
+                    }
+            }
+            __syncwarp();
+            pcl_push_peers<CL, 9>(&mine, &bar[b], q, lane);
+            if (lane == 0) pcl_arrive(&bar[b]);
+        }
+        if (q == 0 && warp == 0) {
+            if (lane == j) {
+#pragma unroll
+                for (int c4 = 0; c4 < PCL_NB / 4; ++c4)
+                    reinterpret_cast<float4 *>(rowj[b])[c4] =
+                        make_float4(a[0][4 * c4], a[0][4 * c4 + 1], a[0][4 * c4 + 2], a[0][4 * c4 + 3]);
+            }
+            __syncwarp();
+            pcl_push_peers<CL, 8>(rowj[b], &bar[b], q, lane);
+            if (lane == 0) pcl_arrive(&bar[b]);
+        }
+        // 3. the winner over the cluster (every warp, from the local records;
+        // row p sits in rank p / R)
+        if (!pcl_wait(&bar[b], (uint32_t)(j >> 1) & 1u, spin_ns)) { tmo = 1; continue; }
+        uint32_t k2 = recs[b][lane % CL].key;
+        int ix = recs[b][lane % CL].row;
+        pcl_warp_best(k2, ix);
+        const int p = ix != PANEL_NONE ? ix : j;
+        const T *urow = ix != PANEL_NONE ? recs[b][ix / R].v : rowj[b];   // the pivot row, columns j ..
+        if (q == 0 && tid == 0) {
+            ipiv[r0 + j] = (int32_t)(r0 + p + 1);
+            s_p[j] = p;
+        }
+        const T piv = urow[0];
+        // 4. swap the windows of rows j and p: their two owner threads load
+        // the other row from the records
+        if (p != j) {
+            if (q == 0 && tid == j) {
+#pragma unroll
+                for (int c4 = 0; c4 < PCL_NB / 4; ++c4) {
+                    const float4 v = reinterpret_cast<const float4 *>(urow)[c4];
+                    a[0][4 * c4] = v.x; a[0][4 * c4 + 1] = v.y; a[0][4 * c4 + 2] = v.z; a[0][4 * c4 + 3] = v.w;
+                }
+            }
+            const int lp = p - q * R;
+            if (lp >= 0 && lp < R && tid == lp % TH) {
+                const int kp = lp / TH;
+#pragma unroll
+                for (int k = 0; k < RPT; ++k)
+                    if (k == kp) {
+#pragma unroll
+                        for (int c4 = 0; c4 < PCL_NB / 4; ++c4) {
+                            const float4 v = reinterpret_cast<const float4 *>(rowj[b])[c4];
+                            a[k][4 * c4] = v.x; a[k][4 * c4 + 1] = v.y; a[k][4 * c4 + 2] = v.z; a[k][4 * c4 + 3] = v.w;
+                        }
+                    }
+            }
+        }
+        // 5. divide column j and store it, update the rest while the window
+        // shifts by one (register c - 1 receives column j + c); blocks of four
+        // columns past nb are skipped (j and nb are uniform), the entries past
+        // nb inside a block are never stored
+        const bool dov = piv != T(0);
+        bool below[RPT];
+        T l[RPT];
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
-            if (bi != PANEL_NONE && gi[k] == bi) {
-#pragma unroll
-                for (int c = 0; c < PCL_NB; ++c) crowv[buf][c] = a[k][c];
-            }
-            if (gi[k] == j) {
-#pragma unroll
-                for (int c = 0; c < PCL_NB; ++c) rowjv[buf][c] = a[k][c];
-            }
+            below[k] = dov && gi[k] < m && gi[k] > j;
+            l[k] = below[k] ? a[k][0] / piv : T(0);
+            if (below[k]) a[k][0] = l[k];
+            if (gi[k] < m) A[(i64)j * lda + gi[k]] = a[k][0];
         }
-        cl.sync();
-        // 3. the winner over the cluster (every warp), the pivot row and row j
-        unsigned long long k2 = 0;
-        int ix = PANEL_NONE, gw = -1;
-        if (lane < CL) {
-            const int qi = *cl.map_shared_rank(&crow[buf], lane);
-            if (qi != PANEL_NONE) { k2 = *cl.map_shared_rank(&ckey[buf], lane); ix = qi; gw = lane; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, k2, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
-            const int og = __shfl_xor_sync(0xffffffffu, gw, o);
-            if (og >= 0 && (gw < 0 || kbetter(ok, oi, k2, ix))) { k2 = ok; ix = oi; gw = og; }
-        }
-        const int p = (gw >= 0) ? ix : j;
-        // row j sits in rank 0 (j < nb <= R); lane c holds column c of each row
-        const T rjl = *cl.map_shared_rank(&rowjv[buf][lane], 0);
-        const T upl = gw >= 0 ? *cl.map_shared_rank(&crowv[buf][lane], gw) : rjl;
-        if (q == 0 && tid == 0) ipiv[r0 + j] = (int32_t)(r0 + p + 1);
-        const T piv = __shfl_sync(0xffffffffu, upl, j);
-        // 4. swap (the owners of rows j and p), divide, update; every lane
-        // takes part in every shuffle, only the owners keep the values
-        if (p != j) {
 #pragma unroll
-            for (int c = 0; c < PCL_NB; ++c) {
-                const T vu = __shfl_sync(0xffffffffu, upl, c);
-                const T vj = __shfl_sync(0xffffffffu, rjl, c);
+        for (int c4 = 0; c4 < PCL_NB / 4; ++c4) {
+            if (j + 4 * c4 < nb) {
+                const float4 u4 = reinterpret_cast<const float4 *>(urow)[c4];
+                const T u[4] = {u4.x, u4.y, u4.z, u4.w};
 #pragma unroll
-                for (int k = 0; k < RPT; ++k) {
-                    if (gi[k] == j) a[k][c] = vu;
-                    else if (gi[k] == p) a[k][c] = vj;
+                for (int e = (c4 == 0 ? 1 : 0); e < 4; ++e) {
+                    const int c = 4 * c4 + e;
+#pragma unroll
+                    for (int k = 0; k < RPT; ++k)
+                        a[k][c - 1] = below[k] ? fma(-l[k], u[e], a[k][c]) : a[k][c];
                 }
             }
         }
-        if (piv != T(0)) {
-            T l[RPT];
+        if (!dov && q == 0 && tid == 0 && *info == 0) *info = (int32_t)(r0 + j + 1);
+    }
+    if (tmo) {
+        s_tmo = 1;
+        if (lane == 0) atomicExch(info, RL_INFO_DEVICE_TIMEOUT);
+    }
+    // the columns past min(m, nb) (wide panels) from the window
+    if (j == mn) {
 #pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                const bool below = gi[k] < m && gi[k] > j;
-                l[k] = below ? a[k][j] / piv : T(0);
-                if (below) a[k][j] = l[k];
+        for (int k = 0; k < RPT; ++k)
+            if (gi[k] < m) {
+#pragma unroll
+                for (int c = 0; c < PCL_NB; ++c)
+                    if (mn + c < nb) A[(i64)(mn + c) * lda + gi[k]] = a[k][c];
             }
-#pragma unroll
-            for (int c = j + 1; c < PCL_NB; ++c) {
-                const T u = __shfl_sync(0xffffffffu, upl, c);
-#pragma unroll
-                for (int k = 0; k < RPT; ++k)
-                    if (gi[k] < m && gi[k] > j) a[k][c] = fma(-l[k], u, a[k][c]);
+    }
+    cl.sync();                                    // every finished column is in A; no record is in flight
+    if (q != 0 || s_tmo) return;
+    // deferred interchanges of the finished columns: column c takes those of
+    // the steps after c.  Rows 0 .. mn-1 are slots 0 .. mn-1, a row p_t >= mn
+    // slot PCL_NB + (first step with that row); gather, interchange, scatter.
+    if (warp == 0) {
+        s_row[lane] = lane < mn ? lane : -1;
+        const int pt = lane < mn ? s_p[lane] : -1 - lane;
+        const int first = __ffs(__match_any_sync(0xffffffffu, pt)) - 1;
+        s_row[PCL_NB + lane] = (lane < mn && pt >= mn && first == lane) ? pt : -1;
+        if (lane < mn) s_slot[lane] = pt < mn ? pt : PCL_NB + first;
+    }
+    __syncthreads();
+    for (int e = tid; e < 2 * PCL_NB * PCL_NB; e += TH) {
+        const int sl = e / PCL_NB, c = e % PCL_NB;
+        const int r = s_row[sl];
+        if (r >= 0 && c < mn) fix[sl][c] = __ldcg(&A[(i64)c * lda + r]);
+    }
+    __syncthreads();
+    if (tid < mn) {
+        const int c = tid;
+        for (int t = c + 1; t < mn; ++t) {
+            const int sp = s_slot[t];
+            if (sp != t) {
+                const T x = fix[t][c];
+                fix[t][c] = fix[sp][c];
+                fix[sp][c] = x;
             }
-        } else if (q == 0 && tid == 0 && *info == 0) {
-            *info = (int32_t)(r0 + j + 1);
-        }
         }
     }
-#pragma unroll
-    for (int k = 0; k < RPT; ++k)
-        if (gi[k] < m) {
-#pragma unroll
-            for (int c = 0; c < PCL_NB; ++c)
-                if (c < nb) A[(i64)c * lda + gi[k]] = a[k][c];
-        }
-    cl.sync();                                    // no CTA leaves while others may read its records
+    __syncthreads();
+    for (int e = tid; e < 2 * PCL_NB * PCL_NB; e += TH) {
+        const int sl = e / PCL_NB, c = e % PCL_NB;
+        const int r = s_row[sl];
+        if (r > c && c < mn) A[(i64)c * lda + r] = fix[sl][c];
+    }
 }
 
 // Launch of the cluster panel with CL CTAs; false if this device cannot
 // place such a cluster (the caller then takes the cooperative kernel).
-template <typename T, int CL, int RPT, int TH>
-static bool launch_panel_cluster(Ctx &c, i64 m, int nb, T *A, i64 lda, int32_t *ipiv, i64 r0)
+template <int CL, int RPT, int TH>
+static bool launch_panel_cluster(Ctx &c, i64 m, int nb, float *A, i64 lda, int32_t *ipiv, i64 r0)
 {
-    auto kern = k_panel_cluster<T, CL, RPT, TH>;
+    auto kern = k_panel_cluster<CL, RPT, TH>;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CL);
     cfg.blockDim = dim3(TH);
@@ -860,12 +1038,13 @@ static bool launch_panel_cluster(Ctx &c, i64 m, int nb, T *A, i64 lda, int32_t *
     }
     int32_t *info = c.info;
     const int32_t *abort = c.abort;
-    note(c, cudaLaunchKernelEx(&cfg, kern, m, nb, A, lda, ipiv, r0, info, abort));
+    long long spin = g_params.spin_ns;
+    note(c, cudaLaunchKernelEx(&cfg, kern, m, nb, A, lda, ipiv, r0, info, spin, abort));
     return true;
 }
 
-// The register-resident cluster panel serves FP32 panels: 256 threads per
-// CTA, four rows of 32 floats per thread.  (FP64 panels measured slower on it
+// The cluster panel serves FP32 panels: 256 threads per CTA, a window of four
+// rows of 32 floats per thread.  (FP64 panels measured slower on it
 // than on the cooperative kernel and keep that one.)
 constexpr int PCL_TH = 256;
 
@@ -879,10 +1058,10 @@ static bool panel_cluster(Ctx &c, i64 m, i64 nb, T *A, i64 lda, int32_t *ipiv, i
     constexpr i64 R = (i64)RPT * PCL_TH;
     if (nb > PCL_NB || m > 16 * R || m <= 0) return false;
     const int ni = (int)nb;
-    if (m <= 2 * R) return launch_panel_cluster<T, 2, RPT, PCL_TH>(c, m, ni, A, lda, ipiv, r0);
-    if (m <= 4 * R) return launch_panel_cluster<T, 4, RPT, PCL_TH>(c, m, ni, A, lda, ipiv, r0);
-    if (m <= 8 * R) return launch_panel_cluster<T, 8, RPT, PCL_TH>(c, m, ni, A, lda, ipiv, r0);
-    return launch_panel_cluster<T, 16, RPT, PCL_TH>(c, m, ni, A, lda, ipiv, r0);
+    if (m <= 2 * R) return launch_panel_cluster<2, RPT, PCL_TH>(c, m, ni, A, lda, ipiv, r0);
+    if (m <= 4 * R) return launch_panel_cluster<4, RPT, PCL_TH>(c, m, ni, A, lda, ipiv, r0);
+    if (m <= 8 * R) return launch_panel_cluster<8, RPT, PCL_TH>(c, m, ni, A, lda, ipiv, r0);
+    return launch_panel_cluster<16, RPT, PCL_TH>(c, m, ni, A, lda, ipiv, r0);
     }
 }
 
