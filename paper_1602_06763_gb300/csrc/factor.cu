@@ -792,7 +792,7 @@ k_panel_cluster(i64 m, int nb, float *A, i64 lda, int32_t *ipiv, i64 r0, int32_t
     __shared__ uint32_t wk[2][NW];
     __shared__ int wi[2][NW];
     __shared__ int s_p[PCL_NB];                   // p_j (rank 0, for the deferred interchanges)
-    __shared__ int s_slot[PCL_NB];                // fix-up slot of row p_j
+    __shared__ unsigned char gsrc[PCL_NB][2 * PCL_NB];   // fix-up source slots per column
     __shared__ int s_row[2 * PCL_NB];             // fix-up slot -> row (-1: unused)
     __shared__ T fix[2 * PCL_NB][PCL_NB + 1];
     __shared__ int s_skip, s_tmo;
@@ -815,17 +815,19 @@ k_panel_cluster(i64 m, int nb, float *A, i64 lda, int32_t *ipiv, i64 r0, int32_t
         cl.sync();                                // rank 0's word is read before it exits
         return;
     }
-    const i64 rbeg = (i64)q * R;
+    // row indices fit an int: the cluster holds at most 16 R rows
+    const int rbeg = q * R;
+    const int mi = (int)m;
     T a[RPT][PCL_NB];
-    i64 gi[RPT];
+    int gi[RPT];
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
-        gi[k] = rbeg + tid + (i64)k * TH;
+        gi[k] = rbeg + tid + k * TH;
 #pragma unroll
         for (int c = 0; c < PCL_NB; ++c)
-            a[k][c] = (gi[k] < m && c < nb) ? A[(i64)c * lda + gi[k]] : T(0);
+            a[k][c] = (gi[k] < mi && c < nb) ? A[(i64)c * lda + gi[k]] : T(0);
     }
-    const int mn = (int)min(m, (i64)nb);
+    const int mn = min(mi, nb);
     int tmo = 0;
     int j = 0;
 #pragma unroll 1
@@ -838,9 +840,9 @@ k_panel_cluster(i64 m, int nb, float *A, i64 lda, int32_t *ipiv, i64 r0, int32_t
         int bi = PANEL_NONE;
 #pragma unroll
         for (int k = 0; k < RPT; ++k)
-            if (gi[k] < m && gi[k] >= j) {
+            if (gi[k] < mi && gi[k] >= j) {
                 const uint32_t key = pcl_key(a[k][0]);
-                if (key > bk || bi == PANEL_NONE) { bk = key; bi = (int)gi[k]; }
+                if (key > bk || bi == PANEL_NONE) { bk = key; bi = gi[k]; }
             }
         pcl_warp_best(bk, bi);
         if (lane == 0) { wk[b][warp] = bk; wi[b][warp] = bi; }
@@ -850,7 +852,7 @@ k_panel_cluster(i64 m, int nb, float *A, i64 lda, int32_t *ipiv, i64 r0, int32_t
         bk = lane < NW ? wk[b][lane] : 0u;
         bi = lane < NW ? wi[b][lane] : PANEL_NONE;
         pcl_warp_best(bk, bi);
-        const int lr = bi != PANEL_NONE ? (int)(bi - rbeg) : 0;   // owner: thread lr % TH, window lr / TH
+        const int lr = bi != PANEL_NONE ? bi - rbeg : 0;   // owner: thread lr % TH, window lr / TH
         if (warp == (lr % TH) >> 5) {
             PclRec &mine = recs[b][q];
             if (lane == 0) { mine.key = bk; mine.row = bi; }
@@ -920,28 +922,46 @@ k_panel_cluster(i64 m, int nb, float *A, i64 lda, int32_t *ipiv, i64 r0, int32_t
         // 5. divide column j and store it, update the rest while the window
         // shifts by one (register c - 1 receives column j + c); blocks of four
         // columns past nb are skipped (j and nb are uniform), the entries past
-        // nb inside a block are never stored
+        // nb inside a block are never stored.  Rows at or above j exist only
+        // in rank 0's warp 0 (k = 0): every other warp updates all its rows
+        // (those past m are never stored) without a per-element select.
         const bool dov = piv != T(0);
         bool below[RPT];
         T l[RPT];
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
-            below[k] = dov && gi[k] < m && gi[k] > j;
+            below[k] = dov && gi[k] < mi && gi[k] > j;
             l[k] = below[k] ? a[k][0] / piv : T(0);
             if (below[k]) a[k][0] = l[k];
-            if (gi[k] < m) A[(i64)j * lda + gi[k]] = a[k][0];
+            if (gi[k] < mi) A[(i64)j * lda + gi[k]] = a[k][0];
         }
+        if (dov && !(q == 0 && warp == 0)) {
 #pragma unroll
-        for (int c4 = 0; c4 < PCL_NB / 4; ++c4) {
-            if (j + 4 * c4 < nb) {
-                const float4 u4 = reinterpret_cast<const float4 *>(urow)[c4];
-                const T u[4] = {u4.x, u4.y, u4.z, u4.w};
+            for (int c4 = 0; c4 < PCL_NB / 4; ++c4) {
+                if (j + 4 * c4 < nb) {
+                    const float4 u4 = reinterpret_cast<const float4 *>(urow)[c4];
+                    const T u[4] = {u4.x, u4.y, u4.z, u4.w};
 #pragma unroll
-                for (int e = (c4 == 0 ? 1 : 0); e < 4; ++e) {
-                    const int c = 4 * c4 + e;
+                    for (int e = (c4 == 0 ? 1 : 0); e < 4; ++e) {
+                        const int c = 4 * c4 + e;
 #pragma unroll
-                    for (int k = 0; k < RPT; ++k)
-                        a[k][c - 1] = below[k] ? fma(-l[k], u[e], a[k][c]) : a[k][c];
+                        for (int k = 0; k < RPT; ++k) a[k][c - 1] = fma(-l[k], u[e], a[k][c]);
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int c4 = 0; c4 < PCL_NB / 4; ++c4) {
+                if (j + 4 * c4 < nb) {
+                    const float4 u4 = reinterpret_cast<const float4 *>(urow)[c4];
+                    const T u[4] = {u4.x, u4.y, u4.z, u4.w};
+#pragma unroll
+                    for (int e = (c4 == 0 ? 1 : 0); e < 4; ++e) {
+                        const int c = 4 * c4 + e;
+#pragma unroll
+                        for (int k = 0; k < RPT; ++k)
+                            a[k][c - 1] = below[k] ? fma(-l[k], u[e], a[k][c]) : a[k][c];
+                    }
                 }
             }
         }
@@ -955,7 +975,7 @@ k_panel_cluster(i64 m, int nb, float *A, i64 lda, int32_t *ipiv, i64 r0, int32_t
     if (j == mn) {
 #pragma unroll
         for (int k = 0; k < RPT; ++k)
-            if (gi[k] < m) {
+            if (gi[k] < mi) {
 #pragma unroll
                 for (int c = 0; c < PCL_NB; ++c)
                     if (mn + c < nb) A[(i64)(mn + c) * lda + gi[k]] = a[k][c];
@@ -964,14 +984,29 @@ k_panel_cluster(i64 m, int nb, float *A, i64 lda, int32_t *ipiv, i64 r0, int32_t
     cl.sync();                                    // every finished column is in A; no record is in flight
     if (q != 0 || s_tmo) return;
     // deferred interchanges of the finished columns: column c takes those of
-    // the steps after c.  Rows 0 .. mn-1 are slots 0 .. mn-1, a row p_t >= mn
-    // slot PCL_NB + (first step with that row); gather, interchange, scatter.
+    // the steps t = c+1 .. mn-1.  Rows 0 .. mn-1 are slots 0 .. mn-1, a row
+    // p_t >= mn slot PCL_NB + (first step with that row).  With tau_t the
+    // interchange of slots t and slot(p_t), the entry that ends in slot s of
+    // column c starts in slot g_c(s) = tau_{c+1}(g_{c+1}(s)), g_{mn-1} = id:
+    // warp 0 builds the tables g_c while the CTA gathers the slots' entries,
+    // then every entry is written once from its source.
     if (warp == 0) {
         s_row[lane] = lane < mn ? lane : -1;
         const int pt = lane < mn ? s_p[lane] : -1 - lane;
         const int first = __ffs(__match_any_sync(0xffffffffu, pt)) - 1;
         s_row[PCL_NB + lane] = (lane < mn && pt >= mn && first == lane) ? pt : -1;
-        if (lane < mn) s_slot[lane] = pt < mn ? pt : PCL_NB + first;
+        const int slot = pt < mn ? pt : PCL_NB + first;    // slot of p_lane (lanes < mn)
+        int g0 = lane, g1 = PCL_NB + lane;
+        gsrc[mn > 0 ? mn - 1 : 0][lane] = (unsigned char)g0;
+        gsrc[mn > 0 ? mn - 1 : 0][PCL_NB + lane] = (unsigned char)g1;
+        for (int c = mn - 2; c >= 0; --c) {
+            const int t = c + 1;
+            const int st = __shfl_sync(0xffffffffu, slot, t);
+            g0 = g0 == t ? st : (g0 == st ? t : g0);
+            g1 = g1 == t ? st : (g1 == st ? t : g1);
+            gsrc[c][lane] = (unsigned char)g0;
+            gsrc[c][PCL_NB + lane] = (unsigned char)g1;
+        }
     }
     __syncthreads();
     for (int e = tid; e < 2 * PCL_NB * PCL_NB; e += TH) {
@@ -980,22 +1015,13 @@ k_panel_cluster(i64 m, int nb, float *A, i64 lda, int32_t *ipiv, i64 r0, int32_t
         if (r >= 0 && c < mn) fix[sl][c] = __ldcg(&A[(i64)c * lda + r]);
     }
     __syncthreads();
-    if (tid < mn) {
-        const int c = tid;
-        for (int t = c + 1; t < mn; ++t) {
-            const int sp = s_slot[t];
-            if (sp != t) {
-                const T x = fix[t][c];
-                fix[t][c] = fix[sp][c];
-                fix[sp][c] = x;
-            }
-        }
-    }
-    __syncthreads();
     for (int e = tid; e < 2 * PCL_NB * PCL_NB; e += TH) {
         const int sl = e / PCL_NB, c = e % PCL_NB;
         const int r = s_row[sl];
-        if (r > c && c < mn) A[(i64)c * lda + r] = fix[sl][c];
+        if (r > c && c < mn) {
+            const int src = gsrc[c][sl];
+            if (src != sl) A[(i64)c * lda + r] = fix[src][c];
+        }
     }
 }
 
@@ -1043,25 +1069,25 @@ static bool launch_panel_cluster(Ctx &c, i64 m, int nb, float *A, i64 lda, int32
     return true;
 }
 
-// The cluster panel serves FP32 panels: 256 threads per CTA, a window of four
-// rows of 32 floats per thread.  (FP64 panels measured slower on it
-// than on the cooperative kernel and keep that one.)
-constexpr int PCL_TH = 256;
-
+// The cluster panel serves FP32 panels of up to 16384 rows.  Fewer rows per
+// CTA shorten the per-column update, which bounds the step, more CTAs
+// lengthen the exchange a little, more warps per CTA hide latency: one row
+// per thread on 256 threads up to 2048 rows, 512 threads above, two rows per
+// thread past 8192 (measured per column on GB300).
 template <typename T>
 static bool panel_cluster(Ctx &c, i64 m, i64 nb, T *A, i64 lda, int32_t *ipiv, i64 r0)
 {
     if constexpr (sizeof(T) != 4) {
         return false;
     } else {
-    constexpr int RPT = 4;
-    constexpr i64 R = (i64)RPT * PCL_TH;
-    if (nb > PCL_NB || m > 16 * R || m <= 0) return false;
+    if (nb > PCL_NB || m > 16 * 1024 || m <= 0) return false;
     const int ni = (int)nb;
-    if (m <= 2 * R) return launch_panel_cluster<2, RPT, PCL_TH>(c, m, ni, A, lda, ipiv, r0);
-    if (m <= 4 * R) return launch_panel_cluster<4, RPT, PCL_TH>(c, m, ni, A, lda, ipiv, r0);
-    if (m <= 8 * R) return launch_panel_cluster<8, RPT, PCL_TH>(c, m, ni, A, lda, ipiv, r0);
-    return launch_panel_cluster<16, RPT, PCL_TH>(c, m, ni, A, lda, ipiv, r0);
+    if (m <= 2 * 256) return launch_panel_cluster<2, 1, 256>(c, m, ni, A, lda, ipiv, r0);
+    if (m <= 4 * 256) return launch_panel_cluster<4, 1, 256>(c, m, ni, A, lda, ipiv, r0);
+    if (m <= 8 * 256) return launch_panel_cluster<8, 1, 256>(c, m, ni, A, lda, ipiv, r0);
+    if (m <= 8 * 512) return launch_panel_cluster<8, 1, 512>(c, m, ni, A, lda, ipiv, r0);
+    if (m <= 16 * 512) return launch_panel_cluster<16, 1, 512>(c, m, ni, A, lda, ipiv, r0);
+    return launch_panel_cluster<16, 2, 512>(c, m, ni, A, lda, ipiv, r0);
     }
 }
 
