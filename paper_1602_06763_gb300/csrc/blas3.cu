@@ -547,19 +547,46 @@ enum TriOp { TRI_FWD = 0, TRI_BWD = 1, TRI_MUL = 2 };
 
 __device__ __forceinline__ int tri_ix(int i, int k) { return i * (i + 1) / 2 + k; }
 
+// One element global -> shared without a register round trip; src_ok false
+// fills the element with zero bytes (src is then not read).  The copies of
+// a thread land once it passes tri_copies_wait.
+template <typename T>
+__device__ __forceinline__ void tri_copy(T *dst, const T *src, bool src_ok)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "n"((int)sizeof(T)), "r"(src_ok ? (int)sizeof(T) : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tri_copies_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Stage the order-n triangle of Tm (lower if !TRANS_UPPER, else the upper
 // triangle stored transposed) into P, padded with identity up to NB.
 template <typename T, int NB, bool TRANS_UPPER, bool CONJ = false>
 __device__ __forceinline__ void stage_tri(T *P, const T *Tm, i64 ldt, int n, bool unit)
 {
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    // every thread issues all its loads before its first store (a rolled
+    // loop would wait for one memory round trip per element)
+    constexpr int PER = (NB * NB + TRI_THREADS - 1) / TRI_THREADS;
+    T v[PER];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int e = threadIdx.x + r * TRI_THREADS;
         const int i = e % NB, k = e / NB;
-        if (i < k) continue;
-        T v;
-        if (i < n && k < n) v = TRANS_UPPER ? Tm[(i64)i * ldt + k] : Tm[(i64)k * ldt + i];
-        else v = (i == k) ? T(1) : T(0);
-        if (unit && i == k) v = T(1);
-        P[tri_ix(i, k)] = CONJ ? cj(v) : v;
+        v[r] = T(0);
+        if (e < NB * NB && i >= k) {
+            if (i < n && k < n) v[r] = TRANS_UPPER ? Tm[(i64)i * ldt + k] : Tm[(i64)k * ldt + i];
+            else v[r] = (i == k) ? T(1) : T(0);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int e = threadIdx.x + r * TRI_THREADS;
+        const int i = e % NB, k = e / NB;
+        if (e < NB * NB && i >= k) {
+            T w = (unit && i == k) ? T(1) : v[r];
+            P[tri_ix(i, k)] = CONJ ? cj(w) : w;
+        }
     }
 }
 
@@ -634,6 +661,89 @@ k_tri(i64 nvec, int n, T alpha, const T *__restrict__ Tm, i64 ldt, T *B, i64 ldb
     }
 }
 
+// Forward substitution (the TRI_FWD form of k_tri, real types) with a body
+// the instruction cache holds: the steps run in a rolled loop over blocks of
+// four (j = 4s .. 4s+3), and the lane's elements live in a window that
+// shifts by one per block (x[t] holds element 4(s + t) + q), so every
+// register index stays a compile-time constant.  An element is final, and
+// stored, when its block ends.  The triangle is staged column by column,
+// P[j * LDP + k] = M(k, j) (zero above the diagonal and in the LDP - NB
+// padding rows), so the reads of one step are immediate offsets from one
+// base.  Elements past the order read the padding and are never stored;
+// chunks of four window entries wholly past NB are skipped (s is uniform).
+// Same operations per element, in the same order, as k_tri (bit-identical).
+template <typename T, int NB, bool ROWS, bool UNIT, bool TRANS_UPPER>
+__global__ void __launch_bounds__(TRI_THREADS)
+k_tri_fwd(i64 nvec, int n, T alpha, const T *__restrict__ Tm, i64 ldt, T *B, i64 ldb, const int32_t *abort)
+{
+    if (abort && *abort != 0) return;
+    constexpr int E = NB / 4, LDP = NB + 16;
+    static_assert(E % 4 == 0, "order a multiple of 16");
+    __shared__ T P[NB * LDP];
+    {
+        // every element in flight at once (cp.async, zero-filled outside the
+        // stored triangle), then each thread sets the unit diagonal entries
+        // of its own elements
+        constexpr int PER = NB * LDP / TRI_THREADS;
+        static_assert(NB * LDP % TRI_THREADS == 0, "whole rounds");
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int e = threadIdx.x + r * TRI_THREADS;
+            const int k = e % LDP, j = e / LDP;    // element M(k, j)
+            const bool ld = k < n && j < n && k >= j && !(UNIT && k == j);
+            tri_copy(&P[e], ld ? (TRANS_UPPER ? Tm + (i64)k * ldt + j : Tm + (i64)j * ldt + k) : Tm, ld);
+        }
+        tri_copies_wait();
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int e = threadIdx.x + r * TRI_THREADS;
+            const int k = e % LDP, j = e / LDP;
+            if (k == j && (UNIT || k >= n)) P[e] = T(1);
+        }
+    }
+    __syncthreads();
+    const int q = threadIdx.x & 3;
+    const int gbase = threadIdx.x & 28;              // first lane of this group
+    const i64 v = (i64)blockIdx.x * TRI_VECS + (threadIdx.x >> 2);
+    const bool live = v < nvec;
+    T x[E];
+#pragma unroll
+    for (int t = 0; t < E; ++t) {
+        const int e = 4 * t + q;
+        T b = T(0);
+        if (live && e < n) b = ROWS ? B[(i64)e * ldb + v] : B[v * ldb + e];
+        x[t] = alpha * b;
+    }
+#pragma unroll 1
+    for (int s = 0; s < E; ++s) {
+#pragma unroll
+        for (int own = 0; own < 4; ++own) {
+            const int j = 4 * s + own;
+            const T *col = P + j * LDP + 4 * s + q;    // M(4(s + t) + q, j) at col[4t]
+            if (!UNIT && q == own) x[0] = x[0] / P[j * LDP + j];
+            const T xj = __shfl_sync(0xffffffffu, x[0], gbase | own);
+            if (q > own) x[0] = fma(-xj, col[0], x[0]);
+#pragma unroll
+            for (int c = 0; c < E / 4; ++c) {
+                if (s + 4 * c < E) {
+#pragma unroll
+                    for (int tt = (c == 0 ? 1 : 0); tt < 4; ++tt) {
+                        const int t = 4 * c + tt;
+                        x[t] = fma(-xj, col[4 * t], x[t]);
+                    }
+                }
+            }
+        }
+        const int e = 4 * s + q;
+        if (live && e < n) {
+            if (ROWS) B[(i64)e * ldb + v] = x[0];
+            else B[v * ldb + e] = x[0];
+        }
+#pragma unroll
+        for (int t = 0; t + 1 < E; ++t) x[t] = x[t + 1];
+    }
+}
+
 // Two lanes per vector: lane q of a pair holds elements e = 2t + q in
 // registers.  The triangle M (order n, identity-padded to NB) is staged as a
 // full square with a padded row stride so that every access in the
@@ -653,14 +763,26 @@ k_tri2(i64 nvec, int n, T alpha, const T *__restrict__ Tm, i64 ldt, T *B, i64 ld
     if (abort && *abort != 0) return;
     constexpr int E = NB / 2, RS = NB + 1;
     __shared__ T S[NB * RS];
-    for (int idx = threadIdx.x; idx < NB * NB; idx += THREADS) {
-        const int k = idx % NB, i = idx / NB;          // element M(i, k)
-        T v;
-        if (i < n && k < n) v = (k > i) ? T(0) : (TRANS_UPPER ? Tm[(i64)i * ldt + k] : Tm[(i64)k * ldt + i]);
-        else v = (i == k) ? T(1) : T(0);
-        if (UNIT && i == k) v = T(1);
-        const int a = (OP == TRI_FWD) ? ((i & 1) * E * RS + (i >> 1) * RS + k) : (i * RS + k);
-        S[a] = v;
+    {
+        // all loads in flight before the first store
+        constexpr int PER = NB * NB / THREADS;
+        static_assert(NB * NB % THREADS == 0, "whole rounds");
+        T w[PER];
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int idx = threadIdx.x + r * THREADS;
+            const int k = idx % NB, i = idx / NB;      // element M(i, k)
+            if (i < n && k < n) w[r] = (k > i) ? T(0) : (TRANS_UPPER ? Tm[(i64)i * ldt + k] : Tm[(i64)k * ldt + i]);
+            else w[r] = (i == k) ? T(1) : T(0);
+            if (UNIT && i == k) w[r] = T(1);
+        }
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int idx = threadIdx.x + r * THREADS;
+            const int k = idx % NB, i = idx / NB;
+            const int a = (OP == TRI_FWD) ? ((i & 1) * E * RS + (i >> 1) * RS + k) : (i * RS + k);
+            S[a] = w[r];
+        }
     }
     __syncthreads();
     const int q = threadIdx.x & 1;
@@ -758,6 +880,18 @@ static void launch_tri(Ctx &c, int kind, i64 nvec, int n, T alpha, const T *Tm, 
             if (n <= 16) launch_tri2<T, 16, OP, ROWS, UNIT, TRANS_UPPER>(c, nvec, n, alpha, Tm, ldt, B, ldb);
             else if (n <= 32) launch_tri2<T, 32, OP, ROWS, UNIT, TRANS_UPPER>(c, nvec, n, alpha, Tm, ldt, B, ldb);
             else launch_tri2<T, 64, OP, ROWS, UNIT, TRANS_UPPER>(c, nvec, n, alpha, Tm, ldt, B, ldb);
+            return;
+        }
+        if constexpr (OP == TRI_FWD) {
+            if (n <= 16)
+                k_tri_fwd<T, 16, ROWS, UNIT, TRANS_UPPER><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, Tm, ldt, B,
+                                                                                       ldb, c.abort);
+            else if (n <= 32)
+                k_tri_fwd<T, 32, ROWS, UNIT, TRANS_UPPER><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, Tm, ldt, B,
+                                                                                       ldb, c.abort);
+            else
+                k_tri_fwd<T, 64, ROWS, UNIT, TRANS_UPPER><<<grid, TRI_THREADS, 0, c.s>>>(nvec, n, alpha, Tm, ldt, B,
+                                                                                       ldb, c.abort);
             return;
         }
     }
