@@ -565,27 +565,49 @@ __device__ __forceinline__ void tri_copies_wait() { asm volatile("cp.async.wait_
 template <typename T, int NB, bool TRANS_UPPER, bool CONJ = false>
 __device__ __forceinline__ void stage_tri(T *P, const T *Tm, i64 ldt, int n, bool unit)
 {
-    // every thread issues all its loads before its first store (a rolled
-    // loop would wait for one memory round trip per element)
     constexpr int PER = (NB * NB + TRI_THREADS - 1) / TRI_THREADS;
-    T v[PER];
+    if constexpr (!is_cplx<T>::value) {
+        // real types: every element in flight at once (cp.async, zero-filled
+        // outside the stored triangle), then each thread sets the unit
+        // diagonal entries of its own elements
 #pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        const int e = threadIdx.x + r * TRI_THREADS;
-        const int i = e % NB, k = e / NB;
-        v[r] = T(0);
-        if (e < NB * NB && i >= k) {
-            if (i < n && k < n) v[r] = TRANS_UPPER ? Tm[(i64)i * ldt + k] : Tm[(i64)k * ldt + i];
-            else v[r] = (i == k) ? T(1) : T(0);
+        for (int r = 0; r < PER; ++r) {
+            const int e = threadIdx.x + r * TRI_THREADS;
+            const int i = e % NB, k = e / NB;
+            if (e < NB * NB && i >= k) {
+                const bool ld = i < n && k < n && !(unit && i == k);
+                tri_copy(&P[tri_ix(i, k)], ld ? (TRANS_UPPER ? Tm + (i64)i * ldt + k : Tm + (i64)k * ldt + i) : Tm,
+                         ld);
+            }
         }
-    }
+        tri_copies_wait();
 #pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        const int e = threadIdx.x + r * TRI_THREADS;
-        const int i = e % NB, k = e / NB;
-        if (e < NB * NB && i >= k) {
-            T w = (unit && i == k) ? T(1) : v[r];
-            P[tri_ix(i, k)] = CONJ ? cj(w) : w;
+        for (int r = 0; r < PER; ++r) {
+            const int e = threadIdx.x + r * TRI_THREADS;
+            const int i = e % NB, k = e / NB;
+            if (e < NB * NB && i == k && (unit || i >= n)) P[tri_ix(i, k)] = T(1);
+        }
+    } else {
+        // complex: all loads into registers before the first store
+        T v[PER];
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int e = threadIdx.x + r * TRI_THREADS;
+            const int i = e % NB, k = e / NB;
+            v[r] = T(0);
+            if (e < NB * NB && i >= k) {
+                if (i < n && k < n) v[r] = TRANS_UPPER ? Tm[(i64)i * ldt + k] : Tm[(i64)k * ldt + i];
+                else v[r] = (i == k) ? T(1) : T(0);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int e = threadIdx.x + r * TRI_THREADS;
+            const int i = e % NB, k = e / NB;
+            if (e < NB * NB && i >= k) {
+                T w = (unit && i == k) ? T(1) : v[r];
+                P[tri_ix(i, k)] = CONJ ? cj(w) : w;
+            }
         }
     }
 }
@@ -764,24 +786,26 @@ k_tri2(i64 nvec, int n, T alpha, const T *__restrict__ Tm, i64 ldt, T *B, i64 ld
     constexpr int E = NB / 2, RS = NB + 1;
     __shared__ T S[NB * RS];
     {
-        // all loads in flight before the first store
+        // every element in flight at once (cp.async, zero-filled outside the
+        // stored triangle), then each thread sets the unit diagonal entries
+        // of its own elements
         constexpr int PER = NB * NB / THREADS;
         static_assert(NB * NB % THREADS == 0, "whole rounds");
-        T w[PER];
 #pragma unroll
         for (int r = 0; r < PER; ++r) {
             const int idx = threadIdx.x + r * THREADS;
             const int k = idx % NB, i = idx / NB;      // element M(i, k)
-            if (i < n && k < n) w[r] = (k > i) ? T(0) : (TRANS_UPPER ? Tm[(i64)i * ldt + k] : Tm[(i64)k * ldt + i]);
-            else w[r] = (i == k) ? T(1) : T(0);
-            if (UNIT && i == k) w[r] = T(1);
+            const int a = (OP == TRI_FWD) ? ((i & 1) * E * RS + (i >> 1) * RS + k) : (i * RS + k);
+            const bool ld = i < n && k < n && k <= i && !(UNIT && i == k);
+            tri_copy(&S[a], ld ? (TRANS_UPPER ? Tm + (i64)i * ldt + k : Tm + (i64)k * ldt + i) : Tm, ld);
         }
+        tri_copies_wait();
 #pragma unroll
         for (int r = 0; r < PER; ++r) {
             const int idx = threadIdx.x + r * THREADS;
             const int k = idx % NB, i = idx / NB;
             const int a = (OP == TRI_FWD) ? ((i & 1) * E * RS + (i >> 1) * RS + k) : (i * RS + k);
-            S[a] = w[r];
+            if (i == k && (UNIT || i >= n)) S[a] = T(1);
         }
     }
     __syncthreads();
